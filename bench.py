@@ -1,0 +1,302 @@
+"""Benchmark of the semistochastic local-energy path on the H50-shaped chain.
+
+One step = one nqs_local_energy call over the whole batch (environments,
+enumeration and Slater-Condon H_nm, the eps split, Philox draws, amplitudes
+of every deterministic and drawn determinant, the E_loc sums). Inputs are
+synthetic (seeded), resident in HBM before the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+  python bench.py --impl reference ...   # the CPU oracle, bounded sample per step
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2507_19276_gb300 import workloads as W  # noqa: E402
+
+METRIC = "E_loc samples/s (H50 shape)"
+UNIT = "samples/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP64 FMA throughput of one GB300, measured with a dependent-chain-free DFMA
+# probe ("FP64 peak"); used as the ALU roofline of the FP64 form.
+FP64_PEAK_TFLOPS = 1.25
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws, device=None):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_rate(sys_, n_samples, threads):
+    """The oracle, as it stands, on the first n_samples of the batch."""
+    from oracle import oracle as O
+    P = O.Problem(sys_.subset(range(n_samples)))
+    t0 = time.perf_counter()
+    O.local_energy(P, threads=threads)
+    dt = time.perf_counter() - t0
+    return n_samples / dt, dt
+
+
+def workload_config(sys_, precision):
+    return {"workload": f"h50_chain K={sys_.K} {sys_.n_alpha}a+{sys_.n_beta}b D={sys_.D} "
+                        f"N_h={sys_.n_hidden} Ns={len(sys_.samples)} eps={sys_.eps:g} "
+                        f"N_eps={sys_.n_draws}",
+            "K": sys_.K, "D": sys_.D, "n_hidden": sys_.n_hidden, "samples": len(sys_.samples),
+            "eps": sys_.eps, "n_draws": sys_.n_draws, "precision": precision,
+            "l2": "working set > L2 (deterministic lists ~2.5 GB per step)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    sys_ = W.h50_chain()
+    cores = os.cpu_count() or 1
+    per_step = max(2, cores)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(sys_, per_step, cores)
+    t = 0.0
+    for _ in range(args.steps):
+        _, dt = cpu_oracle_rate(sys_, per_step, cores)
+        t += dt
+    v = per_step * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(sys_, "fp64-oracle"),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"first {per_step} of {len(sys_.samples)} samples per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run(args):
+    import torch
+    from paper_2507_19276_gb300 import nqs
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sys_ = W.h50_chain(seed_offset=rank, n_samples=args.samples)
+    Ns = len(sys_.samples)
+    ctx = nqs.Context(local)
+    ctx.set_system(sys_)
+    prec = nqs.NQS_PREC_MIXED if args.precision == "mixed" else nqs.NQS_PREC_FP64
+    ctx.set_precision(prec, timing=True)
+
+    samples = torch.from_numpy(sys_.samples.view(np.int64)).to(dev)
+    counts = torch.from_numpy(sys_.counts).to(dev)
+    e_loc = torch.empty(Ns, dtype=torch.float64, device=dev)
+
+    def step(summary=None):
+        nqs.nqs_local_energy(ctx.h, samples, counts, Ns, sys_.eps, sys_.n_draws, sys_.seed, e_loc,
+                             summary)
+
+    summ = nqs.EnergySummary()
+    for _ in range(args.warmup):
+        step(summ)
+    torch.cuda.synchronize()
+    ctx.stage_times()   # reset counters
+
+    stream = torch.cuda.current_stream(dev)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    start.record(stream)
+    for _ in range(args.steps):
+        step()
+    stop.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(ws)
+    ms = start.elapsed_time(stop)
+    stages = ctx.stage_times()
+    ms = max_over_ranks(ms, ws, dev)
+    value = ws * Ns * args.steps / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    hs = torch.from_numpy(sys_.samples.view(np.int64)).pin_memory()
+    hc = torch.from_numpy(sys_.counts).pin_memory()
+    he = torch.empty(Ns, dtype=torch.float64).pin_memory()
+    nqs.nqs_local_energy(ctx.h, hs, hc, Ns, sys_.eps, sys_.n_draws, sys_.seed, he, None)
+    torch.cuda.synchronize()
+    ctx.stage_times()
+    barrier(ws)
+    t0 = time.perf_counter()
+    start.record(stream)
+    for _ in range(args.steps):
+        nqs.nqs_local_energy(ctx.h, hs, hc, Ns, sys_.eps, sys_.n_draws, sys_.seed, he, None)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max(start.elapsed_time(stop), 1e3 * (time.perf_counter() - t0))
+    e2e_ms = max_over_ranks(e2e_ms, ws, dev)
+    ctx.stage_times()
+
+    # roofline of the dominant kernel (amplitudes of the deterministic rows)
+    peaks, src = _peaks()
+    amp_ms, amp_launch = stages["amp_det"]
+    work = summ.as_dict()
+    n_amp = work["n_amplitudes"]
+    span = work.get("span_sites", 0)
+    D = sys_.D
+    flops = 2.0 * D * D * span + 2.0 * D * n_amp       # per step
+    if prec == nqs.NQS_PREC_MIXED:
+        peak = peaks["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "unit": "TFLOP/s",
+                "peak_source": f"{src} bf16 dense (sustained), same rate as fp16 dense"}
+    else:
+        peak = FP64_PEAK_TFLOPS
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak_source": "FP64 DFMA probe (DESIGN.md)"}
+    amp_ms_per_step = (stages["amp_det"][0] + stages["amp_draw"][0]) / args.steps
+    achieved = flops / (amp_ms_per_step / 1e3) / 1e12 if amp_ms_per_step > 0 else 0.0
+    roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
+                 "traffic": None, "kernel": "amplitudes (deterministic + drawn rows)",
+                 "algorithmic_flops_per_step": flops})
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16x3->f32 tensor + f64" if prec == nqs.NQS_PREC_MIXED else "f64",
+            "data": "synthetic", "config": workload_config(sys_, args.precision),
+            "connected_dets_per_s": value * work["n_conn"],
+            "amplitudes_per_s": ws * n_amp * args.steps / (ms / 1e3),
+            "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+            "roofline": roof,
+            "e2e": {"value": ws * Ns * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": Ns * 16 + Ns * 8, "d2h_bytes_per_step": Ns * 8},
+            "clocks": clk,
+            "gpu_launches": int(sum(v[1] for v in stages.values())),
+            "summary": {"e_mean": work["e_mean"], "n_det": work["n_det"],
+                        "n_draw_unique": work["n_draw_unique"]}}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        n_cpu = max(2, min(cores, 16))
+        rate, dt = cpu_oracle_rate(sys_, n_cpu, cores)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"first {n_cpu} of {Ns} samples ({dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--samples", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * nqs.h -- C ABI of the GB300 semistochastic local-energy library.
+ *
+ * Computes, for sampled occupation-number vectors n, the local energy of
+ * Sec. 2.1, Eq. (exactElocal):  E_loc(n) = sum_m H_nm psi(m) / psi(n),
+ * with H from Eq. (Ham) evaluated by the Slater-Condon rules (Sec. 3) and the
+ * semistochastic split of Sec. 2.4: E_loc = E^d(n, eps) + E^s(n, eps, N_eps),
+ * E^d summing every off-diagonal m with |H_nm| >= eps (the diagonal is always
+ * exact) and E^s averaging N_eps draws m' ~ P_n(m') proportional to |H_nm'|
+ * over the remainder |H_nm'| < eps. psi = psi_TN * f is a tensor network
+ * (Eq. MPS-RNN-1D with v = 0 for a chain; Eq. bdg-rnn-update without the
+ * tensor term for a graph) times an RBM correlator (Eq. RBM, 2cosh form).
+ *
+ * Conventions
+ *  - K <= 64 spatial orbitals; spin orbital s = 2p + spin (alpha 0, beta 1),
+ *    the interleaved order of Sec. 3, which fixes the fermionic phases:
+ *    |n> = a+_{s1} a+_{s2} ... |0> with s1 < s2 < ...
+ *  - A determinant is two uint64 words [alpha bits, beta bits]; bit p of a
+ *    word is the occupation of spatial orbital p with that spin.
+ *  - Local state sigma_p = n_{p,alpha} + 2 n_{p,beta}.
+ *  - Connected determinants m of n are ranked 0..n_conn-1 in a canonical
+ *    order: blocks [singles alpha, singles beta, doubles alpha-alpha,
+ *    doubles beta-beta, doubles alpha-beta]; inside a block by the positions
+ *    of the orbitals among the occupied / empty orbitals of that spin
+ *    (ascending, pairs lexicographic; alpha-beta doubles ordered as
+ *    ((i_a * nv_a + a_a) * no_b + j_b) * nv_b + b_b).
+ *
+ * Memory and ownership
+ *  - The caller owns every buffer it passes. Array arguments may point to
+ *    host or device memory; the library tells them apart with
+ *    cudaPointerGetAttributes. Device arrays must be on the context's device.
+ *    Host inputs are staged to the device on the context's stream; host
+ *    outputs are copied back and the stream is synchronised before return.
+ *  - nqs_set_* copy their arguments; the caller may free them afterwards.
+ *  - Outputs are valid only when a call returns NQS_OK.
+ *  - A context is not thread safe; use one context per host thread.
+ *
+ * Errors: every call returns an nqs_status. NQS_ERR_INVALID_ARG names the
+ * offending argument (and sample index) in nqs_last_error(). Nothing aborts;
+ * device-side checks report through an error word that the host reads.
+ */
+#ifndef NQS_H
+#define NQS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NQS_OK = 0,
+    NQS_ERR_INVALID_ARG = 1,   /* bad size, pointer or determinant */
+    NQS_ERR_STATE = 2,         /* call order violated (e.g. no Hamiltonian yet) */
+    NQS_ERR_OOM = 3,           /* device allocation failed */
+    NQS_ERR_CUDA = 4,          /* a CUDA runtime call failed */
+    NQS_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+    NQS_ERR_UNSUPPORTED = 6    /* valid request this build does not handle */
+} nqs_status;
+
+typedef enum {
+    NQS_PREC_FP64 = 0,   /* every step in FP64 on CUDA cores (the plain form) */
+    NQS_PREC_MIXED = 1   /* amplitude contractions on tcgen05 tensor cores in
+                            split FP16 with FP32 accumulation; H_nm, ratios and
+                            the E_loc sums stay FP64 */
+} nqs_precision;
+
+typedef struct nqs_ctx nqs_ctx;
+
+typedef struct {
+    int precision;        /* nqs_precision */
+    int timing;           /* nonzero: time every stage with CUDA events on the
+                             context's stream (see nqs_stage_times) */
+    int reserved[14];     /* must be zero */
+} nqs_options;
+
+/* Stages of the local-energy path, as reported by nqs_stage_times. */
+enum {
+    NQS_STAGE_ENV = 0,        /* input checks, environments, psi(n), f(n), H_nn */
+    NQS_STAGE_COUNT = 1,      /* enumeration pass 1: |H| >= eps counts, max remainder |H| */
+    NQS_STAGE_WRITE = 2,      /* enumeration pass 2: deterministic list, remainder weights */
+    NQS_STAGE_DRAW = 3,       /* Philox draws, inverse CDF, de-duplication */
+    NQS_STAGE_AMP_DET = 4,    /* amplitudes and ratios of the deterministic rows */
+    NQS_STAGE_AMP_DRAW = 5,   /* amplitudes and ratios of the drawn rows */
+    NQS_STAGE_FINAL = 6,      /* E_loc sums and the weighted summary */
+    NQS_STAGE_OTHER = 7,      /* nqs_connected / nqs_amplitude / gradient work */
+    NQS_N_STAGES = 8
+};
+
+typedef struct {
+    double e_mean;          /* sum_n c_n E_loc(n) / sum_n c_n */
+    double sum_counts;      /* sum_n c_n */
+    double log_B;           /* log B, B = sum c f^2 / sum c (Sec. 2.3, real f) */
+    double e_tilde_mean;    /* sum_n c_n E~_loc(n) / sum c, E~ = f^2/B E_loc */
+    int64_t n_conn;         /* connected determinants per sample */
+    int64_t n_det;          /* sum over samples of |{m : |H_nm| >= eps}| */
+    int64_t n_draw_unique;  /* sum over samples of distinct drawn m */
+    int64_t n_amplitudes;   /* amplitudes evaluated = n_det + n_draw_unique */
+    int64_t span_sites;     /* sum over evaluated amplitudes of the number of
+                               sites (chain) or vertices (graph) recomputed; the
+                               contraction work is 2 D^2 span_sites (x in-degree) */
+} nqs_energy_summary;
+
+/* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t
+ * (NULL = the legacy default stream) on which all work of the context runs. */
+int nqs_create(nqs_ctx** out, int device, void* cuda_stream);
+
+/* Release every device buffer of the context. NULL is accepted. */
+int nqs_destroy(nqs_ctx* ctx);
+
+/* Message for the last failing call on this context ("" if none). */
+const char* nqs_last_error(const nqs_ctx* ctx);
+
+/* Select the precision of later calls (default NQS_PREC_FP64). */
+int nqs_set_options(nqs_ctx* ctx, const nqs_options* opt);
+
+/* Device time (ms) and number of kernel launches per stage, accumulated
+ * since the previous call, then reset. `ms` (may be NULL) gets the times of
+ * calls made with nqs_options.timing set; `launches` (may be NULL) counts every
+ * kernel launch of this context. Both arrays hold n entries (n <=
+ * NQS_N_STAGES). Synchronises the context's stream. */
+int nqs_stage_times(nqs_ctx* ctx, double* ms, int64_t* launches, int n);
+
+/* Hamiltonian of Eq. (Ham) in spatial orbitals.
+ *  h1e [n_orb][n_orb]: one-electron integrals h_pq (symmetric).
+ *  cholesky_or_eri: n_chol > 0: vectors L[n_chol][n_orb][n_orb], symmetric in
+ *    (p,q), and (pq|rs) = sum_x L^x_pq L^x_rs is built on the device with a
+ *    fused multiply-add chain over ascending x; n_chol == 0: the chemists'
+ *    integrals (pq|rs) as [n_orb]^4, used as given (must be 8-fold symmetric
+ *    for H_nm = H_mn to hold bitwise).
+ *  1 <= n_orb <= 64, 0 <= n_alpha, n_beta <= n_orb. e_core adds to H_nn. */
+int nqs_set_hamiltonian(nqs_ctx* ctx, const double* h1e, const double* cholesky_or_eri,
+                        int n_chol, int n_orb, int n_alpha, int n_beta, double e_core);
+
+/* Ansatz psi = psi_TN * f (Sec. 2.2-2.3).
+ *  site_tensors [n_edges][4][D][D]: edge tensors M_e^sigma[a][b] with
+ *    h_i = sum_{e=(j->i)} M_e^{sigma_i} h_j (column convention), h_{-1} = e_0,
+ *    psi_TN = (h_{K-1})_0.
+ *  pred_ptr [n_orb+1], pred_idx [n_edges]: the edges into vertex i are
+ *    pred_idx[pred_ptr[i] .. pred_ptr[i+1]) (source vertex, -1 = the boundary
+ *    vector; each source < i). Both NULL: a chain, n_edges = n_orb, edge i
+ *    joins i-1 -> i.
+ *  rbm_W [n_hidden][2*n_orb], rbm_b [n_hidden]: f = prod_k 2cosh(b_k +
+ *    sum_s W[k][s] n_s) over the interleaved spin orbitals; n_hidden = 0 and
+ *    NULL pointers: f = 1.
+ *  1 <= D <= 256; a graph needs in-degree <= 8. */
+int nqs_set_ansatz(nqs_ctx* ctx, const double* site_tensors, int n_edges, int bond_dim,
+                   const int* pred_ptr, const int* pred_idx, const double* rbm_W,
+                   const double* rbm_b, int n_hidden);
+
+/* Connected determinants with |H_mn| >= det_threshold, canonical order.
+ *  samples [Ns][2]; offsets [Ns+1] receives the start of each sample's list.
+ *  rank [capacity], dets [capacity][2], H [capacity], sign [capacity]
+ *  receive, per entry, the canonical rank, the determinant m, <m|H|n> and the
+ *  fermionic phase gamma (+1/-1) of the excitation operator.
+ *  Any of rank/dets/H/sign may be NULL. With all four NULL only offsets is
+ *  written (the sizes query). capacity < offsets[Ns] -> NQS_ERR_INVALID_ARG
+ *  with offsets written. det_threshold 0 lists every connected m. */
+int nqs_connected(nqs_ctx* ctx, const uint64_t* samples, int64_t Ns, double det_threshold,
+                  int64_t* offsets, uint32_t* rank, uint64_t* dets, double* H, int8_t* sign,
+                  int64_t capacity);
+
+/* log|psi| and sign of psi for n determinants (full K-site product, FP64
+ * whatever the precision option). sign is 0 where psi = 0. */
+int nqs_amplitude(nqs_ctx* ctx, const uint64_t* dets, int64_t n, double* log_abs,
+                  int8_t* sign);
+
+/* The stochastic draws of Sec. 2.4 for each sample (exposed for testing).
+ *  ranks [Ns][n_draws] (int64, -1 where the remainder has zero weight),
+ *  w_total [Ns] (may be NULL). Draw d of sample s (s = index in `samples`)
+ *  uses Philox4x64-10 with key (seed, 0) and counter (d, s, 0, 0); its first
+ *  output x picks t = floor(x W / 2^64), and m' is the first remainder entry
+ *  (canonical order) whose inclusive prefix of integer weights exceeds t.
+ *  Weights: w = ceil(|H| 2^shift), shift = 62 - e - bitlen(n_conn), where
+ *  max_{remainder}|H| = f 2^e with f in [0.5, 1). */
+int nqs_draws(nqs_ctx* ctx, const uint64_t* samples, int64_t Ns, double det_threshold,
+              int n_draws, uint64_t philox_seed, int64_t* ranks, uint64_t* w_total);
+
+/* Semistochastic local energy (Sec. 2.4):
+ *  E_loc(n) = H_nn + sum_{|H_nm|>=eps} H_nm r_m
+ *           + (1/N_eps) sum_d H_{m_d} (W / w_{m_d}) r_{m_d},  r_m = psi(m)/psi(n),
+ *  draws as in nqs_draws. counts [Ns] weight the summary (may be NULL: all 1).
+ *  e_loc [Ns] receives E_loc; `out` (host struct, may be NULL) the summary.
+ *  n_draws = 0 keeps only the deterministic part (biased); an empty or
+ *  zero-weight remainder gives E^s = 0. A sample with psi(n) = 0 yields
+ *  NQS_ERR_INVALID_ARG. */
+int nqs_local_energy(nqs_ctx* ctx, const uint64_t* samples, const double* counts, int64_t Ns,
+                     double det_threshold, int n_draws, uint64_t philox_seed, double* e_loc,
+                     nqs_energy_summary* out);
+
+/* Vector-Jacobian product of d log|psi(n)| / d theta (Eq. egrad):
+ *  grad = sum_n u[n] d log|psi(n)| / d theta, theta = (site tensors, W, b).
+ *  grad_sites [n_edges][4][D][D], grad_W [n_hidden][2K], grad_b [n_hidden];
+ *  outputs are overwritten (not accumulated); NULL skips one. With
+ *  u_n = 2 c_n (E_loc(n) - E_mean) / sum c this is the energy gradient. */
+int nqs_grad_log_psi_vjp(nqs_ctx* ctx, const uint64_t* samples, const double* u, int64_t Ns,
+                         double* grad_sites, double* grad_W, double* grad_b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,958 @@
+// nqs_api.cu -- the C ABI of include/nqs.h: context, parameter upload,
+// host/device pointer staging, and the order of the kernels of each call.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/nqs.h"
+#include "nqs_kernels.cuh"
+#include "nqs_mixed.cuh"
+
+using namespace nqs;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace
+
+struct nqs_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    char err[1024] = {0};
+    int precision = NQS_PREC_FP64;
+
+    bool has_ham = false;
+    int K = 0, na = 0, nb = 0;
+    int64_t n_conn = 0;
+    double e_core = 0.0;
+    HamView hv{};
+    DevBuf h1e, eri, pairs, chol;
+
+    bool has_ans = false;
+    AnsatzView av{};
+    DevBuf A, AT, W, b, pred_ptr, pred_idx;
+    MixedAnsatz mixed{};
+    DevBuf mixed_buf;
+
+    // staging and workspace
+    DevBuf st_samples, st_counts, st_u, st_out0, st_out1, st_out2, st_out3, st_out4;
+    DevBuf chunk_cnt, chunk_off, chunk_w, rem_max, det_tot, det_off, det_rank, det_coef;
+    DevBuf Lenv, Lexp, Renv, Rexp, Hst, Hexp, Gst, Gexp, theta, lc, logf, pmant, pexp, hdiag;
+    DevBuf Wtot, draw_rank64, draw_rank, draw_coef, n_unique;
+    DevBuf base_det, base_draw, part_det, part_draw, eloc, edet, estoch, summary, derr;
+    DevBuf span_det, span_draw;
+    DevBuf mixed_ws;
+
+    // stage accounting (nqs_stage_times)
+    int timing = 0;
+    double stage_ms[NQS_N_STAGES] = {0};
+    int64_t stage_launch[NQS_N_STAGES] = {0};
+    struct Pending { int stage; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> free_events;
+    cudaEvent_t open_event[NQS_N_STAGES] = {nullptr};
+};
+
+namespace {
+
+int set_err(nqs_ctx* c, int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return set_err(c, e_ == cudaErrorMemoryAllocation ? NQS_ERR_OOM : NQS_ERR_CUDA, \
+                           "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),      \
+                           __FILE__, __LINE__);                                         \
+    } while (0)
+
+#define TRY(expr)                  \
+    do {                           \
+        int r_ = (expr);           \
+        if (r_ != NQS_OK) return r_; \
+    } while (0)
+
+int ensure(nqs_ctx* c, DevBuf& b, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (b.n >= bytes) return NQS_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+    size_t want = bytes + bytes / 8;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return set_err(c, NQS_ERR_OOM, "cudaMalloc(%zu bytes) failed: %s", want,
+                       cudaGetErrorString(e));
+    }
+    b.n = want;
+    return NQS_OK;
+}
+
+void release(DevBuf& b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+}
+
+bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+int stage_in(nqs_ctx* c, DevBuf& buf, const T* p, size_t n, const T** out)
+{
+    if (!p || is_device_ptr(p)) {
+        *out = p;
+        return NQS_OK;
+    }
+    TRY(ensure(c, buf, n * sizeof(T)));
+    if (n) CK(cudaMemcpyAsync(buf.p, p, n * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    *out = (const T*)buf.p;
+    return NQS_OK;
+}
+
+// Output: device pointer as is, host pointer -> staging buffer copied back later.
+template <typename T>
+int stage_out(nqs_ctx* c, DevBuf& buf, T* p, size_t n, T** dev, bool* host)
+{
+    *host = false;
+    if (!p) {
+        *dev = nullptr;
+        return NQS_OK;
+    }
+    if (is_device_ptr(p)) {
+        *dev = p;
+        return NQS_OK;
+    }
+    TRY(ensure(c, buf, n * sizeof(T)));
+    *dev = (T*)buf.p;
+    *host = true;
+    return NQS_OK;
+}
+
+template <typename T>
+int copy_back(nqs_ctx* c, T* host, const T* dev, size_t n, bool is_host)
+{
+    if (is_host && n) CK(cudaMemcpyAsync(host, dev, n * sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+    return NQS_OK;
+}
+
+int bit_length(uint64_t x)
+{
+    int b = 0;
+    while (x) { ++b; x >>= 1; }
+    return b;
+}
+
+int64_t binom2(int64_t n) { return n * (n - 1) / 2; }
+
+int check_ready(nqs_ctx* c, bool need_ansatz)
+{
+    if (!c) return NQS_ERR_INVALID_ARG;
+    if (!c->has_ham) return set_err(c, NQS_ERR_STATE, "nqs_set_hamiltonian has not been called");
+    if (need_ansatz && !c->has_ans) return set_err(c, NQS_ERR_STATE, "nqs_set_ansatz has not been called");
+    return NQS_OK;
+}
+
+int read_dev_error(nqs_ctx* c)
+{
+    DevError e;
+    CK(cudaMemcpyAsync(&e, c->derr.p, sizeof(e), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (e.code == 0) return NQS_OK;
+    const char* what = "device check failed";
+    if (e.detail == 1) what = "sample has an occupied orbital >= n_orb";
+    else if (e.detail == 2) what = "sample has the wrong number of alpha or beta electrons";
+    else if (e.detail == 3) what = "psi(n) = 0 for sample";
+    else if (e.detail == 4) what = "device wait gave up";
+    return set_err(c, e.code, "%s (samples[%lld])", what, (long long)e.index);
+}
+
+int reset_dev_error(nqs_ctx* c)
+{
+    TRY(ensure(c, c->derr, sizeof(DevError)));
+    CK(cudaMemsetAsync(c->derr.p, 0, sizeof(DevError), c->stream));
+    return NQS_OK;
+}
+
+cudaEvent_t get_event(nqs_ctx* c)
+{
+    if (!c->free_events.empty()) {
+        cudaEvent_t e = c->free_events.back();
+        c->free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void stage_begin(nqs_ctx* c, int id)
+{
+    if (!c->timing) return;
+    c->open_event[id] = get_event(c);
+    cudaEventRecord(c->open_event[id], c->stream);
+}
+
+void stage_end(nqs_ctx* c, int id)
+{
+    if (!c->timing || !c->open_event[id]) return;
+    cudaEvent_t b = get_event(c);
+    cudaEventRecord(b, c->stream);
+    c->pending.push_back({id, c->open_event[id], b});
+    c->open_event[id] = nullptr;
+}
+
+struct StageScope {
+    nqs_ctx* c;
+    int id;
+    StageScope(nqs_ctx* c_, int id_) : c(c_), id(id_) { stage_begin(c, id); }
+    ~StageScope() { stage_end(c, id); }
+};
+
+#define LAUNCH(stage, expr) (c->stage_launch[(stage)] += (expr))
+
+__global__ void k_check_psi(const double* mant, int64_t Ns, DevError* err)
+{
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < Ns && mant[s] == 0.0) report(err, NQS_ERR_INVALID_ARG, 3, s);
+}
+
+int eps_bits(nqs_ctx* c, double eps, uint64_t* bits)
+{
+    if (!(eps >= 0.0) || !std::isfinite(eps))
+        return set_err(c, NQS_ERR_INVALID_ARG, "det_threshold must be finite and >= 0 (got %g)", eps);
+    memcpy(bits, &eps, sizeof(eps));
+    return NQS_OK;
+}
+
+// Count pass + per-sample scans: det_off (device) and the total on the host.
+int count_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, uint64_t eb, int64_t* total)
+{
+    const uint32_t nch = (uint32_t)((c->n_conn + 31) / 32);
+    TRY(ensure(c, c->chunk_cnt, (size_t)Ns * nch * 4));
+    TRY(ensure(c, c->chunk_off, (size_t)Ns * nch * 4));
+    TRY(ensure(c, c->rem_max, (size_t)Ns * 8));
+    TRY(ensure(c, c->det_tot, (size_t)Ns * 8));
+    TRY(ensure(c, c->det_off, (size_t)(Ns + 1) * 8));
+    EnumArgs a{};
+    a.h = c->hv;
+    a.samples = samples;
+    a.eps_bits = eb;
+    a.n_chunks = nch;
+    a.chunk_cnt = (uint32_t*)c->chunk_cnt.p;
+    a.rem_max_bits = (unsigned long long*)c->rem_max.p;
+    StageScope sc(c, NQS_STAGE_COUNT);
+    CK(cudaMemsetAsync(c->rem_max.p, 0, (size_t)Ns * 8, c->stream));
+    LAUNCH(NQS_STAGE_COUNT, launch_enum(a, Ns, false, c->stream));
+    CK(cudaGetLastError());
+    LAUNCH(NQS_STAGE_COUNT, launch_scan_chunks_u32((uint32_t*)c->chunk_cnt.p, (uint32_t*)c->chunk_off.p,
+                                                   (int64_t*)c->det_tot.p, Ns, nch, c->stream));
+    LAUNCH(NQS_STAGE_COUNT, launch_scan_i64((int64_t*)c->det_tot.p, (int64_t*)c->det_off.p, Ns, c->stream));
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(total, (int64_t*)c->det_off.p + Ns, 8, cudaMemcpyDeviceToHost, c->stream));
+    return NQS_OK;
+}
+
+int env_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, bool adjoints)
+{
+    const int K = c->K, D = c->av.D, NH = c->av.n_hidden;
+    EnvArgs e{};
+    e.an = c->av;
+    e.h = c->hv;
+    e.samples = samples;
+    e.Ns = Ns;
+    if (c->av.chain) {
+        TRY(ensure(c, c->Lenv, (size_t)Ns * (K + 1) * D * 8));
+        TRY(ensure(c, c->Renv, (size_t)Ns * (K + 1) * D * 8));
+        TRY(ensure(c, c->Lexp, (size_t)Ns * (K + 1) * 4));
+        TRY(ensure(c, c->Rexp, (size_t)Ns * (K + 1) * 4));
+        e.Lenv = (double*)c->Lenv.p; e.Lexp = (int*)c->Lexp.p;
+        e.Renv = (double*)c->Renv.p; e.Rexp = (int*)c->Rexp.p;
+    } else {
+        TRY(ensure(c, c->Hst, (size_t)Ns * K * D * 8));
+        TRY(ensure(c, c->Hexp, (size_t)Ns * K * 4));
+        e.Hst = (double*)c->Hst.p; e.Hexp = (int*)c->Hexp.p;
+        if (adjoints) {
+            TRY(ensure(c, c->Gst, (size_t)Ns * K * D * 8));
+            TRY(ensure(c, c->Gexp, (size_t)Ns * K * 4));
+            e.Gst = (double*)c->Gst.p; e.Gexp = (int*)c->Gexp.p;
+        }
+    }
+    TRY(ensure(c, c->theta, (size_t)Ns * (NH ? NH : 1) * 8));
+    TRY(ensure(c, c->lc, (size_t)Ns * (NH ? NH : 1) * 8));
+    TRY(ensure(c, c->logf, (size_t)Ns * 8));
+    TRY(ensure(c, c->pmant, (size_t)Ns * 8));
+    TRY(ensure(c, c->pexp, (size_t)Ns * 4));
+    TRY(ensure(c, c->hdiag, (size_t)Ns * 8));
+    e.theta = (double*)c->theta.p;
+    e.lc = (double*)c->lc.p;
+    e.log_f = (double*)c->logf.p;
+    e.psi_mant = (double*)c->pmant.p;
+    e.psi_exp = (int*)c->pexp.p;
+    e.h_diag = (double*)c->hdiag.p;
+    LAUNCH(NQS_STAGE_ENV, launch_env_fp64(e, c->stream));
+    CK(cudaGetLastError());
+    return NQS_OK;
+}
+
+// Amplitudes over one row set, accumulated into per-chunk partial sums.
+int amp_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, RowSet rows, int64_t total_rows,
+             const int64_t* count_dev, DevBuf& base, DevBuf& part, DevBuf& span,
+             int64_t max_rows_per_sample, int stage)
+{
+    StageScope sc(c, stage);
+    const bool mixed = c->precision == NQS_PREC_MIXED && c->av.chain;
+    const int R = mixed ? mixed_rows_per_block(c->mixed) : amp_fp64_rows_per_block(c->av);
+    int64_t max_chunks = total_rows / R + Ns;
+    if (max_rows_per_sample >= 0) max_chunks = Ns * ((max_rows_per_sample + R - 1) / R);
+    TRY(ensure(c, base, (size_t)(Ns + 1) * 8));
+    TRY(ensure(c, part, (size_t)(max_chunks ? max_chunks : 1) * 8));
+    TRY(ensure(c, span, (size_t)(max_chunks ? max_chunks : 1) * 8));
+    LAUNCH(stage, launch_chunk_base(count_dev, R, (int64_t*)base.p, Ns, c->stream));
+    rows.count = count_dev;
+    rows.chunk_base = (const int64_t*)base.p;
+    rows.max_chunks = max_chunks;
+    AmpArgs a{};
+    a.an = c->av;
+    a.h = c->hv;
+    a.samples = samples;
+    a.Ns = Ns;
+    a.rows = rows;
+    a.rows_per_block = R;
+    a.Lenv = (const double*)c->Lenv.p; a.Lexp = (const int*)c->Lexp.p;
+    a.Renv = (const double*)c->Renv.p; a.Rexp = (const int*)c->Rexp.p;
+    a.Hst = (const double*)c->Hst.p; a.Hexp = (const int*)c->Hexp.p;
+    a.theta = (const double*)c->theta.p;
+    a.lc = (const double*)c->lc.p;
+    a.psi_mant = (const double*)c->pmant.p;
+    a.psi_exp = (const int*)c->pexp.p;
+    a.partial = (double*)part.p;
+    a.span = (int64_t*)span.p;
+    if (mixed) {
+        const size_t need = mixed_workspace_bytes(c->mixed, a);
+        TRY(ensure(c, c->mixed_ws, need));
+        int launches = 0;
+        const int st = mixed_amp(c->mixed, a, c->mixed_ws.p, c->stream, &launches);
+        LAUNCH(stage, launches);
+        if (st != NQS_OK) return set_err(c, st, "mixed-precision amplitudes failed");
+    } else {
+        LAUNCH(stage, launch_amp_fp64(a, c->stream));
+    }
+    CK(cudaGetLastError());
+    return NQS_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+
+extern "C" int nqs_create(nqs_ctx** out, int device, void* cuda_stream)
+{
+    if (!out) return NQS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return NQS_ERR_INVALID_ARG;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return NQS_ERR_CUDA;
+    nqs_ctx* c = new nqs_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    *out = c;
+    return NQS_OK;
+}
+
+extern "C" int nqs_destroy(nqs_ctx* c)
+{
+    if (!c) return NQS_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    DevBuf* bufs[] = {&c->h1e, &c->eri, &c->pairs, &c->chol, &c->A, &c->AT, &c->W, &c->b,
+                      &c->pred_ptr, &c->pred_idx, &c->mixed_buf, &c->st_samples, &c->st_counts,
+                      &c->st_u, &c->st_out0, &c->st_out1, &c->st_out2, &c->st_out3, &c->st_out4,
+                      &c->chunk_cnt, &c->chunk_off, &c->chunk_w, &c->rem_max, &c->det_tot,
+                      &c->det_off, &c->det_rank, &c->det_coef, &c->Lenv, &c->Lexp, &c->Renv,
+                      &c->Rexp, &c->Hst, &c->Hexp, &c->Gst, &c->Gexp, &c->theta, &c->lc,
+                      &c->logf, &c->pmant, &c->pexp, &c->hdiag, &c->Wtot, &c->draw_rank64,
+                      &c->draw_rank, &c->draw_coef, &c->n_unique, &c->base_det, &c->base_draw,
+                      &c->part_det, &c->part_draw, &c->eloc, &c->edet, &c->estoch, &c->summary,
+                      &c->derr, &c->mixed_ws, &c->span_det, &c->span_draw};
+    for (DevBuf* b : bufs) release(*b);
+    for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);
+    delete c;
+    return NQS_OK;
+}
+
+extern "C" const char* nqs_last_error(const nqs_ctx* c) { return c ? c->err : "null context"; }
+
+extern "C" int nqs_set_options(nqs_ctx* c, const nqs_options* o)
+{
+    if (!c || !o) return NQS_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    if (o->precision != NQS_PREC_FP64 && o->precision != NQS_PREC_MIXED)
+        return set_err(c, NQS_ERR_INVALID_ARG, "unknown precision %d", o->precision);
+    for (int i = 0; i < 14; ++i)
+        if (o->reserved[i]) return set_err(c, NQS_ERR_INVALID_ARG, "nqs_options.reserved[%d] != 0", i);
+    c->precision = o->precision;
+    c->timing = o->timing ? 1 : 0;
+    return NQS_OK;
+}
+
+extern "C" int nqs_stage_times(nqs_ctx* c, double* ms, int64_t* launches, int n)
+{
+    if (!c || n < 0 || n > NQS_N_STAGES) return NQS_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    cudaSetDevice(c->device);
+    CK(cudaStreamSynchronize(c->stream));
+    for (auto& p : c->pending) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) c->stage_ms[p.stage] += t;
+        else cudaGetLastError();
+        c->free_events.push_back(p.a);
+        c->free_events.push_back(p.b);
+    }
+    c->pending.clear();
+    for (int i = 0; i < n; ++i) {
+        if (ms) ms[i] = c->stage_ms[i];
+        if (launches) launches[i] = c->stage_launch[i];
+    }
+    for (int i = 0; i < NQS_N_STAGES; ++i) { c->stage_ms[i] = 0.0; c->stage_launch[i] = 0; }
+    return NQS_OK;
+}
+
+extern "C" int nqs_set_hamiltonian(nqs_ctx* c, const double* h1e, const double* cholesky_or_eri,
+                                   int n_chol, int K, int na, int nb, double e_core)
+{
+    if (!c) return NQS_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    cudaSetDevice(c->device);
+    if (K < 1 || K > kMaxOrb) return set_err(c, NQS_ERR_INVALID_ARG, "n_orb = %d outside 1..64", K);
+    if (na < 0 || na > K || nb < 0 || nb > K)
+        return set_err(c, NQS_ERR_INVALID_ARG, "n_alpha = %d, n_beta = %d outside 0..n_orb", na, nb);
+    if (!h1e || !cholesky_or_eri) return set_err(c, NQS_ERR_INVALID_ARG, "null integral pointer");
+    if (n_chol < 0) return set_err(c, NQS_ERR_INVALID_ARG, "n_chol = %d < 0", n_chol);
+    c->has_ham = false;
+    const size_t KK = (size_t)K * K;
+    const double* dh;
+    TRY(stage_in(c, c->st_out0, h1e, KK, &dh));
+    TRY(ensure(c, c->h1e, KK * 8));
+    CK(cudaMemcpyAsync(c->h1e.p, dh, KK * 8, cudaMemcpyDeviceToDevice, c->stream));
+    TRY(ensure(c, c->eri, KK * KK * 8));
+    if (n_chol > 0) {
+        const double* dl;
+        TRY(stage_in(c, c->st_out1, cholesky_or_eri, (size_t)n_chol * KK, &dl));
+        LAUNCH(NQS_STAGE_OTHER, launch_build_eri(dl, n_chol, K, (double*)c->eri.p, c->stream));
+        CK(cudaGetLastError());
+    } else {
+        const double* de;
+        TRY(stage_in(c, c->st_out1, cholesky_or_eri, KK * KK, &de));
+        CK(cudaMemcpyAsync(c->eri.p, de, KK * KK * 8, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    // blocks of the canonical order and the pair-unranking tables
+    HamView h{};
+    h.K = K; h.na = na; h.nb = nb;
+    h.no[0] = na; h.no[1] = nb; h.nv[0] = K - na; h.nv[1] = K - nb;
+    const int64_t Sa = (int64_t)h.no[0] * h.nv[0], Sb = (int64_t)h.no[1] * h.nv[1];
+    const int64_t Daa = binom2(h.no[0]) * binom2(h.nv[0]), Dbb = binom2(h.no[1]) * binom2(h.nv[1]);
+    const int64_t nconn = Sa + Sb + Daa + Dbb + Sa * Sb;
+    if (nconn >= (1ll << 21))
+        return set_err(c, NQS_ERR_UNSUPPORTED, "n_conn = %lld too large", (long long)nconn);
+    h.blk[0] = 0; h.blk[1] = (uint32_t)Sa; h.blk[2] = (uint32_t)(Sa + Sb);
+    h.blk[3] = (uint32_t)(Sa + Sb + Daa); h.blk[4] = (uint32_t)(Sa + Sb + Daa + Dbb);
+    h.blk[5] = (uint32_t)nconn;
+    h.div_nv[0] = make_fastdiv(h.nv[0]); h.div_nv[1] = make_fastdiv(h.nv[1]);
+    h.div_vpair[0] = make_fastdiv((uint32_t)binom2(h.nv[0]));
+    h.div_vpair[1] = make_fastdiv((uint32_t)binom2(h.nv[1]));
+    h.div_sb = make_fastdiv((uint32_t)Sb);
+    h.n_conn = (uint32_t)nconn;
+    h.bitlen_nconn = bit_length((uint64_t)nconn);
+    std::vector<uint16_t> tab;
+    const int ns[4] = {h.no[0], h.no[1], h.nv[0], h.nv[1]};
+    for (int t = 0; t < 4; ++t) {
+        h.pair_off[t] = (uint32_t)tab.size();
+        for (int i = 0; i < ns[t]; ++i)
+            for (int j = i + 1; j < ns[t]; ++j) tab.push_back((uint16_t)(i | (j << 8)));
+    }
+    if (tab.empty()) tab.push_back(0);
+    TRY(ensure(c, c->pairs, tab.size() * 2));
+    CK(cudaMemcpyAsync(c->pairs.p, tab.data(), tab.size() * 2, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    h.h1e = (const double*)c->h1e.p;
+    h.eri = (const double*)c->eri.p;
+    h.pairs = (const uint16_t*)c->pairs.p;
+    h.e_core = e_core;
+    c->hv = h;
+    c->K = K; c->na = na; c->nb = nb;
+    c->n_conn = nconn;
+    c->e_core = e_core;
+    c->has_ham = true;
+    if (c->has_ans && c->av.K != K) c->has_ans = false;
+    return NQS_OK;
+}
+
+extern "C" int nqs_set_ansatz(nqs_ctx* c, const double* site_tensors, int n_edges, int D,
+                              const int* pred_ptr, const int* pred_idx, const double* rbm_W,
+                              const double* rbm_b, int n_hidden)
+{
+    if (!c) return NQS_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    cudaSetDevice(c->device);
+    TRY(check_ready(c, false));
+    const int K = c->K;
+    if (D < 1 || D > 256) return set_err(c, NQS_ERR_INVALID_ARG, "bond_dim = %d outside 1..256", D);
+    if (!site_tensors) return set_err(c, NQS_ERR_INVALID_ARG, "site_tensors is NULL");
+    if ((pred_ptr == nullptr) != (pred_idx == nullptr))
+        return set_err(c, NQS_ERR_INVALID_ARG, "pred_ptr and pred_idx must both be given or both NULL");
+    if (n_hidden < 0 || (n_hidden > 0 && (!rbm_W || !rbm_b)))
+        return set_err(c, NQS_ERR_INVALID_ARG, "n_hidden = %d with missing rbm_W / rbm_b", n_hidden);
+    const bool chain = pred_ptr == nullptr;
+    std::vector<int> ptr, idx;
+    if (chain) {
+        if (n_edges != K) return set_err(c, NQS_ERR_INVALID_ARG, "chain needs n_edges = n_orb (%d), got %d", K, n_edges);
+    } else {
+        ptr.resize(K + 1);
+        if (is_device_ptr(pred_ptr)) cudaMemcpy(ptr.data(), pred_ptr, (K + 1) * 4, cudaMemcpyDeviceToHost);
+        else memcpy(ptr.data(), pred_ptr, (K + 1) * 4);
+        if (ptr[0] != 0 || ptr[K] != n_edges)
+            return set_err(c, NQS_ERR_INVALID_ARG, "pred_ptr must start at 0 and end at n_edges");
+        idx.resize(n_edges > 0 ? n_edges : 1);
+        if (is_device_ptr(pred_idx)) cudaMemcpy(idx.data(), pred_idx, n_edges * 4, cudaMemcpyDeviceToHost);
+        else memcpy(idx.data(), pred_idx, (size_t)n_edges * 4);
+        for (int i = 0; i < K; ++i) {
+            const int deg = ptr[i + 1] - ptr[i];
+            if (deg < 1 || deg > 8)
+                return set_err(c, NQS_ERR_INVALID_ARG, "vertex %d has in-degree %d (need 1..8)", i, deg);
+            for (int e = ptr[i]; e < ptr[i + 1]; ++e)
+                if (idx[e] < -1 || idx[e] >= i)
+                    return set_err(c, NQS_ERR_INVALID_ARG, "pred_idx[%d] = %d is not -1 or an earlier vertex of %d", e, idx[e], i);
+        }
+    }
+    c->has_ans = false;
+    const size_t nt = (size_t)n_edges * 4 * D * D;
+    std::vector<double> hA(nt), hAT(nt);
+    if (is_device_ptr(site_tensors)) CK(cudaMemcpy(hA.data(), site_tensors, nt * 8, cudaMemcpyDeviceToHost));
+    else memcpy(hA.data(), site_tensors, nt * 8);
+    for (size_t m = 0; m < (size_t)n_edges * 4; ++m)
+        for (int r = 0; r < D; ++r)
+            for (int q = 0; q < D; ++q) hAT[m * D * D + (size_t)q * D + r] = hA[m * D * D + (size_t)r * D + q];
+    TRY(ensure(c, c->A, nt * 8));
+    TRY(ensure(c, c->AT, nt * 8));
+    CK(cudaMemcpy(c->A.p, hA.data(), nt * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->AT.p, hAT.data(), nt * 8, cudaMemcpyHostToDevice));
+    if (!chain) {
+        TRY(ensure(c, c->pred_ptr, (K + 1) * 4));
+        TRY(ensure(c, c->pred_idx, (size_t)n_edges * 4));
+        CK(cudaMemcpy(c->pred_ptr.p, ptr.data(), (K + 1) * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->pred_idx.p, idx.data(), (size_t)n_edges * 4, cudaMemcpyHostToDevice));
+    }
+    if (n_hidden > 0) {
+        const size_t nw = (size_t)n_hidden * 2 * K;
+        TRY(ensure(c, c->W, nw * 8));
+        TRY(ensure(c, c->b, (size_t)n_hidden * 8));
+        CK(cudaMemcpy(c->W.p, rbm_W, nw * 8, cudaMemcpyDefault));
+        CK(cudaMemcpy(c->b.p, rbm_b, (size_t)n_hidden * 8, cudaMemcpyDefault));
+    }
+    AnsatzView a{};
+    a.K = K; a.D = D; a.n_edges = n_edges; a.chain = chain ? 1 : 0;
+    a.pred_ptr = chain ? nullptr : (const int*)c->pred_ptr.p;
+    a.pred_idx = chain ? nullptr : (const int*)c->pred_idx.p;
+    a.A = (const double*)c->A.p;
+    a.AT = (const double*)c->AT.p;
+    a.n_hidden = n_hidden;
+    a.W = n_hidden ? (const double*)c->W.p : nullptr;
+    a.b = n_hidden ? (const double*)c->b.p : nullptr;
+    c->av = a;
+    if (chain) {
+        // tensor-core copies of the site tensors
+        TRY(ensure(c, c->mixed_buf, mixed_param_bytes(K, D)));
+        const int st = mixed_upload(c->mixed, hA.data(), K, D, c->mixed_buf.p, c->stream);
+        if (st != NQS_OK) return set_err(c, st, "uploading the tensor-core site tensors failed");
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    c->has_ans = true;
+    return NQS_OK;
+}
+
+extern "C" int nqs_connected(nqs_ctx* c, const uint64_t* samples, int64_t Ns, double eps,
+                             int64_t* offsets, uint32_t* rank, uint64_t* dets, double* H,
+                             int8_t* sign, int64_t capacity)
+{
+    if (!c) return NQS_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    cudaSetDevice(c->device);
+    TRY(check_ready(c, false));
+    if (Ns < 0 || (Ns > 0 && !samples) || !offsets)
+        return set_err(c, NQS_ERR_INVALID_ARG, "bad samples / offsets arguments");
+    uint64_t eb;
+    TRY(eps_bits(c, eps, &eb));
+    if (Ns == 0) {
+        int64_t z = 0;
+        if (is_device_ptr(offsets)) CK(cudaMemcpy(offsets, &z, 8, cudaMemcpyHostToDevice));
+        else offsets[0] = 0;
+        return NQS_OK;
+    }
+    const uint64_t* ds;
+    TRY(stage_in(c, c->st_samples, samples, (size_t)Ns * 2, &ds));
+    TRY(reset_dev_error(c));
+    LAUNCH(NQS_STAGE_OTHER, launch_validate(ds, Ns, c->K, c->na, c->nb, (DevError*)c->derr.p, c->stream));
+    int64_t total = 0;
+    TRY(count_pass(c, ds, Ns, eb, &total));
+    TRY(read_dev_error(c));
+    int64_t* doff;
+    bool hoff;
+    TRY(stage_out(c, c->st_out4, offsets, (size_t)Ns + 1, &doff, &hoff));
+    CK(cudaMemcpyAsync(doff, c->det_off.p, (size_t)(Ns + 1) * 8, cudaMemcpyDeviceToDevice, c->stream));
+    TRY(copy_back(c, offsets, doff, (size_t)Ns + 1, hoff));
+    const bool want = rank || dets || H || sign;
+    if (want && capacity < total) {
+        CK(cudaStreamSynchronize(c->stream));
+        return set_err(c, NQS_ERR_INVALID_ARG, "capacity %lld < %lld entries", (long long)capacity, (long long)total);
+    }
+    if (want && total > 0) {
+        uint32_t* drank; uint64_t* ddet; double* dH; int8_t* dsg;
+        bool h0, h1, h2, h3;
+        TRY(stage_out(c, c->st_out0, rank, (size_t)total, &drank, &h0));
+        TRY(stage_out(c, c->st_out1, dets, (size_t)total * 2, &ddet, &h1));
+        TRY(stage_out(c, c->st_out2, H, (size_t)total, &dH, &h2));
+        TRY(stage_out(c, c->st_out3, sign, (size_t)total, &dsg, &h3));
+        EnumArgs a{};
+        a.h = c->hv;
+        a.samples = ds;
+        a.eps_bits = eb;
+        a.n_chunks = (uint32_t)((c->n_conn + 31) / 32);
+        a.rem_max_bits = (unsigned long long*)c->rem_max.p;
+        a.chunk_off = (const uint32_t*)c->chunk_off.p;
+        a.det_off = (const int64_t*)c->det_off.p;
+        a.out_rank = drank; a.out_det = ddet; a.out_H = dH; a.out_sign = dsg;
+        LAUNCH(NQS_STAGE_WRITE, launch_enum(a, Ns, true, c->stream));
+        CK(cudaGetLastError());
+        TRY(copy_back(c, rank, drank, (size_t)total, h0));
+        TRY(copy_back(c, dets, ddet, (size_t)total * 2, h1));
+        TRY(copy_back(c, H, dH, (size_t)total, h2));
+        TRY(copy_back(c, sign, dsg, (size_t)total, h3));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return NQS_OK;
+}
+
+extern "C" int nqs_amplitude(nqs_ctx* c, const uint64_t* dets, int64_t n, double* log_abs,
+                             int8_t* sign)
+{
+    if (!c) return NQS_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    cudaSetDevice(c->device);
+    TRY(check_ready(c, true));
+    if (n < 0 || (n > 0 && (!dets || !log_abs || !sign)))
+        return set_err(c, NQS_ERR_INVALID_ARG, "bad dets / outputs");
+    if (n == 0) return NQS_OK;
+    const uint64_t* dd;
+    TRY(stage_in(c, c->st_samples, dets, (size_t)n * 2, &dd));
+    TRY(reset_dev_error(c));
+    LAUNCH(NQS_STAGE_OTHER, launch_validate(dd, n, c->K, c->na, c->nb, (DevError*)c->derr.p, c->stream));
+    double* dla; int8_t* dsg;
+    bool h0, h1;
+    TRY(stage_out(c, c->st_out0, log_abs, (size_t)n, &dla, &h0));
+    TRY(stage_out(c, c->st_out1, sign, (size_t)n, &dsg, &h1));
+    TRY(read_dev_error(c));
+    LAUNCH(NQS_STAGE_OTHER, launch_full_amp_fp64(c->av, dd, n, dla, dsg, c->stream));
+    CK(cudaGetLastError());
+    TRY(copy_back(c, log_abs, dla, (size_t)n, h0));
+    TRY(copy_back(c, sign, dsg, (size_t)n, h1));
+    if (h0 || h1) CK(cudaStreamSynchronize(c->stream));
+    return NQS_OK;
+}
+
+namespace {
+
+// Steps shared by nqs_draws and nqs_local_energy: weights, prefix, draws.
+int draw_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, uint64_t eb, int n_draws,
+              uint64_t seed, int64_t* rank_out, bool write_dets, bool need_w)
+{
+    const uint32_t nch = (uint32_t)((c->n_conn + 31) / 32);
+    const bool weights = n_draws > 0 || need_w;
+    TRY(ensure(c, c->chunk_w, (size_t)Ns * nch * 8));
+    TRY(ensure(c, c->Wtot, (size_t)Ns * 8));
+    EnumArgs a{};
+    a.h = c->hv;
+    a.samples = ds;
+    a.eps_bits = eb;
+    a.n_chunks = nch;
+    a.rem_max_bits = (unsigned long long*)c->rem_max.p;
+    a.chunk_off = (const uint32_t*)c->chunk_off.p;
+    a.det_off = write_dets ? (const int64_t*)c->det_off.p : nullptr;
+    a.out_rank = write_dets ? (uint32_t*)c->det_rank.p : nullptr;
+    a.out_H = write_dets ? (double*)c->det_coef.p : nullptr;
+    a.chunk_w = weights ? (uint64_t*)c->chunk_w.p : nullptr;
+    if (!write_dets && !weights) return NQS_OK;
+    {
+        StageScope sc(c, NQS_STAGE_WRITE);
+        LAUNCH(NQS_STAGE_WRITE, launch_enum(a, Ns, true, c->stream));
+        CK(cudaGetLastError());
+        if (weights)
+            LAUNCH(NQS_STAGE_WRITE, launch_scan_chunks_u64((uint64_t*)c->chunk_w.p, (uint64_t*)c->Wtot.p,
+                                                          Ns, nch, c->stream));
+    }
+    if (n_draws > 0) {
+        StageScope sc(c, NQS_STAGE_DRAW);
+        DrawArgs d{};
+        d.h = c->hv;
+        d.samples = ds;
+        d.Ns = Ns;
+        d.eps_bits = eb;
+        d.n_chunks = nch;
+        d.chunk_pre = (const uint64_t*)c->chunk_w.p;
+        d.rem_max_bits = (const unsigned long long*)c->rem_max.p;
+        d.n_draws = n_draws;
+        d.seed = seed;
+        d.out_rank = rank_out;
+        LAUNCH(NQS_STAGE_DRAW, launch_draws(d, c->stream));
+    }
+    CK(cudaGetLastError());
+    return NQS_OK;
+}
+
+}  // namespace
+
+extern "C" int nqs_draws(nqs_ctx* c, const uint64_t* samples, int64_t Ns, double eps,
+                         int n_draws, uint64_t seed, int64_t* ranks, uint64_t* w_total)
+{
+    if (!c) return NQS_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    cudaSetDevice(c->device);
+    TRY(check_ready(c, false));
+    if (Ns < 0 || n_draws < 0 || (Ns > 0 && !samples) || (Ns > 0 && n_draws > 0 && !ranks))
+        return set_err(c, NQS_ERR_INVALID_ARG, "bad samples / n_draws / ranks arguments");
+    uint64_t eb;
+    TRY(eps_bits(c, eps, &eb));
+    if (Ns == 0) return NQS_OK;
+    const uint64_t* ds;
+    TRY(stage_in(c, c->st_samples, samples, (size_t)Ns * 2, &ds));
+    TRY(reset_dev_error(c));
+    LAUNCH(NQS_STAGE_OTHER, launch_validate(ds, Ns, c->K, c->na, c->nb, (DevError*)c->derr.p, c->stream));
+    int64_t total = 0;
+    TRY(count_pass(c, ds, Ns, eb, &total));
+    TRY(read_dev_error(c));
+    int64_t* dr = nullptr;
+    bool hr = false;
+    if (n_draws > 0) TRY(stage_out(c, c->st_out0, ranks, (size_t)Ns * n_draws, &dr, &hr));
+    TRY(draw_pass(c, ds, Ns, eb, n_draws, seed, dr, false, w_total != nullptr));
+    if (n_draws > 0) TRY(copy_back(c, ranks, dr, (size_t)Ns * n_draws, hr));
+    if (w_total) {
+        uint64_t* dw;
+        bool hw;
+        TRY(stage_out(c, c->st_out1, w_total, (size_t)Ns, &dw, &hw));
+        CK(cudaMemcpyAsync(dw, c->Wtot.p, (size_t)Ns * 8, cudaMemcpyDeviceToDevice, c->stream));
+        TRY(copy_back(c, w_total, dw, (size_t)Ns, hw));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return NQS_OK;
+}
+
+extern "C" int nqs_local_energy(nqs_ctx* c, const uint64_t* samples, const double* counts,
+                                int64_t Ns, double eps, int n_draws, uint64_t seed, double* e_loc,
+                                nqs_energy_summary* out)
+{
+    if (!c) return NQS_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    cudaSetDevice(c->device);
+    TRY(check_ready(c, true));
+    if (Ns < 0 || (Ns > 0 && (!samples || !e_loc)))
+        return set_err(c, NQS_ERR_INVALID_ARG, "bad samples / e_loc arguments");
+    if (n_draws < 0 || n_draws > 4096)
+        return set_err(c, NQS_ERR_INVALID_ARG, "n_draws = %d outside 0..4096", n_draws);
+    uint64_t eb;
+    TRY(eps_bits(c, eps, &eb));
+    if (out) memset(out, 0, sizeof(*out));
+    if (Ns == 0) return NQS_OK;
+    const uint64_t* ds;
+    const double* dc;
+    TRY(stage_in(c, c->st_samples, samples, (size_t)Ns * 2, &ds));
+    TRY(stage_in(c, c->st_counts, counts, (size_t)Ns, &dc));
+    TRY(reset_dev_error(c));
+    {
+        StageScope sc(c, NQS_STAGE_ENV);
+        LAUNCH(NQS_STAGE_ENV, launch_validate(ds, Ns, c->K, c->na, c->nb, (DevError*)c->derr.p, c->stream));
+        TRY(env_pass(c, ds, Ns, false));
+        k_check_psi<<<(unsigned)((Ns + 255) / 256), 256, 0, c->stream>>>((const double*)c->pmant.p, Ns,
+                                                                       (DevError*)c->derr.p);
+        LAUNCH(NQS_STAGE_ENV, 1);
+    }
+    int64_t total = 0;
+    TRY(count_pass(c, ds, Ns, eb, &total));
+    TRY(read_dev_error(c));
+    TRY(ensure(c, c->det_rank, (size_t)total * 4));
+    TRY(ensure(c, c->det_coef, (size_t)total * 8));
+    if (n_draws > 0) {
+        TRY(ensure(c, c->draw_rank64, (size_t)Ns * n_draws * 8));
+        TRY(ensure(c, c->draw_rank, (size_t)Ns * n_draws * 4));
+        TRY(ensure(c, c->draw_coef, (size_t)Ns * n_draws * 8));
+        TRY(ensure(c, c->n_unique, (size_t)Ns * 8));
+    }
+    TRY(draw_pass(c, ds, Ns, eb, n_draws, seed, (int64_t*)c->draw_rank64.p, true, false));
+    if (n_draws > 0) {
+        StageScope sc(c, NQS_STAGE_DRAW);
+        DedupArgs d{};
+        d.h = c->hv;
+        d.samples = ds;
+        d.ranks = (const int64_t*)c->draw_rank64.p;
+        d.n_draws = n_draws;
+        int p2 = 1;
+        while (p2 < n_draws) p2 <<= 1;
+        d.pow2 = p2;
+        d.rem_max_bits = (const unsigned long long*)c->rem_max.p;
+        d.W = (const uint64_t*)c->Wtot.p;
+        d.out_rank = (uint32_t*)c->draw_rank.p;
+        d.out_coef = (double*)c->draw_coef.p;
+        d.n_unique = (int64_t*)c->n_unique.p;
+        LAUNCH(NQS_STAGE_DRAW, launch_dedup(d, Ns, c->stream));
+        CK(cudaGetLastError());
+    }
+    // amplitudes: deterministic rows, then the distinct drawn rows
+    RowSet rd{};
+    rd.rank = (const uint32_t*)c->det_rank.p;
+    rd.coef = (const double*)c->det_coef.p;
+    rd.begin = (const int64_t*)c->det_off.p;
+    TRY(amp_pass(c, ds, Ns, rd, total, (const int64_t*)c->det_tot.p, c->base_det, c->part_det,
+                 c->span_det, -1, NQS_STAGE_AMP_DET));
+    if (n_draws > 0) {
+        RowSet rs{};
+        rs.rank = (const uint32_t*)c->draw_rank.p;
+        rs.coef = (const double*)c->draw_coef.p;
+        rs.begin = nullptr;
+        rs.stride = n_draws;
+        TRY(amp_pass(c, ds, Ns, rs, (int64_t)Ns * n_draws, (const int64_t*)c->n_unique.p,
+                     c->base_draw, c->part_draw, c->span_draw, n_draws, NQS_STAGE_AMP_DRAW));
+    }
+    double* de;
+    bool he;
+    TRY(stage_out(c, c->st_out0, e_loc, (size_t)Ns, &de, &he));
+    TRY(ensure(c, c->summary, 8 * 8));
+    FinalArgs f{};
+    f.Ns = Ns;
+    f.h_diag = (const double*)c->hdiag.p;
+    f.part_det = (const double*)c->part_det.p;
+    f.base_det = (const int64_t*)c->base_det.p;
+    f.part_draw = n_draws > 0 ? (const double*)c->part_draw.p : nullptr;
+    f.base_draw = n_draws > 0 ? (const int64_t*)c->base_draw.p : nullptr;
+    f.counts = dc;
+    f.log_f = (const double*)c->logf.p;
+    f.det_off = (const int64_t*)c->det_off.p;
+    f.n_unique = n_draws > 0 ? (const int64_t*)c->n_unique.p : nullptr;
+    f.e_loc = de;
+    f.span_det = (const int64_t*)c->span_det.p;
+    f.span_draw = n_draws > 0 ? (const int64_t*)c->span_draw.p : nullptr;
+    f.summary = out ? (double*)c->summary.p : nullptr;
+    {
+        StageScope sc(c, NQS_STAGE_FINAL);
+        LAUNCH(NQS_STAGE_FINAL, launch_finalize(f, c->stream));
+    }
+    CK(cudaGetLastError());
+    TRY(copy_back(c, e_loc, de, (size_t)Ns, he));
+    if (out) {
+        double sm[8];
+        CK(cudaMemcpyAsync(sm, c->summary.p, sizeof(sm), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        out->e_mean = sm[0];
+        out->sum_counts = sm[1];
+        out->log_B = sm[2];
+        out->e_tilde_mean = sm[3];
+        out->n_conn = c->n_conn;
+        out->n_det = (int64_t)llround(sm[4]);
+        out->n_draw_unique = (int64_t)llround(sm[5]);
+        out->n_amplitudes = out->n_det + out->n_draw_unique;
+        out->span_sites = (int64_t)llround(sm[6]);
+    } else if (he) {
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return NQS_OK;
+}
+
+extern "C" int nqs_grad_log_psi_vjp(nqs_ctx* c, const uint64_t* samples, const double* u, int64_t Ns,
+                                    double* grad_sites, double* grad_W, double* grad_b)
+{
+    if (!c) return NQS_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    cudaSetDevice(c->device);
+    TRY(check_ready(c, true));
+    if (Ns < 0 || (Ns > 0 && (!samples || !u)))
+        return set_err(c, NQS_ERR_INVALID_ARG, "bad samples / u arguments");
+    const int K = c->K, D = c->av.D, NH = c->av.n_hidden;
+    const size_t nt = (size_t)c->av.n_edges * 4 * D * D, nw = (size_t)NH * 2 * K;
+    double *dg, *dW, *db;
+    bool hg, hW, hb;
+    TRY(stage_out(c, c->st_out1, grad_sites, nt, &dg, &hg));
+    TRY(stage_out(c, c->st_out2, grad_W, nw, &dW, &hW));
+    TRY(stage_out(c, c->st_out3, grad_b, (size_t)NH, &db, &hb));
+    if (Ns == 0) {
+        if (dg) CK(cudaMemsetAsync(dg, 0, nt * 8, c->stream));
+        if (dW && nw) CK(cudaMemsetAsync(dW, 0, nw * 8, c->stream));
+        if (db && NH) CK(cudaMemsetAsync(db, 0, (size_t)NH * 8, c->stream));
+    } else {
+        const uint64_t* ds;
+        const double* du;
+        TRY(stage_in(c, c->st_samples, samples, (size_t)Ns * 2, &ds));
+        TRY(stage_in(c, c->st_u, u, (size_t)Ns, &du));
+        TRY(reset_dev_error(c));
+        LAUNCH(NQS_STAGE_OTHER, launch_validate(ds, Ns, c->K, c->na, c->nb, (DevError*)c->derr.p, c->stream));
+        TRY(env_pass(c, ds, Ns, true));
+        k_check_psi<<<(unsigned)((Ns + 255) / 256), 256, 0, c->stream>>>((const double*)c->pmant.p, Ns,
+                                                                       (DevError*)c->derr.p);
+        LAUNCH(NQS_STAGE_OTHER, 1);
+        TRY(read_dev_error(c));
+        GradArgs g{};
+        g.an = c->av;
+        g.samples = ds;
+        g.Ns = Ns;
+        g.u = du;
+        g.Lenv = (const double*)c->Lenv.p; g.Lexp = (const int*)c->Lexp.p;
+        g.Renv = (const double*)c->Renv.p; g.Rexp = (const int*)c->Rexp.p;
+        g.Hst = (const double*)c->Hst.p; g.Hexp = (const int*)c->Hexp.p;
+        g.Gst = (const double*)c->Gst.p; g.Gexp = (const int*)c->Gexp.p;
+        g.psi_mant = (const double*)c->pmant.p;
+        g.psi_exp = (const int*)c->pexp.p;
+        g.theta = (const double*)c->theta.p;
+        g.grad_sites = dg;
+        g.grad_W = dW;
+        g.grad_b = db;
+        LAUNCH(NQS_STAGE_OTHER, launch_grad_fp64(g, c->stream));
+        CK(cudaGetLastError());
+    }
+    TRY(copy_back(c, grad_sites, dg, nt, hg));
+    TRY(copy_back(c, grad_W, dW, nw, hW));
+    TRY(copy_back(c, grad_b, db, (size_t)NH, hb));
+    CK(cudaStreamSynchronize(c->stream));
+    return NQS_OK;
+}

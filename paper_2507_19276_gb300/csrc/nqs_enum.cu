@@ -1,0 +1,257 @@
+// nqs_enum.cu -- enumeration of connected determinants, the eps split, the
+// remainder weights and the Philox draws (Sec. 2.4, Sec. 3).
+//
+// Work unit: a "chunk" of 32 consecutive canonical ranks of one sample, one
+// warp-wide evaluation. The count pass records, per chunk, how many entries
+// pass |H| >= eps and the largest remainder |H| of the sample; the write pass
+// compacts the deterministic entries with a ballot prefix and sums the
+// integer remainder weights per chunk; the draw pass inverts the per-sample
+// prefix of those sums and re-evaluates one chunk per draw.
+#include "nqs_kernels.cuh"
+
+namespace nqs {
+
+constexpr int kEnumWarps = 8;       // warps per block
+constexpr int kChunksPerWarp = 4;   // consecutive chunks per warp
+
+__device__ __forceinline__ int shift_of(unsigned long long max_bits, int bitlen_nconn)
+{
+    if (max_bits == 0) return 0;
+    int e;
+    frexp(__longlong_as_double((long long)max_bits), &e);
+    return 62 - e - bitlen_nconn;
+}
+
+template <bool WRITE>
+__global__ void __launch_bounds__(kEnumWarps * 32) k_enum(EnumArgs a)
+{
+    __shared__ OrbLists lists;
+    const int s = a.s0 + blockIdx.y;
+    const uint64_t na = a.samples[2 * s], nb = a.samples[2 * s + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) build_lists_warp(na, nb, a.h.K, lists, lane);
+    __syncthreads();
+    const HamView& h = a.h;
+    int shift = 0;
+    if (WRITE) shift = shift_of(a.rem_max_bits[s], h.bitlen_nconn);
+    uint64_t max_bits = 0;
+    const size_t srow = (size_t)s * a.n_chunks;
+    for (int k = 0; k < kChunksPerWarp; ++k) {
+        const uint32_t c = (blockIdx.x * kEnumWarps + warp) * kChunksPerWarp + k;
+        if (c >= a.n_chunks) break;
+        const uint32_t r = c * 32 + lane;
+        const bool valid = r < h.n_conn;
+        double H = 0.0;
+        uint64_t ma = 0, mb = 0;
+        int odd = 0;
+        if (valid) {
+            Exc e = decode_rank(h, lists, r);
+            H = matrix_element(h, na, nb, e, ma, mb, odd);
+        }
+        const bool det = valid && is_det(H, a.eps_bits);
+        const unsigned bal = __ballot_sync(kFull, det);
+        if (!WRITE) {
+            if (lane == 0) a.chunk_cnt[srow + c] = __popc(bal);
+            if (valid && !det) {
+                uint64_t b = (uint64_t)__double_as_longlong(H) & 0x7fffffffffffffffull;
+                max_bits = b > max_bits ? b : max_bits;
+            }
+        } else {
+            if (det && a.det_off) {
+                const int64_t pos = a.det_off[s] + a.chunk_off[srow + c] +
+                                    __popc(bal & ((1u << lane) - 1u));
+                if (a.out_rank) a.out_rank[pos] = r;
+                if (a.out_H) a.out_H[pos] = H;
+                if (a.out_det) { a.out_det[2 * pos] = ma; a.out_det[2 * pos + 1] = mb; }
+                if (a.out_sign) a.out_sign[pos] = odd ? -1 : 1;
+            }
+            if (a.chunk_w) {
+                uint64_t w = (valid && !det) ? weight_of(H, shift) : 0ull;
+                w = warp_sum_u64(w);
+                if (lane == 0) a.chunk_w[srow + c] = w;
+            }
+        }
+    }
+    if (!WRITE) {
+        for (int o = 16; o; o >>= 1) {
+            uint64_t t = __shfl_xor_sync(kFull, max_bits, o);
+            max_bits = t > max_bits ? t : max_bits;
+        }
+        if (lane == 0 && max_bits) atomicMax(&a.rem_max_bits[s], (unsigned long long)max_bits);
+    }
+}
+
+int launch_enum(const EnumArgs& args, int64_t Ns, bool write, cudaStream_t st)
+{
+    const uint32_t per_block = kEnumWarps * kChunksPerWarp;
+    const uint32_t gx = (args.n_chunks + per_block - 1) / per_block;
+    if (gx == 0) return 0;
+    int n = 0;
+    for (int64_t s0 = 0; s0 < Ns; s0 += 65535, ++n) {
+        EnumArgs a = args;
+        a.s0 = (int)s0;
+        dim3 grid(gx, (unsigned)((Ns - s0) < 65535 ? (Ns - s0) : 65535));
+        if (write) k_enum<true><<<grid, kEnumWarps * 32, 0, st>>>(a);
+        else k_enum<false><<<grid, kEnumWarps * 32, 0, st>>>(a);
+    }
+    return n;
+}
+
+// ---------------------------------------------------------------------------
+// Draws: one warp per (sample, draw)
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) k_draws(DrawArgs a)
+{
+    __shared__ OrbLists lists[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t g = (int64_t)blockIdx.x * 8 + warp;
+    if (g >= a.Ns * (int64_t)a.n_draws) return;
+    const int64_t s = g / a.n_draws;
+    const int d = (int)(g - s * a.n_draws);
+    const size_t srow = (size_t)s * a.n_chunks;
+    const uint64_t W = a.n_chunks ? a.chunk_pre[srow + a.n_chunks - 1] : 0ull;
+    if (W == 0) {
+        if (lane == 0) a.out_rank[g] = -1;
+        return;
+    }
+    const uint64_t na = a.samples[2 * s], nb = a.samples[2 * s + 1];
+    build_lists_warp(na, nb, a.h.K, lists[warp], lane);
+    __syncwarp();
+    // target t = floor(x W / 2^64), then the first chunk whose inclusive prefix > t
+    const uint64_t x = philox_first((uint64_t)d, (uint64_t)s, a.seed);
+    const uint64_t t = __umul64hi(x, W);
+    uint32_t c = 0;
+    if (lane == 0) {
+        uint32_t lo = 0, hi = a.n_chunks - 1;
+        while (lo < hi) {
+            uint32_t mid = lo + (hi - lo) / 2;
+            if (a.chunk_pre[srow + mid] > t) hi = mid; else lo = mid + 1;
+        }
+        c = lo;
+    }
+    c = __shfl_sync(kFull, c, 0);
+    const int shift = shift_of(a.rem_max_bits[s], a.h.bitlen_nconn);
+    const uint32_t r = c * 32 + lane;
+    uint64_t w = 0;
+    if (r < a.h.n_conn) {
+        Exc e = decode_rank(a.h, lists[warp], r);
+        uint64_t ma, mb;
+        int odd;
+        double H = matrix_element(a.h, na, nb, e, ma, mb, odd);
+        if (!is_det(H, a.eps_bits)) w = weight_of(H, shift);
+    }
+    const uint64_t incl = warp_incl_scan_u64(w, lane);
+    const uint64_t base = c ? a.chunk_pre[srow + c - 1] : 0ull;
+    const unsigned hit = __ballot_sync(kFull, base + incl > t);
+    if (lane == 0) a.out_rank[g] = hit ? (int64_t)(c * 32 + (__ffs(hit) - 1)) : -1;
+}
+
+int launch_draws(const DrawArgs& a, cudaStream_t st)
+{
+    const int64_t n = a.Ns * (int64_t)a.n_draws;
+    if (n == 0) return 0;
+    k_draws<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(a);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// Dedup of the draws of a sample: sort, unique, multiplicity -> amplitude rows
+// with coefficient mult/N_eps * H * W / w.
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(1024) k_dedup(DedupArgs a)
+{
+    extern __shared__ uint32_t keys[];      // [P] padded to a power of two
+    __shared__ int head_scan[1024];
+    __shared__ OrbLists lists;
+    const int s = blockIdx.x;
+    const int P = a.pow2;
+    const int64_t base = (int64_t)s * a.n_draws;
+    for (int i = threadIdx.x; i < P; i += blockDim.x)
+        keys[i] = i < a.n_draws && a.ranks[base + i] >= 0 && a.ranks[base + i] < (int64_t)a.h.n_conn
+                      ? (uint32_t)a.ranks[base + i] : 0xffffffffu;
+    const uint64_t na = a.samples[2 * s], nb = a.samples[2 * s + 1];
+    if (threadIdx.x < 32) build_lists_warp(na, nb, a.h.K, lists, threadIdx.x);
+    __syncthreads();
+    // bitonic sort, ascending
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                int l = i ^ j;
+                if (l > i) {
+                    uint32_t x = keys[i], y = keys[l];
+                    bool up = (i & k) == 0;
+                    if ((x > y) == up) { keys[i] = y; keys[l] = x; }
+                }
+            }
+            __syncthreads();
+        }
+    // heads of runs; each thread owns a contiguous slice of `per` entries
+    const int per = (P + blockDim.x - 1) / blockDim.x;
+    const int i0 = threadIdx.x * per;
+    int cnt = 0;
+    for (int i = i0; i < i0 + per && i < P; ++i)
+        if (keys[i] != 0xffffffffu && (i == 0 || keys[i] != keys[i - 1])) ++cnt;
+    head_scan[threadIdx.x] = cnt;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        int v = threadIdx.x >= (unsigned)o ? head_scan[threadIdx.x - o] : 0;
+        __syncthreads();
+        head_scan[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int u = head_scan[threadIdx.x] - cnt;   // exclusive
+    const int total = head_scan[blockDim.x - 1];
+    const int shift = shift_of(a.rem_max_bits[s], a.h.bitlen_nconn);
+    const uint64_t W = a.W[s];
+    for (int i = i0; i < i0 + per && i < P; ++i) {
+        if (keys[i] == 0xffffffffu || (i > 0 && keys[i] == keys[i - 1])) continue;
+        int e = i + 1;
+        while (e < P && keys[e] == keys[i]) ++e;
+        const uint32_t r = keys[i];
+        Exc ex = decode_rank(a.h, lists, r);
+        uint64_t ma, mb;
+        int odd;
+        double H = matrix_element(a.h, na, nb, ex, ma, mb, odd);
+        uint64_t w = weight_of(H, shift);
+        double coef = ((double)(e - i) / (double)a.n_draws) * H * ((double)W / (double)w);
+        a.out_rank[base + u] = r;
+        a.out_coef[base + u] = coef;
+        ++u;
+    }
+    if (threadIdx.x == 0) a.n_unique[s] = total;
+}
+
+int launch_dedup(const DedupArgs& a, int64_t Ns, cudaStream_t st)
+{
+    if (Ns == 0) return 0;
+    const int threads = a.pow2 >= 1024 ? 1024 : (a.pow2 < 32 ? 32 : a.pow2);
+    k_dedup<<<(unsigned)Ns, threads, a.pow2 * sizeof(uint32_t), st>>>(a);
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// Validation of the input determinants
+// ---------------------------------------------------------------------------
+
+__global__ void k_validate(const uint64_t* samples, int64_t Ns, int K, int na, int nb,
+                           DevError* err)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= Ns) return;
+    const uint64_t a = samples[2 * s], b = samples[2 * s + 1];
+    const uint64_t outside = K >= 64 ? 0ull : ~((1ull << K) - 1ull);
+    if ((a & outside) || (b & outside)) report(err, 1, 1, s);
+    else if (__popcll(a) != na || __popcll(b) != nb) report(err, 1, 2, s);
+}
+
+int launch_validate(const uint64_t* samples, int64_t Ns, int K, int na, int nb, DevError* err,
+                    cudaStream_t st)
+{
+    if (Ns == 0) return 0;
+    k_validate<<<(unsigned)((Ns + 255) / 256), 256, 0, st>>>(samples, Ns, K, na, nb, err);
+    return 1;
+}
+
+}  // namespace nqs

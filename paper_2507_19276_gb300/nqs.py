@@ -1,0 +1,297 @@
+"""Python binding of the C ABI in include/nqs.h (ctypes; marshalling only).
+
+Every function of the C library has a same-named Python function here taking
+a context handle; `Context` wraps them with tensor-friendly signatures. Arrays
+may be torch tensors (CUDA or CPU) or numpy arrays; their data pointers are
+passed through as they are, so CUDA tensors stay on the device and host
+arrays are staged by the library. All computation happens in libnqs.so: if it
+cannot be loaded, import fails loudly. There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+NQS_OK = 0
+NQS_PREC_FP64 = 0
+NQS_PREC_MIXED = 1
+STATUS = {0: "NQS_OK", 1: "NQS_ERR_INVALID_ARG", 2: "NQS_ERR_STATE", 3: "NQS_ERR_OOM",
+          4: "NQS_ERR_CUDA", 5: "NQS_ERR_TIMEOUT", 6: "NQS_ERR_UNSUPPORTED"}
+
+
+class NQSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("timing", C.c_int), ("reserved", C.c_int * 14)]
+
+
+N_STAGES = 8
+STAGES = ["env", "count", "write", "draw", "amp_det", "amp_draw", "final", "other"]
+
+
+class EnergySummary(C.Structure):
+    _fields_ = [("e_mean", C.c_double), ("sum_counts", C.c_double), ("log_B", C.c_double),
+                ("e_tilde_mean", C.c_double), ("n_conn", C.c_int64), ("n_det", C.c_int64),
+                ("n_draw_unique", C.c_int64), ("n_amplitudes", C.c_int64),
+                ("span_sites", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libnqs.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        lib = C.CDLL(path)
+        vp, i64, dbl, u64 = C.c_void_p, C.c_int64, C.c_double, C.c_uint64
+        sig = {
+            "nqs_create": [C.POINTER(vp), C.c_int, vp],
+            "nqs_destroy": [vp],
+            "nqs_set_options": [vp, C.POINTER(Options)],
+            "nqs_stage_times": [vp, vp, vp, C.c_int],
+            "nqs_set_hamiltonian": [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, dbl],
+            "nqs_set_ansatz": [vp, vp, C.c_int, C.c_int, vp, vp, vp, vp, C.c_int],
+            "nqs_connected": [vp, vp, i64, dbl, vp, vp, vp, vp, vp, i64],
+            "nqs_amplitude": [vp, vp, i64, vp, vp],
+            "nqs_draws": [vp, vp, i64, dbl, C.c_int, u64, vp, vp],
+            "nqs_local_energy": [vp, vp, vp, i64, dbl, C.c_int, u64, vp, C.POINTER(EnergySummary)],
+            "nqs_grad_log_psi_vjp": [vp, vp, vp, i64, vp, vp, vp],
+        }
+        for name, args in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        lib.nqs_last_error.argtypes = [vp]
+        lib.nqs_last_error.restype = C.c_char_p
+        _lib = lib
+        return lib
+
+
+def exported_symbols():
+    return ["nqs_create", "nqs_destroy", "nqs_last_error", "nqs_set_options", "nqs_stage_times",
+            "nqs_set_hamiltonian", "nqs_set_ansatz", "nqs_connected", "nqs_amplitude",
+            "nqs_draws", "nqs_local_energy", "nqs_grad_log_psi_vjp"]
+
+
+def _ptr(x):
+    """Data pointer of a torch tensor / numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return C.c_void_p(x.ctypes.data)
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _check(ctx, status):
+    if status != NQS_OK:
+        msg = load().nqs_last_error(ctx)
+        raise NQSError(status, (msg or b"").decode())
+
+
+# ---- same-named wrappers of the C ABI --------------------------------------
+
+def nqs_create(device: int = 0, stream: int = 0):
+    h = C.c_void_p()
+    st = load().nqs_create(C.byref(h), device, C.c_void_p(stream or None))
+    if st != NQS_OK:
+        raise NQSError(st, f"nqs_create(device={device}) failed")
+    return h
+
+
+def nqs_destroy(ctx):
+    load().nqs_destroy(ctx)
+
+
+def nqs_last_error(ctx) -> str:
+    return (load().nqs_last_error(ctx) or b"").decode()
+
+
+def nqs_set_options(ctx, precision: int, timing: int = 0):
+    o = Options()
+    o.precision = precision
+    o.timing = timing
+    _check(ctx, load().nqs_set_options(ctx, C.byref(o)))
+
+
+def nqs_stage_times(ctx, ms, launches, n=N_STAGES):
+    _check(ctx, load().nqs_stage_times(ctx, _ptr(ms), _ptr(launches), n))
+
+
+def nqs_set_hamiltonian(ctx, h1e, chol_or_eri, n_chol, n_orb, n_alpha, n_beta, e_core=0.0):
+    _check(ctx, load().nqs_set_hamiltonian(ctx, _ptr(h1e), _ptr(chol_or_eri), n_chol, n_orb,
+                                           n_alpha, n_beta, float(e_core)))
+
+
+def nqs_set_ansatz(ctx, tensors, n_edges, bond_dim, pred_ptr, pred_idx, rbm_W, rbm_b, n_hidden):
+    _check(ctx, load().nqs_set_ansatz(ctx, _ptr(tensors), n_edges, bond_dim, _ptr(pred_ptr),
+                                      _ptr(pred_idx), _ptr(rbm_W), _ptr(rbm_b), n_hidden))
+
+
+def nqs_connected(ctx, samples, Ns, eps, offsets, rank, dets, H, sign, capacity):
+    _check(ctx, load().nqs_connected(ctx, _ptr(samples), Ns, float(eps), _ptr(offsets), _ptr(rank),
+                                     _ptr(dets), _ptr(H), _ptr(sign), capacity))
+
+
+def nqs_amplitude(ctx, dets, n, log_abs, sign):
+    _check(ctx, load().nqs_amplitude(ctx, _ptr(dets), n, _ptr(log_abs), _ptr(sign)))
+
+
+def nqs_draws(ctx, samples, Ns, eps, n_draws, seed, ranks, w_total):
+    _check(ctx, load().nqs_draws(ctx, _ptr(samples), Ns, float(eps), n_draws, seed, _ptr(ranks),
+                                 _ptr(w_total)))
+
+
+def nqs_local_energy(ctx, samples, counts, Ns, eps, n_draws, seed, e_loc, summary=None):
+    _check(ctx, load().nqs_local_energy(ctx, _ptr(samples), _ptr(counts), Ns, float(eps), n_draws,
+                                        seed, _ptr(e_loc),
+                                        C.byref(summary) if summary is not None else None))
+
+
+def nqs_grad_log_psi_vjp(ctx, samples, u, Ns, grad_sites, grad_W, grad_b):
+    _check(ctx, load().nqs_grad_log_psi_vjp(ctx, _ptr(samples), _ptr(u), Ns, _ptr(grad_sites),
+                                            _ptr(grad_W), _ptr(grad_b)))
+
+
+# ---- convenience wrapper ----------------------------------------------------
+
+def _np(a, dt):
+    return None if a is None else np.ascontiguousarray(a, dtype=dt)
+
+
+class Context:
+    """One library context bound to a device and a CUDA stream."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self.device = device
+        self.h = nqs_create(device, stream)
+        self.K = None
+        self.n_edges = None
+        self.D = None
+        self.n_hidden = 0
+
+    def close(self):
+        if self.h is not None:
+            nqs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_precision(self, precision: int, timing: bool = False):
+        nqs_set_options(self.h, precision, int(bool(timing)))
+
+    def stage_times(self):
+        """{stage: (device ms, kernel launches)} since the previous call."""
+        ms = np.zeros(N_STAGES, np.float64)
+        nl = np.zeros(N_STAGES, np.int64)
+        nqs_stage_times(self.h, ms, nl, N_STAGES)
+        return {k: (float(ms[i]), int(nl[i])) for i, k in enumerate(STAGES)}
+
+    def set_system(self, sys_, use_eri=None):
+        """Upload the Hamiltonian and ansatz of a workloads.System."""
+        h1e = _np(sys_.h1e, np.float64)
+        if use_eri is not None:
+            nqs_set_hamiltonian(self.h, h1e, _np(use_eri, np.float64), 0, sys_.K, sys_.n_alpha,
+                                sys_.n_beta, sys_.e_core)
+        else:
+            L = _np(sys_.chol, np.float64)
+            nqs_set_hamiltonian(self.h, h1e, L, L.shape[0], sys_.K, sys_.n_alpha, sys_.n_beta,
+                                sys_.e_core)
+        self.K = sys_.K
+        self.set_ansatz(sys_.tensors, sys_.pred_ptr, sys_.pred_idx, sys_.rbm_W, sys_.rbm_b)
+
+    def set_ansatz(self, tensors, pred_ptr=None, pred_idx=None, W=None, b=None):
+        T = tensors if hasattr(tensors, "data_ptr") else _np(tensors, np.float64)
+        self.n_edges, self.D = int(T.shape[0]), int(T.shape[-1])
+        self.n_hidden = 0 if W is None else int(W.shape[0])
+        self._keep = (T, _np(pred_ptr, np.int32), _np(pred_idx, np.int32),
+                      W if (W is None or hasattr(W, "data_ptr")) else _np(W, np.float64),
+                      b if (b is None or hasattr(b, "data_ptr")) else _np(b, np.float64))
+        T, pp, pi, Wc, bc = self._keep
+        nqs_set_ansatz(self.h, T, self.n_edges, self.D, pp, pi, Wc, bc, self.n_hidden)
+
+    def connected(self, samples, eps=0.0):
+        """Host-side lists: (offsets, rank, dets, H, sign) as numpy arrays."""
+        s = _np(samples, np.uint64).reshape(-1, 2)
+        Ns = len(s)
+        off = np.zeros(Ns + 1, np.int64)
+        nqs_connected(self.h, s, Ns, eps, off, None, None, None, None, 0)
+        n = int(off[-1])
+        rank = np.empty(max(n, 1), np.uint32)
+        dets = np.empty((max(n, 1), 2), np.uint64)
+        H = np.empty(max(n, 1), np.float64)
+        sg = np.empty(max(n, 1), np.int8)
+        nqs_connected(self.h, s, Ns, eps, off, rank, dets, H, sg, n)
+        return off, rank[:n], dets[:n], H[:n], sg[:n]
+
+    def amplitude(self, dets):
+        d = _np(dets, np.uint64).reshape(-1, 2)
+        la = np.empty(len(d), np.float64)
+        sg = np.empty(len(d), np.int8)
+        nqs_amplitude(self.h, d, len(d), la, sg)
+        return la, sg
+
+    def draws(self, samples, eps, n_draws, seed):
+        s = _np(samples, np.uint64).reshape(-1, 2)
+        r = np.empty((len(s), max(n_draws, 1)), np.int64)
+        w = np.empty(len(s), np.uint64)
+        nqs_draws(self.h, s, len(s), eps, n_draws, seed, r, w)
+        return r[:, :n_draws], w
+
+    def local_energy(self, samples, counts=None, eps=0.0, n_draws=0, seed=0, out=None):
+        """E_loc per sample and the summary. `samples` / `counts` / `out` may be
+        CUDA tensors (no host copies) or host arrays."""
+        if hasattr(samples, "data_ptr"):
+            Ns = int(samples.shape[0])
+            s = samples
+        else:
+            s = _np(samples, np.uint64).reshape(-1, 2)
+            Ns = len(s)
+        c = counts if (counts is None or hasattr(counts, "data_ptr")) else _np(counts, np.float64)
+        e = out if out is not None else np.empty(Ns, np.float64)
+        summ = EnergySummary()
+        nqs_local_energy(self.h, s, c, Ns, eps, n_draws, seed, e, summ)
+        return e, summ.as_dict()
+
+    def grad_log_psi_vjp(self, samples, u):
+        s = _np(samples, np.uint64).reshape(-1, 2)
+        uu = _np(u, np.float64)
+        gT = np.empty((self.n_edges, 4, self.D, self.D), np.float64)
+        gW = np.empty((self.n_hidden, 2 * self.K), np.float64) if self.n_hidden else None
+        gb = np.empty(self.n_hidden, np.float64) if self.n_hidden else None
+        nqs_grad_log_psi_vjp(self.h, s, uu, len(s), gT, gW, gb)
+        return gT, gW, gb

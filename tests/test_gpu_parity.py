@@ -1,0 +1,237 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Bars (from the method's statement of the problem):
+  * connected lists, canonical ranks, determinants, fermionic signs, H_nm and
+    deterministic-set membership: bit-exact;
+  * drawn indices of the stochastic part and the total remainder weight W:
+    bit-exact;
+  * FP64 local energies: within 1e-12 relative of the oracle;
+  * log|psi|: within 1e-12 absolute; gradients within 1e-10 relative.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2507_19276_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2507_19276_gb300 import nqs  # noqa: E402
+
+RTOL_FP64 = 1e-12
+
+
+def _cases():
+    h50 = W.h50_chain()
+    fe = W.fe2s2_dense()
+    h18 = W.h18_graph()
+    return {
+        "tiny": W.tiny_system(K=6, na=3, nb=2, D=4, n_hidden=5, seed=3),
+        "tiny_graph": W.tiny_system(K=6, na=3, nb=3, D=4, n_hidden=5, seed=4, graph=True),
+        "k8": W.small_chain(),
+        "h50": h50.subset([0, 1, 2, 4095]),
+        "fe2s2": fe.subset([0, 8191]),
+        "h18": h18.subset([0, 1, 2, 3, 16380, 16381, 16382, 16383]),
+    }
+
+
+@pytest.fixture(scope="module")
+def cases():
+    return _cases()
+
+
+@pytest.fixture(scope="module")
+def problems(cases):
+    return {k: O.Problem(v) for k, v in cases.items()}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = nqs.Context(0)
+    yield c
+    c.close()
+
+
+def _load(ctx, sys_, precision=nqs.NQS_PREC_FP64):
+    ctx.set_system(sys_)
+    ctx.set_precision(precision)
+
+
+# ---------------------------------------------------------------------------
+# connectivity
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["tiny", "tiny_graph", "k8", "h50", "fe2s2", "h18"])
+def test_connected_lists_bit_exact(ctx, cases, problems, name):
+    sys_, P = cases[name], problems[name]
+    _load(ctx, sys_)
+    for eps in sorted({0.0, 1e-3, 2e-2}):
+        off, rank, dets, H, sg = ctx.connected(sys_.samples, eps)
+        assert off[0] == 0
+        for s, n in enumerate(sys_.samples):
+            od, oh, os_ = O.connected(P, n)
+            keep = np.nonzero(np.abs(oh) >= eps)[0]
+            a, b = off[s], off[s + 1]
+            assert b - a == len(keep), (name, eps, s)
+            assert np.array_equal(rank[a:b], keep.astype(np.uint32))
+            assert np.array_equal(dets[a:b], od[keep])
+            assert np.array_equal(H[a:b].view(np.uint64), oh[keep].view(np.uint64))
+            assert np.array_equal(sg[a:b], os_[keep])
+
+
+def test_connected_sizes_query_and_capacity(ctx, cases):
+    sys_ = cases["k8"]
+    _load(ctx, sys_)
+    s = np.ascontiguousarray(sys_.samples[:3])
+    off = np.zeros(4, np.int64)
+    nqs.nqs_connected(ctx.h, s, 3, 0.0, off, None, None, None, None, 0)
+    assert off[-1] == 3 * O.n_conn(8, 4, 4)
+    rank = np.empty(10, np.uint32)
+    with pytest.raises(nqs.NQSError) as ei:
+        nqs.nqs_connected(ctx.h, s, 3, 0.0, off, rank, None, None, None, 10)
+    assert ei.value.status == 1 and "capacity" in str(ei.value)
+
+
+# ---------------------------------------------------------------------------
+# stochastic draws
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,eps,nd", [("h50", 1e-3, 1024), ("tiny", 0.05, 333),
+                                         ("h18", 1e-2, 100), ("fe2s2", 1e-2, 257)])
+def test_draws_bit_exact(ctx, cases, problems, name, eps, nd):
+    sys_, P = cases[name], problems[name]
+    _load(ctx, sys_)
+    seed = 2507192761
+    ranks, wt = ctx.draws(sys_.samples, eps, nd, seed)
+    for s, n in enumerate(sys_.samples):
+        ref, Wref, _ = O.draws(P, n, s, eps, nd, seed)
+        assert int(wt[s]) == Wref
+        assert np.array_equal(ranks[s], ref)
+
+
+# ---------------------------------------------------------------------------
+# local energy, FP64
+# ---------------------------------------------------------------------------
+
+def _rel(a, b):
+    return np.max(np.abs(a - b) / np.maximum(1e-300, np.abs(b)))
+
+
+@pytest.mark.parametrize("name", ["tiny", "tiny_graph", "k8", "h50", "fe2s2", "h18"])
+def test_local_energy_fp64_matches_oracle(ctx, cases, problems, name):
+    sys_, P = cases[name], problems[name]
+    _load(ctx, sys_)
+    e, summ = ctx.local_energy(sys_.samples, sys_.counts, sys_.eps, sys_.n_draws, sys_.seed)
+    ref = O.local_energy(P)
+    assert _rel(e, ref["e_loc"]) < RTOL_FP64
+    ebar = np.sum(sys_.counts * ref["e_loc"]) / np.sum(sys_.counts)
+    assert abs(summ["e_mean"] - ebar) < RTOL_FP64 * abs(ebar)
+    assert summ["n_det"] == int(np.sum(ref["n_det"]))
+    assert summ["n_conn"] == O.n_conn(sys_.K, sys_.n_alpha, sys_.n_beta)
+    eb, Bs, m, et = O.summary(ref, sys_.counts)
+    assert abs(summ["log_B"] - (m + np.log(Bs))) < 1e-10
+    etm = np.sum(sys_.counts * et) / np.sum(sys_.counts)
+    assert abs(summ["e_tilde_mean"] - etm) < 1e-10 * abs(etm)
+
+
+def test_local_energy_stochastic_edge_cases(ctx, cases, problems):
+    sys_, P = cases["tiny"], problems["tiny"]
+    _load(ctx, sys_)
+    exact = O.local_energy(P, eps=0.0, n_draws=0)["e_loc"]
+    # eps = 0 with draws: empty remainder, E^s = 0
+    e, s = ctx.local_energy(sys_.samples, None, 0.0, 64, 5)
+    assert _rel(e, exact) < RTOL_FP64 and s["n_draw_unique"] == 0
+    # eps above every |H|: everything is drawn
+    ref = O.local_energy(P, eps=1e3, n_draws=200, seed=9)
+    e, s = ctx.local_energy(sys_.samples, None, 1e3, 200, 9)
+    assert s["n_det"] == 0 and _rel(e, ref["e_loc"]) < RTOL_FP64
+    # no draws: deterministic part only
+    ref = O.local_energy(P, eps=0.05, n_draws=0)
+    e, _ = ctx.local_energy(sys_.samples, None, 0.05, 0, 9)
+    assert _rel(e, ref["e_loc"]) < RTOL_FP64
+    # empty batch
+    e, s = ctx.local_energy(np.zeros((0, 2), np.uint64), None, 0.0, 0, 0)
+    assert len(e) == 0
+
+
+def test_invalid_samples_are_rejected(ctx, cases):
+    sys_ = cases["k8"]
+    _load(ctx, sys_)
+    bad = np.array(sys_.samples[:5], copy=True)
+    bad[3, 0] = np.uint64(0b111)                     # 3 alpha electrons, 4 expected
+    with pytest.raises(nqs.NQSError) as ei:
+        ctx.local_energy(bad, None, 0.0, 0, 0)
+    assert ei.value.status == 1 and "samples[3]" in str(ei.value)
+    bad[3, 0] = np.uint64(0b1111) | np.uint64(1 << 9)
+    with pytest.raises(nqs.NQSError):
+        ctx.connected(bad, 0.0)
+    with pytest.raises(nqs.NQSError):
+        ctx.local_energy(sys_.samples, None, -1.0, 0, 0)
+    with pytest.raises(nqs.NQSError):
+        ctx.local_energy(sys_.samples, None, 0.0, 5000, 0)
+
+
+def test_degenerate_systems(ctx):
+    # one orbital pair: no excitations at all, E_loc = H_nn
+    for K, na, nb in [(1, 1, 1), (2, 1, 0), (2, 2, 1), (3, 0, 3)]:
+        sys_ = W.tiny_system(K=K, na=na, nb=nb, D=2, seed=K + na)
+        P = O.Problem(sys_)
+        _load(ctx, sys_)
+        e, s = ctx.local_energy(sys_.samples, None, 0.0, 8, 1)
+        ref = O.local_energy(P, eps=0.0, n_draws=8, seed=1)
+        assert _rel(e, ref["e_loc"]) < RTOL_FP64
+        assert s["n_conn"] == O.n_conn(K, na, nb)
+
+
+def test_device_and_host_buffers_agree(ctx, cases):
+    sys_ = cases["h18"]
+    _load(ctx, sys_)
+    e_host, _ = ctx.local_energy(sys_.samples, sys_.counts, 0.0, 0, 0)
+    s_dev = torch.from_numpy(sys_.samples.view(np.int64)).cuda()
+    c_dev = torch.from_numpy(sys_.counts).cuda()
+    out = torch.empty(len(sys_.samples), dtype=torch.float64, device="cuda")
+    ctx.local_energy(s_dev, c_dev, 0.0, 0, 0, out=out)
+    assert np.array_equal(out.cpu().numpy(), e_host)
+
+
+# ---------------------------------------------------------------------------
+# amplitudes and gradients
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["tiny", "tiny_graph", "k8", "h50", "fe2s2", "h18"])
+def test_amplitude_matches_oracle(ctx, cases, problems, name):
+    sys_, P = cases[name], problems[name]
+    _load(ctx, sys_)
+    od, _, _ = O.connected(P, sys_.samples[0])
+    dets = np.concatenate([sys_.samples, od[:: max(1, len(od) // 200)]])
+    la, sg = ctx.amplitude(dets)
+    for d, l, s in zip(dets, la, sg):
+        rl, rs, _ = O.log_psi(P, d)
+        assert s == rs and abs(l - rl) < 1e-12 * max(1.0, abs(rl))
+
+
+@pytest.mark.parametrize("name", ["tiny", "tiny_graph", "k8", "h18"])
+def test_grad_vjp_matches_oracle(ctx, cases, problems, name):
+    sys_, P = cases[name], problems[name]
+    _load(ctx, sys_)
+    rng = np.random.default_rng(1)
+    u = rng.normal(size=len(sys_.samples))
+    gT, gW, gb = ctx.grad_log_psi_vjp(sys_.samples, u)
+    rT = np.zeros_like(gT)
+    rW = np.zeros_like(gW) if gW is not None else None
+    rb = np.zeros_like(gb) if gb is not None else None
+    for ui, d in zip(u, sys_.samples):
+        t, w, b = O.grad_log_psi(P, d)
+        rT += ui * t
+        if rW is not None:
+            rW += ui * w
+            rb += ui * b
+    scale = np.max(np.abs(rT))
+    assert np.max(np.abs(gT - rT)) < 1e-10 * scale
+    if rW is not None:
+        assert np.max(np.abs(gW - rW)) < 1e-10 * max(1.0, np.max(np.abs(rW)))
+        assert np.max(np.abs(gb - rb)) < 1e-10 * max(1.0, np.max(np.abs(rb)))
