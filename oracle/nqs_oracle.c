@@ -472,7 +472,7 @@ static void one_sample(const or_ham* h, const or_ansatz* a, const uint64_t* n, i
     o->w_shift = sp.shift;
 
     /* deterministic part: sum over |H_nm| >= eps in canonical order */
-    double ed = 0.0;
+    double ed = 0.0, eabs = fabs(o->h_diag);
     int64_t ndet = 0;
     for (int64_t r = 0; r < sp.nc; ++r) {
         if (!(fabs(sp.H[r]) >= eps)) continue;
@@ -482,6 +482,7 @@ static void one_sample(const or_ham* h, const or_ansatz* a, const uint64_t* n, i
         or_log_psi(a, &sp.dets[2 * r], &la_m, &sg_m, &lf_m);
         double ratio = (double)(sg_m * sg_n) * exp(la_m - la_n);
         ed += sp.H[r] * ratio;
+        eabs += fabs(sp.H[r] * ratio);
     }
     o->n_det = ndet;
     o->e_det = ed;
@@ -498,10 +499,12 @@ static void one_sample(const or_ham* h, const or_ansatz* a, const uint64_t* n, i
             or_log_psi(a, &sp.dets[2 * r], &la_m, &sg_m, &lf_m);
             double ratio = (double)(sg_m * sg_n) * exp(la_m - la_n);
             es += sp.H[r] * ((double)sp.W / (double)w) * ratio;
+            eabs += fabs(sp.H[r] * ((double)sp.W / (double)w) * ratio) / (double)n_draws;
         }
         es /= (double)n_draws;
     }
     o->e_stoch = es;
+    o->e_abs = eabs;
     o->e_loc = o->h_diag + ed + es;
     split_free(&sp);
 }

@@ -53,6 +53,8 @@ typedef struct {
 
 typedef struct {
     double e_loc, e_det, e_stoch, h_diag;
+    double e_abs;            /* |H_nn| + sum |terms| of E^d and E^s: the scale
+                                that rounding errors of the sums are relative to */
     double log_abs_psi;      /* log|psi(n)| (TN x correlator) */
     double log_f;            /* log f(n) */
     int sign_psi;

@@ -48,7 +48,8 @@ class Ansatz(C.Structure):
 
 class SampleOut(C.Structure):
     _fields_ = [("e_loc", C.c_double), ("e_det", C.c_double), ("e_stoch", C.c_double),
-                ("h_diag", C.c_double), ("log_abs_psi", C.c_double), ("log_f", C.c_double),
+                ("h_diag", C.c_double), ("e_abs", C.c_double), ("log_abs_psi", C.c_double),
+                ("log_f", C.c_double),
                 ("sign_psi", C.c_int), ("n_det", C.c_int64), ("n_rem", C.c_int64),
                 ("w_total", C.c_uint64), ("w_shift", C.c_int)]
 
@@ -154,7 +155,7 @@ def draws(P: Problem, det, sample_index, eps, n_draws, seed):
 
 
 SAMPLE_DTYPE = np.dtype([("e_loc", "f8"), ("e_det", "f8"), ("e_stoch", "f8"),
-                         ("h_diag", "f8"), ("log_abs_psi", "f8"), ("log_f", "f8"),
+                         ("h_diag", "f8"), ("e_abs", "f8"), ("log_abs_psi", "f8"), ("log_f", "f8"),
                          ("sign_psi", "i4"), ("n_det", "i8"), ("n_rem", "i8"),
                          ("w_total", "u8"), ("w_shift", "i4")], align=True)
 assert SAMPLE_DTYPE.itemsize == C.sizeof(SampleOut)

@@ -98,7 +98,7 @@ int launch_scan_chunks_u64(uint64_t* w, uint64_t* total, int64_t Ns, uint32_t n_
     return 1;
 }
 
-__global__ void k_scan_i64(const int64_t* in, int64_t* out, int64_t n, int rows)
+__global__ void __launch_bounds__(1024) k_scan_i64(const int64_t* in, int64_t* out, int64_t n, int rows)
 {
     __shared__ int64_t wt[32];
     int64_t carry = 0;
@@ -157,7 +157,7 @@ __device__ double block_reduce_sum(double v, double* sh)
     return r;   // valid in thread 0
 }
 
-__global__ void k_summary(FinalArgs a)
+__global__ void __launch_bounds__(256) k_summary(FinalArgs a)
 {
     __shared__ double sh[32];
     __shared__ double bc;
@@ -218,7 +218,7 @@ int launch_finalize(const FinalArgs& a, cudaStream_t st)
 {
     if (a.Ns == 0) return 0;
     k_final_samples<<<(unsigned)((a.Ns + 255) / 256), 256, 0, st>>>(a);
-    if (a.summary) k_summary<<<1, 1024, 0, st>>>(a);
+    if (a.summary) k_summary<<<1, 256, 0, st>>>(a);
     return a.summary ? 2 : 1;
 }
 
