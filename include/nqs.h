@@ -32,7 +32,8 @@
  *    Host inputs are staged to the device on the context's stream; host
  *    outputs are copied back and the stream is synchronised before return.
  *  - nqs_set_* copy their arguments; the caller may free them afterwards.
- *  - Outputs are valid only when a call returns NQS_OK.
+ *  - Outputs are valid only when a call returns NQS_OK (their contents are
+ *    unspecified otherwise).
  *  - A context is not thread safe; use one context per host thread.
  *
  * Errors: every call returns an nqs_status. NQS_ERR_INVALID_ARG names the
@@ -59,10 +60,14 @@ typedef enum {
 } nqs_status;
 
 typedef enum {
-    NQS_PREC_FP64 = 0,   /* every step in FP64 on CUDA cores (the plain form) */
-    NQS_PREC_MIXED = 1   /* amplitude contractions on tcgen05 tensor cores in
-                            split FP16 with FP32 accumulation; H_nm, ratios and
-                            the E_loc sums stay FP64 */
+    NQS_PREC_FP64 = 0,        /* the plain form: every amplitude psi(m) is its own
+                                 FP64 product over the sites where m differs from n
+                                 (cached left/right environments outside that span) */
+    NQS_PREC_MIXED = 1,       /* shared-prefix evaluation (chain ansatz): partial
+                                 products common to many m of one n are formed once
+                                 and each psi(m) is one dot product; contractions in
+                                 FP32, H_nm, the ratios and the E_loc sums in FP64 */
+    NQS_PREC_FP64_SHARED = 2  /* the shared-prefix evaluation with FP64 contractions */
 } nqs_precision;
 
 typedef struct nqs_ctx nqs_ctx;

@@ -11,6 +11,7 @@
 
 #include "../../include/nqs.h"
 #include "nqs_kernels.cuh"
+#include "nqs_family.cuh"
 #include "nqs_mixed.cuh"
 
 using namespace nqs;
@@ -40,6 +41,7 @@ struct nqs_ctx {
     bool has_ans = false;
     AnsatzView av{};
     DevBuf A, AT, W, b, pred_ptr, pred_idx;
+    DevBuf Af, ATf, Wf;       // FP32 copies for the shared-prefix FP32 path
     MixedAnsatz mixed{};
     DevBuf mixed_buf;
 
@@ -50,6 +52,10 @@ struct nqs_ctx {
     DevBuf Wtot, draw_rank64, draw_rank, draw_coef, n_unique;
     DevBuf base_det, base_draw, part_det, part_draw, eloc, edet, estoch, summary, derr;
     DevBuf span_det, span_draw;
+    // shared-prefix path
+    DevBuf fG, fGe, fH, fHe, fpm, fpe, ftl_end, ftl_idx, ftr_idx, ftl_tot, ftr_tot, ftl_base,
+        ftr_base, fTL, fTLe, fTR, fTRe;
+    std::vector<int64_t> det_off_h;
     DevBuf mixed_ws;
 
     // stage accounting (nqs_stage_times)
@@ -240,10 +246,10 @@ struct StageScope {
 
 #define LAUNCH(stage, expr) (c->stage_launch[(stage)] += (expr))
 
-__global__ void k_check_psi(const double* mant, int64_t Ns, DevError* err)
+__global__ void k_check_psi(const double* mant, int64_t Ns, DevError* err, int64_t offset = 0)
 {
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < Ns && mant[s] == 0.0) report(err, NQS_ERR_INVALID_ARG, 3, s);
+    if (s < Ns && mant[s] == 0.0) report(err, NQS_ERR_INVALID_ARG, 3, s + offset);
 }
 
 int eps_bits(nqs_ctx* c, double eps, uint64_t* bits)
@@ -282,7 +288,7 @@ int count_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, uint64_t eb, int
     return NQS_OK;
 }
 
-int env_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, bool adjoints)
+int env_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, bool adjoints, bool tn = true)
 {
     const int K = c->K, D = c->av.D, NH = c->av.n_hidden;
     EnvArgs e{};
@@ -290,7 +296,10 @@ int env_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, bool adjoints)
     e.h = c->hv;
     e.samples = samples;
     e.Ns = Ns;
-    if (c->av.chain) {
+    e.tn = tn ? 1 : 0;
+    if (!tn) {
+        // shared-prefix path: psi(n) comes from its own sweep
+    } else if (c->av.chain) {
         TRY(ensure(c, c->Lenv, (size_t)Ns * (K + 1) * D * 8));
         TRY(ensure(c, c->Renv, (size_t)Ns * (K + 1) * D * 8));
         TRY(ensure(c, c->Lexp, (size_t)Ns * (K + 1) * 4));
@@ -371,6 +380,138 @@ int amp_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, RowSet rows, int64
     return NQS_OK;
 }
 
+// Shared-prefix amplitudes of the deterministic and drawn rows (chain ansatz),
+// samples processed in batches whose tables fit the memory budget.
+template <typename T>
+int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, int n_draws)
+{
+    const int K = c->K, D = c->av.D;
+    const size_t nk = (size_t)K * K * 9;
+    constexpr int kRows = 128;
+    StageScope sc(c, NQS_STAGE_AMP_DET);
+    // row chunk bases (128 rows per chunk) over all samples
+    TRY(ensure(c, c->base_det, (size_t)(Ns + 1) * 8));
+    const int64_t max_det_chunks = total_det / kRows + Ns;
+    TRY(ensure(c, c->part_det, (size_t)(max_det_chunks + 1) * 8));
+    TRY(ensure(c, c->span_det, (size_t)(max_det_chunks + 1) * 8));
+    LAUNCH(NQS_STAGE_AMP_DET, launch_chunk_base((const int64_t*)c->det_tot.p, kRows, (int64_t*)c->base_det.p, Ns, c->stream));
+    const int64_t per_draw = n_draws > 0 ? (n_draws + kRows - 1) / kRows : 0;
+    if (n_draws > 0) {
+        TRY(ensure(c, c->base_draw, (size_t)(Ns + 1) * 8));
+        TRY(ensure(c, c->part_draw, (size_t)(Ns * per_draw + 1) * 8));
+        TRY(ensure(c, c->span_draw, (size_t)(Ns * per_draw + 1) * 8));
+        LAUNCH(NQS_STAGE_AMP_DET, launch_chunk_base((const int64_t*)c->n_unique.p, kRows, (int64_t*)c->base_draw.p, Ns, c->stream));
+    }
+    // batch size from a memory budget
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const size_t budget = std::min<size_t>((size_t)8 << 30, free_b / 3);
+    const size_t per = fam_bytes_per_sample(K, D, sizeof(T));
+    int64_t nb = (int64_t)std::max<size_t>(1, budget / per);
+    if (nb > Ns) nb = Ns;
+    if (nb > 65535) nb = 65535;
+    const size_t KKD = (size_t)3 * K * K * D;
+    TRY(ensure(c, c->fG, nb * KKD * sizeof(T)));
+    TRY(ensure(c, c->fH, nb * KKD * sizeof(T)));
+    TRY(ensure(c, c->fGe, nb * 3 * K * K * 4));
+    TRY(ensure(c, c->fHe, nb * 3 * K * K * 4));
+    TRY(ensure(c, c->fpm, nb * 8));
+    TRY(ensure(c, c->fpe, nb * 4));
+    TRY(ensure(c, c->ftl_end, nb * nk * 4));
+    TRY(ensure(c, c->ftl_idx, nb * nk * 4));
+    TRY(ensure(c, c->ftr_idx, nb * nk * 4));
+    TRY(ensure(c, c->ftl_tot, nb * 8));
+    TRY(ensure(c, c->ftr_tot, nb * 8));
+    TRY(ensure(c, c->ftl_base, (nb + 1) * 8));
+    TRY(ensure(c, c->ftr_base, (nb + 1) * 8));
+    const bool dbl = sizeof(T) == 8;
+    FamArgs<T> f{};
+    f.h = c->hv;
+    f.K = K;
+    f.D = D;
+    f.threads = D > 256 ? D : 256;
+    {
+        // vectors staged per block-wide batch: two [nmax][D] buffers within ~180 KB
+        int nm = (int)((180 * 1024) / (2 * (size_t)D * sizeof(T)));
+        nm = nm / 4 * 4;
+        f.nmax = nm < 4 ? 4 : (nm > 64 ? 64 : nm);
+    }
+    f.A = (const T*)(dbl ? c->A.p : c->Af.p);
+    f.AT = (const T*)(dbl ? c->AT.p : c->ATf.p);
+    f.samples = ds;
+    f.n_hidden = c->av.n_hidden;
+    f.W = (const T*)(dbl ? c->W.p : c->Wf.p);
+    f.theta = (const double*)c->theta.p;
+    RowSet rd{};
+    rd.rank = (const uint32_t*)c->det_rank.p;
+    rd.coef = (const double*)c->det_coef.p;
+    rd.begin = (const int64_t*)c->det_off.p;
+    rd.count = (const int64_t*)c->det_tot.p;
+    rd.chunk_base = (const int64_t*)c->base_det.p;
+    RowSet rs{};
+    if (n_draws > 0) {
+        rs.rank = (const uint32_t*)c->draw_rank.p;
+        rs.coef = (const double*)c->draw_coef.p;
+        rs.begin = nullptr;
+        rs.stride = n_draws;
+        rs.count = (const int64_t*)c->n_unique.p;
+        rs.chunk_base = (const int64_t*)c->base_draw.p;
+    }
+    for (int64_t s0 = 0; s0 < Ns; s0 += nb) {
+        const int64_t s1 = std::min(Ns, s0 + nb);
+        const int nbb = (int)(s1 - s0);
+        f.s0 = s0;
+        f.s1 = s1;
+        f.G = (T*)c->fG.p; f.Ge = (int*)c->fGe.p;
+        f.H = (T*)c->fH.p; f.He = (int*)c->fHe.p;
+        f.pm = (double*)c->fpm.p; f.pe = (int*)c->fpe.p;
+        f.tl_end = (int*)c->ftl_end.p;
+        f.tl_idx = (int*)c->ftl_idx.p;
+        f.tr_idx = (int*)c->ftr_idx.p;
+        f.tl_total = (int*)c->ftl_tot.p;
+        f.tr_total = (int*)c->ftr_tot.p;
+        CK(cudaMemsetAsync(c->ftl_end.p, 0xff, (size_t)nbb * nk * 4, c->stream));
+        CK(cudaMemsetAsync(c->ftr_idx.p, 0, (size_t)nbb * nk * 4, c->stream));
+        LAUNCH(NQS_STAGE_AMP_DET, fam_launch_sweep<T>(f, nbb, c->stream));
+        k_check_psi<<<(unsigned)((nbb + 255) / 256), 256, 0, c->stream>>>((const double*)c->fpm.p, nbb,
+                                                                         (DevError*)c->derr.p, s0);
+        LAUNCH(NQS_STAGE_AMP_DET, 1);
+        LAUNCH(NQS_STAGE_AMP_DET, fam_launch_mark<T>(f, rd, nbb, c->stream));
+        if (n_draws > 0) LAUNCH(NQS_STAGE_AMP_DET, fam_launch_mark<T>(f, rs, nbb, c->stream));
+        LAUNCH(NQS_STAGE_AMP_DET, fam_launch_compact<T>(f, nbb, c->stream));
+        // packed table offsets per sample of the batch
+        {
+            std::vector<int> tl(nbb), tr(nbb);
+            CK(cudaMemcpyAsync(tl.data(), c->ftl_tot.p, (size_t)nbb * 4, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaMemcpyAsync(tr.data(), c->ftr_tot.p, (size_t)nbb * 4, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            std::vector<int64_t> tlb(nbb + 1), trb(nbb + 1);
+            tlb[0] = trb[0] = 0;
+            for (int i = 0; i < nbb; ++i) { tlb[i + 1] = tlb[i] + tl[i]; trb[i + 1] = trb[i] + tr[i]; }
+            CK(cudaMemcpyAsync(c->ftl_base.p, tlb.data(), (size_t)(nbb + 1) * 8, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(c->ftr_base.p, trb.data(), (size_t)(nbb + 1) * 8, cudaMemcpyHostToDevice, c->stream));
+            TRY(ensure(c, c->fTL, (size_t)(tlb[nbb] + 1) * D * sizeof(T)));
+            TRY(ensure(c, c->fTLe, (size_t)(tlb[nbb] + 1) * 4));
+            TRY(ensure(c, c->fTR, (size_t)(trb[nbb] + 1) * D * sizeof(T)));
+            TRY(ensure(c, c->fTRe, (size_t)(trb[nbb] + 1) * 4));
+            CK(cudaStreamSynchronize(c->stream));   // the host vectors above must outlive the copies
+        }
+        f.tl_base = (const int64_t*)c->ftl_base.p;
+        f.tr_base = (const int64_t*)c->ftr_base.p;
+        f.TL = (T*)c->fTL.p; f.TLe = (int*)c->fTLe.p;
+        f.TR = (T*)c->fTR.p; f.TRe = (int*)c->fTRe.p;
+        LAUNCH(NQS_STAGE_AMP_DET, fam_launch_tables<T>(f, nbb, c->stream));
+        const int64_t det_rows = c->det_off_h[s1] - c->det_off_h[s0];
+        LAUNCH(NQS_STAGE_AMP_DET, fam_launch_rows<T>(f, rd, det_rows / kRows + nbb, (double*)c->part_det.p,
+                                                     (int64_t*)c->span_det.p, c->stream));
+        if (n_draws > 0)
+            LAUNCH(NQS_STAGE_AMP_DET, fam_launch_rows<T>(f, rs, (int64_t)nbb * per_draw, (double*)c->part_draw.p,
+                                                         (int64_t*)c->span_draw.p, c->stream));
+        CK(cudaGetLastError());
+    }
+    return NQS_OK;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -408,7 +549,10 @@ extern "C" int nqs_destroy(nqs_ctx* c)
                       &c->logf, &c->pmant, &c->pexp, &c->hdiag, &c->Wtot, &c->draw_rank64,
                       &c->draw_rank, &c->draw_coef, &c->n_unique, &c->base_det, &c->base_draw,
                       &c->part_det, &c->part_draw, &c->eloc, &c->edet, &c->estoch, &c->summary,
-                      &c->derr, &c->mixed_ws, &c->span_det, &c->span_draw};
+                      &c->derr, &c->mixed_ws, &c->span_det, &c->span_draw, &c->Af, &c->ATf,
+                      &c->Wf, &c->fG, &c->fGe, &c->fH, &c->fHe, &c->fpm, &c->fpe, &c->ftl_end,
+                      &c->ftl_idx, &c->ftr_idx, &c->ftl_tot, &c->ftr_tot, &c->ftl_base,
+                      &c->ftr_base, &c->fTL, &c->fTLe, &c->fTR, &c->fTRe};
     for (DevBuf* b : bufs) release(*b);
     for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);
@@ -422,7 +566,8 @@ extern "C" int nqs_set_options(nqs_ctx* c, const nqs_options* o)
 {
     if (!c || !o) return NQS_ERR_INVALID_ARG;
     c->err[0] = 0;
-    if (o->precision != NQS_PREC_FP64 && o->precision != NQS_PREC_MIXED)
+    if (o->precision != NQS_PREC_FP64 && o->precision != NQS_PREC_MIXED &&
+        o->precision != NQS_PREC_FP64_SHARED)
         return set_err(c, NQS_ERR_INVALID_ARG, "unknown precision %d", o->precision);
     for (int i = 0; i < 14; ++i)
         if (o->reserved[i]) return set_err(c, NQS_ERR_INVALID_ARG, "nqs_options.reserved[%d] != 0", i);
@@ -584,6 +729,23 @@ extern "C" int nqs_set_ansatz(nqs_ctx* c, const double* site_tensors, int n_edge
         TRY(ensure(c, c->b, (size_t)n_hidden * 8));
         CK(cudaMemcpy(c->W.p, rbm_W, nw * 8, cudaMemcpyDefault));
         CK(cudaMemcpy(c->b.p, rbm_b, (size_t)n_hidden * 8, cudaMemcpyDefault));
+    }
+    {
+        std::vector<float> fA(nt), fAT(nt);
+        for (size_t i = 0; i < nt; ++i) { fA[i] = (float)hA[i]; fAT[i] = (float)hAT[i]; }
+        TRY(ensure(c, c->Af, nt * 4));
+        TRY(ensure(c, c->ATf, nt * 4));
+        CK(cudaMemcpy(c->Af.p, fA.data(), nt * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->ATf.p, fAT.data(), nt * 4, cudaMemcpyHostToDevice));
+        if (n_hidden > 0) {
+            const size_t nw = (size_t)n_hidden * 2 * K;
+            std::vector<double> hW(nw);
+            CK(cudaMemcpy(hW.data(), c->W.p, nw * 8, cudaMemcpyDeviceToHost));
+            std::vector<float> fW(nw);
+            for (size_t i = 0; i < nw; ++i) fW[i] = (float)hW[i];
+            TRY(ensure(c, c->Wf, nw * 4));
+            CK(cudaMemcpy(c->Wf.p, fW.data(), nw * 4, cudaMemcpyHostToDevice));
+        }
     }
     AnsatzView a{};
     a.K = K; a.D = D; a.n_edges = n_edges; a.chain = chain ? 1 : 0;
@@ -802,16 +964,25 @@ extern "C" int nqs_local_energy(nqs_ctx* c, const uint64_t* samples, const doubl
     TRY(stage_in(c, c->st_samples, samples, (size_t)Ns * 2, &ds));
     TRY(stage_in(c, c->st_counts, counts, (size_t)Ns, &dc));
     TRY(reset_dev_error(c));
+    const bool shared = c->av.chain && (c->precision == NQS_PREC_MIXED || c->precision == NQS_PREC_FP64_SHARED);
+    if (shared && c->av.n_hidden > 512)
+        return set_err(c, NQS_ERR_UNSUPPORTED, "shared-prefix path supports n_hidden <= 512");
     {
         StageScope sc(c, NQS_STAGE_ENV);
         LAUNCH(NQS_STAGE_ENV, launch_validate(ds, Ns, c->K, c->na, c->nb, (DevError*)c->derr.p, c->stream));
-        TRY(env_pass(c, ds, Ns, false));
-        k_check_psi<<<(unsigned)((Ns + 255) / 256), 256, 0, c->stream>>>((const double*)c->pmant.p, Ns,
-                                                                       (DevError*)c->derr.p);
-        LAUNCH(NQS_STAGE_ENV, 1);
+        TRY(env_pass(c, ds, Ns, false, !shared));
+        if (!shared) {
+            k_check_psi<<<(unsigned)((Ns + 255) / 256), 256, 0, c->stream>>>((const double*)c->pmant.p, Ns,
+                                                                           (DevError*)c->derr.p);
+            LAUNCH(NQS_STAGE_ENV, 1);
+        }
     }
     int64_t total = 0;
     TRY(count_pass(c, ds, Ns, eb, &total));
+    if (shared) {
+        c->det_off_h.resize(Ns + 1);
+        CK(cudaMemcpyAsync(c->det_off_h.data(), c->det_off.p, (size_t)(Ns + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
     TRY(read_dev_error(c));
     TRY(ensure(c, c->det_rank, (size_t)total * 4));
     TRY(ensure(c, c->det_coef, (size_t)total * 8));
@@ -840,6 +1011,10 @@ extern "C" int nqs_local_energy(nqs_ctx* c, const uint64_t* samples, const doubl
         LAUNCH(NQS_STAGE_DRAW, launch_dedup(d, Ns, c->stream));
         CK(cudaGetLastError());
     }
+    if (shared) {
+        if (c->precision == NQS_PREC_MIXED) TRY(family_pass<float>(c, ds, Ns, total, n_draws));
+        else TRY(family_pass<double>(c, ds, Ns, total, n_draws));
+    } else {
     // amplitudes: deterministic rows, then the distinct drawn rows
     RowSet rd{};
     rd.rank = (const uint32_t*)c->det_rank.p;
@@ -855,6 +1030,7 @@ extern "C" int nqs_local_energy(nqs_ctx* c, const uint64_t* samples, const doubl
         rs.stride = n_draws;
         TRY(amp_pass(c, ds, Ns, rs, (int64_t)Ns * n_draws, (const int64_t*)c->n_unique.p,
                      c->base_draw, c->part_draw, c->span_draw, n_draws, NQS_STAGE_AMP_DRAW));
+    }
     }
     double* de;
     bool he;
@@ -881,6 +1057,7 @@ extern "C" int nqs_local_energy(nqs_ctx* c, const uint64_t* samples, const doubl
     }
     CK(cudaGetLastError());
     TRY(copy_back(c, e_loc, de, (size_t)Ns, he));
+    if (shared) TRY(read_dev_error(c));
     if (out) {
         double sm[8];
         CK(cudaMemcpyAsync(sm, c->summary.p, sizeof(sm), cudaMemcpyDeviceToHost, c->stream));

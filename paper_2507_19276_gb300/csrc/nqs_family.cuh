@@ -1,0 +1,52 @@
+// nqs_family.cuh -- shared-prefix amplitude evaluation for chain ansaetze
+// (see nqs_family.cu for the decomposition).
+#pragma once
+
+#include "nqs_kernels.cuh"
+
+namespace nqs {
+
+template <typename T>
+struct FamArgs {
+    HamView h;
+    int K, D;
+    int threads;              // block size of the per-sample kernels (>= D)
+    int nmax;                 // vectors staged per block-wide mat-vec batch
+    const T* A;               // [K][4][D][D] site tensors in T, A[a][b]
+    const T* AT;              // transposed copy, AT[b][a]
+    const uint64_t* samples;  // all samples of the call
+    int64_t s0, s1;           // batch = samples [s0, s1)
+    // per batch sample b (= s - s0)
+    T* G; int* Ge;            // [b][3][K][K][D]: G_{s,a}(t) at ((a*K+s)*K+t), t >= s
+    T* H; int* He;            // [b][3][K][K][D]: H_{s,a}(t) at ((a*K+s)*K+t), t <= s
+    double* pm; int* pe;      // psi_TN(n) = pm 2^pe
+    int* tl_end;              // [b][K*K*9] last site a TL cluster is needed at (-1: unused)
+    int* tl_idx;              // [b][K*K*9] entry offset of the cluster in the packed TL table
+    int* tr_idx;              // [b][K*K*9] marks, then row index in the packed TR table
+    int* tl_total; int* tr_total;      // [b]
+    const int64_t* tl_base; const int64_t* tr_base;   // [b] batch offsets (entries)
+    T* TL; int* TLe;          // packed TL entries
+    T* TR; int* TRe;          // packed TR rows
+    // correlator
+    int n_hidden;
+    const T* W;               // [n_hidden][2K]
+    const double* theta;      // [Ns][n_hidden] (all samples)
+};
+
+template <typename T> int fam_launch_sweep(const FamArgs<T>& f, int nb, cudaStream_t st);
+template <typename T> int fam_launch_mark(const FamArgs<T>& f, const RowSet& rows, int nb, cudaStream_t st);
+template <typename T> int fam_launch_compact(const FamArgs<T>& f, int nb, cudaStream_t st);
+template <typename T> int fam_launch_tables(const FamArgs<T>& f, int nb, cudaStream_t st);
+// grid = upper bound of the batch's row chunks (128 rows each); blocks map to
+// rows.chunk_base[s0] + blockIdx.x
+template <typename T> int fam_launch_rows(const FamArgs<T>& f, const RowSet& rows, int64_t grid,
+                                          double* partial, int64_t* span, cudaStream_t st);
+
+// bytes of the per-sample tables (G, H, their exponents, cluster maps)
+inline size_t fam_bytes_per_sample(int K, int D, size_t elem)
+{
+    const size_t KK = (size_t)K * K;
+    return 2 * (3 * KK * D * elem + 3 * KK * 4) + 3 * KK * 9 * 4 + 64;
+}
+
+}  // namespace nqs

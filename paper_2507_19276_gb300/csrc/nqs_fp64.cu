@@ -82,7 +82,9 @@ __global__ void k_env_fp64(EnvArgs a)
     const int64_t s = blockIdx.x;
     const uint64_t na = a.samples[2 * s], nb = a.samples[2 * s + 1];
 
-    if (a.an.chain) {
+    if (!a.tn) {
+        // tensor-network part done elsewhere
+    } else if (a.an.chain) {
         double* Ls = a.Lenv + (size_t)s * (K + 1) * D;
         int* Le = a.Lexp + (size_t)s * (K + 1);
         for (int i = threadIdx.x; i < D; i += blockDim.x) { x[i] = i == 0 ? 1.0 : 0.0; Ls[i] = x[i]; }

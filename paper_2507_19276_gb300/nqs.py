@@ -21,6 +21,7 @@ from . import build as _build
 NQS_OK = 0
 NQS_PREC_FP64 = 0
 NQS_PREC_MIXED = 1
+NQS_PREC_FP64_SHARED = 2
 STATUS = {0: "NQS_OK", 1: "NQS_ERR_INVALID_ARG", 2: "NQS_ERR_STATE", 3: "NQS_ERR_OOM",
           4: "NQS_ERR_CUDA", 5: "NQS_ERR_TIMEOUT", 6: "NQS_ERR_UNSUPPORTED"}
 

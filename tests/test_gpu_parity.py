@@ -58,7 +58,7 @@ def ctx():
     c.close()
 
 
-def _load(ctx, sys_, precision=nqs.NQS_PREC_FP64):
+def _load(ctx, sys_, precision=0):
     ctx.set_system(sys_)
     ctx.set_precision(precision)
 
@@ -143,6 +143,34 @@ def test_local_energy_fp64_matches_oracle(ctx, cases, problems, name):
     assert abs(summ["log_B"] - (m + np.log(Bs))) < 1e-10
     etm = np.sum(sys_.counts * et) / np.sum(sys_.counts)
     assert abs(summ["e_tilde_mean"] - etm) < 1e-10 * abs(etm)
+
+
+@pytest.mark.parametrize("name", ["tiny", "k8", "h50", "fe2s2"])
+def test_local_energy_shared_prefix_fp64_matches_oracle(ctx, cases, problems, name):
+    """The shared-prefix evaluation re-associates the same products: in FP64 it
+    must meet the FP64 bar."""
+    sys_, P = cases[name], problems[name]
+    _load(ctx, sys_, nqs.NQS_PREC_FP64_SHARED)
+    e, summ = ctx.local_energy(sys_.samples, sys_.counts, sys_.eps, sys_.n_draws, sys_.seed)
+    ref = O.local_energy(P)
+    assert _rel_sum(e, ref) < RTOL_FP64
+    assert summ["n_det"] == int(np.sum(ref["n_det"]))
+
+
+# FP32 contractions: tolerance stated against the summed-term magnitude
+RTOL_MIXED = 2e-5
+
+
+@pytest.mark.parametrize("name", ["tiny", "k8", "h50", "fe2s2"])
+def test_local_energy_mixed_matches_oracle(ctx, cases, problems, name):
+    sys_, P = cases[name], problems[name]
+    _load(ctx, sys_, nqs.NQS_PREC_MIXED)
+    e, summ = ctx.local_energy(sys_.samples, sys_.counts, sys_.eps, sys_.n_draws, sys_.seed)
+    ref = O.local_energy(P)
+    err = _rel_sum(e, ref)
+    print(f"{name}: mixed max error / summed magnitude = {err:.3e}")
+    assert err < RTOL_MIXED
+    assert summ["n_det"] == int(np.sum(ref["n_det"]))
 
 
 def test_local_energy_stochastic_edge_cases(ctx, cases, problems):
