@@ -42,7 +42,7 @@ def _peaks():
 
 # FP64 FMA throughput of one GB300, measured with a dependent-chain-free DFMA
 # probe ("FP64 peak"); used as the ALU roofline of the FP64 form.
-FP64_PEAK_TFLOPS = 1.25
+FP64_PEAK_TFLOPS = 1.196
 
 
 class ClockSampler:
@@ -182,7 +182,8 @@ def run(args):
     Ns = len(sys_.samples)
     ctx = nqs.Context(local)
     ctx.set_system(sys_)
-    prec = nqs.NQS_PREC_MIXED if args.precision == "mixed" else nqs.NQS_PREC_FP64
+    prec = {"mixed": nqs.NQS_PREC_MIXED, "fp64": nqs.NQS_PREC_FP64,
+            "fp64_shared": nqs.NQS_PREC_FP64_SHARED}[args.precision]
     ctx.set_precision(prec, timing=True)
 
     samples = torch.from_numpy(sys_.samples.view(np.int64)).to(dev)
@@ -235,31 +236,44 @@ def run(args):
     e2e_ms = max_over_ranks(e2e_ms, ws, dev)
     ctx.stage_times()
 
-    # roofline of the dominant kernel (amplitudes of the deterministic rows)
+    # roofline of the dominant kernel
     peaks, src = _peaks()
-    amp_ms, amp_launch = stages["amp_det"]
     work = summ.as_dict()
-    n_amp = work["n_amplitudes"]
-    span = work.get("span_sites", 0)
-    D = sys_.D
-    flops = 2.0 * D * D * span + 2.0 * D * n_amp       # per step
-    if prec == nqs.NQS_PREC_MIXED:
-        peak = peaks["bf16_tflops_sustained"]
-        roof = {"bound": "tensor", "unit": "TFLOP/s",
-                "peak_source": f"{src} bf16 dense (sustained), same rate as fp16 dense"}
+    n_amp, n_det = work["n_amplitudes"], work["n_det"]
+    D, NH = sys_.D, sys_.n_hidden
+    det_ms = stages["amp_det"][0] / args.steps
+    if prec == nqs.NQS_PREC_FP64:
+        # per-amplitude FP64 products: 2 D^2 flops per site of each row's span
+        flops = 2.0 * D * D * work["span_sites"] + 2.0 * D * n_amp
+        amp_ms = (stages["amp_det"][0] + stages["amp_draw"][0]) / args.steps
+        achieved = flops / (amp_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "peak_source": "FP64 DFMA probe, measured (DESIGN.md)",
+                "kernel": "k_amp_chain_fp64 (deterministic + drawn rows)",
+                "algorithmic_flops_per_step": flops}
     else:
-        peak = FP64_PEAK_TFLOPS
-        roof = {"bound": "alu", "unit": "TFLOP/s", "peak_source": "FP64 DFMA probe (DESIGN.md)"}
-    amp_ms_per_step = (stages["amp_det"][0] + stages["amp_draw"][0]) / args.steps
-    achieved = flops / (amp_ms_per_step / 1e3) / 1e12 if amp_ms_per_step > 0 else 0.0
-    roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
-                 "traffic": None, "kernel": "amplitudes (deterministic + drawn rows)",
-                 "algorithmic_flops_per_step": flops})
+        # k_fam_rows: per deterministic row the rank and coefficient, one left state and
+        # one right covector (D values each) and the two correlator factor rows
+        # (N_h+4 and 2 N_h values), in the contraction's element size
+        el = 4 if prec == nqs.NQS_PREC_MIXED else 8
+        np_ = (NH + 3) // 4 * 4 if NH else 0
+        per_row = 4 + 8 + 2 * D * el + ((np_ + 4) + 2 * np_) * el
+        nbytes = per_row * n_det
+        achieved = nbytes / (det_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "peak_source": f"{src} HBM copy bandwidth",
+                "kernel": "k_fam_rows (deterministic rows)",
+                "algorithmic_bytes_per_step": nbytes, "bytes_per_row": per_row}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel_ms_per_step"] = det_ms
+    roof["launches_per_step"] = stages["amp_det"][1] / args.steps
+    roof["matvecs_per_step"] = work["matvecs"]
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f16x3->f32 tensor + f64" if prec == nqs.NQS_PREC_MIXED else "f64",
+            "dtype": "f32 contractions + f64 H/ratios/sums" if prec == nqs.NQS_PREC_MIXED else "f64",
             "data": "synthetic", "config": workload_config(sys_, args.precision),
             "connected_dets_per_s": value * work["n_conn"],
             "amplitudes_per_s": ws * n_amp * args.steps / (ms / 1e3),
@@ -288,7 +302,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp64_shared"])
     ap.add_argument("--samples", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

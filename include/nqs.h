@@ -89,7 +89,9 @@ enum {
     NQS_STAGE_AMP_DRAW = 5,   /* amplitudes and ratios of the drawn rows */
     NQS_STAGE_FINAL = 6,      /* E_loc sums and the weighted summary */
     NQS_STAGE_OTHER = 7,      /* nqs_connected / nqs_amplitude / gradient work */
-    NQS_N_STAGES = 8
+    NQS_STAGE_TABLES = 8,     /* shared-prefix tables: family sweeps, cluster marks,
+                                 two-change clusters and their propagation */
+    NQS_N_STAGES = 9
 };
 
 typedef struct {
@@ -102,8 +104,13 @@ typedef struct {
     int64_t n_draw_unique;  /* sum over samples of distinct drawn m */
     int64_t n_amplitudes;   /* amplitudes evaluated = n_det + n_draw_unique */
     int64_t span_sites;     /* sum over evaluated amplitudes of the number of
-                               sites (chain) or vertices (graph) recomputed; the
-                               contraction work is 2 D^2 span_sites (x in-degree) */
+                               sites (chain) or vertices (graph) between the first
+                               and last changed one: the products a per-amplitude
+                               evaluation performs */
+    int64_t matvecs;        /* D x D matrix-vector products this call performed
+                               (equals span_sites, x in-degree for graphs, in the
+                               plain form; family sweeps plus two-change clusters in
+                               the shared-prefix form) */
 } nqs_energy_summary;
 
 /* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t

@@ -54,8 +54,10 @@ struct nqs_ctx {
     DevBuf span_det, span_draw;
     // shared-prefix path
     DevBuf fG, fGe, fH, fHe, fpm, fpe, ftl_end, ftl_idx, ftr_idx, ftl_tot, ftr_tot, ftl_base,
-        ftr_base, fTL, fTLe, fTR, fTRe;
+        ftr_base, fTL, fTLe, fTR, fTRe, ftl_ci, ftl_list, ftr_list, ftl_cnt, frbl, frbr, frbl_base,
+        frbr_base;
     std::vector<int64_t> det_off_h;
+    int64_t fam_matvecs = 0;   // work of the last shared-prefix pass
     DevBuf mixed_ws;
 
     // stage accounting (nqs_stage_times)
@@ -388,7 +390,7 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
     const int K = c->K, D = c->av.D;
     const size_t nk = (size_t)K * K * 9;
     constexpr int kRows = 128;
-    StageScope sc(c, NQS_STAGE_AMP_DET);
+    c->fam_matvecs = 0;
     // row chunk bases (128 rows per chunk) over all samples
     TRY(ensure(c, c->base_det, (size_t)(Ns + 1) * 8));
     const int64_t max_det_chunks = total_det / kRows + Ns;
@@ -420,6 +422,12 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
     TRY(ensure(c, c->ftl_end, nb * nk * 4));
     TRY(ensure(c, c->ftl_idx, nb * nk * 4));
     TRY(ensure(c, c->ftr_idx, nb * nk * 4));
+    TRY(ensure(c, c->ftl_ci, nb * nk * 4));
+    TRY(ensure(c, c->ftl_list, nb * nk * 4));
+    TRY(ensure(c, c->ftr_list, nb * nk * 4));
+    TRY(ensure(c, c->ftl_cnt, nb * 4));
+    TRY(ensure(c, c->frbl_base, (nb + 1) * 8));
+    TRY(ensure(c, c->frbr_base, (nb + 1) * 8));
     TRY(ensure(c, c->ftl_tot, nb * 8));
     TRY(ensure(c, c->ftr_tot, nb * 8));
     TRY(ensure(c, c->ftl_base, (nb + 1) * 8));
@@ -440,8 +448,9 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
     f.AT = (const T*)(dbl ? c->AT.p : c->ATf.p);
     f.samples = ds;
     f.n_hidden = c->av.n_hidden;
-    f.W = (const T*)(dbl ? c->W.p : c->Wf.p);
+    f.Wd = (const double*)c->W.p;
     f.theta = (const double*)c->theta.p;
+    const int NH = c->av.n_hidden;
     RowSet rd{};
     rd.rank = (const uint32_t*)c->det_rank.p;
     rd.coef = (const double*)c->det_coef.p;
@@ -470,24 +479,45 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
         f.tr_idx = (int*)c->ftr_idx.p;
         f.tl_total = (int*)c->ftl_tot.p;
         f.tr_total = (int*)c->ftr_tot.p;
+        f.tl_ci = (int*)c->ftl_ci.p;
+        f.tl_list = (int*)c->ftl_list.p;
+        f.tr_list = (int*)c->ftr_list.p;
+        f.tl_count = (int*)c->ftl_cnt.p;
+        stage_begin(c, NQS_STAGE_TABLES);
         CK(cudaMemsetAsync(c->ftl_end.p, 0xff, (size_t)nbb * nk * 4, c->stream));
         CK(cudaMemsetAsync(c->ftr_idx.p, 0, (size_t)nbb * nk * 4, c->stream));
-        LAUNCH(NQS_STAGE_AMP_DET, fam_launch_sweep<T>(f, nbb, c->stream));
+        LAUNCH(NQS_STAGE_TABLES, fam_launch_sweep<T>(f, nbb, c->stream));
         k_check_psi<<<(unsigned)((nbb + 255) / 256), 256, 0, c->stream>>>((const double*)c->fpm.p, nbb,
                                                                          (DevError*)c->derr.p, s0);
-        LAUNCH(NQS_STAGE_AMP_DET, 1);
-        LAUNCH(NQS_STAGE_AMP_DET, fam_launch_mark<T>(f, rd, nbb, c->stream));
-        if (n_draws > 0) LAUNCH(NQS_STAGE_AMP_DET, fam_launch_mark<T>(f, rs, nbb, c->stream));
-        LAUNCH(NQS_STAGE_AMP_DET, fam_launch_compact<T>(f, nbb, c->stream));
+        LAUNCH(NQS_STAGE_TABLES, 1);
+        LAUNCH(NQS_STAGE_TABLES, fam_launch_mark<T>(f, rd, nbb, c->stream));
+        if (n_draws > 0) LAUNCH(NQS_STAGE_TABLES, fam_launch_mark<T>(f, rs, nbb, c->stream));
+        LAUNCH(NQS_STAGE_TABLES, fam_launch_compact<T>(f, nbb, c->stream));
         // packed table offsets per sample of the batch
         {
-            std::vector<int> tl(nbb), tr(nbb);
+            std::vector<int> tl(nbb), tr(nbb), tn(nbb);
             CK(cudaMemcpyAsync(tl.data(), c->ftl_tot.p, (size_t)nbb * 4, cudaMemcpyDeviceToHost, c->stream));
             CK(cudaMemcpyAsync(tr.data(), c->ftr_tot.p, (size_t)nbb * 4, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaMemcpyAsync(tn.data(), c->ftl_cnt.p, (size_t)nbb * 4, cudaMemcpyDeviceToHost, c->stream));
             CK(cudaStreamSynchronize(c->stream));
-            std::vector<int64_t> tlb(nbb + 1), trb(nbb + 1);
-            tlb[0] = trb[0] = 0;
-            for (int i = 0; i < nbb; ++i) { tlb[i + 1] = tlb[i] + tl[i]; trb[i + 1] = trb[i] + tr[i]; }
+            std::vector<int64_t> tlb(nbb + 1), trb(nbb + 1), lb(nbb + 1), rb(nbb + 1);
+            tlb[0] = trb[0] = lb[0] = rb[0] = 0;
+            for (int i = 0; i < nbb; ++i) {
+                tlb[i + 1] = tlb[i] + tl[i];
+                trb[i + 1] = trb[i] + tr[i];
+                lb[i + 1] = lb[i] + 3 * K + tn[i];
+                rb[i + 1] = rb[i] + 3 * K + tr[i];
+            }
+            CK(cudaMemcpyAsync(c->frbl_base.p, lb.data(), (size_t)(nbb + 1) * 8, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(c->frbr_base.p, rb.data(), (size_t)(nbb + 1) * 8, cudaMemcpyHostToDevice, c->stream));
+            if (NH > 0) {
+                const size_t np = (size_t)((NH + 3) & ~3);
+                TRY(ensure(c, c->frbl, (size_t)lb[nbb] * (np + 4) * sizeof(T)));
+                TRY(ensure(c, c->frbr, (size_t)rb[nbb] * 2 * np * sizeof(T)));
+            }
+            // work: both sweeps (4 + 3t products at step t), every TL entry, every TR row
+            c->fam_matvecs += (int64_t)nbb * 2 * (4 * (int64_t)K + 3 * (int64_t)K * (K - 1) / 2) +
+                              tlb[nbb] + trb[nbb];
             CK(cudaMemcpyAsync(c->ftl_base.p, tlb.data(), (size_t)(nbb + 1) * 8, cudaMemcpyHostToDevice, c->stream));
             CK(cudaMemcpyAsync(c->ftr_base.p, trb.data(), (size_t)(nbb + 1) * 8, cudaMemcpyHostToDevice, c->stream));
             TRY(ensure(c, c->fTL, (size_t)(tlb[nbb] + 1) * D * sizeof(T)));
@@ -500,13 +530,21 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
         f.tr_base = (const int64_t*)c->ftr_base.p;
         f.TL = (T*)c->fTL.p; f.TLe = (int*)c->fTLe.p;
         f.TR = (T*)c->fTR.p; f.TRe = (int*)c->fTRe.p;
-        LAUNCH(NQS_STAGE_AMP_DET, fam_launch_tables<T>(f, nbb, c->stream));
+        f.rbl = (T*)c->frbl.p; f.rbr = (T*)c->frbr.p;
+        f.rbl_base = (const int64_t*)c->frbl_base.p;
+        f.rbr_base = (const int64_t*)c->frbr_base.p;
+        LAUNCH(NQS_STAGE_TABLES, fam_launch_tables<T>(f, nbb, c->stream));
+        stage_end(c, NQS_STAGE_TABLES);
+        stage_begin(c, NQS_STAGE_AMP_DET);
         const int64_t det_rows = c->det_off_h[s1] - c->det_off_h[s0];
         LAUNCH(NQS_STAGE_AMP_DET, fam_launch_rows<T>(f, rd, det_rows / kRows + nbb, (double*)c->part_det.p,
                                                      (int64_t*)c->span_det.p, c->stream));
+        stage_end(c, NQS_STAGE_AMP_DET);
+        stage_begin(c, NQS_STAGE_AMP_DRAW);
         if (n_draws > 0)
-            LAUNCH(NQS_STAGE_AMP_DET, fam_launch_rows<T>(f, rs, (int64_t)nbb * per_draw, (double*)c->part_draw.p,
-                                                         (int64_t*)c->span_draw.p, c->stream));
+            LAUNCH(NQS_STAGE_AMP_DRAW, fam_launch_rows<T>(f, rs, (int64_t)nbb * per_draw, (double*)c->part_draw.p,
+                                                          (int64_t*)c->span_draw.p, c->stream));
+        stage_end(c, NQS_STAGE_AMP_DRAW);
         CK(cudaGetLastError());
     }
     return NQS_OK;
@@ -552,7 +590,9 @@ extern "C" int nqs_destroy(nqs_ctx* c)
                       &c->derr, &c->mixed_ws, &c->span_det, &c->span_draw, &c->Af, &c->ATf,
                       &c->Wf, &c->fG, &c->fGe, &c->fH, &c->fHe, &c->fpm, &c->fpe, &c->ftl_end,
                       &c->ftl_idx, &c->ftr_idx, &c->ftl_tot, &c->ftr_tot, &c->ftl_base,
-                      &c->ftr_base, &c->fTL, &c->fTLe, &c->fTR, &c->fTRe};
+                      &c->ftr_base, &c->fTL, &c->fTLe, &c->fTR, &c->fTRe, &c->ftl_ci,
+                      &c->ftl_list, &c->ftr_list, &c->ftl_cnt, &c->frbl, &c->frbr, &c->frbl_base,
+                      &c->frbr_base};
     for (DevBuf* b : bufs) release(*b);
     for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);
@@ -1071,6 +1111,7 @@ extern "C" int nqs_local_energy(nqs_ctx* c, const uint64_t* samples, const doubl
         out->n_draw_unique = (int64_t)llround(sm[5]);
         out->n_amplitudes = out->n_det + out->n_draw_unique;
         out->span_sites = (int64_t)llround(sm[6]);
+        out->matvecs = shared ? c->fam_matvecs : out->span_sites;
     } else if (he) {
         CK(cudaStreamSynchronize(c->stream));
     }

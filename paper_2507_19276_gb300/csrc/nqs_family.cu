@@ -1,20 +1,27 @@
 // nqs_family.cu -- shared-prefix evaluation of the connected amplitudes of a
-// chain tensor network (Eq. MPS-RNN-1D with v = 0).
+// chain tensor network (Eq. MPS-RNN-1D with v = 0) times the RBM correlator.
 //
 // For a sample n and a connected m that changes the local states of the sorted
-// sites s1 < s2 (< s3 (< s4)), psi(m) = R^T A_{K-1} ... A_0 l with the changed
-// sites' matrices replaced. The product is re-associated so that partial
-// products are shared between the many m of one n:
+// sites s1 < s2 (< s3 (< s4)), psi_TN(m) = r^T A_{K-1} ... A_0 l with the
+// changed sites' matrices replaced. The product is re-associated so that the
+// partial products shared by the many m of one n are formed once:
 //   one-change left families  G_{s,a}(t) = A_t ... A_{s+1} A_s^{a} L_{s-1}, t >= s
 //   one-change right families H_{s,a}(t) = R_{s+1} A_s^{a} A_{s-1} ... A_t,  t <= s
 //   two-change left clusters  TL_{s1a1,s2a2}(t) = A_t ... A_{s2+1} A_{s2}^{a2} G_{s1,a1}(s2-1)
 //   two-change right clusters TR_{sAaA,sBaB} = H_{sB,aB}(sA+1) A_{sA}^{aA}
 // where A_t = A_t^{sigma_t(n)} and A_s^{a} is the a-th local state other than
-// sigma_s(n). Then
-//   2 sites: psi(m) = G_{s1,a1}(s2-1) . H_{s2,a2}(s2)
-//   3 sites: psi(m) = G_{s1,a1}(s2-1) . TR_{s2a2,s3a3}
-//   4 sites: psi(m) = TL_{s1a1,s2a2}(s3-1) . TR_{s3a3,s4a4}
-// Every vector carries a power-of-two exponent; T is the arithmetic type.
+// sigma_s(n) (ascending). Then
+//   2 sites: psi_TN(m) = G_{s1,a1}(s2-1) . H_{s2,a2}(s2)
+//   3 sites: psi_TN(m) = G_{s1,a1}(s2-1) . TR_{s2a2,s3a3}
+//   4 sites: psi_TN(m) = TL_{s1a1,s2a2}(s3-1) . TR_{s3a3,s4a4}
+// The correlator ratio (Eq. RBM) splits the same way: with theta_k(n), the
+// left part's spin-orbital flips dL and the right part's dR,
+//   f(m)/f(n) = prod_k cosh(theta_k + dL_k + dR_k) / cosh(theta_k)
+//             = PL * prod_k (1 + tanh(theta_k + dL_k) sinh(dR_k) + cosh(dR_k) - 1),
+//   PL = prod_k cosh(theta_k + dL_k) / cosh(theta_k),
+// so every left object stores tanh(theta + dL) and PL - 1, every right object
+// sinh(dR) and cosh(dR) - 1. Every vector carries a power-of-two exponent; T
+// is the arithmetic type of the contractions.
 #include "nqs_family.cuh"
 
 namespace nqs {
@@ -26,22 +33,54 @@ __device__ __forceinline__ int sig_of_alt(int a, int own) { return a + (a >= own
 template <typename T>
 __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
 
-// Block-wide: y_i = M x_i for vectors in shared memory; MT[b][a] = M[a][b].
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { typedef float4 type; };
+template <> struct Vec4<double> { typedef double4 type; };
+
+// Block-wide: y_i = M x_i for nv vectors in shared memory; MT[b][a] = M[a][b].
+// Each thread owns two outputs (a, a + D/2) of four vectors.
 template <typename T>
 __device__ void mv_block(const T* __restrict__ MT, int D, const T* X, T* Y, int nv)
 {
-    const int a = threadIdx.x % D, g = threadIdx.x / D, G = blockDim.x / D;
+    if ((D & 3) != 0 || D < 4) {
+        const int a = threadIdx.x % D, g = threadIdx.x / D, G = blockDim.x / D;
+        if (g >= G) return;
+        for (int i = g; i < nv; i += G) {
+            T acc = T(0);
+            for (int b = 0; b < D; ++b) acc = fma(__ldg(MT + (size_t)b * D + a), X[(size_t)i * D + b], acc);
+            Y[(size_t)i * D + a] = acc;
+        }
+        return;
+    }
+    typedef typename Vec4<T>::type V4;
+    const int H = D >> 1;
+    const int a = threadIdx.x % H, g = threadIdx.x / H, G = blockDim.x / H;
     if (g >= G) return;
     for (int i = g * 4; i < nv; i += G * 4) {
         const int n4 = nv - i < 4 ? nv - i : 4;
-        T acc[4] = {T(0), T(0), T(0), T(0)};
-        for (int b = 0; b < D; ++b) {
-            const T m = __ldg(MT + (size_t)b * D + a);
+        T acc0[4] = {T(0), T(0), T(0), T(0)}, acc1[4] = {T(0), T(0), T(0), T(0)};
+        for (int b = 0; b < D; b += 4) {
+            T m0[4], m1[4];
             #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (q < n4) acc[q] = fma(m, X[(size_t)(i + q) * D + b], acc[q]);
+            for (int u = 0; u < 4; ++u) {
+                m0[u] = __ldg(MT + (size_t)(b + u) * D + a);
+                m1[u] = __ldg(MT + (size_t)(b + u) * D + a + H);
+            }
+            #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q < n4) {
+                    const V4 x = *(const V4*)(X + (size_t)(i + q) * D + b);
+                    acc0[q] = fma(m0[0], x.x, acc0[q]); acc1[q] = fma(m1[0], x.x, acc1[q]);
+                    acc0[q] = fma(m0[1], x.y, acc0[q]); acc1[q] = fma(m1[1], x.y, acc1[q]);
+                    acc0[q] = fma(m0[2], x.z, acc0[q]); acc1[q] = fma(m1[2], x.z, acc1[q]);
+                    acc0[q] = fma(m0[3], x.w, acc0[q]); acc1[q] = fma(m1[3], x.w, acc1[q]);
+                }
+            }
         }
-        for (int q = 0; q < n4; ++q) Y[(size_t)(i + q) * D + a] = acc[q];
+        for (int q = 0; q < n4; ++q) {
+            Y[(size_t)(i + q) * D + a] = acc0[q];
+            Y[(size_t)(i + q) * D + a + H] = acc1[q];
+        }
     }
 }
 
@@ -63,6 +102,31 @@ __device__ void renorm_rows(T* Y, int D, int nv, int* ex)
     }
 }
 
+// Cluster keys: TL sorted by (s2, a2, s1, a1), TR by (sA, aA, sB, aB), so that the
+// clusters created with one matrix form contiguous runs.
+__device__ __forceinline__ int tl_key(int K, int s1, int a1, int s2, int a2)
+{
+    return ((s2 * 3 + a2) * K + s1) * 3 + a1;
+}
+
+__device__ __forceinline__ int tr_key(int K, int sA, int aA, int sB, int aB)
+{
+    return ((sA * 3 + aA) * K + sB) * 3 + aB;
+}
+
+// fields of a key: first site, its alternative, second site, its alternative
+__device__ __forceinline__ void key_fields(int K, int key, int& site_hi, int& alt_hi, int& site_lo,
+                                           int& alt_lo)
+{
+    site_hi = key / (9 * K);
+    alt_hi = (key / (3 * K)) % 3;
+    site_lo = (key / 3) % K;
+    alt_lo = key % 3;
+}
+
+// padded correlator-factor row lengths (multiples of 4 elements)
+__device__ __forceinline__ int nh_pad(int NH) { return (NH + 3) & ~3; }
+
 // ---------------------------------------------------------------------------
 // F1: left and right family sweeps, one block per sample. L (or R) stays in
 // shared memory; the families are read back from the tables in batches.
@@ -71,12 +135,12 @@ __device__ void renorm_rows(T* Y, int D, int nv, int* ex)
 template <typename T>
 __global__ void k_fam_sweep(FamArgs<T> f)
 {
-    extern __shared__ unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     T* X = (T*)smraw;                           // [nmax][D]
     T* Y = X + (size_t)f.nmax * f.D;            // [nmax][D]
-    int* eo = (int*)(Y + (size_t)f.nmax * f.D); // [nmax]
+    T* Lv = Y + (size_t)f.nmax * f.D;           // [D]
+    int* eo = (int*)(Lv + f.D);                 // [nmax]
     int* pos = eo + f.nmax;                     // [nmax] table positions
-    T* Lv = (T*)(pos + f.nmax);                 // [D] (aligned: nmax multiple of 4)
     __shared__ int eL;
     const int b = blockIdx.x, K = f.K, D = f.D;
     const int64_t s = f.s0 + b;
@@ -113,15 +177,15 @@ __global__ void k_fam_sweep(FamArgs<T> f)
             if (threadIdx.x == 0) eL = eL_new;
             // (b) existing families: s < t (left) or s > t (right)
             const int nfam = 3 * step;
+            const int tprev = side == 0 ? t - 1 : t + 1;
             for (int c0 = 0; c0 < nfam; c0 += f.nmax) {
                 const int n = nfam - c0 < f.nmax ? nfam - c0 : f.nmax;
                 for (int i = threadIdx.x; i < n; i += blockDim.x) {
                     const int j = (c0 + i) / 3, a = (c0 + i) % 3;
                     const int sf = side == 0 ? j : K - 1 - j;
-                    pos[i] = (a * K + sf) * K;     // + t later
+                    pos[i] = (a * K + sf) * K;
                 }
                 __syncthreads();
-                const int tprev = side == 0 ? t - 1 : t + 1;
                 for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
                     const int i = q / D, c = q - i * D;
                     X[q] = Tb[((size_t)pos[i] + tprev) * D + c];
@@ -177,16 +241,6 @@ __device__ __forceinline__ RowParts row_parts(const HamView& h, const OrbLists& 
     return r;
 }
 
-__device__ __forceinline__ int tl_key(int K, int s1, int a1, int s2, int a2)
-{
-    return ((s2 * K + s1) * 3 + a1) * 3 + a2;
-}
-
-__device__ __forceinline__ int tr_key(int K, int sA, int aA, int sB, int aB)
-{
-    return ((sA * K + sB) * 3 + aA) * 3 + aB;
-}
-
 // F2: mark the clusters the rows need (TL end site, TR use)
 template <typename T>
 __global__ void k_fam_mark(FamArgs<T> f, RowSet rows)
@@ -213,8 +267,30 @@ __global__ void k_fam_mark(FamArgs<T> f, RowSet rows)
     }
 }
 
-// F3: per-sample compaction of the marks: tl_idx[key] = entry offset of
-// (cluster, t = s2) in the packed TL table (or -1), tr_idx[key] = TR row.
+// Block-wide exclusive scan of one int per thread; returns the total.
+__device__ int block_excl_scan(int v, int* ex, int* wt)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) { const int u = __shfl_up_sync(kFull, x, o); if (lane >= o) x += u; }
+    if (lane == 31) wt[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? wt[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) { const int u = __shfl_up_sync(kFull, w, o); if (lane >= o) w += u; }
+        if (lane < nw) wt[lane] = w;
+    }
+    __syncthreads();
+    *ex = x - v + (warp ? wt[warp - 1] : 0);
+    const int tot = wt[nw - 1];
+    __syncthreads();
+    return tot;
+}
+
+// F3: per-sample compaction of the marks, keys in ascending order:
+//   tl_idx[key] = entry offset of (cluster, t = s2) in the packed TL table,
+//   tl_ci[key]  = cluster index (TL list position), tl_list[ci] = key,
+//   tr_idx[key] = TR row index, tr_list[row] = key; -1 where unused.
 template <typename T>
 __global__ void k_fam_compact(FamArgs<T> f)
 {
@@ -223,113 +299,89 @@ __global__ void k_fam_compact(FamArgs<T> f)
     const size_t nk = (size_t)K * K * 9;
     const int* te = f.tl_end + (size_t)b * nk;
     int* tl = f.tl_idx + (size_t)b * nk;
+    int* tci = f.tl_ci + (size_t)b * nk;
     int* tr = f.tr_idx + (size_t)b * nk;
-    int carry_l = 0, carry_r = 0;
+    int* tll = f.tl_list + (size_t)b * nk;
+    int* trl = f.tr_list + (size_t)b * nk;
+    int carry_e = 0, carry_c = 0, carry_r = 0;
     for (size_t k0 = 0; k0 < nk; k0 += blockDim.x) {
         const size_t k = k0 + threadIdx.x;
-        int cl = 0, cr = 0, end = -1, flag = 0, s2 = 0;
+        int ce = 0, cc = 0, cr = 0, end = -1, flag = 0;
         if (k < nk) {
             end = te[k];
             flag = tr[k];
-            s2 = (int)(k / 9) / K;
-            cl = end >= 0 ? end - s2 + 1 : 0;
+            const int s2 = (int)(k / (9 * (size_t)K));
+            ce = end >= 0 ? end - s2 + 1 : 0;
+            cc = end >= 0 ? 1 : 0;
             cr = flag > 0 ? 1 : 0;
         }
-        // two block scans (lengths, flags)
-        int v = cl;
-        for (int o = 1; o < 32; o <<= 1) { int u = __shfl_up_sync(kFull, v, o); if ((threadIdx.x & 31) >= o) v += u; }
-        if ((threadIdx.x & 31) == 31) wt[threadIdx.x >> 5] = v;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            int w = threadIdx.x < (blockDim.x >> 5) ? wt[threadIdx.x] : 0;
-            for (int o = 1; o < 32; o <<= 1) { int u = __shfl_up_sync(kFull, w, o); if (threadIdx.x >= o) w += u; }
-            wt[threadIdx.x] = w;
-        }
-        __syncthreads();
-        const int incl_l = v + ((threadIdx.x >> 5) ? wt[(threadIdx.x >> 5) - 1] : 0);
-        const int tot_l = wt[(blockDim.x >> 5) - 1];
-        __syncthreads();
-        v = cr;
-        for (int o = 1; o < 32; o <<= 1) { int u = __shfl_up_sync(kFull, v, o); if ((threadIdx.x & 31) >= o) v += u; }
-        if ((threadIdx.x & 31) == 31) wt[threadIdx.x >> 5] = v;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            int w = threadIdx.x < (blockDim.x >> 5) ? wt[threadIdx.x] : 0;
-            for (int o = 1; o < 32; o <<= 1) { int u = __shfl_up_sync(kFull, w, o); if (threadIdx.x >= o) w += u; }
-            wt[threadIdx.x] = w;
-        }
-        __syncthreads();
-        const int incl_r = v + ((threadIdx.x >> 5) ? wt[(threadIdx.x >> 5) - 1] : 0);
-        const int tot_r = wt[(blockDim.x >> 5) - 1];
-        __syncthreads();
+        int xe, xc, xr;
+        const int te_tot = block_excl_scan(ce, &xe, wt);
+        const int tc_tot = block_excl_scan(cc, &xc, wt);
+        const int tr_tot = block_excl_scan(cr, &xr, wt);
         if (k < nk) {
-            tl[k] = end >= 0 ? carry_l + incl_l - cl : -1;
-            tr[k] = flag > 0 ? carry_r + incl_r - 1 : -1;
+            tl[k] = end >= 0 ? carry_e + xe : -1;
+            tci[k] = end >= 0 ? carry_c + xc : -1;
+            if (end >= 0) tll[carry_c + xc] = (int)k;
+            tr[k] = flag > 0 ? carry_r + xr : -1;
+            if (flag > 0) trl[carry_r + xr] = (int)k;
         }
-        carry_l += tot_l;
-        carry_r += tot_r;
+        carry_e += te_tot;
+        carry_c += tc_tot;
+        carry_r += tr_tot;
     }
-    if (threadIdx.x == 0) { f.tl_total[b] = carry_l; f.tr_total[b] = carry_r; }
+    if (threadIdx.x == 0) {
+        f.tl_total[b] = carry_e;
+        f.tl_count[b] = carry_c;
+        f.tr_total[b] = carry_r;
+    }
 }
 
-// F4a: TR_{sA aA, sB aB} = H_{sB,aB}(sA+1) A_{sA}^{aA}, one block per sample,
-// sites sA ascending; the needed (sB, aB) of a (sA, aA) are gathered first.
+// F4a: TR_{sA aA, sB aB} = H_{sB,aB}(sA+1) A_{sA}^{aA}; the TR list is in key
+// order, i.e. grouped by (sA, aA): one matrix per run.
 template <typename T>
 __global__ void k_fam_tr(FamArgs<T> f)
 {
-    extern __shared__ unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     T* X = (T*)smraw;
     T* Y = X + (size_t)f.nmax * f.D;
-    int* eo = (int*)(Y + (size_t)f.nmax * f.D);
-    int* ei = eo + f.nmax;
-    int* dst = ei + f.nmax;
-    __shared__ int cnt;
+    int* eo = (int*)(Y + (size_t)(f.nmax + 1) * f.D);
+    int* hp = eo + f.nmax;
     const int b = blockIdx.x, K = f.K, D = f.D;
     const int64_t s = f.s0 + b;
     const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
     const size_t nk = (size_t)K * K * 9;
-    const int* tr = f.tr_idx + (size_t)b * nk;
+    const int* trl = f.tr_list + (size_t)b * nk;
+    const int ntr = f.tr_total[b];
     const T* H = f.H + (size_t)b * 3 * K * K * D;
     const int* He = f.He + (size_t)b * 3 * K * K;
     T* TR = f.TR + (size_t)f.tr_base[b] * D;
     int* TRe = f.TRe + f.tr_base[b];
-    for (int sA = 0; sA < K - 1; ++sA) {
-        const int own = sigma_at(na, nb, sA);
-        for (int aA = 0; aA < 3; ++aA) {
-            // candidates (sB, aB), sB > sA, processed in batches of nmax
-            const int ncand = 3 * (K - 1 - sA);
-            for (int c0 = 0; c0 < ncand; c0 += f.nmax) {
-                if (threadIdx.x == 0) cnt = 0;
-                __syncthreads();
-                for (int c = c0 + threadIdx.x; c < ncand && c < c0 + f.nmax; c += blockDim.x) {
-                    const int sB = sA + 1 + c / 3, aB = c % 3;
-                    const int idx = tr[tr_key(K, sA, aA, sB, aB)];
-                    if (idx >= 0) {
-                        const int slot = atomicAdd(&cnt, 1);
-                        dst[slot] = idx;
-                        ei[slot] = ((aB * K + sB) * K + sA + 1);   // H table position
-                    }
-                }
-                __syncthreads();
-                const int n = cnt;
-                if (n == 0) { __syncthreads(); continue; }
-                for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
-                    const int i = q / D, cc = q - i * D;
-                    X[q] = H[(size_t)ei[i] * D + cc];
-                }
-                __syncthreads();
-                mv_block<T>(f.A + ((size_t)sA * 4 + sig_of_alt(aA, own)) * D * D, D, X, Y, n);
-                __syncthreads();
-                renorm_rows<T>(Y, D, n, eo);
-                __syncthreads();
-                for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
-                    const int i = q / D, cc = q - i * D;
-                    TR[(size_t)dst[i] * D + cc] = Y[q];
-                }
-                for (int i = threadIdx.x; i < n; i += blockDim.x) TRe[dst[i]] = eo[i] + He[ei[i]];
-                __syncthreads();
-            }
+    int i0 = 0;
+    while (i0 < ntr) {
+        const int grp0 = trl[i0] / (3 * K);              // (sA, aA)
+        const int sA = grp0 / 3, aA = grp0 % 3;
+        int n = 1;
+        while (i0 + n < ntr && n < f.nmax && trl[i0 + n] / (3 * K) == grp0) ++n;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int k = trl[i0 + i];
+            const int sB = (k / 3) % K, aB = k % 3;
+            hp[i] = (aB * K + sB) * K + sA + 1;
         }
+        __syncthreads();
+        for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
+            const int i = q / D, c = q - i * D;
+            X[q] = H[(size_t)hp[i] * D + c];
+        }
+        __syncthreads();
+        mv_block<T>(f.A + ((size_t)sA * 4 + sig_of_alt(aA, sigma_at(na, nb, sA))) * D * D, D, X, Y, n);
+        __syncthreads();
+        renorm_rows<T>(Y, D, n, eo);
+        __syncthreads();
+        for (int q = threadIdx.x; q < n * D; q += blockDim.x) TR[(size_t)i0 * D + q] = Y[q];
+        for (int i = threadIdx.x; i < n; i += blockDim.x) TRe[i0 + i] = eo[i] + He[hp[i]];
+        __syncthreads();
+        i0 += n;
     }
 }
 
@@ -338,45 +390,47 @@ __global__ void k_fam_tr(FamArgs<T> f)
 template <typename T>
 __global__ void k_fam_tl(FamArgs<T> f)
 {
-    extern __shared__ unsigned char smraw[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     T* X = (T*)smraw;
     T* Y = X + (size_t)f.nmax * f.D;
-    int* eo = (int*)(Y + (size_t)f.nmax * f.D);
-    int* ei = eo + f.nmax;
-    int* src = ei + f.nmax;
+    int* eo = (int*)(Y + (size_t)(f.nmax + 1) * f.D);
+    int* src = eo + f.nmax;
     int* dst = src + f.nmax;
-    __shared__ int cnt;
+    int* pbuf_src = dst + f.nmax;                 // [nmax + blockDim]
+    int* pbuf_dst = pbuf_src + f.nmax + blockDim.x;
+    __shared__ int wt[32];
     const int b = blockIdx.x, K = f.K, D = f.D;
     const int64_t s = f.s0 + b;
     const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
     const size_t nk = (size_t)K * K * 9;
     const int* tl = f.tl_idx + (size_t)b * nk;
     const int* tl_end = f.tl_end + (size_t)b * nk;
+    const int* tll = f.tl_list + (size_t)b * nk;
+    const int ncl = f.tl_count[b];
     const T* G = f.G + (size_t)b * 3 * K * K * D;
     const int* Ge = f.Ge + (size_t)b * 3 * K * K;
     T* TL = f.TL + (size_t)f.tl_base[b] * D;
     int* TLe = f.TLe + f.tl_base[b];
+    // the list is in key order, i.e. ascending s2: clusters created at t form a run
+    int first = 0;                       // first cluster with s2 >= t
     for (int t = 1; t < K; ++t) {
         const int own = sigma_at(na, nb, t);
-        // (1) creation at s2 = t from G_{s1,a1}(t-1), per alternative a2
-        for (int a2 = 0; a2 < 3; ++a2) {
-            const int ncand = 3 * t;      // (s1 < t, a1)
-            for (int c0 = 0; c0 < ncand; c0 += f.nmax) {
-                if (threadIdx.x == 0) cnt = 0;
-                __syncthreads();
-                for (int c = c0 + threadIdx.x; c < ncand && c < c0 + f.nmax; c += blockDim.x) {
-                    const int s1 = c / 3, a1 = c % 3;
-                    const int key = tl_key(K, s1, a1, t, a2);
-                    const int off = tl[key];
-                    if (off >= 0) {
-                        const int slot = atomicAdd(&cnt, 1);
-                        dst[slot] = off;
-                        src[slot] = (a1 * K + s1) * K + (t - 1);
-                    }
+        while (first < ncl && tll[first] / (9 * K) < t) ++first;
+        // (1) creation: runs of one (s2 = t, a2) share the matrix A_t^{a2}
+        int c0 = first;
+        while (c0 < ncl && tll[c0] / (9 * K) == t) {
+            const int grp = tll[c0] / (3 * K);
+            const int a2 = grp % 3;
+            int n = 1;
+            while (c0 + n < ncl && n < f.nmax && tll[c0 + n] / (3 * K) == grp) ++n;
+            {
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    const int key = tll[c0 + i];
+                    const int s1 = (key / 3) % K, a1 = key % 3;
+                    dst[i] = tl[key];
+                    src[i] = (a1 * K + s1) * K + (t - 1);
                 }
                 __syncthreads();
-                const int n = cnt;
-                if (n == 0) { __syncthreads(); continue; }
                 for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
                     const int i = q / D, cc = q - i * D;
                     X[q] = G[(size_t)src[i] * D + cc];
@@ -393,47 +447,148 @@ __global__ void k_fam_tl(FamArgs<T> f)
                 for (int i = threadIdx.x; i < n; i += blockDim.x) TLe[dst[i]] = eo[i] + Ge[src[i]];
                 __syncthreads();
             }
+            c0 += n;
         }
-        // (2) propagation of clusters with s2 < t <= end
-        const int nkeys_t = t * K * 9;            // keys with s2 < t come first (s2-major)
-        for (int c0 = 0; c0 < nkeys_t; c0 += f.nmax) {
-            if (threadIdx.x == 0) cnt = 0;
-            __syncthreads();
-            for (int c = c0 + threadIdx.x; c < nkeys_t && c < c0 + f.nmax; c += blockDim.x) {
-                const int off = tl[c];
-                if (off < 0) continue;
-                const int s2 = (c / 9) / K;
-                if (t > tl_end[c]) continue;
-                const int slot = atomicAdd(&cnt, 1);
-                src[slot] = off + (t - 1 - s2);
-                dst[slot] = off + (t - s2);
+        // (2) propagation of clusters with s2 < t <= end: the list prefix [0, first)
+        // is compacted window by window into a buffer; full batches are multiplied.
+        int nbuf = 0;
+        for (int w0 = 0; w0 < first || nbuf > 0; w0 += blockDim.x) {
+            if (w0 < first) {
+                const int c = w0 + threadIdx.x;
+                int act = 0, key = 0;
+                if (c < first) {
+                    key = tll[c];
+                    act = t <= tl_end[key] ? 1 : 0;
+                }
+                int pos;
+                const int tot = block_excl_scan(act, &pos, wt);
+                if (act) {
+                    const int s2 = key / (9 * K), off = tl[key];
+                    pbuf_src[nbuf + pos] = off + (t - 1 - s2);
+                    pbuf_dst[nbuf + pos] = off + (t - s2);
+                }
+                nbuf += tot;
+                __syncthreads();
             }
-            __syncthreads();
-            const int n = cnt;
-            if (n == 0) { __syncthreads(); continue; }
-            for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
-                const int i = q / D, cc = q - i * D;
-                X[q] = TL[(size_t)src[i] * D + cc];
+            const bool last_window = w0 + (int)blockDim.x >= first;
+            while (nbuf >= f.nmax || (last_window && nbuf > 0)) {
+                const int n = nbuf < f.nmax ? nbuf : f.nmax;
+                for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
+                    const int i = q / D, cc = q - i * D;
+                    X[q] = TL[(size_t)pbuf_src[i] * D + cc];
+                }
+                __syncthreads();
+                mv_block<T>(f.AT + ((size_t)t * 4 + own) * D * D, D, X, Y, n);
+                __syncthreads();
+                renorm_rows<T>(Y, D, n, eo);
+                __syncthreads();
+                for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
+                    const int i = q / D, cc = q - i * D;
+                    TL[(size_t)pbuf_dst[i] * D + cc] = Y[q];
+                }
+                for (int i = threadIdx.x; i < n; i += blockDim.x) TLe[pbuf_dst[i]] = eo[i] + TLe[pbuf_src[i]];
+                __syncthreads();
+                // shift the rest of the buffer down
+                const int rest = nbuf - n;
+                int sv = 0, dv = 0;
+                const bool mv = (int)threadIdx.x < rest;
+                if (mv) { sv = pbuf_src[n + threadIdx.x]; dv = pbuf_dst[n + threadIdx.x]; }
+                __syncthreads();
+                if (mv) { pbuf_src[threadIdx.x] = sv; pbuf_dst[threadIdx.x] = dv; }
+                nbuf = rest;
+                __syncthreads();
             }
-            __syncthreads();
-            mv_block<T>(f.AT + ((size_t)t * 4 + own) * D * D, D, X, Y, n);
-            __syncthreads();
-            renorm_rows<T>(Y, D, n, eo);
-            __syncthreads();
-            for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
-                const int i = q / D, cc = q - i * D;
-                TL[(size_t)dst[i] * D + cc] = Y[q];
-            }
-            for (int i = threadIdx.x; i < n; i += blockDim.x) TLe[dst[i]] = eo[i] + TLe[src[i]];
-            __syncthreads();
+            if (w0 >= first) break;
         }
     }
 }
 
-// F5: one thread per row: psi(m) as a dot product of a left state and a right
-// covector, the RBM ratio, coefficient x ratio; block partial sums in order.
+// ---------------------------------------------------------------------------
+// F4c: correlator factors of the left and right objects of a sample.
+//   left  objects: G families (s, a) [3K] then TL clusters [tl_count]
+//   right objects: H families (s, a) [3K] then TR rows [tr_total]
+// left:  tanh(theta_k + dL_k) for k < N_h, then PL - 1 at index N_h
+// right: sinh(dR_k), then cosh(dR_k) - 1 at index N_h + k
+// ---------------------------------------------------------------------------
+
+// spin-orbital flips of the change of site s to its a-th alternative state
+__device__ __forceinline__ int site_flips(uint64_t na, uint64_t nb, int s, int a, int* fs, int* sg, int nf)
+{
+    const int own = sigma_at(na, nb, s);
+    const int to = sig_of_alt(a, own);
+    if ((own ^ to) & 1) { fs[nf] = 2 * s; sg[nf] = (to & 1) ? 1 : -1; ++nf; }
+    if ((own ^ to) & 2) { fs[nf] = 2 * s + 1; sg[nf] = (to & 2) ? 1 : -1; ++nf; }
+    return nf;
+}
+
+template <typename T>
+__global__ void k_fam_rbm(FamArgs<T> f)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* th_s = (T*)smraw;               // theta_k(n)
+    T* tt_s = th_s + f.n_hidden;       // tanh theta_k(n)
+    const int b = blockIdx.y, K = f.K, NH = f.n_hidden, NP = nh_pad(NH);
+    const int64_t s = f.s0 + b;
+    const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
+    for (int k = threadIdx.x; k < NH; k += blockDim.x) {
+        th_s[k] = (T)f.theta[s * NH + k];
+        tt_s[k] = (T)tanh(f.theta[s * NH + k]);
+    }
+    __syncthreads();
+    const size_t nk = (size_t)K * K * 9;
+    const int nleft = 3 * K + f.tl_count[b], nright = 3 * K + f.tr_total[b];
+    const int64_t lbase = f.rbl_base[b], rbase = f.rbr_base[b];
+    const int nobj = nleft + nright;
+    const int lane = threadIdx.x & 31;
+    for (int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); o < nobj;
+         o += gridDim.x * (blockDim.x >> 5)) {
+        int fs[4], sg[4], nf = 0;
+        const bool left = o < nleft;
+        const int oi = left ? o : o - nleft;
+        if (oi < 3 * K) {
+            nf = site_flips(na, nb, oi / 3, oi % 3, fs, sg, 0);
+        } else {
+            const int key = left ? f.tl_list[(size_t)b * nk + (oi - 3 * K)]
+                                 : f.tr_list[(size_t)b * nk + (oi - 3 * K)];
+            int s_hi, a_hi, s_lo, a_lo;
+            key_fields(K, key, s_hi, a_hi, s_lo, a_lo);
+            nf = site_flips(na, nb, s_hi, a_hi, fs, sg, 0);
+            nf = site_flips(na, nb, s_lo, a_lo, fs, sg, nf);
+        }
+        if (left) {
+            T* out = f.rbl + (size_t)(lbase + oi) * (NP + 4);
+            T lp = T(0);                        // log PL
+            for (int k = lane; k < NP; k += 32) {
+                if (k >= NH) { out[k] = T(0); continue; }
+                T d = T(0);
+                for (int q = 0; q < nf; ++q) d += sg[q] > 0 ? (T)f.Wd[(size_t)k * 2 * K + fs[q]] : -(T)f.Wd[(size_t)k * 2 * K + fs[q]];
+                out[k] = tanh(th_s[k] + d);
+                // log(cosh(theta + d) / cosh(theta)) = log1p(cosh d - 1 + tanh(theta) sinh d)
+                const T em = expm1(d);
+                const T inv = T(1) / (T(1) + em);
+                lp += log1p(T(0.5) * em * em * inv + tt_s[k] * (T(0.5) * em * (T(1) + inv)));
+            }
+            for (int o2 = 16; o2; o2 >>= 1) lp += __shfl_xor_sync(kFull, lp, o2);
+            if (lane == 0) out[NP] = expm1(lp);
+        } else {
+            T* out = f.rbr + (size_t)(rbase + oi) * (2 * NP);
+            for (int k = lane; k < NP; k += 32) {
+                if (k >= NH) { out[k] = T(0); out[NP + k] = T(0); continue; }
+                T d = T(0);
+                for (int q = 0; q < nf; ++q) d += sg[q] > 0 ? (T)f.Wd[(size_t)k * 2 * K + fs[q]] : -(T)f.Wd[(size_t)k * 2 * K + fs[q]];
+                const T em = expm1(d);
+                const T inv = T(1) / (T(1) + em);
+                out[k] = T(0.5) * em * (T(1) + inv);        // sinh d
+                out[NP + k] = T(0.5) * em * em * inv;       // cosh d - 1
+            }
+        }
+    }
+}
+
+// F5: one thread per row: psi_TN(m) as a dot product of a left state and a
+// right covector, the factorised correlator ratio, coefficient x ratio; block
+// partial sums in a fixed order.
 constexpr int kFamRows = 128;
-constexpr int kFamMaxHidden = 512;
 
 template <typename T>
 __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows, double* partial,
@@ -441,7 +596,7 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
 {
     __shared__ OrbLists lists;
     __shared__ double contrib[kFamRows];
-    __shared__ T tanh_s[kFamMaxHidden];
+    __shared__ int spsum[kFamRows];
     const int64_t* cb = rows.chunk_base;
     const int64_t blk = cb[f.s0] + blockIdx.x;
     if (blk >= cb[f.s1]) return;
@@ -460,7 +615,6 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
     const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
     const int NH = f.n_hidden;
     if (threadIdx.x < 32) build_lists_warp(na, nb, f.h.K, lists, threadIdx.x);
-    for (int k = threadIdx.x; k < NH; k += blockDim.x) tanh_s[k] = (T)tanh(f.theta[s * NH + k]);
     __syncthreads();
     const size_t nk = (size_t)K * K * 9;
     double val = 0.0;
@@ -473,7 +627,7 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
         const int* He = f.He + (size_t)b * 3 * K * K;
         const T* Lv;
         const T* Rv;
-        int eL, eR;
+        int eL, eR, lobj, robj;
         if (p.nsite == 4) {
             const int key = tl_key(K, p.s[0], p.a[0], p.s[1], p.a[1]);
             const int off = f.tl_idx[(size_t)b * nk + key] + (p.s[2] - 1 - p.s[1]);
@@ -482,18 +636,23 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
             eL = f.TLe[f.tl_base[b] + off];
             Rv = f.TR + ((size_t)f.tr_base[b] + ti) * D;
             eR = f.TRe[f.tr_base[b] + ti];
+            lobj = 3 * K + f.tl_ci[(size_t)b * nk + key];
+            robj = 3 * K + ti;
         } else {
             const size_t gi = ((size_t)p.a[0] * K + p.s[0]) * K + p.s[1] - 1;
             Lv = G + gi * D;
             eL = Ge[gi];
+            lobj = 3 * p.s[0] + p.a[0];
             if (p.nsite == 2) {
                 const size_t hi2 = ((size_t)p.a[1] * K + p.s[1]) * K + p.s[1];
                 Rv = H + hi2 * D;
                 eR = He[hi2];
+                robj = 3 * p.s[1] + p.a[1];
             } else {
                 const int ti = f.tr_idx[(size_t)b * nk + tr_key(K, p.s[1], p.a[1], p.s[2], p.a[2])];
                 Rv = f.TR + ((size_t)f.tr_base[b] + ti) * D;
                 eR = f.TRe[f.tr_base[b] + ti];
+                robj = 3 * K + ti;
             }
         }
         nmv = p.s[p.nsite - 1] - p.s[0] + 1;
@@ -510,29 +669,28 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
         }
         const double dot = (double)sum + (double)comp;
         double ratio = ldexp(dot / f.pm[b], eL + eR - f.pe[b]);
-        // RBM: prod_k cosh(theta_k + d_k) / cosh(theta_k) = prod_k (1 + (cosh d_k - 1) + tanh(theta_k) sinh d_k)
         if (NH > 0) {
-            int fs[4], sg[4], nf = 0;
-            uint64_t da = na ^ p.ma, db = nb ^ p.mb;
-            while (da && nf < 4) { const int q = __ffsll((long long)da) - 1; fs[nf] = 2 * q; sg[nf] = ((p.ma >> q) & 1ull) ? 1 : -1; ++nf; da &= da - 1; }
-            while (db && nf < 4) { const int q = __ffsll((long long)db) - 1; fs[nf] = 2 * q + 1; sg[nf] = ((p.mb >> q) & 1ull) ? 1 : -1; ++nf; db &= db - 1; }
-            T lsum = T(0);
-            for (int k = 0; k < NH; ++k) {
-                const T* Wk = f.W + (size_t)k * 2 * K;
-                T d = T(0);
-                for (int q = 0; q < nf; ++q) d += sg[q] > 0 ? Wk[fs[q]] : -Wk[fs[q]];
-                const T em = expm1(d);                       // e^d - 1
-                const T inv = T(1) / (T(1) + em);            // e^-d
-                const T sh = T(0.5) * em * (T(1) + inv);      // sinh d
-                const T c1 = T(0.5) * em * em * inv;          // cosh d - 1
-                lsum += log1p(c1 + tanh_s[k] * sh);
+            typedef typename Vec4<T>::type V4;
+            const int NP = nh_pad(NH);
+            const V4* lt = (const V4*)(f.rbl + (size_t)(f.rbl_base[b] + lobj) * (NP + 4));
+            const V4* rs = (const V4*)(f.rbr + (size_t)(f.rbr_base[b] + robj) * (2 * NP));
+            const V4* rc = rs + NP / 4;
+            // product of (1 + x_k) kept as X = product - 1
+            T X = T(0);
+            for (int k4 = 0; k4 < NP / 4; ++k4) {
+                const V4 t = lt[k4], sh = rs[k4], c1 = rc[k4];
+                T x;
+                x = fma(t.x, sh.x, c1.x); X = fma(X, x, X + x);
+                x = fma(t.y, sh.y, c1.y); X = fma(X, x, X + x);
+                x = fma(t.z, sh.z, c1.z); X = fma(X, x, X + x);
+                x = fma(t.w, sh.w, c1.w); X = fma(X, x, X + x);
             }
-            ratio *= exp((double)lsum);
+            const T XL = ((const T*)lt)[NP];
+            ratio *= (1.0 + (double)XL) * (1.0 + (double)X);
         }
         val = rows.coef[r0 + threadIdx.x] * ratio;
     }
     contrib[threadIdx.x] = val;
-    __shared__ int spsum[kFamRows];
     spsum[threadIdx.x] = nmv;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -549,9 +707,15 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
 // ---------------------------------------------------------------------------
 
 template <typename T>
+static size_t stage_smem(const FamArgs<T>& f, int nints)
+{
+    return (size_t)(2 * f.nmax + 1) * f.D * sizeof(T) + (size_t)nints * f.nmax * sizeof(int);
+}
+
+template <typename T>
 int fam_launch_sweep(const FamArgs<T>& f, int nb, cudaStream_t st)
 {
-    const size_t smem = (size_t)(2 * f.nmax + 1) * f.D * sizeof(T) + 2 * f.nmax * sizeof(int);
+    const size_t smem = stage_smem(f, 2);
     cudaFuncSetAttribute(k_fam_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_fam_sweep<T><<<nb, f.threads, smem, st>>>(f);
     return 1;
@@ -575,12 +739,19 @@ int fam_launch_compact(const FamArgs<T>& f, int nb, cudaStream_t st)
 template <typename T>
 int fam_launch_tables(const FamArgs<T>& f, int nb, cudaStream_t st)
 {
-    const size_t smem = (size_t)2 * f.nmax * f.D * sizeof(T) + 4 * f.nmax * sizeof(int);
+    const size_t smem = stage_smem(f, 3);
+    const size_t smem_tl = smem + (size_t)2 * (f.nmax + f.threads) * sizeof(int);
     cudaFuncSetAttribute(k_fam_tr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_fam_tl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_fam_tl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tl);
     k_fam_tr<T><<<nb, f.threads, smem, st>>>(f);
-    k_fam_tl<T><<<nb, f.threads, smem, st>>>(f);
-    return 2;
+    k_fam_tl<T><<<nb, f.threads, smem_tl, st>>>(f);
+    int n = 2;
+    if (f.n_hidden > 0) {
+        dim3 grid(8, nb);
+        k_fam_rbm<T><<<grid, 256, 2 * f.n_hidden * sizeof(T), st>>>(f);
+        ++n;
+    }
+    return n;
 }
 
 template <typename T>

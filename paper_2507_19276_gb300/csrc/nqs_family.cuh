@@ -22,15 +22,20 @@ struct FamArgs {
     double* pm; int* pe;      // psi_TN(n) = pm 2^pe
     int* tl_end;              // [b][K*K*9] last site a TL cluster is needed at (-1: unused)
     int* tl_idx;              // [b][K*K*9] entry offset of the cluster in the packed TL table
+    int* tl_ci;               // [b][K*K*9] cluster index of a TL key
+    int* tl_list;             // [b][K*K*9] TL keys in ascending order
     int* tr_idx;              // [b][K*K*9] marks, then row index in the packed TR table
-    int* tl_total; int* tr_total;      // [b]
+    int* tr_list;             // [b][K*K*9] TR keys in ascending order
+    int* tl_total; int* tl_count; int* tr_total;      // [b] TL entries, TL clusters, TR rows
     const int64_t* tl_base; const int64_t* tr_base;   // [b] batch offsets (entries)
     T* TL; int* TLe;          // packed TL entries
     T* TR; int* TRe;          // packed TR rows
     // correlator
     int n_hidden;
-    const T* W;               // [n_hidden][2K]
+    const double* Wd;         // [n_hidden][2K]
     const double* theta;      // [Ns][n_hidden] (all samples)
+    T* rbl; T* rbr;           // per-object correlator factors (see nqs_family.cu)
+    const int64_t* rbl_base; const int64_t* rbr_base;   // [b] object offsets
 };
 
 template <typename T> int fam_launch_sweep(const FamArgs<T>& f, int nb, cudaStream_t st);
@@ -46,7 +51,7 @@ template <typename T> int fam_launch_rows(const FamArgs<T>& f, const RowSet& row
 inline size_t fam_bytes_per_sample(int K, int D, size_t elem)
 {
     const size_t KK = (size_t)K * K;
-    return 2 * (3 * KK * D * elem + 3 * KK * 4) + 3 * KK * 9 * 4 + 64;
+    return 2 * (3 * KK * D * elem + 3 * KK * 4) + 6 * KK * 9 * 4 + 64;
 }
 
 }  // namespace nqs

@@ -36,15 +36,15 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("timing", C.c_int), ("reserved", C.c_int * 14)]
 
 
-N_STAGES = 8
-STAGES = ["env", "count", "write", "draw", "amp_det", "amp_draw", "final", "other"]
+N_STAGES = 9
+STAGES = ["env", "count", "write", "draw", "amp_det", "amp_draw", "final", "other", "tables"]
 
 
 class EnergySummary(C.Structure):
     _fields_ = [("e_mean", C.c_double), ("sum_counts", C.c_double), ("log_B", C.c_double),
                 ("e_tilde_mean", C.c_double), ("n_conn", C.c_int64), ("n_det", C.c_int64),
                 ("n_draw_unique", C.c_int64), ("n_amplitudes", C.c_int64),
-                ("span_sites", C.c_int64)]
+                ("span_sites", C.c_int64), ("matvecs", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
