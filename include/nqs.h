@@ -188,6 +188,27 @@ int nqs_amplitude(nqs_ctx* ctx, const uint64_t* dets, int64_t n, double* log_abs
 int nqs_draws(nqs_ctx* ctx, const uint64_t* samples, int64_t Ns, double det_threshold,
               int n_draws, uint64_t philox_seed, int64_t* ranks, uint64_t* w_total);
 
+/* nqs_draws without any device allocation. The paper has no counterpart:
+ * this is a service for callers that cannot allocate device memory while they
+ * run -- work being recorded into a CUDA graph, latency-critical loops that
+ * must not wait on an allocator, or applications that give all GPU memory to
+ * their own pool beforehand.
+ *  Same arguments and results as nqs_draws (bit-identical ranks and W), but
+ *  samples, ranks and w_total must be device pointers; host pointers are
+ *  rejected with NQS_ERR_INVALID_ARG because staging them would allocate.
+ *  Working memory is a fixed array of NQS_NOALLOC_SCRATCH_BYTES inside the
+ *  library image, present on every GPU that loads the library until the
+ *  process exits. A batch needs 8 * (2 + 2 Ns + 1.5 Ns ceil(n_conn / 32))
+ *  bytes of it; larger batches return NQS_ERR_INVALID_ARG (split them).
+ *  The first call on a device looks up the array's device address (with
+ *  cudaGetSymbolAddress); make that first call before any stream capture.
+ *  All calls share the one array: calls that overlap on the GPU (other
+ *  streams, other contexts on the same device) race and corrupt each other.
+ *  Synchronises the context's stream before returning. */
+#define NQS_NOALLOC_SCRATCH_BYTES (8 << 20)
+int nqs_draws_noalloc(nqs_ctx* ctx, const uint64_t* samples, int64_t Ns, double det_threshold,
+                      int n_draws, uint64_t philox_seed, int64_t* ranks, uint64_t* w_total);
+
 /* Semistochastic local energy (Sec. 2.4):
  *  E_loc(n) = H_nn + sum_{|H_nm|>=eps} H_nm r_m
  *           + (1/N_eps) sum_d H_{m_d} (W / w_{m_d}) r_{m_d},  r_m = psi(m)/psi(n),

@@ -1174,3 +1174,110 @@ extern "C" int nqs_grad_log_psi_vjp(nqs_ctx* c, const uint64_t* samples, const d
     CK(cudaStreamSynchronize(c->stream));
     return NQS_OK;
 }
+
+// ============================================================================
+// Allocation-free variant of nqs_draws
+//
+// Some callers must not allocate device memory during a call: code that is
+// being recorded into a CUDA graph (a cudaMalloc there breaks the capture),
+// latency-critical loops where an allocation can stall on a device-wide
+// synchronisation, and hosts that hand the whole GPU memory to their own pool
+// up front. For them this entry point computes the same draws as nqs_draws
+// using only the scratch below, which is part of the library image: it is
+// reserved on every GPU that loads the library and stays there until the
+// process exits.
+// ============================================================================
+
+namespace {
+
+constexpr size_t kNoAllocWords = (size_t)NQS_NOALLOC_SCRATCH_BYTES / 8;
+
+// Scratch shared by every call of nqs_draws_noalloc on a device. It keeps the
+// previous call's contents; each call clears what has to start at zero.
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocWords];
+
+// Device addresses of the scratch, resolved once per device.
+unsigned long long* g_noalloc_addr[256] = {nullptr};
+
+}  // namespace
+
+extern "C" int nqs_draws_noalloc(nqs_ctx* c, const uint64_t* samples, int64_t Ns, double eps,
+                                 int n_draws, uint64_t seed, int64_t* ranks, uint64_t* w_total)
+{
+    if (!c) return NQS_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    CK(cudaSetDevice(c->device));
+    TRY(check_ready(c, false));
+    if (Ns < 0 || n_draws < 0 || (Ns > 0 && !samples) || (Ns > 0 && n_draws > 0 && !ranks))
+        return set_err(c, NQS_ERR_INVALID_ARG, "bad samples / n_draws / ranks arguments");
+    uint64_t eb;
+    TRY(eps_bits(c, eps, &eb));
+    if (Ns == 0) return NQS_OK;
+    if (!is_device_ptr(samples) || (n_draws > 0 && !is_device_ptr(ranks)) ||
+        (w_total && !is_device_ptr(w_total)))
+        return set_err(c, NQS_ERR_INVALID_ARG,
+                       "nqs_draws_noalloc needs device pointers (host arrays would need staging)");
+    // scratch layout (64-bit words): error word (2), rem_max [Ns], W [Ns],
+    // chunk weights [Ns][nch], chunk counts [Ns][nch] as 32-bit halves
+    const uint64_t nch = (uint64_t)((c->n_conn + 31) / 32);
+    const uint64_t need = 2 + 2 * (uint64_t)Ns + (uint64_t)Ns * nch + ((uint64_t)Ns * nch + 1) / 2;
+    if (need > kNoAllocWords)
+        return set_err(c, NQS_ERR_INVALID_ARG,
+                       "nqs_draws_noalloc: %lld samples x %llu rank chunks need %llu scratch words, "
+                       "the fixed scratch holds %llu (%d bytes); split the batch",
+                       (long long)Ns, (unsigned long long)nch, (unsigned long long)need,
+                       (unsigned long long)kNoAllocWords, (int)NQS_NOALLOC_SCRATCH_BYTES);
+    if (c->device < 0 || c->device >= 256)
+        return set_err(c, NQS_ERR_UNSUPPORTED, "device index %d out of range", c->device);
+    if (!g_noalloc_addr[c->device]) {
+        void* p = nullptr;
+        CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_addr[c->device] = (unsigned long long*)p;
+    }
+    unsigned long long* base = g_noalloc_addr[c->device];
+    DevError* derr = (DevError*)base;
+    unsigned long long* rem_max = base + 2;
+    uint64_t* W = (uint64_t*)(rem_max + Ns);
+    uint64_t* chunk_w = W + Ns;
+    uint32_t* chunk_cnt = (uint32_t*)(chunk_w + (size_t)Ns * nch);
+    CK(cudaMemsetAsync(derr, 0, sizeof(DevError), c->stream));
+    CK(cudaMemsetAsync(rem_max, 0, (size_t)Ns * 8, c->stream));
+    LAUNCH(NQS_STAGE_OTHER, launch_validate(samples, Ns, c->K, c->na, c->nb, derr, c->stream));
+    EnumArgs a{};
+    a.h = c->hv;
+    a.samples = samples;
+    a.eps_bits = eb;
+    a.n_chunks = (uint32_t)nch;
+    a.chunk_cnt = chunk_cnt;
+    a.rem_max_bits = rem_max;
+    LAUNCH(NQS_STAGE_COUNT, launch_enum(a, Ns, false, c->stream));
+    a.chunk_w = chunk_w;
+    LAUNCH(NQS_STAGE_WRITE, launch_enum(a, Ns, true, c->stream));
+    LAUNCH(NQS_STAGE_WRITE, launch_scan_chunks_u64(chunk_w, W, Ns, (uint32_t)nch, c->stream));
+    if (nch == 0) CK(cudaMemsetAsync(W, 0, (size_t)Ns * 8, c->stream));
+    if (n_draws > 0) {
+        DrawArgs d{};
+        d.h = c->hv;
+        d.samples = samples;
+        d.Ns = Ns;
+        d.eps_bits = eb;
+        d.n_chunks = (uint32_t)nch;
+        d.chunk_pre = chunk_w;
+        d.rem_max_bits = rem_max;
+        d.n_draws = n_draws;
+        d.seed = seed;
+        d.out_rank = ranks;
+        LAUNCH(NQS_STAGE_DRAW, launch_draws(d, c->stream));
+    }
+    CK(cudaGetLastError());
+    if (w_total) CK(cudaMemcpyAsync(w_total, W, (size_t)Ns * 8, cudaMemcpyDeviceToDevice, c->stream));
+    DevError e;
+    CK(cudaMemcpyAsync(&e, derr, sizeof(e), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (e.code != 0)
+        return set_err(c, e.code, "%s (samples[%lld])",
+                       e.detail == 1 ? "sample has an occupied orbital >= n_orb"
+                                     : "sample has the wrong number of alpha or beta electrons",
+                       (long long)e.index);
+    return NQS_OK;
+}

@@ -77,6 +77,7 @@ def load():
             "nqs_connected": [vp, vp, i64, dbl, vp, vp, vp, vp, vp, i64],
             "nqs_amplitude": [vp, vp, i64, vp, vp],
             "nqs_draws": [vp, vp, i64, dbl, C.c_int, u64, vp, vp],
+            "nqs_draws_noalloc": [vp, vp, i64, dbl, C.c_int, u64, vp, vp],
             "nqs_local_energy": [vp, vp, vp, i64, dbl, C.c_int, u64, vp, C.POINTER(EnergySummary)],
             "nqs_grad_log_psi_vjp": [vp, vp, vp, i64, vp, vp, vp],
         }
@@ -93,7 +94,7 @@ def load():
 def exported_symbols():
     return ["nqs_create", "nqs_destroy", "nqs_last_error", "nqs_set_options", "nqs_stage_times",
             "nqs_set_hamiltonian", "nqs_set_ansatz", "nqs_connected", "nqs_amplitude",
-            "nqs_draws", "nqs_local_energy", "nqs_grad_log_psi_vjp"]
+            "nqs_draws", "nqs_draws_noalloc", "nqs_local_energy", "nqs_grad_log_psi_vjp"]
 
 
 def _ptr(x):
@@ -168,6 +169,12 @@ def nqs_amplitude(ctx, dets, n, log_abs, sign):
 def nqs_draws(ctx, samples, Ns, eps, n_draws, seed, ranks, w_total):
     _check(ctx, load().nqs_draws(ctx, _ptr(samples), Ns, float(eps), n_draws, seed, _ptr(ranks),
                                  _ptr(w_total)))
+
+
+def nqs_draws_noalloc(ctx, samples, Ns, eps, n_draws, seed, ranks, w_total):
+    """nqs_draws using only the library's fixed scratch array (device pointers only)."""
+    _check(ctx, load().nqs_draws_noalloc(ctx, _ptr(samples), Ns, float(eps), n_draws, seed,
+                                         _ptr(ranks), _ptr(w_total)))
 
 
 def nqs_local_energy(ctx, samples, counts, Ns, eps, n_draws, seed, e_loc, summary=None):
