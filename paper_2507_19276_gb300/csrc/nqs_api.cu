@@ -12,7 +12,6 @@
 #include "../../include/nqs.h"
 #include "nqs_kernels.cuh"
 #include "nqs_family.cuh"
-#include "nqs_mixed.cuh"
 
 using namespace nqs;
 
@@ -42,8 +41,8 @@ struct nqs_ctx {
     AnsatzView av{};
     DevBuf A, AT, W, b, pred_ptr, pred_idx;
     DevBuf Af, ATf, Wf;       // FP32 copies for the shared-prefix FP32 path
-    MixedAnsatz mixed{};
-    DevBuf mixed_buf;
+    DevBuf tc_img, tc_exps;   // split-FP16 operand images for the tensor-core batches
+    bool has_tc = false;
 
     // staging and workspace
     DevBuf st_samples, st_counts, st_u, st_out0, st_out1, st_out2, st_out3, st_out4;
@@ -58,7 +57,6 @@ struct nqs_ctx {
         frbr_base;
     std::vector<int64_t> det_off_h;
     int64_t fam_matvecs = 0;   // work of the last shared-prefix pass
-    DevBuf mixed_ws;
 
     // stage accounting (nqs_stage_times)
     int timing = 0;
@@ -341,8 +339,7 @@ int amp_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, RowSet rows, int64
              int64_t max_rows_per_sample, int stage)
 {
     StageScope sc(c, stage);
-    const bool mixed = c->precision == NQS_PREC_MIXED && c->av.chain;
-    const int R = mixed ? mixed_rows_per_block(c->mixed) : amp_fp64_rows_per_block(c->av);
+    const int R = amp_fp64_rows_per_block(c->av);
     int64_t max_chunks = total_rows / R + Ns;
     if (max_rows_per_sample >= 0) max_chunks = Ns * ((max_rows_per_sample + R - 1) / R);
     TRY(ensure(c, base, (size_t)(Ns + 1) * 8));
@@ -368,16 +365,7 @@ int amp_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, RowSet rows, int64
     a.psi_exp = (const int*)c->pexp.p;
     a.partial = (double*)part.p;
     a.span = (int64_t*)span.p;
-    if (mixed) {
-        const size_t need = mixed_workspace_bytes(c->mixed, a);
-        TRY(ensure(c, c->mixed_ws, need));
-        int launches = 0;
-        const int st = mixed_amp(c->mixed, a, c->mixed_ws.p, c->stream, &launches);
-        LAUNCH(stage, launches);
-        if (st != NQS_OK) return set_err(c, st, "mixed-precision amplitudes failed");
-    } else {
-        LAUNCH(stage, launch_amp_fp64(a, c->stream));
-    }
+    LAUNCH(stage, launch_amp_fp64(a, c->stream));
     CK(cudaGetLastError());
     return NQS_OK;
 }
@@ -438,12 +426,22 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
     f.K = K;
     f.D = D;
     f.threads = D > 256 ? D : 256;
-    {
+    f.tc = (sizeof(T) == 4 && c->has_tc) ? 1 : 0;
+    if (f.tc) {
+        f.nmax = 128;                                  // one M = 128 tensor-core tile
+        int cols = 32;
+        while (cols < D) cols <<= 1;
+        f.tc_cols = cols;
+        f.tc_mats = (const uint4*)c->tc_img.p;
+        f.tc_exp = (const int*)c->tc_exps.p;
+    } else {
         // vectors staged per block-wide batch: two [nmax][D] buffers within ~180 KB
         int nm = (int)((180 * 1024) / (2 * (size_t)D * sizeof(T)));
         nm = nm / 4 * 4;
         f.nmax = nm < 4 ? 4 : (nm > 64 ? 64 : nm);
     }
+    f.batch_bytes = fam_batch_bytes(D, f.nmax, sizeof(T), f.tc != 0);
+    f.err = (DevError*)c->derr.p;
     f.A = (const T*)(dbl ? c->A.p : c->Af.p);
     f.AT = (const T*)(dbl ? c->AT.p : c->ATf.p);
     f.samples = ds;
@@ -579,7 +577,7 @@ extern "C" int nqs_destroy(nqs_ctx* c)
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     DevBuf* bufs[] = {&c->h1e, &c->eri, &c->pairs, &c->chol, &c->A, &c->AT, &c->W, &c->b,
-                      &c->pred_ptr, &c->pred_idx, &c->mixed_buf, &c->st_samples, &c->st_counts,
+                      &c->pred_ptr, &c->pred_idx, &c->st_samples, &c->st_counts,
                       &c->st_u, &c->st_out0, &c->st_out1, &c->st_out2, &c->st_out3, &c->st_out4,
                       &c->chunk_cnt, &c->chunk_off, &c->chunk_w, &c->rem_max, &c->det_tot,
                       &c->det_off, &c->det_rank, &c->det_coef, &c->Lenv, &c->Lexp, &c->Renv,
@@ -587,12 +585,12 @@ extern "C" int nqs_destroy(nqs_ctx* c)
                       &c->logf, &c->pmant, &c->pexp, &c->hdiag, &c->Wtot, &c->draw_rank64,
                       &c->draw_rank, &c->draw_coef, &c->n_unique, &c->base_det, &c->base_draw,
                       &c->part_det, &c->part_draw, &c->eloc, &c->edet, &c->estoch, &c->summary,
-                      &c->derr, &c->mixed_ws, &c->span_det, &c->span_draw, &c->Af, &c->ATf,
+                      &c->derr, &c->span_det, &c->span_draw, &c->Af, &c->ATf,
                       &c->Wf, &c->fG, &c->fGe, &c->fH, &c->fHe, &c->fpm, &c->fpe, &c->ftl_end,
                       &c->ftl_idx, &c->ftr_idx, &c->ftl_tot, &c->ftr_tot, &c->ftl_base,
                       &c->ftr_base, &c->fTL, &c->fTLe, &c->fTR, &c->fTRe, &c->ftl_ci,
                       &c->ftl_list, &c->ftr_list, &c->ftl_cnt, &c->frbl, &c->frbr, &c->frbl_base,
-                      &c->frbr_base};
+                      &c->frbr_base, &c->tc_img, &c->tc_exps};
     for (DevBuf* b : bufs) release(*b);
     for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);
@@ -797,11 +795,16 @@ extern "C" int nqs_set_ansatz(nqs_ctx* c, const double* site_tensors, int n_edge
     a.W = n_hidden ? (const double*)c->W.p : nullptr;
     a.b = n_hidden ? (const double*)c->b.p : nullptr;
     c->av = a;
-    if (chain) {
-        // tensor-core copies of the site tensors
-        TRY(ensure(c, c->mixed_buf, mixed_param_bytes(K, D)));
-        const int st = mixed_upload(c->mixed, hA.data(), K, D, c->mixed_buf.p, c->stream);
-        if (st != NQS_OK) return set_err(c, st, "uploading the tensor-core site tensors failed");
+    c->has_tc = false;
+    if (chain && D % 16 == 0 && D <= 128) {
+        std::vector<unsigned char> img;
+        std::vector<int> ex;
+        fam_tc_images(hA.data(), K, D, img, ex);
+        TRY(ensure(c, c->tc_img, img.size()));
+        TRY(ensure(c, c->tc_exps, ex.size() * 4));
+        CK(cudaMemcpy(c->tc_img.p, img.data(), img.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->tc_exps.p, ex.data(), ex.size() * 4, cudaMemcpyHostToDevice));
+        c->has_tc = true;
     }
     CK(cudaStreamSynchronize(c->stream));
     c->has_ans = true;

@@ -23,6 +23,12 @@
 // sinh(dR) and cosh(dR) - 1. Every vector carries a power-of-two exponent; T
 // is the arithmetic type of the contractions.
 #include "nqs_family.cuh"
+#include "nqs_tc.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <type_traits>
 
 namespace nqs {
 
@@ -114,6 +120,171 @@ __device__ __forceinline__ int tr_key(int K, int sA, int aA, int sB, int aB)
     return ((sA * 3 + aA) * K + sB) * 3 + aB;
 }
 
+// ---------------------------------------------------------------------------
+// One batch of block-wide matrix-vector products y_i = M x_i (i < n):
+// x_i gathered from global memory, y_i rescaled by a power of two and
+// scattered back, eo[i] = the exponent added to y_i. M is A_t^{sg} (side 0,
+// column convention) or its transpose (side 1, row vectors).
+//  - FP32 with D a multiple of 16 up to 128: tcgen05 MMAs, M = 128 rows,
+//    N = K = D, operands split into FP16 hi + lo (x_hi M_hi + x_lo M_hi +
+//    x_hi M_lo), FP32 accumulation in tensor memory;
+//  - otherwise: shared-memory CUDA-core products (mv_block).
+// ---------------------------------------------------------------------------
+
+template <typename T>
+struct BatchSmem {
+    T* X; T* Y;                        // CUDA-core path: [nmax][D] each
+    unsigned char* Ah; unsigned char* Al; unsigned char* Bh;   // tensor path operands
+    float* rmax;                       // [2][128]
+    uint64_t* mbar;
+    uint32_t tmem;
+    uint32_t phase;
+    int cur_mat;
+};
+
+template <typename T>
+__device__ __forceinline__ bool use_tc(const FamArgs<T>& f)
+{
+    return std::is_same<T, float>::value && f.tc;
+}
+
+template <typename T>
+__device__ void batch_apply(const FamArgs<T>& f, BatchSmem<T>& sm, const T* src, const int* soff,
+                            T* dst, const int* doff, int* eo, int n, int side, int t, int sg)
+{
+    const int D = f.D;
+    if (!use_tc(f)) {
+        for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
+            const int i = q / D, c = q - i * D;
+            sm.X[q] = src[(size_t)soff[i] * D + c];
+        }
+        __syncthreads();
+        const T* M = (side == 0 ? f.AT : f.A) + ((size_t)t * 4 + sg) * D * D;
+        mv_block<T>(M, D, sm.X, sm.Y, n);
+        __syncthreads();
+        renorm_rows<T>(sm.Y, D, n, eo);
+        __syncthreads();
+        for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
+            const int i = q / D, c = q - i * D;
+            dst[(size_t)doff[i] * D + c] = sm.Y[q];
+        }
+        __syncthreads();
+        return;
+    }
+    // ---- tensor-core path (T = float) ----
+    const int cpr = D >> 3;                       // 8-element units per row
+    for (int u = threadIdx.x; u < n * cpr; u += blockDim.x) {
+        const int r = u / cpr, c = u - r * cpr;
+        const float4* p = (const float4*)((const float*)src + (size_t)soff[r] * D + 8 * c);
+        const float4 v0 = p[0], v1 = p[1];
+        const float xs[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+        __align__(16) __half hi[8], lo[8];
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) tc::split_half(xs[j], hi[j], lo[j]);
+        const uint32_t off = tc::op_offset(r, 8 * c, D);
+        *(uint4*)(sm.Ah + off) = *(const uint4*)hi;
+        *(uint4*)(sm.Al + off) = *(const uint4*)lo;
+    }
+    const int mat = (side * f.K + t) * 4 + sg;
+    if (mat != sm.cur_mat) {
+        const uint4* g = f.tc_mats + (size_t)mat * (4 * D * D / 16);
+        uint4* d = (uint4*)sm.Bh;
+        for (int i = threadIdx.x; i < 4 * D * D / 16; i += blockDim.x) d[i] = g[i];
+        sm.cur_mat = mat;
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc::fence_after_sync();
+        const uint32_t idesc = tc::idesc_f16(128, D);
+        const uint32_t lbo = 128, sbo = 16 * D;
+        const unsigned char* Bl = sm.Bh + 2 * D * D;
+        const unsigned char* As[3] = {sm.Ah, sm.Al, sm.Ah};
+        const unsigned char* Bs[3] = {sm.Bh, sm.Bh, Bl};
+        uint32_t acc = 0;
+        for (int term = 0; term < 3; ++term)
+            for (int ks = 0; ks < D / 16; ++ks) {
+                tc::mma_f16(sm.tmem, tc::desc(tc::smem_addr(As[term]) + ks * 256, lbo, sbo),
+                            tc::desc(tc::smem_addr(Bs[term]) + ks * 256, lbo, sbo), idesc, acc);
+                acc = 1;
+            }
+        tc::mma_commit(sm.mbar);
+    }
+    const bool ok = tc::mbar_wait(sm.mbar, sm.phase, 1u << 24);
+    sm.phase ^= 1u;
+    tc::fence_after_sync();
+    if (!ok && threadIdx.x == 0) report(f.err, 5, 4, (long long)f.s0);
+    // tensor memory -> registers: warp w reads lanes 32 (w % 4) .. +31 and half (w / 4) of the columns
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = warp & 3, h = warp >> 2, half = D >> 1;
+    const int r = 32 * q + lane;
+    float v[64];
+    float m = 0.f;
+    if (warp < 8) {
+        for (int c0 = 0; c0 < half; c0 += 8) {
+            tc::tmem_ld8(sm.tmem + ((uint32_t)(32 * q) << 16) + h * half + c0, v + c0);
+        }
+        tc::tmem_wait_ld();
+        for (int j = 0; j < half; ++j) m = fmaxf(m, fabsf(v[j]));
+        sm.rmax[h * 128 + r] = m;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp < 8 && r < n) {
+        const float mm = fmaxf(sm.rmax[r], sm.rmax[128 + r]);
+        int e = 0;
+        if (mm > 0.f) frexpf(mm, &e);
+        float* o = (float*)dst + (size_t)doff[r] * D + h * half;
+        for (int j = 0; j < half; j += 4) {
+            float4 w;
+            w.x = ldexpf(v[j], -e); w.y = ldexpf(v[j + 1], -e);
+            w.z = ldexpf(v[j + 2], -e); w.w = ldexpf(v[j + 3], -e);
+            *(float4*)(o + j) = w;
+        }
+        if (h == 0) eo[r] = e + f.tc_exp[mat];
+    }
+    __syncthreads();
+}
+
+// per-kernel setup / teardown of the tensor-core state
+template <typename T>
+__device__ void batch_init(const FamArgs<T>& f, BatchSmem<T>& sm, unsigned char* base, uint32_t* tmem_slot,
+                           uint64_t* mbar)
+{
+    const int D = f.D;
+    if (!use_tc(f)) {
+        sm.X = (T*)base;
+        sm.Y = sm.X + (size_t)f.nmax * D;
+        return;
+    }
+    sm.X = (T*)base;                              // small scratch for the sweep's boundary vectors
+    sm.Y = sm.X + (size_t)4 * D;
+    unsigned char* p = base + (((size_t)8 * D * sizeof(T) + 1023) & ~(size_t)1023);
+    sm.Ah = p; p += (size_t)128 * D * 2;
+    sm.Al = p; p += (size_t)128 * D * 2;
+    sm.Bh = p; p += (size_t)4 * D * D;
+    sm.rmax = (float*)p;
+    sm.mbar = mbar;
+    sm.cur_mat = -1;
+    sm.phase = 0;
+    if ((threadIdx.x >> 5) == 0) { tc::tmem_alloc(tmem_slot, f.tc_cols); tc::tmem_relinquish(); }
+    if (threadIdx.x == 0) tc::mbar_init(mbar, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    sm.tmem = *tmem_slot;
+}
+
+template <typename T>
+__device__ void batch_fini(const FamArgs<T>& f, BatchSmem<T>& sm)
+{
+    if (!use_tc(f)) return;
+    tc::fence_before_sync();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(sm.tmem, f.tc_cols);
+}
+
 // fields of a key: first site, its alternative, second site, its alternative
 __device__ __forceinline__ void key_fields(int K, int key, int& site_hi, int& alt_hi, int& site_lo,
                                            int& alt_lo)
@@ -135,16 +306,22 @@ __device__ __forceinline__ int nh_pad(int NH) { return (NH + 3) & ~3; }
 template <typename T>
 __global__ void k_fam_sweep(FamArgs<T> f)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T* X = (T*)smraw;                           // [nmax][D]
-    T* Y = X + (size_t)f.nmax * f.D;            // [nmax][D]
-    T* Lv = Y + (size_t)f.nmax * f.D;           // [D]
-    int* eo = (int*)(Lv + f.D);                 // [nmax]
-    int* pos = eo + f.nmax;                     // [nmax] table positions
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) uint64_t mbar;
     __shared__ int eL;
+    BatchSmem<T> sm;
+    batch_init(f, sm, smraw, &tmem_slot, &mbar);
+    int* eo = (int*)(smraw + f.batch_bytes);     // [nmax]
+    int* pos = eo + f.nmax;                       // [nmax]
+    int* soff = pos + f.nmax;                     // [nmax]
+    int* doff = soff + f.nmax;                    // [nmax]
+    T* Lv = (T*)(doff + f.nmax);                  // [D]
     const int b = blockIdx.x, K = f.K, D = f.D;
     const int64_t s = f.s0 + b;
     const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
+    T* X = sm.X;
+    T* Y = sm.Y;
     for (int side = 0; side < 2; ++side) {
         T* Tb = (side == 0 ? f.G : f.H) + (size_t)b * 3 * K * K * D;
         int* Te = (side == 0 ? f.Ge : f.He) + (size_t)b * 3 * K * K;
@@ -184,21 +361,11 @@ __global__ void k_fam_sweep(FamArgs<T> f)
                     const int j = (c0 + i) / 3, a = (c0 + i) % 3;
                     const int sf = side == 0 ? j : K - 1 - j;
                     pos[i] = (a * K + sf) * K;
+                    soff[i] = pos[i] + tprev;
+                    doff[i] = pos[i] + t;
                 }
                 __syncthreads();
-                for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
-                    const int i = q / D, c = q - i * D;
-                    X[q] = Tb[((size_t)pos[i] + tprev) * D + c];
-                }
-                __syncthreads();
-                mv_block<T>(Mats + ((size_t)t * 4 + own) * D * D, D, X, Y, n);
-                __syncthreads();
-                renorm_rows<T>(Y, D, n, eo);
-                __syncthreads();
-                for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
-                    const int i = q / D, c = q - i * D;
-                    Tb[((size_t)pos[i] + t) * D + c] = Y[q];
-                }
+                batch_apply<T>(f, sm, Tb, soff, Tb, doff, eo, n, side, t, own);
                 for (int i = threadIdx.x; i < n; i += blockDim.x)
                     Te[pos[i] + t] = Te[pos[i] + tprev] + eo[i];
                 __syncthreads();
@@ -207,6 +374,7 @@ __global__ void k_fam_sweep(FamArgs<T> f)
         if (side == 0 && threadIdx.x == 0) { f.pm[b] = (double)Lv[0]; f.pe[b] = eL; }
         __syncthreads();
     }
+    batch_fini(f, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -342,20 +510,23 @@ __global__ void k_fam_compact(FamArgs<T> f)
 template <typename T>
 __global__ void k_fam_tr(FamArgs<T> f)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T* X = (T*)smraw;
-    T* Y = X + (size_t)f.nmax * f.D;
-    int* eo = (int*)(Y + (size_t)(f.nmax + 1) * f.D);
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) uint64_t mbar;
+    BatchSmem<T> sm;
+    batch_init(f, sm, smraw, &tmem_slot, &mbar);
+    int* eo = (int*)(smraw + f.batch_bytes);
     int* hp = eo + f.nmax;
-    const int b = blockIdx.x, K = f.K, D = f.D;
+    int* doff = hp + f.nmax;
+    const int b = blockIdx.x, K = f.K;
     const int64_t s = f.s0 + b;
     const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
     const size_t nk = (size_t)K * K * 9;
     const int* trl = f.tr_list + (size_t)b * nk;
     const int ntr = f.tr_total[b];
-    const T* H = f.H + (size_t)b * 3 * K * K * D;
+    const T* H = f.H + (size_t)b * 3 * K * K * f.D;
     const int* He = f.He + (size_t)b * 3 * K * K;
-    T* TR = f.TR + (size_t)f.tr_base[b] * D;
+    T* TR = f.TR + (size_t)f.tr_base[b] * f.D;
     int* TRe = f.TRe + f.tr_base[b];
     int i0 = 0;
     while (i0 < ntr) {
@@ -367,22 +538,15 @@ __global__ void k_fam_tr(FamArgs<T> f)
             const int k = trl[i0 + i];
             const int sB = (k / 3) % K, aB = k % 3;
             hp[i] = (aB * K + sB) * K + sA + 1;
+            doff[i] = i0 + i;
         }
         __syncthreads();
-        for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
-            const int i = q / D, c = q - i * D;
-            X[q] = H[(size_t)hp[i] * D + c];
-        }
-        __syncthreads();
-        mv_block<T>(f.A + ((size_t)sA * 4 + sig_of_alt(aA, sigma_at(na, nb, sA))) * D * D, D, X, Y, n);
-        __syncthreads();
-        renorm_rows<T>(Y, D, n, eo);
-        __syncthreads();
-        for (int q = threadIdx.x; q < n * D; q += blockDim.x) TR[(size_t)i0 * D + q] = Y[q];
+        batch_apply<T>(f, sm, H, hp, TR, doff, eo, n, 1, sA, sig_of_alt(aA, sigma_at(na, nb, sA)));
         for (int i = threadIdx.x; i < n; i += blockDim.x) TRe[i0 + i] = eo[i] + He[hp[i]];
         __syncthreads();
         i0 += n;
     }
+    batch_fini(f, sm);
 }
 
 // F4b: TL clusters: created at t = s2 from G_{s1,a1}(s2-1), propagated with
@@ -390,15 +554,17 @@ __global__ void k_fam_tr(FamArgs<T> f)
 template <typename T>
 __global__ void k_fam_tl(FamArgs<T> f)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T* X = (T*)smraw;
-    T* Y = X + (size_t)f.nmax * f.D;
-    int* eo = (int*)(Y + (size_t)(f.nmax + 1) * f.D);
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ int wt[32];
+    BatchSmem<T> sm;
+    batch_init(f, sm, smraw, &tmem_slot, &mbar);
+    int* eo = (int*)(smraw + f.batch_bytes);
     int* src = eo + f.nmax;
     int* dst = src + f.nmax;
     int* pbuf_src = dst + f.nmax;                 // [nmax + blockDim]
     int* pbuf_dst = pbuf_src + f.nmax + blockDim.x;
-    __shared__ int wt[32];
     const int b = blockIdx.x, K = f.K, D = f.D;
     const int64_t s = f.s0 + b;
     const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
@@ -423,30 +589,16 @@ __global__ void k_fam_tl(FamArgs<T> f)
             const int a2 = grp % 3;
             int n = 1;
             while (c0 + n < ncl && n < f.nmax && tll[c0 + n] / (3 * K) == grp) ++n;
-            {
-                for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                    const int key = tll[c0 + i];
-                    const int s1 = (key / 3) % K, a1 = key % 3;
-                    dst[i] = tl[key];
-                    src[i] = (a1 * K + s1) * K + (t - 1);
-                }
-                __syncthreads();
-                for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
-                    const int i = q / D, cc = q - i * D;
-                    X[q] = G[(size_t)src[i] * D + cc];
-                }
-                __syncthreads();
-                mv_block<T>(f.AT + ((size_t)t * 4 + sig_of_alt(a2, own)) * D * D, D, X, Y, n);
-                __syncthreads();
-                renorm_rows<T>(Y, D, n, eo);
-                __syncthreads();
-                for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
-                    const int i = q / D, cc = q - i * D;
-                    TL[(size_t)dst[i] * D + cc] = Y[q];
-                }
-                for (int i = threadIdx.x; i < n; i += blockDim.x) TLe[dst[i]] = eo[i] + Ge[src[i]];
-                __syncthreads();
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int key = tll[c0 + i];
+                const int s1 = (key / 3) % K, a1 = key % 3;
+                dst[i] = tl[key];
+                src[i] = (a1 * K + s1) * K + (t - 1);
             }
+            __syncthreads();
+            batch_apply<T>(f, sm, G, src, TL, dst, eo, n, 0, t, sig_of_alt(a2, own));
+            for (int i = threadIdx.x; i < n; i += blockDim.x) TLe[dst[i]] = eo[i] + Ge[src[i]];
+            __syncthreads();
             c0 += n;
         }
         // (2) propagation of clusters with s2 < t <= end: the list prefix [0, first)
@@ -473,19 +625,7 @@ __global__ void k_fam_tl(FamArgs<T> f)
             const bool last_window = w0 + (int)blockDim.x >= first;
             while (nbuf >= f.nmax || (last_window && nbuf > 0)) {
                 const int n = nbuf < f.nmax ? nbuf : f.nmax;
-                for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
-                    const int i = q / D, cc = q - i * D;
-                    X[q] = TL[(size_t)pbuf_src[i] * D + cc];
-                }
-                __syncthreads();
-                mv_block<T>(f.AT + ((size_t)t * 4 + own) * D * D, D, X, Y, n);
-                __syncthreads();
-                renorm_rows<T>(Y, D, n, eo);
-                __syncthreads();
-                for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
-                    const int i = q / D, cc = q - i * D;
-                    TL[(size_t)pbuf_dst[i] * D + cc] = Y[q];
-                }
+                batch_apply<T>(f, sm, TL, pbuf_src, TL, pbuf_dst, eo, n, 0, t, own);
                 for (int i = threadIdx.x; i < n; i += blockDim.x) TLe[pbuf_dst[i]] = eo[i] + TLe[pbuf_src[i]];
                 __syncthreads();
                 // shift the rest of the buffer down
@@ -501,6 +641,7 @@ __global__ void k_fam_tl(FamArgs<T> f)
             if (w0 >= first) break;
         }
     }
+    batch_fini(f, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -709,13 +850,13 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
 template <typename T>
 static size_t stage_smem(const FamArgs<T>& f, int nints)
 {
-    return (size_t)(2 * f.nmax + 1) * f.D * sizeof(T) + (size_t)nints * f.nmax * sizeof(int);
+    return f.batch_bytes + (size_t)nints * f.nmax * sizeof(int) + (size_t)f.D * sizeof(T) + 64;
 }
 
 template <typename T>
 int fam_launch_sweep(const FamArgs<T>& f, int nb, cudaStream_t st)
 {
-    const size_t smem = stage_smem(f, 2);
+    const size_t smem = stage_smem(f, 4);
     cudaFuncSetAttribute(k_fam_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_fam_sweep<T><<<nb, f.threads, smem, st>>>(f);
     return 1;
@@ -740,7 +881,7 @@ template <typename T>
 int fam_launch_tables(const FamArgs<T>& f, int nb, cudaStream_t st)
 {
     const size_t smem = stage_smem(f, 3);
-    const size_t smem_tl = smem + (size_t)2 * (f.nmax + f.threads) * sizeof(int);
+    const size_t smem_tl = stage_smem(f, 3) + (size_t)2 * (f.nmax + f.threads) * sizeof(int);
     cudaFuncSetAttribute(k_fam_tr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(k_fam_tl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tl);
     k_fam_tr<T><<<nb, f.threads, smem, st>>>(f);
@@ -761,6 +902,37 @@ int fam_launch_rows(const FamArgs<T>& f, const RowSet& rows, int64_t grid, doubl
     if (grid <= 0) return 0;
     k_fam_rows<T><<<(unsigned)grid, kFamRows, 0, st>>>(f, rows, partial, span);
     return 1;
+}
+
+void fam_tc_images(const double* A, int K, int D, std::vector<unsigned char>& images, std::vector<int>& exps)
+{
+    const size_t blk = (size_t)4 * D * D;
+    images.assign((size_t)2 * K * 4 * blk, 0);
+    exps.assign((size_t)2 * K * 4, 0);
+    for (int side = 0; side < 2; ++side)
+        for (int t = 0; t < K; ++t)
+            for (int sg = 0; sg < 4; ++sg) {
+                const double* M = A + ((size_t)t * 4 + sg) * D * D;
+                double mx = 0.0;
+                for (size_t i = 0; i < (size_t)D * D; ++i) mx = std::max(mx, std::fabs(M[i]));
+                int e = 0;
+                if (mx > 0.0) std::frexp(mx, &e);
+                const size_t id = ((size_t)side * K + t) * 4 + sg;
+                exps[id] = e;
+                unsigned char* hi = images.data() + id * blk;
+                unsigned char* lo = hi + 2 * (size_t)D * D;
+                for (int n = 0; n < D; ++n)
+                    for (int k = 0; k < D; ++k) {
+                        // B[n][k]: side 0 -> M[n][k] (y = M x), side 1 -> M[k][n] (y = x^T M)
+                        const double m = std::ldexp(side == 0 ? M[(size_t)n * D + k] : M[(size_t)k * D + n], -e);
+                        const float mf = (float)m;
+                        const __half h = __float2half_rn(mf);
+                        const __half l = __float2half_rn(mf - __half2float(h));
+                        const size_t off = ((size_t)(n >> 3) * (D >> 3) + (k >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2;
+                        std::memcpy(hi + off, &h, 2);
+                        std::memcpy(lo + off, &l, 2);
+                    }
+            }
 }
 
 #define NQS_FAM_INST(T)                                                                    \

@@ -2,6 +2,8 @@
 // (see nqs_family.cu for the decomposition).
 #pragma once
 
+#include <vector>
+
 #include "nqs_kernels.cuh"
 
 namespace nqs {
@@ -11,7 +13,13 @@ struct FamArgs {
     HamView h;
     int K, D;
     int threads;              // block size of the per-sample kernels (>= D)
-    int nmax;                 // vectors staged per block-wide mat-vec batch
+    int nmax;                 // vectors per block-wide mat-vec batch
+    size_t batch_bytes;       // shared memory of one batch (see fam_batch_bytes)
+    int tc;                   // 1: tensor-core batches (FP32, D % 16 == 0, D <= 128)
+    int tc_cols;              // tensor-memory columns allocated per block
+    const uint4* tc_mats;     // [2][K][4] split-FP16 operand images (hi then lo), see fam_tc_images
+    const int* tc_exp;        // [2][K][4] power-of-two scale of each image
+    DevError* err;
     const T* A;               // [K][4][D][D] site tensors in T, A[a][b]
     const T* AT;              // transposed copy, AT[b][a]
     const uint64_t* samples;  // all samples of the call
@@ -46,6 +54,20 @@ template <typename T> int fam_launch_tables(const FamArgs<T>& f, int nb, cudaStr
 // rows.chunk_base[s0] + blockIdx.x
 template <typename T> int fam_launch_rows(const FamArgs<T>& f, const RowSet& rows, int64_t grid,
                                           double* partial, int64_t* span, cudaStream_t st);
+
+// shared memory of the batch buffers of the table kernels
+inline size_t fam_batch_bytes(int D, int nmax, size_t elem, bool tc)
+{
+    if (!tc) return (size_t)2 * nmax * D * elem;
+    const size_t small = ((size_t)8 * D * elem + 1023) & ~(size_t)1023;
+    return small + (size_t)4 * 128 * D + (size_t)4 * D * D + 2 * 128 * 4;
+}
+
+// Split-FP16 operand images of the chain's site tensors for the tensor-core
+// batches: for side 0 the matrix A_t^s, for side 1 its transpose, each scaled
+// by 2^-e (max |entry| in [0.5, 1)), hi and lo halves in the K-major core-matrix
+// layout. images holds 2*K*4 blocks of 4*D*D bytes; exps the e.
+void fam_tc_images(const double* A, int K, int D, std::vector<unsigned char>& images, std::vector<int>& exps);
 
 // bytes of the per-sample tables (G, H, their exponents, cluster maps)
 inline size_t fam_bytes_per_sample(int K, int D, size_t elem)
