@@ -726,10 +726,20 @@ __global__ void k_fam_rbm(FamArgs<T> f)
     }
 }
 
-// F5: one thread per row: psi_TN(m) as a dot product of a left state and a
-// right covector, the factorised correlator ratio, coefficient x ratio; block
-// partial sums in a fixed order.
+// F5: psi_TN(m) as a dot product of a left state and a right covector, the
+// factorised correlator ratio, coefficient x ratio; block partial sums in a
+// fixed order. Each lane decodes one row; then each warp evaluates its 32 rows
+// one at a time with coalesced loads (lanes split the vectors and the hidden
+// units), a compensated tree for the dot product and a tree for the product.
 constexpr int kFamRows = 128;
+
+template <typename T>
+__device__ __forceinline__ void two_sum(T a, T b, T& s, T& e)
+{
+    s = a + b;
+    const T z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows, double* partial,
@@ -754,20 +764,25 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
     const int64_t r0 = beg + j * kFamRows;
     const int nr = (int)((cnt - j * kFamRows) < kFamRows ? (cnt - j * kFamRows) : kFamRows);
     const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
-    const int NH = f.n_hidden;
-    if (threadIdx.x < 32) build_lists_warp(na, nb, f.h.K, lists, threadIdx.x);
+    const int NH = f.n_hidden, NP = nh_pad(NH);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp == 0) build_lists_warp(na, nb, f.h.K, lists, lane);
     __syncthreads();
     const size_t nk = (size_t)K * K * 9;
-    double val = 0.0;
-    int nmv = 0;
-    if ((int)threadIdx.x < nr) {
-        const RowParts p = row_parts(f.h, lists, na, nb, rows.rank[r0 + threadIdx.x]);
+    // ---- per-lane decode of one row
+    const T* Lv = nullptr;
+    const T* Rv = nullptr;
+    const T* lt = nullptr;
+    const T* rs = nullptr;
+    int ex = 0, nmv = 0;
+    double coef = 0.0;
+    const int myrow = (int)threadIdx.x;
+    if (myrow < nr) {
+        const RowParts p = row_parts(f.h, lists, na, nb, rows.rank[r0 + myrow]);
         const T* G = f.G + (size_t)b * 3 * K * K * D;
         const int* Ge = f.Ge + (size_t)b * 3 * K * K;
         const T* H = f.H + (size_t)b * 3 * K * K * D;
         const int* He = f.He + (size_t)b * 3 * K * K;
-        const T* Lv;
-        const T* Rv;
         int eL, eR, lobj, robj;
         if (p.nsite == 4) {
             const int key = tl_key(K, p.s[0], p.a[0], p.s[1], p.a[1]);
@@ -796,42 +811,99 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
                 robj = 3 * K + ti;
             }
         }
+        ex = eL + eR;
         nmv = p.s[p.nsite - 1] - p.s[0] + 1;
+        coef = rows.coef[r0 + myrow];
+        if (NH > 0) {
+            lt = f.rbl + (size_t)(f.rbl_base[b] + lobj) * (NP + 4);
+            rs = f.rbr + (size_t)(f.rbr_base[b] + robj) * (2 * NP);
+        }
+    }
+    const double inv_pm = 1.0 / f.pm[b];
+    const int pe = f.pe[b];
+    // ---- evaluation: 8 lanes per row, 4 rows of the warp at a time
+    const int wbase = warp * 32;
+    const int wrows = nr - wbase < 32 ? (nr - wbase > 0 ? nr - wbase : 0) : 32;
+    const int g = lane >> 3, sub = lane & 7;
+    double myval = 0.0;
+    for (int q0 = 0; q0 < wrows; q0 += 4) {
+        const int q = q0 + g;                       // the row this lane group evaluates
+        const int qs = q < 32 ? q : 31;
+        const T* Lq = (const T*)__shfl_sync(kFull, (unsigned long long)Lv, qs);
+        const T* Rq = (const T*)__shfl_sync(kFull, (unsigned long long)Rv, qs);
+        const T* ltq = (const T*)__shfl_sync(kFull, (unsigned long long)lt, qs);
+        const T* rsq = (const T*)__shfl_sync(kFull, (unsigned long long)rs, qs);
+        const int exq = __shfl_sync(kFull, ex, qs);
+        const double cq = __shfl_sync(kFull, coef, qs);
+        const bool live = q < wrows;
         // dot product with error-free product / sum transformations
         T sum = T(0), comp = T(0);
-        for (int c = 0; c < D; ++c) {
-            const T x = Lv[c], y = Rv[c];
-            const T pr = x * y;
-            const T pe = fma(x, y, -pr);
-            const T t = sum + pr;
-            const T z = t - sum;
-            comp += ((sum - (t - z)) + (pr - z)) + pe;
-            sum = t;
+        if (live) {
+            if ((D & 3) == 0) {
+                typedef typename Vec4<T>::type V4;
+                for (int c4 = sub; c4 < D / 4; c4 += 8) {
+                    const V4 x = ((const V4*)Lq)[c4], y = ((const V4*)Rq)[c4];
+                    const T xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+                    #pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const T pr = xs[u] * ys[u];
+                        const T pe2 = fma(xs[u], ys[u], -pr);
+                        T t, e;
+                        two_sum(sum, pr, t, e);
+                        sum = t;
+                        comp += e + pe2;
+                    }
+                }
+            } else {
+                for (int c = sub; c < D; c += 8) {
+                    const T pr = Lq[c] * Rq[c];
+                    const T pe2 = fma(Lq[c], Rq[c], -pr);
+                    T t, e;
+                    two_sum(sum, pr, t, e);
+                    sum = t;
+                    comp += e + pe2;
+                }
+            }
         }
-        const double dot = (double)sum + (double)comp;
-        double ratio = ldexp(dot / f.pm[b], eL + eR - f.pe[b]);
+        for (int o = 4; o; o >>= 1) {
+            const T so = __shfl_xor_sync(kFull, sum, o);
+            const T co = __shfl_xor_sync(kFull, comp, o);
+            T t, e;
+            two_sum(sum, so, t, e);
+            sum = t;
+            comp += co + e;
+        }
+        double ratio = (double)sum + (double)comp;
         if (NH > 0) {
             typedef typename Vec4<T>::type V4;
-            const int NP = nh_pad(NH);
-            const V4* lt = (const V4*)(f.rbl + (size_t)(f.rbl_base[b] + lobj) * (NP + 4));
-            const V4* rs = (const V4*)(f.rbr + (size_t)(f.rbr_base[b] + robj) * (2 * NP));
-            const V4* rc = rs + NP / 4;
-            // product of (1 + x_k) kept as X = product - 1
-            T X = T(0);
-            for (int k4 = 0; k4 < NP / 4; ++k4) {
-                const V4 t = lt[k4], sh = rs[k4], c1 = rc[k4];
-                T x;
-                x = fma(t.x, sh.x, c1.x); X = fma(X, x, X + x);
-                x = fma(t.y, sh.y, c1.y); X = fma(X, x, X + x);
-                x = fma(t.z, sh.z, c1.z); X = fma(X, x, X + x);
-                x = fma(t.w, sh.w, c1.w); X = fma(X, x, X + x);
+            T X = T(0);                            // product of (1 + x_k) minus 1
+            if (live) {
+                const V4* l4 = (const V4*)ltq;
+                const V4* s4 = (const V4*)rsq;
+                const V4* c4p = s4 + NP / 4;
+                for (int k4 = sub; k4 < NP / 4; k4 += 8) {
+                    const V4 t = l4[k4], sh = s4[k4], c1 = c4p[k4];
+                    T x;
+                    x = fma(t.x, sh.x, c1.x); X = fma(X, x, X + x);
+                    x = fma(t.y, sh.y, c1.y); X = fma(X, x, X + x);
+                    x = fma(t.z, sh.z, c1.z); X = fma(X, x, X + x);
+                    x = fma(t.w, sh.w, c1.w); X = fma(X, x, X + x);
+                }
             }
-            const T XL = ((const T*)lt)[NP];
-            ratio *= (1.0 + (double)XL) * (1.0 + (double)X);
+            for (int o = 4; o; o >>= 1) {
+                const T Y = __shfl_xor_sync(kFull, X, o);
+                X = fma(X, Y, X + Y);
+            }
+            if (live) ratio *= (1.0 + (double)ltq[NP]) * (1.0 + (double)X);
         }
-        val = rows.coef[r0 + threadIdx.x] * ratio;
+        const double val = live ? cq * ldexp(ratio * inv_pm, exq - pe) : 0.0;
+        // hand the value to the lane that decoded the row
+        for (int gg = 0; gg < 4; ++gg) {
+            const double v = __shfl_sync(kFull, val, gg * 8);
+            if (lane == q0 + gg) myval = v;
+        }
     }
-    contrib[threadIdx.x] = val;
+    contrib[threadIdx.x] = myval;
     spsum[threadIdx.x] = nmv;
     __syncthreads();
     if (threadIdx.x == 0) {
