@@ -510,14 +510,15 @@ static void one_sample(const or_ham* h, const or_ansatz* a, const uint64_t* n, i
 }
 
 int or_local_energy(const or_ham* h, const or_ansatz* a, const uint64_t* samples, int64_t Ns,
-                    double eps, int n_draws, uint64_t seed, or_sample_out* out, int n_threads)
+                    double eps, int n_draws, uint64_t seed, or_sample_out* out, int n_threads,
+                    const int64_t* index)
 {
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
     for (int64_t s = 0; s < Ns; ++s)
-        one_sample(h, a, &samples[2 * s], s, eps, n_draws, seed, &out[s]);
+        one_sample(h, a, &samples[2 * s], index ? index[s] : s, eps, n_draws, seed, &out[s]);
     return 0;
 }
 

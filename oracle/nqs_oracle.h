@@ -91,10 +91,12 @@ void or_log_psi(const or_ansatz* a, const uint64_t* det, double* log_abs, int* s
 int or_draws(const or_ham* ham, const uint64_t* n, int64_t sample_index, double eps,
              int n_draws, uint64_t seed, int64_t* ranks, uint64_t* w_total, int* shift);
 
-/* Semistochastic local energy for a batch (OpenMP over samples). */
+/* Semistochastic local energy for a batch (OpenMP over samples). Sample s
+ * draws with Philox counter index `index[s]` (NULL: s itself), so that a few
+ * samples of a larger batch can be recomputed with their batch positions. */
 int or_local_energy(const or_ham* ham, const or_ansatz* a, const uint64_t* samples,
                     int64_t Ns, double eps, int n_draws, uint64_t seed,
-                    or_sample_out* out, int n_threads);
+                    or_sample_out* out, int n_threads, const int64_t* index);
 
 /* d log|psi(n)| / d theta for one determinant: grad_t [n_edges][4][D][D],
  * grad_W [n_hidden][2K], grad_b [n_hidden] (any may be NULL). */

@@ -161,16 +161,18 @@ SAMPLE_DTYPE = np.dtype([("e_loc", "f8"), ("e_det", "f8"), ("e_stoch", "f8"),
 assert SAMPLE_DTYPE.itemsize == C.sizeof(SampleOut)
 
 
-def local_energy(P: Problem, samples=None, eps=None, n_draws=None, seed=None, threads=0):
-    """Semistochastic E_loc for each sample (structured array, SAMPLE_DTYPE)."""
+def local_energy(P: Problem, samples=None, eps=None, n_draws=None, seed=None, threads=0, index=None):
+    """Semistochastic E_loc for each sample (structured array, SAMPLE_DTYPE).
+    ``index`` gives each sample's position in the batch (Philox counter)."""
     s = _c(P.sys.samples if samples is None else samples, np.uint64).reshape(-1, 2)
+    idx = None if index is None else _c(index, np.int64)
     eps = P.sys.eps if eps is None else eps
     n_draws = P.sys.n_draws if n_draws is None else n_draws
     seed = P.sys.seed if seed is None else seed
     out = np.zeros(len(s), SAMPLE_DTYPE)
     lib().or_local_energy(C.byref(P.ham), C.byref(P.ans), _p(s), C.c_int64(len(s)),
                           C.c_double(eps), int(n_draws), C.c_uint64(seed), _p(out),
-                          int(threads))
+                          int(threads), _p(idx))
     return out
 
 

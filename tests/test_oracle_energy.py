@@ -303,6 +303,18 @@ def test_stochastic_estimate_is_unbiased(h50_small):
     assert np.all(np.abs(det_only - exact) > 1e-3)
 
 
+def test_batch_index_selects_the_draw_counter(h50_small):
+    """A sample recomputed alone with its batch position gives the batch's
+    value bit for bit; at another position it draws other determinants."""
+    sys_, P = h50_small
+    full = O.local_energy(P)
+    one = O.local_energy(P, samples=sys_.samples[1:2], index=[1])
+    assert one["e_loc"][0] == full["e_loc"][1] and one["e_stoch"][0] == full["e_stoch"][1]
+    other = O.local_energy(P, samples=sys_.samples[1:2], index=[0])
+    assert other["e_det"][0] == full["e_det"][1]
+    assert other["e_stoch"][0] != full["e_stoch"][1]
+
+
 def test_zero_eps_has_no_stochastic_part(h50_small):
     sys_, P = h50_small
     out = O.local_energy(P, eps=0.0, n_draws=32)
