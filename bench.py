@@ -26,6 +26,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2507_19276_gb300 import shard  # noqa: E402
 from paper_2507_19276_gb300 import workloads as W  # noqa: E402
 
 METRIC = "E_loc samples/s (H50 shape)"
@@ -43,6 +44,16 @@ def _peaks():
 # FP64 FMA throughput of one GB300, measured with a dependent-chain-free DFMA
 # probe ("FP64 peak"); used as the ALU roofline of the FP64 form.
 FP64_PEAK_TFLOPS = 1.196
+
+
+# DRAM bytes (read + write) per evaluated amplitude of the amplitude stage,
+# summed over its kernels, from ncu counters on the H50 shape (D = 64) with
+# 512 samples; the stage's traffic grows in proportion to the amplitudes
+# evaluated. None until taken for the current kernels.
+STAGE_TRAFFIC_PER_AMP = {"mixed": None, "fp64_shared": None}
+
+DTYPES = {"mixed": "f16x3 tensor-core products (f32 accumulate) + f32 gathers; f64 H, ratios, sums",
+          "fp64_shared": "f64", "fp64": "f64"}
 
 
 class ClockSampler:
@@ -138,11 +149,12 @@ def cpu_oracle_rate(sys_, n_samples, threads):
     return n_samples / dt, dt
 
 
-def workload_config(sys_, precision):
+def workload_config(sys_, precision, ws=1):
     return {"workload": f"h50_chain K={sys_.K} {sys_.n_alpha}a+{sys_.n_beta}b D={sys_.D} "
-                        f"N_h={sys_.n_hidden} Ns={len(sys_.samples)} eps={sys_.eps:g} "
+                        f"N_h={sys_.n_hidden} Ns={len(sys_.samples)} per GPU eps={sys_.eps:g} "
                         f"N_eps={sys_.n_draws}",
-            "K": sys_.K, "D": sys_.D, "n_hidden": sys_.n_hidden, "samples": len(sys_.samples),
+            "K": sys_.K, "D": sys_.D, "n_hidden": sys_.n_hidden,
+            "samples_per_gpu": len(sys_.samples), "global_batch": ws * len(sys_.samples),
             "eps": sys_.eps, "n_draws": sys_.n_draws, "precision": precision,
             "l2": "working set > L2 (deterministic lists ~2.5 GB per step)"}
 
@@ -178,21 +190,31 @@ def run(args):
     ws, rank, local = dist_setup()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    sys_ = W.h50_chain(seed_offset=rank, n_samples=args.samples)
+    # weak scaling: one batch of args.samples unique samples per GPU, split
+    # contiguously; each shard's draws are keyed by global sample position
+    total = args.samples * ws
+    lo, hi = shard.shard_range(total, ws, rank)
+    sys_ = W.h50_chain(n_samples=total).subset(range(lo, hi))
     Ns = len(sys_.samples)
     ctx = nqs.Context(local)
     ctx.set_system(sys_)
     prec = {"mixed": nqs.NQS_PREC_MIXED, "fp64": nqs.NQS_PREC_FP64,
             "fp64_shared": nqs.NQS_PREC_FP64_SHARED}[args.precision]
-    ctx.set_precision(prec, timing=True)
+    ctx.set_precision(prec, timing=True, sample_index_base=lo)
 
     samples = torch.from_numpy(sys_.samples.view(np.int64)).to(dev)
     counts = torch.from_numpy(sys_.counts).to(dev)
     e_loc = torch.empty(Ns, dtype=torch.float64, device=dev)
 
     def step(summary=None):
+        if ws > 1 and summary is None:
+            summary = nqs.EnergySummary()
         nqs.nqs_local_energy(ctx.h, samples, counts, Ns, sys_.eps, sys_.n_draws, sys_.seed, e_loc,
                              summary)
+        if ws > 1:
+            # the one exchange of the method: the weighted-energy sums
+            return shard.allreduce(summary.as_dict(), device=dev)
+        return None
 
     summ = nqs.EnergySummary()
     for _ in range(args.warmup):
@@ -216,7 +238,7 @@ def run(args):
     ms = start.elapsed_time(stop)
     stages = ctx.stage_times()
     ms = max_over_ranks(ms, ws, dev)
-    value = ws * Ns * args.steps / (ms / 1e3)
+    value = total * args.steps / (ms / 1e3)
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     hs = torch.from_numpy(sys_.samples.view(np.int64)).pin_memory()
@@ -236,50 +258,69 @@ def run(args):
     e2e_ms = max_over_ranks(e2e_ms, ws, dev)
     ctx.stage_times()
 
-    # roofline of the dominant kernel
+    # roofline of the amplitude contraction (the dominant stage)
     peaks, src = _peaks()
     work = summ.as_dict()
-    n_amp, n_det = work["n_amplitudes"], work["n_det"]
-    D, NH = sys_.D, sys_.n_hidden
-    det_ms = stages["amp_det"][0] / args.steps
-    if prec == nqs.NQS_PREC_FP64:
-        # per-amplitude FP64 products: 2 D^2 flops per site of each row's span
-        flops = 2.0 * D * D * work["span_sites"] + 2.0 * D * n_amp
-        amp_ms = (stages["amp_det"][0] + stages["amp_draw"][0]) / args.steps
-        achieved = flops / (amp_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "peak_source": "FP64 DFMA probe, measured (DESIGN.md)",
-                "kernel": "k_amp_chain_fp64 (deterministic + drawn rows)",
-                "algorithmic_flops_per_step": flops}
+    n_amp = work["n_amplitudes"]
+    D = sys_.D
+    amp_ms = sum(stages[k][0] for k in ("tables", "amp_det", "amp_draw")) / args.steps
+    amp_launches = sum(stages[k][1] for k in ("tables", "amp_det", "amp_draw")) / args.steps
+    # the method's work per amplitude: one D x D product per site of the span
+    # between the first and last changed site, plus the closing dot product
+    flops = 2.0 * D * D * work["span_sites"] + 2.0 * D * n_amp
+    executed = 2.0 * D * D * work["matvecs"] + 2.0 * D * n_amp
+    achieved = flops / (amp_ms / 1e3) / 1e12
+    if prec == nqs.NQS_PREC_MIXED:
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "achieved": achieved,
+                "peak": peaks["bf16_tflops_sustained"],
+                "peak_source": f"{src} dense bf16 (sustained; f16 has the same nominal rate)",
+                "kernel": "amplitude stage: k_fam_sweep, k_fam_mark, k_fam_compact, k_fam_tr, "
+                          "k_fam_tl (tcgen05), k_fam_rbm, k_fam_rows"}
     else:
-        # k_fam_rows: per deterministic row the rank and coefficient, one left state and
-        # one right covector (D values each) and the two correlator factor rows
-        # (N_h+4 and 2 N_h values), in the contraction's element size
-        el = 4 if prec == nqs.NQS_PREC_MIXED else 8
-        np_ = (NH + 3) // 4 * 4 if NH else 0
-        per_row = 4 + 8 + 2 * D * el + ((np_ + 4) + 2 * np_) * el
-        nbytes = per_row * n_det
-        achieved = nbytes / (det_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "peak_source": f"{src} HBM copy bandwidth",
-                "kernel": "k_fam_rows (deterministic rows)",
-                "algorithmic_bytes_per_step": nbytes, "bytes_per_row": per_row}
+        roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "peak_source": "FP64 FMA probe, measured",
+                "kernel": ("amplitude stage (shared prefixes, FP64)" if prec == nqs.NQS_PREC_FP64_SHARED
+                           else "k_amp_chain_fp64 / k_amp_graph_fp64 (one amplitude per row)")}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
-    roof["kernel_ms_per_step"] = det_ms
-    roof["launches_per_step"] = stages["amp_det"][1] / args.steps
-    roof["matvecs_per_step"] = work["matvecs"]
+    key = args.precision if sys_.D == 64 else None
+    roof["traffic"] = STAGE_TRAFFIC_PER_AMP.get(key, None)
+    if roof["traffic"] is not None:
+        roof["traffic"] *= n_amp
+    roof.update({"algorithmic_flops_per_step": flops, "executed_flops_per_step": executed,
+                 "stage_ms_per_step": amp_ms, "launches_per_step": amp_launches,
+                 "span_sites_per_step": work["span_sites"], "matvecs_per_step": work["matvecs"]})
+
+    # the FP64 GPU form on the same batch: its throughput and the energy difference
+    fp64 = None
+    if not args.no_fp64_compare and prec == nqs.NQS_PREC_MIXED:
+        e_mixed = e_loc.clone()
+        ctx.set_precision(nqs.NQS_PREC_FP64_SHARED, timing=False)
+        s64 = nqs.EnergySummary()
+        step(s64)
+        torch.cuda.synchronize()
+        start.record(stream)
+        step(s64)
+        stop.record(stream)
+        torch.cuda.synchronize()
+        ms64 = start.elapsed_time(stop)
+        d = (e_loc - e_mixed).abs()
+        fp64 = {"precision": "fp64_shared", "value": total / (ms64 / 1e3), "unit": UNIT,
+                "ms_per_step": ms64,
+                "e_mean_diff_ha": abs(s64.as_dict()["e_mean"] - work["e_mean"]),
+                "max_abs_diff_ha": float(d.max().item()),
+                "median_abs_diff_ha": float(d.median().item())}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 contractions + f64 H/ratios/sums" if prec == nqs.NQS_PREC_MIXED else "f64",
-            "data": "synthetic", "config": workload_config(sys_, args.precision),
+            "dtype": DTYPES[args.precision],
+            "data": "synthetic", "config": workload_config(sys_, args.precision, ws),
             "connected_dets_per_s": value * work["n_conn"],
             "amplitudes_per_s": ws * n_amp * args.steps / (ms / 1e3),
             "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
             "roofline": roof,
-            "e2e": {"value": ws * Ns * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+            "fp64_gpu": fp64,
+            "e2e": {"value": total * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": Ns * 16 + Ns * 8, "d2h_bytes_per_step": Ns * 8},
             "clocks": clk,
             "gpu_launches": int(sum(v[1] for v in stages.values())),
@@ -305,6 +346,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp64_shared"])
     ap.add_argument("--samples", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -76,7 +76,12 @@ typedef struct {
     int precision;        /* nqs_precision */
     int timing;           /* nonzero: time every stage with CUDA events on the
                              context's stream (see nqs_stage_times) */
-    int reserved[14];     /* must be zero */
+    int64_t sample_index_base;  /* global position of samples[0] when one batch
+                             is split across calls or devices: sample s of a
+                             call draws with Philox counter (d, base + s), so
+                             the draws do not depend on the split (default 0;
+                             must be >= 0) */
+    int reserved[12];     /* must be zero */
 } nqs_options;
 
 /* Stages of the local-energy path, as reported by nqs_stage_times. */

@@ -60,6 +60,7 @@ struct nqs_ctx {
 
     // stage accounting (nqs_stage_times)
     int timing = 0;
+    int64_t index_base = 0;    // Philox sample counter of samples[0]
     double stage_ms[NQS_N_STAGES] = {0};
     int64_t stage_launch[NQS_N_STAGES] = {0};
     struct Pending { int stage; cudaEvent_t a, b; };
@@ -600,6 +601,8 @@ extern "C" int nqs_destroy(nqs_ctx* c)
 
 extern "C" const char* nqs_last_error(const nqs_ctx* c) { return c ? c->err : "null context"; }
 
+static_assert(sizeof(nqs_options) == 64, "nqs_options layout");
+
 extern "C" int nqs_set_options(nqs_ctx* c, const nqs_options* o)
 {
     if (!c || !o) return NQS_ERR_INVALID_ARG;
@@ -607,9 +610,12 @@ extern "C" int nqs_set_options(nqs_ctx* c, const nqs_options* o)
     if (o->precision != NQS_PREC_FP64 && o->precision != NQS_PREC_MIXED &&
         o->precision != NQS_PREC_FP64_SHARED)
         return set_err(c, NQS_ERR_INVALID_ARG, "unknown precision %d", o->precision);
-    for (int i = 0; i < 14; ++i)
+    for (int i = 0; i < 12; ++i)
         if (o->reserved[i]) return set_err(c, NQS_ERR_INVALID_ARG, "nqs_options.reserved[%d] != 0", i);
+    if (o->sample_index_base < 0)
+        return set_err(c, NQS_ERR_INVALID_ARG, "nqs_options.sample_index_base < 0");
     c->precision = o->precision;
+    c->index_base = o->sample_index_base;
     c->timing = o->timing ? 1 : 0;
     return NQS_OK;
 }
@@ -942,6 +948,7 @@ int draw_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, uint64_t eb, int n_dra
         d.rem_max_bits = (const unsigned long long*)c->rem_max.p;
         d.n_draws = n_draws;
         d.seed = seed;
+        d.index_base = c->index_base;
         d.out_rank = rank_out;
         LAUNCH(NQS_STAGE_DRAW, launch_draws(d, c->stream));
     }
@@ -1269,6 +1276,7 @@ extern "C" int nqs_draws_noalloc(nqs_ctx* c, const uint64_t* samples, int64_t Ns
         d.rem_max_bits = rem_max;
         d.n_draws = n_draws;
         d.seed = seed;
+        d.index_base = c->index_base;
         d.out_rank = ranks;
         LAUNCH(NQS_STAGE_DRAW, launch_draws(d, c->stream));
     }

@@ -36,6 +36,7 @@ struct DrawArgs {
     const unsigned long long* rem_max_bits;
     int n_draws;
     uint64_t seed;
+    int64_t index_base;                  // Philox sample counter of samples[0]
     int64_t* out_rank;                   // [Ns][n_draws]
 };
 int launch_draws(const DrawArgs& a, cudaStream_t st);

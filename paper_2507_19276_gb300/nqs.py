@@ -33,7 +33,8 @@ class NQSError(RuntimeError):
 
 
 class Options(C.Structure):
-    _fields_ = [("precision", C.c_int), ("timing", C.c_int), ("reserved", C.c_int * 14)]
+    _fields_ = [("precision", C.c_int), ("timing", C.c_int),
+                ("sample_index_base", C.c_int64), ("reserved", C.c_int * 12)]
 
 
 N_STAGES = 9
@@ -136,10 +137,11 @@ def nqs_last_error(ctx) -> str:
     return (load().nqs_last_error(ctx) or b"").decode()
 
 
-def nqs_set_options(ctx, precision: int, timing: int = 0):
+def nqs_set_options(ctx, precision: int, timing: int = 0, sample_index_base: int = 0):
     o = Options()
     o.precision = precision
     o.timing = timing
+    o.sample_index_base = sample_index_base
     _check(ctx, load().nqs_set_options(ctx, C.byref(o)))
 
 
@@ -219,8 +221,8 @@ class Context:
         except Exception:
             pass
 
-    def set_precision(self, precision: int, timing: bool = False):
-        nqs_set_options(self.h, precision, int(bool(timing)))
+    def set_precision(self, precision: int, timing: bool = False, sample_index_base: int = 0):
+        nqs_set_options(self.h, precision, int(bool(timing)), sample_index_base)
 
     def stage_times(self):
         """{stage: (device ms, kernel launches)} since the previous call."""

@@ -115,6 +115,30 @@ def test_draws_bit_exact(ctx, cases, problems, name, eps, nd):
         assert np.array_equal(ranks[s], ref)
 
 
+def test_sample_index_base_shifts_the_draw_counter(ctx, cases, problems):
+    """A shard of a batch, passed with its global position, draws what the
+    whole batch draws at those positions (and its E_loc matches the oracle's
+    at the same positions)."""
+    sys_, P = cases["h50"], problems["h50"]
+    _load(ctx, sys_)
+    base = 1000
+    try:
+        ctx.set_precision(nqs.NQS_PREC_FP64, sample_index_base=base)
+        ranks, wt = ctx.draws(sys_.samples, sys_.eps, 64, 5)
+        for s, n in enumerate(sys_.samples):
+            ref, Wref, _ = O.draws(P, n, base + s, sys_.eps, 64, 5)
+            assert int(wt[s]) == Wref and np.array_equal(ranks[s], ref)
+        sub = sys_.subset([0, 1])
+        e, _ = ctx.local_energy(sub.samples, None, sys_.eps, 64, 5)
+        ref = O.local_energy(P, samples=sub.samples, eps=sys_.eps, n_draws=64, seed=5,
+                             index=[base, base + 1])
+        assert _rel_sum(e, ref) < RTOL_FP64
+        with pytest.raises(nqs.NQSError):
+            ctx.set_precision(nqs.NQS_PREC_FP64, sample_index_base=-1)
+    finally:
+        ctx.set_precision(nqs.NQS_PREC_FP64)
+
+
 # ---------------------------------------------------------------------------
 # local energy, FP64
 # ---------------------------------------------------------------------------
