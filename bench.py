@@ -225,9 +225,10 @@ def run(args):
     stream = torch.cuda.current_stream(dev)
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(1.0)     # nvidia-smi's start-up (NVML init) stays outside the timed region
     barrier(ws)
     torch.cuda.synchronize()
-    clocks.start()
     start.record(stream)
     for _ in range(args.steps):
         step()

@@ -339,6 +339,78 @@ void or_log_psi(const or_ansatz* a, const uint64_t* det, double* log_abs, int* s
     *log_abs = log(fabs(mant)) + (double)e * M_LN2 + lf;
 }
 
+/* S 2^Se += v 2^e, keeping the larger exponent */
+static void add_scaled(double* S, int* Se, double v, int e)
+{
+    if (v == 0.0) return;
+    if (*S == 0.0) { *S = v; *Se = e; }
+    else if (e > *Se) { *S = ldexp(*S, *Se - e) + v; *Se = e; }
+    else *S += ldexp(v, e - *Se);
+    int k;
+    *S = frexp(*S, &k);
+    *Se += k;
+}
+
+double or_log_psi_p1(const or_ansatz* a, const uint64_t* det)
+{
+    const int K = a->K, D = a->D;
+    int sigma[64];
+    sigma_of(K, det, sigma);
+    double* hs = (double*)malloc(sizeof(double) * (size_t)K * D);
+    int* ex = (int*)malloc(sizeof(int) * K);
+    forward_states(a, sigma, hs, ex);
+    /* adjoints g_i = d psi_TN / d h_i, scaled with exponents gx */
+    double* gs = (double*)calloc((size_t)K * D, sizeof(double));
+    int* gx = (int*)calloc(K, sizeof(int));
+    int* gset = (int*)calloc(K, sizeof(int));
+    double* tmp = (double*)malloc(sizeof(double) * D);
+    gs[(size_t)(K - 1) * D + 0] = 1.0;
+    gset[K - 1] = 1;
+    double S = 0.0;
+    int Se = 0;
+    for (int i = K - 1; i >= 0; --i) {        /* every successor of i is done */
+        if (!gset[i]) continue;               /* i does not reach the readout */
+        const double* g = gs + (size_t)i * D;
+        int e0, e1;
+        edges_of(a, i, &e0, &e1);
+        for (int e = e0; e < e1; ++e) {
+            const int j = edge_src(a, e);
+            const double* M = tensor(a, e, sigma[i]);
+            /* |g_i|^T |M_e| |h_j| (h_{-1} = e_0) */
+            double t = 0.0;
+            for (int r = 0; r < D; ++r) {
+                double s = 0.0;
+                for (int q = 0; q < D; ++q) {
+                    double hj = (j < 0) ? (q == 0 ? 1.0 : 0.0) : hs[(size_t)j * D + q];
+                    s += fabs(M[r * D + q]) * fabs(hj);
+                }
+                t += fabs(g[r]) * s;
+            }
+            add_scaled(&S, &Se, t, gx[i] + (j < 0 ? 0 : ex[j]));
+            if (j < 0) continue;
+            /* g_j += M_e^T g_i */
+            for (int q = 0; q < D; ++q) {
+                double s = 0.0;
+                for (int r = 0; r < D; ++r) s += M[r * D + q] * g[r];
+                tmp[q] = s;
+            }
+            double* gj = gs + (size_t)j * D;
+            if (!gset[j]) {
+                for (int q = 0; q < D; ++q) gj[q] = tmp[q];
+                gx[j] = gx[i];
+                gset[j] = 1;
+            } else {
+                const int em = gx[j] > gx[i] ? gx[j] : gx[i];
+                for (int q = 0; q < D; ++q) gj[q] = ldexp(gj[q], gx[j] - em) + ldexp(tmp[q], gx[i] - em);
+                gx[j] = em;
+            }
+            gx[j] += renorm(gj, D);
+        }
+    }
+    free(hs); free(ex); free(gs); free(gx); free(gset); free(tmp);
+    return S > 0.0 ? log(S) + (double)Se * M_LN2 : -INFINITY;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Semistochastic local energy (Sec. 2.4)                                    */
 /* ------------------------------------------------------------------------ */
@@ -452,8 +524,16 @@ int or_draws(const or_ham* h, const uint64_t* n, int64_t si, double eps, int n_d
     return 0;
 }
 
+/* |a| (P1(m) f(m) + kappa_n |psi(m)|) / |psi(n)| for one term (see e_cond) */
+static double cond_term(const or_ansatz* a, const uint64_t* m, double coef, double la_m,
+                        double lf_m, double la_n, double kappa_n)
+{
+    const double lp = or_log_psi_p1(a, m);
+    return fabs(coef) * (exp(lp + lf_m - la_n) + kappa_n * exp(la_m - la_n));
+}
+
 static void one_sample(const or_ham* h, const or_ansatz* a, const uint64_t* n, int64_t si,
-                       double eps, int n_draws, uint64_t seed, or_sample_out* o)
+                       double eps, int n_draws, uint64_t seed, or_sample_out* o, int with_cond)
 {
     memset(o, 0, sizeof(*o));
     double la_n, lf_n;
@@ -464,6 +544,9 @@ static void one_sample(const or_ham* h, const or_ansatz* a, const uint64_t* n, i
     o->log_f = lf_n;
     o->h_diag = or_diag(h, n);
     if (sg_n == 0) { o->e_loc = NAN; return; }
+    /* kappa_n = P1(n) / |psi_TN(n)| */
+    const double kappa_n = with_cond ? exp(or_log_psi_p1(a, n) - (la_n - lf_n)) : 0.0;
+    double econd = 0.0;
 
     split_t sp;
     split_build(h, n, eps, &sp);
@@ -483,6 +566,7 @@ static void one_sample(const or_ham* h, const or_ansatz* a, const uint64_t* n, i
         double ratio = (double)(sg_m * sg_n) * exp(la_m - la_n);
         ed += sp.H[r] * ratio;
         eabs += fabs(sp.H[r] * ratio);
+        if (with_cond) econd += cond_term(a, &sp.dets[2 * r], sp.H[r], la_m, lf_m, la_n, kappa_n);
     }
     o->n_det = ndet;
     o->e_det = ed;
@@ -500,25 +584,29 @@ static void one_sample(const or_ham* h, const or_ansatz* a, const uint64_t* n, i
             double ratio = (double)(sg_m * sg_n) * exp(la_m - la_n);
             es += sp.H[r] * ((double)sp.W / (double)w) * ratio;
             eabs += fabs(sp.H[r] * ((double)sp.W / (double)w) * ratio) / (double)n_draws;
+            if (with_cond)
+                econd += cond_term(a, &sp.dets[2 * r], sp.H[r] * ((double)sp.W / (double)w) / (double)n_draws,
+                                   la_m, lf_m, la_n, kappa_n);
         }
         es /= (double)n_draws;
     }
     o->e_stoch = es;
     o->e_abs = eabs;
+    o->e_cond = with_cond ? econd : 0.0;
     o->e_loc = o->h_diag + ed + es;
     split_free(&sp);
 }
 
 int or_local_energy(const or_ham* h, const or_ansatz* a, const uint64_t* samples, int64_t Ns,
                     double eps, int n_draws, uint64_t seed, or_sample_out* out, int n_threads,
-                    const int64_t* index)
+                    const int64_t* index, int with_cond)
 {
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
     for (int64_t s = 0; s < Ns; ++s)
-        one_sample(h, a, &samples[2 * s], index ? index[s] : s, eps, n_draws, seed, &out[s]);
+        one_sample(h, a, &samples[2 * s], index ? index[s] : s, eps, n_draws, seed, &out[s], with_cond);
     return 0;
 }
 

@@ -55,6 +55,14 @@ typedef struct {
     double e_loc, e_det, e_stoch, h_diag;
     double e_abs;            /* |H_nn| + sum |terms| of E^d and E^s: the scale
                                 that rounding errors of the sums are relative to */
+    double e_cond;           /* (with_cond only, else 0) first-order rounding scale
+                                of the ratios: sum |a_m| (P1(m) f(m) + kappa_n
+                                |psi(m)|) / |psi(n)|, a_m the term's coefficient,
+                                P1 the first-order bound of the contraction (see
+                                or_log_psi_p1) and kappa_n = P1(n)/|psi_TN(n)|: to
+                                first order in the unit roundoff u, evaluating every
+                                ratio in precision u moves E_loc by at most about
+                                u e_cond (times the length of a mat-vec row) */
     double log_abs_psi;      /* log|psi(n)| (TN x correlator) */
     double log_f;            /* log f(n) */
     int sign_psi;
@@ -86,6 +94,16 @@ void or_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out
 void or_log_psi(const or_ansatz* a, const uint64_t* det, double* log_abs, int* sign,
                 double* log_f);
 
+/* log P1(det), P1 = sum over edges e = (j -> i) of |g_i|^T |M_e^{sigma_i}| |h_j|,
+ * with h_j the forward states of Sec. 2.2 (h_{-1} = e_0) and g_i = d psi_TN /
+ * d h_i the exact adjoints. Each mat-vec h_i = sum_e M_e h_j rounded in precision
+ * u errs by at most ~u |M_e| |h_j| per entry, and that error reaches psi_TN
+ * through g_i, so u P1 bounds the rounding error of psi_TN to first order
+ * (running-error analysis; Higham, Accuracy and Stability of Numerical
+ * Algorithms, 2nd ed., Ch. 3). For a chain it is
+ * sum_t |R_{t+1}|^T |A_t^{sigma_t}| |L_{t-1}|, which grows linearly in K. */
+double or_log_psi_p1(const or_ansatz* a, const uint64_t* det);
+
 /* Draw indices (canonical rank) of the stochastic part for sample n with
  * batch index `sample_index`; returns W and the shift through the pointers. */
 int or_draws(const or_ham* ham, const uint64_t* n, int64_t sample_index, double eps,
@@ -96,7 +114,7 @@ int or_draws(const or_ham* ham, const uint64_t* n, int64_t sample_index, double 
  * samples of a larger batch can be recomputed with their batch positions. */
 int or_local_energy(const or_ham* ham, const or_ansatz* a, const uint64_t* samples,
                     int64_t Ns, double eps, int n_draws, uint64_t seed,
-                    or_sample_out* out, int n_threads, const int64_t* index);
+                    or_sample_out* out, int n_threads, const int64_t* index, int with_cond);
 
 /* d log|psi(n)| / d theta for one determinant: grad_t [n_edges][4][D][D],
  * grad_W [n_hidden][2K], grad_b [n_hidden] (any may be NULL). */

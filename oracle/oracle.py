@@ -48,7 +48,8 @@ class Ansatz(C.Structure):
 
 class SampleOut(C.Structure):
     _fields_ = [("e_loc", C.c_double), ("e_det", C.c_double), ("e_stoch", C.c_double),
-                ("h_diag", C.c_double), ("e_abs", C.c_double), ("log_abs_psi", C.c_double),
+                ("h_diag", C.c_double), ("e_abs", C.c_double), ("e_cond", C.c_double),
+                ("log_abs_psi", C.c_double),
                 ("log_f", C.c_double),
                 ("sign_psi", C.c_int), ("n_det", C.c_int64), ("n_rem", C.c_int64),
                 ("w_total", C.c_uint64), ("w_shift", C.c_int)]
@@ -61,6 +62,7 @@ def lib():
             _lib = C.CDLL(build())
             _lib.or_n_conn.restype = C.c_int64
             _lib.or_diag.restype = C.c_double
+            _lib.or_log_psi_p1.restype = C.c_double
             _lib.or_connected.restype = C.c_int64
     return _lib
 
@@ -144,6 +146,12 @@ def log_psi(P: Problem, det):
     return la.value, sg.value, lf.value
 
 
+def log_psi_p1(P: Problem, det):
+    """log P1: first-order rounding bound of the tensor-network contraction."""
+    d = _c(det, np.uint64)
+    return float(lib().or_log_psi_p1(C.byref(P.ans), _p(d)))
+
+
 def draws(P: Problem, det, sample_index, eps, n_draws, seed):
     d = _c(det, np.uint64)
     ranks = np.empty(max(n_draws, 1), np.int64)
@@ -155,15 +163,18 @@ def draws(P: Problem, det, sample_index, eps, n_draws, seed):
 
 
 SAMPLE_DTYPE = np.dtype([("e_loc", "f8"), ("e_det", "f8"), ("e_stoch", "f8"),
-                         ("h_diag", "f8"), ("e_abs", "f8"), ("log_abs_psi", "f8"), ("log_f", "f8"),
+                         ("h_diag", "f8"), ("e_abs", "f8"), ("e_cond", "f8"), ("log_abs_psi", "f8"),
+                         ("log_f", "f8"),
                          ("sign_psi", "i4"), ("n_det", "i8"), ("n_rem", "i8"),
                          ("w_total", "u8"), ("w_shift", "i4")], align=True)
 assert SAMPLE_DTYPE.itemsize == C.sizeof(SampleOut)
 
 
-def local_energy(P: Problem, samples=None, eps=None, n_draws=None, seed=None, threads=0, index=None):
+def local_energy(P: Problem, samples=None, eps=None, n_draws=None, seed=None, threads=0, index=None,
+                 cond=False):
     """Semistochastic E_loc for each sample (structured array, SAMPLE_DTYPE).
-    ``index`` gives each sample's position in the batch (Philox counter)."""
+    ``index`` gives each sample's position in the batch (Philox counter);
+    ``cond`` also fills e_cond (doubles the amplitude work)."""
     s = _c(P.sys.samples if samples is None else samples, np.uint64).reshape(-1, 2)
     idx = None if index is None else _c(index, np.int64)
     eps = P.sys.eps if eps is None else eps
@@ -172,7 +183,7 @@ def local_energy(P: Problem, samples=None, eps=None, n_draws=None, seed=None, th
     out = np.zeros(len(s), SAMPLE_DTYPE)
     lib().or_local_energy(C.byref(P.ham), C.byref(P.ans), _p(s), C.c_int64(len(s)),
                           C.c_double(eps), int(n_draws), C.c_uint64(seed), _p(out),
-                          int(threads), _p(idx))
+                          int(threads), _p(idx), int(bool(cond)))
     return out
 
 

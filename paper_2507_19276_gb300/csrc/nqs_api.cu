@@ -52,7 +52,7 @@ struct nqs_ctx {
     DevBuf base_det, base_draw, part_det, part_draw, eloc, edet, estoch, summary, derr;
     DevBuf span_det, span_draw;
     // shared-prefix path
-    DevBuf fG, fGe, fH, fHe, fpm, fpe, ftl_end, ftl_idx, ftr_idx, ftl_tot, ftr_tot, ftl_base,
+    DevBuf fG, fGe, fH, fHe, ftl_end, ftl_idx, ftr_idx, ftl_tot, ftr_tot, ftl_base,
         ftr_base, fTL, fTLe, fTR, fTRe, ftl_ci, ftl_list, ftr_list, ftl_cnt, frbl, frbr, frbl_base,
         frbr_base;
     std::vector<int64_t> det_off_h;
@@ -289,7 +289,9 @@ int count_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, uint64_t eb, int
     return NQS_OK;
 }
 
-int env_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, bool adjoints, bool tn = true)
+// tn: 1 = psi(n) and the environments; 2 = psi(n) only (chain, shared-prefix
+// path: its FP64 value is the denominator of every ratio of the sample)
+int env_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, bool adjoints, int tn = 1)
 {
     const int K = c->K, D = c->av.D, NH = c->av.n_hidden;
     EnvArgs e{};
@@ -297,9 +299,9 @@ int env_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, bool adjoints, boo
     e.h = c->hv;
     e.samples = samples;
     e.Ns = Ns;
-    e.tn = tn ? 1 : 0;
-    if (!tn) {
-        // shared-prefix path: psi(n) comes from its own sweep
+    e.tn = tn;
+    if (tn == 2) {
+        // psi(n) only
     } else if (c->av.chain) {
         TRY(ensure(c, c->Lenv, (size_t)Ns * (K + 1) * D * 8));
         TRY(ensure(c, c->Renv, (size_t)Ns * (K + 1) * D * 8));
@@ -406,8 +408,6 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
     TRY(ensure(c, c->fH, nb * KKD * sizeof(T)));
     TRY(ensure(c, c->fGe, nb * 3 * K * K * 4));
     TRY(ensure(c, c->fHe, nb * 3 * K * K * 4));
-    TRY(ensure(c, c->fpm, nb * 8));
-    TRY(ensure(c, c->fpe, nb * 4));
     TRY(ensure(c, c->ftl_end, nb * nk * 4));
     TRY(ensure(c, c->ftl_idx, nb * nk * 4));
     TRY(ensure(c, c->ftr_idx, nb * nk * 4));
@@ -472,7 +472,7 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
         f.s1 = s1;
         f.G = (T*)c->fG.p; f.Ge = (int*)c->fGe.p;
         f.H = (T*)c->fH.p; f.He = (int*)c->fHe.p;
-        f.pm = (double*)c->fpm.p; f.pe = (int*)c->fpe.p;
+        f.pm = (const double*)c->pmant.p + s0; f.pe = (const int*)c->pexp.p + s0;
         f.tl_end = (int*)c->ftl_end.p;
         f.tl_idx = (int*)c->ftl_idx.p;
         f.tr_idx = (int*)c->ftr_idx.p;
@@ -486,9 +486,6 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
         CK(cudaMemsetAsync(c->ftl_end.p, 0xff, (size_t)nbb * nk * 4, c->stream));
         CK(cudaMemsetAsync(c->ftr_idx.p, 0, (size_t)nbb * nk * 4, c->stream));
         LAUNCH(NQS_STAGE_TABLES, fam_launch_sweep<T>(f, nbb, c->stream));
-        k_check_psi<<<(unsigned)((nbb + 255) / 256), 256, 0, c->stream>>>((const double*)c->fpm.p, nbb,
-                                                                         (DevError*)c->derr.p, s0);
-        LAUNCH(NQS_STAGE_TABLES, 1);
         LAUNCH(NQS_STAGE_TABLES, fam_launch_mark<T>(f, rd, nbb, c->stream));
         if (n_draws > 0) LAUNCH(NQS_STAGE_TABLES, fam_launch_mark<T>(f, rs, nbb, c->stream));
         LAUNCH(NQS_STAGE_TABLES, fam_launch_compact<T>(f, nbb, c->stream));
@@ -587,7 +584,7 @@ extern "C" int nqs_destroy(nqs_ctx* c)
                       &c->draw_rank, &c->draw_coef, &c->n_unique, &c->base_det, &c->base_draw,
                       &c->part_det, &c->part_draw, &c->eloc, &c->edet, &c->estoch, &c->summary,
                       &c->derr, &c->span_det, &c->span_draw, &c->Af, &c->ATf,
-                      &c->Wf, &c->fG, &c->fGe, &c->fH, &c->fHe, &c->fpm, &c->fpe, &c->ftl_end,
+                      &c->Wf, &c->fG, &c->fGe, &c->fH, &c->fHe, &c->ftl_end,
                       &c->ftl_idx, &c->ftr_idx, &c->ftl_tot, &c->ftr_tot, &c->ftl_base,
                       &c->ftr_base, &c->fTL, &c->fTLe, &c->fTR, &c->fTRe, &c->ftl_ci,
                       &c->ftl_list, &c->ftr_list, &c->ftl_cnt, &c->frbl, &c->frbr, &c->frbl_base,
@@ -1020,12 +1017,10 @@ extern "C" int nqs_local_energy(nqs_ctx* c, const uint64_t* samples, const doubl
     {
         StageScope sc(c, NQS_STAGE_ENV);
         LAUNCH(NQS_STAGE_ENV, launch_validate(ds, Ns, c->K, c->na, c->nb, (DevError*)c->derr.p, c->stream));
-        TRY(env_pass(c, ds, Ns, false, !shared));
-        if (!shared) {
-            k_check_psi<<<(unsigned)((Ns + 255) / 256), 256, 0, c->stream>>>((const double*)c->pmant.p, Ns,
-                                                                           (DevError*)c->derr.p);
-            LAUNCH(NQS_STAGE_ENV, 1);
-        }
+        TRY(env_pass(c, ds, Ns, false, shared ? 2 : 1));
+        k_check_psi<<<(unsigned)((Ns + 255) / 256), 256, 0, c->stream>>>((const double*)c->pmant.p, Ns,
+                                                                       (DevError*)c->derr.p);
+        LAUNCH(NQS_STAGE_ENV, 1);
     }
     int64_t total = 0;
     TRY(count_pass(c, ds, Ns, eb, &total));

@@ -371,7 +371,6 @@ __global__ void k_fam_sweep(FamArgs<T> f)
                 __syncthreads();
             }
         }
-        if (side == 0 && threadIdx.x == 0) { f.pm[b] = (double)Lv[0]; f.pe[b] = eL; }
         __syncthreads();
     }
     batch_fini(f, sm);

@@ -27,7 +27,7 @@ struct FamArgs {
     // per batch sample b (= s - s0)
     T* G; int* Ge;            // [b][3][K][K][D]: G_{s,a}(t) at ((a*K+s)*K+t), t >= s
     T* H; int* He;            // [b][3][K][K][D]: H_{s,a}(t) at ((a*K+s)*K+t), t <= s
-    double* pm; int* pe;      // psi_TN(n) = pm 2^pe
+    const double* pm; const int* pe;   // psi_TN(n) = pm 2^pe (FP64, batch-relative)
     int* tl_end;              // [b][K*K*9] last site a TL cluster is needed at (-1: unused)
     int* tl_idx;              // [b][K*K*9] entry offset of the cluster in the packed TL table
     int* tl_ci;               // [b][K*K*9] cluster index of a TL key

@@ -85,10 +85,11 @@ __global__ void k_env_fp64(EnvArgs a)
     if (!a.tn) {
         // tensor-network part done elsewhere
     } else if (a.an.chain) {
-        double* Ls = a.Lenv + (size_t)s * (K + 1) * D;
-        int* Le = a.Lexp + (size_t)s * (K + 1);
-        for (int i = threadIdx.x; i < D; i += blockDim.x) { x[i] = i == 0 ? 1.0 : 0.0; Ls[i] = x[i]; }
-        if (threadIdx.x == 0) Le[0] = 0;
+        const bool keep = a.tn == 1;    // store the environments
+        double* Ls = keep ? a.Lenv + (size_t)s * (K + 1) * D : nullptr;
+        int* Le = keep ? a.Lexp + (size_t)s * (K + 1) : nullptr;
+        for (int i = threadIdx.x; i < D; i += blockDim.x) { x[i] = i == 0 ? 1.0 : 0.0; if (keep) Ls[i] = x[i]; }
+        if (keep && threadIdx.x == 0) Le[0] = 0;
         int ex = 0;
         __syncthreads();
         for (int t = 0; t < K; ++t) {
@@ -100,30 +101,35 @@ __global__ void k_env_fp64(EnvArgs a)
             }
             __syncthreads();
             ex += block_renorm(y, D, sh);
-            for (int i = threadIdx.x; i < D; i += blockDim.x) { x[i] = y[i]; Ls[(size_t)(t + 1) * D + i] = y[i]; }
-            if (threadIdx.x == 0) Le[t + 1] = ex;
+            for (int i = threadIdx.x; i < D; i += blockDim.x) {
+                x[i] = y[i];
+                if (keep) Ls[(size_t)(t + 1) * D + i] = y[i];
+            }
+            if (keep && threadIdx.x == 0) Le[t + 1] = ex;
             __syncthreads();
         }
         if (threadIdx.x == 0) { a.psi_mant[s] = x[0]; a.psi_exp[s] = ex; }
         __syncthreads();
-        double* Rs = a.Renv + (size_t)s * (K + 1) * D;
-        int* Re = a.Rexp + (size_t)s * (K + 1);
-        for (int i = threadIdx.x; i < D; i += blockDim.x) { x[i] = i == 0 ? 1.0 : 0.0; Rs[(size_t)K * D + i] = x[i]; }
-        if (threadIdx.x == 0) Re[K] = 0;
-        ex = 0;
-        __syncthreads();
-        for (int t = K - 1; t >= 0; --t) {
-            const double* A = tens(a.an.A, t, sigma_at(na, nb, t), D);
-            for (int c = threadIdx.x; c < D; c += blockDim.x) {
-                double acc = 0.0;
-                for (int r = 0; r < D; ++r) acc = fma(x[r], __ldg(A + r * D + c), acc);
-                y[c] = acc;
+        if (keep) {
+            double* Rs = a.Renv + (size_t)s * (K + 1) * D;
+            int* Re = a.Rexp + (size_t)s * (K + 1);
+            for (int i = threadIdx.x; i < D; i += blockDim.x) { x[i] = i == 0 ? 1.0 : 0.0; Rs[(size_t)K * D + i] = x[i]; }
+            if (threadIdx.x == 0) Re[K] = 0;
+            ex = 0;
+            __syncthreads();
+            for (int t = K - 1; t >= 0; --t) {
+                const double* A = tens(a.an.A, t, sigma_at(na, nb, t), D);
+                for (int c = threadIdx.x; c < D; c += blockDim.x) {
+                    double acc = 0.0;
+                    for (int r = 0; r < D; ++r) acc = fma(x[r], __ldg(A + r * D + c), acc);
+                    y[c] = acc;
+                }
+                __syncthreads();
+                ex += block_renorm(y, D, sh);
+                for (int i = threadIdx.x; i < D; i += blockDim.x) { x[i] = y[i]; Rs[(size_t)t * D + i] = y[i]; }
+                if (threadIdx.x == 0) Re[t] = ex;
+                __syncthreads();
             }
-            __syncthreads();
-            ex += block_renorm(y, D, sh);
-            for (int i = threadIdx.x; i < D; i += blockDim.x) { x[i] = y[i]; Rs[(size_t)t * D + i] = y[i]; }
-            if (threadIdx.x == 0) Re[t] = ex;
-            __syncthreads();
         }
     } else {
         double* Hs = a.Hst + (size_t)s * K * D;

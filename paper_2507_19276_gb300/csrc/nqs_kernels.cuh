@@ -120,7 +120,8 @@ struct EnvArgs {
     double* log_f;                       // [Ns]
     double* psi_mant; int* psi_exp;      // [Ns] psi_TN = mant 2^exp
     double* h_diag;                      // [Ns]
-    int tn;                              // 0: skip the tensor-network part (psi, envs)
+    int tn;                              // 0: skip the tensor-network part; 1: psi(n) and the
+                                         // environments; 2 (chain): psi(n) only
 };
 int launch_env_fp64(const EnvArgs& a, cudaStream_t st);
 

@@ -5,9 +5,15 @@ Bars (from the method's statement of the problem):
     deterministic-set membership: bit-exact;
   * drawn indices of the stochastic part and the total remainder weight W:
     bit-exact;
-  * FP64 local energies: within 1e-12 relative of the oracle, relative to the
-    magnitude of the summed terms |H_nn| + sum |H_nm r_m| (the scale rounding
-    errors of a sum are bounded by; it equals |E_loc| when nothing cancels);
+  * FP64 local energies: |E - E_oracle| <= 1e-12 max(|E|, e_abs) + 2^-52 e_cond.
+    e_abs = |H_nn| + sum |H_nm r_m| is the scale rounding errors of the sums
+    are bounded by (|E_loc| when nothing cancels). e_cond is the oracle's
+    first-order rounding scale of the ratios (the contractions' running-error
+    bound P1, weighted like the terms): near a node of psi, psi(n) itself is
+    ill-conditioned, and two FP64 evaluations in different orders differ by
+    up to ~u e_cond, which no implementation can remove;
+  * mixed (FP32 contractions, FP64 psi(n), ratios and sums): within 1e-6 of
+    max(|E|, e_abs);
   * log|psi|: within 1e-12 absolute; gradients within 1e-10 relative.
 """
 import numpy as np
@@ -35,7 +41,9 @@ def _cases():
         "tiny": W.tiny_system(K=6, na=3, nb=2, D=4, n_hidden=5, seed=3),
         "tiny_graph": W.tiny_system(K=6, na=3, nb=3, D=4, n_hidden=5, seed=4, graph=True),
         "k8": W.small_chain(),
-        "h50": h50.subset([0, 1, 2, 4095]),
+        # 3532: the batch's smallest |psi(n)| (E_loc ~ 1.9e6 Ha, ratios ~ 1e4):
+        # the ratio denominators must not lose accuracy to cancellation
+        "h50": h50.subset([0, 1, 2, 3532, 4095]),
         "fe2s2": fe.subset([0, 8191]),
         "h18": h18.subset([0, 1, 2, 3, 16380, 16381, 16382, 16383]),
     }
@@ -131,7 +139,7 @@ def test_sample_index_base_shifts_the_draw_counter(ctx, cases, problems):
         sub = sys_.subset([0, 1])
         e, _ = ctx.local_energy(sub.samples, None, sys_.eps, 64, 5)
         ref = O.local_energy(P, samples=sub.samples, eps=sys_.eps, n_draws=64, seed=5,
-                             index=[base, base + 1])
+                             index=[base, base + 1], cond=True)
         assert _rel_sum(e, ref) < RTOL_FP64
         with pytest.raises(nqs.NQSError):
             ctx.set_precision(nqs.NQS_PREC_FP64, sample_index_base=-1)
@@ -147,8 +155,18 @@ def _rel(a, b):
     return np.max(np.abs(a - b) / np.maximum(1e-300, np.abs(b)))
 
 
+U64 = 2.0 ** -52    # unit roundoff of FP64, both sides
+
+
 def _rel_sum(e, ref):
-    """Error of E_loc relative to the magnitude of its summed terms."""
+    """Error of E_loc over max(|E|, e_abs) + (U64 / RTOL_FP64) e_cond, so that
+    `_rel_sum(e, ref) < RTOL_FP64` is the FP64 bar."""
+    scale = np.maximum(np.abs(ref["e_loc"]), ref["e_abs"]) + (U64 / RTOL_FP64) * ref["e_cond"]
+    return np.max(np.abs(e - ref["e_loc"]) / scale)
+
+
+def _rel_abs(e, ref):
+    """Error relative to the summed-term magnitude only (reported)."""
     return np.max(np.abs(e - ref["e_loc"]) / np.maximum(np.abs(ref["e_loc"]), ref["e_abs"]))
 
 
@@ -157,7 +175,7 @@ def test_local_energy_fp64_matches_oracle(ctx, cases, problems, name):
     sys_, P = cases[name], problems[name]
     _load(ctx, sys_)
     e, summ = ctx.local_energy(sys_.samples, sys_.counts, sys_.eps, sys_.n_draws, sys_.seed)
-    ref = O.local_energy(P)
+    ref = O.local_energy(P, cond=True)
     assert _rel_sum(e, ref) < RTOL_FP64
     ebar = np.sum(sys_.counts * ref["e_loc"]) / np.sum(sys_.counts)
     assert abs(summ["e_mean"] - ebar) < RTOL_FP64 * abs(ebar)
@@ -176,13 +194,13 @@ def test_local_energy_shared_prefix_fp64_matches_oracle(ctx, cases, problems, na
     sys_, P = cases[name], problems[name]
     _load(ctx, sys_, nqs.NQS_PREC_FP64_SHARED)
     e, summ = ctx.local_energy(sys_.samples, sys_.counts, sys_.eps, sys_.n_draws, sys_.seed)
-    ref = O.local_energy(P)
+    ref = O.local_energy(P, cond=True)
     assert _rel_sum(e, ref) < RTOL_FP64
     assert summ["n_det"] == int(np.sum(ref["n_det"]))
 
 
 # FP32 contractions: tolerance stated against the summed-term magnitude
-RTOL_MIXED = 2e-5
+RTOL_MIXED = 1e-6
 
 
 @pytest.mark.parametrize("name", ["tiny", "k8", "h50", "fe2s2"])
@@ -191,8 +209,8 @@ def test_local_energy_mixed_matches_oracle(ctx, cases, problems, name):
     _load(ctx, sys_, nqs.NQS_PREC_MIXED)
     e, summ = ctx.local_energy(sys_.samples, sys_.counts, sys_.eps, sys_.n_draws, sys_.seed)
     ref = O.local_energy(P)
-    err = _rel_sum(e, ref)
-    print(f"{name}: mixed max error / summed magnitude = {err:.3e}")
+    err = _rel_abs(e, ref)
+    print(f"{name}: mixed max error / max(|E|, e_abs) = {err:.3e}")
     assert err < RTOL_MIXED
     assert summ["n_det"] == int(np.sum(ref["n_det"]))
 
@@ -200,16 +218,16 @@ def test_local_energy_mixed_matches_oracle(ctx, cases, problems, name):
 def test_local_energy_stochastic_edge_cases(ctx, cases, problems):
     sys_, P = cases["tiny"], problems["tiny"]
     _load(ctx, sys_)
-    exact = O.local_energy(P, eps=0.0, n_draws=0)
+    exact = O.local_energy(P, eps=0.0, n_draws=0, cond=True)
     # eps = 0 with draws: empty remainder, E^s = 0
     e, s = ctx.local_energy(sys_.samples, None, 0.0, 64, 5)
     assert _rel_sum(e, exact) < RTOL_FP64 and s["n_draw_unique"] == 0
     # eps above every |H|: everything is drawn
-    ref = O.local_energy(P, eps=1e3, n_draws=200, seed=9)
+    ref = O.local_energy(P, eps=1e3, n_draws=200, seed=9, cond=True)
     e, s = ctx.local_energy(sys_.samples, None, 1e3, 200, 9)
     assert s["n_det"] == 0 and _rel_sum(e, ref) < RTOL_FP64
     # no draws: deterministic part only
-    ref = O.local_energy(P, eps=0.05, n_draws=0)
+    ref = O.local_energy(P, eps=0.05, n_draws=0, cond=True)
     e, _ = ctx.local_energy(sys_.samples, None, 0.05, 0, 9)
     assert _rel_sum(e, ref) < RTOL_FP64
     # empty batch
@@ -241,7 +259,7 @@ def test_degenerate_systems(ctx):
         P = O.Problem(sys_)
         _load(ctx, sys_)
         e, s = ctx.local_energy(sys_.samples, None, 0.0, 8, 1)
-        ref = O.local_energy(P, eps=0.0, n_draws=8, seed=1)
+        ref = O.local_energy(P, eps=0.0, n_draws=8, seed=1, cond=True)
         assert _rel_sum(e, ref) < RTOL_FP64
         assert s["n_conn"] == O.n_conn(K, na, nb)
 

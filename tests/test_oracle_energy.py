@@ -132,6 +132,70 @@ def test_chain_as_graph_is_bitwise_equal():
         assert O.log_psi(P, det) == O.log_psi(Pg, det)
 
 
+def p1_paths(sys_, det):
+    """First-order rounding bound by plain recursion over the DAG (no scaling):
+    h(j) = sum of paths from the boundary to j, g(i) = d psi / d h_i = sum of
+    transposed paths from the readout back to i, then
+    P1 = sum over edges e = (j -> i) of |g(i)|^T |M_e| |h(j)|."""
+    K, D = sys_.K, sys_.D
+    sg = sigmas(det, K)
+    if sys_.pred_ptr is None:
+        edges = [(i - 1, i, i) for i in range(K)]
+    else:
+        edges = [(int(sys_.pred_idx[e]), i, e) for i in range(K)
+                 for e in range(sys_.pred_ptr[i], sys_.pred_ptr[i + 1])]
+    e0 = np.zeros(D); e0[0] = 1.0
+
+    def h(j):
+        if j < 0:
+            return e0
+        return sum(sys_.tensors[e, sg[i]] @ h(jj) for jj, i, e in edges if i == j)
+
+    def g(i):
+        if i == K - 1:
+            return e0
+        return sum(sys_.tensors[e, sg[k]].T @ g(k) for j, k, e in edges if j == i)
+
+    return sum(np.abs(g(i)) @ np.abs(sys_.tensors[e, sg[i]]) @ np.abs(h(j)) for j, i, e in edges)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_first_order_bound_is_the_path_recursion(graph):
+    sys_ = W.tiny_system(K=6, na=3, nb=2, D=4, seed=9, graph=graph)
+    P = O.Problem(sys_)
+    for det in sys_.samples[::11]:
+        ref = p1_paths(sys_, det)
+        assert abs(O.log_psi_p1(P, det) - np.log(ref)) < 1e-12
+        la, _, lf = O.log_psi(P, det)
+        assert O.log_psi_p1(P, det) >= (la - lf) - 1e-12
+
+
+def test_first_order_bound_closed_form_for_nonnegative_chain():
+    """No cancellation: every edge term equals psi, so P1 = K psi_TN."""
+    sys_ = W.small_chain()
+    pos = W.System(**{**sys_.__dict__})
+    pos.tensors = np.abs(sys_.tensors)
+    P = O.Problem(pos)
+    for det in sys_.samples[:16]:
+        la, s, lf = O.log_psi(P, det)
+        assert s == 1
+        assert abs(O.log_psi_p1(P, det) - (la - lf + np.log(sys_.K))) < 1e-12
+
+
+def test_condition_scale_closed_form_for_nonnegative_tensors():
+    """With nonnegative tensors kappa_n = K and P1(m) = K psi_TN(m), so each
+    term contributes 2K |a_m r_m|: e_cond = 2K (e_abs - |H_nn|)."""
+    sys_ = W.tiny_system(K=6, na=3, nb=3, D=4, n_hidden=5, seed=12, eps=0.02, n_draws=50)
+    pos = W.System(**{**sys_.__dict__})
+    pos.tensors = np.abs(sys_.tensors)
+    out = O.local_energy(O.Problem(pos), cond=True)
+    hd = np.abs(out["h_diag"])
+    assert np.allclose(out["e_cond"], 2 * sys_.K * (out["e_abs"] - hd), rtol=1e-12, atol=0)
+    signed = O.local_energy(O.Problem(sys_), cond=True)
+    assert np.all(signed["e_cond"] >= 2 * (signed["e_abs"] - np.abs(signed["h_diag"])) * (1 - 1e-14))
+    assert np.all(O.local_energy(O.Problem(sys_))["e_cond"] == 0.0)
+
+
 def test_rbm_param_count_matches_paper():
     """Sec. 4.1: cos-RBM(alpha=2) adds 20200 parameters to the H50 ansatz,
     i.e. N_h*N_v + N_h with N_v = 2K spin orbitals and N_h = alpha*N_v."""
