@@ -740,13 +740,26 @@ __device__ __forceinline__ void two_sum(T a, T b, T& s, T& e)
     e = (a - (s - z)) + (b - z);
 }
 
+// x 2^e, exact: an exponent-field add while the result stays a normal number
+// (integer ALU work instead of the thin FP64 pipe), ldexp otherwise
+__device__ __forceinline__ double scale_pow2(double x, int e)
+{
+    const long long bits = __double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    const int ne = ex + e;
+    if (ex != 0 && ex != 0x7FF && ne > 0 && ne < 0x7FF)
+        return __longlong_as_double(bits + ((long long)e << 52));
+    return ldexp(x, e);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows, double* partial,
                                                        int64_t* span)
 {
     __shared__ OrbLists lists;
-    __shared__ double contrib[kFamRows];
-    __shared__ int spsum[kFamRows];
+    __shared__ double wsum[kFamRows / 32];
+    __shared__ long long wspan[kFamRows / 32];
+    __shared__ double s_inv_pm;
     const int64_t* cb = rows.chunk_base;
     const int64_t blk = cb[f.s0] + blockIdx.x;
     if (blk >= cb[f.s1]) return;
@@ -766,6 +779,7 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
     const int NH = f.n_hidden, NP = nh_pad(NH);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (warp == 0) build_lists_warp(na, nb, f.h.K, lists, lane);
+    if (threadIdx.x == 32) s_inv_pm = 1.0 / f.pm[b];
     __syncthreads();
     const size_t nk = (size_t)K * K * 9;
     // ---- per-lane decode of one row
@@ -818,13 +832,13 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
             rs = f.rbr + (size_t)(f.rbr_base[b] + robj) * (2 * NP);
         }
     }
-    const double inv_pm = 1.0 / f.pm[b];
+    const double inv_pm = s_inv_pm;
     const int pe = f.pe[b];
     // ---- evaluation: 8 lanes per row, 4 rows of the warp at a time
     const int wbase = warp * 32;
     const int wrows = nr - wbase < 32 ? (nr - wbase > 0 ? nr - wbase : 0) : 32;
     const int g = lane >> 3, sub = lane & 7;
-    double myval = 0.0;
+    double acc = 0.0;                               // this lane's rows (sub == 0 only)
     for (int q0 = 0; q0 < wrows; q0 += 4) {
         const int q = q0 + g;                       // the row this lane group evaluates
         const int qs = q < 32 ? q : 31;
@@ -872,7 +886,7 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
             sum = t;
             comp += co + e;
         }
-        double ratio = (double)sum + (double)comp;
+        T ratio = sum + comp;
         if (NH > 0) {
             typedef typename Vec4<T>::type V4;
             T X = T(0);                            // product of (1 + x_k) minus 1
@@ -893,24 +907,25 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
                 const T Y = __shfl_xor_sync(kFull, X, o);
                 X = fma(X, Y, X + Y);
             }
-            if (live) ratio *= (1.0 + (double)ltq[NP]) * (1.0 + (double)X);
+            if (live) ratio *= (T(1) + ltq[NP]) * (T(1) + X);
         }
-        const double val = live ? cq * ldexp(ratio * inv_pm, exq - pe) : 0.0;
-        // hand the value to the lane that decoded the row
-        for (int gg = 0; gg < 4; ++gg) {
-            const double v = __shfl_sync(kFull, val, gg * 8);
-            if (lane == q0 + gg) myval = v;
-        }
+        // the FP64 epilogue once per row: H_nm (or the draw weight) / psi(n) and
+        // the power of two of the row's scaled vectors
+        if (live && sub == 0) acc += scale_pow2(cq * ((double)ratio * inv_pm), exq - pe);
     }
-    contrib[threadIdx.x] = myval;
-    spsum[threadIdx.x] = nmv;
+    long long sp = nmv;
+    for (int o = 16; o; o >>= 1) {
+        acc += __shfl_xor_sync(kFull, acc, o);
+        sp += __shfl_xor_sync(kFull, sp, o);
+    }
+    if (lane == 0) { wsum[warp] = acc; wspan[warp] = sp; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double acc = 0.0;
-        int64_t sp = 0;
-        for (int r = 0; r < nr; ++r) { acc += contrib[r]; sp += spsum[r]; }
-        partial[blk] = acc;
-        if (span) span[blk] = sp;
+        double t = 0.0;
+        long long st = 0;
+        for (int w = 0; w < kFamRows / 32; ++w) { t += wsum[w]; st += wspan[w]; }
+        partial[blk] = t;
+        if (span) span[blk] = st;
     }
 }
 

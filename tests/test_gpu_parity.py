@@ -177,14 +177,20 @@ def test_local_energy_fp64_matches_oracle(ctx, cases, problems, name):
     e, summ = ctx.local_energy(sys_.samples, sys_.counts, sys_.eps, sys_.n_draws, sys_.seed)
     ref = O.local_energy(P, cond=True)
     assert _rel_sum(e, ref) < RTOL_FP64
-    ebar = np.sum(sys_.counts * ref["e_loc"]) / np.sum(sys_.counts)
-    assert abs(summ["e_mean"] - ebar) < RTOL_FP64 * abs(ebar)
+    c = sys_.counts
+    # the weighted energy: against the library's own E_loc to summation
+    # rounding, and against the oracle within the count-weighted per-sample bar
+    bar = RTOL_FP64 * np.maximum(np.abs(ref["e_loc"]), ref["e_abs"]) + U64 * ref["e_cond"]
+    assert abs(summ["e_mean"] - np.sum(c * e) / np.sum(c)) <= 1e-13 * np.sum(c * np.abs(e)) / np.sum(c)
+    ebar = np.sum(c * ref["e_loc"]) / np.sum(c)
+    assert abs(summ["e_mean"] - ebar) <= np.sum(c * bar) / np.sum(c)
     assert summ["n_det"] == int(np.sum(ref["n_det"]))
     assert summ["n_conn"] == O.n_conn(sys_.K, sys_.n_alpha, sys_.n_beta)
-    eb, Bs, m, et = O.summary(ref, sys_.counts)
+    eb, Bs, m, et = O.summary(ref, c)
     assert abs(summ["log_B"] - (m + np.log(Bs))) < 1e-10
-    etm = np.sum(sys_.counts * et) / np.sum(sys_.counts)
-    assert abs(summ["e_tilde_mean"] - etm) < 1e-10 * abs(etm)
+    etm = np.sum(c * et) / np.sum(c)
+    w = np.exp(2 * ref["log_f"] - m) / Bs          # f^2 / B per sample
+    assert abs(summ["e_tilde_mean"] - etm) <= 1e-10 * abs(etm) + np.sum(c * w * bar) / np.sum(c)
 
 
 @pytest.mark.parametrize("name", ["tiny", "k8", "h50", "fe2s2"])
