@@ -52,7 +52,8 @@ FP64_PEAK_TFLOPS = 1.196
 # evaluated. None until taken for the current kernels.
 STAGE_TRAFFIC_PER_AMP = {"mixed": None, "fp64_shared": None}
 
-DTYPES = {"mixed": "f16x3 tensor-core products (f32 accumulate) + f32 gathers; f64 H, ratios, sums",
+DTYPES = {"mixed": "f16x3 tensor-core products (f32 accumulate) + f32 gathers; f64 H, psi(n), "
+                   "ratios, sums; heaviest samples re-evaluated in f64 to the energy tolerance",
           "fp64_shared": "f64", "fp64": "f64"}
 
 
@@ -149,13 +150,14 @@ def cpu_oracle_rate(sys_, n_samples, threads):
     return n_samples / dt, dt
 
 
-def workload_config(sys_, precision, ws=1):
+def workload_config(sys_, precision, ws=1, energy_tol=0.0):
     return {"workload": f"h50_chain K={sys_.K} {sys_.n_alpha}a+{sys_.n_beta}b D={sys_.D} "
                         f"N_h={sys_.n_hidden} Ns={len(sys_.samples)} per GPU eps={sys_.eps:g} "
                         f"N_eps={sys_.n_draws}",
             "K": sys_.K, "D": sys_.D, "n_hidden": sys_.n_hidden,
             "samples_per_gpu": len(sys_.samples), "global_batch": ws * len(sys_.samples),
             "eps": sys_.eps, "n_draws": sys_.n_draws, "precision": precision,
+            "energy_tolerance_ha": energy_tol,
             "l2": "working set > L2 (deterministic lists ~2.5 GB per step)"}
 
 
@@ -200,7 +202,8 @@ def run(args):
     ctx.set_system(sys_)
     prec = {"mixed": nqs.NQS_PREC_MIXED, "fp64": nqs.NQS_PREC_FP64,
             "fp64_shared": nqs.NQS_PREC_FP64_SHARED}[args.precision]
-    ctx.set_precision(prec, timing=True, sample_index_base=lo)
+    tol = args.energy_tol if prec == nqs.NQS_PREC_MIXED else 0.0
+    ctx.set_precision(prec, timing=True, sample_index_base=lo, energy_tolerance=tol)
 
     samples = torch.from_numpy(sys_.samples.view(np.int64)).to(dev)
     counts = torch.from_numpy(sys_.counts).to(dev)
@@ -295,7 +298,7 @@ def run(args):
     fp64 = None
     if not args.no_fp64_compare and prec == nqs.NQS_PREC_MIXED:
         e_mixed = e_loc.clone()
-        ctx.set_precision(nqs.NQS_PREC_FP64_SHARED, timing=False)
+        ctx.set_precision(nqs.NQS_PREC_FP64_SHARED, timing=False, sample_index_base=lo)
         s64 = nqs.EnergySummary()
         step(s64)
         torch.cuda.synchronize()
@@ -315,7 +318,7 @@ def run(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[args.precision],
-            "data": "synthetic", "config": workload_config(sys_, args.precision, ws),
+            "data": "synthetic", "config": workload_config(sys_, args.precision, ws, tol),
             "connected_dets_per_s": value * work["n_conn"],
             "amplitudes_per_s": ws * n_amp * args.steps / (ms / 1e3),
             "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
@@ -326,7 +329,8 @@ def run(args):
             "clocks": clk,
             "gpu_launches": int(sum(v[1] for v in stages.values())),
             "summary": {"e_mean": work["e_mean"], "n_det": work["n_det"],
-                        "n_draw_unique": work["n_draw_unique"]}}
+                        "n_draw_unique": work["n_draw_unique"], "n_refined": work["n_refined"],
+                        "e_error_bound_ha": work["e_error_bound"]}}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         n_cpu = max(2, min(cores, 16))
@@ -348,6 +352,9 @@ def main():
     ap.add_argument("--samples", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--energy-tol", type=float, default=1e-6,
+                    help="mixed form: bound (Ha) on the weighted-energy error, met by "
+                         "re-evaluating the heaviest samples in FP64 (0: none)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

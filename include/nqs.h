@@ -81,7 +81,19 @@ typedef struct {
                              call draws with Philox counter (d, base + s), so
                              the draws do not depend on the split (default 0;
                              must be >= 0) */
-    int reserved[12];     /* must be zero */
+    double energy_tolerance;    /* mixed form, chain ansatz: bound (Ha) on the
+                             error of the weighted energy sum c E_loc / sum c
+                             that nqs_local_energy guarantees by re-evaluating
+                             samples in the FP64 shared-prefix form. After the
+                             mixed pass, samples are taken in decreasing order
+                             of c_n e_abs_n (e_abs = |H_nn| + sum |terms|) until
+                             1e-6 * sum over the others of c_n e_abs_n / sum c
+                             <= energy_tolerance (1e-6: the per-sample error of
+                             the mixed form relative to e_abs that the parity
+                             tests hold it to); their E_loc are replaced by the
+                             FP64 values. 0 (default): no re-evaluation.
+                             Ignored by the FP64 forms. Must be finite, >= 0 */
+    int reserved[10];     /* must be zero */
 } nqs_options;
 
 /* Stages of the local-energy path, as reported by nqs_stage_times. */
@@ -115,7 +127,12 @@ typedef struct {
     int64_t matvecs;        /* D x D matrix-vector products this call performed
                                (equals span_sites, x in-degree for graphs, in the
                                plain form; family sweeps plus two-change clusters in
-                               the shared-prefix form) */
+                               the shared-prefix form; of the pass over the whole
+                               batch) */
+    int64_t n_refined;      /* samples re-evaluated in FP64 (energy_tolerance) */
+    double e_error_bound;   /* with energy_tolerance > 0 in the mixed form: the
+                               bound 1e-6 * sum c_n e_abs_n / sum c over the samples
+                               left in the mixed form (<= energy_tolerance); else 0 */
 } nqs_energy_summary;
 
 /* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t

@@ -61,6 +61,9 @@ struct nqs_ctx {
     // stage accounting (nqs_stage_times)
     int timing = 0;
     int64_t index_base = 0;    // Philox sample counter of samples[0]
+    double energy_tol = 0.0;   // mixed form: re-evaluate heavy samples in FP64 to this bound
+    DevBuf part_det_abs, part_draw_abs, eabs, logf_save, summary2, ref_idx, ref_s, ref_c, ref_pos,
+        ref_e;
     double stage_ms[NQS_N_STAGES] = {0};
     int64_t stage_launch[NQS_N_STAGES] = {0};
     struct Pending { int stage; cudaEvent_t a, b; };
@@ -376,7 +379,8 @@ int amp_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, RowSet rows, int64
 // Shared-prefix amplitudes of the deterministic and drawn rows (chain ansatz),
 // samples processed in batches whose tables fit the memory budget.
 template <typename T>
-int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, int n_draws)
+int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, int n_draws,
+                bool want_abs)
 {
     const int K = c->K, D = c->av.D;
     const size_t nk = (size_t)K * K * 9;
@@ -387,12 +391,14 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
     const int64_t max_det_chunks = total_det / kRows + Ns;
     TRY(ensure(c, c->part_det, (size_t)(max_det_chunks + 1) * 8));
     TRY(ensure(c, c->span_det, (size_t)(max_det_chunks + 1) * 8));
+    if (want_abs) TRY(ensure(c, c->part_det_abs, (size_t)(max_det_chunks + 1) * 8));
     LAUNCH(NQS_STAGE_AMP_DET, launch_chunk_base((const int64_t*)c->det_tot.p, kRows, (int64_t*)c->base_det.p, Ns, c->stream));
     const int64_t per_draw = n_draws > 0 ? (n_draws + kRows - 1) / kRows : 0;
     if (n_draws > 0) {
         TRY(ensure(c, c->base_draw, (size_t)(Ns + 1) * 8));
         TRY(ensure(c, c->part_draw, (size_t)(Ns * per_draw + 1) * 8));
         TRY(ensure(c, c->span_draw, (size_t)(Ns * per_draw + 1) * 8));
+        if (want_abs) TRY(ensure(c, c->part_draw_abs, (size_t)(Ns * per_draw + 1) * 8));
         LAUNCH(NQS_STAGE_AMP_DET, launch_chunk_base((const int64_t*)c->n_unique.p, kRows, (int64_t*)c->base_draw.p, Ns, c->stream));
     }
     // batch size from a memory budget
@@ -534,12 +540,16 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
         stage_begin(c, NQS_STAGE_AMP_DET);
         const int64_t det_rows = c->det_off_h[s1] - c->det_off_h[s0];
         LAUNCH(NQS_STAGE_AMP_DET, fam_launch_rows<T>(f, rd, det_rows / kRows + nbb, (double*)c->part_det.p,
-                                                     (int64_t*)c->span_det.p, c->stream));
+                                                     (int64_t*)c->span_det.p,
+                                                     want_abs ? (double*)c->part_det_abs.p : nullptr,
+                                                     c->stream));
         stage_end(c, NQS_STAGE_AMP_DET);
         stage_begin(c, NQS_STAGE_AMP_DRAW);
         if (n_draws > 0)
             LAUNCH(NQS_STAGE_AMP_DRAW, fam_launch_rows<T>(f, rs, (int64_t)nbb * per_draw, (double*)c->part_draw.p,
-                                                          (int64_t*)c->span_draw.p, c->stream));
+                                                          (int64_t*)c->span_draw.p,
+                                                          want_abs ? (double*)c->part_draw_abs.p : nullptr,
+                                                          c->stream));
         stage_end(c, NQS_STAGE_AMP_DRAW);
         CK(cudaGetLastError());
     }
@@ -588,7 +598,9 @@ extern "C" int nqs_destroy(nqs_ctx* c)
                       &c->ftl_idx, &c->ftr_idx, &c->ftl_tot, &c->ftr_tot, &c->ftl_base,
                       &c->ftr_base, &c->fTL, &c->fTLe, &c->fTR, &c->fTRe, &c->ftl_ci,
                       &c->ftl_list, &c->ftr_list, &c->ftl_cnt, &c->frbl, &c->frbr, &c->frbl_base,
-                      &c->frbr_base, &c->tc_img, &c->tc_exps};
+                      &c->frbr_base, &c->tc_img, &c->tc_exps, &c->part_det_abs,
+                      &c->part_draw_abs, &c->eabs, &c->logf_save, &c->summary2, &c->ref_idx,
+                      &c->ref_s, &c->ref_c, &c->ref_pos, &c->ref_e};
     for (DevBuf* b : bufs) release(*b);
     for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);
@@ -607,12 +619,15 @@ extern "C" int nqs_set_options(nqs_ctx* c, const nqs_options* o)
     if (o->precision != NQS_PREC_FP64 && o->precision != NQS_PREC_MIXED &&
         o->precision != NQS_PREC_FP64_SHARED)
         return set_err(c, NQS_ERR_INVALID_ARG, "unknown precision %d", o->precision);
-    for (int i = 0; i < 12; ++i)
+    for (int i = 0; i < 10; ++i)
         if (o->reserved[i]) return set_err(c, NQS_ERR_INVALID_ARG, "nqs_options.reserved[%d] != 0", i);
     if (o->sample_index_base < 0)
         return set_err(c, NQS_ERR_INVALID_ARG, "nqs_options.sample_index_base < 0");
+    if (!(o->energy_tolerance >= 0.0) || !std::isfinite(o->energy_tolerance))
+        return set_err(c, NQS_ERR_INVALID_ARG, "nqs_options.energy_tolerance must be finite and >= 0");
     c->precision = o->precision;
     c->index_base = o->sample_index_base;
+    c->energy_tol = o->energy_tolerance;
     c->timing = o->timing ? 1 : 0;
     return NQS_OK;
 }
@@ -907,7 +922,8 @@ namespace {
 
 // Steps shared by nqs_draws and nqs_local_energy: weights, prefix, draws.
 int draw_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, uint64_t eb, int n_draws,
-              uint64_t seed, int64_t* rank_out, bool write_dets, bool need_w)
+              uint64_t seed, int64_t* rank_out, bool write_dets, bool need_w,
+              const int64_t* index = nullptr)
 {
     const uint32_t nch = (uint32_t)((c->n_conn + 31) / 32);
     const bool weights = n_draws > 0 || need_w;
@@ -946,6 +962,7 @@ int draw_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, uint64_t eb, int n_dra
         d.n_draws = n_draws;
         d.seed = seed;
         d.index_base = c->index_base;
+        d.index = index;
         d.out_rank = rank_out;
         LAUNCH(NQS_STAGE_DRAW, launch_draws(d, c->stream));
     }
@@ -990,30 +1007,25 @@ extern "C" int nqs_draws(nqs_ctx* c, const uint64_t* samples, int64_t Ns, double
     return NQS_OK;
 }
 
-extern "C" int nqs_local_energy(nqs_ctx* c, const uint64_t* samples, const double* counts,
-                                int64_t Ns, double eps, int n_draws, uint64_t seed, double* e_loc,
-                                nqs_energy_summary* out)
+namespace {
+
+// Per-sample error of the mixed form relative to max(|E_loc|, e_abs): the
+// bound the parity tests hold it to (measured up to ~2e-7 on the workloads).
+constexpr double kMixedRelError = 1e-6;
+
+// The local-energy pipeline on device-resident samples in precision `prec`:
+// E_loc into de, |H_nn| + sum |terms| into deabs (shared-prefix forms only; may
+// be NULL), the summary into c->summary when want_summary. `dindex` (may be
+// NULL) gives each sample's Philox counter.
+int le_core(nqs_ctx* c, const uint64_t* ds, const double* dc, int64_t Ns, uint64_t eb, int n_draws,
+            uint64_t seed, int prec, const int64_t* dindex, double* de, double* deabs,
+            bool want_summary)
 {
-    if (!c) return NQS_ERR_INVALID_ARG;
-    c->err[0] = 0;
-    cudaSetDevice(c->device);
-    TRY(check_ready(c, true));
-    if (Ns < 0 || (Ns > 0 && (!samples || !e_loc)))
-        return set_err(c, NQS_ERR_INVALID_ARG, "bad samples / e_loc arguments");
-    if (n_draws < 0 || n_draws > 4096)
-        return set_err(c, NQS_ERR_INVALID_ARG, "n_draws = %d outside 0..4096", n_draws);
-    uint64_t eb;
-    TRY(eps_bits(c, eps, &eb));
-    if (out) memset(out, 0, sizeof(*out));
-    if (Ns == 0) return NQS_OK;
-    const uint64_t* ds;
-    const double* dc;
-    TRY(stage_in(c, c->st_samples, samples, (size_t)Ns * 2, &ds));
-    TRY(stage_in(c, c->st_counts, counts, (size_t)Ns, &dc));
     TRY(reset_dev_error(c));
-    const bool shared = c->av.chain && (c->precision == NQS_PREC_MIXED || c->precision == NQS_PREC_FP64_SHARED);
+    const bool shared = c->av.chain && (prec == NQS_PREC_MIXED || prec == NQS_PREC_FP64_SHARED);
     if (shared && c->av.n_hidden > 512)
         return set_err(c, NQS_ERR_UNSUPPORTED, "shared-prefix path supports n_hidden <= 512");
+    if (deabs && !shared) return set_err(c, NQS_ERR_STATE, "e_abs needs a shared-prefix form");
     {
         StageScope sc(c, NQS_STAGE_ENV);
         LAUNCH(NQS_STAGE_ENV, launch_validate(ds, Ns, c->K, c->na, c->nb, (DevError*)c->derr.p, c->stream));
@@ -1037,7 +1049,7 @@ extern "C" int nqs_local_energy(nqs_ctx* c, const uint64_t* samples, const doubl
         TRY(ensure(c, c->draw_coef, (size_t)Ns * n_draws * 8));
         TRY(ensure(c, c->n_unique, (size_t)Ns * 8));
     }
-    TRY(draw_pass(c, ds, Ns, eb, n_draws, seed, (int64_t*)c->draw_rank64.p, true, false));
+    TRY(draw_pass(c, ds, Ns, eb, n_draws, seed, (int64_t*)c->draw_rank64.p, true, false, dindex));
     if (n_draws > 0) {
         StageScope sc(c, NQS_STAGE_DRAW);
         DedupArgs d{};
@@ -1057,29 +1069,26 @@ extern "C" int nqs_local_energy(nqs_ctx* c, const uint64_t* samples, const doubl
         CK(cudaGetLastError());
     }
     if (shared) {
-        if (c->precision == NQS_PREC_MIXED) TRY(family_pass<float>(c, ds, Ns, total, n_draws));
-        else TRY(family_pass<double>(c, ds, Ns, total, n_draws));
+        if (prec == NQS_PREC_MIXED) TRY(family_pass<float>(c, ds, Ns, total, n_draws, deabs != nullptr));
+        else TRY(family_pass<double>(c, ds, Ns, total, n_draws, deabs != nullptr));
     } else {
-    // amplitudes: deterministic rows, then the distinct drawn rows
-    RowSet rd{};
-    rd.rank = (const uint32_t*)c->det_rank.p;
-    rd.coef = (const double*)c->det_coef.p;
-    rd.begin = (const int64_t*)c->det_off.p;
-    TRY(amp_pass(c, ds, Ns, rd, total, (const int64_t*)c->det_tot.p, c->base_det, c->part_det,
-                 c->span_det, -1, NQS_STAGE_AMP_DET));
-    if (n_draws > 0) {
-        RowSet rs{};
-        rs.rank = (const uint32_t*)c->draw_rank.p;
-        rs.coef = (const double*)c->draw_coef.p;
-        rs.begin = nullptr;
-        rs.stride = n_draws;
-        TRY(amp_pass(c, ds, Ns, rs, (int64_t)Ns * n_draws, (const int64_t*)c->n_unique.p,
-                     c->base_draw, c->part_draw, c->span_draw, n_draws, NQS_STAGE_AMP_DRAW));
+        // amplitudes: deterministic rows, then the distinct drawn rows
+        RowSet rd{};
+        rd.rank = (const uint32_t*)c->det_rank.p;
+        rd.coef = (const double*)c->det_coef.p;
+        rd.begin = (const int64_t*)c->det_off.p;
+        TRY(amp_pass(c, ds, Ns, rd, total, (const int64_t*)c->det_tot.p, c->base_det, c->part_det,
+                     c->span_det, -1, NQS_STAGE_AMP_DET));
+        if (n_draws > 0) {
+            RowSet rs{};
+            rs.rank = (const uint32_t*)c->draw_rank.p;
+            rs.coef = (const double*)c->draw_coef.p;
+            rs.begin = nullptr;
+            rs.stride = n_draws;
+            TRY(amp_pass(c, ds, Ns, rs, (int64_t)Ns * n_draws, (const int64_t*)c->n_unique.p,
+                         c->base_draw, c->part_draw, c->span_draw, n_draws, NQS_STAGE_AMP_DRAW));
+        }
     }
-    }
-    double* de;
-    bool he;
-    TRY(stage_out(c, c->st_out0, e_loc, (size_t)Ns, &de, &he));
     TRY(ensure(c, c->summary, 8 * 8));
     FinalArgs f{};
     f.Ns = Ns;
@@ -1095,28 +1104,135 @@ extern "C" int nqs_local_energy(nqs_ctx* c, const uint64_t* samples, const doubl
     f.e_loc = de;
     f.span_det = (const int64_t*)c->span_det.p;
     f.span_draw = n_draws > 0 ? (const int64_t*)c->span_draw.p : nullptr;
-    f.summary = out ? (double*)c->summary.p : nullptr;
+    f.summary = want_summary ? (double*)c->summary.p : nullptr;
+    f.e_abs = deabs;
+    f.part_det_abs = deabs ? (const double*)c->part_det_abs.p : nullptr;
+    f.part_draw_abs = deabs && n_draws > 0 ? (const double*)c->part_draw_abs.p : nullptr;
     {
         StageScope sc(c, NQS_STAGE_FINAL);
         LAUNCH(NQS_STAGE_FINAL, launch_finalize(f, c->stream));
     }
     CK(cudaGetLastError());
-    TRY(copy_back(c, e_loc, de, (size_t)Ns, he));
     if (shared) TRY(read_dev_error(c));
-    if (out) {
-        double sm[8];
-        CK(cudaMemcpyAsync(sm, c->summary.p, sizeof(sm), cudaMemcpyDeviceToHost, c->stream));
+    return NQS_OK;
+}
+
+// Error-budgeted refinement of a mixed-form result (de, with c->eabs): the
+// samples with the largest c_n e_abs_n are re-evaluated in the FP64
+// shared-prefix form until kMixedRelError * sum_{rest} c_n e_abs_n / sum c is
+// within c->energy_tol; the corrected summary goes to c->summary2.
+int refine_pass(nqs_ctx* c, const uint64_t* ds, const double* dc, int64_t Ns, uint64_t eb,
+                int n_draws, uint64_t seed, double* de, int64_t* n_ref, double* bound)
+{
+    std::vector<double> ea((size_t)Ns), cn((size_t)Ns, 1.0);
+    CK(cudaMemcpyAsync(ea.data(), c->eabs.p, (size_t)Ns * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (dc) CK(cudaMemcpyAsync(cn.data(), dc, (size_t)Ns * 8, cudaMemcpyDeviceToHost, c->stream));
+    TRY(ensure(c, c->logf_save, (size_t)Ns * 8));
+    CK(cudaMemcpyAsync(c->logf_save.p, c->logf.p, (size_t)Ns * 8, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    double sc = 0.0;
+    for (int64_t s = 0; s < Ns; ++s) sc += cn[(size_t)s];
+    std::vector<int64_t> order((size_t)Ns);
+    for (int64_t s = 0; s < Ns; ++s) order[(size_t)s] = s;
+    std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+        const double a = cn[(size_t)x] * ea[(size_t)x], b = cn[(size_t)y] * ea[(size_t)y];
+        return a != b ? a > b : x < y;
+    });
+    // suffix bounds: rest[k] = bound when the first k of `order` are re-evaluated
+    std::vector<double> rest((size_t)Ns + 1, 0.0);
+    for (int64_t k = Ns - 1; k >= 0; --k) {
+        const int64_t s = order[(size_t)k];
+        rest[(size_t)k] = rest[(size_t)k + 1] + kMixedRelError * cn[(size_t)s] * ea[(size_t)s] / sc;
+    }
+    int64_t k = 0;
+    while (k < Ns && !(rest[(size_t)k] <= c->energy_tol)) ++k;
+    *n_ref = k;
+    *bound = rest[(size_t)k];
+    if (k > 0) {
+        std::vector<int64_t> pick(order.begin(), order.begin() + k);
+        std::sort(pick.begin(), pick.end());
+        TRY(ensure(c, c->ref_idx, (size_t)k * 8));
+        TRY(ensure(c, c->ref_s, (size_t)k * 16));
+        TRY(ensure(c, c->ref_c, (size_t)k * 8));
+        TRY(ensure(c, c->ref_pos, (size_t)k * 8));
+        TRY(ensure(c, c->ref_e, (size_t)k * 8));
+        CK(cudaMemcpyAsync(c->ref_idx.p, pick.data(), (size_t)k * 8, cudaMemcpyHostToDevice, c->stream));
+        LAUNCH(NQS_STAGE_OTHER, launch_gather_picked((const int64_t*)c->ref_idx.p, k, ds, dc, c->index_base,
+                                                     (uint64_t*)c->ref_s.p, (double*)c->ref_c.p,
+                                                     (int64_t*)c->ref_pos.p, c->stream));
+        TRY(le_core(c, (const uint64_t*)c->ref_s.p, (const double*)c->ref_c.p, k, eb, n_draws, seed,
+                    NQS_PREC_FP64_SHARED, (const int64_t*)c->ref_pos.p, (double*)c->ref_e.p, nullptr,
+                    false));
+        LAUNCH(NQS_STAGE_OTHER, launch_scatter_picked((const int64_t*)c->ref_idx.p, k,
+                                                      (const double*)c->ref_e.p, de, c->stream));
+        // pick is host memory the copy above reads: wait before it goes away
         CK(cudaStreamSynchronize(c->stream));
-        out->e_mean = sm[0];
-        out->sum_counts = sm[1];
-        out->log_B = sm[2];
-        out->e_tilde_mean = sm[3];
+    }
+    TRY(ensure(c, c->summary2, 8 * 8));
+    FinalArgs f{};
+    f.Ns = Ns;
+    f.counts = dc;
+    f.log_f = (const double*)c->logf_save.p;
+    f.e_loc = de;
+    f.summary = (double*)c->summary2.p;
+    LAUNCH(NQS_STAGE_FINAL, launch_summary(f, c->stream));
+    CK(cudaGetLastError());
+    return NQS_OK;
+}
+
+}  // namespace
+
+extern "C" int nqs_local_energy(nqs_ctx* c, const uint64_t* samples, const double* counts,
+                                int64_t Ns, double eps, int n_draws, uint64_t seed, double* e_loc,
+                                nqs_energy_summary* out)
+{
+    if (!c) return NQS_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    cudaSetDevice(c->device);
+    TRY(check_ready(c, true));
+    if (Ns < 0 || (Ns > 0 && (!samples || !e_loc)))
+        return set_err(c, NQS_ERR_INVALID_ARG, "bad samples / e_loc arguments");
+    if (n_draws < 0 || n_draws > 4096)
+        return set_err(c, NQS_ERR_INVALID_ARG, "n_draws = %d outside 0..4096", n_draws);
+    uint64_t eb;
+    TRY(eps_bits(c, eps, &eb));
+    if (out) memset(out, 0, sizeof(*out));
+    if (Ns == 0) return NQS_OK;
+    const uint64_t* ds;
+    const double* dc;
+    TRY(stage_in(c, c->st_samples, samples, (size_t)Ns * 2, &ds));
+    TRY(stage_in(c, c->st_counts, counts, (size_t)Ns, &dc));
+    double* de;
+    bool he;
+    TRY(stage_out(c, c->st_out0, e_loc, (size_t)Ns, &de, &he));
+    const bool refine = c->energy_tol > 0.0 && c->precision == NQS_PREC_MIXED && c->av.chain;
+    if (refine) TRY(ensure(c, c->eabs, (size_t)Ns * 8));
+    TRY(le_core(c, ds, dc, Ns, eb, n_draws, seed, c->precision, nullptr, de,
+                refine ? (double*)c->eabs.p : nullptr, out != nullptr));
+    int64_t n_ref = 0;
+    double bound = 0.0;
+    const int64_t matvecs = c->fam_matvecs;      // of the pass over the whole batch
+    if (refine) TRY(refine_pass(c, ds, dc, Ns, eb, n_draws, seed, de, &n_ref, &bound));
+    TRY(copy_back(c, e_loc, de, (size_t)Ns, he));
+    if (out) {
+        double sm[8], sm2[8];
+        CK(cudaMemcpyAsync(sm, c->summary.p, sizeof(sm), cudaMemcpyDeviceToHost, c->stream));
+        if (refine) CK(cudaMemcpyAsync(sm2, c->summary2.p, sizeof(sm2), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        const bool shared = c->av.chain && c->precision != NQS_PREC_FP64;
+        const double* se = refine ? sm2 : sm;   // energies after re-evaluation
+        out->e_mean = se[0];
+        out->sum_counts = se[1];
+        out->log_B = se[2];
+        out->e_tilde_mean = se[3];
         out->n_conn = c->n_conn;
         out->n_det = (int64_t)llround(sm[4]);
         out->n_draw_unique = (int64_t)llround(sm[5]);
         out->n_amplitudes = out->n_det + out->n_draw_unique;
         out->span_sites = (int64_t)llround(sm[6]);
-        out->matvecs = shared ? c->fam_matvecs : out->span_sites;
+        out->matvecs = shared ? matvecs : out->span_sites;
+        out->n_refined = n_ref;
+        out->e_error_bound = bound;
     } else if (he) {
         CK(cudaStreamSynchronize(c->stream));
     }

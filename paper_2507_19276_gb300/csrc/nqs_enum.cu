@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) k_draws(DrawArgs a)
     build_lists_warp(na, nb, a.h.K, lists[warp], lane);
     __syncwarp();
     // target t = floor(x W / 2^64), then the first chunk whose inclusive prefix > t
-    const uint64_t x = philox_first((uint64_t)d, (uint64_t)(a.index_base + s), a.seed);
+    const uint64_t x = philox_first((uint64_t)d, (uint64_t)(a.index ? a.index[s] : a.index_base + s), a.seed);
     const uint64_t t = __umul64hi(x, W);
     uint32_t c = 0;
     if (lane == 0) {

@@ -754,10 +754,12 @@ __device__ __forceinline__ double scale_pow2(double x, int e)
 
 template <typename T>
 __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows, double* partial,
-                                                       int64_t* span)
+                                                       int64_t* span, double* partial_abs)
 {
     __shared__ OrbLists lists;
+    __shared__ T s_ratio[kFamRows];                  // each row's ratio in the contraction type
     __shared__ double wsum[kFamRows / 32];
+    __shared__ double wabs[kFamRows / 32];
     __shared__ long long wspan[kFamRows / 32];
     __shared__ double s_inv_pm;
     const int64_t* cb = rows.chunk_base;
@@ -838,7 +840,6 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
     const int wbase = warp * 32;
     const int wrows = nr - wbase < 32 ? (nr - wbase > 0 ? nr - wbase : 0) : 32;
     const int g = lane >> 3, sub = lane & 7;
-    double acc = 0.0;                               // this lane's rows (sub == 0 only)
     for (int q0 = 0; q0 < wrows; q0 += 4) {
         const int q = q0 + g;                       // the row this lane group evaluates
         const int qs = q < 32 ? q : 31;
@@ -846,8 +847,6 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
         const T* Rq = (const T*)__shfl_sync(kFull, (unsigned long long)Rv, qs);
         const T* ltq = (const T*)__shfl_sync(kFull, (unsigned long long)lt, qs);
         const T* rsq = (const T*)__shfl_sync(kFull, (unsigned long long)rs, qs);
-        const int exq = __shfl_sync(kFull, ex, qs);
-        const double cq = __shfl_sync(kFull, coef, qs);
         const bool live = q < wrows;
         // dot product with error-free product / sum transformations
         T sum = T(0), comp = T(0);
@@ -909,23 +908,31 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
             }
             if (live) ratio *= (T(1) + ltq[NP]) * (T(1) + X);
         }
-        // the FP64 epilogue once per row: H_nm (or the draw weight) / psi(n) and
-        // the power of two of the row's scaled vectors
-        if (live && sub == 0) acc += scale_pow2(cq * ((double)ratio * inv_pm), exq - pe);
+        if (live && sub == 0) s_ratio[wbase + q] = ratio;
+    }
+    __syncwarp();
+    // the FP64 epilogue once per row, by the lane that decoded it: H_nm (or the
+    // draw weight) / psi(n) and the power of two of the row's scaled vectors
+    double acc = 0.0, aacc = 0.0;
+    if (myrow < nr) {
+        acc = scale_pow2(coef * ((double)s_ratio[myrow] * inv_pm), ex - pe);
+        if (partial_abs) aacc = fabs(acc);
     }
     long long sp = nmv;
     for (int o = 16; o; o >>= 1) {
         acc += __shfl_xor_sync(kFull, acc, o);
         sp += __shfl_xor_sync(kFull, sp, o);
+        if (partial_abs) aacc += __shfl_xor_sync(kFull, aacc, o);
     }
-    if (lane == 0) { wsum[warp] = acc; wspan[warp] = sp; }
+    if (lane == 0) { wsum[warp] = acc; wspan[warp] = sp; wabs[warp] = aacc; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
+        double t = 0.0, ta = 0.0;
         long long st = 0;
-        for (int w = 0; w < kFamRows / 32; ++w) { t += wsum[w]; st += wspan[w]; }
+        for (int w = 0; w < kFamRows / 32; ++w) { t += wsum[w]; st += wspan[w]; ta += wabs[w]; }
         partial[blk] = t;
         if (span) span[blk] = st;
+        if (partial_abs) partial_abs[blk] = ta;
     }
 }
 
@@ -983,10 +990,10 @@ int fam_launch_tables(const FamArgs<T>& f, int nb, cudaStream_t st)
 
 template <typename T>
 int fam_launch_rows(const FamArgs<T>& f, const RowSet& rows, int64_t grid, double* partial,
-                    int64_t* span, cudaStream_t st)
+                    int64_t* span, double* partial_abs, cudaStream_t st)
 {
     if (grid <= 0) return 0;
-    k_fam_rows<T><<<(unsigned)grid, kFamRows, 0, st>>>(f, rows, partial, span);
+    k_fam_rows<T><<<(unsigned)grid, kFamRows, 0, st>>>(f, rows, partial, span, partial_abs);
     return 1;
 }
 
@@ -1027,7 +1034,7 @@ void fam_tc_images(const double* A, int K, int D, std::vector<unsigned char>& im
     template int fam_launch_compact<T>(const FamArgs<T>&, int, cudaStream_t);              \
     template int fam_launch_tables<T>(const FamArgs<T>&, int, cudaStream_t);               \
     template int fam_launch_rows<T>(const FamArgs<T>&, const RowSet&, int64_t, double*,    \
-                                    int64_t*, cudaStream_t);
+                                    int64_t*, double*, cudaStream_t);
 NQS_FAM_INST(float)
 NQS_FAM_INST(double)
 

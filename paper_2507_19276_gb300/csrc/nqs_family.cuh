@@ -51,9 +51,11 @@ template <typename T> int fam_launch_mark(const FamArgs<T>& f, const RowSet& row
 template <typename T> int fam_launch_compact(const FamArgs<T>& f, int nb, cudaStream_t st);
 template <typename T> int fam_launch_tables(const FamArgs<T>& f, int nb, cudaStream_t st);
 // grid = upper bound of the batch's row chunks (128 rows each); blocks map to
-// rows.chunk_base[s0] + blockIdx.x
+// rows.chunk_base[s0] + blockIdx.x. partial_abs (may be NULL) gets each chunk's
+// sum of |term|.
 template <typename T> int fam_launch_rows(const FamArgs<T>& f, const RowSet& rows, int64_t grid,
-                                          double* partial, int64_t* span, cudaStream_t st);
+                                          double* partial, int64_t* span, double* partial_abs,
+                                          cudaStream_t st);
 
 // shared memory of the batch buffers of the table kernels
 inline size_t fam_batch_bytes(int D, int nmax, size_t elem, bool tc)

@@ -183,7 +183,8 @@ __device__ __forceinline__ double matrix_element(const HamView& h, uint64_t na, 
     ma = wa;
     mb = wb;
     odd = c & 1;
-    return odd ? -v : v;
+    // the phase as a sign-bit flip (integer ALU, not the FP64 pipe)
+    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)odd << 63));
 }
 
 // |H| >= eps on the bit patterns (eps finite, >= 0; H not NaN).

@@ -37,6 +37,7 @@ struct DrawArgs {
     int n_draws;
     uint64_t seed;
     int64_t index_base;                  // Philox sample counter of samples[0]
+    const int64_t* index;                // per-sample Philox counters (NULL: index_base + s)
     int64_t* out_rank;                   // [Ns][n_draws]
 };
 int launch_draws(const DrawArgs& a, cudaStream_t st);
@@ -81,7 +82,7 @@ struct FinalArgs {
     const int64_t* base_draw;            // NULL when there are no draws
     const double* counts;                // [Ns] or NULL
     const double* log_f;                 // [Ns]
-    const int64_t* det_off;              // [Ns+1]
+    const int64_t* det_off;              // [Ns+1] (NULL: the summary skips the work counts)
     const int64_t* n_unique;             // [Ns] or NULL
     double* e_loc;                       // [Ns]
     double* e_det;                       // [Ns] (optional)
@@ -89,8 +90,16 @@ struct FinalArgs {
     const int64_t* span_det;             // [chunks] from the amplitude kernels
     const int64_t* span_draw;
     double* summary;                     // [8] e_mean, sum_c, log_B, e_tilde_mean, n_det, n_uniq, span
+    const double* part_det_abs;          // chunk sums of |term| (NULL: no e_abs)
+    const double* part_draw_abs;
+    double* e_abs;                       // [Ns] |H_nn| + sum |terms| (optional)
 };
 int launch_finalize(const FinalArgs& a, cudaStream_t st);
+int launch_summary(const FinalArgs& a, cudaStream_t st);     // the summary alone
+// re-evaluation of picked samples: gather (words, counts, base + position), scatter
+int launch_gather_picked(const int64_t* idx, int64_t n, const uint64_t* samples, const double* counts,
+                         int64_t base, uint64_t* out_s, double* out_c, int64_t* out_pos, cudaStream_t st);
+int launch_scatter_picked(const int64_t* idx, int64_t n, const double* v, double* out, cudaStream_t st);
 
 // ---- FP64 ansatz (nqs_fp64.cu) ---------------------------------------------
 

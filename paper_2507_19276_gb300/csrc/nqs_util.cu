@@ -140,6 +140,13 @@ __global__ void k_final_samples(FinalArgs a)
     if (a.base_draw)
         for (int64_t b = a.base_draw[s]; b < a.base_draw[s + 1]; ++b) es += a.part_draw[b];
     a.e_loc[s] = a.h_diag[s] + ed + es;
+    if (a.e_abs) {
+        double ea = fabs(a.h_diag[s]);
+        for (int64_t b = a.base_det[s]; b < a.base_det[s + 1]; ++b) ea += a.part_det_abs[b];
+        if (a.base_draw && a.part_draw_abs)
+            for (int64_t b = a.base_draw[s]; b < a.base_draw[s + 1]; ++b) ea += a.part_draw_abs[b];
+        a.e_abs[s] = ea;
+    }
     if (a.e_det) a.e_det[s] = ed;
     if (a.e_stoch) a.e_stoch[s] = es;
 }
@@ -180,7 +187,7 @@ __global__ void __launch_bounds__(256) k_summary(FinalArgs a)
         sc += c;
         sce += c * a.e_loc[s];
         scf += c * exp(2.0 * a.log_f[s] - m);
-        ndet += (double)(a.det_off[s + 1] - a.det_off[s]);
+        if (a.det_off) ndet += (double)(a.det_off[s + 1] - a.det_off[s]);
         if (a.n_unique) nu += (double)a.n_unique[s];
     }
     double sp = 0.0;
@@ -212,6 +219,49 @@ __global__ void __launch_bounds__(256) k_summary(FinalArgs a)
         a.summary[5] = nu;
         a.summary[6] = sp;
     }
+}
+
+int launch_summary(const FinalArgs& a, cudaStream_t st)
+{
+    if (a.Ns == 0 || !a.summary) return 0;
+    k_summary<<<1, 256, 0, st>>>(a);
+    return 1;
+}
+
+// samples picked for re-evaluation: their words, counts and global positions
+__global__ void k_gather_picked(const int64_t* idx, int64_t n, const uint64_t* samples,
+                                const double* counts, int64_t base, uint64_t* out_s, double* out_c,
+                                int64_t* out_pos)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int64_t s = idx[j];
+    out_s[2 * j] = samples[2 * s];
+    out_s[2 * j + 1] = samples[2 * s + 1];
+    out_c[j] = counts ? counts[s] : 1.0;
+    out_pos[j] = base + s;
+}
+
+__global__ void k_scatter_picked(const int64_t* idx, int64_t n, const double* v, double* out)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) out[idx[j]] = v[j];
+}
+
+int launch_gather_picked(const int64_t* idx, int64_t n, const uint64_t* samples, const double* counts,
+                         int64_t base, uint64_t* out_s, double* out_c, int64_t* out_pos, cudaStream_t st)
+{
+    if (n == 0) return 0;
+    k_gather_picked<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(idx, n, samples, counts, base, out_s,
+                                                                 out_c, out_pos);
+    return 1;
+}
+
+int launch_scatter_picked(const int64_t* idx, int64_t n, const double* v, double* out, cudaStream_t st)
+{
+    if (n == 0) return 0;
+    k_scatter_picked<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(idx, n, v, out);
+    return 1;
 }
 
 int launch_finalize(const FinalArgs& a, cudaStream_t st)

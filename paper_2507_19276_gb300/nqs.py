@@ -34,7 +34,8 @@ class NQSError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("timing", C.c_int),
-                ("sample_index_base", C.c_int64), ("reserved", C.c_int * 12)]
+                ("sample_index_base", C.c_int64), ("energy_tolerance", C.c_double),
+                ("reserved", C.c_int * 10)]
 
 
 N_STAGES = 9
@@ -45,7 +46,8 @@ class EnergySummary(C.Structure):
     _fields_ = [("e_mean", C.c_double), ("sum_counts", C.c_double), ("log_B", C.c_double),
                 ("e_tilde_mean", C.c_double), ("n_conn", C.c_int64), ("n_det", C.c_int64),
                 ("n_draw_unique", C.c_int64), ("n_amplitudes", C.c_int64),
-                ("span_sites", C.c_int64), ("matvecs", C.c_int64)]
+                ("span_sites", C.c_int64), ("matvecs", C.c_int64), ("n_refined", C.c_int64),
+                ("e_error_bound", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -137,11 +139,13 @@ def nqs_last_error(ctx) -> str:
     return (load().nqs_last_error(ctx) or b"").decode()
 
 
-def nqs_set_options(ctx, precision: int, timing: int = 0, sample_index_base: int = 0):
+def nqs_set_options(ctx, precision: int, timing: int = 0, sample_index_base: int = 0,
+                    energy_tolerance: float = 0.0):
     o = Options()
     o.precision = precision
     o.timing = timing
     o.sample_index_base = sample_index_base
+    o.energy_tolerance = energy_tolerance
     _check(ctx, load().nqs_set_options(ctx, C.byref(o)))
 
 
@@ -221,8 +225,9 @@ class Context:
         except Exception:
             pass
 
-    def set_precision(self, precision: int, timing: bool = False, sample_index_base: int = 0):
-        nqs_set_options(self.h, precision, int(bool(timing)), sample_index_base)
+    def set_precision(self, precision: int, timing: bool = False, sample_index_base: int = 0,
+                      energy_tolerance: float = 0.0):
+        nqs_set_options(self.h, precision, int(bool(timing)), sample_index_base, energy_tolerance)
 
     def stage_times(self):
         """{stage: (device ms, kernel launches)} since the previous call."""

@@ -131,3 +131,35 @@ def test_h18_graph_full_batch_fp64_sampled_against_oracle(ctx):
     err, _ = _check_sampled(sys_, e, idx, RTOL_FP64)
     print(f"h18 full fp64: {dt:.2f} s, sampled max error {err:.3e}")
     assert err < RTOL_FP64
+
+
+def test_h50_energy_tolerance_refinement_meets_the_bound(ctx):
+    """Mixed form with energy_tolerance = 1e-6 Ha: the heaviest samples are
+    re-evaluated in FP64, the weighted energy lands within the tolerance of
+    the FP64 form's, the re-evaluated E_loc are the FP64 ones, and every other
+    sample keeps its mixed value bit for bit."""
+    sys_ = W.h50_chain()
+    e64, s64, _ = _run_full(ctx, sys_, nqs.NQS_PREC_FP64_SHARED)
+    emx, smx, _ = _run_full(ctx, sys_, nqs.NQS_PREC_MIXED)
+    assert smx["n_refined"] == 0 and smx["e_error_bound"] == 0.0
+    ctx.set_precision(nqs.NQS_PREC_MIXED, energy_tolerance=1e-6)
+    try:
+        s = torch.from_numpy(sys_.samples.view(np.int64)).cuda()
+        c = torch.from_numpy(sys_.counts).cuda()
+        out = torch.empty(len(sys_.samples), dtype=torch.float64, device="cuda")
+        _, summ = ctx.local_energy(s, c, sys_.eps, sys_.n_draws, sys_.seed, out=out)
+        e = out.cpu().numpy()
+    finally:
+        ctx.set_precision(nqs.NQS_PREC_FP64)
+    k = summ["n_refined"]
+    print(f"refined {k} of {len(e)}; bound {summ['e_error_bound']:.3e}; "
+          f"|E_bar - E_bar_fp64| mixed {abs(smx['e_mean'] - s64['e_mean']):.3e} "
+          f"refined {abs(summ['e_mean'] - s64['e_mean']):.3e}")
+    assert 0 < k < len(e) and summ["e_error_bound"] <= 1e-6
+    changed = e != emx
+    assert changed.sum() <= k
+    np.testing.assert_allclose(e[changed], e64[changed], rtol=1e-13, atol=0)
+    assert np.array_equal(e[~changed], emx[~changed])
+    # within the tolerance, plus the FP64 form's own rounding of the mean
+    assert abs(summ["e_mean"] - s64["e_mean"]) <= 1e-6 + 1e-12 * abs(s64["e_mean"])
+    assert summ["n_det"] == smx["n_det"] and summ["log_B"] == smx["log_B"]
