@@ -243,6 +243,34 @@ int nqs_local_energy(nqs_ctx* ctx, const uint64_t* samples, const double* counts
                      double det_threshold, int n_draws, uint64_t philox_seed, double* e_loc,
                      nqs_energy_summary* out);
 
+/* One system of a multi-system batch (nqs_local_energy_batch): the arguments
+ * of nqs_local_energy for that system, and its status on return. */
+typedef struct {
+    const uint64_t* samples;     /* [n_samples][2], host or device */
+    const double* counts;        /* [n_samples] or NULL */
+    int64_t n_samples;
+    double det_threshold;        /* eps */
+    int n_draws;                 /* N_eps */
+    uint64_t philox_seed;
+    double* e_loc;               /* [n_samples] out */
+    nqs_energy_summary* summary; /* host struct or NULL */
+    int status;                  /* out: this system's nqs_status */
+} nqs_batch_item;
+
+/* Local energies of independent systems in one call (no counterpart in the
+ * paper, which treats one molecule at a time; the path of each system is the
+ * one of nqs_local_energy, Sec. 2.4). ctxs[i] holds system i's Hamiltonian,
+ * ansatz and options (systems may differ in K, N_alpha, N_beta, D, precision);
+ * the contexts must be distinct. Systems are taken in decreasing order of
+ * estimated cost (n_samples * n_conn * K * D) from a shared queue by
+ * `n_workers` host threads (<= 0: min(n_sys, 8)), each driving its system's
+ * context stream, so the work of several systems overlaps on the GPU.
+ * Returns NQS_OK when every system succeeded, else the status of the first
+ * failing system (by index; nqs_last_error(ctxs[i]) has its message); every
+ * item's `status` is set. Each context's stream is synchronised on return.
+ * Systems overlap only if their contexts run on distinct non-default streams. */
+int nqs_local_energy_batch(nqs_ctx* const* ctxs, int n_sys, nqs_batch_item* items, int n_workers);
+
 /* Vector-Jacobian product of d log|psi(n)| / d theta (Eq. egrad):
  *  grad = sum_n u[n] d log|psi(n)| / d theta, theta = (site tensors, W, b).
  *  grad_sites [n_edges][4][D][D], grad_W [n_hidden][2K], grad_b [n_hidden];

@@ -1403,3 +1403,27 @@ extern "C" int nqs_draws_noalloc(nqs_ctx* c, const uint64_t* samples, int64_t Ns
                        (long long)e.index);
     return NQS_OK;
 }
+
+namespace nqs {
+
+// shape of a context's system (0 where not set yet)
+int ctx_shape(const nqs_ctx* c, int* K, int* na, int* nb, int* D)
+{
+    if (!c) return NQS_ERR_INVALID_ARG;
+    *K = c->K;
+    *na = c->na;
+    *nb = c->nb;
+    *D = c->av.D;
+    return NQS_OK;
+}
+
+int ctx_sync(nqs_ctx* c)
+{
+    if (!c) return NQS_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    const cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return set_err(c, NQS_ERR_CUDA, "%s", cudaGetErrorString(e));
+    return NQS_OK;
+}
+
+}  // namespace nqs

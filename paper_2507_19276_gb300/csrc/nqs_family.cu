@@ -950,7 +950,7 @@ template <typename T>
 int fam_launch_sweep(const FamArgs<T>& f, int nb, cudaStream_t st)
 {
     const size_t smem = stage_smem(f, 4);
-    cudaFuncSetAttribute(k_fam_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem(k_fam_sweep<T>);
     k_fam_sweep<T><<<nb, f.threads, smem, st>>>(f);
     return 1;
 }
@@ -975,8 +975,8 @@ int fam_launch_tables(const FamArgs<T>& f, int nb, cudaStream_t st)
 {
     const size_t smem = stage_smem(f, 3);
     const size_t smem_tl = stage_smem(f, 3) + (size_t)2 * (f.nmax + f.threads) * sizeof(int);
-    cudaFuncSetAttribute(k_fam_tr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_fam_tl<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tl);
+    allow_max_smem(k_fam_tr<T>);
+    allow_max_smem(k_fam_tl<T>);
     k_fam_tr<T><<<nb, f.threads, smem, st>>>(f);
     k_fam_tl<T><<<nb, f.threads, smem_tl, st>>>(f);
     int n = 2;

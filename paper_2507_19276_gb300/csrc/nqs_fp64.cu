@@ -532,10 +532,10 @@ int launch_amp_fp64(const AmpArgs& a, cudaStream_t st)
     if (a.rows.max_chunks == 0) return 0;
     const size_t smem = amp_fp64_smem(a.an, a.rows_per_block);
     if (a.an.chain) {
-        cudaFuncSetAttribute(k_amp_chain_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_smem(k_amp_chain_fp64);
         k_amp_chain_fp64<<<(unsigned)a.rows.max_chunks, 256, smem, st>>>(a);
     } else {
-        cudaFuncSetAttribute(k_amp_graph_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_smem(k_amp_graph_fp64);
         k_amp_graph_fp64<<<(unsigned)a.rows.max_chunks, 256, smem, st>>>(a);
     }
     return 1;
@@ -639,7 +639,7 @@ int launch_full_amp_fp64(const AnsatzView& an, const uint64_t* dets, int64_t n, 
     if (n == 0) return 0;
     int launches = 0;
     const size_t smem = (34 + (an.chain ? 2 * (size_t)an.D : (size_t)an.K * an.D)) * sizeof(double);
-    cudaFuncSetAttribute(k_full_amp_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem(k_full_amp_fp64);
     const int threads = an.D >= 256 ? 256 : (an.D > 64 ? 128 : 64);
     for (int64_t i0 = 0; i0 < n; i0 += (1ll << 30)) {
         const int64_t m = (n - i0) < (1ll << 30) ? (n - i0) : (1ll << 30);

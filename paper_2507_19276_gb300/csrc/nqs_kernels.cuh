@@ -6,6 +6,23 @@
 
 namespace nqs {
 
+// Allow a kernel the largest dynamic shared memory the device permits next
+// to its static shared memory. The attribute is process-wide per function, so
+// setting each launch's exact size would race between host threads launching
+// with different sizes; this value is the same for every caller, and occupancy
+// still follows the size each launch requests.
+template <typename F>
+inline void allow_max_smem(F* kernel)
+{
+    int dev = 0, mx = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, kernel);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes);
+}
+
+
 // ---- enumeration (nqs_enum.cu) ---------------------------------------------
 
 struct EnumArgs {

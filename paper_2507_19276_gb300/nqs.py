@@ -53,6 +53,12 @@ class EnergySummary(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("samples", C.c_void_p), ("counts", C.c_void_p), ("n_samples", C.c_int64),
+                ("det_threshold", C.c_double), ("n_draws", C.c_int), ("philox_seed", C.c_uint64),
+                ("e_loc", C.c_void_p), ("summary", C.POINTER(EnergySummary)), ("status", C.c_int)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -83,6 +89,7 @@ def load():
             "nqs_draws_noalloc": [vp, vp, i64, dbl, C.c_int, u64, vp, vp],
             "nqs_local_energy": [vp, vp, vp, i64, dbl, C.c_int, u64, vp, C.POINTER(EnergySummary)],
             "nqs_grad_log_psi_vjp": [vp, vp, vp, i64, vp, vp, vp],
+            "nqs_local_energy_batch": [C.POINTER(vp), C.c_int, C.POINTER(BatchItem), C.c_int],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -97,7 +104,8 @@ def load():
 def exported_symbols():
     return ["nqs_create", "nqs_destroy", "nqs_last_error", "nqs_set_options", "nqs_stage_times",
             "nqs_set_hamiltonian", "nqs_set_ansatz", "nqs_connected", "nqs_amplitude",
-            "nqs_draws", "nqs_draws_noalloc", "nqs_local_energy", "nqs_grad_log_psi_vjp"]
+            "nqs_draws", "nqs_draws_noalloc", "nqs_local_energy", "nqs_local_energy_batch",
+            "nqs_grad_log_psi_vjp"]
 
 
 def _ptr(x):
@@ -187,6 +195,20 @@ def nqs_local_energy(ctx, samples, counts, Ns, eps, n_draws, seed, e_loc, summar
     _check(ctx, load().nqs_local_energy(ctx, _ptr(samples), _ptr(counts), Ns, float(eps), n_draws,
                                         seed, _ptr(e_loc),
                                         C.byref(summary) if summary is not None else None))
+
+
+def nqs_local_energy_batch(ctxs, items, n_workers=0):
+    """ctxs: context handles; items: a ctypes array of BatchItem (statuses are
+    written back). Raises NQSError naming the first failing system."""
+    n = len(ctxs)
+    arr = (C.c_void_p * n)(*[C.c_void_p(h.value if isinstance(h, C.c_void_p) else h) for h in ctxs])
+    st = load().nqs_local_energy_batch(arr, n, items, n_workers)
+    if st != NQS_OK:
+        bad = [i for i in range(n) if items[i].status != NQS_OK]
+        if not bad:
+            raise NQSError(st, "invalid batch (null or repeated context)")
+        msg = load().nqs_last_error(ctxs[bad[0]])
+        raise NQSError(items[bad[0]].status, f"system {bad[0]}: " + (msg or b"").decode())
 
 
 def nqs_grad_log_psi_vjp(ctx, samples, u, Ns, grad_sites, grad_W, grad_b):
@@ -310,3 +332,38 @@ class Context:
         gb = np.empty(self.n_hidden, np.float64) if self.n_hidden else None
         nqs_grad_log_psi_vjp(self.h, s, uu, len(s), gT, gW, gb)
         return gT, gW, gb
+
+
+def local_energy_batch(contexts, args, n_workers=0):
+    """E_loc of independent systems in one nqs_local_energy_batch call.
+
+    contexts: one Context per system (each on its own stream for overlap);
+    args: per system a dict with samples, counts (or None), eps, n_draws, seed
+    (host arrays or CUDA tensors). Returns [(e_loc, summary dict)]."""
+    n = len(contexts)
+    items = (BatchItem * n)()
+    keep, outs, sums = [], [], []
+    for i, (ctx, a) in enumerate(zip(contexts, args)):
+        smp = a["samples"]
+        if not hasattr(smp, "data_ptr"):
+            smp = _np(smp, np.uint64).reshape(-1, 2)
+        cnt = a.get("counts")
+        if cnt is not None and not hasattr(cnt, "data_ptr"):
+            cnt = _np(cnt, np.float64)
+        ns = int(smp.shape[0])
+        e = np.empty(ns, np.float64)
+        sm = EnergySummary()
+        keep += [smp, cnt]
+        outs.append(e)
+        sums.append(sm)
+        it = items[i]
+        it.samples = _ptr(smp)
+        it.counts = _ptr(cnt)
+        it.n_samples = ns
+        it.det_threshold = float(a.get("eps", 0.0))
+        it.n_draws = int(a.get("n_draws", 0))
+        it.philox_seed = int(a.get("seed", 0))
+        it.e_loc = _ptr(e)
+        it.summary = C.pointer(sm)
+    nqs_local_energy_batch([c.h for c in contexts], items, n_workers)
+    return [(e, sm.as_dict()) for e, sm in zip(outs, sums)]
