@@ -32,6 +32,18 @@ from paper_2507_19276_gb300 import workloads as W  # noqa: E402
 METRIC = "E_loc samples/s (H50 shape)"
 UNIT = "samples/s"
 
+# workload -> (generator(n_samples, seed_offset), default samples per GPU,
+# default precision, metric)
+WORKLOADS = {
+    "h50": (lambda n, o: W.h50_chain(n_samples=n, seed_offset=o), 4096, "mixed", METRIC),
+    "k8": (lambda n, o: W.small_chain(n_samples=n, seed_offset=o), 256, "fp64",
+           "E_loc samples/s (K8 chain, D=8, plain FP64)"),
+    "fe2s2": (lambda n, o: W.fe2s2_dense(n_samples=n, seed_offset=o), 8192, "mixed",
+              "E_loc samples/s (Fe2S2 shape, D=256)"),
+    "h18": (lambda n, o: W.h18_graph(n_samples=n, seed_offset=o), 16384, "fp64",
+            "E_loc samples/s (H18 graph, D=32)"),
+}
+
 
 def _peaks():
     try:
@@ -151,36 +163,51 @@ def cpu_oracle_rate(sys_, n_samples, threads):
 
 
 def workload_config(sys_, precision, ws=1, energy_tol=0.0):
-    return {"workload": f"h50_chain K={sys_.K} {sys_.n_alpha}a+{sys_.n_beta}b D={sys_.D} "
+    kind = "graph" if sys_.pred_ptr is not None else "chain"
+    return {"workload": f"{sys_.name} {kind} K={sys_.K} {sys_.n_alpha}a+{sys_.n_beta}b D={sys_.D} "
                         f"N_h={sys_.n_hidden} Ns={len(sys_.samples)} per GPU eps={sys_.eps:g} "
                         f"N_eps={sys_.n_draws}",
             "K": sys_.K, "D": sys_.D, "n_hidden": sys_.n_hidden,
             "samples_per_gpu": len(sys_.samples), "global_batch": ws * len(sys_.samples),
             "eps": sys_.eps, "n_draws": sys_.n_draws, "precision": precision,
             "energy_tolerance_ha": energy_tol,
-            "l2": "working set > L2 (deterministic lists ~2.5 GB per step)"}
+            "l2": "inputs > L2 (deterministic lists and shared-prefix tables exceed 129 MB)"
+            if sys_.K >= 20 else "small case: working set may sit in L2"}
 
 
 def run_reference(args):
     ws, rank, _ = dist_setup()
     if rank != 0:
         return
-    sys_ = W.h50_chain()
     cores = os.cpu_count() or 1
-    per_step = max(2, cores)
+    if args.workload == "uneven":
+        # the first samples of the first systems, one oracle call per system
+        systems = [s.subset(range(2)) for s in W.uneven_batch()[:max(1, cores // 2)]]
+        metric, sys_ = BATCH_METRIC, systems[0]
+        per_step = sum(len(s.samples) for s in systems)
+
+        def one_step():
+            return sum(cpu_oracle_rate(s, len(s.samples), cores)[1] for s in systems)
+    else:
+        gen, n_def, _, metric = WORKLOADS[args.workload]
+        sys_ = gen(args.samples or n_def, 0)
+        per_step = min(len(sys_.samples), max(2, cores))
+
+        def one_step():
+            return cpu_oracle_rate(sys_, per_step, cores)[1]
     for _ in range(args.warmup):
-        cpu_oracle_rate(sys_, per_step, cores)
+        one_step()
     t = 0.0
     for _ in range(args.steps):
-        _, dt = cpu_oracle_rate(sys_, per_step, cores)
-        t += dt
+        t += one_step()
     v = per_step * args.steps / t
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": metric, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(sys_, "fp64-oracle"),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"first {per_step} of {len(sys_.samples)} samples per step"},
+                             "sample": f"{per_step} samples per step (the first of the workload's "
+                                       f"batch{'es' if args.workload == 'uneven' else ''})"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -194,9 +221,10 @@ def run(args):
     dev = torch.device("cuda", local)
     # weak scaling: one batch of args.samples unique samples per GPU, split
     # contiguously; each shard's draws are keyed by global sample position
-    total = args.samples * ws
+    gen, n_def, _, metric = WORKLOADS[args.workload]
+    total = (args.samples or n_def) * ws
     lo, hi = shard.shard_range(total, ws, rank)
-    sys_ = W.h50_chain(n_samples=total).subset(range(lo, hi))
+    sys_ = gen(total, 0).subset(range(lo, hi))
     Ns = len(sys_.samples)
     ctx = nqs.Context(local)
     ctx.set_system(sys_)
@@ -271,7 +299,10 @@ def run(args):
     amp_launches = sum(stages[k][1] for k in ("tables", "amp_det", "amp_draw")) / args.steps
     # the method's work per amplitude: one D x D product per site of the span
     # between the first and last changed site, plus the closing dot product
-    flops = 2.0 * D * D * work["span_sites"] + 2.0 * D * n_amp
+    # chains: D x D products over each amplitude's span; graphs: per in-edge
+    # of every recomputed vertex (the plain form's matvecs)
+    mv_alg = work["span_sites"] if sys_.pred_ptr is None else work["matvecs"]
+    flops = 2.0 * D * D * mv_alg + 2.0 * D * n_amp
     executed = 2.0 * D * D * work["matvecs"] + 2.0 * D * n_amp
     achieved = flops / (amp_ms / 1e3) / 1e12
     if prec == nqs.NQS_PREC_MIXED:
@@ -286,7 +317,7 @@ def run(args):
                 "kernel": ("amplitude stage (shared prefixes, FP64)" if prec == nqs.NQS_PREC_FP64_SHARED
                            else "k_amp_chain_fp64 / k_amp_graph_fp64 (one amplitude per row)")}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    key = args.precision if sys_.D == 64 else None
+    key = args.precision if args.workload == "h50" else None
     roof["traffic"] = STAGE_TRAFFIC_PER_AMP.get(key, None)
     if roof["traffic"] is not None:
         roof["traffic"] *= n_amp
@@ -314,7 +345,7 @@ def run(args):
                 "max_abs_diff_ha": float(d.max().item()),
                 "median_abs_diff_ha": float(d.median().item())}
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+    line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPES[args.precision],
@@ -342,22 +373,155 @@ def run(args):
     ctx.close()
 
 
+BATCH_METRIC = "E_loc samples/s (64-system uneven batch, one call)"
+
+
+def run_batch(args):
+    """64 independent chains (K 12..40, D 16/32/64, 512..4096 samples each) in
+    one nqs_local_energy_batch call per step, each system on its own context
+    and stream. The step is timed with CUDA events on the current stream; the
+    call returns only after every system's stream has finished."""
+    import torch
+    from paper_2507_19276_gb300 import nqs
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    systems = W.uneven_batch(seed_offset=rank)
+    prec = {"mixed": nqs.NQS_PREC_MIXED, "fp64": nqs.NQS_PREC_FP64,
+            "fp64_shared": nqs.NQS_PREC_FP64_SHARED}[args.precision]
+    tol = args.energy_tol if prec == nqs.NQS_PREC_MIXED else 0.0
+    streams, ctxs, dargs, hargs = [], [], [], []
+    for s in systems:
+        st = torch.cuda.Stream(dev)
+        c = nqs.Context(local, stream=st.cuda_stream)
+        c.set_system(s)
+        c.set_precision(prec, timing=True, energy_tolerance=tol)
+        streams.append(st)
+        ctxs.append(c)
+        common = {"eps": s.eps, "n_draws": s.n_draws, "seed": s.seed}
+        dargs.append(dict(common, samples=torch.from_numpy(s.samples.view(np.int64)).to(dev),
+                          counts=torch.from_numpy(s.counts).to(dev),
+                          out=torch.empty(len(s.samples), dtype=torch.float64, device=dev)))
+        hargs.append(dict(common, samples=s.samples, counts=s.counts,
+                          out=np.empty(len(s.samples), np.float64)))
+    n_total = sum(len(s.samples) for s in systems)
+
+    def step(a):
+        return nqs.local_energy_batch(ctxs, a, n_workers=args.workers)
+
+    res = None
+    for _ in range(args.warmup):
+        res = step(dargs)
+    torch.cuda.synchronize()
+    for c in ctxs:
+        c.stage_times()
+    stream = torch.cuda.current_stream(dev)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(1.0)
+    barrier(ws)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for _ in range(args.steps):
+        res = step(dargs)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(ws)
+    ms = max_over_ranks(start.elapsed_time(stop), ws, dev)
+    stages = {}
+    launches = 0
+    for c in ctxs:
+        for k, (t, n) in c.stage_times().items():
+            stages[k] = stages.get(k, 0.0) + t / args.steps
+            launches += n
+    value = ws * n_total * args.steps / (ms / 1e3)
+
+    # end to end with host buffers
+    step(hargs)
+    torch.cuda.synchronize()
+    for c in ctxs:
+        c.stage_times()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(hargs)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0), ws, dev)
+    for c in ctxs:
+        c.stage_times()
+
+    peaks, src = _peaks()
+    flops = sum(2.0 * s.D * s.D * r[1]["span_sites"] + 2.0 * s.D * r[1]["n_amplitudes"]
+                for s, r in zip(systems, res))
+    executed = sum(2.0 * s.D * s.D * r[1]["matvecs"] + 2.0 * s.D * r[1]["n_amplitudes"]
+                   for s, r in zip(systems, res))
+    achieved = flops / (ms / args.steps / 1e3) / 1e12
+    roof = {"bound": "tensor", "unit": "TFLOP/s", "achieved": achieved,
+            "peak": peaks["bf16_tflops_sustained"],
+            "peak_source": f"{src} dense bf16 (sustained; f16 has the same nominal rate)",
+            "kernel": "whole batch step (all stages of 64 systems, overlapped on streams)",
+            "frac": achieved / peaks["bf16_tflops_sustained"], "traffic": None,
+            "algorithmic_flops_per_step": flops, "executed_flops_per_step": executed}
+    Ks = [s.K for s in systems]
+    line = {"metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision],
+            "data": "synthetic",
+            "config": {"workload": f"uneven_batch: 64 chains K {min(Ks)}..{max(Ks)}, D 16/32/64, "
+                                   f"{n_total} samples per GPU, eps=1e-3, N_eps=1024",
+                       "systems": len(systems), "samples_per_gpu": n_total,
+                       "precision": args.precision, "energy_tolerance_ha": tol,
+                       "workers": args.workers,
+                       "l2": "inputs > L2 (deterministic lists exceed 129 MB)"},
+            "connected_dets_per_s": ws * args.steps * sum(
+                len(s.samples) * r[1]["n_conn"] for s, r in zip(systems, res)) / (ms / 1e3),
+            "amplitudes_per_s": ws * args.steps * sum(r[1]["n_amplitudes"] for r in res) / (ms / 1e3),
+            "stage_ms_per_step_summed_over_systems": stages,
+            "roofline": roof,
+            "e2e": {"value": ws * n_total * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": 24 * n_total, "d2h_bytes_per_step": 8 * n_total},
+            "clocks": clk, "gpu_launches": int(launches),
+            "summary": {"n_refined": int(sum(r[1]["n_refined"] for r in res))}}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        sub_ = [s.subset(range(2)) for s in systems[:8]]
+        t = sum(cpu_oracle_rate(s, 2, cores)[1] for s in sub_)
+        line["cpu_baseline"] = {"value": 2 * len(sub_) / t, "unit": UNIT, "cores": cores,
+                                "kind": "oracle", "sample": f"first 2 samples of the first "
+                                                            f"{len(sub_)} systems ({t:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for c in ctxs:
+        c.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp64_shared"])
-    ap.add_argument("--samples", type=int, default=4096)
+    ap.add_argument("--workload", default="h50", choices=sorted(WORKLOADS) + ["uneven"],
+                    help="h50 (default), k8, fe2s2, h18, or uneven (64 systems in one batch call)")
+    ap.add_argument("--precision", default=None, choices=["mixed", "fp64", "fp64_shared"],
+                    help="default: the workload's (mixed for chains with D %% 16 == 0, fp64 otherwise)")
+    ap.add_argument("--samples", type=int, default=None, help="samples per GPU (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--workers", type=int, default=8, help="host worker threads (uneven batch)")
     ap.add_argument("--energy-tol", type=float, default=1e-6,
                     help="mixed form: bound (Ha) on the weighted-energy error, met by "
                          "re-evaluating the heaviest samples in FP64 (0: none)")
     args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "mixed" if args.workload == "uneven" else WORKLOADS[args.workload][2]
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "uneven":
+        run_batch(args)
     else:
         run(args)
 

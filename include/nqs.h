@@ -265,6 +265,8 @@ typedef struct {
  * estimated cost (n_samples * n_conn * K * D) from a shared queue by
  * `n_workers` host threads (<= 0: min(n_sys, 8)), each driving its system's
  * context stream, so the work of several systems overlaps on the GPU.
+ * Each context's shared-prefix tables are capped at a 1/(3 n_sys) share of the
+ * device memory free at the call (contexts keep their buffers between calls).
  * Returns NQS_OK when every system succeeded, else the status of the first
  * failing system (by index; nqs_last_error(ctxs[i]) has its message); every
  * item's `status` is set. Each context's stream is synchronised on return.

@@ -61,6 +61,8 @@ struct nqs_ctx {
     // stage accounting (nqs_stage_times)
     int timing = 0;
     int64_t index_base = 0;    // Philox sample counter of samples[0]
+    int n_sm = 152;            // multiprocessors of the device
+    size_t fam_budget = 0;     // cap on the shared-prefix tables (0: none beyond free/3)
     double energy_tol = 0.0;   // mixed form: re-evaluate heavy samples in FP64 to this bound
     DevBuf part_det_abs, part_draw_abs, eabs, logf_save, summary2, ref_idx, ref_s, ref_c, ref_pos,
         ref_e;
@@ -404,7 +406,8 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
     // batch size from a memory budget
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
-    const size_t budget = std::min<size_t>((size_t)8 << 30, free_b / 3);
+    size_t budget = std::min<size_t>((size_t)8 << 30, free_b / 3);
+    if (c->fam_budget > 0) budget = std::min(budget, c->fam_budget);
     const size_t per = fam_bytes_per_sample(K, D, sizeof(T));
     int64_t nb = (int64_t)std::max<size_t>(1, budget / per);
     if (nb > Ns) nb = Ns;
@@ -476,6 +479,9 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
         const int nbb = (int)(s1 - s0);
         f.s0 = s0;
         f.s1 = s1;
+        // few samples (a small call, FP64 re-evaluation): spread each sample's
+        // tables over several blocks so that about two blocks per SM run
+        f.split = nbb >= 2 * c->n_sm ? 1 : std::min(32, (2 * c->n_sm + nbb - 1) / nbb);
         f.G = (T*)c->fG.p; f.Ge = (int*)c->fGe.p;
         f.H = (T*)c->fH.p; f.He = (int*)c->fHe.p;
         f.pm = (const double*)c->pmant.p + s0; f.pe = (const int*)c->pexp.p + s0;
@@ -574,6 +580,7 @@ extern "C" int nqs_create(nqs_ctx** out, int device, void* cuda_stream)
     if (cudaSetDevice(device) != cudaSuccess) return NQS_ERR_CUDA;
     nqs_ctx* c = new nqs_ctx();
     c->device = device;
+    cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
     c->stream = (cudaStream_t)cuda_stream;
     *out = c;
     return NQS_OK;
@@ -1415,6 +1422,20 @@ int ctx_shape(const nqs_ctx* c, int* K, int* na, int* nb, int* D)
     *nb = c->nb;
     *D = c->av.D;
     return NQS_OK;
+}
+
+void ctx_set_table_budget(nqs_ctx* c, size_t bytes)
+{
+    if (c) c->fam_budget = bytes;
+}
+
+size_t ctx_free_memory(nqs_ctx* c)
+{
+    size_t fr = 0, tot = 0;
+    if (!c) return 0;
+    cudaSetDevice(c->device);
+    cudaMemGetInfo(&fr, &tot);
+    return fr;
 }
 
 int ctx_sync(nqs_ctx* c)

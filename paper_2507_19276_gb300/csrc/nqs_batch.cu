@@ -14,6 +14,8 @@ namespace nqs {
 // context queries of nqs_api.cu
 int ctx_shape(const nqs_ctx* c, int* K, int* na, int* nb, int* D);
 int ctx_sync(nqs_ctx* c);
+void ctx_set_table_budget(nqs_ctx* c, size_t bytes);
+size_t ctx_free_memory(nqs_ctx* c);
 }  // namespace nqs
 
 namespace {
@@ -47,6 +49,10 @@ extern "C" int nqs_local_energy_batch(nqs_ctx* const* ctxs, int n_sys, nqs_batch
         cost[(size_t)i] = (double)items[i].n_samples * n_conn_of(K, na, nb) * K * D;
         items[i].status = NQS_ERR_STATE;
     }
+    // every context keeps its tables between calls: share a third of the free
+    // memory among the systems of the batch
+    const size_t share = nqs::ctx_free_memory(ctxs[0]) / 3 / (size_t)n_sys;
+    for (int i = 0; i < n_sys; ++i) nqs::ctx_set_table_budget(ctxs[i], share);
     std::vector<int> order((size_t)n_sys);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[(size_t)a] > cost[(size_t)b]; });

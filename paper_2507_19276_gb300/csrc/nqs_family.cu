@@ -299,8 +299,9 @@ __device__ __forceinline__ void key_fields(int K, int key, int& site_hi, int& al
 __device__ __forceinline__ int nh_pad(int NH) { return (NH + 3) & ~3; }
 
 // ---------------------------------------------------------------------------
-// F1: left and right family sweeps, one block per sample. L (or R) stays in
-// shared memory; the families are read back from the tables in batches.
+// F1: left and right family sweeps, f.split blocks per sample and side. L (or
+// R) stays in shared memory (each block forms it); block g owns the families
+// created at steps j = g, g + split, ... and reads them back in batches.
 // ---------------------------------------------------------------------------
 
 template <typename T>
@@ -317,12 +318,14 @@ __global__ void k_fam_sweep(FamArgs<T> f)
     int* soff = pos + f.nmax;                     // [nmax]
     int* doff = soff + f.nmax;                    // [nmax]
     T* Lv = (T*)(doff + f.nmax);                  // [D]
-    const int b = blockIdx.x, K = f.K, D = f.D;
+    const int G = f.split;
+    const int b = blockIdx.x / (2 * G), side = (blockIdx.x / G) & 1, g = blockIdx.x % G;
+    const int K = f.K, D = f.D;
     const int64_t s = f.s0 + b;
     const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
     T* X = sm.X;
     T* Y = sm.Y;
-    for (int side = 0; side < 2; ++side) {
+    {
         T* Tb = (side == 0 ? f.G : f.H) + (size_t)b * 3 * K * K * D;
         int* Te = (side == 0 ? f.Ge : f.He) + (size_t)b * 3 * K * K;
         const T* Mats = side == 0 ? f.AT : f.A;   // column convention left, row vectors right
@@ -344,21 +347,23 @@ __global__ void k_fam_sweep(FamArgs<T> f)
             __syncthreads();
             const int e_in = eL;
             const int eL_new = e_in + eo[3];
-            for (int q = threadIdx.x; q < 3 * D; q += blockDim.x) {
-                const int a = q / D, c = q - a * D;
-                Tb[(((size_t)a * K + t) * K + t) * D + c] = Y[q];
+            if (step % G == g) {
+                for (int q = threadIdx.x; q < 3 * D; q += blockDim.x) {
+                    const int a = q / D, c = q - a * D;
+                    Tb[(((size_t)a * K + t) * K + t) * D + c] = Y[q];
+                }
+                for (int a = threadIdx.x; a < 3; a += blockDim.x) Te[((size_t)a * K + t) * K + t] = e_in + eo[a];
             }
-            for (int a = threadIdx.x; a < 3; a += blockDim.x) Te[((size_t)a * K + t) * K + t] = e_in + eo[a];
             for (int c = threadIdx.x; c < D; c += blockDim.x) Lv[c] = Y[3 * D + c];
             __syncthreads();
             if (threadIdx.x == 0) eL = eL_new;
-            // (b) existing families: s < t (left) or s > t (right)
-            const int nfam = 3 * step;
+            // (b) this block's existing families: created at steps j < step, j = g mod G
+            const int nfam = 3 * (step > g ? (step - 1 - g) / G + 1 : 0);
             const int tprev = side == 0 ? t - 1 : t + 1;
             for (int c0 = 0; c0 < nfam; c0 += f.nmax) {
                 const int n = nfam - c0 < f.nmax ? nfam - c0 : f.nmax;
                 for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                    const int j = (c0 + i) / 3, a = (c0 + i) % 3;
+                    const int j = g + ((c0 + i) / 3) * G, a = (c0 + i) % 3;
                     const int sf = side == 0 ? j : K - 1 - j;
                     pos[i] = (a * K + sf) * K;
                     soff[i] = pos[i] + tprev;
@@ -517,7 +522,7 @@ __global__ void k_fam_tr(FamArgs<T> f)
     int* eo = (int*)(smraw + f.batch_bytes);
     int* hp = eo + f.nmax;
     int* doff = hp + f.nmax;
-    const int b = blockIdx.x, K = f.K;
+    const int G = f.split, b = blockIdx.x / G, g = blockIdx.x % G, K = f.K;
     const int64_t s = f.s0 + b;
     const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
     const size_t nk = (size_t)K * K * 9;
@@ -532,16 +537,22 @@ __global__ void k_fam_tr(FamArgs<T> f)
         const int grp0 = trl[i0] / (3 * K);              // (sA, aA)
         const int sA = grp0 / 3, aA = grp0 % 3;
         int n = 1;
-        while (i0 + n < ntr && n < f.nmax && trl[i0 + n] / (3 * K) == grp0) ++n;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int k = trl[i0 + i];
+        while (i0 + n < ntr && n < f.nmax * G && trl[i0 + n] / (3 * K) == grp0) ++n;
+        // this block's rows of the run: i0 + i with i0 + i = g (mod G)
+        const int sel = ((g - i0) % G + G) % G;
+        const int m = sel < n ? (n - 1 - sel) / G + 1 : 0;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const int r = i0 + sel + i * G;
+            const int k = trl[r];
             const int sB = (k / 3) % K, aB = k % 3;
             hp[i] = (aB * K + sB) * K + sA + 1;
-            doff[i] = i0 + i;
+            doff[i] = r;
         }
         __syncthreads();
-        batch_apply<T>(f, sm, H, hp, TR, doff, eo, n, 1, sA, sig_of_alt(aA, sigma_at(na, nb, sA)));
-        for (int i = threadIdx.x; i < n; i += blockDim.x) TRe[i0 + i] = eo[i] + He[hp[i]];
+        if (m > 0) {
+            batch_apply<T>(f, sm, H, hp, TR, doff, eo, m, 1, sA, sig_of_alt(aA, sigma_at(na, nb, sA)));
+            for (int i = threadIdx.x; i < m; i += blockDim.x) TRe[doff[i]] = eo[i] + He[hp[i]];
+        }
         __syncthreads();
         i0 += n;
     }
@@ -564,7 +575,7 @@ __global__ void k_fam_tl(FamArgs<T> f)
     int* dst = src + f.nmax;
     int* pbuf_src = dst + f.nmax;                 // [nmax + blockDim]
     int* pbuf_dst = pbuf_src + f.nmax + blockDim.x;
-    const int b = blockIdx.x, K = f.K, D = f.D;
+    const int G = f.split, b = blockIdx.x / G, g = blockIdx.x % G, K = f.K, D = f.D;
     const int64_t s = f.s0 + b;
     const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
     const size_t nk = (size_t)K * K * 9;
@@ -572,7 +583,7 @@ __global__ void k_fam_tl(FamArgs<T> f)
     const int* tl_end = f.tl_end + (size_t)b * nk;
     const int* tll = f.tl_list + (size_t)b * nk;
     const int ncl = f.tl_count[b];
-    const T* G = f.G + (size_t)b * 3 * K * K * D;
+    const T* Gf = f.G + (size_t)b * 3 * K * K * D;
     const int* Ge = f.Ge + (size_t)b * 3 * K * K;
     T* TL = f.TL + (size_t)f.tl_base[b] * D;
     int* TLe = f.TLe + f.tl_base[b];
@@ -587,16 +598,21 @@ __global__ void k_fam_tl(FamArgs<T> f)
             const int grp = tll[c0] / (3 * K);
             const int a2 = grp % 3;
             int n = 1;
-            while (c0 + n < ncl && n < f.nmax && tll[c0 + n] / (3 * K) == grp) ++n;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                const int key = tll[c0 + i];
+            while (c0 + n < ncl && n < f.nmax * G && tll[c0 + n] / (3 * K) == grp) ++n;
+            // this block's clusters of the run: c0 + i = g (mod G)
+            const int sel = ((g - c0) % G + G) % G;
+            const int m = sel < n ? (n - 1 - sel) / G + 1 : 0;
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                const int key = tll[c0 + sel + i * G];
                 const int s1 = (key / 3) % K, a1 = key % 3;
                 dst[i] = tl[key];
                 src[i] = (a1 * K + s1) * K + (t - 1);
             }
             __syncthreads();
-            batch_apply<T>(f, sm, G, src, TL, dst, eo, n, 0, t, sig_of_alt(a2, own));
-            for (int i = threadIdx.x; i < n; i += blockDim.x) TLe[dst[i]] = eo[i] + Ge[src[i]];
+            if (m > 0) {
+                batch_apply<T>(f, sm, Gf, src, TL, dst, eo, m, 0, t, sig_of_alt(a2, own));
+                for (int i = threadIdx.x; i < m; i += blockDim.x) TLe[dst[i]] = eo[i] + Ge[src[i]];
+            }
             __syncthreads();
             c0 += n;
         }
@@ -607,7 +623,7 @@ __global__ void k_fam_tl(FamArgs<T> f)
             if (w0 < first) {
                 const int c = w0 + threadIdx.x;
                 int act = 0, key = 0;
-                if (c < first) {
+                if (c < first && c % G == g) {
                     key = tll[c];
                     act = t <= tl_end[key] ? 1 : 0;
                 }
@@ -951,7 +967,7 @@ int fam_launch_sweep(const FamArgs<T>& f, int nb, cudaStream_t st)
 {
     const size_t smem = stage_smem(f, 4);
     allow_max_smem(k_fam_sweep<T>);
-    k_fam_sweep<T><<<nb, f.threads, smem, st>>>(f);
+    k_fam_sweep<T><<<(unsigned)(nb * 2 * f.split), f.threads, smem, st>>>(f);
     return 1;
 }
 
@@ -977,11 +993,11 @@ int fam_launch_tables(const FamArgs<T>& f, int nb, cudaStream_t st)
     const size_t smem_tl = stage_smem(f, 3) + (size_t)2 * (f.nmax + f.threads) * sizeof(int);
     allow_max_smem(k_fam_tr<T>);
     allow_max_smem(k_fam_tl<T>);
-    k_fam_tr<T><<<nb, f.threads, smem, st>>>(f);
-    k_fam_tl<T><<<nb, f.threads, smem_tl, st>>>(f);
+    k_fam_tr<T><<<(unsigned)(nb * f.split), f.threads, smem, st>>>(f);
+    k_fam_tl<T><<<(unsigned)(nb * f.split), f.threads, smem_tl, st>>>(f);
     int n = 2;
     if (f.n_hidden > 0) {
-        dim3 grid(8, nb);
+        dim3 grid(8 * f.split, nb);
         k_fam_rbm<T><<<grid, 256, 2 * f.n_hidden * sizeof(T), st>>>(f);
         ++n;
     }

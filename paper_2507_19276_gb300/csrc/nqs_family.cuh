@@ -13,6 +13,8 @@ struct FamArgs {
     HamView h;
     int K, D;
     int threads;              // block size of the per-sample kernels (>= D)
+    int split;                // blocks per sample (per side in the sweep) of the table
+                              // kernels; each takes every split-th family / cluster
     int nmax;                 // vectors per block-wide mat-vec batch
     size_t batch_bytes;       // shared memory of one batch (see fam_batch_bytes)
     int tc;                   // 1: tensor-core batches (FP32, D % 16 == 0, D <= 128)

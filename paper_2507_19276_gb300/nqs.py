@@ -339,7 +339,8 @@ def local_energy_batch(contexts, args, n_workers=0):
 
     contexts: one Context per system (each on its own stream for overlap);
     args: per system a dict with samples, counts (or None), eps, n_draws, seed
-    (host arrays or CUDA tensors). Returns [(e_loc, summary dict)]."""
+    (host arrays or CUDA tensors) and optionally out (E_loc destination, host
+    array or CUDA tensor). Returns [(e_loc, summary dict)]."""
     n = len(contexts)
     items = (BatchItem * n)()
     keep, outs, sums = [], [], []
@@ -351,7 +352,9 @@ def local_energy_batch(contexts, args, n_workers=0):
         if cnt is not None and not hasattr(cnt, "data_ptr"):
             cnt = _np(cnt, np.float64)
         ns = int(smp.shape[0])
-        e = np.empty(ns, np.float64)
+        e = a.get("out")
+        if e is None:
+            e = np.empty(ns, np.float64)
         sm = EnergySummary()
         keep += [smp, cnt]
         outs.append(e)
@@ -367,3 +370,71 @@ def local_energy_batch(contexts, args, n_workers=0):
         it.summary = C.pointer(sm)
     nqs_local_energy_batch([c.h for c in contexts], items, n_workers)
     return [(e, sm.as_dict()) for e, sm in zip(outs, sums)]
+
+
+_LOG_PSI = None
+
+
+def log_psi(context, samples, tensors, W=None, b=None, pred_ptr=None, pred_idx=None):
+    """log|psi(n)| (and the sign) as a differentiable function of the ansatz
+    parameters: forward is nqs_amplitude, backward nqs_grad_log_psi_vjp (the
+    hand-written reverse sweep of Eq. egrad's d ln psi / d theta).
+
+    tensors [n_edges][4][D][D], W [n_hidden][2K], b [n_hidden]: torch tensors
+    (CUDA or CPU; gradients come back on the same device and dtype). The
+    context must hold the system's Hamiltonian and run on the current torch
+    stream (the default of Context). Returns (log_abs [Ns] float64, sign [Ns]
+    int8, not differentiable)."""
+    global _LOG_PSI
+    if _LOG_PSI is None:
+        _LOG_PSI = _make_log_psi()
+    return _LOG_PSI.apply(context, samples, tensors, W, b, pred_ptr, pred_idx)
+
+
+def _make_log_psi():
+    import torch
+
+    def upload(context, T, W, b, pp, pi):
+        context.set_ansatz(T, pp, pi, W, b)
+        context._ansatz_token = object()
+        return context._ansatz_token
+
+    def f64(x):
+        return None if x is None else x.detach().to(torch.float64).contiguous()
+
+    class LogPsi(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, context, samples, tensors, W, b, pred_ptr, pred_idx):
+            T, Wd, bd = f64(tensors), f64(W), f64(b)
+            token = upload(context, T, Wd, bd, pred_ptr, pred_idx)
+            s = samples if hasattr(samples, "data_ptr") else torch.from_numpy(
+                _np(samples, np.uint64).reshape(-1, 2).view(np.int64))
+            s = s.to(T.device).contiguous()
+            Ns = int(s.shape[0])
+            la = torch.empty(Ns, dtype=torch.float64, device=T.device)
+            sg = torch.empty(Ns, dtype=torch.int8, device=T.device)
+            nqs_amplitude(context.h, s, Ns, la, sg)
+            fctx.context, fctx.token, fctx.graph = context, token, (pred_ptr, pred_idx)
+            fctx.dtypes = (tensors.dtype, None if W is None else W.dtype, None if b is None else b.dtype)
+            fctx.save_for_backward(s, T, *( [Wd, bd] if Wd is not None else []))
+            fctx.mark_non_differentiable(sg)
+            return la, sg
+
+        @staticmethod
+        def backward(fctx, g_la, g_sg):
+            saved = fctx.saved_tensors
+            s, T = saved[0], saved[1]
+            Wd, bd = (saved[2], saved[3]) if len(saved) > 2 else (None, None)
+            context = fctx.context
+            if getattr(context, "_ansatz_token", None) is not fctx.token:
+                upload(context, T, Wd, bd, *fctx.graph)   # parameters changed since forward
+            u = g_la.detach().to(device=T.device, dtype=torch.float64).contiguous()
+            gT = torch.empty_like(T)
+            gW = torch.empty_like(Wd) if Wd is not None else None
+            gb = torch.empty_like(bd) if bd is not None else None
+            nqs_grad_log_psi_vjp(context.h, s, u, int(s.shape[0]), gT, gW, gb)
+            dt, dw, db = fctx.dtypes
+            return (None, None, gT.to(dt), None if gW is None else gW.to(dw),
+                    None if gb is None else gb.to(db), None, None)
+
+    return LogPsi
