@@ -63,6 +63,7 @@ struct nqs_ctx {
     int64_t index_base = 0;    // Philox sample counter of samples[0]
     int n_sm = 152;            // multiprocessors of the device
     size_t fam_budget = 0;     // cap on the shared-prefix tables (0: none beyond free/3)
+    DevBuf h_all;              // stored H_nm of the last local-energy call
     double energy_tol = 0.0;   // mixed form: re-evaluate heavy samples in FP64 to this bound
     DevBuf part_det_abs, part_draw_abs, eabs, logf_save, summary2, ref_idx, ref_s, ref_c, ref_pos,
         ref_e;
@@ -267,7 +268,8 @@ int eps_bits(nqs_ctx* c, double eps, uint64_t* bits)
 }
 
 // Count pass + per-sample scans: det_off (device) and the total on the host.
-int count_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, uint64_t eb, int64_t* total)
+int count_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, uint64_t eb, int64_t* total,
+               double* h_store = nullptr)
 {
     const uint32_t nch = (uint32_t)((c->n_conn + 31) / 32);
     TRY(ensure(c, c->chunk_cnt, (size_t)Ns * nch * 4));
@@ -282,6 +284,7 @@ int count_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, uint64_t eb, int
     a.n_chunks = nch;
     a.chunk_cnt = (uint32_t*)c->chunk_cnt.p;
     a.rem_max_bits = (unsigned long long*)c->rem_max.p;
+    a.h_store = h_store;
     StageScope sc(c, NQS_STAGE_COUNT);
     CK(cudaMemsetAsync(c->rem_max.p, 0, (size_t)Ns * 8, c->stream));
     LAUNCH(NQS_STAGE_COUNT, launch_enum(a, Ns, false, c->stream));
@@ -607,7 +610,7 @@ extern "C" int nqs_destroy(nqs_ctx* c)
                       &c->ftl_list, &c->ftr_list, &c->ftl_cnt, &c->frbl, &c->frbr, &c->frbl_base,
                       &c->frbr_base, &c->tc_img, &c->tc_exps, &c->part_det_abs,
                       &c->part_draw_abs, &c->eabs, &c->logf_save, &c->summary2, &c->ref_idx,
-                      &c->ref_s, &c->ref_c, &c->ref_pos, &c->ref_e};
+                      &c->ref_s, &c->ref_c, &c->ref_pos, &c->ref_e, &c->h_all};
     for (DevBuf* b : bufs) release(*b);
     for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);
@@ -930,7 +933,7 @@ namespace {
 // Steps shared by nqs_draws and nqs_local_energy: weights, prefix, draws.
 int draw_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, uint64_t eb, int n_draws,
               uint64_t seed, int64_t* rank_out, bool write_dets, bool need_w,
-              const int64_t* index = nullptr)
+              const int64_t* index = nullptr, const double* h_all = nullptr)
 {
     const uint32_t nch = (uint32_t)((c->n_conn + 31) / 32);
     const bool weights = n_draws > 0 || need_w;
@@ -947,6 +950,7 @@ int draw_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, uint64_t eb, int n_dra
     a.out_rank = write_dets ? (uint32_t*)c->det_rank.p : nullptr;
     a.out_H = write_dets ? (double*)c->det_coef.p : nullptr;
     a.chunk_w = weights ? (uint64_t*)c->chunk_w.p : nullptr;
+    a.h_in = h_all;
     if (!write_dets && !weights) return NQS_OK;
     {
         StageScope sc(c, NQS_STAGE_WRITE);
@@ -971,6 +975,7 @@ int draw_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, uint64_t eb, int n_dra
         d.index_base = c->index_base;
         d.index = index;
         d.out_rank = rank_out;
+        d.h_all = h_all;
         LAUNCH(NQS_STAGE_DRAW, launch_draws(d, c->stream));
     }
     CK(cudaGetLastError());
@@ -1041,8 +1046,23 @@ int le_core(nqs_ctx* c, const uint64_t* ds, const double* dc, int64_t Ns, uint64
                                                                        (DevError*)c->derr.p);
         LAUNCH(NQS_STAGE_ENV, 1);
     }
+    // every H_nm of the batch, stored once by the count pass when it fits: the
+    // write pass, the draws and the dedup then read it instead of evaluating
+    // the Slater-Condon elements again
+    double* hall = nullptr;
+    {
+        const size_t hbytes = (size_t)Ns * (size_t)c->n_conn * 8;
+        size_t fr = 0, tt = 0;
+        cudaMemGetInfo(&fr, &tt);
+        size_t cap = std::min<size_t>((size_t)32 << 30, fr / 4);
+        if (c->fam_budget > 0) cap = std::min(cap, c->fam_budget);
+        if (hbytes <= c->h_all.n || hbytes <= cap) {
+            TRY(ensure(c, c->h_all, hbytes));
+            hall = (double*)c->h_all.p;
+        }
+    }
     int64_t total = 0;
-    TRY(count_pass(c, ds, Ns, eb, &total));
+    TRY(count_pass(c, ds, Ns, eb, &total, hall));
     if (shared) {
         c->det_off_h.resize(Ns + 1);
         CK(cudaMemcpyAsync(c->det_off_h.data(), c->det_off.p, (size_t)(Ns + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
@@ -1056,7 +1076,7 @@ int le_core(nqs_ctx* c, const uint64_t* ds, const double* dc, int64_t Ns, uint64
         TRY(ensure(c, c->draw_coef, (size_t)Ns * n_draws * 8));
         TRY(ensure(c, c->n_unique, (size_t)Ns * 8));
     }
-    TRY(draw_pass(c, ds, Ns, eb, n_draws, seed, (int64_t*)c->draw_rank64.p, true, false, dindex));
+    TRY(draw_pass(c, ds, Ns, eb, n_draws, seed, (int64_t*)c->draw_rank64.p, true, false, dindex, hall));
     if (n_draws > 0) {
         StageScope sc(c, NQS_STAGE_DRAW);
         DedupArgs d{};
@@ -1072,6 +1092,7 @@ int le_core(nqs_ctx* c, const uint64_t* ds, const double* dc, int64_t Ns, uint64
         d.out_rank = (uint32_t*)c->draw_rank.p;
         d.out_coef = (double*)c->draw_coef.p;
         d.n_unique = (int64_t*)c->n_unique.p;
+        d.h_all = hall;
         LAUNCH(NQS_STAGE_DRAW, launch_dedup(d, Ns, c->stream));
         CK(cudaGetLastError());
     }

@@ -36,6 +36,17 @@ __global__ void __launch_bounds__(kEnumWarps * 32) k_enum(EnumArgs a)
     if (WRITE) shift = shift_of(a.rem_max_bits[s], h.bitlen_nconn);
     uint64_t max_bits = 0;
     const size_t srow = (size_t)s * a.n_chunks;
+    // stored elements: issue the loads of all of this warp's chunks at once
+    double Hpre[kChunksPerWarp];
+    if (WRITE && a.h_in) {
+        #pragma unroll
+        for (int k = 0; k < kChunksPerWarp; ++k) {
+            const uint32_t c = (blockIdx.x * kEnumWarps + warp) * kChunksPerWarp + k;
+            const uint32_t r = c * 32 + lane;
+            Hpre[k] = (c < a.n_chunks && r < h.n_conn) ? __ldcs(a.h_in + (size_t)s * h.n_conn + r) : 0.0;
+        }
+    }
+    #pragma unroll
     for (int k = 0; k < kChunksPerWarp; ++k) {
         const uint32_t c = (blockIdx.x * kEnumWarps + warp) * kChunksPerWarp + k;
         if (c >= a.n_chunks) break;
@@ -45,8 +56,13 @@ __global__ void __launch_bounds__(kEnumWarps * 32) k_enum(EnumArgs a)
         uint64_t ma = 0, mb = 0;
         int odd = 0;
         if (valid) {
-            Exc e = decode_rank(h, lists, r);
-            H = matrix_element(h, na, nb, e, ma, mb, odd);
+            if (WRITE && a.h_in) {
+                H = Hpre[k];
+            } else {
+                Exc e = decode_rank(h, lists, r);
+                H = matrix_element(h, na, nb, e, ma, mb, odd);
+                if (!WRITE && a.h_store) a.h_store[(size_t)s * h.n_conn + r] = H;
+            }
         }
         const bool det = valid && is_det(H, a.eps_bits);
         const unsigned bal = __ballot_sync(kFull, det);
@@ -116,29 +132,49 @@ __global__ void __launch_bounds__(256) k_draws(DrawArgs a)
         return;
     }
     const uint64_t na = a.samples[2 * s], nb = a.samples[2 * s + 1];
-    build_lists_warp(na, nb, a.h.K, lists[warp], lane);
-    __syncwarp();
+    if (!a.h_all) {
+        build_lists_warp(na, nb, a.h.K, lists[warp], lane);
+        __syncwarp();
+    }
     // target t = floor(x W / 2^64), then the first chunk whose inclusive prefix > t
     const uint64_t x = philox_first((uint64_t)d, (uint64_t)(a.index ? a.index[s] : a.index_base + s), a.seed);
     const uint64_t t = __umul64hi(x, W);
-    uint32_t c = 0;
-    if (lane == 0) {
-        uint32_t lo = 0, hi = a.n_chunks - 1;
-        while (lo < hi) {
-            uint32_t mid = lo + (hi - lo) / 2;
-            if (a.chunk_pre[srow + mid] > t) hi = mid; else lo = mid + 1;
-        }
-        c = lo;
+    // first chunk whose inclusive prefix exceeds t, by a 32-way search: each
+    // round the lanes probe 32 evenly spaced chunks of [lo, hi] (the prefix is
+    // nondecreasing and its last entry W > t, so the answer stays in range)
+    uint32_t lo = 0, hi = a.n_chunks - 1;
+    while (hi - lo >= 32) {
+        const uint32_t span = hi - lo + 1;
+        const uint32_t p = lo + (uint32_t)(((uint64_t)span * (lane + 1)) / 32) - 1;   // p <= hi
+        const unsigned above = __ballot_sync(kFull, a.chunk_pre[srow + p] > t);
+        // the first probe above t bounds the answer from above, the one before from below
+        const int f = __ffs(above) - 1;                 // above != 0: lane 31 probes hi
+        const uint32_t nhi = (uint32_t)__shfl_sync(kFull, p, f);
+        const uint32_t nlo = f ? (uint32_t)__shfl_sync(kFull, p, f - 1) + 1 : lo;
+        __syncwarp();
+        lo = nlo;
+        hi = nhi;
     }
-    c = __shfl_sync(kFull, c, 0);
+    {
+        const uint32_t p = lo + lane;
+        const bool in = p <= hi;
+        const unsigned above = __ballot_sync(kFull, in && a.chunk_pre[srow + p] > t);
+        lo = lo + (uint32_t)(__ffs(above) - 1);
+    }
+    const uint32_t c = lo;
     const int shift = shift_of(a.rem_max_bits[s], a.h.bitlen_nconn);
     const uint32_t r = c * 32 + lane;
     uint64_t w = 0;
     if (r < a.h.n_conn) {
-        Exc e = decode_rank(a.h, lists[warp], r);
-        uint64_t ma, mb;
-        int odd;
-        double H = matrix_element(a.h, na, nb, e, ma, mb, odd);
+        double H;
+        if (a.h_all) {
+            H = a.h_all[(size_t)s * a.h.n_conn + r];
+        } else {
+            Exc e = decode_rank(a.h, lists[warp], r);
+            uint64_t ma, mb;
+            int odd;
+            H = matrix_element(a.h, na, nb, e, ma, mb, odd);
+        }
         if (!is_det(H, a.eps_bits)) w = weight_of(H, shift);
     }
     const uint64_t incl = warp_incl_scan_u64(w, lane);
@@ -210,10 +246,15 @@ __global__ void __launch_bounds__(1024) k_dedup(DedupArgs a)
         int e = i + 1;
         while (e < P && keys[e] == keys[i]) ++e;
         const uint32_t r = keys[i];
-        Exc ex = decode_rank(a.h, lists, r);
-        uint64_t ma, mb;
-        int odd;
-        double H = matrix_element(a.h, na, nb, ex, ma, mb, odd);
+        double H;
+        if (a.h_all) {
+            H = a.h_all[(size_t)s * a.h.n_conn + r];
+        } else {
+            Exc ex = decode_rank(a.h, lists, r);
+            uint64_t ma, mb;
+            int odd;
+            H = matrix_element(a.h, na, nb, ex, ma, mb, odd);
+        }
         uint64_t w = weight_of(H, shift);
         double coef = ((double)(e - i) / (double)a.n_draws) * H * ((double)W / (double)w);
         a.out_rank[base + u] = r;

@@ -40,6 +40,9 @@ struct EnumArgs {
     uint64_t* out_det;
     int8_t* out_sign;
     uint64_t* chunk_w;                   // [Ns][n_chunks] remainder weight sums (NULL: skip)
+    double* h_store;                     // count pass: every H_nm at [s][rank] (NULL: none)
+    const double* h_in;                  // write pass: read H_nm there instead of evaluating
+                                         // (only without out_det / out_sign)
 };
 int launch_enum(const EnumArgs& a, int64_t Ns, bool write, cudaStream_t st);
 
@@ -56,6 +59,7 @@ struct DrawArgs {
     int64_t index_base;                  // Philox sample counter of samples[0]
     const int64_t* index;                // per-sample Philox counters (NULL: index_base + s)
     int64_t* out_rank;                   // [Ns][n_draws]
+    const double* h_all;                 // stored H_nm [Ns][n_conn] (NULL: evaluate)
 };
 int launch_draws(const DrawArgs& a, cudaStream_t st);
 
@@ -70,6 +74,7 @@ struct DedupArgs {
     uint32_t* out_rank;                  // [Ns][n_draws] unique ranks (first n_unique)
     double* out_coef;                    // [Ns][n_draws]
     int64_t* n_unique;                   // [Ns]
+    const double* h_all;                 // stored H_nm [Ns][n_conn] (NULL: evaluate)
 };
 int launch_dedup(const DedupArgs& a, int64_t Ns, cudaStream_t st);
 
