@@ -172,79 +172,125 @@ __device__ void batch_apply(const FamArgs<T>& f, BatchSmem<T>& sm, const T* src,
         return;
     }
     // ---- tensor-core path (T = float) ----
-    const int cpr = D >> 3;                       // 8-element units per row
-    for (int u = threadIdx.x; u < n * cpr; u += blockDim.x) {
-        const int r = u / cpr, c = u - r * cpr;
-        const float4* p = (const float4*)((const float*)src + (size_t)soff[r] * D + 8 * c);
-        const float4 v0 = p[0], v1 = p[1];
-        const float xs[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-        __align__(16) __half hi[8], lo[8];
-        #pragma unroll
-        for (int j = 0; j < 8; ++j) tc::split_half(xs[j], hi[j], lo[j]);
-        const uint32_t off = tc::op_offset(r, 8 * c, D);
-        *(uint4*)(sm.Ah + off) = *(const uint4*)hi;
-        *(uint4*)(sm.Al + off) = *(const uint4*)lo;
-    }
-    const int mat = (side * f.K + t) * 4 + sg;
-    if (mat != sm.cur_mat) {
-        const uint4* g = f.tc_mats + (size_t)mat * (4 * D * D / 16);
-        uint4* d = (uint4*)sm.Bh;
-        for (int i = threadIdx.x; i < 4 * D * D / 16; i += blockDim.x) d[i] = g[i];
-        sm.cur_mat = mat;
-    }
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        tc::fence_after_sync();
-        const uint32_t idesc = tc::idesc_f16(128, D);
-        const uint32_t lbo = 128, sbo = 16 * D;
-        const unsigned char* Bl = sm.Bh + 2 * D * D;
-        const unsigned char* As[3] = {sm.Ah, sm.Al, sm.Ah};
-        const unsigned char* Bs[3] = {sm.Bh, sm.Bh, Bl};
-        uint32_t acc = 0;
-        for (int term = 0; term < 3; ++term)
-            for (int ks = 0; ks < D / 16; ++ks) {
-                tc::mma_f16(sm.tmem, tc::desc(tc::smem_addr(As[term]) + ks * 256, lbo, sbo),
-                            tc::desc(tc::smem_addr(Bs[term]) + ks * 256, lbo, sbo), idesc, acc);
-                acc = 1;
+    if constexpr (std::is_same<T, float>::value) {
+        // gather: each thread takes up to 2 units of 8 elements per round and
+        // issues all their loads before splitting any (latency-bound otherwise)
+        const int cpr = D >> 3;                       // 8-element units per row
+        const int nun = n * cpr;
+        for (int u0 = 0; u0 < nun; u0 += 2 * blockDim.x) {
+            float4 v4[2][2];
+            #pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int u = u0 + k * blockDim.x + threadIdx.x;
+                if (u < nun) {
+                    const int r = u / cpr, c = u - r * cpr;
+                    const float4* p = (const float4*)((const float*)src + (size_t)soff[r] * D + 8 * c);
+                    v4[k][0] = p[0];
+                    v4[k][1] = p[1];
+                }
             }
-        tc::mma_commit(sm.mbar);
-    }
-    const bool ok = tc::mbar_wait(sm.mbar, sm.phase, 1u << 24);
-    sm.phase ^= 1u;
-    tc::fence_after_sync();
-    if (!ok && threadIdx.x == 0) report(f.err, 5, 4, (long long)f.s0);
-    // tensor memory -> registers: warp w reads lanes 32 (w % 4) .. +31 and half (w / 4) of the columns
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int q = warp & 3, h = warp >> 2, half = D >> 1;
-    const int r = 32 * q + lane;
-    float v[64];
-    float m = 0.f;
-    if (warp < 8) {
-        for (int c0 = 0; c0 < half; c0 += 8) {
-            tc::tmem_ld8(sm.tmem + ((uint32_t)(32 * q) << 16) + h * half + c0, v + c0);
+            #pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int u = u0 + k * blockDim.x + threadIdx.x;
+                if (u < nun) {
+                    const int r = u / cpr, c = u - r * cpr;
+                    const float xs[8] = {v4[k][0].x, v4[k][0].y, v4[k][0].z, v4[k][0].w,
+                                         v4[k][1].x, v4[k][1].y, v4[k][1].z, v4[k][1].w};
+                    __align__(16) __half hi[8], lo[8];
+                    #pragma unroll
+                    for (int j = 0; j < 8; ++j) tc::split_half(xs[j], hi[j], lo[j]);
+                    const uint32_t off = tc::op_offset(r, 8 * c, D);
+                    *(uint4*)(sm.Ah + off) = *(const uint4*)hi;
+                    *(uint4*)(sm.Al + off) = *(const uint4*)lo;
+                }
+            }
         }
-        tc::tmem_wait_ld();
-        for (int j = 0; j < half; ++j) m = fmaxf(m, fabsf(v[j]));
-        sm.rmax[h * 128 + r] = m;
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    if (warp < 8 && r < n) {
-        const float mm = fmaxf(sm.rmax[r], sm.rmax[128 + r]);
-        int e = 0;
-        if (mm > 0.f) frexpf(mm, &e);
-        float* o = (float*)dst + (size_t)doff[r] * D + h * half;
-        for (int j = 0; j < half; j += 4) {
-            float4 w;
-            w.x = ldexpf(v[j], -e); w.y = ldexpf(v[j + 1], -e);
-            w.z = ldexpf(v[j + 2], -e); w.w = ldexpf(v[j + 3], -e);
-            *(float4*)(o + j) = w;
+        const int mat = (side * f.K + t) * 4 + sg;
+        if (mat != sm.cur_mat) {
+            const uint4* __restrict__ g = f.tc_mats + (size_t)mat * (4 * D * D / 16);
+            uint4* d = (uint4*)sm.Bh;
+            const int nimg = 4 * D * D / 16;
+            for (int i0 = 0; i0 < nimg; i0 += 4 * blockDim.x) {
+                uint4 w[4];
+                #pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int i = i0 + k * blockDim.x + threadIdx.x;
+                    if (i < nimg) w[k] = __ldg(g + i);
+                }
+                #pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int i = i0 + k * blockDim.x + threadIdx.x;
+                    if (i < nimg) d[i] = w[k];
+                }
+            }
+            sm.cur_mat = mat;
         }
-        if (h == 0) eo[r] = e + f.tc_exp[mat];
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc::fence_after_sync();
+            const uint32_t idesc = tc::idesc_f16(128, D);
+            const uint32_t lbo = 128, sbo = 16 * D;
+            const unsigned char* Bl = sm.Bh + 2 * D * D;
+            const unsigned char* As[3] = {sm.Ah, sm.Al, sm.Ah};
+            const unsigned char* Bs[3] = {sm.Bh, sm.Bh, Bl};
+            uint32_t acc = 0;
+            for (int term = 0; term < 3; ++term)
+                for (int ks = 0; ks < D / 16; ++ks) {
+                    tc::mma_f16(sm.tmem, tc::desc(tc::smem_addr(As[term]) + ks * 256, lbo, sbo),
+                                tc::desc(tc::smem_addr(Bs[term]) + ks * 256, lbo, sbo), idesc, acc);
+                    acc = 1;
+                }
+            tc::mma_commit(sm.mbar);
+        }
+        const bool ok = tc::mbar_wait(sm.mbar, sm.phase, 1u << 24);
+        sm.phase ^= 1u;
+        tc::fence_after_sync();
+        if (!ok && threadIdx.x == 0) report(f.err, 5, 4, (long long)f.s0);
+        // tensor memory -> registers, twice (row maximum, then the scaled row), 8
+        // columns at a time so that nothing indexed by D lives in local memory.
+        // Warp w reads lanes 32 (w % 4) .. +31 and half (w / 4) of the columns.
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int q = warp & 3, h = warp >> 2, half = D >> 1;
+        const int r = 32 * q + lane;
+        const uint32_t trow = sm.tmem + ((uint32_t)(32 * q) << 16) + h * half;
+        if (warp < 8) {
+            float m = 0.f;
+            for (int c0 = 0; c0 < half; c0 += 8) {
+                float v[8];
+                tc::tmem_ld8(trow + c0, v);
+                tc::tmem_wait_ld();
+                #pragma unroll
+                for (int j = 0; j < 8; ++j) m = fmaxf(m, fabsf(v[j]));
+            }
+            sm.rmax[h * 128 + r] = m;
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (warp < 8) {
+            const float mm = fmaxf(sm.rmax[r], sm.rmax[128 + r]);
+            int e = 0;
+            if (mm > 0.f) frexpf(mm, &e);
+            float* o = (float*)dst + (size_t)(r < n ? doff[r] : 0) * D + h * half;
+            for (int c0 = 0; c0 < half; c0 += 8) {
+                float v[8];
+                tc::tmem_ld8(trow + c0, v);     // every lane of the warp takes part
+                tc::tmem_wait_ld();
+                if (r < n) {
+                    float4 w0, w1;
+                    w0.x = ldexpf(v[0], -e); w0.y = ldexpf(v[1], -e); w0.z = ldexpf(v[2], -e); w0.w = ldexpf(v[3], -e);
+                    w1.x = ldexpf(v[4], -e); w1.y = ldexpf(v[5], -e); w1.z = ldexpf(v[6], -e); w1.w = ldexpf(v[7], -e);
+                    *(float4*)(o + c0) = w0;
+                    *(float4*)(o + c0 + 4) = w1;
+                }
+            }
+            if (h == 0 && r < n) eo[r] = e + f.tc_exp[mat];
+        }
+        tc::fence_before_sync();
+        __syncthreads();
     }
-    __syncthreads();
 }
 
 // per-kernel setup / teardown of the tensor-core state
@@ -305,7 +351,7 @@ __device__ __forceinline__ int nh_pad(int NH) { return (NH + 3) & ~3; }
 // ---------------------------------------------------------------------------
 
 template <typename T>
-__global__ void k_fam_sweep(FamArgs<T> f)
+__global__ void __launch_bounds__(256, 3) k_fam_sweep(FamArgs<T> f)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ uint32_t tmem_slot;
@@ -512,7 +558,7 @@ __global__ void k_fam_compact(FamArgs<T> f)
 // F4a: TR_{sA aA, sB aB} = H_{sB,aB}(sA+1) A_{sA}^{aA}; the TR list is in key
 // order, i.e. grouped by (sA, aA): one matrix per run.
 template <typename T>
-__global__ void k_fam_tr(FamArgs<T> f)
+__global__ void __launch_bounds__(256, 3) k_fam_tr(FamArgs<T> f)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ uint32_t tmem_slot;
@@ -562,7 +608,7 @@ __global__ void k_fam_tr(FamArgs<T> f)
 // F4b: TL clusters: created at t = s2 from G_{s1,a1}(s2-1), propagated with
 // A_t^{sigma_t(n)} up to their last use; every step is stored.
 template <typename T>
-__global__ void k_fam_tl(FamArgs<T> f)
+__global__ void __launch_bounds__(256, 3) k_fam_tl(FamArgs<T> f)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ uint32_t tmem_slot;
