@@ -294,9 +294,17 @@ __device__ void batch_apply(const FamArgs<T>& f, BatchSmem<T>& sm, const T* src,
 }
 
 // per-kernel setup / teardown of the tensor-core state
+// Shared-memory bytes of a kernel's batch buffers: the sweep keeps the small
+// scratch, the other table kernels start their buffers without it.
+template <typename T>
+__device__ __forceinline__ size_t batch_span(const FamArgs<T>& f, bool small)
+{
+    return f.batch_bytes - (small ? 0 : fam_small_bytes(f.D, sizeof(T), use_tc(f)));
+}
+
 template <typename T>
 __device__ void batch_init(const FamArgs<T>& f, BatchSmem<T>& sm, unsigned char* base, uint32_t* tmem_slot,
-                           uint64_t* mbar)
+                           uint64_t* mbar, bool small = true)
 {
     const int D = f.D;
     if (!use_tc(f)) {
@@ -306,7 +314,7 @@ __device__ void batch_init(const FamArgs<T>& f, BatchSmem<T>& sm, unsigned char*
     }
     sm.X = (T*)base;                              // small scratch for the sweep's boundary vectors
     sm.Y = sm.X + (size_t)4 * D;
-    unsigned char* p = base + (((size_t)8 * D * sizeof(T) + 1023) & ~(size_t)1023);
+    unsigned char* p = base + (small ? fam_small_bytes(D, sizeof(T), true) : 0);
     sm.Ah = p; p += (size_t)128 * D * 2;
     sm.Al = p; p += (size_t)128 * D * 2;
     sm.Bh = p; p += (size_t)4 * D * D;
@@ -558,14 +566,14 @@ __global__ void k_fam_compact(FamArgs<T> f)
 // F4a: TR_{sA aA, sB aB} = H_{sB,aB}(sA+1) A_{sA}^{aA}; the TR list is in key
 // order, i.e. grouped by (sA, aA): one matrix per run.
 template <typename T>
-__global__ void __launch_bounds__(256, 3) k_fam_tr(FamArgs<T> f)
+__global__ void __launch_bounds__(256, 4) k_fam_tr(FamArgs<T> f)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) uint64_t mbar;
     BatchSmem<T> sm;
-    batch_init(f, sm, smraw, &tmem_slot, &mbar);
-    int* eo = (int*)(smraw + f.batch_bytes);
+    batch_init(f, sm, smraw, &tmem_slot, &mbar, false);
+    int* eo = (int*)(smraw + batch_span(f, false));
     int* hp = eo + f.nmax;
     int* doff = hp + f.nmax;
     const int G = f.split, b = blockIdx.x / G, g = blockIdx.x % G, K = f.K;
@@ -608,15 +616,15 @@ __global__ void __launch_bounds__(256, 3) k_fam_tr(FamArgs<T> f)
 // F4b: TL clusters: created at t = s2 from G_{s1,a1}(s2-1), propagated with
 // A_t^{sigma_t(n)} up to their last use; every step is stored.
 template <typename T>
-__global__ void __launch_bounds__(256, 3) k_fam_tl(FamArgs<T> f)
+__global__ void __launch_bounds__(256, 4) k_fam_tl(FamArgs<T> f)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) uint64_t mbar;
     __shared__ int wt[32];
     BatchSmem<T> sm;
-    batch_init(f, sm, smraw, &tmem_slot, &mbar);
-    int* eo = (int*)(smraw + f.batch_bytes);
+    batch_init(f, sm, smraw, &tmem_slot, &mbar, false);
+    int* eo = (int*)(smraw + batch_span(f, false));
     int* src = eo + f.nmax;
     int* dst = src + f.nmax;
     int* pbuf_src = dst + f.nmax;                 // [nmax + blockDim]
@@ -1003,9 +1011,11 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
 // ---------------------------------------------------------------------------
 
 template <typename T>
-static size_t stage_smem(const FamArgs<T>& f, int nints)
+static size_t stage_smem(const FamArgs<T>& f, int nints, bool small = true)
 {
-    return f.batch_bytes + (size_t)nints * f.nmax * sizeof(int) + (size_t)f.D * sizeof(T) + 64;
+    const size_t bb = f.batch_bytes - (small ? 0 : fam_small_bytes(f.D, sizeof(T), f.tc != 0 &&
+                                                                   std::is_same<T, float>::value));
+    return bb + (size_t)nints * f.nmax * sizeof(int) + (size_t)f.D * sizeof(T) + 64;
 }
 
 template <typename T>
@@ -1035,8 +1045,8 @@ int fam_launch_compact(const FamArgs<T>& f, int nb, cudaStream_t st)
 template <typename T>
 int fam_launch_tables(const FamArgs<T>& f, int nb, cudaStream_t st)
 {
-    const size_t smem = stage_smem(f, 3);
-    const size_t smem_tl = stage_smem(f, 3) + (size_t)2 * (f.nmax + f.threads) * sizeof(int);
+    const size_t smem = stage_smem(f, 3, false);
+    const size_t smem_tl = stage_smem(f, 3, false) + (size_t)2 * (f.nmax + f.threads) * sizeof(int);
     allow_max_smem(k_fam_tr<T>);
     allow_max_smem(k_fam_tl<T>);
     k_fam_tr<T><<<(unsigned)(nb * f.split), f.threads, smem, st>>>(f);

@@ -59,12 +59,17 @@ template <typename T> int fam_launch_rows(const FamArgs<T>& f, const RowSet& row
                                           double* partial, int64_t* span, double* partial_abs,
                                           cudaStream_t st);
 
-// shared memory of the batch buffers of the table kernels
-inline size_t fam_batch_bytes(int D, int nmax, size_t elem, bool tc)
+// shared memory of the batch buffers of the table kernels; the tensor-core
+// layout starts with a small scratch for the sweep's boundary vectors
+// (fam_small_bytes), which the other table kernels leave out
+__host__ __device__ inline size_t fam_small_bytes(int D, size_t elem, bool tc)
+{
+    return tc ? (((size_t)8 * D * elem + 1023) & ~(size_t)1023) : 0;
+}
+__host__ __device__ inline size_t fam_batch_bytes(int D, int nmax, size_t elem, bool tc)
 {
     if (!tc) return (size_t)2 * nmax * D * elem;
-    const size_t small = ((size_t)8 * D * elem + 1023) & ~(size_t)1023;
-    return small + (size_t)4 * 128 * D + (size_t)4 * D * D + 2 * 128 * 4;
+    return fam_small_bytes(D, elem, tc) + (size_t)4 * 128 * D + (size_t)4 * D * D + 2 * 128 * 4;
 }
 
 // Split-FP16 operand images of the chain's site tensors for the tensor-core
