@@ -824,7 +824,9 @@ extern "C" int nqs_set_ansatz(nqs_ctx* c, const double* site_tensors, int n_edge
     a.b = n_hidden ? (const double*)c->b.p : nullptr;
     c->av = a;
     c->has_tc = false;
-    if (chain && D % 16 == 0 && D <= 128) {
+    // tensor-core batches: D % 16 == 0 up to 128 in one reduction chunk, or
+    // 192 / 256 in chunks of 64 (N = D <= 256 accumulator columns)
+    if (chain && D % 16 == 0 && (D <= 128 || (D % 64 == 0 && D <= 256))) {
         std::vector<unsigned char> img;
         std::vector<int> ex;
         fam_tc_images(hA.data(), K, D, img, ex);

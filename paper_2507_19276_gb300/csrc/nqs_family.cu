@@ -173,80 +173,90 @@ __device__ void batch_apply(const FamArgs<T>& f, BatchSmem<T>& sm, const T* src,
     }
     // ---- tensor-core path (T = float) ----
     if constexpr (std::is_same<T, float>::value) {
-        // gather: each thread takes up to 2 units of 8 elements per round and
-        // issues all their loads before splitting any (latency-bound otherwise)
-        const int cpr = D >> 3;                       // 8-element units per row
-        const int nun = n * cpr;
-        for (int u0 = 0; u0 < nun; u0 += 2 * blockDim.x) {
-            float4 v4[2][2];
-            #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int u = u0 + k * blockDim.x + threadIdx.x;
-                if (u < nun) {
-                    const int r = u / cpr, c = u - r * cpr;
-                    const float4* p = (const float4*)((const float*)src + (size_t)soff[r] * D + 8 * c);
-                    v4[k][0] = p[0];
-                    v4[k][1] = p[1];
-                }
-            }
-            #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int u = u0 + k * blockDim.x + threadIdx.x;
-                if (u < nun) {
-                    const int r = u / cpr, c = u - r * cpr;
-                    const float xs[8] = {v4[k][0].x, v4[k][0].y, v4[k][0].z, v4[k][0].w,
-                                         v4[k][1].x, v4[k][1].y, v4[k][1].z, v4[k][1].w};
-                    __align__(16) __half hi[8], lo[8];
-                    #pragma unroll
-                    for (int j = 0; j < 8; ++j) tc::split_half(xs[j], hi[j], lo[j]);
-                    const uint32_t off = tc::op_offset(r, 8 * c, D);
-                    *(uint4*)(sm.Ah + off) = *(const uint4*)hi;
-                    *(uint4*)(sm.Al + off) = *(const uint4*)lo;
-                }
-            }
-        }
+        // The reduction runs over D / KC chunks of KC columns (one chunk up to
+        // D = 128): per chunk the batch rows' columns are gathered and split
+        // into FP16 hi / lo, the matrix image's chunk is staged, and the MMAs
+        // accumulate into the same tensor-memory columns.
+        const int KC = fam_tc_kc(D), nck = D / KC;
         const int mat = (side * f.K + t) * 4 + sg;
-        if (mat != sm.cur_mat) {
-            const uint4* __restrict__ g = f.tc_mats + (size_t)mat * (4 * D * D / 16);
-            uint4* d = (uint4*)sm.Bh;
-            const int nimg = 4 * D * D / 16;
-            for (int i0 = 0; i0 < nimg; i0 += 4 * blockDim.x) {
-                uint4 w[4];
+        const int cpr = KC >> 3;                      // 8-element units per row of a chunk
+        const int nun = n * cpr;
+        bool ok = true;
+        for (int ck = 0; ck < nck; ++ck) {
+            // gather: each thread takes up to 2 units per round and issues all
+            // their loads before splitting any (latency-bound otherwise)
+            for (int u0 = 0; u0 < nun; u0 += 2 * blockDim.x) {
+                float4 v4[2][2];
                 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int i = i0 + k * blockDim.x + threadIdx.x;
-                    if (i < nimg) w[k] = __ldg(g + i);
+                for (int k = 0; k < 2; ++k) {
+                    const int u = u0 + k * blockDim.x + threadIdx.x;
+                    if (u < nun) {
+                        const int r = u / cpr, c = u - r * cpr;
+                        const float4* p = (const float4*)((const float*)src + (size_t)soff[r] * D + ck * KC + 8 * c);
+                        v4[k][0] = p[0];
+                        v4[k][1] = p[1];
+                    }
                 }
                 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int i = i0 + k * blockDim.x + threadIdx.x;
-                    if (i < nimg) d[i] = w[k];
+                for (int k = 0; k < 2; ++k) {
+                    const int u = u0 + k * blockDim.x + threadIdx.x;
+                    if (u < nun) {
+                        const int r = u / cpr, c = u - r * cpr;
+                        const float xs[8] = {v4[k][0].x, v4[k][0].y, v4[k][0].z, v4[k][0].w,
+                                             v4[k][1].x, v4[k][1].y, v4[k][1].z, v4[k][1].w};
+                        __align__(16) __half hi[8], lo[8];
+                        #pragma unroll
+                        for (int j = 0; j < 8; ++j) tc::split_half(xs[j], hi[j], lo[j]);
+                        const uint32_t off = tc::op_offset(r, 8 * c, KC);
+                        *(uint4*)(sm.Ah + off) = *(const uint4*)hi;
+                        *(uint4*)(sm.Al + off) = *(const uint4*)lo;
+                    }
                 }
             }
-            sm.cur_mat = mat;
-        }
-        tc::fence_proxy_async();
-        tc::fence_before_sync();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            tc::fence_after_sync();
-            const uint32_t idesc = tc::idesc_f16(128, D);
-            const uint32_t lbo = 128, sbo = 16 * D;
-            const unsigned char* Bl = sm.Bh + 2 * D * D;
-            const unsigned char* As[3] = {sm.Ah, sm.Al, sm.Ah};
-            const unsigned char* Bs[3] = {sm.Bh, sm.Bh, Bl};
-            uint32_t acc = 0;
-            for (int term = 0; term < 3; ++term)
-                for (int ks = 0; ks < D / 16; ++ks) {
-                    tc::mma_f16(sm.tmem, tc::desc(tc::smem_addr(As[term]) + ks * 256, lbo, sbo),
-                                tc::desc(tc::smem_addr(Bs[term]) + ks * 256, lbo, sbo), idesc, acc);
-                    acc = 1;
+            // the image chunk (kept across batches when one chunk holds the matrix)
+            if (nck > 1 || mat != sm.cur_mat) {
+                const int nimg = 4 * D * KC / 16;
+                const uint4* __restrict__ g = f.tc_mats + (size_t)mat * (4 * D * D / 16) + (size_t)ck * nimg;
+                uint4* d = (uint4*)sm.Bh;
+                for (int i0 = 0; i0 < nimg; i0 += 4 * blockDim.x) {
+                    uint4 w[4];
+                    #pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int i = i0 + k * blockDim.x + threadIdx.x;
+                        if (i < nimg) w[k] = __ldg(g + i);
+                    }
+                    #pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int i = i0 + k * blockDim.x + threadIdx.x;
+                        if (i < nimg) d[i] = w[k];
+                    }
                 }
-            tc::mma_commit(sm.mbar);
+                sm.cur_mat = nck > 1 ? -1 : mat;
+            }
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                tc::fence_after_sync();
+                const uint32_t idesc = tc::idesc_f16(128, D);
+                const uint32_t lbo = 128, sbo = 16 * KC;
+                const unsigned char* Bl = sm.Bh + 2 * D * KC;
+                const unsigned char* As[3] = {sm.Ah, sm.Al, sm.Ah};
+                const unsigned char* Bs[3] = {sm.Bh, sm.Bh, Bl};
+                uint32_t acc = ck > 0 ? 1u : 0u;
+                for (int term = 0; term < 3; ++term)
+                    for (int ks = 0; ks < KC / 16; ++ks) {
+                        tc::mma_f16(sm.tmem, tc::desc(tc::smem_addr(As[term]) + ks * 256, lbo, sbo),
+                                    tc::desc(tc::smem_addr(Bs[term]) + ks * 256, lbo, sbo), idesc, acc);
+                        acc = 1;
+                    }
+                tc::mma_commit(sm.mbar);
+            }
+            // the chunk's operands may be overwritten once its MMAs are done
+            ok = tc::mbar_wait(sm.mbar, sm.phase, 1u << 24) && ok;
+            sm.phase ^= 1u;
+            tc::fence_after_sync();
         }
-        const bool ok = tc::mbar_wait(sm.mbar, sm.phase, 1u << 24);
-        sm.phase ^= 1u;
-        tc::fence_after_sync();
         if (!ok && threadIdx.x == 0) report(f.err, 5, 4, (long long)f.s0);
         // tensor memory -> registers, twice (row maximum, then the scaled row), 8
         // columns at a time so that nothing indexed by D lives in local memory.
@@ -315,9 +325,10 @@ __device__ void batch_init(const FamArgs<T>& f, BatchSmem<T>& sm, unsigned char*
     sm.X = (T*)base;                              // small scratch for the sweep's boundary vectors
     sm.Y = sm.X + (size_t)4 * D;
     unsigned char* p = base + (small ? fam_small_bytes(D, sizeof(T), true) : 0);
-    sm.Ah = p; p += (size_t)128 * D * 2;
-    sm.Al = p; p += (size_t)128 * D * 2;
-    sm.Bh = p; p += (size_t)4 * D * D;
+    const size_t kc = (size_t)fam_tc_kc(D);
+    sm.Ah = p; p += (size_t)128 * kc * 2;
+    sm.Al = p; p += (size_t)128 * kc * 2;
+    sm.Bh = p; p += (size_t)4 * D * kc;
     sm.rmax = (float*)p;
     sm.mbar = mbar;
     sm.cur_mat = -1;
@@ -1084,8 +1095,8 @@ void fam_tc_images(const double* A, int K, int D, std::vector<unsigned char>& im
                 if (mx > 0.0) std::frexp(mx, &e);
                 const size_t id = ((size_t)side * K + t) * 4 + sg;
                 exps[id] = e;
-                unsigned char* hi = images.data() + id * blk;
-                unsigned char* lo = hi + 2 * (size_t)D * D;
+                const int kc = fam_tc_kc(D);
+                const size_t chunk = (size_t)4 * D * kc;     // hi + lo of one reduction chunk
                 for (int n = 0; n < D; ++n)
                     for (int k = 0; k < D; ++k) {
                         // B[n][k]: side 0 -> M[n][k] (y = M x), side 1 -> M[k][n] (y = x^T M)
@@ -1093,7 +1104,10 @@ void fam_tc_images(const double* A, int K, int D, std::vector<unsigned char>& im
                         const float mf = (float)m;
                         const __half h = __float2half_rn(mf);
                         const __half l = __float2half_rn(mf - __half2float(h));
-                        const size_t off = ((size_t)(n >> 3) * (D >> 3) + (k >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2;
+                        const int ck = k / kc, kk = k - ck * kc;
+                        unsigned char* hi = images.data() + id * blk + (size_t)ck * chunk;
+                        unsigned char* lo = hi + (size_t)2 * D * kc;
+                        const size_t off = ((size_t)(n >> 3) * (kc >> 3) + (kk >> 3)) * 128 + (n & 7) * 16 + (kk & 7) * 2;
                         std::memcpy(hi + off, &h, 2);
                         std::memcpy(lo + off, &l, 2);
                     }

@@ -17,9 +17,9 @@ struct FamArgs {
                               // kernels; each takes every split-th family / cluster
     int nmax;                 // vectors per block-wide mat-vec batch
     size_t batch_bytes;       // shared memory of one batch (see fam_batch_bytes)
-    int tc;                   // 1: tensor-core batches (FP32, D % 16 == 0, D <= 128)
+    int tc;                   // 1: tensor-core batches (FP32; D % 16 == 0 up to 128, or 192 / 256)
     int tc_cols;              // tensor-memory columns allocated per block
-    const uint4* tc_mats;     // [2][K][4] split-FP16 operand images (hi then lo), see fam_tc_images
+    const uint4* tc_mats;     // [2][K][4] split-FP16 operand images, see fam_tc_images
     const int* tc_exp;        // [2][K][4] power-of-two scale of each image
     DevError* err;
     const T* A;               // [K][4][D][D] site tensors in T, A[a][b]
@@ -66,16 +66,22 @@ __host__ __device__ inline size_t fam_small_bytes(int D, size_t elem, bool tc)
 {
     return tc ? (((size_t)8 * D * elem + 1023) & ~(size_t)1023) : 0;
 }
+// width of the reduction chunks of a tensor-core batch: the whole D up to 128,
+// else 64 (the operands of one chunk then fit shared memory)
+__host__ __device__ inline int fam_tc_kc(int D) { return D <= 128 ? D : 64; }
 __host__ __device__ inline size_t fam_batch_bytes(int D, int nmax, size_t elem, bool tc)
 {
     if (!tc) return (size_t)2 * nmax * D * elem;
-    return fam_small_bytes(D, elem, tc) + (size_t)4 * 128 * D + (size_t)4 * D * D + 2 * 128 * 4;
+    const size_t kc = (size_t)fam_tc_kc(D);
+    return fam_small_bytes(D, elem, tc) + (size_t)4 * 128 * kc + (size_t)4 * D * kc + 2 * 128 * 4;
 }
 
 // Split-FP16 operand images of the chain's site tensors for the tensor-core
 // batches: for side 0 the matrix A_t^s, for side 1 its transpose, each scaled
-// by 2^-e (max |entry| in [0.5, 1)), hi and lo halves in the K-major core-matrix
-// layout. images holds 2*K*4 blocks of 4*D*D bytes; exps the e.
+// by 2^-e (max |entry| in [0.5, 1)). Each image is D / kc reduction chunks
+// (kc = fam_tc_kc(D)), each chunk its hi then its lo half, D rows x kc columns
+// in the K-major core-matrix layout. images holds 2*K*4 blocks of 4*D*D bytes;
+// exps the e.
 void fam_tc_images(const double* A, int K, int D, std::vector<unsigned char>& images, std::vector<int>& exps);
 
 // bytes of the per-sample tables (G, H, their exponents, cluster maps)
