@@ -64,6 +64,7 @@ struct nqs_ctx {
     int n_sm = 152;            // multiprocessors of the device
     size_t fam_budget = 0;     // cap on the shared-prefix tables (0: none beyond free/3)
     DevBuf h_all;              // stored H_nm of the last local-energy call
+    DevBuf site_cnt, site_offs, site_bounds, site_items;
     double energy_tol = 0.0;   // mixed form: re-evaluate heavy samples in FP64 to this bound
     DevBuf part_det_abs, part_draw_abs, eabs, logf_save, summary2, ref_idx, ref_s, ref_c, ref_pos,
         ref_e;
@@ -381,6 +382,34 @@ int amp_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, RowSet rows, int64
     return NQS_OK;
 }
 
+// Site-synchronous sweeps, TL clusters and TR rows of one sample batch
+// (tensor-core path): boundary vectors and first-site families per sample,
+// then count the items per (step, group, sample), read the per-step group
+// bounds back, write the items, and one launch per site step.
+int site_tables(nqs_ctx* c, const FamArgs<float>& f, int nbb)
+{
+    const int K = f.K;
+    const int64_t ncnt = (int64_t)K * 8 * nbb;
+    TRY(ensure(c, c->site_cnt, (size_t)ncnt * 8));
+    TRY(ensure(c, c->site_offs, (size_t)(ncnt + 1) * 8));
+    TRY(ensure(c, c->site_bounds, ((size_t)K * 8 + 1) * 8));
+    SiteBufs sb{};
+    sb.counts = (int64_t*)c->site_cnt.p;
+    sb.offs = (int64_t*)c->site_offs.p;
+    sb.bounds = (int64_t*)c->site_bounds.p;
+    LAUNCH(NQS_STAGE_TABLES, fam_site_count(f, sb, nbb, c->stream));
+    std::vector<int64_t> bounds((size_t)K * 8 + 1);
+    CK(cudaMemcpyAsync(bounds.data(), c->site_bounds.p, bounds.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    TRY(ensure(c, c->site_items, (size_t)(bounds.back() + 1) * sizeof(SiteItem)));
+    sb.items = (SiteItem*)c->site_items.p;
+    LAUNCH(NQS_STAGE_TABLES, fam_site_fill(f, sb, nbb, c->stream));
+    for (int tau = 0; tau < K; ++tau)
+        LAUNCH(NQS_STAGE_TABLES, fam_site_step(f, sb, tau, bounds.data(), 4 * c->n_sm, c->stream));
+    CK(cudaGetLastError());
+    return NQS_OK;
+}
+
 // Shared-prefix amplitudes of the deterministic and drawn rows (chain ansatz),
 // samples processed in batches whose tables fit the memory budget.
 template <typename T>
@@ -500,7 +529,9 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
         stage_begin(c, NQS_STAGE_TABLES);
         CK(cudaMemsetAsync(c->ftl_end.p, 0xff, (size_t)nbb * nk * 4, c->stream));
         CK(cudaMemsetAsync(c->ftr_idx.p, 0, (size_t)nbb * nk * 4, c->stream));
-        LAUNCH(NQS_STAGE_TABLES, fam_launch_sweep<T>(f, nbb, c->stream));
+        // tensor-core path: the sweeps run with TL and TR, site-synchronously, below
+        const bool site = std::is_same<T, float>::value && f.tc;
+        if (!site) LAUNCH(NQS_STAGE_TABLES, fam_launch_sweep<T>(f, nbb, c->stream));
         LAUNCH(NQS_STAGE_TABLES, fam_launch_mark<T>(f, rd, nbb, c->stream));
         if (n_draws > 0) LAUNCH(NQS_STAGE_TABLES, fam_launch_mark<T>(f, rs, nbb, c->stream));
         LAUNCH(NQS_STAGE_TABLES, fam_launch_compact<T>(f, nbb, c->stream));
@@ -544,7 +575,13 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
         f.rbl = (T*)c->frbl.p; f.rbr = (T*)c->frbr.p;
         f.rbl_base = (const int64_t*)c->frbl_base.p;
         f.rbr_base = (const int64_t*)c->frbr_base.p;
-        LAUNCH(NQS_STAGE_TABLES, fam_launch_tables<T>(f, nbb, c->stream));
+        if constexpr (std::is_same<T, float>::value) {
+            if (site) {
+                TRY(site_tables(c, f, nbb));
+                LAUNCH(NQS_STAGE_TABLES, fam_launch_rbm<T>(f, nbb, c->stream));
+            }
+        }
+        if (!site) LAUNCH(NQS_STAGE_TABLES, fam_launch_tables<T>(f, nbb, c->stream));
         stage_end(c, NQS_STAGE_TABLES);
         stage_begin(c, NQS_STAGE_AMP_DET);
         const int64_t det_rows = c->det_off_h[s1] - c->det_off_h[s0];
@@ -610,7 +647,8 @@ extern "C" int nqs_destroy(nqs_ctx* c)
                       &c->ftl_list, &c->ftr_list, &c->ftl_cnt, &c->frbl, &c->frbr, &c->frbl_base,
                       &c->frbr_base, &c->tc_img, &c->tc_exps, &c->part_det_abs,
                       &c->part_draw_abs, &c->eabs, &c->logf_save, &c->summary2, &c->ref_idx,
-                      &c->ref_s, &c->ref_c, &c->ref_pos, &c->ref_e, &c->h_all};
+                      &c->ref_s, &c->ref_c, &c->ref_pos, &c->ref_e, &c->h_all, &c->site_cnt,
+                      &c->site_offs, &c->site_bounds, &c->site_items};
     for (DevBuf* b : bufs) release(*b);
     for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);

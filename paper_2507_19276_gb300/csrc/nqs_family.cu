@@ -148,6 +148,144 @@ __device__ __forceinline__ bool use_tc(const FamArgs<T>& f)
     return std::is_same<T, float>::value && f.tc;
 }
 
+// One tensor-core batch (T = float) of n <= 128 rows through the matrix image
+// `mat`: y_r = M x_r with x_r = acc.src(r), y_r rescaled by a power of two and
+// written to acc.dst(r), acc.set_exp(r, e) receiving the exponent added (the
+// row's power of two plus the image's). Row sources and destinations come
+// from the accessor, so the per-sample kernels and the site-synchronous
+// kernel share the arithmetic (results per row do not depend on the batch).
+template <class Acc>
+__device__ void tc_apply(const FamArgs<float>& f, BatchSmem<float>& sm, const Acc& acc, int n, int mat)
+{
+    const int D = f.D;
+    // The reduction runs over D / KC chunks of KC columns (one chunk up to
+    // D = 128): per chunk the batch rows' columns are gathered and split
+    // into FP16 hi / lo, the matrix image's chunk is staged, and the MMAs
+    // accumulate into the same tensor-memory columns.
+    const int KC = fam_tc_kc(D), nck = D / KC;
+    const int cpr = KC >> 3;                      // 8-element units per row of a chunk
+    const int nun = n * cpr;
+    bool ok = true;
+    for (int ck = 0; ck < nck; ++ck) {
+        // gather: each thread takes up to 2 units per round and issues all
+        // their loads before splitting any (latency-bound otherwise)
+        for (int u0 = 0; u0 < nun; u0 += 2 * blockDim.x) {
+            float4 v4[2][2];
+            #pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int u = u0 + k * blockDim.x + threadIdx.x;
+                if (u < nun) {
+                    const int r = u / cpr, c = u - r * cpr;
+                    const float4* p = (const float4*)(acc.src(r) + ck * KC + 8 * c);
+                    v4[k][0] = p[0];
+                    v4[k][1] = p[1];
+                }
+            }
+            #pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int u = u0 + k * blockDim.x + threadIdx.x;
+                if (u < nun) {
+                    const int r = u / cpr, c = u - r * cpr;
+                    const float xs[8] = {v4[k][0].x, v4[k][0].y, v4[k][0].z, v4[k][0].w,
+                                         v4[k][1].x, v4[k][1].y, v4[k][1].z, v4[k][1].w};
+                    __align__(16) __half hi[8], lo[8];
+                    #pragma unroll
+                    for (int j = 0; j < 8; ++j) tc::split_half(xs[j], hi[j], lo[j]);
+                    const uint32_t off = tc::op_offset(r, 8 * c, KC);
+                    *(uint4*)(sm.Ah + off) = *(const uint4*)hi;
+                    *(uint4*)(sm.Al + off) = *(const uint4*)lo;
+                }
+            }
+        }
+        // the image chunk (kept across batches when one chunk holds the matrix)
+        if (nck > 1 || mat != sm.cur_mat) {
+            const int nimg = 4 * D * KC / 16;
+            const uint4* __restrict__ g = f.tc_mats + (size_t)mat * (4 * D * D / 16) + (size_t)ck * nimg;
+            uint4* d = (uint4*)sm.Bh;
+            for (int i0 = 0; i0 < nimg; i0 += 4 * blockDim.x) {
+                uint4 w[4];
+                #pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int i = i0 + k * blockDim.x + threadIdx.x;
+                    if (i < nimg) w[k] = __ldg(g + i);
+                }
+                #pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int i = i0 + k * blockDim.x + threadIdx.x;
+                    if (i < nimg) d[i] = w[k];
+                }
+            }
+            sm.cur_mat = nck > 1 ? -1 : mat;
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc::fence_after_sync();
+            const uint32_t idesc = tc::idesc_f16(128, D);
+            const uint32_t lbo = 128, sbo = 16 * KC;
+            const unsigned char* Bl = sm.Bh + 2 * D * KC;
+            const unsigned char* As[3] = {sm.Ah, sm.Al, sm.Ah};
+            const unsigned char* Bs[3] = {sm.Bh, sm.Bh, Bl};
+            uint32_t acc = ck > 0 ? 1u : 0u;
+            for (int term = 0; term < 3; ++term)
+                for (int ks = 0; ks < KC / 16; ++ks) {
+                    tc::mma_f16(sm.tmem, tc::desc(tc::smem_addr(As[term]) + ks * 256, lbo, sbo),
+                                tc::desc(tc::smem_addr(Bs[term]) + ks * 256, lbo, sbo), idesc, acc);
+                    acc = 1;
+                }
+            tc::mma_commit(sm.mbar);
+        }
+        // the chunk's operands may be overwritten once its MMAs are done
+        ok = tc::mbar_wait(sm.mbar, sm.phase, 1u << 24) && ok;
+        sm.phase ^= 1u;
+        tc::fence_after_sync();
+    }
+    if (!ok && threadIdx.x == 0) report(f.err, 5, 4, (long long)f.s0);
+    // tensor memory -> registers, twice (row maximum, then the scaled row), 8
+    // columns at a time so that nothing indexed by D lives in local memory.
+    // Warp w reads lanes 32 (w % 4) .. +31 and half (w / 4) of the columns.
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = warp & 3, h = warp >> 2, half = D >> 1;
+    const int r = 32 * q + lane;
+    const uint32_t trow = sm.tmem + ((uint32_t)(32 * q) << 16) + h * half;
+    if (warp < 8) {
+        float m = 0.f;
+        for (int c0 = 0; c0 < half; c0 += 8) {
+            float v[8];
+            tc::tmem_ld8(trow + c0, v);
+            tc::tmem_wait_ld();
+            #pragma unroll
+            for (int j = 0; j < 8; ++j) m = fmaxf(m, fabsf(v[j]));
+        }
+        sm.rmax[h * 128 + r] = m;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp < 8) {
+        const float mm = fmaxf(sm.rmax[r], sm.rmax[128 + r]);
+        int e = 0;
+        if (mm > 0.f) frexpf(mm, &e);
+        float* o = acc.dst(r < n ? r : 0) + h * half;
+        for (int c0 = 0; c0 < half; c0 += 8) {
+            float v[8];
+            tc::tmem_ld8(trow + c0, v);     // every lane of the warp takes part
+            tc::tmem_wait_ld();
+            if (r < n) {
+                float4 w0, w1;
+                w0.x = ldexpf(v[0], -e); w0.y = ldexpf(v[1], -e); w0.z = ldexpf(v[2], -e); w0.w = ldexpf(v[3], -e);
+                w1.x = ldexpf(v[4], -e); w1.y = ldexpf(v[5], -e); w1.z = ldexpf(v[6], -e); w1.w = ldexpf(v[7], -e);
+                *(float4*)(o + c0) = w0;
+                *(float4*)(o + c0 + 4) = w1;
+            }
+        }
+        if (h == 0 && r < n) acc.set_exp(r, e + f.tc_exp[mat]);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+}
+
 template <typename T>
 __device__ void batch_apply(const FamArgs<T>& f, BatchSmem<T>& sm, const T* src, const int* soff,
                             T* dst, const int* doff, int* eo, int n, int side, int t, int sg)
@@ -173,133 +311,13 @@ __device__ void batch_apply(const FamArgs<T>& f, BatchSmem<T>& sm, const T* src,
     }
     // ---- tensor-core path (T = float) ----
     if constexpr (std::is_same<T, float>::value) {
-        // The reduction runs over D / KC chunks of KC columns (one chunk up to
-        // D = 128): per chunk the batch rows' columns are gathered and split
-        // into FP16 hi / lo, the matrix image's chunk is staged, and the MMAs
-        // accumulate into the same tensor-memory columns.
-        const int KC = fam_tc_kc(D), nck = D / KC;
-        const int mat = (side * f.K + t) * 4 + sg;
-        const int cpr = KC >> 3;                      // 8-element units per row of a chunk
-        const int nun = n * cpr;
-        bool ok = true;
-        for (int ck = 0; ck < nck; ++ck) {
-            // gather: each thread takes up to 2 units per round and issues all
-            // their loads before splitting any (latency-bound otherwise)
-            for (int u0 = 0; u0 < nun; u0 += 2 * blockDim.x) {
-                float4 v4[2][2];
-                #pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const int u = u0 + k * blockDim.x + threadIdx.x;
-                    if (u < nun) {
-                        const int r = u / cpr, c = u - r * cpr;
-                        const float4* p = (const float4*)((const float*)src + (size_t)soff[r] * D + ck * KC + 8 * c);
-                        v4[k][0] = p[0];
-                        v4[k][1] = p[1];
-                    }
-                }
-                #pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const int u = u0 + k * blockDim.x + threadIdx.x;
-                    if (u < nun) {
-                        const int r = u / cpr, c = u - r * cpr;
-                        const float xs[8] = {v4[k][0].x, v4[k][0].y, v4[k][0].z, v4[k][0].w,
-                                             v4[k][1].x, v4[k][1].y, v4[k][1].z, v4[k][1].w};
-                        __align__(16) __half hi[8], lo[8];
-                        #pragma unroll
-                        for (int j = 0; j < 8; ++j) tc::split_half(xs[j], hi[j], lo[j]);
-                        const uint32_t off = tc::op_offset(r, 8 * c, KC);
-                        *(uint4*)(sm.Ah + off) = *(const uint4*)hi;
-                        *(uint4*)(sm.Al + off) = *(const uint4*)lo;
-                    }
-                }
-            }
-            // the image chunk (kept across batches when one chunk holds the matrix)
-            if (nck > 1 || mat != sm.cur_mat) {
-                const int nimg = 4 * D * KC / 16;
-                const uint4* __restrict__ g = f.tc_mats + (size_t)mat * (4 * D * D / 16) + (size_t)ck * nimg;
-                uint4* d = (uint4*)sm.Bh;
-                for (int i0 = 0; i0 < nimg; i0 += 4 * blockDim.x) {
-                    uint4 w[4];
-                    #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int i = i0 + k * blockDim.x + threadIdx.x;
-                        if (i < nimg) w[k] = __ldg(g + i);
-                    }
-                    #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int i = i0 + k * blockDim.x + threadIdx.x;
-                        if (i < nimg) d[i] = w[k];
-                    }
-                }
-                sm.cur_mat = nck > 1 ? -1 : mat;
-            }
-            tc::fence_proxy_async();
-            tc::fence_before_sync();
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                tc::fence_after_sync();
-                const uint32_t idesc = tc::idesc_f16(128, D);
-                const uint32_t lbo = 128, sbo = 16 * KC;
-                const unsigned char* Bl = sm.Bh + 2 * D * KC;
-                const unsigned char* As[3] = {sm.Ah, sm.Al, sm.Ah};
-                const unsigned char* Bs[3] = {sm.Bh, sm.Bh, Bl};
-                uint32_t acc = ck > 0 ? 1u : 0u;
-                for (int term = 0; term < 3; ++term)
-                    for (int ks = 0; ks < KC / 16; ++ks) {
-                        tc::mma_f16(sm.tmem, tc::desc(tc::smem_addr(As[term]) + ks * 256, lbo, sbo),
-                                    tc::desc(tc::smem_addr(Bs[term]) + ks * 256, lbo, sbo), idesc, acc);
-                        acc = 1;
-                    }
-                tc::mma_commit(sm.mbar);
-            }
-            // the chunk's operands may be overwritten once its MMAs are done
-            ok = tc::mbar_wait(sm.mbar, sm.phase, 1u << 24) && ok;
-            sm.phase ^= 1u;
-            tc::fence_after_sync();
-        }
-        if (!ok && threadIdx.x == 0) report(f.err, 5, 4, (long long)f.s0);
-        // tensor memory -> registers, twice (row maximum, then the scaled row), 8
-        // columns at a time so that nothing indexed by D lives in local memory.
-        // Warp w reads lanes 32 (w % 4) .. +31 and half (w / 4) of the columns.
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int q = warp & 3, h = warp >> 2, half = D >> 1;
-        const int r = 32 * q + lane;
-        const uint32_t trow = sm.tmem + ((uint32_t)(32 * q) << 16) + h * half;
-        if (warp < 8) {
-            float m = 0.f;
-            for (int c0 = 0; c0 < half; c0 += 8) {
-                float v[8];
-                tc::tmem_ld8(trow + c0, v);
-                tc::tmem_wait_ld();
-                #pragma unroll
-                for (int j = 0; j < 8; ++j) m = fmaxf(m, fabsf(v[j]));
-            }
-            sm.rmax[h * 128 + r] = m;
-        }
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (warp < 8) {
-            const float mm = fmaxf(sm.rmax[r], sm.rmax[128 + r]);
-            int e = 0;
-            if (mm > 0.f) frexpf(mm, &e);
-            float* o = (float*)dst + (size_t)(r < n ? doff[r] : 0) * D + h * half;
-            for (int c0 = 0; c0 < half; c0 += 8) {
-                float v[8];
-                tc::tmem_ld8(trow + c0, v);     // every lane of the warp takes part
-                tc::tmem_wait_ld();
-                if (r < n) {
-                    float4 w0, w1;
-                    w0.x = ldexpf(v[0], -e); w0.y = ldexpf(v[1], -e); w0.z = ldexpf(v[2], -e); w0.w = ldexpf(v[3], -e);
-                    w1.x = ldexpf(v[4], -e); w1.y = ldexpf(v[5], -e); w1.z = ldexpf(v[6], -e); w1.w = ldexpf(v[7], -e);
-                    *(float4*)(o + c0) = w0;
-                    *(float4*)(o + c0 + 4) = w1;
-                }
-            }
-            if (h == 0 && r < n) eo[r] = e + f.tc_exp[mat];
-        }
-        tc::fence_before_sync();
-        __syncthreads();
+        struct Acc {
+            const float* s; const int* so; float* d; const int* dof; int* e; int D;
+            __device__ const float* src(int r) const { return s + (size_t)so[r] * D; }
+            __device__ float* dst(int r) const { return d + (size_t)dof[r] * D; }
+            __device__ void set_exp(int r, int x) const { e[r] = x; }
+        } acc{(const float*)src, soff, (float*)dst, doff, eo, D};
+        tc_apply(f, sm, acc, n, (side * f.K + t) * 4 + sg);
     }
 }
 
@@ -806,6 +824,220 @@ __global__ void k_fam_rbm(FamArgs<T> f)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Site-synchronous tables (tensor-core path). Step tau advances the left side
+// through site tau and the right side through site K-1-tau for every sample
+// of the batch at once; the items of a step read only what earlier steps wrote.
+// Groups: g = side * 4 + sigma, the local state whose matrix the item applies.
+// ---------------------------------------------------------------------------
+
+template <bool FILL>
+__global__ void __launch_bounds__(256) k_site_build(FamArgs<float> f, SiteBufs sb)
+{
+    __shared__ int cnt[kMaxOrb * 8];               // counts, then fill cursors
+    __shared__ int own[kMaxOrb];
+    const int b = blockIdx.x, K = f.K, D = f.D;
+    const int nbb = (int)(f.s1 - f.s0);
+    const int64_t s = f.s0 + b;
+    const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
+    for (int i = threadIdx.x; i < K * 8; i += blockDim.x) cnt[i] = 0;
+    for (int i = threadIdx.x; i < K; i += blockDim.x) own[i] = sigma_at(na, nb, i);
+    __syncthreads();
+    const size_t nk = (size_t)K * K * 9;
+    float* Gb = f.G + (size_t)b * 3 * K * K * D;
+    int* Geb = f.Ge + (size_t)b * 3 * K * K;
+    float* Hb = f.H + (size_t)b * 3 * K * K * D;
+    int* Heb = f.He + (size_t)b * 3 * K * K;
+    auto put = [&](int tau, int g, const float* src, const int* se, float* dst, int* de) {
+        const int slot = atomicAdd(&cnt[tau * 8 + g], 1);
+        if (FILL) {
+            const int64_t at = sb.offs[((int64_t)tau * 8 + g) * nbb + b] + slot;
+            SiteItem it;
+            it.src = src; it.dst = dst; it.se = se; it.de = de;
+            sb.items[at] = it;
+        }
+    };
+    // (1) families created before the step (k_site_boundary makes the new ones
+    // at their first site): thread per (step, side)
+    for (int w = threadIdx.x; w < 2 * K; w += blockDim.x) {
+        const int tau = w >> 1, side = w & 1;
+        const int t = side == 0 ? tau : K - 1 - tau;
+        const int o = own[t];
+        float* Tb = side == 0 ? Gb : Hb;
+        int* Te = side == 0 ? Geb : Heb;
+        const int tp = side == 0 ? t - 1 : t + 1;      // the family's previous site
+        for (int j = 0; j < tau; ++j) {
+            const int sf = side == 0 ? j : K - 1 - j;
+            for (int a = 0; a < 3; ++a) {
+                const size_t base = ((size_t)a * K + sf) * K;
+                put(tau, side * 4 + o, Tb + (base + tp) * D, Te + base + tp, Tb + (base + t) * D, Te + base + t);
+            }
+        }
+    }
+    // (2) TL clusters: creation at s2 with A_{s2}^{a2}, then A_t^{own} up to the last use
+    const int ncl = f.tl_count[b];
+    const int* tll = f.tl_list + (size_t)b * nk;
+    float* TLb = f.TL + (size_t)f.tl_base[b] * D;
+    int* TLeb = f.TLe + f.tl_base[b];
+    for (int c = threadIdx.x; c < ncl; c += blockDim.x) {
+        const int key = tll[c];
+        int s2, a2, s1, a1;
+        key_fields(K, key, s2, a2, s1, a1);
+        const int off = f.tl_idx[(size_t)b * nk + key];
+        const int end = f.tl_end[(size_t)b * nk + key];
+        const size_t gi = ((size_t)a1 * K + s1) * K + (s2 - 1);
+        put(s2, sig_of_alt(a2, own[s2]), Gb + gi * D, Geb + gi, TLb + (size_t)off * D, TLeb + off);
+        for (int t = s2 + 1; t <= end; ++t) {
+            const int q = off + (t - s2);
+            put(t, own[t], TLb + (size_t)(q - 1) * D, TLeb + q - 1, TLb + (size_t)q * D, TLeb + q);
+        }
+    }
+    // (3) TR rows: H_{sB,aB}(sA+1) A_{sA}^{aA} at the right step of site sA
+    const int ntr = f.tr_total[b];
+    const int* trl = f.tr_list + (size_t)b * nk;
+    float* TRb = f.TR + (size_t)f.tr_base[b] * D;
+    int* TReb = f.TRe + f.tr_base[b];
+    for (int i = threadIdx.x; i < ntr; i += blockDim.x) {
+        const int key = trl[i];
+        int sA, aA, sB, aB;
+        key_fields(K, key, sA, aA, sB, aB);
+        const size_t hi = ((size_t)aB * K + sB) * K + sA + 1;
+        put(K - 1 - sA, 4 + sig_of_alt(aA, own[sA]), Hb + hi * D, Heb + hi, TRb + (size_t)i * D, TReb + i);
+    }
+    if (!FILL) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < K * 8; i += blockDim.x)
+            sb.counts[(int64_t)i * nbb + b] = cnt[i];
+    }
+}
+
+// Boundary vectors L_t (R_t) of each sample and side and the three families
+// that start at each site, on the CUDA cores in FP32 (the arithmetic of the
+// per-sample sweep): one block per (sample, side), steps in order.
+__global__ void __launch_bounds__(256) k_site_boundary(FamArgs<float> f)
+{
+    extern __shared__ __align__(16) unsigned char smb[];
+    __shared__ int eo[4];
+    __shared__ int eL;
+    const int b = blockIdx.x >> 1, side = blockIdx.x & 1, K = f.K, D = f.D;
+    float* X = (float*)smb;                       // [D]
+    float* Y = X + D;                             // [4][D]
+    const int64_t s = f.s0 + b;
+    const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
+    float* Tb = (side == 0 ? f.G : f.H) + (size_t)b * 3 * K * K * D;
+    int* Te = (side == 0 ? f.Ge : f.He) + (size_t)b * 3 * K * K;
+    const float* Mats = side == 0 ? f.AT : f.A;   // column convention left, row vectors right
+    for (int c = threadIdx.x; c < D; c += blockDim.x) X[c] = c == 0 ? 1.f : 0.f;
+    if (threadIdx.x == 0) eL = 0;
+    __syncthreads();
+    for (int step = 0; step < K; ++step) {
+        const int t = side == 0 ? step : K - 1 - step;
+        const int own = sigma_at(na, nb, t);
+        for (int a = 0; a < 4; ++a) {
+            const int sg = a == 3 ? own : sig_of_alt(a, own);
+            mv_block<float>(Mats + ((size_t)t * 4 + sg) * D * D, D, X, Y + (size_t)a * D, 1);
+        }
+        __syncthreads();
+        renorm_rows<float>(Y, D, 4, eo);
+        __syncthreads();
+        const int e_in = eL;
+        for (int q = threadIdx.x; q < 3 * D; q += blockDim.x) {
+            const int a = q / D, c = q - a * D;
+            Tb[(((size_t)a * K + t) * K + t) * D + c] = Y[q];
+        }
+        for (int a = threadIdx.x; a < 3; a += blockDim.x) Te[((size_t)a * K + t) * K + t] = e_in + eo[a];
+        for (int c = threadIdx.x; c < D; c += blockDim.x) X[c] = Y[3 * D + c];
+        __syncthreads();
+        if (threadIdx.x == 0) eL = e_in + eo[3];
+        __syncthreads();
+    }
+}
+
+// first item of every (step, group): bounds[i] = offs[i * nbb], bounds[K*8] = total
+__global__ void k_site_bounds(const int64_t* offs, int n, int nbb, int64_t* bounds)
+{
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) bounds[i] = offs[(int64_t)i * nbb];
+}
+
+struct SiteStep {
+    int64_t gbeg[8], gend[8];   // item range of each group
+    int tbeg[9];                // first tile of each group; tbeg[8] = tiles of the step
+    int mat[8];                 // matrix image of each group
+};
+
+__global__ void __launch_bounds__(256, 4) k_site_tiles(FamArgs<float> f, const SiteItem* items, SiteStep st)
+{
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ const float* s_src[128];
+    __shared__ float* s_dst[128];
+    __shared__ const int* s_se[128];
+    __shared__ int* s_de[128];
+    BatchSmem<float> sm;
+    batch_init(f, sm, smraw, &tmem_slot, &mbar, false);
+    struct Acc {
+        const float* const* s; float* const* d; const int* const* se; int* const* de;
+        __device__ const float* src(int r) const { return s[r]; }
+        __device__ float* dst(int r) const { return d[r]; }
+        __device__ void set_exp(int r, int x) const { *de[r] = *se[r] + x; }
+    } acc{s_src, s_dst, s_se, s_de};
+    const int ntiles = st.tbeg[8];
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int g = 0;
+        while (g < 7 && tile >= st.tbeg[g + 1]) ++g;
+        const int64_t i0 = st.gbeg[g] + (int64_t)(tile - st.tbeg[g]) * 128;
+        const int64_t left = st.gend[g] - i0;
+        const int n = (int)(left < 128 ? left : 128);
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+            const SiteItem it = items[i0 + r];
+            s_src[r] = it.src; s_dst[r] = it.dst; s_se[r] = it.se; s_de[r] = it.de;
+        }
+        __syncthreads();
+        tc_apply(f, sm, acc, n, st.mat[g]);          // ends with a block barrier
+    }
+    batch_fini(f, sm);
+}
+
+int fam_site_count(const FamArgs<float>& f, const SiteBufs& b, int nbb, cudaStream_t st)
+{
+    const int n = f.K * 8;
+    k_site_boundary<<<nbb * 2, 256, (size_t)5 * f.D * sizeof(float), st>>>(f);
+    k_site_build<false><<<nbb, 256, 0, st>>>(f, b);
+    launch_scan_i64(b.counts, b.offs, (int64_t)n * nbb, st);
+    k_site_bounds<<<1, 256, 0, st>>>(b.offs, n, nbb, b.bounds);
+    return 4;
+}
+
+int fam_site_fill(const FamArgs<float>& f, const SiteBufs& b, int nbb, cudaStream_t st)
+{
+    k_site_build<true><<<nbb, 256, 0, st>>>(f, b);
+    return 1;
+}
+
+int fam_site_step(const FamArgs<float>& f, const SiteBufs& b, int tau, const int64_t* bounds,
+                  int max_ctas, cudaStream_t st)
+{
+    SiteStep ss{};
+    int tiles = 0;
+    for (int g = 0; g < 8; ++g) {
+        ss.gbeg[g] = bounds[tau * 8 + g];
+        ss.gend[g] = bounds[tau * 8 + g + 1];
+        ss.tbeg[g] = tiles;
+        tiles += (int)((ss.gend[g] - ss.gbeg[g] + 127) / 128);
+        const int side = g >> 2;
+        const int t = side == 0 ? tau : f.K - 1 - tau;
+        ss.mat[g] = (side * f.K + t) * 4 + (g & 3);
+    }
+    ss.tbeg[8] = tiles;
+    if (tiles == 0) return 0;
+    const size_t smem = f.batch_bytes - fam_small_bytes(f.D, sizeof(float), true);
+    allow_max_smem(k_site_tiles);
+    const int grid = tiles < max_ctas ? tiles : max_ctas;
+    k_site_tiles<<<grid, 256, smem, st>>>(f, b.items, ss);
+    return 1;
+}
+
 // F5: psi_TN(m) as a dot product of a left state and a right covector, the
 // factorised correlator ratio, coefficient x ratio; block partial sums in a
 // fixed order. Each lane decodes one row; then each warp evaluates its 32 rows
@@ -1072,6 +1304,15 @@ int fam_launch_tables(const FamArgs<T>& f, int nb, cudaStream_t st)
 }
 
 template <typename T>
+int fam_launch_rbm(const FamArgs<T>& f, int nb, cudaStream_t st)
+{
+    if (f.n_hidden <= 0) return 0;
+    dim3 grid(8 * f.split, nb);
+    k_fam_rbm<T><<<grid, 256, 2 * f.n_hidden * sizeof(T), st>>>(f);
+    return 1;
+}
+
+template <typename T>
 int fam_launch_rows(const FamArgs<T>& f, const RowSet& rows, int64_t grid, double* partial,
                     int64_t* span, double* partial_abs, cudaStream_t st)
 {
@@ -1119,6 +1360,7 @@ void fam_tc_images(const double* A, int K, int D, std::vector<unsigned char>& im
     template int fam_launch_mark<T>(const FamArgs<T>&, const RowSet&, int, cudaStream_t);  \
     template int fam_launch_compact<T>(const FamArgs<T>&, int, cudaStream_t);              \
     template int fam_launch_tables<T>(const FamArgs<T>&, int, cudaStream_t);               \
+    template int fam_launch_rbm<T>(const FamArgs<T>&, int, cudaStream_t);                  \
     template int fam_launch_rows<T>(const FamArgs<T>&, const RowSet&, int64_t, double*,    \
                                     int64_t*, double*, cudaStream_t);
 NQS_FAM_INST(float)

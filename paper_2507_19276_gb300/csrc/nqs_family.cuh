@@ -59,6 +59,37 @@ template <typename T> int fam_launch_rows(const FamArgs<T>& f, const RowSet& row
                                           double* partial, int64_t* span, double* partial_abs,
                                           cudaStream_t st);
 
+// ---- site-synchronous tables (tensor-core path) ----------------------------
+// The boundary vectors and the families at their first site are formed per
+// sample on the CUDA cores (FP32, as in the per-sample sweep); every other
+// vector update of the tables of a sample batch -- one-change families past
+// their first site, TL creation and propagation, TR rows -- is one item. The
+// items of site step tau fall into 8 groups (side x local state of the
+// matrix), each one matrix image, and one launch per step runs 128-row tiles
+// over all samples' items.
+struct SiteItem {
+    const float* src;   // input vector
+    float* dst;         // output vector
+    const int* se;      // input power-of-two exponent
+    int* de;            // output exponent (= input + the product's own)
+};
+struct SiteBufs {
+    int64_t* counts;    // [K][8][nbb] items per (step, group, sample)
+    int64_t* offs;      // [K*8*nbb + 1] exclusive prefix of counts
+    int64_t* bounds;    // [K*8 + 1] first item of each (step, group)
+    SiteItem* items;
+};
+// boundary vectors and first-site families, then the item counts, their
+// prefix and the (step, group) bounds (device); returns launches
+int fam_site_count(const FamArgs<float>& f, const SiteBufs& b, int nbb, cudaStream_t st);
+// write the items (after the counts)
+int fam_site_fill(const FamArgs<float>& f, const SiteBufs& b, int nbb, cudaStream_t st);
+// run the tiles of step tau; bounds: host copy of SiteBufs::bounds
+int fam_site_step(const FamArgs<float>& f, const SiteBufs& b, int tau, const int64_t* bounds,
+                  int max_ctas, cudaStream_t st);
+// the correlator factors alone (the site-synchronous path builds the tables)
+template <typename T> int fam_launch_rbm(const FamArgs<T>& f, int nb, cudaStream_t st);
+
 // shared memory of the batch buffers of the table kernels; the tensor-core
 // layout starts with a small scratch for the sweep's boundary vectors
 // (fam_small_bytes), which the other table kernels leave out
