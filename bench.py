@@ -309,8 +309,8 @@ def run(args):
         roof = {"bound": "tensor", "unit": "TFLOP/s", "achieved": achieved,
                 "peak": peaks["bf16_tflops_sustained"],
                 "peak_source": f"{src} dense bf16 (sustained; f16 has the same nominal rate)",
-                "kernel": "amplitude stage: k_fam_sweep, k_fam_mark, k_fam_compact, k_fam_tr, "
-                          "k_fam_tl (tcgen05), k_fam_rbm, k_fam_rows"}
+                "kernel": "amplitude stage: k_fam_mark, k_fam_compact, k_site_boundary, "
+                          "k_site_build, k_site_tiles (tcgen05), k_fam_rbm, k_fam_rows"}
     else:
         roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "peak_source": "FP64 FMA probe, measured",

@@ -386,7 +386,8 @@ int amp_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, RowSet rows, int64
 // (tensor-core path): boundary vectors and first-site families per sample,
 // then count the items per (step, group, sample), read the per-step group
 // bounds back, write the items, and one launch per site step.
-int site_tables(nqs_ctx* c, const FamArgs<float>& f, int nbb)
+template <typename T>
+int site_tables(nqs_ctx* c, const FamArgs<T>& f, int nbb)
 {
     const int K = f.K;
     const int64_t ncnt = (int64_t)K * 8 * nbb;
@@ -401,8 +402,8 @@ int site_tables(nqs_ctx* c, const FamArgs<float>& f, int nbb)
     std::vector<int64_t> bounds((size_t)K * 8 + 1);
     CK(cudaMemcpyAsync(bounds.data(), c->site_bounds.p, bounds.size() * 8, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    TRY(ensure(c, c->site_items, (size_t)(bounds.back() + 1) * sizeof(SiteItem)));
-    sb.items = (SiteItem*)c->site_items.p;
+    TRY(ensure(c, c->site_items, (size_t)(bounds.back() + 1) * sizeof(SiteItemT<T>)));
+    sb.items = c->site_items.p;
     LAUNCH(NQS_STAGE_TABLES, fam_site_fill(f, sb, nbb, c->stream));
     for (int tau = 0; tau < K; ++tau)
         LAUNCH(NQS_STAGE_TABLES, fam_site_step(f, sb, tau, bounds.data(), 4 * c->n_sm, c->stream));
@@ -467,7 +468,6 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
     f.h = c->hv;
     f.K = K;
     f.D = D;
-    f.threads = D > 256 ? D : 256;
     f.tc = (sizeof(T) == 4 && c->has_tc) ? 1 : 0;
     if (f.tc) {
         f.nmax = 128;                                  // one M = 128 tensor-core tile
@@ -512,7 +512,7 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
         f.s0 = s0;
         f.s1 = s1;
         // few samples (a small call, FP64 re-evaluation): spread each sample's
-        // tables over several blocks so that about two blocks per SM run
+        // correlator factors over several blocks so that about two blocks per SM run
         f.split = nbb >= 2 * c->n_sm ? 1 : std::min(32, (2 * c->n_sm + nbb - 1) / nbb);
         f.G = (T*)c->fG.p; f.Ge = (int*)c->fGe.p;
         f.H = (T*)c->fH.p; f.He = (int*)c->fHe.p;
@@ -529,9 +529,7 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
         stage_begin(c, NQS_STAGE_TABLES);
         CK(cudaMemsetAsync(c->ftl_end.p, 0xff, (size_t)nbb * nk * 4, c->stream));
         CK(cudaMemsetAsync(c->ftr_idx.p, 0, (size_t)nbb * nk * 4, c->stream));
-        // tensor-core path: the sweeps run with TL and TR, site-synchronously, below
-        const bool site = std::is_same<T, float>::value && f.tc;
-        if (!site) LAUNCH(NQS_STAGE_TABLES, fam_launch_sweep<T>(f, nbb, c->stream));
+        // (the sweeps run with TL and TR, site-synchronously, below)
         LAUNCH(NQS_STAGE_TABLES, fam_launch_mark<T>(f, rd, nbb, c->stream));
         if (n_draws > 0) LAUNCH(NQS_STAGE_TABLES, fam_launch_mark<T>(f, rs, nbb, c->stream));
         LAUNCH(NQS_STAGE_TABLES, fam_launch_compact<T>(f, nbb, c->stream));
@@ -575,13 +573,8 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
         f.rbl = (T*)c->frbl.p; f.rbr = (T*)c->frbr.p;
         f.rbl_base = (const int64_t*)c->frbl_base.p;
         f.rbr_base = (const int64_t*)c->frbr_base.p;
-        if constexpr (std::is_same<T, float>::value) {
-            if (site) {
-                TRY(site_tables(c, f, nbb));
-                LAUNCH(NQS_STAGE_TABLES, fam_launch_rbm<T>(f, nbb, c->stream));
-            }
-        }
-        if (!site) LAUNCH(NQS_STAGE_TABLES, fam_launch_tables<T>(f, nbb, c->stream));
+        TRY(site_tables(c, f, nbb));
+        LAUNCH(NQS_STAGE_TABLES, fam_launch_rbm<T>(f, nbb, c->stream));
         stage_end(c, NQS_STAGE_TABLES);
         stage_begin(c, NQS_STAGE_AMP_DET);
         const int64_t det_rows = c->det_off_h[s1] - c->det_off_h[s0];

@@ -121,13 +121,12 @@ __device__ __forceinline__ int tr_key(int K, int sA, int aA, int sB, int aB)
 }
 
 // ---------------------------------------------------------------------------
-// One batch of block-wide matrix-vector products y_i = M x_i (i < n):
-// x_i gathered from global memory, y_i rescaled by a power of two and
-// scattered back, eo[i] = the exponent added to y_i. M is A_t^{sg} (side 0,
-// column convention) or its transpose (side 1, row vectors).
-//  - FP32 with D a multiple of 16 up to 128: tcgen05 MMAs, M = 128 rows,
-//    N = K = D, operands split into FP16 hi + lo (x_hi M_hi + x_lo M_hi +
-//    x_hi M_lo), FP32 accumulation in tensor memory;
+// Batches of block-wide matrix-vector products y_i = M x_i: x_i gathered from
+// global memory, y_i rescaled by a power of two and scattered back. M is
+// A_t^{sg} (side 0, column convention) or its transpose (side 1, row vectors).
+//  - FP32 with tensor-core images: tcgen05 MMAs, M = 128 rows, N = D,
+//    operands split into FP16 hi + lo (x_hi M_hi + x_lo M_hi + x_hi M_lo),
+//    FP32 accumulation in tensor memory (tc_apply);
 //  - otherwise: shared-memory CUDA-core products (mv_block).
 // ---------------------------------------------------------------------------
 
@@ -287,52 +286,8 @@ __device__ void tc_apply(const FamArgs<float>& f, BatchSmem<float>& sm, const Ac
 }
 
 template <typename T>
-__device__ void batch_apply(const FamArgs<T>& f, BatchSmem<T>& sm, const T* src, const int* soff,
-                            T* dst, const int* doff, int* eo, int n, int side, int t, int sg)
-{
-    const int D = f.D;
-    if (!use_tc(f)) {
-        for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
-            const int i = q / D, c = q - i * D;
-            sm.X[q] = src[(size_t)soff[i] * D + c];
-        }
-        __syncthreads();
-        const T* M = (side == 0 ? f.AT : f.A) + ((size_t)t * 4 + sg) * D * D;
-        mv_block<T>(M, D, sm.X, sm.Y, n);
-        __syncthreads();
-        renorm_rows<T>(sm.Y, D, n, eo);
-        __syncthreads();
-        for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
-            const int i = q / D, c = q - i * D;
-            dst[(size_t)doff[i] * D + c] = sm.Y[q];
-        }
-        __syncthreads();
-        return;
-    }
-    // ---- tensor-core path (T = float) ----
-    if constexpr (std::is_same<T, float>::value) {
-        struct Acc {
-            const float* s; const int* so; float* d; const int* dof; int* e; int D;
-            __device__ const float* src(int r) const { return s + (size_t)so[r] * D; }
-            __device__ float* dst(int r) const { return d + (size_t)dof[r] * D; }
-            __device__ void set_exp(int r, int x) const { e[r] = x; }
-        } acc{(const float*)src, soff, (float*)dst, doff, eo, D};
-        tc_apply(f, sm, acc, n, (side * f.K + t) * 4 + sg);
-    }
-}
-
-// per-kernel setup / teardown of the tensor-core state
-// Shared-memory bytes of a kernel's batch buffers: the sweep keeps the small
-// scratch, the other table kernels start their buffers without it.
-template <typename T>
-__device__ __forceinline__ size_t batch_span(const FamArgs<T>& f, bool small)
-{
-    return f.batch_bytes - (small ? 0 : fam_small_bytes(f.D, sizeof(T), use_tc(f)));
-}
-
-template <typename T>
 __device__ void batch_init(const FamArgs<T>& f, BatchSmem<T>& sm, unsigned char* base, uint32_t* tmem_slot,
-                           uint64_t* mbar, bool small = true)
+                           uint64_t* mbar)
 {
     const int D = f.D;
     if (!use_tc(f)) {
@@ -340,9 +295,7 @@ __device__ void batch_init(const FamArgs<T>& f, BatchSmem<T>& sm, unsigned char*
         sm.Y = sm.X + (size_t)f.nmax * D;
         return;
     }
-    sm.X = (T*)base;                              // small scratch for the sweep's boundary vectors
-    sm.Y = sm.X + (size_t)4 * D;
-    unsigned char* p = base + (small ? fam_small_bytes(D, sizeof(T), true) : 0);
+    unsigned char* p = base;
     const size_t kc = (size_t)fam_tc_kc(D);
     sm.Ah = p; p += (size_t)128 * kc * 2;
     sm.Al = p; p += (size_t)128 * kc * 2;
@@ -380,89 +333,6 @@ __device__ __forceinline__ void key_fields(int K, int key, int& site_hi, int& al
 
 // padded correlator-factor row lengths (multiples of 4 elements)
 __device__ __forceinline__ int nh_pad(int NH) { return (NH + 3) & ~3; }
-
-// ---------------------------------------------------------------------------
-// F1: left and right family sweeps, f.split blocks per sample and side. L (or
-// R) stays in shared memory (each block forms it); block g owns the families
-// created at steps j = g, g + split, ... and reads them back in batches.
-// ---------------------------------------------------------------------------
-
-template <typename T>
-__global__ void __launch_bounds__(256, 3) k_fam_sweep(FamArgs<T> f)
-{
-    extern __shared__ __align__(1024) unsigned char smraw[];
-    __shared__ uint32_t tmem_slot;
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ int eL;
-    BatchSmem<T> sm;
-    batch_init(f, sm, smraw, &tmem_slot, &mbar);
-    int* eo = (int*)(smraw + f.batch_bytes);     // [nmax]
-    int* pos = eo + f.nmax;                       // [nmax]
-    int* soff = pos + f.nmax;                     // [nmax]
-    int* doff = soff + f.nmax;                    // [nmax]
-    T* Lv = (T*)(doff + f.nmax);                  // [D]
-    const int G = f.split;
-    const int b = blockIdx.x / (2 * G), side = (blockIdx.x / G) & 1, g = blockIdx.x % G;
-    const int K = f.K, D = f.D;
-    const int64_t s = f.s0 + b;
-    const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
-    T* X = sm.X;
-    T* Y = sm.Y;
-    {
-        T* Tb = (side == 0 ? f.G : f.H) + (size_t)b * 3 * K * K * D;
-        int* Te = (side == 0 ? f.Ge : f.He) + (size_t)b * 3 * K * K;
-        const T* Mats = side == 0 ? f.AT : f.A;   // column convention left, row vectors right
-        for (int c = threadIdx.x; c < D; c += blockDim.x) Lv[c] = c == 0 ? T(1) : T(0);
-        if (threadIdx.x == 0) eL = 0;
-        __syncthreads();
-        for (int step = 0; step < K; ++step) {
-            const int t = side == 0 ? step : K - 1 - step;
-            const int own = sigma_at(na, nb, t);
-            // (a) the boundary vector and the three families that start at t
-            for (int q = threadIdx.x; q < D; q += blockDim.x) X[q] = Lv[q];
-            __syncthreads();
-            for (int a = 0; a < 4; ++a) {
-                const int sg = a == 3 ? own : sig_of_alt(a, own);
-                mv_block<T>(Mats + ((size_t)t * 4 + sg) * D * D, D, X, Y + (size_t)a * D, 1);
-            }
-            __syncthreads();
-            renorm_rows<T>(Y, D, 4, eo);
-            __syncthreads();
-            const int e_in = eL;
-            const int eL_new = e_in + eo[3];
-            if (step % G == g) {
-                for (int q = threadIdx.x; q < 3 * D; q += blockDim.x) {
-                    const int a = q / D, c = q - a * D;
-                    Tb[(((size_t)a * K + t) * K + t) * D + c] = Y[q];
-                }
-                for (int a = threadIdx.x; a < 3; a += blockDim.x) Te[((size_t)a * K + t) * K + t] = e_in + eo[a];
-            }
-            for (int c = threadIdx.x; c < D; c += blockDim.x) Lv[c] = Y[3 * D + c];
-            __syncthreads();
-            if (threadIdx.x == 0) eL = eL_new;
-            // (b) this block's existing families: created at steps j < step, j = g mod G
-            const int nfam = 3 * (step > g ? (step - 1 - g) / G + 1 : 0);
-            const int tprev = side == 0 ? t - 1 : t + 1;
-            for (int c0 = 0; c0 < nfam; c0 += f.nmax) {
-                const int n = nfam - c0 < f.nmax ? nfam - c0 : f.nmax;
-                for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                    const int j = g + ((c0 + i) / 3) * G, a = (c0 + i) % 3;
-                    const int sf = side == 0 ? j : K - 1 - j;
-                    pos[i] = (a * K + sf) * K;
-                    soff[i] = pos[i] + tprev;
-                    doff[i] = pos[i] + t;
-                }
-                __syncthreads();
-                batch_apply<T>(f, sm, Tb, soff, Tb, doff, eo, n, side, t, own);
-                for (int i = threadIdx.x; i < n; i += blockDim.x)
-                    Te[pos[i] + t] = Te[pos[i] + tprev] + eo[i];
-                __syncthreads();
-            }
-        }
-        __syncthreads();
-    }
-    batch_fini(f, sm);
-}
 
 // ---------------------------------------------------------------------------
 // Row decomposition (shared by the marking and the evaluation passes)
@@ -592,156 +462,6 @@ __global__ void k_fam_compact(FamArgs<T> f)
     }
 }
 
-// F4a: TR_{sA aA, sB aB} = H_{sB,aB}(sA+1) A_{sA}^{aA}; the TR list is in key
-// order, i.e. grouped by (sA, aA): one matrix per run.
-template <typename T>
-__global__ void __launch_bounds__(256, 4) k_fam_tr(FamArgs<T> f)
-{
-    extern __shared__ __align__(1024) unsigned char smraw[];
-    __shared__ uint32_t tmem_slot;
-    __shared__ __align__(8) uint64_t mbar;
-    BatchSmem<T> sm;
-    batch_init(f, sm, smraw, &tmem_slot, &mbar, false);
-    int* eo = (int*)(smraw + batch_span(f, false));
-    int* hp = eo + f.nmax;
-    int* doff = hp + f.nmax;
-    const int G = f.split, b = blockIdx.x / G, g = blockIdx.x % G, K = f.K;
-    const int64_t s = f.s0 + b;
-    const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
-    const size_t nk = (size_t)K * K * 9;
-    const int* trl = f.tr_list + (size_t)b * nk;
-    const int ntr = f.tr_total[b];
-    const T* H = f.H + (size_t)b * 3 * K * K * f.D;
-    const int* He = f.He + (size_t)b * 3 * K * K;
-    T* TR = f.TR + (size_t)f.tr_base[b] * f.D;
-    int* TRe = f.TRe + f.tr_base[b];
-    int i0 = 0;
-    while (i0 < ntr) {
-        const int grp0 = trl[i0] / (3 * K);              // (sA, aA)
-        const int sA = grp0 / 3, aA = grp0 % 3;
-        int n = 1;
-        while (i0 + n < ntr && n < f.nmax * G && trl[i0 + n] / (3 * K) == grp0) ++n;
-        // this block's rows of the run: i0 + i with i0 + i = g (mod G)
-        const int sel = ((g - i0) % G + G) % G;
-        const int m = sel < n ? (n - 1 - sel) / G + 1 : 0;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            const int r = i0 + sel + i * G;
-            const int k = trl[r];
-            const int sB = (k / 3) % K, aB = k % 3;
-            hp[i] = (aB * K + sB) * K + sA + 1;
-            doff[i] = r;
-        }
-        __syncthreads();
-        if (m > 0) {
-            batch_apply<T>(f, sm, H, hp, TR, doff, eo, m, 1, sA, sig_of_alt(aA, sigma_at(na, nb, sA)));
-            for (int i = threadIdx.x; i < m; i += blockDim.x) TRe[doff[i]] = eo[i] + He[hp[i]];
-        }
-        __syncthreads();
-        i0 += n;
-    }
-    batch_fini(f, sm);
-}
-
-// F4b: TL clusters: created at t = s2 from G_{s1,a1}(s2-1), propagated with
-// A_t^{sigma_t(n)} up to their last use; every step is stored.
-template <typename T>
-__global__ void __launch_bounds__(256, 4) k_fam_tl(FamArgs<T> f)
-{
-    extern __shared__ __align__(1024) unsigned char smraw[];
-    __shared__ uint32_t tmem_slot;
-    __shared__ __align__(8) uint64_t mbar;
-    __shared__ int wt[32];
-    BatchSmem<T> sm;
-    batch_init(f, sm, smraw, &tmem_slot, &mbar, false);
-    int* eo = (int*)(smraw + batch_span(f, false));
-    int* src = eo + f.nmax;
-    int* dst = src + f.nmax;
-    int* pbuf_src = dst + f.nmax;                 // [nmax + blockDim]
-    int* pbuf_dst = pbuf_src + f.nmax + blockDim.x;
-    const int G = f.split, b = blockIdx.x / G, g = blockIdx.x % G, K = f.K, D = f.D;
-    const int64_t s = f.s0 + b;
-    const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
-    const size_t nk = (size_t)K * K * 9;
-    const int* tl = f.tl_idx + (size_t)b * nk;
-    const int* tl_end = f.tl_end + (size_t)b * nk;
-    const int* tll = f.tl_list + (size_t)b * nk;
-    const int ncl = f.tl_count[b];
-    const T* Gf = f.G + (size_t)b * 3 * K * K * D;
-    const int* Ge = f.Ge + (size_t)b * 3 * K * K;
-    T* TL = f.TL + (size_t)f.tl_base[b] * D;
-    int* TLe = f.TLe + f.tl_base[b];
-    // the list is in key order, i.e. ascending s2: clusters created at t form a run
-    int first = 0;                       // first cluster with s2 >= t
-    for (int t = 1; t < K; ++t) {
-        const int own = sigma_at(na, nb, t);
-        while (first < ncl && tll[first] / (9 * K) < t) ++first;
-        // (1) creation: runs of one (s2 = t, a2) share the matrix A_t^{a2}
-        int c0 = first;
-        while (c0 < ncl && tll[c0] / (9 * K) == t) {
-            const int grp = tll[c0] / (3 * K);
-            const int a2 = grp % 3;
-            int n = 1;
-            while (c0 + n < ncl && n < f.nmax * G && tll[c0 + n] / (3 * K) == grp) ++n;
-            // this block's clusters of the run: c0 + i = g (mod G)
-            const int sel = ((g - c0) % G + G) % G;
-            const int m = sel < n ? (n - 1 - sel) / G + 1 : 0;
-            for (int i = threadIdx.x; i < m; i += blockDim.x) {
-                const int key = tll[c0 + sel + i * G];
-                const int s1 = (key / 3) % K, a1 = key % 3;
-                dst[i] = tl[key];
-                src[i] = (a1 * K + s1) * K + (t - 1);
-            }
-            __syncthreads();
-            if (m > 0) {
-                batch_apply<T>(f, sm, Gf, src, TL, dst, eo, m, 0, t, sig_of_alt(a2, own));
-                for (int i = threadIdx.x; i < m; i += blockDim.x) TLe[dst[i]] = eo[i] + Ge[src[i]];
-            }
-            __syncthreads();
-            c0 += n;
-        }
-        // (2) propagation of clusters with s2 < t <= end: the list prefix [0, first)
-        // is compacted window by window into a buffer; full batches are multiplied.
-        int nbuf = 0;
-        for (int w0 = 0; w0 < first || nbuf > 0; w0 += blockDim.x) {
-            if (w0 < first) {
-                const int c = w0 + threadIdx.x;
-                int act = 0, key = 0;
-                if (c < first && c % G == g) {
-                    key = tll[c];
-                    act = t <= tl_end[key] ? 1 : 0;
-                }
-                int pos;
-                const int tot = block_excl_scan(act, &pos, wt);
-                if (act) {
-                    const int s2 = key / (9 * K), off = tl[key];
-                    pbuf_src[nbuf + pos] = off + (t - 1 - s2);
-                    pbuf_dst[nbuf + pos] = off + (t - s2);
-                }
-                nbuf += tot;
-                __syncthreads();
-            }
-            const bool last_window = w0 + (int)blockDim.x >= first;
-            while (nbuf >= f.nmax || (last_window && nbuf > 0)) {
-                const int n = nbuf < f.nmax ? nbuf : f.nmax;
-                batch_apply<T>(f, sm, TL, pbuf_src, TL, pbuf_dst, eo, n, 0, t, own);
-                for (int i = threadIdx.x; i < n; i += blockDim.x) TLe[pbuf_dst[i]] = eo[i] + TLe[pbuf_src[i]];
-                __syncthreads();
-                // shift the rest of the buffer down
-                const int rest = nbuf - n;
-                int sv = 0, dv = 0;
-                const bool mv = (int)threadIdx.x < rest;
-                if (mv) { sv = pbuf_src[n + threadIdx.x]; dv = pbuf_dst[n + threadIdx.x]; }
-                __syncthreads();
-                if (mv) { pbuf_src[threadIdx.x] = sv; pbuf_dst[threadIdx.x] = dv; }
-                nbuf = rest;
-                __syncthreads();
-            }
-            if (w0 >= first) break;
-        }
-    }
-    batch_fini(f, sm);
-}
-
 // ---------------------------------------------------------------------------
 // F4c: correlator factors of the left and right objects of a sample.
 //   left  objects: G families (s, a) [3K] then TL clusters [tl_count]
@@ -831,8 +551,8 @@ __global__ void k_fam_rbm(FamArgs<T> f)
 // Groups: g = side * 4 + sigma, the local state whose matrix the item applies.
 // ---------------------------------------------------------------------------
 
-template <bool FILL>
-__global__ void __launch_bounds__(256) k_site_build(FamArgs<float> f, SiteBufs sb)
+template <typename T, bool FILL>
+__global__ void __launch_bounds__(256) k_site_build(FamArgs<T> f, SiteBufs sb)
 {
     __shared__ int cnt[kMaxOrb * 8];               // counts, then fill cursors
     __shared__ int own[kMaxOrb];
@@ -844,17 +564,17 @@ __global__ void __launch_bounds__(256) k_site_build(FamArgs<float> f, SiteBufs s
     for (int i = threadIdx.x; i < K; i += blockDim.x) own[i] = sigma_at(na, nb, i);
     __syncthreads();
     const size_t nk = (size_t)K * K * 9;
-    float* Gb = f.G + (size_t)b * 3 * K * K * D;
+    T* Gb = f.G + (size_t)b * 3 * K * K * D;
     int* Geb = f.Ge + (size_t)b * 3 * K * K;
-    float* Hb = f.H + (size_t)b * 3 * K * K * D;
+    T* Hb = f.H + (size_t)b * 3 * K * K * D;
     int* Heb = f.He + (size_t)b * 3 * K * K;
-    auto put = [&](int tau, int g, const float* src, const int* se, float* dst, int* de) {
+    auto put = [&](int tau, int g, const T* src, const int* se, T* dst, int* de) {
         const int slot = atomicAdd(&cnt[tau * 8 + g], 1);
         if (FILL) {
             const int64_t at = sb.offs[((int64_t)tau * 8 + g) * nbb + b] + slot;
-            SiteItem it;
+            SiteItemT<T> it;
             it.src = src; it.dst = dst; it.se = se; it.de = de;
-            sb.items[at] = it;
+            ((SiteItemT<T>*)sb.items)[at] = it;
         }
     };
     // (1) families created before the step (k_site_boundary makes the new ones
@@ -863,7 +583,7 @@ __global__ void __launch_bounds__(256) k_site_build(FamArgs<float> f, SiteBufs s
         const int tau = w >> 1, side = w & 1;
         const int t = side == 0 ? tau : K - 1 - tau;
         const int o = own[t];
-        float* Tb = side == 0 ? Gb : Hb;
+        T* Tb = side == 0 ? Gb : Hb;
         int* Te = side == 0 ? Geb : Heb;
         const int tp = side == 0 ? t - 1 : t + 1;      // the family's previous site
         for (int j = 0; j < tau; ++j) {
@@ -877,7 +597,7 @@ __global__ void __launch_bounds__(256) k_site_build(FamArgs<float> f, SiteBufs s
     // (2) TL clusters: creation at s2 with A_{s2}^{a2}, then A_t^{own} up to the last use
     const int ncl = f.tl_count[b];
     const int* tll = f.tl_list + (size_t)b * nk;
-    float* TLb = f.TL + (size_t)f.tl_base[b] * D;
+    T* TLb = f.TL + (size_t)f.tl_base[b] * D;
     int* TLeb = f.TLe + f.tl_base[b];
     for (int c = threadIdx.x; c < ncl; c += blockDim.x) {
         const int key = tll[c];
@@ -895,7 +615,7 @@ __global__ void __launch_bounds__(256) k_site_build(FamArgs<float> f, SiteBufs s
     // (3) TR rows: H_{sB,aB}(sA+1) A_{sA}^{aA} at the right step of site sA
     const int ntr = f.tr_total[b];
     const int* trl = f.tr_list + (size_t)b * nk;
-    float* TRb = f.TR + (size_t)f.tr_base[b] * D;
+    T* TRb = f.TR + (size_t)f.tr_base[b] * D;
     int* TReb = f.TRe + f.tr_base[b];
     for (int i = threadIdx.x; i < ntr; i += blockDim.x) {
         const int key = trl[i];
@@ -914,31 +634,39 @@ __global__ void __launch_bounds__(256) k_site_build(FamArgs<float> f, SiteBufs s
 // Boundary vectors L_t (R_t) of each sample and side and the three families
 // that start at each site, on the CUDA cores in FP32 (the arithmetic of the
 // per-sample sweep): one block per (sample, side), steps in order.
-__global__ void __launch_bounds__(256) k_site_boundary(FamArgs<float> f)
+template <typename T>
+__global__ void __launch_bounds__(256) k_site_boundary(FamArgs<T> f)
 {
     extern __shared__ __align__(16) unsigned char smb[];
     __shared__ int eo[4];
     __shared__ int eL;
     const int b = blockIdx.x >> 1, side = blockIdx.x & 1, K = f.K, D = f.D;
-    float* X = (float*)smb;                       // [D]
-    float* Y = X + D;                             // [4][D]
+    T* X = (T*)smb;                               // [D]
+    T* Y = X + D;                                 // [4][D]
     const int64_t s = f.s0 + b;
     const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
-    float* Tb = (side == 0 ? f.G : f.H) + (size_t)b * 3 * K * K * D;
+    T* Tb = (side == 0 ? f.G : f.H) + (size_t)b * 3 * K * K * D;
     int* Te = (side == 0 ? f.Ge : f.He) + (size_t)b * 3 * K * K;
-    const float* Mats = side == 0 ? f.AT : f.A;   // column convention left, row vectors right
-    for (int c = threadIdx.x; c < D; c += blockDim.x) X[c] = c == 0 ? 1.f : 0.f;
+    const T* Mats = side == 0 ? f.AT : f.A;       // column convention left, row vectors right
+    for (int c = threadIdx.x; c < D; c += blockDim.x) X[c] = c == 0 ? T(1) : T(0);
     if (threadIdx.x == 0) eL = 0;
     __syncthreads();
     for (int step = 0; step < K; ++step) {
         const int t = side == 0 ? step : K - 1 - step;
         const int own = sigma_at(na, nb, t);
-        for (int a = 0; a < 4; ++a) {
+        // the four products (three alternatives, then the own state) at once: one
+        // output per thread, fma over the input index in ascending order (the
+        // order of mv_block, so the results are the same bit for bit)
+        for (int q = threadIdx.x; q < 4 * D; q += blockDim.x) {
+            const int a = q / D, r = q - a * D;
             const int sg = a == 3 ? own : sig_of_alt(a, own);
-            mv_block<float>(Mats + ((size_t)t * 4 + sg) * D * D, D, X, Y + (size_t)a * D, 1);
+            const T* MT = Mats + ((size_t)t * 4 + sg) * D * D;
+            T acc = T(0);
+            for (int c = 0; c < D; ++c) acc = fma(__ldg(MT + (size_t)c * D + r), X[c], acc);
+            Y[q] = acc;
         }
         __syncthreads();
-        renorm_rows<float>(Y, D, 4, eo);
+        renorm_rows<T>(Y, D, 4, eo);
         __syncthreads();
         const int e_in = eL;
         for (int q = threadIdx.x; q < 3 * D; q += blockDim.x) {
@@ -963,78 +691,120 @@ struct SiteStep {
     int64_t gbeg[8], gend[8];   // item range of each group
     int tbeg[9];                // first tile of each group; tbeg[8] = tiles of the step
     int mat[8];                 // matrix image of each group
+    int rows;                   // rows per tile
 };
 
-__global__ void __launch_bounds__(256, 4) k_site_tiles(FamArgs<float> f, const SiteItem* items, SiteStep st)
+template <typename T>
+__global__ void __launch_bounds__(256, 4) k_site_tiles(FamArgs<T> f, const SiteItemT<T>* items, SiteStep st)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) uint64_t mbar;
-    __shared__ const float* s_src[128];
-    __shared__ float* s_dst[128];
+    __shared__ const T* s_src[128];
+    __shared__ T* s_dst[128];
     __shared__ const int* s_se[128];
     __shared__ int* s_de[128];
-    BatchSmem<float> sm;
-    batch_init(f, sm, smraw, &tmem_slot, &mbar, false);
-    struct Acc {
-        const float* const* s; float* const* d; const int* const* se; int* const* de;
-        __device__ const float* src(int r) const { return s[r]; }
-        __device__ float* dst(int r) const { return d[r]; }
-        __device__ void set_exp(int r, int x) const { *de[r] = *se[r] + x; }
-    } acc{s_src, s_dst, s_se, s_de};
+    __shared__ int s_eo[128];
+    BatchSmem<T> sm;
+    batch_init(f, sm, smraw, &tmem_slot, &mbar);
+    const bool tc = use_tc(f);
+    const int rows = st.rows, D = f.D;
     const int ntiles = st.tbeg[8];
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         int g = 0;
         while (g < 7 && tile >= st.tbeg[g + 1]) ++g;
-        const int64_t i0 = st.gbeg[g] + (int64_t)(tile - st.tbeg[g]) * 128;
+        const int64_t i0 = st.gbeg[g] + (int64_t)(tile - st.tbeg[g]) * rows;
         const int64_t left = st.gend[g] - i0;
-        const int n = (int)(left < 128 ? left : 128);
+        const int n = (int)(left < rows ? left : rows);
         for (int r = threadIdx.x; r < n; r += blockDim.x) {
-            const SiteItem it = items[i0 + r];
+            const SiteItemT<T> it = items[i0 + r];
             s_src[r] = it.src; s_dst[r] = it.dst; s_se[r] = it.se; s_de[r] = it.de;
         }
         __syncthreads();
-        tc_apply(f, sm, acc, n, st.mat[g]);          // ends with a block barrier
+        const int mat = st.mat[g];
+        if constexpr (std::is_same<T, float>::value) {
+            if (tc) {
+                struct Acc {
+                    const float* const* s; float* const* d; const int* const* se; int* const* de;
+                    __device__ const float* src(int r) const { return s[r]; }
+                    __device__ float* dst(int r) const { return d[r]; }
+                    __device__ void set_exp(int r, int x) const { *de[r] = *se[r] + x; }
+                } acc{s_src, s_dst, s_se, s_de};
+                tc_apply(f, sm, acc, n, mat);          // ends with a block barrier
+                continue;
+            }
+        }
+        // CUDA-core batch: gather, y = M x with the FP32/FP64 matrices, rescale, scatter
+        const int side = mat / (4 * f.K), t = (mat >> 2) % f.K, sg = mat & 3;
+        for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
+            const int i = q / D, c = q - i * D;
+            sm.X[q] = s_src[i][c];
+        }
+        __syncthreads();
+        mv_block<T>((side == 0 ? f.AT : f.A) + ((size_t)t * 4 + sg) * D * D, D, sm.X, sm.Y, n);
+        __syncthreads();
+        renorm_rows<T>(sm.Y, D, n, s_eo);
+        __syncthreads();
+        for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
+            const int i = q / D, c = q - i * D;
+            s_dst[i][c] = sm.Y[q];
+        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) *s_de[i] = *s_se[i] + s_eo[i];
+        __syncthreads();
     }
     batch_fini(f, sm);
 }
 
-int fam_site_count(const FamArgs<float>& f, const SiteBufs& b, int nbb, cudaStream_t st)
+template <typename T>
+int fam_site_count(const FamArgs<T>& f, const SiteBufs& b, int nbb, cudaStream_t st)
 {
     const int n = f.K * 8;
-    k_site_boundary<<<nbb * 2, 256, (size_t)5 * f.D * sizeof(float), st>>>(f);
-    k_site_build<false><<<nbb, 256, 0, st>>>(f, b);
+    k_site_boundary<T><<<nbb * 2, 256, (size_t)5 * f.D * sizeof(T), st>>>(f);
+    k_site_build<T, false><<<nbb, 256, 0, st>>>(f, b);
     launch_scan_i64(b.counts, b.offs, (int64_t)n * nbb, st);
     k_site_bounds<<<1, 256, 0, st>>>(b.offs, n, nbb, b.bounds);
     return 4;
 }
 
-int fam_site_fill(const FamArgs<float>& f, const SiteBufs& b, int nbb, cudaStream_t st)
+template <typename T>
+int fam_site_fill(const FamArgs<T>& f, const SiteBufs& b, int nbb, cudaStream_t st)
 {
-    k_site_build<true><<<nbb, 256, 0, st>>>(f, b);
+    k_site_build<T, true><<<nbb, 256, 0, st>>>(f, b);
     return 1;
 }
 
-int fam_site_step(const FamArgs<float>& f, const SiteBufs& b, int tau, const int64_t* bounds,
+template <typename T>
+int fam_site_step(const FamArgs<T>& f, const SiteBufs& b, int tau, const int64_t* bounds,
                   int max_ctas, cudaStream_t st)
 {
+    const bool tc = std::is_same<T, float>::value && f.tc;
+    // tensor-core tiles are 128 rows; CUDA-core tiles shrink (to 4 rows) when a
+    // step has few items, so that they still spread over about half the CTAs
+    // (an FP64 tile is slow on one SM)
+    int rows = 128;
+    if (!tc) {
+        const int64_t items = bounds[tau * 8 + 8] - bounds[tau * 8];
+        const int64_t want = (items + max_ctas / 2 - 1) / (max_ctas / 2 > 0 ? max_ctas / 2 : 1);
+        rows = (int)std::min<int64_t>(f.nmax, std::max<int64_t>(4, (want + 3) / 4 * 4));
+    }
     SiteStep ss{};
+    ss.rows = rows;
     int tiles = 0;
     for (int g = 0; g < 8; ++g) {
         ss.gbeg[g] = bounds[tau * 8 + g];
         ss.gend[g] = bounds[tau * 8 + g + 1];
         ss.tbeg[g] = tiles;
-        tiles += (int)((ss.gend[g] - ss.gbeg[g] + 127) / 128);
+        tiles += (int)((ss.gend[g] - ss.gbeg[g] + rows - 1) / rows);
         const int side = g >> 2;
         const int t = side == 0 ? tau : f.K - 1 - tau;
         ss.mat[g] = (side * f.K + t) * 4 + (g & 3);
     }
     ss.tbeg[8] = tiles;
     if (tiles == 0) return 0;
-    const size_t smem = f.batch_bytes - fam_small_bytes(f.D, sizeof(float), true);
-    allow_max_smem(k_site_tiles);
+    allow_max_smem(k_site_tiles<T>);
+    const size_t smem = f.batch_bytes;
     const int grid = tiles < max_ctas ? tiles : max_ctas;
-    k_site_tiles<<<grid, 256, smem, st>>>(f, b.items, ss);
+    k_site_tiles<T><<<grid, 256, smem, st>>>(f, (const SiteItemT<T>*)b.items, ss);
     return 1;
 }
 
@@ -1254,23 +1024,6 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
 // ---------------------------------------------------------------------------
 
 template <typename T>
-static size_t stage_smem(const FamArgs<T>& f, int nints, bool small = true)
-{
-    const size_t bb = f.batch_bytes - (small ? 0 : fam_small_bytes(f.D, sizeof(T), f.tc != 0 &&
-                                                                   std::is_same<T, float>::value));
-    return bb + (size_t)nints * f.nmax * sizeof(int) + (size_t)f.D * sizeof(T) + 64;
-}
-
-template <typename T>
-int fam_launch_sweep(const FamArgs<T>& f, int nb, cudaStream_t st)
-{
-    const size_t smem = stage_smem(f, 4);
-    allow_max_smem(k_fam_sweep<T>);
-    k_fam_sweep<T><<<(unsigned)(nb * 2 * f.split), f.threads, smem, st>>>(f);
-    return 1;
-}
-
-template <typename T>
 int fam_launch_mark(const FamArgs<T>& f, const RowSet& rows, int nb, cudaStream_t st)
 {
     dim3 grid(16, nb);
@@ -1283,24 +1036,6 @@ int fam_launch_compact(const FamArgs<T>& f, int nb, cudaStream_t st)
 {
     k_fam_compact<T><<<nb, 1024, 0, st>>>(f);
     return 1;
-}
-
-template <typename T>
-int fam_launch_tables(const FamArgs<T>& f, int nb, cudaStream_t st)
-{
-    const size_t smem = stage_smem(f, 3, false);
-    const size_t smem_tl = stage_smem(f, 3, false) + (size_t)2 * (f.nmax + f.threads) * sizeof(int);
-    allow_max_smem(k_fam_tr<T>);
-    allow_max_smem(k_fam_tl<T>);
-    k_fam_tr<T><<<(unsigned)(nb * f.split), f.threads, smem, st>>>(f);
-    k_fam_tl<T><<<(unsigned)(nb * f.split), f.threads, smem_tl, st>>>(f);
-    int n = 2;
-    if (f.n_hidden > 0) {
-        dim3 grid(8 * f.split, nb);
-        k_fam_rbm<T><<<grid, 256, 2 * f.n_hidden * sizeof(T), st>>>(f);
-        ++n;
-    }
-    return n;
 }
 
 template <typename T>
@@ -1356,11 +1091,13 @@ void fam_tc_images(const double* A, int K, int D, std::vector<unsigned char>& im
 }
 
 #define NQS_FAM_INST(T)                                                                    \
-    template int fam_launch_sweep<T>(const FamArgs<T>&, int, cudaStream_t);                \
     template int fam_launch_mark<T>(const FamArgs<T>&, const RowSet&, int, cudaStream_t);  \
     template int fam_launch_compact<T>(const FamArgs<T>&, int, cudaStream_t);              \
-    template int fam_launch_tables<T>(const FamArgs<T>&, int, cudaStream_t);               \
     template int fam_launch_rbm<T>(const FamArgs<T>&, int, cudaStream_t);                  \
+    template int fam_site_count<T>(const FamArgs<T>&, const SiteBufs&, int, cudaStream_t);  \
+    template int fam_site_fill<T>(const FamArgs<T>&, const SiteBufs&, int, cudaStream_t);   \
+    template int fam_site_step<T>(const FamArgs<T>&, const SiteBufs&, int, const int64_t*,  \
+                                  int, cudaStream_t);                                       \
     template int fam_launch_rows<T>(const FamArgs<T>&, const RowSet&, int64_t, double*,    \
                                     int64_t*, double*, cudaStream_t);
 NQS_FAM_INST(float)

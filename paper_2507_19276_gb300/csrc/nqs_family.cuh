@@ -12,9 +12,7 @@ template <typename T>
 struct FamArgs {
     HamView h;
     int K, D;
-    int threads;              // block size of the per-sample kernels (>= D)
-    int split;                // blocks per sample (per side in the sweep) of the table
-                              // kernels; each takes every split-th family / cluster
+    int split;                // blocks per sample of the correlator-factor kernel
     int nmax;                 // vectors per block-wide mat-vec batch
     size_t batch_bytes;       // shared memory of one batch (see fam_batch_bytes)
     int tc;                   // 1: tensor-core batches (FP32; D % 16 == 0 up to 128, or 192 / 256)
@@ -48,10 +46,8 @@ struct FamArgs {
     const int64_t* rbl_base; const int64_t* rbr_base;   // [b] object offsets
 };
 
-template <typename T> int fam_launch_sweep(const FamArgs<T>& f, int nb, cudaStream_t st);
 template <typename T> int fam_launch_mark(const FamArgs<T>& f, const RowSet& rows, int nb, cudaStream_t st);
 template <typename T> int fam_launch_compact(const FamArgs<T>& f, int nb, cudaStream_t st);
-template <typename T> int fam_launch_tables(const FamArgs<T>& f, int nb, cudaStream_t st);
 // grid = upper bound of the batch's row chunks (128 rows each); blocks map to
 // rows.chunk_base[s0] + blockIdx.x. partial_abs (may be NULL) gets each chunk's
 // sum of |term|.
@@ -67,36 +63,34 @@ template <typename T> int fam_launch_rows(const FamArgs<T>& f, const RowSet& row
 // items of site step tau fall into 8 groups (side x local state of the
 // matrix), each one matrix image, and one launch per step runs 128-row tiles
 // over all samples' items.
-struct SiteItem {
-    const float* src;   // input vector
-    float* dst;         // output vector
+template <typename T>
+struct SiteItemT {
+    const T* src;       // input vector
+    T* dst;             // output vector
     const int* se;      // input power-of-two exponent
     int* de;            // output exponent (= input + the product's own)
 };
+using SiteItem = SiteItemT<float>;       // the same size for every T
 struct SiteBufs {
     int64_t* counts;    // [K][8][nbb] items per (step, group, sample)
     int64_t* offs;      // [K*8*nbb + 1] exclusive prefix of counts
     int64_t* bounds;    // [K*8 + 1] first item of each (step, group)
-    SiteItem* items;
+    void* items;        // SiteItemT<T>[total]
 };
 // boundary vectors and first-site families, then the item counts, their
 // prefix and the (step, group) bounds (device); returns launches
-int fam_site_count(const FamArgs<float>& f, const SiteBufs& b, int nbb, cudaStream_t st);
+// Tiles: 128-row tensor-core batches (FP32 with images), else f.nmax-row
+// CUDA-core batches (FP64, or FP32 without images).
+template <typename T> int fam_site_count(const FamArgs<T>& f, const SiteBufs& b, int nbb, cudaStream_t st);
 // write the items (after the counts)
-int fam_site_fill(const FamArgs<float>& f, const SiteBufs& b, int nbb, cudaStream_t st);
+template <typename T> int fam_site_fill(const FamArgs<T>& f, const SiteBufs& b, int nbb, cudaStream_t st);
 // run the tiles of step tau; bounds: host copy of SiteBufs::bounds
-int fam_site_step(const FamArgs<float>& f, const SiteBufs& b, int tau, const int64_t* bounds,
-                  int max_ctas, cudaStream_t st);
+template <typename T> int fam_site_step(const FamArgs<T>& f, const SiteBufs& b, int tau,
+                                        const int64_t* bounds, int max_ctas, cudaStream_t st);
 // the correlator factors alone (the site-synchronous path builds the tables)
 template <typename T> int fam_launch_rbm(const FamArgs<T>& f, int nb, cudaStream_t st);
 
-// shared memory of the batch buffers of the table kernels; the tensor-core
-// layout starts with a small scratch for the sweep's boundary vectors
-// (fam_small_bytes), which the other table kernels leave out
-__host__ __device__ inline size_t fam_small_bytes(int D, size_t elem, bool tc)
-{
-    return tc ? (((size_t)8 * D * elem + 1023) & ~(size_t)1023) : 0;
-}
+// shared memory of the batch buffers of the site tiles
 // width of the reduction chunks of a tensor-core batch: the whole D up to 128,
 // else 64 (the operands of one chunk then fit shared memory)
 __host__ __device__ inline int fam_tc_kc(int D) { return D <= 128 ? D : 64; }
@@ -104,7 +98,7 @@ __host__ __device__ inline size_t fam_batch_bytes(int D, int nmax, size_t elem, 
 {
     if (!tc) return (size_t)2 * nmax * D * elem;
     const size_t kc = (size_t)fam_tc_kc(D);
-    return fam_small_bytes(D, elem, tc) + (size_t)4 * 128 * kc + (size_t)4 * D * kc + 2 * 128 * 4;
+    return (size_t)4 * 128 * kc + (size_t)4 * D * kc + 2 * 128 * 4;
 }
 
 // Split-FP16 operand images of the chain's site tensors for the tensor-core
