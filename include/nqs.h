@@ -99,8 +99,8 @@ typedef struct {
 /* Stages of the local-energy path, as reported by nqs_stage_times. */
 enum {
     NQS_STAGE_ENV = 0,        /* input checks, environments, psi(n), f(n), H_nn */
-    NQS_STAGE_COUNT = 1,      /* enumeration pass 1: |H| >= eps counts, max remainder |H| */
-    NQS_STAGE_WRITE = 2,      /* enumeration pass 2: deterministic list, remainder weights */
+    NQS_STAGE_COUNT = 1,      /* enumeration pass 1: |H| >= eps counts, remainder weight sums */
+    NQS_STAGE_WRITE = 2,      /* enumeration pass 2: deterministic lists (chunks holding entries) */
     NQS_STAGE_DRAW = 3,       /* Philox draws, inverse CDF, de-duplication */
     NQS_STAGE_AMP_DET = 4,    /* amplitudes and ratios of the deterministic rows */
     NQS_STAGE_AMP_DRAW = 5,   /* amplitudes and ratios of the drawn rows */
@@ -206,7 +206,8 @@ int nqs_amplitude(nqs_ctx* ctx, const uint64_t* dets, int64_t n, double* log_abs
  *  output x picks t = floor(x W / 2^64), and m' is the first remainder entry
  *  (canonical order) whose inclusive prefix of integer weights exceeds t.
  *  Weights: w = ceil(|H| 2^shift), shift = 62 - e - bitlen(n_conn), where
- *  max_{remainder}|H| = f 2^e with f in [0.5, 1). */
+ *  det_threshold = f 2^e with f in [0.5, 1): every remainder |H| is below
+ *  det_threshold, so every per-sample sum stays below 2^62. */
 int nqs_draws(nqs_ctx* ctx, const uint64_t* samples, int64_t Ns, double det_threshold,
               int n_draws, uint64_t philox_seed, int64_t* ranks, uint64_t* w_total);
 
@@ -220,7 +221,7 @@ int nqs_draws(nqs_ctx* ctx, const uint64_t* samples, int64_t Ns, double det_thre
  *  rejected with NQS_ERR_INVALID_ARG because staging them would allocate.
  *  Working memory is a fixed array of NQS_NOALLOC_SCRATCH_BYTES inside the
  *  library image, present on every GPU that loads the library until the
- *  process exits. A batch needs 8 * (2 + 2 Ns + 1.5 Ns ceil(n_conn / 32))
+ *  process exits. A batch needs 8 * (2 + Ns + 1.5 Ns ceil(n_conn / 32))
  *  bytes of it; larger batches return NQS_ERR_INVALID_ARG (split them).
  *  The first call on a device looks up the array's device address (with
  *  cudaGetSymbolAddress); make that first call before any stream capture.

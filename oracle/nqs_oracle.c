@@ -422,12 +422,13 @@ static int bit_length(uint64_t x)
     return b;
 }
 
-/* Remainder weights w = ceil(|H| 2^s) with s = 62 - e(M) - bitlen(n_conn),
- * M = max|H| over the remainder, so that sum w < 2^63. */
-static int weight_shift(double max_abs, int64_t nconn)
+/* Remainder weights w = ceil(|H| 2^s) (P_n(m) proportional to |H_nm|, Sec.
+ * 2.4, as exact integers) with s = 62 - e - bitlen(n_conn), eps = f 2^e,
+ * f in [0.5, 1): every remainder |H| < eps, so sum w < 2^62. */
+static int weight_shift(double eps, int64_t nconn)
 {
-    int e;
-    frexp(max_abs, &e);
+    int e = 0;
+    if (eps > 0.0) frexp(eps, &e);
     return 62 - e - bit_length((uint64_t)nconn);
 }
 
@@ -459,26 +460,16 @@ static void split_build(const or_ham* h, const uint64_t* n, double eps, split_t*
     sp->H = (double*)malloc(sizeof(double) * (size_t)(nc + 1));
     sp->dets = (uint64_t*)malloc(sizeof(uint64_t) * 2 * (size_t)(nc + 1));
     or_connected(h, n, sp->dets, sp->H, NULL);
-    double M = 0.0;
     int64_t nrem = 0;
     for (int64_t r = 0; r < nc; ++r)
-        if (!(fabs(sp->H[r]) >= eps)) {
-            ++nrem;
-            if (fabs(sp->H[r]) > M) M = fabs(sp->H[r]);
-        }
+        if (!(fabs(sp->H[r]) >= eps)) ++nrem;
     sp->nrem = nrem;
     sp->rem_rank = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nrem + 1));
     sp->prefix = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(nrem + 1));
     sp->W = 0;
     sp->shift = 0;
-    if (nrem == 0 || M == 0.0) {
-        sp->nrem = nrem;
-        int64_t c = 0;
-        for (int64_t r = 0; r < nc; ++r)
-            if (!(fabs(sp->H[r]) >= eps)) { sp->rem_rank[c] = r; sp->prefix[c] = 0; ++c; }
-        return;
-    }
-    sp->shift = weight_shift(M, nc);
+    if (nrem == 0) return;
+    sp->shift = weight_shift(eps, nc);
     uint64_t run = 0;
     int64_t c = 0;
     for (int64_t r = 0; r < nc; ++r)

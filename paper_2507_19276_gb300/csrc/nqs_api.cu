@@ -46,7 +46,7 @@ struct nqs_ctx {
 
     // staging and workspace
     DevBuf st_samples, st_counts, st_u, st_out0, st_out1, st_out2, st_out3, st_out4;
-    DevBuf chunk_cnt, chunk_off, chunk_w, rem_max, det_tot, det_off, det_rank, det_coef;
+    DevBuf chunk_cnt, chunk_off, chunk_w, det_tot, det_off, det_rank, det_coef;
     DevBuf Lenv, Lexp, Renv, Rexp, Hst, Hexp, Gst, Gexp, theta, lc, logf, pmant, pexp, hdiag;
     DevBuf Wtot, draw_rank64, draw_rank, draw_coef, n_unique;
     DevBuf base_det, base_draw, part_det, part_draw, eloc, edet, estoch, summary, derr;
@@ -63,7 +63,6 @@ struct nqs_ctx {
     int64_t index_base = 0;    // Philox sample counter of samples[0]
     int n_sm = 152;            // multiprocessors of the device
     size_t fam_budget = 0;     // cap on the shared-prefix tables (0: none beyond free/3)
-    DevBuf h_all;              // stored H_nm of the last local-energy call
     DevBuf site_cnt, site_offs, site_bounds, site_items;
     double energy_tol = 0.0;   // mixed form: re-evaluate heavy samples in FP64 to this bound
     DevBuf part_det_abs, part_draw_abs, eabs, logf_save, summary2, ref_idx, ref_s, ref_c, ref_pos,
@@ -268,28 +267,48 @@ int eps_bits(nqs_ctx* c, double eps, uint64_t* bits)
     return NQS_OK;
 }
 
-// Count pass + per-sample scans: det_off (device) and the total on the host.
+// Remainder weights w = ceil(|H| 2^shift) (Sec. 2.4: P_n(m) proportional to
+// |H_nm|, as exact integers). Every remainder element has |H| < eps = f 2^e with
+// f in [0.5, 1), so shift = 62 - e - bitlen(n_conn) keeps every per-sample sum
+// below 2^62 and fixes the shift before any element is evaluated.
+int weight_shift(const nqs_ctx* c, uint64_t eps_bits)
+{
+    double eps;
+    memcpy(&eps, &eps_bits, sizeof(eps));
+    int e = 0;
+    if (eps > 0.0) std::frexp(eps, &e);
+    return 62 - e - c->hv.bitlen_nconn;
+}
+
+// Count pass + per-sample scans: det_off (device) and the total on the host;
+// with `weights`, also the remainder weight sums per chunk, their per-sample
+// inclusive prefix (chunk_w) and totals (Wtot).
 int count_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, uint64_t eb, int64_t* total,
-               double* h_store = nullptr)
+               bool weights)
 {
     const uint32_t nch = (uint32_t)((c->n_conn + 31) / 32);
     TRY(ensure(c, c->chunk_cnt, (size_t)Ns * nch * 4));
     TRY(ensure(c, c->chunk_off, (size_t)Ns * nch * 4));
-    TRY(ensure(c, c->rem_max, (size_t)Ns * 8));
     TRY(ensure(c, c->det_tot, (size_t)Ns * 8));
     TRY(ensure(c, c->det_off, (size_t)(Ns + 1) * 8));
+    if (weights) {
+        TRY(ensure(c, c->chunk_w, (size_t)Ns * nch * 8));
+        TRY(ensure(c, c->Wtot, (size_t)Ns * 8));
+    }
     EnumArgs a{};
     a.h = c->hv;
     a.samples = samples;
     a.eps_bits = eb;
     a.n_chunks = nch;
     a.chunk_cnt = (uint32_t*)c->chunk_cnt.p;
-    a.rem_max_bits = (unsigned long long*)c->rem_max.p;
-    a.h_store = h_store;
+    a.shift = weight_shift(c, eb);
+    a.chunk_w = weights ? (uint64_t*)c->chunk_w.p : nullptr;
     StageScope sc(c, NQS_STAGE_COUNT);
-    CK(cudaMemsetAsync(c->rem_max.p, 0, (size_t)Ns * 8, c->stream));
     LAUNCH(NQS_STAGE_COUNT, launch_enum(a, Ns, false, c->stream));
     CK(cudaGetLastError());
+    if (weights)
+        LAUNCH(NQS_STAGE_COUNT, launch_scan_chunks_u64((uint64_t*)c->chunk_w.p, (uint64_t*)c->Wtot.p,
+                                                       Ns, nch, c->stream));
     LAUNCH(NQS_STAGE_COUNT, launch_scan_chunks_u32((uint32_t*)c->chunk_cnt.p, (uint32_t*)c->chunk_off.p,
                                                    (int64_t*)c->det_tot.p, Ns, nch, c->stream));
     LAUNCH(NQS_STAGE_COUNT, launch_scan_i64((int64_t*)c->det_tot.p, (int64_t*)c->det_off.p, Ns, c->stream));
@@ -627,7 +646,7 @@ extern "C" int nqs_destroy(nqs_ctx* c)
     DevBuf* bufs[] = {&c->h1e, &c->eri, &c->pairs, &c->chol, &c->A, &c->AT, &c->W, &c->b,
                       &c->pred_ptr, &c->pred_idx, &c->st_samples, &c->st_counts,
                       &c->st_u, &c->st_out0, &c->st_out1, &c->st_out2, &c->st_out3, &c->st_out4,
-                      &c->chunk_cnt, &c->chunk_off, &c->chunk_w, &c->rem_max, &c->det_tot,
+                      &c->chunk_cnt, &c->chunk_off, &c->chunk_w, &c->det_tot,
                       &c->det_off, &c->det_rank, &c->det_coef, &c->Lenv, &c->Lexp, &c->Renv,
                       &c->Rexp, &c->Hst, &c->Hexp, &c->Gst, &c->Gexp, &c->theta, &c->lc,
                       &c->logf, &c->pmant, &c->pexp, &c->hdiag, &c->Wtot, &c->draw_rank64,
@@ -640,7 +659,7 @@ extern "C" int nqs_destroy(nqs_ctx* c)
                       &c->ftl_list, &c->ftr_list, &c->ftl_cnt, &c->frbl, &c->frbr, &c->frbl_base,
                       &c->frbr_base, &c->tc_img, &c->tc_exps, &c->part_det_abs,
                       &c->part_draw_abs, &c->eabs, &c->logf_save, &c->summary2, &c->ref_idx,
-                      &c->ref_s, &c->ref_c, &c->ref_pos, &c->ref_e, &c->h_all, &c->site_cnt,
+                      &c->ref_s, &c->ref_c, &c->ref_pos, &c->ref_e, &c->site_cnt,
                       &c->site_offs, &c->site_bounds, &c->site_items};
     for (DevBuf* b : bufs) release(*b);
     for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
@@ -895,7 +914,7 @@ extern "C" int nqs_connected(nqs_ctx* c, const uint64_t* samples, int64_t Ns, do
     TRY(reset_dev_error(c));
     LAUNCH(NQS_STAGE_OTHER, launch_validate(ds, Ns, c->K, c->na, c->nb, (DevError*)c->derr.p, c->stream));
     int64_t total = 0;
-    TRY(count_pass(c, ds, Ns, eb, &total));
+    TRY(count_pass(c, ds, Ns, eb, &total, false));
     TRY(read_dev_error(c));
     int64_t* doff;
     bool hoff;
@@ -919,7 +938,7 @@ extern "C" int nqs_connected(nqs_ctx* c, const uint64_t* samples, int64_t Ns, do
         a.samples = ds;
         a.eps_bits = eb;
         a.n_chunks = (uint32_t)((c->n_conn + 31) / 32);
-        a.rem_max_bits = (unsigned long long*)c->rem_max.p;
+        a.chunk_cnt = (uint32_t*)c->chunk_cnt.p;
         a.chunk_off = (const uint32_t*)c->chunk_off.p;
         a.det_off = (const int64_t*)c->det_off.p;
         a.out_rank = drank; a.out_det = ddet; a.out_H = dH; a.out_sign = dsg;
@@ -964,34 +983,26 @@ extern "C" int nqs_amplitude(nqs_ctx* c, const uint64_t* dets, int64_t n, double
 namespace {
 
 // Steps shared by nqs_draws and nqs_local_energy: weights, prefix, draws.
+// Steps after the count pass (which made the weights when draws follow):
+// the deterministic lists, then the draws.
 int draw_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, uint64_t eb, int n_draws,
-              uint64_t seed, int64_t* rank_out, bool write_dets, bool need_w,
-              const int64_t* index = nullptr, const double* h_all = nullptr)
+              uint64_t seed, int64_t* rank_out, bool write_dets, const int64_t* index = nullptr)
 {
     const uint32_t nch = (uint32_t)((c->n_conn + 31) / 32);
-    const bool weights = n_draws > 0 || need_w;
-    TRY(ensure(c, c->chunk_w, (size_t)Ns * nch * 8));
-    TRY(ensure(c, c->Wtot, (size_t)Ns * 8));
-    EnumArgs a{};
-    a.h = c->hv;
-    a.samples = ds;
-    a.eps_bits = eb;
-    a.n_chunks = nch;
-    a.rem_max_bits = (unsigned long long*)c->rem_max.p;
-    a.chunk_off = (const uint32_t*)c->chunk_off.p;
-    a.det_off = write_dets ? (const int64_t*)c->det_off.p : nullptr;
-    a.out_rank = write_dets ? (uint32_t*)c->det_rank.p : nullptr;
-    a.out_H = write_dets ? (double*)c->det_coef.p : nullptr;
-    a.chunk_w = weights ? (uint64_t*)c->chunk_w.p : nullptr;
-    a.h_in = h_all;
-    if (!write_dets && !weights) return NQS_OK;
-    {
+    if (write_dets) {
+        EnumArgs a{};
+        a.h = c->hv;
+        a.samples = ds;
+        a.eps_bits = eb;
+        a.n_chunks = nch;
+        a.chunk_cnt = (uint32_t*)c->chunk_cnt.p;
+        a.chunk_off = (const uint32_t*)c->chunk_off.p;
+        a.det_off = (const int64_t*)c->det_off.p;
+        a.out_rank = (uint32_t*)c->det_rank.p;
+        a.out_H = (double*)c->det_coef.p;
         StageScope sc(c, NQS_STAGE_WRITE);
         LAUNCH(NQS_STAGE_WRITE, launch_enum(a, Ns, true, c->stream));
         CK(cudaGetLastError());
-        if (weights)
-            LAUNCH(NQS_STAGE_WRITE, launch_scan_chunks_u64((uint64_t*)c->chunk_w.p, (uint64_t*)c->Wtot.p,
-                                                          Ns, nch, c->stream));
     }
     if (n_draws > 0) {
         StageScope sc(c, NQS_STAGE_DRAW);
@@ -1002,13 +1013,12 @@ int draw_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, uint64_t eb, int n_dra
         d.eps_bits = eb;
         d.n_chunks = nch;
         d.chunk_pre = (const uint64_t*)c->chunk_w.p;
-        d.rem_max_bits = (const unsigned long long*)c->rem_max.p;
+        d.shift = weight_shift(c, eb);
         d.n_draws = n_draws;
         d.seed = seed;
         d.index_base = c->index_base;
         d.index = index;
         d.out_rank = rank_out;
-        d.h_all = h_all;
         LAUNCH(NQS_STAGE_DRAW, launch_draws(d, c->stream));
     }
     CK(cudaGetLastError());
@@ -1034,12 +1044,12 @@ extern "C" int nqs_draws(nqs_ctx* c, const uint64_t* samples, int64_t Ns, double
     TRY(reset_dev_error(c));
     LAUNCH(NQS_STAGE_OTHER, launch_validate(ds, Ns, c->K, c->na, c->nb, (DevError*)c->derr.p, c->stream));
     int64_t total = 0;
-    TRY(count_pass(c, ds, Ns, eb, &total));
+    TRY(count_pass(c, ds, Ns, eb, &total, n_draws > 0 || w_total != nullptr));
     TRY(read_dev_error(c));
     int64_t* dr = nullptr;
     bool hr = false;
     if (n_draws > 0) TRY(stage_out(c, c->st_out0, ranks, (size_t)Ns * n_draws, &dr, &hr));
-    TRY(draw_pass(c, ds, Ns, eb, n_draws, seed, dr, false, w_total != nullptr));
+    TRY(draw_pass(c, ds, Ns, eb, n_draws, seed, dr, false));
     if (n_draws > 0) TRY(copy_back(c, ranks, dr, (size_t)Ns * n_draws, hr));
     if (w_total) {
         uint64_t* dw;
@@ -1079,23 +1089,8 @@ int le_core(nqs_ctx* c, const uint64_t* ds, const double* dc, int64_t Ns, uint64
                                                                        (DevError*)c->derr.p);
         LAUNCH(NQS_STAGE_ENV, 1);
     }
-    // every H_nm of the batch, stored once by the count pass when it fits: the
-    // write pass, the draws and the dedup then read it instead of evaluating
-    // the Slater-Condon elements again
-    double* hall = nullptr;
-    {
-        const size_t hbytes = (size_t)Ns * (size_t)c->n_conn * 8;
-        size_t fr = 0, tt = 0;
-        cudaMemGetInfo(&fr, &tt);
-        size_t cap = std::min<size_t>((size_t)32 << 30, fr / 4);
-        if (c->fam_budget > 0) cap = std::min(cap, c->fam_budget);
-        if (hbytes <= c->h_all.n || hbytes <= cap) {
-            TRY(ensure(c, c->h_all, hbytes));
-            hall = (double*)c->h_all.p;
-        }
-    }
     int64_t total = 0;
-    TRY(count_pass(c, ds, Ns, eb, &total, hall));
+    TRY(count_pass(c, ds, Ns, eb, &total, n_draws > 0));
     if (shared) {
         c->det_off_h.resize(Ns + 1);
         CK(cudaMemcpyAsync(c->det_off_h.data(), c->det_off.p, (size_t)(Ns + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
@@ -1109,7 +1104,7 @@ int le_core(nqs_ctx* c, const uint64_t* ds, const double* dc, int64_t Ns, uint64
         TRY(ensure(c, c->draw_coef, (size_t)Ns * n_draws * 8));
         TRY(ensure(c, c->n_unique, (size_t)Ns * 8));
     }
-    TRY(draw_pass(c, ds, Ns, eb, n_draws, seed, (int64_t*)c->draw_rank64.p, true, false, dindex, hall));
+    TRY(draw_pass(c, ds, Ns, eb, n_draws, seed, (int64_t*)c->draw_rank64.p, true, dindex));
     if (n_draws > 0) {
         StageScope sc(c, NQS_STAGE_DRAW);
         DedupArgs d{};
@@ -1120,12 +1115,11 @@ int le_core(nqs_ctx* c, const uint64_t* ds, const double* dc, int64_t Ns, uint64
         int p2 = 1;
         while (p2 < n_draws) p2 <<= 1;
         d.pow2 = p2;
-        d.rem_max_bits = (const unsigned long long*)c->rem_max.p;
+        d.shift = weight_shift(c, eb);
         d.W = (const uint64_t*)c->Wtot.p;
         d.out_rank = (uint32_t*)c->draw_rank.p;
         d.out_coef = (double*)c->draw_coef.p;
         d.n_unique = (int64_t*)c->n_unique.p;
-        d.h_all = hall;
         LAUNCH(NQS_STAGE_DRAW, launch_dedup(d, Ns, c->stream));
         CK(cudaGetLastError());
     }
@@ -1399,10 +1393,10 @@ extern "C" int nqs_draws_noalloc(nqs_ctx* c, const uint64_t* samples, int64_t Ns
         (w_total && !is_device_ptr(w_total)))
         return set_err(c, NQS_ERR_INVALID_ARG,
                        "nqs_draws_noalloc needs device pointers (host arrays would need staging)");
-    // scratch layout (64-bit words): error word (2), rem_max [Ns], W [Ns],
-    // chunk weights [Ns][nch], chunk counts [Ns][nch] as 32-bit halves
+    // scratch layout (64-bit words): error word (2), W [Ns], chunk weights
+    // [Ns][nch], chunk counts [Ns][nch] as 32-bit halves
     const uint64_t nch = (uint64_t)((c->n_conn + 31) / 32);
-    const uint64_t need = 2 + 2 * (uint64_t)Ns + (uint64_t)Ns * nch + ((uint64_t)Ns * nch + 1) / 2;
+    const uint64_t need = 2 + (uint64_t)Ns + (uint64_t)Ns * nch + ((uint64_t)Ns * nch + 1) / 2;
     if (need > kNoAllocWords)
         return set_err(c, NQS_ERR_INVALID_ARG,
                        "nqs_draws_noalloc: %lld samples x %llu rank chunks need %llu scratch words, "
@@ -1418,12 +1412,10 @@ extern "C" int nqs_draws_noalloc(nqs_ctx* c, const uint64_t* samples, int64_t Ns
     }
     unsigned long long* base = g_noalloc_addr[c->device];
     DevError* derr = (DevError*)base;
-    unsigned long long* rem_max = base + 2;
-    uint64_t* W = (uint64_t*)(rem_max + Ns);
+    uint64_t* W = (uint64_t*)(base + 2);
     uint64_t* chunk_w = W + Ns;
     uint32_t* chunk_cnt = (uint32_t*)(chunk_w + (size_t)Ns * nch);
     CK(cudaMemsetAsync(derr, 0, sizeof(DevError), c->stream));
-    CK(cudaMemsetAsync(rem_max, 0, (size_t)Ns * 8, c->stream));
     LAUNCH(NQS_STAGE_OTHER, launch_validate(samples, Ns, c->K, c->na, c->nb, derr, c->stream));
     EnumArgs a{};
     a.h = c->hv;
@@ -1431,11 +1423,10 @@ extern "C" int nqs_draws_noalloc(nqs_ctx* c, const uint64_t* samples, int64_t Ns
     a.eps_bits = eb;
     a.n_chunks = (uint32_t)nch;
     a.chunk_cnt = chunk_cnt;
-    a.rem_max_bits = rem_max;
-    LAUNCH(NQS_STAGE_COUNT, launch_enum(a, Ns, false, c->stream));
+    a.shift = weight_shift(c, eb);
     a.chunk_w = chunk_w;
-    LAUNCH(NQS_STAGE_WRITE, launch_enum(a, Ns, true, c->stream));
-    LAUNCH(NQS_STAGE_WRITE, launch_scan_chunks_u64(chunk_w, W, Ns, (uint32_t)nch, c->stream));
+    LAUNCH(NQS_STAGE_COUNT, launch_enum(a, Ns, false, c->stream));
+    LAUNCH(NQS_STAGE_COUNT, launch_scan_chunks_u64(chunk_w, W, Ns, (uint32_t)nch, c->stream));
     if (nch == 0) CK(cudaMemsetAsync(W, 0, (size_t)Ns * 8, c->stream));
     if (n_draws > 0) {
         DrawArgs d{};
@@ -1445,7 +1436,7 @@ extern "C" int nqs_draws_noalloc(nqs_ctx* c, const uint64_t* samples, int64_t Ns
         d.eps_bits = eb;
         d.n_chunks = (uint32_t)nch;
         d.chunk_pre = chunk_w;
-        d.rem_max_bits = rem_max;
+        d.shift = weight_shift(c, eb);
         d.n_draws = n_draws;
         d.seed = seed;
         d.index_base = c->index_base;

@@ -3,24 +3,17 @@
 //
 // Work unit: a "chunk" of 32 consecutive canonical ranks of one sample, one
 // warp-wide evaluation. The count pass records, per chunk, how many entries
-// pass |H| >= eps and the largest remainder |H| of the sample; the write pass
-// compacts the deterministic entries with a ballot prefix and sums the
-// integer remainder weights per chunk; the draw pass inverts the per-sample
-// prefix of those sums and re-evaluates one chunk per draw.
+// pass |H| >= eps and the sum of the integer remainder weights (their shift
+// depends only on eps and n_conn, so one pass suffices); the write pass
+// revisits only the chunks that hold deterministic entries and compacts them
+// with a ballot prefix; the draw pass inverts the per-sample prefix of the
+// weight sums and re-evaluates one chunk per draw.
 #include "nqs_kernels.cuh"
 
 namespace nqs {
 
 constexpr int kEnumWarps = 8;       // warps per block
 constexpr int kChunksPerWarp = 4;   // consecutive chunks per warp
-
-__device__ __forceinline__ int shift_of(unsigned long long max_bits, int bitlen_nconn)
-{
-    if (max_bits == 0) return 0;
-    int e;
-    frexp(__longlong_as_double((long long)max_bits), &e);
-    return 62 - e - bitlen_nconn;
-}
 
 template <bool WRITE>
 __global__ void __launch_bounds__(kEnumWarps * 32) k_enum(EnumArgs a)
@@ -32,68 +25,36 @@ __global__ void __launch_bounds__(kEnumWarps * 32) k_enum(EnumArgs a)
     if (warp == 0) build_lists_warp(na, nb, a.h.K, lists, lane);
     __syncthreads();
     const HamView& h = a.h;
-    int shift = 0;
-    if (WRITE) shift = shift_of(a.rem_max_bits[s], h.bitlen_nconn);
-    uint64_t max_bits = 0;
     const size_t srow = (size_t)s * a.n_chunks;
-    // stored elements: issue the loads of all of this warp's chunks at once
-    double Hpre[kChunksPerWarp];
-    if (WRITE && a.h_in) {
-        #pragma unroll
-        for (int k = 0; k < kChunksPerWarp; ++k) {
-            const uint32_t c = (blockIdx.x * kEnumWarps + warp) * kChunksPerWarp + k;
-            const uint32_t r = c * 32 + lane;
-            Hpre[k] = (c < a.n_chunks && r < h.n_conn) ? __ldcs(a.h_in + (size_t)s * h.n_conn + r) : 0.0;
-        }
-    }
-    #pragma unroll
     for (int k = 0; k < kChunksPerWarp; ++k) {
         const uint32_t c = (blockIdx.x * kEnumWarps + warp) * kChunksPerWarp + k;
         if (c >= a.n_chunks) break;
+        if (WRITE && a.chunk_cnt[srow + c] == 0) continue;   // no deterministic entry here
         const uint32_t r = c * 32 + lane;
         const bool valid = r < h.n_conn;
         double H = 0.0;
         uint64_t ma = 0, mb = 0;
         int odd = 0;
         if (valid) {
-            if (WRITE && a.h_in) {
-                H = Hpre[k];
-            } else {
-                Exc e = decode_rank(h, lists, r);
-                H = matrix_element(h, na, nb, e, ma, mb, odd);
-                if (!WRITE && a.h_store) a.h_store[(size_t)s * h.n_conn + r] = H;
-            }
+            Exc e = decode_rank(h, lists, r);
+            H = matrix_element(h, na, nb, e, ma, mb, odd);
         }
         const bool det = valid && is_det(H, a.eps_bits);
         const unsigned bal = __ballot_sync(kFull, det);
         if (!WRITE) {
             if (lane == 0) a.chunk_cnt[srow + c] = __popc(bal);
-            if (valid && !det) {
-                uint64_t b = (uint64_t)__double_as_longlong(H) & 0x7fffffffffffffffull;
-                max_bits = b > max_bits ? b : max_bits;
-            }
-        } else {
-            if (det && a.det_off) {
-                const int64_t pos = a.det_off[s] + a.chunk_off[srow + c] +
-                                    __popc(bal & ((1u << lane) - 1u));
-                if (a.out_rank) a.out_rank[pos] = r;
-                if (a.out_H) a.out_H[pos] = H;
-                if (a.out_det) { a.out_det[2 * pos] = ma; a.out_det[2 * pos + 1] = mb; }
-                if (a.out_sign) a.out_sign[pos] = odd ? -1 : 1;
-            }
             if (a.chunk_w) {
-                uint64_t w = (valid && !det) ? weight_of(H, shift) : 0ull;
+                uint64_t w = (valid && !det) ? weight_of(H, a.shift) : 0ull;
                 w = warp_sum_u64(w);
                 if (lane == 0) a.chunk_w[srow + c] = w;
             }
+        } else if (det) {
+            const int64_t pos = a.det_off[s] + a.chunk_off[srow + c] + __popc(bal & ((1u << lane) - 1u));
+            if (a.out_rank) a.out_rank[pos] = r;
+            if (a.out_H) a.out_H[pos] = H;
+            if (a.out_det) { a.out_det[2 * pos] = ma; a.out_det[2 * pos + 1] = mb; }
+            if (a.out_sign) a.out_sign[pos] = odd ? -1 : 1;
         }
-    }
-    if (!WRITE) {
-        for (int o = 16; o; o >>= 1) {
-            uint64_t t = __shfl_xor_sync(kFull, max_bits, o);
-            max_bits = t > max_bits ? t : max_bits;
-        }
-        if (lane == 0 && max_bits) atomicMax(&a.rem_max_bits[s], (unsigned long long)max_bits);
     }
 }
 
@@ -132,10 +93,8 @@ __global__ void __launch_bounds__(256) k_draws(DrawArgs a)
         return;
     }
     const uint64_t na = a.samples[2 * s], nb = a.samples[2 * s + 1];
-    if (!a.h_all) {
-        build_lists_warp(na, nb, a.h.K, lists[warp], lane);
-        __syncwarp();
-    }
+    build_lists_warp(na, nb, a.h.K, lists[warp], lane);
+    __syncwarp();
     // target t = floor(x W / 2^64), then the first chunk whose inclusive prefix > t
     const uint64_t x = philox_first((uint64_t)d, (uint64_t)(a.index ? a.index[s] : a.index_base + s), a.seed);
     const uint64_t t = __umul64hi(x, W);
@@ -162,20 +121,14 @@ __global__ void __launch_bounds__(256) k_draws(DrawArgs a)
         lo = lo + (uint32_t)(__ffs(above) - 1);
     }
     const uint32_t c = lo;
-    const int shift = shift_of(a.rem_max_bits[s], a.h.bitlen_nconn);
     const uint32_t r = c * 32 + lane;
     uint64_t w = 0;
     if (r < a.h.n_conn) {
-        double H;
-        if (a.h_all) {
-            H = a.h_all[(size_t)s * a.h.n_conn + r];
-        } else {
-            Exc e = decode_rank(a.h, lists[warp], r);
-            uint64_t ma, mb;
-            int odd;
-            H = matrix_element(a.h, na, nb, e, ma, mb, odd);
-        }
-        if (!is_det(H, a.eps_bits)) w = weight_of(H, shift);
+        Exc e = decode_rank(a.h, lists[warp], r);
+        uint64_t ma, mb;
+        int odd;
+        const double H = matrix_element(a.h, na, nb, e, ma, mb, odd);
+        if (!is_det(H, a.eps_bits)) w = weight_of(H, a.shift);
     }
     const uint64_t incl = warp_incl_scan_u64(w, lane);
     const uint64_t base = c ? a.chunk_pre[srow + c - 1] : 0ull;
@@ -239,23 +192,17 @@ __global__ void __launch_bounds__(1024) k_dedup(DedupArgs a)
     }
     int u = head_scan[threadIdx.x] - cnt;   // exclusive
     const int total = head_scan[blockDim.x - 1];
-    const int shift = shift_of(a.rem_max_bits[s], a.h.bitlen_nconn);
     const uint64_t W = a.W[s];
     for (int i = i0; i < i0 + per && i < P; ++i) {
         if (keys[i] == 0xffffffffu || (i > 0 && keys[i] == keys[i - 1])) continue;
         int e = i + 1;
         while (e < P && keys[e] == keys[i]) ++e;
         const uint32_t r = keys[i];
-        double H;
-        if (a.h_all) {
-            H = a.h_all[(size_t)s * a.h.n_conn + r];
-        } else {
-            Exc ex = decode_rank(a.h, lists, r);
-            uint64_t ma, mb;
-            int odd;
-            H = matrix_element(a.h, na, nb, ex, ma, mb, odd);
-        }
-        uint64_t w = weight_of(H, shift);
+        Exc ex = decode_rank(a.h, lists, r);
+        uint64_t ma, mb;
+        int odd;
+        const double H = matrix_element(a.h, na, nb, ex, ma, mb, odd);
+        uint64_t w = weight_of(H, a.shift);
         double coef = ((double)(e - i) / (double)a.n_draws) * H * ((double)W / (double)w);
         a.out_rank[base + u] = r;
         a.out_coef[base + u] = coef;

@@ -31,18 +31,17 @@ struct EnumArgs {
     int s0;                              // first sample of this launch (set by the launcher)
     uint64_t eps_bits;                   // bits of |eps|
     uint32_t n_chunks;                   // ceil(n_conn / 32)
-    uint32_t* chunk_cnt;                 // count pass: [Ns][n_chunks] entries with |H| >= eps
-    unsigned long long* rem_max_bits;    // [Ns] bits of max |H| over the remainder
+    uint32_t* chunk_cnt;                 // [Ns][n_chunks] entries with |H| >= eps (count pass
+                                         // writes; the write pass skips chunks without any)
+    int shift;                           // remainder weights w = ceil(|H| 2^shift)
     const uint32_t* chunk_off;           // write pass: exclusive prefix of chunk_cnt per sample
     const int64_t* det_off;              // [Ns+1] start of each sample's list (NULL: no list)
     uint32_t* out_rank;
     double* out_H;
     uint64_t* out_det;
     int8_t* out_sign;
-    uint64_t* chunk_w;                   // [Ns][n_chunks] remainder weight sums (NULL: skip)
-    double* h_store;                     // count pass: every H_nm at [s][rank] (NULL: none)
-    const double* h_in;                  // write pass: read H_nm there instead of evaluating
-                                         // (only without out_det / out_sign)
+    uint64_t* chunk_w;                   // count pass: [Ns][n_chunks] remainder weight sums
+                                         // (NULL: skip)
 };
 int launch_enum(const EnumArgs& a, int64_t Ns, bool write, cudaStream_t st);
 
@@ -53,13 +52,12 @@ struct DrawArgs {
     uint64_t eps_bits;
     uint32_t n_chunks;
     const uint64_t* chunk_pre;           // [Ns][n_chunks] inclusive prefix of weights
-    const unsigned long long* rem_max_bits;
+    int shift;                           // remainder weight shift
     int n_draws;
     uint64_t seed;
     int64_t index_base;                  // Philox sample counter of samples[0]
     const int64_t* index;                // per-sample Philox counters (NULL: index_base + s)
     int64_t* out_rank;                   // [Ns][n_draws]
-    const double* h_all;                 // stored H_nm [Ns][n_conn] (NULL: evaluate)
 };
 int launch_draws(const DrawArgs& a, cudaStream_t st);
 
@@ -69,12 +67,11 @@ struct DedupArgs {
     const int64_t* ranks;                // [Ns][n_draws]
     int n_draws;
     int pow2;                            // next power of two >= n_draws
-    const unsigned long long* rem_max_bits;
+    int shift;                           // remainder weight shift
     const uint64_t* W;                   // [Ns] total remainder weight
     uint32_t* out_rank;                  // [Ns][n_draws] unique ranks (first n_unique)
     double* out_coef;                    // [Ns][n_draws]
     int64_t* n_unique;                   // [Ns]
-    const double* h_all;                 // stored H_nm [Ns][n_conn] (NULL: evaluate)
 };
 int launch_dedup(const DedupArgs& a, int64_t Ns, cudaStream_t st);
 
