@@ -46,7 +46,7 @@ struct nqs_ctx {
 
     // staging and workspace
     DevBuf st_samples, st_counts, st_u, st_out0, st_out1, st_out2, st_out3, st_out4;
-    DevBuf chunk_cnt, chunk_off, chunk_w, det_tot, det_off, det_rank, det_coef;
+    DevBuf chunk_cnt, chunk_mask, chunk_off, chunk_w, det_tot, det_off, det_rank, det_coef;
     DevBuf Lenv, Lexp, Renv, Rexp, Hst, Hexp, Gst, Gexp, theta, lc, logf, pmant, pexp, hdiag;
     DevBuf Wtot, draw_rank64, draw_rank, draw_coef, n_unique;
     DevBuf base_det, base_draw, part_det, part_draw, eloc, edet, estoch, summary, derr;
@@ -288,6 +288,7 @@ int count_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, uint64_t eb, int
 {
     const uint32_t nch = (uint32_t)((c->n_conn + 31) / 32);
     TRY(ensure(c, c->chunk_cnt, (size_t)Ns * nch * 4));
+    TRY(ensure(c, c->chunk_mask, (size_t)Ns * nch * 4));
     TRY(ensure(c, c->chunk_off, (size_t)Ns * nch * 4));
     TRY(ensure(c, c->det_tot, (size_t)Ns * 8));
     TRY(ensure(c, c->det_off, (size_t)(Ns + 1) * 8));
@@ -301,6 +302,7 @@ int count_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, uint64_t eb, int
     a.eps_bits = eb;
     a.n_chunks = nch;
     a.chunk_cnt = (uint32_t*)c->chunk_cnt.p;
+    a.chunk_mask = (uint32_t*)c->chunk_mask.p;
     a.shift = weight_shift(c, eb);
     a.chunk_w = weights ? (uint64_t*)c->chunk_w.p : nullptr;
     StageScope sc(c, NQS_STAGE_COUNT);
@@ -646,7 +648,7 @@ extern "C" int nqs_destroy(nqs_ctx* c)
     DevBuf* bufs[] = {&c->h1e, &c->eri, &c->pairs, &c->chol, &c->A, &c->AT, &c->W, &c->b,
                       &c->pred_ptr, &c->pred_idx, &c->st_samples, &c->st_counts,
                       &c->st_u, &c->st_out0, &c->st_out1, &c->st_out2, &c->st_out3, &c->st_out4,
-                      &c->chunk_cnt, &c->chunk_off, &c->chunk_w, &c->det_tot,
+                      &c->chunk_cnt, &c->chunk_mask, &c->chunk_off, &c->chunk_w, &c->det_tot,
                       &c->det_off, &c->det_rank, &c->det_coef, &c->Lenv, &c->Lexp, &c->Renv,
                       &c->Rexp, &c->Hst, &c->Hexp, &c->Gst, &c->Gexp, &c->theta, &c->lc,
                       &c->logf, &c->pmant, &c->pexp, &c->hdiag, &c->Wtot, &c->draw_rank64,
@@ -939,6 +941,7 @@ extern "C" int nqs_connected(nqs_ctx* c, const uint64_t* samples, int64_t Ns, do
         a.eps_bits = eb;
         a.n_chunks = (uint32_t)((c->n_conn + 31) / 32);
         a.chunk_cnt = (uint32_t*)c->chunk_cnt.p;
+        a.chunk_mask = (uint32_t*)c->chunk_mask.p;
         a.chunk_off = (const uint32_t*)c->chunk_off.p;
         a.det_off = (const int64_t*)c->det_off.p;
         a.out_rank = drank; a.out_det = ddet; a.out_H = dH; a.out_sign = dsg;
@@ -996,6 +999,7 @@ int draw_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, uint64_t eb, int n_dra
         a.eps_bits = eb;
         a.n_chunks = nch;
         a.chunk_cnt = (uint32_t*)c->chunk_cnt.p;
+        a.chunk_mask = (uint32_t*)c->chunk_mask.p;
         a.chunk_off = (const uint32_t*)c->chunk_off.p;
         a.det_off = (const int64_t*)c->det_off.p;
         a.out_rank = (uint32_t*)c->det_rank.p;

@@ -2,12 +2,12 @@
 // remainder weights and the Philox draws (Sec. 2.4, Sec. 3).
 //
 // Work unit: a "chunk" of 32 consecutive canonical ranks of one sample, one
-// warp-wide evaluation. The count pass records, per chunk, how many entries
-// pass |H| >= eps and the sum of the integer remainder weights (their shift
-// depends only on eps and n_conn, so one pass suffices); the write pass
-// revisits only the chunks that hold deterministic entries and compacts them
-// with a ballot prefix; the draw pass inverts the per-sample prefix of the
-// weight sums and re-evaluates one chunk per draw.
+// warp-wide evaluation. The count pass records, per chunk, the ballot mask of
+// the entries with |H| >= eps, their number and the sum of the integer
+// remainder weights (their shift depends only on eps and n_conn, so one pass
+// suffices); the write pass evaluates only the deterministic entries, packed
+// densely into warps by the masks; the draw pass inverts the per-sample prefix
+// of the weight sums and re-evaluates one chunk per draw.
 #include "nqs_kernels.cuh"
 
 namespace nqs {
@@ -15,7 +15,6 @@ namespace nqs {
 constexpr int kEnumWarps = 8;       // warps per block
 constexpr int kChunksPerWarp = 4;   // consecutive chunks per warp
 
-template <bool WRITE>
 __global__ void __launch_bounds__(kEnumWarps * 32) k_enum(EnumArgs a)
 {
     __shared__ OrbLists lists;
@@ -29,38 +28,89 @@ __global__ void __launch_bounds__(kEnumWarps * 32) k_enum(EnumArgs a)
     for (int k = 0; k < kChunksPerWarp; ++k) {
         const uint32_t c = (blockIdx.x * kEnumWarps + warp) * kChunksPerWarp + k;
         if (c >= a.n_chunks) break;
-        if (WRITE && a.chunk_cnt[srow + c] == 0) continue;   // no deterministic entry here
         const uint32_t r = c * 32 + lane;
         const bool valid = r < h.n_conn;
         double H = 0.0;
-        uint64_t ma = 0, mb = 0;
-        int odd = 0;
         if (valid) {
+            uint64_t ma, mb;
+            int odd;
             Exc e = decode_rank(h, lists, r);
             H = matrix_element(h, na, nb, e, ma, mb, odd);
         }
         const bool det = valid && is_det(H, a.eps_bits);
         const unsigned bal = __ballot_sync(kFull, det);
-        if (!WRITE) {
-            if (lane == 0) a.chunk_cnt[srow + c] = __popc(bal);
-            if (a.chunk_w) {
-                uint64_t w = (valid && !det) ? weight_of(H, a.shift) : 0ull;
-                w = warp_sum_u64(w);
-                if (lane == 0) a.chunk_w[srow + c] = w;
-            }
-        } else if (det) {
-            const int64_t pos = a.det_off[s] + a.chunk_off[srow + c] + __popc(bal & ((1u << lane) - 1u));
-            if (a.out_rank) a.out_rank[pos] = r;
-            if (a.out_H) a.out_H[pos] = H;
-            if (a.out_det) { a.out_det[2 * pos] = ma; a.out_det[2 * pos + 1] = mb; }
-            if (a.out_sign) a.out_sign[pos] = odd ? -1 : 1;
+        if (lane == 0) {
+            a.chunk_cnt[srow + c] = __popc(bal);
+            if (a.chunk_mask) a.chunk_mask[srow + c] = bal;
         }
+        if (a.chunk_w) {
+            uint64_t w = (valid && !det) ? weight_of(H, a.shift) : 0ull;
+            w = warp_sum_u64(w);
+            if (lane == 0) a.chunk_w[srow + c] = w;
+        }
+    }
+}
+
+// Write pass: the deterministic entries of 8 consecutive chunks per warp,
+// dealt out one per lane through the chunks' ballot masks (about 30 per warp
+// on H50 instead of 8 live lanes out of 32 per chunk). Entry j of the group
+// lies in the chunk whose mask prefix brackets j; its list position is that
+// chunk's offset plus its rank among the chunk's set bits, so the lists stay
+// in canonical order.
+constexpr int kWriteChunks = 8;
+
+__global__ void __launch_bounds__(kEnumWarps * 32) k_write_dets(EnumArgs a)
+{
+    __shared__ OrbLists lists;
+    const int s = a.s0 + blockIdx.y;
+    const uint64_t na = a.samples[2 * s], nb = a.samples[2 * s + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) build_lists_warp(na, nb, a.h.K, lists, lane);
+    __syncthreads();
+    const HamView& h = a.h;
+    const size_t srow = (size_t)s * a.n_chunks;
+    const uint32_t c0 = (blockIdx.x * kEnumWarps + warp) * kWriteChunks;
+    if (c0 >= a.n_chunks) return;
+    uint32_t m = 0;
+    if (lane < kWriteChunks && c0 + lane < a.n_chunks) m = a.chunk_mask[srow + c0 + lane];
+    const int cnt = __popc(m);
+    int incl = cnt;
+    for (int o = 1; o < kWriteChunks; o <<= 1) {
+        const int u = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += u;
+    }
+    int ex[kWriteChunks];
+    uint32_t mk[kWriteChunks];
+    #pragma unroll
+    for (int k = 0; k < kWriteChunks; ++k) {
+        ex[k] = __shfl_sync(kFull, incl - cnt, k);
+        mk[k] = __shfl_sync(kFull, m, k);
+    }
+    const int total = __shfl_sync(kFull, incl, kWriteChunks - 1);
+    for (int j = lane; j < total; j += 32) {
+        int k = 0;
+        #pragma unroll
+        for (int q = 1; q < kWriteChunks; ++q)
+            if (ex[q] <= j) k = q;
+        const int idx = j - ex[k];                   // rank among the chunk's set bits
+        uint32_t bits = mk[k];
+        for (int q = 0; q < idx; ++q) bits &= bits - 1u;
+        const uint32_t r = (c0 + k) * 32 + (uint32_t)(__ffs(bits) - 1);
+        uint64_t ma, mb;
+        int odd;
+        const Exc e = decode_rank(h, lists, r);
+        const double H = matrix_element(h, na, nb, e, ma, mb, odd);
+        const int64_t pos = a.det_off[s] + a.chunk_off[srow + c0 + k] + idx;
+        if (a.out_rank) a.out_rank[pos] = r;
+        if (a.out_H) a.out_H[pos] = H;
+        if (a.out_det) { a.out_det[2 * pos] = ma; a.out_det[2 * pos + 1] = mb; }
+        if (a.out_sign) a.out_sign[pos] = odd ? -1 : 1;
     }
 }
 
 int launch_enum(const EnumArgs& args, int64_t Ns, bool write, cudaStream_t st)
 {
-    const uint32_t per_block = kEnumWarps * kChunksPerWarp;
+    const uint32_t per_block = kEnumWarps * (write ? kWriteChunks : kChunksPerWarp);
     const uint32_t gx = (args.n_chunks + per_block - 1) / per_block;
     if (gx == 0) return 0;
     int n = 0;
@@ -68,8 +118,8 @@ int launch_enum(const EnumArgs& args, int64_t Ns, bool write, cudaStream_t st)
         EnumArgs a = args;
         a.s0 = (int)s0;
         dim3 grid(gx, (unsigned)((Ns - s0) < 65535 ? (Ns - s0) : 65535));
-        if (write) k_enum<true><<<grid, kEnumWarps * 32, 0, st>>>(a);
-        else k_enum<false><<<grid, kEnumWarps * 32, 0, st>>>(a);
+        if (write) k_write_dets<<<grid, kEnumWarps * 32, 0, st>>>(a);
+        else k_enum<<<grid, kEnumWarps * 32, 0, st>>>(a);
     }
     return n;
 }

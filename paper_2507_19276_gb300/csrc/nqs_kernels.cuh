@@ -33,6 +33,8 @@ struct EnumArgs {
     uint32_t n_chunks;                   // ceil(n_conn / 32)
     uint32_t* chunk_cnt;                 // [Ns][n_chunks] entries with |H| >= eps (count pass
                                          // writes; the write pass skips chunks without any)
+    uint32_t* chunk_mask;                // [Ns][n_chunks] ballot of |H| >= eps (count pass writes
+                                         // if non-NULL; the write pass needs it)
     int shift;                           // remainder weights w = ceil(|H| 2^shift)
     const uint32_t* chunk_off;           // write pass: exclusive prefix of chunk_cnt per sample
     const int64_t* det_off;              // [Ns+1] start of each sample's list (NULL: no list)
