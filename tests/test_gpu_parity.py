@@ -318,3 +318,28 @@ def test_grad_vjp_matches_oracle(ctx, cases, problems, name):
     if rW is not None:
         assert np.max(np.abs(gW - rW)) < 1e-10 * max(1.0, np.max(np.abs(rW)))
         assert np.max(np.abs(gb - rb)) < 1e-10 * max(1.0, np.max(np.abs(rb)))
+
+
+@pytest.mark.parametrize("D", [16, 32, 48, 128, 192, 256])
+def test_bond_dimensions_of_the_tensor_core_path(ctx, D):
+    """Every tile shape of the shared-prefix path: D = 16..128 in one
+    reduction chunk (48 through the run-time-D epilogue), 192 and 256 in
+    chunks of 64; mixed against the mixed bar, FP64 shared against the FP64
+    bar, with draws."""
+    sys_ = W.tiny_system(K=7, na=3, nb=3, D=D, n_hidden=6, seed=60 + D, eps=0.02, n_draws=48,
+                         n_samples=10)
+    P = O.Problem(sys_)
+    ref = O.local_energy(P, cond=True)
+    try:
+        for prec in (nqs.NQS_PREC_MIXED, nqs.NQS_PREC_FP64_SHARED):
+            _load(ctx, sys_, prec)
+            e, summ = ctx.local_energy(sys_.samples, sys_.counts, sys_.eps, sys_.n_draws, sys_.seed)
+            assert summ["n_det"] == int(np.sum(ref["n_det"]))
+            if prec == nqs.NQS_PREC_MIXED:
+                err = _rel_abs(e, ref)
+                print(f"D={D}: mixed max error / max(|E|, e_abs) = {err:.3e}")
+                assert err < RTOL_MIXED
+            else:
+                assert _rel_sum(e, ref) < RTOL_FP64
+    finally:
+        ctx.set_precision(nqs.NQS_PREC_FP64)
