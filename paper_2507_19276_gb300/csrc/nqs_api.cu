@@ -40,7 +40,8 @@ struct nqs_ctx {
     bool has_ans = false;
     AnsatzView av{};
     DevBuf A, AT, W, b, pred_ptr, pred_idx;
-    DevBuf Af, ATf, Wf;       // FP32 copies for the shared-prefix FP32 path
+    DevBuf WT;                // W transposed, [2K][n_hidden rounded up to 4], zero-padded
+    DevBuf Af, ATf, WTf;      // FP32 copies for the shared-prefix FP32 path
     DevBuf tc_img, tc_exps;   // split-FP16 operand images for the tensor-core batches
     bool has_tc = false;
 
@@ -509,7 +510,7 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
     f.AT = (const T*)(dbl ? c->AT.p : c->ATf.p);
     f.samples = ds;
     f.n_hidden = c->av.n_hidden;
-    f.Wd = (const double*)c->W.p;
+    f.WT = (const T*)(dbl ? c->WT.p : c->WTf.p);
     f.theta = (const double*)c->theta.p;
     const int NH = c->av.n_hidden;
     RowSet rd{};
@@ -572,9 +573,9 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
             CK(cudaMemcpyAsync(c->frbl_base.p, lb.data(), (size_t)(nbb + 1) * 8, cudaMemcpyHostToDevice, c->stream));
             CK(cudaMemcpyAsync(c->frbr_base.p, rb.data(), (size_t)(nbb + 1) * 8, cudaMemcpyHostToDevice, c->stream));
             if (NH > 0) {
-                const size_t np = (size_t)((NH + 3) & ~3);
-                TRY(ensure(c, c->frbl, (size_t)lb[nbb] * (np + 4) * sizeof(T)));
-                TRY(ensure(c, c->frbr, (size_t)rb[nbb] * 2 * np * sizeof(T)));
+                const size_t rl = (size_t)rbm_row_len(NH);
+                TRY(ensure(c, c->frbl, (size_t)lb[nbb] * rl * sizeof(T)));
+                TRY(ensure(c, c->frbr, (size_t)rb[nbb] * rl * sizeof(T)));
             }
             // work: both sweeps (4 + 3t products at step t), every TL entry, every TR row
             c->fam_matvecs += (int64_t)nbb * 2 * (4 * (int64_t)K + 3 * (int64_t)K * (K - 1) / 2) +
@@ -655,7 +656,7 @@ extern "C" int nqs_destroy(nqs_ctx* c)
                       &c->draw_rank, &c->draw_coef, &c->n_unique, &c->base_det, &c->base_draw,
                       &c->part_det, &c->part_draw, &c->eloc, &c->edet, &c->estoch, &c->summary,
                       &c->derr, &c->span_det, &c->span_draw, &c->Af, &c->ATf,
-                      &c->Wf, &c->fG, &c->fGe, &c->fH, &c->fHe, &c->ftl_end,
+                      &c->WT, &c->WTf, &c->fG, &c->fGe, &c->fH, &c->fHe, &c->ftl_end,
                       &c->ftl_idx, &c->ftr_idx, &c->ftl_tot, &c->ftr_tot, &c->ftl_base,
                       &c->ftr_base, &c->fTL, &c->fTLe, &c->fTR, &c->fTRe, &c->ftl_ci,
                       &c->ftl_list, &c->ftr_list, &c->ftl_cnt, &c->frbl, &c->frbr, &c->frbl_base,
@@ -856,13 +857,21 @@ extern "C" int nqs_set_ansatz(nqs_ctx* c, const double* site_tensors, int n_edge
         CK(cudaMemcpy(c->Af.p, fA.data(), nt * 4, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(c->ATf.p, fAT.data(), nt * 4, cudaMemcpyHostToDevice));
         if (n_hidden > 0) {
-            const size_t nw = (size_t)n_hidden * 2 * K;
-            std::vector<double> hW(nw);
+            // transposed copies for the correlator factors: lanes over hidden units
+            // read consecutive words of one spin-orbital's column
+            const size_t nw = (size_t)n_hidden * 2 * K, np = (size_t)((n_hidden + 3) & ~3);
+            std::vector<double> hW(nw), hWT((size_t)2 * K * np, 0.0);
             CK(cudaMemcpy(hW.data(), c->W.p, nw * 8, cudaMemcpyDeviceToHost));
-            std::vector<float> fW(nw);
-            for (size_t i = 0; i < nw; ++i) fW[i] = (float)hW[i];
-            TRY(ensure(c, c->Wf, nw * 4));
-            CK(cudaMemcpy(c->Wf.p, fW.data(), nw * 4, cudaMemcpyHostToDevice));
+            std::vector<float> fWT(hWT.size(), 0.0f);
+            for (int k = 0; k < n_hidden; ++k)
+                for (int q = 0; q < 2 * K; ++q) {
+                    hWT[(size_t)q * np + k] = hW[(size_t)k * 2 * K + q];
+                    fWT[(size_t)q * np + k] = (float)hW[(size_t)k * 2 * K + q];
+                }
+            TRY(ensure(c, c->WT, hWT.size() * 8));
+            TRY(ensure(c, c->WTf, fWT.size() * 4));
+            CK(cudaMemcpy(c->WT.p, hWT.data(), hWT.size() * 8, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(c->WTf.p, fWT.data(), fWT.size() * 4, cudaMemcpyHostToDevice));
         }
     }
     AnsatzView a{};

@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(kEnumWarps * 32) k_enum(EnumArgs a)
         }
         if (a.chunk_w) {
             uint64_t w = (valid && !det) ? weight_of(H, a.shift) : 0ull;
-            w = warp_sum_u64(w);
+            w = warp_sum_sliced(w);
             if (lane == 0) a.chunk_w[srow + c] = w;
         }
     }
@@ -58,6 +58,18 @@ __global__ void __launch_bounds__(kEnumWarps * 32) k_enum(EnumArgs a)
 // chunk's offset plus its rank among the chunk's set bits, so the lists stay
 // in canonical order.
 constexpr int kWriteChunks = 8;
+
+// position of the (k+1)-th set bit of m (k < popc(m)), by halving with popc
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int k)
+{
+    int pos = 0;
+    #pragma unroll
+    for (int w = 16; w >= 2; w >>= 1) {
+        const int c = __popc(m & ((1u << w) - 1u));
+        if (k >= c) { k -= c; m >>= w; pos += w; }
+    }
+    return pos + (k >= (int)(m & 1u) ? 1 : 0);
+}
 
 __global__ void __launch_bounds__(kEnumWarps * 32) k_write_dets(EnumArgs a)
 {
@@ -88,14 +100,13 @@ __global__ void __launch_bounds__(kEnumWarps * 32) k_write_dets(EnumArgs a)
     }
     const int total = __shfl_sync(kFull, incl, kWriteChunks - 1);
     for (int j = lane; j < total; j += 32) {
-        int k = 0;
+        int k = 0, e0 = ex[0];                       // chunk of entry j, selected with
+        uint32_t bits = mk[0];                       // static indices (no local memory)
         #pragma unroll
         for (int q = 1; q < kWriteChunks; ++q)
-            if (ex[q] <= j) k = q;
-        const int idx = j - ex[k];                   // rank among the chunk's set bits
-        uint32_t bits = mk[k];
-        for (int q = 0; q < idx; ++q) bits &= bits - 1u;
-        const uint32_t r = (c0 + k) * 32 + (uint32_t)(__ffs(bits) - 1);
+            if (ex[q] <= j) { k = q; e0 = ex[q]; bits = mk[q]; }
+        const int idx = j - e0;                      // rank among the chunk's set bits
+        const uint32_t r = (c0 + k) * 32 + (uint32_t)nth_set_bit(bits, idx);
         uint64_t ma, mb;
         int odd;
         const Exc e = decode_rank(h, lists, r);

@@ -17,11 +17,12 @@
 // The correlator ratio (Eq. RBM) splits the same way: with theta_k(n), the
 // left part's spin-orbital flips dL and the right part's dR,
 //   f(m)/f(n) = prod_k cosh(theta_k + dL_k + dR_k) / cosh(theta_k)
-//             = PL * prod_k (1 + tanh(theta_k + dL_k) sinh(dR_k) + cosh(dR_k) - 1),
-//   PL = prod_k cosh(theta_k + dL_k) / cosh(theta_k),
-// so every left object stores tanh(theta + dL) and PL - 1, every right object
-// sinh(dR) and cosh(dR) - 1. Every vector carries a power-of-two exponent; T
-// is the arithmetic type of the contractions.
+//             = PL * PR * prod_k (1 + tanh(theta_k + dL_k) tanh(dR_k)),
+//   PL = prod_k cosh(theta_k + dL_k) / cosh(theta_k),  PR = prod_k cosh(dR_k)
+// (cosh(x + y) = cosh x cosh y (1 + tanh x tanh y)), so every left object
+// stores tanh(theta + dL) and PL - 1, every right object tanh(dR) and PR - 1:
+// a row reads one value per hidden unit from each side. Every vector carries a
+// power-of-two exponent; T is the arithmetic type of the contractions.
 #include "nqs_family.cuh"
 #include "nqs_tc.cuh"
 
@@ -341,6 +342,7 @@ __device__ __forceinline__ int nh_pad(int NH) { return (NH + 3) & ~3; }
 struct RowParts {
     int nsite;           // 2, 3 or 4 changed sites
     int s[4], a[4];      // sites ascending and alternative indices
+    int last;            // the last changed site
     uint64_t ma, mb;
 };
 
@@ -354,12 +356,18 @@ __device__ __forceinline__ RowParts row_parts(const HamView& h, const OrbLists& 
     if (e.kind == 2) { flip(ma, mb, e.j); flip(ma, mb, e.b); }
     uint64_t ch = (na ^ ma) | (nb ^ mb);
     r.nsite = 0;
-    while (ch && r.nsite < 4) {
-        const int p = __ffsll((long long)ch) - 1;
-        r.s[r.nsite] = p;
-        r.a[r.nsite] = alt_of(sigma_at(ma, mb, p), sigma_at(na, nb, p));
-        ++r.nsite;
-        ch &= ch - 1;
+    r.last = 0;
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) {          // static indices: the parts stay in registers
+        r.s[q] = 0; r.a[q] = 0;
+        if (ch) {
+            const int p = __ffsll((long long)ch) - 1;
+            r.s[q] = p;
+            r.a[q] = alt_of(sigma_at(ma, mb, p), sigma_at(na, nb, p));
+            r.nsite = q + 1;
+            r.last = p;
+            ch &= ch - 1;
+        }
     }
     r.ma = ma;
     r.mb = mb;
@@ -466,24 +474,38 @@ __global__ void k_fam_compact(FamArgs<T> f)
 // F4c: correlator factors of the left and right objects of a sample.
 //   left  objects: G families (s, a) [3K] then TL clusters [tl_count]
 //   right objects: H families (s, a) [3K] then TR rows [tr_total]
-// left:  tanh(theta_k + dL_k) for k < N_h, then PL - 1 at index N_h
-// right: sinh(dR_k), then cosh(dR_k) - 1 at index N_h + k
+// left:  tanh(theta_k + dL_k) for k < N_h, then PL - 1 at index NP
+// right: tanh(dR_k) for k < N_h, then PR - 1 at index NP
+// (NP = N_h rounded up to 4, zero padding in between; rows of rbm_row_len
+// elements, a multiple of 32, so that every row starts on a 128-byte line)
 // ---------------------------------------------------------------------------
 
 // spin-orbital flips of the change of site s to its a-th alternative state
-__device__ __forceinline__ int site_flips(uint64_t na, uint64_t nb, int s, int a, int* fs, int* sg, int nf)
+// appended to `pk` one byte per flip: spin-orbital index, bit 7 set when the
+// orbital becomes occupied
+__device__ __forceinline__ int site_flips(uint64_t na, uint64_t nb, int s, int a, uint32_t& pk, int nf)
 {
     const int own = sigma_at(na, nb, s);
     const int to = sig_of_alt(a, own);
-    if ((own ^ to) & 1) { fs[nf] = 2 * s; sg[nf] = (to & 1) ? 1 : -1; ++nf; }
-    if ((own ^ to) & 2) { fs[nf] = 2 * s + 1; sg[nf] = (to & 2) ? 1 : -1; ++nf; }
+    if ((own ^ to) & 1) { pk |= (uint32_t)(2 * s | ((to & 1) ? 0x80 : 0)) << (8 * nf); ++nf; }
+    if ((own ^ to) & 2) { pk |= (uint32_t)((2 * s + 1) | ((to & 2) ? 0x80 : 0)) << (8 * nf); ++nf; }
     return nf;
+}
+
+// cosh d - 1 and sinh d for |d| <= 1 from their Taylor series in z = d^2
+// (terms up to d^10 and d^11; the first omitted term is below 2^-28 of the sum)
+__device__ __forceinline__ void cosh_sinh_small(float d, float& ch1, float& sh)
+{
+    const float z = d * d;
+    ch1 = z * fmaf(z, fmaf(z, fmaf(z, fmaf(z, 1.f / 3628800.f, 1.f / 40320.f), 1.f / 720.f), 1.f / 24.f), 0.5f);
+    sh = fmaf(d * z, fmaf(z, fmaf(z, fmaf(z, fmaf(z, 1.f / 39916800.f, 1.f / 362880.f), 1.f / 5040.f),
+                                 1.f / 120.f), 1.f / 6.f), d);
 }
 
 template <typename T>
 __global__ void k_fam_rbm(FamArgs<T> f)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(1024) unsigned char smraw[];
     T* th_s = (T*)smraw;               // theta_k(n)
     T* tt_s = th_s + f.n_hidden;       // tanh theta_k(n)
     const int b = blockIdx.y, K = f.K, NH = f.n_hidden, NP = nh_pad(NH);
@@ -501,46 +523,76 @@ __global__ void k_fam_rbm(FamArgs<T> f)
     const int lane = threadIdx.x & 31;
     for (int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); o < nobj;
          o += gridDim.x * (blockDim.x >> 5)) {
-        int fs[4], sg[4], nf = 0;
+        uint32_t pk = 0;
+        int nf = 0;
         const bool left = o < nleft;
         const int oi = left ? o : o - nleft;
         if (oi < 3 * K) {
-            nf = site_flips(na, nb, oi / 3, oi % 3, fs, sg, 0);
+            nf = site_flips(na, nb, oi / 3, oi % 3, pk, 0);
         } else {
             const int key = left ? f.tl_list[(size_t)b * nk + (oi - 3 * K)]
                                  : f.tr_list[(size_t)b * nk + (oi - 3 * K)];
             int s_hi, a_hi, s_lo, a_lo;
             key_fields(K, key, s_hi, a_hi, s_lo, a_lo);
-            nf = site_flips(na, nb, s_hi, a_hi, fs, sg, 0);
-            nf = site_flips(na, nb, s_lo, a_lo, fs, sg, nf);
+            nf = site_flips(na, nb, s_hi, a_hi, pk, 0);
+            nf = site_flips(na, nb, s_lo, a_lo, pk, nf);
         }
-        if (left) {
-            T* out = f.rbl + (size_t)(lbase + oi) * (NP + 4);
-            T lp = T(0);                        // log PL
-            for (int k = lane; k < NP; k += 32) {
-                if (k >= NH) { out[k] = T(0); continue; }
-                T d = T(0);
-                for (int q = 0; q < nf; ++q) d += sg[q] > 0 ? (T)f.Wd[(size_t)k * 2 * K + fs[q]] : -(T)f.Wd[(size_t)k * 2 * K + fs[q]];
-                out[k] = tanh(th_s[k] + d);
-                // log(cosh(theta + d) / cosh(theta)) = log1p(cosh d - 1 + tanh(theta) sinh d)
+        // products of (1 + y_k) are carried as P - 1 (X <- X + y + X y), exact
+        // for P near 1 and free of a logarithm per unit
+        const int RL = rbm_row_len(NH);
+        T* out = (left ? f.rbl + (size_t)(lbase + oi) * RL : f.rbr + (size_t)(rbase + oi) * RL);
+        T pm1 = T(0);
+        for (int k = lane; k < NP; k += 32) {
+            if (k >= NH) { out[k] = T(0); continue; }
+            T d = T(0);
+            #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q < nf) {
+                    const uint32_t fb = (pk >> (8 * q)) & 0xFFu;
+                    const T w = f.WT[(size_t)(fb & 0x7Fu) * NP + k];
+                    d += (fb & 0x80u) ? w : -w;
+                }
+            }
+            T y;
+            bool done = false;
+            if constexpr (std::is_same<T, float>::value) {
+                // FP32 tables, |d| <= 1: series for cosh d - 1 and sinh d, and
+                // tanh(theta + d) = (t cosh d + sinh d) / (cosh d + t sinh d),
+                // t = tanh theta (the denominator is at least e^-|d|)
+                if (fabsf(d) <= 1.f) {
+                    float ch1, sh;
+                    cosh_sinh_small(d, ch1, sh);
+                    const float c = 1.f + ch1;
+                    if (left) {
+                        out[k] = __fdividef(fmaf(tt_s[k], c, sh), fmaf(tt_s[k], sh, c));
+                        y = ch1 + tt_s[k] * sh;
+                    } else {
+                        out[k] = __fdividef(sh, c);
+                        y = ch1;
+                    }
+                    done = true;
+                }
+            }
+            if (!done) {
+                // em = e^d - 1, inv = e^-d: cosh d - 1 = em^2 inv / 2, sinh d = em (1 + inv) / 2
                 const T em = expm1(d);
                 const T inv = T(1) / (T(1) + em);
-                lp += log1p(T(0.5) * em * em * inv + tt_s[k] * (T(0.5) * em * (T(1) + inv)));
+                const T ch1 = T(0.5) * em * em * inv, sh = T(0.5) * em * (T(1) + inv);
+                if (left) {
+                    out[k] = tanh(th_s[k] + d);
+                    y = ch1 + tt_s[k] * sh;             // cosh(theta + d) / cosh(theta) - 1
+                } else {
+                    out[k] = sh / (T(1) + ch1);         // tanh d
+                    y = ch1;                            // cosh d - 1
+                }
             }
-            for (int o2 = 16; o2; o2 >>= 1) lp += __shfl_xor_sync(kFull, lp, o2);
-            if (lane == 0) out[NP] = expm1(lp);
-        } else {
-            T* out = f.rbr + (size_t)(rbase + oi) * (2 * NP);
-            for (int k = lane; k < NP; k += 32) {
-                if (k >= NH) { out[k] = T(0); out[NP + k] = T(0); continue; }
-                T d = T(0);
-                for (int q = 0; q < nf; ++q) d += sg[q] > 0 ? (T)f.Wd[(size_t)k * 2 * K + fs[q]] : -(T)f.Wd[(size_t)k * 2 * K + fs[q]];
-                const T em = expm1(d);
-                const T inv = T(1) / (T(1) + em);
-                out[k] = T(0.5) * em * (T(1) + inv);        // sinh d
-                out[NP + k] = T(0.5) * em * em * inv;       // cosh d - 1
-            }
+            pm1 = fma(pm1, y, pm1 + y);
         }
+        for (int o2 = 16; o2; o2 >>= 1) {
+            const T z = __shfl_xor_sync(kFull, pm1, o2);
+            pm1 = fma(pm1, z, pm1 + z);
+        }
+        if (lane == 0) out[NP] = pm1;
     }
 }
 
@@ -755,6 +807,240 @@ __global__ void __launch_bounds__(256, 4) k_site_tiles(FamArgs<T> f, const SiteI
     batch_fini(f, sm);
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined tensor-core site step (FP32 tables, D <= 64: one reduction chunk).
+// A block walks a contiguous range of tiles (one matrix image for most of
+// them) with two row stages: while tile i is split into
+// FP16 hi / lo, multiplied and written back, the rows of tile i+1 stream into
+// the other stage with cp.async and the items of tile i+2 are read into
+// registers, so that each SM keeps two tiles' gathers in flight. A stage holds
+// the raw FP32 rows (stride 4D + 16 bytes, so that the split's reads fall on
+// distinct banks) and, once split in place, the A operand (hi then lo, in the
+// core-matrix layout). Per row the arithmetic is that of tc_apply (same split,
+// same MMAs in the same order, same rescaling), so the results are bitwise
+// those of the unpipelined kernel.
+// ---------------------------------------------------------------------------
+constexpr int kPipeRows = 128;
+
+inline size_t pipe_stage_bytes(int D)
+{
+    const size_t raw = (size_t)kPipeRows * (4 * D + 16);
+    return (raw + 1023) & ~(size_t)1023;
+}
+inline size_t pipe_smem_bytes(int D) { return 2 * pipe_stage_bytes(D) + (size_t)4 * D * D; }
+
+__global__ void __launch_bounds__(256, 2) k_site_tiles_pipe(FamArgs<float> f, const SiteItem* items, SiteStep st,
+                                                           uint32_t stage_bytes)
+{
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ uint32_t tmem_slot;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ const float* s_src[3][kPipeRows];
+    __shared__ float* s_dst[3][kPipeRows];
+    __shared__ const int* s_se[3][kPipeRows];
+    __shared__ int* s_de[3][kPipeRows];
+    __shared__ int s_sev[2][kPipeRows];
+    __shared__ float s_rmax[2][kPipeRows];
+    const int D = f.D, tid = threadIdx.x;
+    const int RS = 4 * D + 16;                         // stage row stride, bytes
+    unsigned char* const stage0 = smraw;
+    unsigned char* const Bh = smraw + 2 * (size_t)stage_bytes;
+    const int ntiles = st.tbeg[8];
+    // this block's tiles: [t_beg, t_end), non-empty as the grid never exceeds the tiles
+    const int t_beg = (int)((int64_t)blockIdx.x * ntiles / gridDim.x);
+    const int t_end = (int)((int64_t)(blockIdx.x + 1) * ntiles / gridDim.x);
+    if (tid < 32) { tc::tmem_alloc(&tmem_slot, f.tc_cols); tc::tmem_relinquish(); }
+    if (tid == 0) tc::mbar_init(&mbar, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    auto tile_info = [&](int tile, int& g, int64_t& i0, int& n) {
+        g = 0;
+        while (g < 7 && tile >= st.tbeg[g + 1]) ++g;
+        i0 = st.gbeg[g] + (int64_t)(tile - st.tbeg[g]) * kPipeRows;
+        const int64_t left = st.gend[g] - i0;
+        n = (int)(left < kPipeRows ? left : kPipeRows);
+    };
+    auto put_item = [&](int slot, int r, const SiteItem& it) {
+        s_src[slot][r] = it.src; s_dst[slot][r] = it.dst; s_se[slot][r] = it.se; s_de[slot][r] = it.de;
+    };
+    // rows and source exponents of the tile in item slot `slot` into stage `buf`
+    // piece v = tid + 256 j of a tile is row v / qpr, 16-byte piece v % qpr
+    const int qpr = D >> 2;
+    const int f_r0 = tid / qpr, f_q0 = tid - f_r0 * qpr;
+    const int f_dr = 256 / qpr, f_dq = 256 - f_dr * qpr;
+    auto fetch = [&](int slot, int buf, int n) {
+        unsigned char* sg = stage0 + (size_t)buf * stage_bytes;
+        int r = f_r0, q = f_q0;
+        while (r < n) {
+            tc::cp_async16(sg + r * RS + q * 16, s_src[slot][r] + 4 * q);
+            r += f_dr; q += f_dq;
+            if (q >= qpr) { q -= qpr; ++r; }
+        }
+        if (tid < n) tc::cp_async4(&s_sev[buf][tid], s_se[slot][tid]);
+    };
+    {
+        int g, n; int64_t i0;
+        tile_info(t_beg, g, i0, n);
+        if (tid < n) put_item(0, tid, items[i0 + tid]);
+        if (t_beg + 1 < t_end) {
+            tile_info(t_beg + 1, g, i0, n);
+            if (tid < n) put_item(1, tid, items[i0 + tid]);
+        }
+        __syncthreads();
+        tile_info(t_beg, g, i0, n);
+        fetch(0, 0, n);
+        tc::cp_async_commit();
+    }
+    // the split's units (8 columns of one row) of this thread: stage read and
+    // operand write offsets, the same for every tile
+    const int cpr = D >> 3, nun = kPipeRows * cpr;
+    int rd_off[4];
+    uint32_t wr_off[4];
+    #pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int u = tid + k * 256;
+        const int r8 = u & 7, rest = u >> 3, c = rest % cpr, rg = rest / cpr;
+        rd_off[k] = (8 * rg + r8) * RS + 32 * c;
+        wr_off[k] = tc::op_offset(8 * rg + r8, 8 * c, D);
+    }
+    int cur_mat = -1;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int i = 0, tile = t_beg; tile < t_end; ++i, ++tile) {
+        const int cur = i & 1, ri = i % 3;
+        unsigned char* const sc = stage0 + (size_t)cur * stage_bytes;
+        int g, n; int64_t i0;
+        tile_info(tile, g, i0, n);
+        // (1) the next tile's rows into the other stage (its last reader, the
+        // MMAs of tile i-1, completed before the previous epilogue)
+        if (tile + 1 < t_end) {
+            int g1, n1; int64_t i1;
+            tile_info(tile + 1, g1, i1, n1);
+            fetch((i + 1) % 3, cur ^ 1, n1);
+        }
+        tc::cp_async_commit();
+        // (2) the items of the tile after next, into registers
+        SiteItem nx{};
+        int n2 = 0;
+        if (tile + 2 < t_end) {
+            int g2; int64_t i2;
+            tile_info(tile + 2, g2, i2, n2);
+            if (tid < n2) nx = items[i2 + tid];
+        }
+        // (3) this tile's rows have landed
+        tc::cp_async_wait<1>();
+        __syncthreads();
+        // (4) split in place: every read before any write. Unit u = 8 columns
+        // of one row; the 8 lanes of a unit group take the 8 rows of one
+        // core matrix, so each group's stores fill one 128-byte core matrix.
+        float xv[4][8];
+        #pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (tid + k * 256 < nun) {
+                const float4* p = (const float4*)(sc + rd_off[k]);
+                const float4 a = p[0], b = p[1];
+                xv[k][0] = a.x; xv[k][1] = a.y; xv[k][2] = a.z; xv[k][3] = a.w;
+                xv[k][4] = b.x; xv[k][5] = b.y; xv[k][6] = b.z; xv[k][7] = b.w;
+            }
+        }
+        __syncthreads();
+        #pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (tid + k * 256 < nun) {
+                __align__(16) __half hi[8], lo[8];
+                #pragma unroll
+                for (int j = 0; j < 8; ++j) tc::split_half(xv[k][j], hi[j], lo[j]);
+                const uint32_t off = wr_off[k];
+                *(uint4*)(sc + off) = *(const uint4*)hi;
+                *(uint4*)(sc + (size_t)kPipeRows * D * 2 + off) = *(const uint4*)lo;
+            }
+        }
+        // (5) the matrix image when the group's matrix changes
+        const int mat = st.mat[g];
+        if (mat != cur_mat) {
+            const int nimg = 4 * D * D / 16;
+            const uint4* __restrict__ gsrc = f.tc_mats + (size_t)mat * nimg;
+            for (int q = tid; q < nimg; q += blockDim.x) ((uint4*)Bh)[q] = __ldg(gsrc + q);
+            cur_mat = mat;
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        // (6) x_hi M_hi + x_lo M_hi + x_hi M_lo into tensor memory
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t idesc = tc::idesc_f16(128, D);
+            const uint32_t lbo = 128, sbo = 16 * D;
+            const unsigned char* As[3] = {sc, sc + (size_t)kPipeRows * D * 2, sc};
+            const unsigned char* Bs[3] = {Bh, Bh, Bh + 2 * D * D};
+            uint32_t acc = 0;
+            for (int term = 0; term < 3; ++term)
+                for (int ks = 0; ks < D / 16; ++ks) {
+                    tc::mma_f16(tmem, tc::desc(tc::smem_addr(As[term]) + ks * 256, lbo, sbo),
+                                tc::desc(tc::smem_addr(Bs[term]) + ks * 256, lbo, sbo), idesc, acc);
+                    acc = 1;
+                }
+            tc::mma_commit(&mbar);
+        }
+        ok = tc::mbar_wait(&mbar, phase, 1u << 24) && ok;
+        phase ^= 1u;
+        tc::fence_after_sync();
+        // (7) the items fetched in (2) replace those of tile i-1
+        if (tid < n2) put_item((i + 2) % 3, tid, nx);
+        // (8) tensor memory -> registers twice (row maximum, then the scaled
+        // row), 8 columns at a time; warp w reads lanes 32 (w % 4) .. +31 and
+        // half (w / 4) of the columns
+        const int warp = tid >> 5, lane = tid & 31;
+        const int q = warp & 3, h = warp >> 2, half = D >> 1;
+        const int r = 32 * q + lane;
+        const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + h * half;
+        {
+            float m = 0.f;
+            for (int c0 = 0; c0 < half; c0 += 8) {
+                float v[8];
+                tc::tmem_ld8(trow + c0, v);
+                tc::tmem_wait_ld();
+                #pragma unroll
+                for (int j = 0; j < 8; ++j) m = fmaxf(m, fabsf(v[j]));
+            }
+            s_rmax[h][r] = m;
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        {
+            const float mm = fmaxf(s_rmax[0][r], s_rmax[1][r]);
+            int e = 0;
+            if (mm > 0.f) frexpf(mm, &e);
+            float* o = s_dst[ri][r < n ? r : 0] + h * half;
+            // x 2^-e: one multiply by a normal power of two rounds as ldexpf does
+            const bool pw = e >= -126 && e <= 126;
+            const float sc2 = pw ? __int_as_float((127 - e) << 23) : 0.f;
+            for (int c0 = 0; c0 < half; c0 += 8) {
+                float v[8];
+                tc::tmem_ld8(trow + c0, v);     // every lane of the warp takes part
+                tc::tmem_wait_ld();
+                if (r < n) {
+                    #pragma unroll
+                    for (int j = 0; j < 8; ++j) v[j] = pw ? v[j] * sc2 : ldexpf(v[j], -e);
+                    *(float4*)(o + c0) = make_float4(v[0], v[1], v[2], v[3]);
+                    *(float4*)(o + c0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
+                }
+            }
+            if (h == 0 && r < n) *s_de[ri][r] = s_sev[cur][r] + e + f.tc_exp[mat];
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    tc::cp_async_wait<0>();
+    if (!ok && tid == 0) report(f.err, 5, 4, (long long)f.s0);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid < 32) tc::tmem_dealloc(tmem, f.tc_cols);
+}
+
 template <typename T>
 int fam_site_count(const FamArgs<T>& f, const SiteBufs& b, int nbb, cudaStream_t st)
 {
@@ -801,6 +1087,18 @@ int fam_site_step(const FamArgs<T>& f, const SiteBufs& b, int tau, const int64_t
     }
     ss.tbeg[8] = tiles;
     if (tiles == 0) return 0;
+    if constexpr (std::is_same<T, float>::value) {
+        if (tc && f.D <= 64) {
+            // two blocks per SM, each with two tiles' rows in flight
+            allow_max_smem(k_site_tiles_pipe);
+            cudaFuncSetAttribute(k_site_tiles_pipe, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+            const int grid = tiles < max_ctas / 2 ? tiles : max_ctas / 2;
+            k_site_tiles_pipe<<<grid, 256, pipe_smem_bytes(f.D), st>>>(
+                f, (const SiteItem*)b.items, ss, (uint32_t)pipe_stage_bytes(f.D));
+            return 1;
+        }
+    }
     allow_max_smem(k_site_tiles<T>);
     const size_t smem = f.batch_bytes;
     const int grid = tiles < max_ctas ? tiles : max_ctas;
@@ -836,11 +1134,12 @@ __device__ __forceinline__ double scale_pow2(double x, int e)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows, double* partial,
+__global__ void __launch_bounds__(kFamRows, 8) k_fam_rows(FamArgs<T> f, RowSet rows, double* partial,
                                                        int64_t* span, double* partial_abs)
 {
     __shared__ OrbLists lists;
     __shared__ T s_ratio[kFamRows];                  // each row's ratio in the contraction type
+    __shared__ __align__(16) const T* s_ptr[kFamRows][4];   // each row's L, R and correlator rows
     __shared__ double wsum[kFamRows / 32];
     __shared__ double wabs[kFamRows / 32];
     __shared__ long long wspan[kFamRows / 32];
@@ -910,13 +1209,15 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
             }
         }
         ex = eL + eR;
-        nmv = p.s[p.nsite - 1] - p.s[0] + 1;
+        nmv = p.last - p.s[0] + 1;
         coef = rows.coef[r0 + myrow];
         if (NH > 0) {
-            lt = f.rbl + (size_t)(f.rbl_base[b] + lobj) * (NP + 4);
-            rs = f.rbr + (size_t)(f.rbr_base[b] + robj) * (2 * NP);
+            lt = f.rbl + (size_t)(f.rbl_base[b] + lobj) * rbm_row_len(NH);
+            rs = f.rbr + (size_t)(f.rbr_base[b] + robj) * rbm_row_len(NH);
         }
     }
+    s_ptr[myrow][0] = Lv; s_ptr[myrow][1] = Rv; s_ptr[myrow][2] = lt; s_ptr[myrow][3] = rs;
+    __syncwarp();                                   // a warp reads only its own rows' pointers
     const double inv_pm = s_inv_pm;
     const int pe = f.pe[b];
     // ---- evaluation: 8 lanes per row, 4 rows of the warp at a time
@@ -924,12 +1225,13 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
     const int wrows = nr - wbase < 32 ? (nr - wbase > 0 ? nr - wbase : 0) : 32;
     const int g = lane >> 3, sub = lane & 7;
     for (int q0 = 0; q0 < wrows; q0 += 4) {
-        const int q = q0 + g;                       // the row this lane group evaluates
-        const int qs = q < 32 ? q : 31;
-        const T* Lq = (const T*)__shfl_sync(kFull, (unsigned long long)Lv, qs);
-        const T* Rq = (const T*)__shfl_sync(kFull, (unsigned long long)Rv, qs);
-        const T* ltq = (const T*)__shfl_sync(kFull, (unsigned long long)lt, qs);
-        const T* rsq = (const T*)__shfl_sync(kFull, (unsigned long long)rs, qs);
+        const int q = q0 + g;                       // the row this lane group evaluates (< 32)
+        const ulonglong2 p01 = *(const ulonglong2*)&s_ptr[wbase + q][0];
+        const ulonglong2 p23 = *(const ulonglong2*)&s_ptr[wbase + q][2];
+        const T* Lq = (const T*)p01.x;
+        const T* Rq = (const T*)p01.y;
+        const T* ltq = (const T*)p23.x;
+        const T* rsq = (const T*)p23.y;
         const bool live = q < wrows;
         // dot product with error-free product / sum transformations
         T sum = T(0), comp = T(0);
@@ -974,22 +1276,21 @@ __global__ void __launch_bounds__(kFamRows) k_fam_rows(FamArgs<T> f, RowSet rows
             T X = T(0);                            // product of (1 + x_k) minus 1
             if (live) {
                 const V4* l4 = (const V4*)ltq;
-                const V4* s4 = (const V4*)rsq;
-                const V4* c4p = s4 + NP / 4;
+                const V4* r4 = (const V4*)rsq;
                 for (int k4 = sub; k4 < NP / 4; k4 += 8) {
-                    const V4 t = l4[k4], sh = s4[k4], c1 = c4p[k4];
+                    const V4 t = l4[k4], u = r4[k4];
                     T x;
-                    x = fma(t.x, sh.x, c1.x); X = fma(X, x, X + x);
-                    x = fma(t.y, sh.y, c1.y); X = fma(X, x, X + x);
-                    x = fma(t.z, sh.z, c1.z); X = fma(X, x, X + x);
-                    x = fma(t.w, sh.w, c1.w); X = fma(X, x, X + x);
+                    x = t.x * u.x; X = fma(X, x, X + x);
+                    x = t.y * u.y; X = fma(X, x, X + x);
+                    x = t.z * u.z; X = fma(X, x, X + x);
+                    x = t.w * u.w; X = fma(X, x, X + x);
                 }
             }
             for (int o = 4; o; o >>= 1) {
                 const T Y = __shfl_xor_sync(kFull, X, o);
                 X = fma(X, Y, X + Y);
             }
-            if (live) ratio *= (T(1) + ltq[NP]) * (T(1) + X);
+            if (live) ratio *= (T(1) + ltq[NP]) * (T(1) + rsq[NP]) * (T(1) + X);
         }
         if (live && sub == 0) s_ratio[wbase + q] = ratio;
     }

@@ -40,7 +40,7 @@ struct FamArgs {
     T* TR; int* TRe;          // packed TR rows
     // correlator
     int n_hidden;
-    const double* Wd;         // [n_hidden][2K]
+    const T* WT;              // [2K][NP] W transposed, zero-padded to NP = n_hidden rounded up to 4
     const double* theta;      // [Ns][n_hidden] (all samples)
     T* rbl; T* rbr;           // per-object correlator factors (see nqs_family.cu)
     const int64_t* rbl_base; const int64_t* rbr_base;   // [b] object offsets
@@ -110,6 +110,10 @@ __host__ __device__ inline size_t fam_batch_bytes(int D, int nmax, size_t elem, 
 void fam_tc_images(const double* A, int K, int D, std::vector<unsigned char>& images, std::vector<int>& exps);
 
 // bytes of the per-sample tables (G, H, their exponents, cluster maps)
+// elements of one correlator-factor row: N_h rounded up to 4, one more for the
+// product term, rounded up to 32
+__host__ __device__ inline int rbm_row_len(int NH) { return ((((NH + 3) & ~3) + 1) + 31) & ~31; }
+
 inline size_t fam_bytes_per_sample(int K, int D, size_t elem)
 {
     const size_t KK = (size_t)K * K;

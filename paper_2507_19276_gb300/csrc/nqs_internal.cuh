@@ -50,16 +50,22 @@ struct HamView {
     double e_core;
 };
 
-// Per-determinant orbital lists: positions of occupied / empty orbitals.
+// Per-determinant orbital lists: positions of occupied / empty orbitals, and
+// for each listed orbital the number of occupied spin orbitals of n with a
+// smaller interleaved index (the count a creation or annihilation operator
+// there picks up in n).
 struct OrbLists {
     uint8_t occ[2][kMaxOrb];
     uint8_t vir[2][kMaxOrb];
+    uint8_t ocb[2][kMaxOrb];
+    uint8_t vcb[2][kMaxOrb];
 };
 
 // Spin-orbital excitation: i (,j) emptied, a (,b) filled; m = a+_a a+_b a_j a_i n.
 struct Exc {
     int kind;          // 1 single, 2 double
     int i, j, a, b;    // spin-orbital indices 2p+spin (j, b = -1 for singles)
+    int odd;           // parity of the fermionic phase of <m| a+_a a+_b a_j a_i |n>
 };
 
 __device__ __forceinline__ uint64_t low_mask(int p)
@@ -89,13 +95,25 @@ __device__ __forceinline__ void build_lists_warp(uint64_t wa, uint64_t wb, int K
         for (int sp = 0; sp < 2; ++sp) {
             uint64_t w = sp ? wb : wa;
             int below = __popcll(w & low_mask(p));
-            if ((w >> p) & 1ull) L.occ[sp][below] = (uint8_t)p;
-            else L.vir[sp][p - below] = (uint8_t)p;
+            const uint8_t c = (uint8_t)count_below(wa, wb, 2 * p + sp);
+            if ((w >> p) & 1ull) { L.occ[sp][below] = (uint8_t)p; L.ocb[sp][below] = c; }
+            else { L.vir[sp][p - below] = (uint8_t)p; L.vcb[sp][p - below] = c; }
         }
     }
 }
 
-// Canonical rank -> excitation.
+// The operators of a double act on n in the order a_i, a_j, a+_b, a+_a; each
+// picks up the occupied spin orbitals below it in the determinant it meets,
+// which differs from n by the operators already applied:
+//   c = cb(i) + cb(j) - [i<j] + cb(b) - [i<b] - [j<b] + cb(a) - [i<a] - [j<a] + [b<a]
+// with cb() counted in n. Only the parity matters, so the signs of the order
+// terms drop out. (A single: c = cb(i) + cb(a) - [i<a].)
+__device__ __forceinline__ int double_order(const Exc& e)
+{
+    return (e.i < e.j) + (e.i < e.b) + (e.j < e.b) + (e.i < e.a) + (e.j < e.a) + (e.b < e.a);
+}
+
+// Canonical rank -> excitation (with its phase parity).
 __device__ __forceinline__ Exc decode_rank(const HamView& h, const OrbLists& L, uint32_t r)
 {
     Exc e;
@@ -108,6 +126,7 @@ __device__ __forceinline__ Exc decode_rank(const HamView& h, const OrbLists& L, 
         e.i = 2 * L.occ[sp][io] + sp;
         e.a = 2 * L.vir[sp][ao] + sp;
         e.j = e.b = -1;
+        e.odd = (L.ocb[sp][io] + L.vcb[sp][ao] + (e.i < e.a)) & 1;
     } else if (r < h.blk[4]) {                  // same-spin doubles
         int sp = r >= h.blk[3];
         uint32_t x = r - h.blk[2 + sp];
@@ -120,6 +139,8 @@ __device__ __forceinline__ Exc decode_rank(const HamView& h, const OrbLists& L, 
         e.j = 2 * L.occ[sp][to >> 8] + sp;
         e.a = 2 * L.vir[sp][tv & 0xff] + sp;
         e.b = 2 * L.vir[sp][tv >> 8] + sp;
+        e.odd = (L.ocb[sp][to & 0xff] + L.ocb[sp][to >> 8] + L.vcb[sp][tv & 0xff] +
+                 L.vcb[sp][tv >> 8] + double_order(e)) & 1;
     } else {                                    // alpha-beta doubles
         uint32_t x = r - h.blk[4];
         uint32_t ia = fdiv(x, h.div_sb);
@@ -133,31 +154,31 @@ __device__ __forceinline__ Exc decode_rank(const HamView& h, const OrbLists& L, 
         e.a = 2 * L.vir[0][ao];
         e.j = 2 * L.occ[1][jo] + 1;
         e.b = 2 * L.vir[1][bo] + 1;
+        e.odd = (L.ocb[0][io] + L.vcb[0][ao] + L.ocb[1][jo] + L.vcb[1][bo] + double_order(e)) & 1;
     }
     return e;
 }
 
 __device__ __forceinline__ double eri_at(const HamView& h, int p, int q, int r, int s)
 {
-    const size_t K = (size_t)h.K;
-    return __ldg(h.eri + (((size_t)p * K + q) * K + r) * K + s);
+    const uint32_t K = (uint32_t)h.K;          // K <= 64: K^4 <= 2^24
+    return __ldg(h.eri + ((((uint32_t)p * K + (uint32_t)q) * K + (uint32_t)r) * K + (uint32_t)s));
 }
 
-// <m|H|n> for m = gamma a+_a (a+_b a_j) a_i |n>; writes m and the phase bit.
-// Singles: F = h_ai + sum_{common occ s'} (ai|jj) - sum_{common occ s', same
-// spin} (aj|ji), added in ascending s'. Doubles: (ai|bj) - [same spin] (aj|bi).
+// <m|H|n> for m = gamma a+_a (a+_b a_j) a_i |n>; writes m and the phase bit
+// (e.odd, from decode_rank). Singles: F = h_ai + sum_{common occ s'} (ai|jj) -
+// sum_{common occ s', same spin} (aj|ji), added in ascending s'. Doubles:
+// (ai|bj) - [same spin] (aj|bi).
 __device__ __forceinline__ double matrix_element(const HamView& h, uint64_t na, uint64_t nb,
                                                  const Exc& e, uint64_t& ma, uint64_t& mb,
                                                  int& odd)
 {
     uint64_t wa = na, wb = nb;
-    int c = count_below(wa, wb, e.i);
     flip(wa, wb, e.i);
+    flip(wa, wb, e.a);
     double v;
     const int I = e.i >> 1, A = e.a >> 1;
     if (e.kind == 1) {
-        c += count_below(wa, wb, e.a);
-        flip(wa, wb, e.a);
         v = __ldg(h.h1e + A * h.K + I);
         // Coulomb part over common occupied spin orbitals, ascending s' = 2p+spin
         const uint64_t ca = (e.i & 1) ? na : (na & ~(1ull << I));
@@ -170,19 +191,15 @@ __device__ __forceinline__ double matrix_element(const HamView& h, uint64_t na, 
         for (int p = 0; p < h.K; ++p)
             if ((cs >> p) & 1ull) v = v - eri_at(h, A, p, p, I);
     } else {
-        c += count_below(wa, wb, e.j);
         flip(wa, wb, e.j);
-        c += count_below(wa, wb, e.b);
         flip(wa, wb, e.b);
-        c += count_below(wa, wb, e.a);
-        flip(wa, wb, e.a);
         const int J = e.j >> 1, B = e.b >> 1;
         v = eri_at(h, A, I, B, J);
         if ((e.i & 1) == (e.j & 1)) v = v - eri_at(h, A, J, B, I);
     }
     ma = wa;
     mb = wb;
-    odd = c & 1;
+    odd = e.odd;
     // the phase as a sign-bit flip (integer ALU, not the FP64 pipe)
     return __longlong_as_double(__double_as_longlong(v) ^ ((long long)odd << 63));
 }
@@ -235,6 +252,16 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v)
 {
     for (int o = 16; o; o >>= 1) v += __shfl_down_sync(kFull, v, o);
     return v;
+}
+
+// Exact warp sum of 64-bit values whose total stays below 2^64, on every
+// lane: three 24-bit slices summed by the warp-reduce unit (slice sums < 2^29).
+__device__ __forceinline__ uint64_t warp_sum_sliced(uint64_t v)
+{
+    const unsigned s0 = __reduce_add_sync(kFull, (unsigned)(v & 0xFFFFFFu));
+    const unsigned s1 = __reduce_add_sync(kFull, (unsigned)((v >> 24) & 0xFFFFFFu));
+    const unsigned s2 = __reduce_add_sync(kFull, (unsigned)(v >> 48));
+    return (uint64_t)s0 + ((uint64_t)s1 << 24) + ((uint64_t)s2 << 48);
 }
 
 __device__ __forceinline__ double warp_sum_f64(double v)

@@ -112,6 +112,24 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v)
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Asynchronous global -> shared copies (LDGSTS): 16 bytes bypassing L1, or 4
+// bytes; completion is tracked per thread in commit groups.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_addr(sdst)), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(smem_addr(sdst)), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// wait until at most N of this thread's most recent groups are pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
 // split x into a hi and a lo half whose sum carries ~22 bits of x
 __device__ __forceinline__ void split_half(float x, __half& h, __half& l)
 {
