@@ -62,7 +62,7 @@ FP64_PEAK_TFLOPS = 1.196
 # summed over its kernels, from ncu counters on the H50 shape (D = 64) with
 # 512 samples; the stage's traffic grows in proportion to the amplitudes
 # evaluated. None until taken for the current kernels.
-STAGE_TRAFFIC_PER_AMP = {"mixed": 375.0, "fp64_shared": None}
+STAGE_TRAFFIC_PER_AMP = {"mixed": None, "fp64_shared": None}
 
 DTYPES = {"mixed": "f16x3 tensor-core products (f32 accumulate) + f32 gathers; f64 H, psi(n), "
                    "ratios, sums; heaviest samples re-evaluated in f64 to the energy tolerance",
@@ -310,7 +310,7 @@ def run(args):
                 "peak": peaks["bf16_tflops_sustained"],
                 "peak_source": f"{src} dense bf16 (sustained; f16 has the same nominal rate)",
                 "kernel": "amplitude stage: k_fam_mark, k_fam_compact, k_site_boundary, "
-                          "k_site_build, k_site_tiles (tcgen05), k_fam_rbm, k_fam_rows"}
+                          "k_site_build, k_site_tiles_pipe (tcgen05), k_fam_rbm, k_fam_rows"}
     else:
         roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "peak_source": "FP64 FMA probe, measured",

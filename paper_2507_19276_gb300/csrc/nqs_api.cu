@@ -64,7 +64,7 @@ struct nqs_ctx {
     int64_t index_base = 0;    // Philox sample counter of samples[0]
     int n_sm = 152;            // multiprocessors of the device
     size_t fam_budget = 0;     // cap on the shared-prefix tables (0: none beyond free/3)
-    DevBuf site_cnt, site_offs, site_bounds, site_items;
+    DevBuf site_cnt, site_offs, site_bounds, site_items, site_scan;
     double energy_tol = 0.0;   // mixed form: re-evaluate heavy samples in FP64 to this bound
     DevBuf part_det_abs, part_draw_abs, eabs, logf_save, summary2, ref_idx, ref_s, ref_c, ref_pos,
         ref_e;
@@ -416,7 +416,9 @@ int site_tables(nqs_ctx* c, const FamArgs<T>& f, int nbb)
     TRY(ensure(c, c->site_cnt, (size_t)ncnt * 8));
     TRY(ensure(c, c->site_offs, (size_t)(ncnt + 1) * 8));
     TRY(ensure(c, c->site_bounds, ((size_t)K * 8 + 1) * 8));
+    TRY(ensure(c, c->site_scan, (size_t)scan_i64_tmp_elems(ncnt) * 8));
     SiteBufs sb{};
+    sb.scan_tmp = (int64_t*)c->site_scan.p;
     sb.counts = (int64_t*)c->site_cnt.p;
     sb.offs = (int64_t*)c->site_offs.p;
     sb.bounds = (int64_t*)c->site_bounds.p;
@@ -489,6 +491,8 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
     FamArgs<T> f{};
     f.h = c->hv;
     f.K = K;
+    f.div3K = make_fastdiv((uint32_t)(3 * K));
+    f.div9K = make_fastdiv((uint32_t)(9 * K));
     f.D = D;
     f.tc = (sizeof(T) == 4 && c->has_tc) ? 1 : 0;
     if (f.tc) {
@@ -663,7 +667,7 @@ extern "C" int nqs_destroy(nqs_ctx* c)
                       &c->frbr_base, &c->tc_img, &c->tc_exps, &c->part_det_abs,
                       &c->part_draw_abs, &c->eabs, &c->logf_save, &c->summary2, &c->ref_idx,
                       &c->ref_s, &c->ref_c, &c->ref_pos, &c->ref_e, &c->site_cnt,
-                      &c->site_offs, &c->site_bounds, &c->site_items};
+                      &c->site_offs, &c->site_bounds, &c->site_items, &c->site_scan};
     for (DevBuf* b : bufs) release(*b);
     for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);

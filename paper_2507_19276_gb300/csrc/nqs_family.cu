@@ -236,9 +236,12 @@ __device__ void tc_apply(const FamArgs<float>& f, BatchSmem<float>& sm, const Ac
                 }
             tc::mma_commit(sm.mbar);
         }
-        // the chunk's operands may be overwritten once its MMAs are done
-        ok = tc::mbar_wait(sm.mbar, sm.phase, 1u << 24) && ok;
+        // the chunk's operands may be overwritten once its MMAs are done (one
+        // warp polls the mbarrier, the others wait at the barrier)
+        if (threadIdx.x < 32) ok = tc::mbar_wait(sm.mbar, sm.phase, 1u << 24) && ok;
         sm.phase ^= 1u;
+        tc::fence_before_sync();
+        __syncthreads();
         tc::fence_after_sync();
     }
     if (!ok && threadIdx.x == 0) report(f.err, 5, 4, (long long)f.s0);
@@ -323,13 +326,18 @@ __device__ void batch_fini(const FamArgs<T>& f, BatchSmem<T>& sm)
 }
 
 // fields of a key: first site, its alternative, second site, its alternative
-__device__ __forceinline__ void key_fields(int K, int key, int& site_hi, int& alt_hi, int& site_lo,
-                                           int& alt_lo)
+template <typename T>
+__device__ __forceinline__ void key_fields(const FamArgs<T>& f, int key, int& site_hi, int& alt_hi,
+                                           int& site_lo, int& alt_lo)
 {
-    site_hi = key / (9 * K);
-    alt_hi = (key / (3 * K)) % 3;
-    site_lo = (key / 3) % K;
-    alt_lo = key % 3;
+    // key = ((site_hi * 3 + alt_hi) * K + site_lo) * 3 + alt_lo, key < 9 K^2 <= 36864
+    const uint32_t k = (uint32_t)key;
+    const uint32_t q9 = fdiv(k, f.div9K), r9 = k - q9 * f.div9K.d;
+    const uint32_t q3 = fdiv(r9, f.div3K), r3 = r9 - q3 * f.div3K.d;
+    site_hi = (int)q9;
+    alt_hi = (int)q3;
+    site_lo = (int)(r3 / 3u);
+    alt_lo = (int)(r3 - 3u * (r3 / 3u));
 }
 
 // padded correlator-factor row lengths (multiples of 4 elements)
@@ -520,20 +528,24 @@ __global__ void k_fam_rbm(FamArgs<T> f)
     const int nleft = 3 * K + f.tl_count[b], nright = 3 * K + f.tr_total[b];
     const int64_t lbase = f.rbl_base[b], rbase = f.rbr_base[b];
     const int nobj = nleft + nright;
-    const int lane = threadIdx.x & 31;
-    for (int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); o < nobj;
-         o += gridDim.x * (blockDim.x >> 5)) {
+    // two objects per warp, one per half-warp (16 lanes over the hidden units)
+    const int lane = threadIdx.x & 31, hl = lane & 15;
+    for (int ob = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 2; ob < nobj;
+         ob += gridDim.x * (blockDim.x >> 5) * 2) {
+        const int o = ob + (lane >> 4);
+        const bool valid = o < nobj;
         uint32_t pk = 0;
         int nf = 0;
         const bool left = o < nleft;
         const int oi = left ? o : o - nleft;
-        if (oi < 3 * K) {
+        if (!valid) {
+        } else if (oi < 3 * K) {
             nf = site_flips(na, nb, oi / 3, oi % 3, pk, 0);
         } else {
             const int key = left ? f.tl_list[(size_t)b * nk + (oi - 3 * K)]
                                  : f.tr_list[(size_t)b * nk + (oi - 3 * K)];
             int s_hi, a_hi, s_lo, a_lo;
-            key_fields(K, key, s_hi, a_hi, s_lo, a_lo);
+            key_fields(f, key, s_hi, a_hi, s_lo, a_lo);
             nf = site_flips(na, nb, s_hi, a_hi, pk, 0);
             nf = site_flips(na, nb, s_lo, a_lo, pk, nf);
         }
@@ -542,7 +554,7 @@ __global__ void k_fam_rbm(FamArgs<T> f)
         const int RL = rbm_row_len(NH);
         T* out = (left ? f.rbl + (size_t)(lbase + oi) * RL : f.rbr + (size_t)(rbase + oi) * RL);
         T pm1 = T(0);
-        for (int k = lane; k < NP; k += 32) {
+        for (int k = hl; valid && k < NP; k += 16) {
             if (k >= NH) { out[k] = T(0); continue; }
             T d = T(0);
             #pragma unroll
@@ -588,11 +600,12 @@ __global__ void k_fam_rbm(FamArgs<T> f)
             }
             pm1 = fma(pm1, y, pm1 + y);
         }
-        for (int o2 = 16; o2; o2 >>= 1) {
+        for (int o2 = 8; o2; o2 >>= 1) {
             const T z = __shfl_xor_sync(kFull, pm1, o2);
             pm1 = fma(pm1, z, pm1 + z);
         }
-        if (lane == 0) out[NP] = pm1;
+        if (valid && hl == 0) out[NP] = pm1;
+        if (valid && hl < 3) out[NP + 1 + hl] = T(0);
     }
 }
 
@@ -654,7 +667,7 @@ __global__ void __launch_bounds__(256) k_site_build(FamArgs<T> f, SiteBufs sb)
     for (int c = threadIdx.x; c < ncl; c += blockDim.x) {
         const int key = tll[c];
         int s2, a2, s1, a1;
-        key_fields(K, key, s2, a2, s1, a1);
+        key_fields(f, key, s2, a2, s1, a1);
         const int off = f.tl_idx[(size_t)b * nk + key];
         const int end = f.tl_end[(size_t)b * nk + key];
         const size_t gi = ((size_t)a1 * K + s1) * K + (s2 - 1);
@@ -672,7 +685,7 @@ __global__ void __launch_bounds__(256) k_site_build(FamArgs<T> f, SiteBufs sb)
     for (int i = threadIdx.x; i < ntr; i += blockDim.x) {
         const int key = trl[i];
         int sA, aA, sB, aB;
-        key_fields(K, key, sA, aA, sB, aB);
+        key_fields(f, key, sA, aA, sB, aB);
         const size_t hi = ((size_t)aB * K + sB) * K + sA + 1;
         put(K - 1 - sA, 4 + sig_of_alt(aA, own[sA]), Hb + hi * D, Heb + hi, TRb + (size_t)i * D, TReb + i);
     }
@@ -855,8 +868,9 @@ __global__ void __launch_bounds__(256, 2) k_site_tiles_pipe(FamArgs<float> f, co
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_slot;
+    // tile -> (group, first item, rows); the group search starts from g, as a
+    // block's tiles ascend
     auto tile_info = [&](int tile, int& g, int64_t& i0, int& n) {
-        g = 0;
         while (g < 7 && tile >= st.tbeg[g + 1]) ++g;
         i0 = st.gbeg[g] + (int64_t)(tile - st.tbeg[g]) * kPipeRows;
         const int64_t left = st.gend[g] - i0;
@@ -880,17 +894,20 @@ __global__ void __launch_bounds__(256, 2) k_site_tiles_pipe(FamArgs<float> f, co
         }
         if (tid < n) tc::cp_async4(&s_sev[buf][tid], s_se[slot][tid]);
     };
+    // (group, rows) of tiles i, i+1, i+2 of the loop, carried forward
+    int g0 = 0, g1 = 0, g2 = 0, n0 = 0, n1 = 0;
     {
-        int g, n; int64_t i0;
-        tile_info(t_beg, g, i0, n);
-        if (tid < n) put_item(0, tid, items[i0 + tid]);
+        int64_t i0;
+        tile_info(t_beg, g0, i0, n0);
+        if (tid < n0) put_item(0, tid, items[i0 + tid]);
+        g1 = g0;
         if (t_beg + 1 < t_end) {
-            tile_info(t_beg + 1, g, i0, n);
-            if (tid < n) put_item(1, tid, items[i0 + tid]);
+            tile_info(t_beg + 1, g1, i0, n1);
+            if (tid < n1) put_item(1, tid, items[i0 + tid]);
         }
+        g2 = g1;
         __syncthreads();
-        tile_info(t_beg, g, i0, n);
-        fetch(0, 0, n);
+        fetch(0, 0, n0);
         tc::cp_async_commit();
     }
     // the split's units (8 columns of one row) of this thread: stage read and
@@ -905,27 +922,22 @@ __global__ void __launch_bounds__(256, 2) k_site_tiles_pipe(FamArgs<float> f, co
         rd_off[k] = (8 * rg + r8) * RS + 32 * c;
         wr_off[k] = tc::op_offset(8 * rg + r8, 8 * c, D);
     }
-    int cur_mat = -1;
+    int cur_mat = -1, mat_exp = 0;
     uint32_t phase = 0;
     bool ok = true;
     for (int i = 0, tile = t_beg; tile < t_end; ++i, ++tile) {
         const int cur = i & 1, ri = i % 3;
         unsigned char* const sc = stage0 + (size_t)cur * stage_bytes;
-        int g, n; int64_t i0;
-        tile_info(tile, g, i0, n);
+        const int g = g0, n = n0;
         // (1) the next tile's rows into the other stage (its last reader, the
         // MMAs of tile i-1, completed before the previous epilogue)
-        if (tile + 1 < t_end) {
-            int g1, n1; int64_t i1;
-            tile_info(tile + 1, g1, i1, n1);
-            fetch((i + 1) % 3, cur ^ 1, n1);
-        }
+        if (tile + 1 < t_end) fetch((i + 1) % 3, cur ^ 1, n1);
         tc::cp_async_commit();
         // (2) the items of the tile after next, into registers
         SiteItem nx{};
         int n2 = 0;
         if (tile + 2 < t_end) {
-            int g2; int64_t i2;
+            int64_t i2;
             tile_info(tile + 2, g2, i2, n2);
             if (tid < n2) nx = items[i2 + tid];
         }
@@ -949,20 +961,21 @@ __global__ void __launch_bounds__(256, 2) k_site_tiles_pipe(FamArgs<float> f, co
         #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (tid + k * 256 < nun) {
-                __align__(16) __half hi[8], lo[8];
+                __align__(16) __half2 hi[4], lo[4];
                 #pragma unroll
-                for (int j = 0; j < 8; ++j) tc::split_half(xv[k][j], hi[j], lo[j]);
+                for (int j = 0; j < 4; ++j) tc::split_half2(xv[k][2 * j], xv[k][2 * j + 1], hi[j], lo[j]);
                 const uint32_t off = wr_off[k];
                 *(uint4*)(sc + off) = *(const uint4*)hi;
                 *(uint4*)(sc + (size_t)kPipeRows * D * 2 + off) = *(const uint4*)lo;
             }
         }
-        // (5) the matrix image when the group's matrix changes
+        // (5) the matrix image (and its scale) when the group's matrix changes
         const int mat = st.mat[g];
         if (mat != cur_mat) {
             const int nimg = 4 * D * D / 16;
             const uint4* __restrict__ gsrc = f.tc_mats + (size_t)mat * nimg;
             for (int q = tid; q < nimg; q += blockDim.x) ((uint4*)Bh)[q] = __ldg(gsrc + q);
+            mat_exp = f.tc_exp[mat];
             cur_mat = mat;
         }
         tc::fence_proxy_async();
@@ -984,14 +997,12 @@ __global__ void __launch_bounds__(256, 2) k_site_tiles_pipe(FamArgs<float> f, co
                 }
             tc::mma_commit(&mbar);
         }
+        // (7) the items fetched in (2) replace those of tile i-1
+        if (tid < n2) put_item((i + 2) % 3, tid, nx);
         ok = tc::mbar_wait(&mbar, phase, 1u << 24) && ok;
         phase ^= 1u;
         tc::fence_after_sync();
-        // (7) the items fetched in (2) replace those of tile i-1
-        if (tid < n2) put_item((i + 2) % 3, tid, nx);
-        // (8) tensor memory -> registers twice (row maximum, then the scaled
-        // row), 8 columns at a time; warp w reads lanes 32 (w % 4) .. +31 and
-        // half (w / 4) of the columns
+        // (8) two passes over tensor memory, 8 columns at a time
         const int warp = tid >> 5, lane = tid & 31;
         const int q = warp & 3, h = warp >> 2, half = D >> 1;
         const int r = 32 * q + lane;
@@ -1015,12 +1026,11 @@ __global__ void __launch_bounds__(256, 2) k_site_tiles_pipe(FamArgs<float> f, co
             int e = 0;
             if (mm > 0.f) frexpf(mm, &e);
             float* o = s_dst[ri][r < n ? r : 0] + h * half;
-            // x 2^-e: one multiply by a normal power of two rounds as ldexpf does
             const bool pw = e >= -126 && e <= 126;
             const float sc2 = pw ? __int_as_float((127 - e) << 23) : 0.f;
             for (int c0 = 0; c0 < half; c0 += 8) {
                 float v[8];
-                tc::tmem_ld8(trow + c0, v);     // every lane of the warp takes part
+                tc::tmem_ld8(trow + c0, v);
                 tc::tmem_wait_ld();
                 if (r < n) {
                     #pragma unroll
@@ -1029,10 +1039,12 @@ __global__ void __launch_bounds__(256, 2) k_site_tiles_pipe(FamArgs<float> f, co
                     *(float4*)(o + c0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
                 }
             }
-            if (h == 0 && r < n) *s_de[ri][r] = s_sev[cur][r] + e + f.tc_exp[mat];
+            if (h == 0 && r < n) *s_de[ri][r] = s_sev[cur][r] + e + mat_exp;
         }
         tc::fence_before_sync();
         __syncthreads();
+        g0 = g1; n0 = n1;
+        g1 = g2; n1 = n2;
     }
     tc::cp_async_wait<0>();
     if (!ok && tid == 0) report(f.err, 5, 4, (long long)f.s0);
@@ -1047,9 +1059,9 @@ int fam_site_count(const FamArgs<T>& f, const SiteBufs& b, int nbb, cudaStream_t
     const int n = f.K * 8;
     k_site_boundary<T><<<nbb * 2, 256, (size_t)5 * f.D * sizeof(T), st>>>(f);
     k_site_build<T, false><<<nbb, 256, 0, st>>>(f, b);
-    launch_scan_i64(b.counts, b.offs, (int64_t)n * nbb, st);
+    const int ns = launch_scan_i64_wide(b.counts, b.offs, (int64_t)n * nbb, b.scan_tmp, st);
     k_site_bounds<<<1, 256, 0, st>>>(b.offs, n, nbb, b.bounds);
-    return 4;
+    return 3 + ns;
 }
 
 template <typename T>
@@ -1134,12 +1146,14 @@ __device__ __forceinline__ double scale_pow2(double x, int e)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kFamRows, 8) k_fam_rows(FamArgs<T> f, RowSet rows, double* partial,
+__global__ void __launch_bounds__(kFamRows, 12) k_fam_rows(FamArgs<T> f, RowSet rows, double* partial,
                                                        int64_t* span, double* partial_abs)
 {
     __shared__ OrbLists lists;
     __shared__ T s_ratio[kFamRows];                  // each row's ratio in the contraction type
     __shared__ __align__(16) const T* s_ptr[kFamRows][4];   // each row's L, R and correlator rows
+    __shared__ double s_coef[kFamRows];              // each row's coefficient, exponent and span,
+    __shared__ int s_ex[kFamRows], s_nmv[kFamRows];  // kept out of registers during the evaluation
     __shared__ double wsum[kFamRows / 32];
     __shared__ double wabs[kFamRows / 32];
     __shared__ long long wspan[kFamRows / 32];
@@ -1217,7 +1231,8 @@ __global__ void __launch_bounds__(kFamRows, 8) k_fam_rows(FamArgs<T> f, RowSet r
         }
     }
     s_ptr[myrow][0] = Lv; s_ptr[myrow][1] = Rv; s_ptr[myrow][2] = lt; s_ptr[myrow][3] = rs;
-    __syncwarp();                                   // a warp reads only its own rows' pointers
+    s_coef[myrow] = coef; s_ex[myrow] = ex; s_nmv[myrow] = nmv;
+    __syncwarp();                                   // a warp reads only its own rows' values
     const double inv_pm = s_inv_pm;
     const int pe = f.pe[b];
     // ---- evaluation: 8 lanes per row, 4 rows of the warp at a time
@@ -1277,10 +1292,11 @@ __global__ void __launch_bounds__(kFamRows, 8) k_fam_rows(FamArgs<T> f, RowSet r
             if (live) {
                 const V4* l4 = (const V4*)ltq;
                 const V4* r4 = (const V4*)rsq;
-                for (int k4 = sub; k4 < NP / 4; k4 += 8) {
+                for (int k4 = sub; k4 <= NP / 4; k4 += 8) {
                     const V4 t = l4[k4], u = r4[k4];
                     T x;
-                    x = t.x * u.x; X = fma(X, x, X + x);
+                    // the last group holds PL - 1 and PR - 1 (then zeros): (1 + a)(1 + b) - 1
+                    x = k4 == NP / 4 ? fma(t.x, u.x, t.x + u.x) : t.x * u.x; X = fma(X, x, X + x);
                     x = t.y * u.y; X = fma(X, x, X + x);
                     x = t.z * u.z; X = fma(X, x, X + x);
                     x = t.w * u.w; X = fma(X, x, X + x);
@@ -1290,7 +1306,7 @@ __global__ void __launch_bounds__(kFamRows, 8) k_fam_rows(FamArgs<T> f, RowSet r
                 const T Y = __shfl_xor_sync(kFull, X, o);
                 X = fma(X, Y, X + Y);
             }
-            if (live) ratio *= (T(1) + ltq[NP]) * (T(1) + rsq[NP]) * (T(1) + X);
+            if (live) ratio *= T(1) + X;
         }
         if (live && sub == 0) s_ratio[wbase + q] = ratio;
     }
@@ -1299,10 +1315,10 @@ __global__ void __launch_bounds__(kFamRows, 8) k_fam_rows(FamArgs<T> f, RowSet r
     // draw weight) / psi(n) and the power of two of the row's scaled vectors
     double acc = 0.0, aacc = 0.0;
     if (myrow < nr) {
-        acc = scale_pow2(coef * ((double)s_ratio[myrow] * inv_pm), ex - pe);
+        acc = scale_pow2(s_coef[myrow] * ((double)s_ratio[myrow] * inv_pm), s_ex[myrow] - pe);
         if (partial_abs) aacc = fabs(acc);
     }
-    long long sp = nmv;
+    long long sp = s_nmv[myrow];
     for (int o = 16; o; o >>= 1) {
         acc += __shfl_xor_sync(kFull, acc, o);
         sp += __shfl_xor_sync(kFull, sp, o);

@@ -12,6 +12,7 @@ template <typename T>
 struct FamArgs {
     HamView h;
     int K, D;
+    FastDiv div3K, div9K;     // / 3K, / 9K (cluster key fields)
     int split;                // blocks per sample of the correlator-factor kernel
     int nmax;                 // vectors per block-wide mat-vec batch
     size_t batch_bytes;       // shared memory of one batch (see fam_batch_bytes)
@@ -76,6 +77,7 @@ struct SiteBufs {
     int64_t* offs;      // [K*8*nbb + 1] exclusive prefix of counts
     int64_t* bounds;    // [K*8 + 1] first item of each (step, group)
     void* items;        // SiteItemT<T>[total]
+    int64_t* scan_tmp;  // scan_i64_tmp_elems(K*8*nbb) values
 };
 // boundary vectors and first-site families, then the item counts, their
 // prefix and the (step, group) bounds (device); returns launches

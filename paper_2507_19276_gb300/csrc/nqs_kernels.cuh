@@ -91,6 +91,9 @@ int launch_scan_chunks_u64(uint64_t* w, uint64_t* total, int64_t Ns, uint32_t n_
                             cudaStream_t st);
 // exclusive scan of n values -> out[0..n] (out[n] = total); single block
 int launch_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st);
+// the same over many blocks for large n; tmp holds scan_i64_tmp_elems(n) values
+inline int64_t scan_i64_tmp_elems(int64_t n) { return 2 * (n / 4096 + 2); }
+int launch_scan_i64_wide(const int64_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStream_t st);
 // chunk bases for row sets: out[s] = sum_{s'<s} ceil(cnt[s'] / rows), out[Ns] total
 int launch_chunk_base(const int64_t* cnt, int rows, int64_t* out, int64_t Ns, cudaStream_t st);
 

@@ -120,6 +120,58 @@ int launch_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st)
     return 1;
 }
 
+// Multi-block exclusive scan: sums of 4096-element tiles, one block scans the
+// sums, then every tile rescans its elements from its offset (integers: the
+// result does not depend on the tiling).
+constexpr int kScanTile = 4096;   // 1024 threads x 4 elements
+
+__global__ void __launch_bounds__(1024) k_scan_tile_sums(const int64_t* in, int64_t n, int64_t* sums)
+{
+    __shared__ int64_t wt[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int64_t v = 0;
+    #pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t i = base + k * 1024 + threadIdx.x;
+        if (i < n) v += in[i];
+    }
+    v = block_incl_scan<int64_t>(v, wt);
+    if (threadIdx.x == blockDim.x - 1) sums[blockIdx.x] = v;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(const int64_t* in, int64_t* out, int64_t n,
+                                                      const int64_t* tile_off)
+{
+    __shared__ int64_t wt[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + 4 * (int64_t)threadIdx.x;
+    int64_t x[4], s = 0;
+    #pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        x[k] = base + k < n ? in[base + k] : 0;
+        s += x[k];
+    }
+    const int64_t inc = block_incl_scan<int64_t>(s, wt);
+    int64_t run = tile_off[blockIdx.x] + inc - s;
+    #pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += x[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) out[n] = run;
+}
+
+int launch_scan_i64_wide(const int64_t* in, int64_t* out, int64_t n, int64_t* tmp, cudaStream_t st)
+{
+    if (n <= 16 * kScanTile || !tmp) return launch_scan_i64(in, out, n, st);
+    const int64_t nt = (n + kScanTile - 1) / kScanTile;
+    int64_t* sums = tmp;
+    int64_t* offs = tmp + nt + 1;
+    k_scan_tile_sums<<<(unsigned)nt, 1024, 0, st>>>(in, n, sums);
+    k_scan_i64<<<1, 1024, 0, st>>>(sums, offs, nt, 0);
+    k_scan_tiles<<<(unsigned)nt, 1024, 0, st>>>(in, out, n, offs);
+    return 3;
+}
+
 int launch_chunk_base(const int64_t* cnt, int rows, int64_t* out, int64_t Ns, cudaStream_t st)
 {
     k_scan_i64<<<1, 1024, 0, st>>>(cnt, out, Ns, rows);
