@@ -53,8 +53,9 @@ struct nqs_ctx {
     DevBuf base_det, base_draw, part_det, part_draw, eloc, edet, estoch, summary, derr;
     DevBuf span_det, span_draw;
     // shared-prefix path
-    DevBuf fG, fGe, fH, fHe, ftl_end, ftl_idx, ftr_idx, ftl_tot, ftr_tot, ftl_base,
-        ftr_base, fTL, fTLe, fTR, fTRe, ftl_ci, ftl_list, ftr_list, ftl_cnt, frbl, frbr, frbl_base,
+    DevBuf fpool, fpoole;      // table rows (G, H, TL, TR of a batch) and their exponents
+    DevBuf ftl_end, ftl_idx, ftr_idx, ftl_tot, ftr_tot, ftl_base,
+        ftr_base, ftl_ci, ftl_list, ftr_list, ftl_cnt, frbl, frbr, frbl_base,
         frbr_base;
     std::vector<int64_t> det_off_h;
     int64_t fam_matvecs = 0;   // work of the last shared-prefix pass
@@ -426,7 +427,7 @@ int site_tables(nqs_ctx* c, const FamArgs<T>& f, int nbb)
     std::vector<int64_t> bounds((size_t)K * 8 + 1);
     CK(cudaMemcpyAsync(bounds.data(), c->site_bounds.p, bounds.size() * 8, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    TRY(ensure(c, c->site_items, (size_t)(bounds.back() + 1) * sizeof(SiteItemT<T>)));
+    TRY(ensure(c, c->site_items, (size_t)(bounds.back() + 1) * sizeof(SiteItem)));
     sb.items = c->site_items.p;
     LAUNCH(NQS_STAGE_TABLES, fam_site_fill(f, sb, nbb, c->stream));
     for (int tau = 0; tau < K; ++tau)
@@ -469,11 +470,6 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
     int64_t nb = (int64_t)std::max<size_t>(1, budget / per);
     if (nb > Ns) nb = Ns;
     if (nb > 65535) nb = 65535;
-    const size_t KKD = (size_t)3 * K * K * D;
-    TRY(ensure(c, c->fG, nb * KKD * sizeof(T)));
-    TRY(ensure(c, c->fH, nb * KKD * sizeof(T)));
-    TRY(ensure(c, c->fGe, nb * 3 * K * K * 4));
-    TRY(ensure(c, c->fHe, nb * 3 * K * K * 4));
     TRY(ensure(c, c->ftl_end, nb * nk * 4));
     TRY(ensure(c, c->ftl_idx, nb * nk * 4));
     TRY(ensure(c, c->ftr_idx, nb * nk * 4));
@@ -540,8 +536,6 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
         // few samples (a small call, FP64 re-evaluation): spread each sample's
         // correlator factors over several blocks so that about two blocks per SM run
         f.split = nbb >= 2 * c->n_sm ? 1 : std::min(32, (2 * c->n_sm + nbb - 1) / nbb);
-        f.G = (T*)c->fG.p; f.Ge = (int*)c->fGe.p;
-        f.H = (T*)c->fH.p; f.He = (int*)c->fHe.p;
         f.pm = (const double*)c->pmant.p + s0; f.pe = (const int*)c->pexp.p + s0;
         f.tl_end = (int*)c->ftl_end.p;
         f.tl_idx = (int*)c->ftl_idx.p;
@@ -586,16 +580,27 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
                               tlb[nbb] + trb[nbb];
             CK(cudaMemcpyAsync(c->ftl_base.p, tlb.data(), (size_t)(nbb + 1) * 8, cudaMemcpyHostToDevice, c->stream));
             CK(cudaMemcpyAsync(c->ftr_base.p, trb.data(), (size_t)(nbb + 1) * 8, cudaMemcpyHostToDevice, c->stream));
-            TRY(ensure(c, c->fTL, (size_t)(tlb[nbb] + 1) * D * sizeof(T)));
-            TRY(ensure(c, c->fTLe, (size_t)(tlb[nbb] + 1) * 4));
-            TRY(ensure(c, c->fTR, (size_t)(trb[nbb] + 1) * D * sizeof(T)));
-            TRY(ensure(c, c->fTRe, (size_t)(trb[nbb] + 1) * 4));
+            // one pool of table rows: G families, H families, TL entries, TR rows
+            const int64_t fam_rows = (int64_t)nbb * 3 * K * K;
+            f.row_H = fam_rows;
+            f.row_TL = 2 * fam_rows;
+            f.row_TR = f.row_TL + tlb[nbb] + 1;
+            const int64_t rows_total = f.row_TR + trb[nbb] + 1;
+            if (rows_total >= ((int64_t)1 << 32))
+                return set_err(c, NQS_ERR_UNSUPPORTED, "shared-prefix tables of %lld rows exceed 2^32",
+                               (long long)rows_total);
+            TRY(ensure(c, c->fpool, (size_t)rows_total * D * sizeof(T)));
+            TRY(ensure(c, c->fpoole, (size_t)rows_total * 4));
             CK(cudaStreamSynchronize(c->stream));   // the host vectors above must outlive the copies
         }
+        f.pool = (T*)c->fpool.p;
+        f.pool_e = (int*)c->fpoole.p;
+        f.G = f.pool; f.Ge = f.pool_e;
+        f.H = f.pool + (size_t)f.row_H * D; f.He = f.pool_e + f.row_H;
         f.tl_base = (const int64_t*)c->ftl_base.p;
         f.tr_base = (const int64_t*)c->ftr_base.p;
-        f.TL = (T*)c->fTL.p; f.TLe = (int*)c->fTLe.p;
-        f.TR = (T*)c->fTR.p; f.TRe = (int*)c->fTRe.p;
+        f.TL = f.pool + (size_t)f.row_TL * D; f.TLe = f.pool_e + f.row_TL;
+        f.TR = f.pool + (size_t)f.row_TR * D; f.TRe = f.pool_e + f.row_TR;
         f.rbl = (T*)c->frbl.p; f.rbr = (T*)c->frbr.p;
         f.rbl_base = (const int64_t*)c->frbl_base.p;
         f.rbr_base = (const int64_t*)c->frbr_base.p;
@@ -660,9 +665,9 @@ extern "C" int nqs_destroy(nqs_ctx* c)
                       &c->draw_rank, &c->draw_coef, &c->n_unique, &c->base_det, &c->base_draw,
                       &c->part_det, &c->part_draw, &c->eloc, &c->edet, &c->estoch, &c->summary,
                       &c->derr, &c->span_det, &c->span_draw, &c->Af, &c->ATf,
-                      &c->WT, &c->WTf, &c->fG, &c->fGe, &c->fH, &c->fHe, &c->ftl_end,
+                      &c->WT, &c->WTf, &c->fpool, &c->fpoole, &c->ftl_end,
                       &c->ftl_idx, &c->ftr_idx, &c->ftl_tot, &c->ftr_tot, &c->ftl_base,
-                      &c->ftr_base, &c->fTL, &c->fTLe, &c->fTR, &c->fTRe, &c->ftl_ci,
+                      &c->ftr_base, &c->ftl_ci,
                       &c->ftl_list, &c->ftr_list, &c->ftl_cnt, &c->frbl, &c->frbr, &c->frbl_base,
                       &c->frbr_base, &c->tc_img, &c->tc_exps, &c->part_det_abs,
                       &c->part_draw_abs, &c->eabs, &c->logf_save, &c->summary2, &c->ref_idx,

@@ -629,17 +629,15 @@ __global__ void __launch_bounds__(256) k_site_build(FamArgs<T> f, SiteBufs sb)
     for (int i = threadIdx.x; i < K; i += blockDim.x) own[i] = sigma_at(na, nb, i);
     __syncthreads();
     const size_t nk = (size_t)K * K * 9;
-    T* Gb = f.G + (size_t)b * 3 * K * K * D;
-    int* Geb = f.Ge + (size_t)b * 3 * K * K;
-    T* Hb = f.H + (size_t)b * 3 * K * K * D;
-    int* Heb = f.He + (size_t)b * 3 * K * K;
-    auto put = [&](int tau, int g, const T* src, const int* se, T* dst, int* de) {
+    // pool rows of this sample's G and H families
+    const int64_t Gr = (int64_t)b * 3 * K * K, Hr = f.row_H + (int64_t)b * 3 * K * K;
+    auto put = [&](int tau, int g, int64_t src, int64_t dst) {
         const int slot = atomicAdd(&cnt[tau * 8 + g], 1);
         if (FILL) {
             const int64_t at = sb.offs[((int64_t)tau * 8 + g) * nbb + b] + slot;
-            SiteItemT<T> it;
-            it.src = src; it.dst = dst; it.se = se; it.de = de;
-            ((SiteItemT<T>*)sb.items)[at] = it;
+            SiteItem it;
+            it.src = (uint32_t)src; it.dst = (uint32_t)dst;
+            ((SiteItem*)sb.items)[at] = it;
         }
     };
     // (1) families created before the step (k_site_boundary makes the new ones
@@ -648,46 +646,43 @@ __global__ void __launch_bounds__(256) k_site_build(FamArgs<T> f, SiteBufs sb)
         const int tau = w >> 1, side = w & 1;
         const int t = side == 0 ? tau : K - 1 - tau;
         const int o = own[t];
-        T* Tb = side == 0 ? Gb : Hb;
-        int* Te = side == 0 ? Geb : Heb;
+        const int64_t Tr = side == 0 ? Gr : Hr;
         const int tp = side == 0 ? t - 1 : t + 1;      // the family's previous site
         for (int j = 0; j < tau; ++j) {
             const int sf = side == 0 ? j : K - 1 - j;
             for (int a = 0; a < 3; ++a) {
-                const size_t base = ((size_t)a * K + sf) * K;
-                put(tau, side * 4 + o, Tb + (base + tp) * D, Te + base + tp, Tb + (base + t) * D, Te + base + t);
+                const int64_t base = Tr + ((int64_t)a * K + sf) * K;
+                put(tau, side * 4 + o, base + tp, base + t);
             }
         }
     }
     // (2) TL clusters: creation at s2 with A_{s2}^{a2}, then A_t^{own} up to the last use
     const int ncl = f.tl_count[b];
     const int* tll = f.tl_list + (size_t)b * nk;
-    T* TLb = f.TL + (size_t)f.tl_base[b] * D;
-    int* TLeb = f.TLe + f.tl_base[b];
+    const int64_t TLr = f.row_TL + f.tl_base[b];
     for (int c = threadIdx.x; c < ncl; c += blockDim.x) {
         const int key = tll[c];
         int s2, a2, s1, a1;
         key_fields(f, key, s2, a2, s1, a1);
         const int off = f.tl_idx[(size_t)b * nk + key];
         const int end = f.tl_end[(size_t)b * nk + key];
-        const size_t gi = ((size_t)a1 * K + s1) * K + (s2 - 1);
-        put(s2, sig_of_alt(a2, own[s2]), Gb + gi * D, Geb + gi, TLb + (size_t)off * D, TLeb + off);
+        const int64_t gi = Gr + ((int64_t)a1 * K + s1) * K + (s2 - 1);
+        put(s2, sig_of_alt(a2, own[s2]), gi, TLr + off);
         for (int t = s2 + 1; t <= end; ++t) {
-            const int q = off + (t - s2);
-            put(t, own[t], TLb + (size_t)(q - 1) * D, TLeb + q - 1, TLb + (size_t)q * D, TLeb + q);
+            const int64_t q = TLr + off + (t - s2);
+            put(t, own[t], q - 1, q);
         }
     }
     // (3) TR rows: H_{sB,aB}(sA+1) A_{sA}^{aA} at the right step of site sA
     const int ntr = f.tr_total[b];
     const int* trl = f.tr_list + (size_t)b * nk;
-    T* TRb = f.TR + (size_t)f.tr_base[b] * D;
-    int* TReb = f.TRe + f.tr_base[b];
+    const int64_t TRr = f.row_TR + f.tr_base[b];
     for (int i = threadIdx.x; i < ntr; i += blockDim.x) {
         const int key = trl[i];
         int sA, aA, sB, aB;
         key_fields(f, key, sA, aA, sB, aB);
-        const size_t hi = ((size_t)aB * K + sB) * K + sA + 1;
-        put(K - 1 - sA, 4 + sig_of_alt(aA, own[sA]), Hb + hi * D, Heb + hi, TRb + (size_t)i * D, TReb + i);
+        const int64_t hi = Hr + ((int64_t)aB * K + sB) * K + sA + 1;
+        put(K - 1 - sA, 4 + sig_of_alt(aA, own[sA]), hi, TRr + i);
     }
     if (!FILL) {
         __syncthreads();
@@ -760,7 +755,7 @@ struct SiteStep {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_site_tiles(FamArgs<T> f, const SiteItemT<T>* items, SiteStep st)
+__global__ void __launch_bounds__(256, 4) k_site_tiles(FamArgs<T> f, const SiteItem* items, SiteStep st)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ uint32_t tmem_slot;
@@ -782,8 +777,9 @@ __global__ void __launch_bounds__(256, 4) k_site_tiles(FamArgs<T> f, const SiteI
         const int64_t left = st.gend[g] - i0;
         const int n = (int)(left < rows ? left : rows);
         for (int r = threadIdx.x; r < n; r += blockDim.x) {
-            const SiteItemT<T> it = items[i0 + r];
-            s_src[r] = it.src; s_dst[r] = it.dst; s_se[r] = it.se; s_de[r] = it.de;
+            const SiteItem it = items[i0 + r];
+            s_src[r] = f.pool + (size_t)it.src * D; s_dst[r] = f.pool + (size_t)it.dst * D;
+            s_se[r] = f.pool_e + it.src; s_de[r] = f.pool_e + it.dst;
         }
         __syncthreads();
         const int mat = st.mat[g];
@@ -848,10 +844,8 @@ __global__ void __launch_bounds__(256, 2) k_site_tiles_pipe(FamArgs<float> f, co
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ uint32_t tmem_slot;
     __shared__ __align__(8) uint64_t mbar;
-    __shared__ const float* s_src[3][kPipeRows];
-    __shared__ float* s_dst[3][kPipeRows];
-    __shared__ const int* s_se[3][kPipeRows];
-    __shared__ int* s_de[3][kPipeRows];
+    __shared__ uint32_t s_src[3][kPipeRows];          // pool rows of the items
+    __shared__ uint32_t s_dst[3][kPipeRows];
     __shared__ int s_sev[2][kPipeRows];
     __shared__ float s_rmax[2][kPipeRows];
     const int D = f.D, tid = threadIdx.x;
@@ -877,7 +871,7 @@ __global__ void __launch_bounds__(256, 2) k_site_tiles_pipe(FamArgs<float> f, co
         n = (int)(left < kPipeRows ? left : kPipeRows);
     };
     auto put_item = [&](int slot, int r, const SiteItem& it) {
-        s_src[slot][r] = it.src; s_dst[slot][r] = it.dst; s_se[slot][r] = it.se; s_de[slot][r] = it.de;
+        s_src[slot][r] = it.src; s_dst[slot][r] = it.dst;
     };
     // rows and source exponents of the tile in item slot `slot` into stage `buf`
     // piece v = tid + 256 j of a tile is row v / qpr, 16-byte piece v % qpr
@@ -888,11 +882,11 @@ __global__ void __launch_bounds__(256, 2) k_site_tiles_pipe(FamArgs<float> f, co
         unsigned char* sg = stage0 + (size_t)buf * stage_bytes;
         int r = f_r0, q = f_q0;
         while (r < n) {
-            tc::cp_async16(sg + r * RS + q * 16, s_src[slot][r] + 4 * q);
+            tc::cp_async16(sg + r * RS + q * 16, f.pool + (size_t)s_src[slot][r] * D + 4 * q);
             r += f_dr; q += f_dq;
             if (q >= qpr) { q -= qpr; ++r; }
         }
-        if (tid < n) tc::cp_async4(&s_sev[buf][tid], s_se[slot][tid]);
+        if (tid < n) tc::cp_async4(&s_sev[buf][tid], f.pool_e + s_src[slot][tid]);
     };
     // (group, rows) of tiles i, i+1, i+2 of the loop, carried forward
     int g0 = 0, g1 = 0, g2 = 0, n0 = 0, n1 = 0;
@@ -1022,26 +1016,37 @@ __global__ void __launch_bounds__(256, 2) k_site_tiles_pipe(FamArgs<float> f, co
         __syncthreads();
         tc::fence_after_sync();
         {
+            // the scaled rows go to the stage (free since the MMAs completed;
+            // stride RS, so 8 consecutive rows fill the 32 banks), then leave
+            // it row by row with coalesced stores
             const float mm = fmaxf(s_rmax[0][r], s_rmax[1][r]);
             int e = 0;
             if (mm > 0.f) frexpf(mm, &e);
-            float* o = s_dst[ri][r < n ? r : 0] + h * half;
+            float* o = (float*)(sc + r * RS) + h * half;
             const bool pw = e >= -126 && e <= 126;
             const float sc2 = pw ? __int_as_float((127 - e) << 23) : 0.f;
             for (int c0 = 0; c0 < half; c0 += 8) {
                 float v[8];
                 tc::tmem_ld8(trow + c0, v);
                 tc::tmem_wait_ld();
-                if (r < n) {
-                    #pragma unroll
-                    for (int j = 0; j < 8; ++j) v[j] = pw ? v[j] * sc2 : ldexpf(v[j], -e);
-                    *(float4*)(o + c0) = make_float4(v[0], v[1], v[2], v[3]);
-                    *(float4*)(o + c0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
-                }
+                #pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = pw ? v[j] * sc2 : ldexpf(v[j], -e);
+                *(float4*)(o + c0) = make_float4(v[0], v[1], v[2], v[3]);
+                *(float4*)(o + c0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
             }
-            if (h == 0 && r < n) *s_de[ri][r] = s_sev[cur][r] + e + mat_exp;
+            if (h == 0 && r < n) f.pool_e[s_dst[ri][r]] = s_sev[cur][r] + e + mat_exp;
         }
         tc::fence_before_sync();
+        __syncthreads();
+        {
+            int rr = f_r0, qq = f_q0;             // the fetch's piece order: lanes along a row
+            while (rr < n) {
+                const float4 w = *(const float4*)(sc + rr * RS + qq * 16);
+                *(float4*)(f.pool + (size_t)s_dst[ri][rr] * D + 4 * qq) = w;
+                rr += f_dr; qq += f_dq;
+                if (qq >= qpr) { qq -= qpr; ++rr; }
+            }
+        }
         __syncthreads();
         g0 = g1; n0 = n1;
         g1 = g2; n1 = n2;
@@ -1114,7 +1119,7 @@ int fam_site_step(const FamArgs<T>& f, const SiteBufs& b, int tau, const int64_t
     allow_max_smem(k_site_tiles<T>);
     const size_t smem = f.batch_bytes;
     const int grid = tiles < max_ctas ? tiles : max_ctas;
-    k_site_tiles<T><<<grid, 256, smem, st>>>(f, (const SiteItemT<T>*)b.items, ss);
+    k_site_tiles<T><<<grid, 256, smem, st>>>(f, (const SiteItem*)b.items, ss);
     return 1;
 }
 

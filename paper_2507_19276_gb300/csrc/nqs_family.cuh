@@ -25,6 +25,10 @@ struct FamArgs {
     const T* AT;              // transposed copy, AT[b][a]
     const uint64_t* samples;  // all samples of the call
     int64_t s0, s1;           // batch = samples [s0, s1)
+    // table pool of the batch: rows of D elements (and one exponent each) for the
+    // G families, then the H families, the TL entries and the TR rows
+    T* pool; int* pool_e;
+    int64_t row_H, row_TL, row_TR;   // first pool row of the H, TL and TR tables
     // per batch sample b (= s - s0)
     T* G; int* Ge;            // [b][3][K][K][D]: G_{s,a}(t) at ((a*K+s)*K+t), t >= s
     T* H; int* He;            // [b][3][K][K][D]: H_{s,a}(t) at ((a*K+s)*K+t), t <= s
@@ -64,19 +68,17 @@ template <typename T> int fam_launch_rows(const FamArgs<T>& f, const RowSet& row
 // items of site step tau fall into 8 groups (side x local state of the
 // matrix), each one matrix image, and one launch per step runs 128-row tiles
 // over all samples' items.
-template <typename T>
-struct SiteItemT {
-    const T* src;       // input vector
-    T* dst;             // output vector
-    const int* se;      // input power-of-two exponent
-    int* de;            // output exponent (= input + the product's own)
+// One product of a site step: row `src` of the table pool times the step's
+// site matrix into row `dst` (rows of D elements; each row's exponent at the
+// same index of the exponent pool).
+struct SiteItem {
+    uint32_t src, dst;
 };
-using SiteItem = SiteItemT<float>;       // the same size for every T
 struct SiteBufs {
     int64_t* counts;    // [K][8][nbb] items per (step, group, sample)
     int64_t* offs;      // [K*8*nbb + 1] exclusive prefix of counts
     int64_t* bounds;    // [K*8 + 1] first item of each (step, group)
-    void* items;        // SiteItemT<T>[total]
+    void* items;        // SiteItem[total]
     int64_t* scan_tmp;  // scan_i64_tmp_elems(K*8*nbb) values
 };
 // boundary vectors and first-site families, then the item counts, their
