@@ -266,25 +266,46 @@ __device__ void tc_apply(const FamArgs<float>& f, BatchSmem<float>& sm, const Ac
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    // the scaled rows leave through shared memory in column slices of up to 64
+    // (row stride 272 bytes: 8 consecutive rows fill the 32 banks), copied out
+    // row by row so that a warp's stores fill whole lines. The slice buffer
+    // overlays the operands (free now that the MMAs completed); for D > 128 it
+    // reaches into the matrix image, which is reloaded per chunk there anyway.
+    constexpr int kSRS = 272;
+    float mm = 0.f;
+    int e = 0;
     if (warp < 8) {
-        const float mm = fmaxf(sm.rmax[r], sm.rmax[128 + r]);
-        int e = 0;
+        mm = fmaxf(sm.rmax[r], sm.rmax[128 + r]);
         if (mm > 0.f) frexpf(mm, &e);
-        float* o = acc.dst(r < n ? r : 0) + h * half;
-        for (int c0 = 0; c0 < half; c0 += 8) {
-            float v[8];
-            tc::tmem_ld8(trow + c0, v);     // every lane of the warp takes part
-            tc::tmem_wait_ld();
-            if (r < n) {
-                float4 w0, w1;
-                w0.x = ldexpf(v[0], -e); w0.y = ldexpf(v[1], -e); w0.z = ldexpf(v[2], -e); w0.w = ldexpf(v[3], -e);
-                w1.x = ldexpf(v[4], -e); w1.y = ldexpf(v[5], -e); w1.z = ldexpf(v[6], -e); w1.w = ldexpf(v[7], -e);
-                *(float4*)(o + c0) = w0;
-                *(float4*)(o + c0 + 4) = w1;
-            }
-        }
         if (h == 0 && r < n) acc.set_exp(r, e + f.tc_exp[mat]);
     }
+    const bool pw = e >= -126 && e <= 126;
+    const float sc2 = pw ? __int_as_float((127 - e) << 23) : 0.f;
+    unsigned char* slice = sm.Ah;
+    for (int cs = 0; cs < D; cs += 64) {
+        const int sw = D - cs < 64 ? D - cs : 64, hw = sw >> 1;
+        if (warp < 8) {
+            float* o = (float*)(slice + r * kSRS) + h * hw;
+            const uint32_t tr = sm.tmem + ((uint32_t)(32 * q) << 16) + cs + h * hw;
+            for (int c0 = 0; c0 < hw; c0 += 8) {
+                float v[8];
+                tc::tmem_ld8(tr + c0, v);   // every lane of the warp takes part
+                tc::tmem_wait_ld();
+                #pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = pw ? v[j] * sc2 : ldexpf(v[j], -e);
+                *(float4*)(o + c0) = make_float4(v[0], v[1], v[2], v[3]);
+                *(float4*)(o + c0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
+            }
+        }
+        __syncthreads();
+        const int qpr = sw >> 2;                  // 16-byte pieces per row of the slice
+        for (int v = threadIdx.x; v < n * qpr; v += blockDim.x) {
+            const int rr = v / qpr, qq = v - rr * qpr;
+            *(float4*)(acc.dst(rr) + cs + 4 * qq) = *(const float4*)(slice + rr * kSRS + qq * 16);
+        }
+        __syncthreads();
+    }
+    if (128 * kSRS > 4 * 128 * KC) sm.cur_mat = -1;   // the slice reached into the image
     tc::fence_before_sync();
     __syncthreads();
 }
