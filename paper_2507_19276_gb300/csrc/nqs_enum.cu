@@ -83,8 +83,11 @@ __global__ void __launch_bounds__(kEnumWarps * 32) k_write_dets(EnumArgs a)
     const size_t srow = (size_t)s * a.n_chunks;
     const uint32_t c0 = (blockIdx.x * kEnumWarps + warp) * kWriteChunks;
     if (c0 >= a.n_chunks) return;
-    uint32_t m = 0;
-    if (lane < kWriteChunks && c0 + lane < a.n_chunks) m = a.chunk_mask[srow + c0 + lane];
+    uint32_t m = 0, co = 0;
+    if (lane < kWriteChunks && c0 + lane < a.n_chunks) {
+        m = a.chunk_mask[srow + c0 + lane];
+        co = a.chunk_off[srow + c0 + lane];
+    }
     const int cnt = __popc(m);
     int incl = cnt;
     for (int o = 1; o < kWriteChunks; o <<= 1) {
@@ -92,26 +95,28 @@ __global__ void __launch_bounds__(kEnumWarps * 32) k_write_dets(EnumArgs a)
         if (lane >= o) incl += u;
     }
     int ex[kWriteChunks];
-    uint32_t mk[kWriteChunks];
+    uint32_t mk[kWriteChunks], cof[kWriteChunks];
     #pragma unroll
     for (int k = 0; k < kWriteChunks; ++k) {
         ex[k] = __shfl_sync(kFull, incl - cnt, k);
         mk[k] = __shfl_sync(kFull, m, k);
+        cof[k] = __shfl_sync(kFull, co, k);
     }
+    const int64_t base = a.det_off[s];
     const int total = __shfl_sync(kFull, incl, kWriteChunks - 1);
     for (int j = lane; j < total; j += 32) {
         int k = 0, e0 = ex[0];                       // chunk of entry j, selected with
-        uint32_t bits = mk[0];                       // static indices (no local memory)
+        uint32_t bits = mk[0], off = cof[0];         // static indices (no local memory)
         #pragma unroll
         for (int q = 1; q < kWriteChunks; ++q)
-            if (ex[q] <= j) { k = q; e0 = ex[q]; bits = mk[q]; }
+            if (ex[q] <= j) { k = q; e0 = ex[q]; bits = mk[q]; off = cof[q]; }
         const int idx = j - e0;                      // rank among the chunk's set bits
         const uint32_t r = (c0 + k) * 32 + (uint32_t)nth_set_bit(bits, idx);
         uint64_t ma, mb;
         int odd;
         const Exc e = decode_rank(h, lists, r);
         const double H = matrix_element(h, na, nb, e, ma, mb, odd);
-        const int64_t pos = a.det_off[s] + a.chunk_off[srow + c0 + k] + idx;
+        const int64_t pos = base + off + idx;
         if (a.out_rank) a.out_rank[pos] = r;
         if (a.out_H) a.out_H[pos] = H;
         if (a.out_det) { a.out_det[2 * pos] = ma; a.out_det[2 * pos + 1] = mb; }
