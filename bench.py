@@ -62,7 +62,7 @@ FP64_PEAK_TFLOPS = 1.196
 # summed over its kernels, from ncu counters on the H50 shape (D = 64) with
 # 512 samples; the stage's traffic grows in proportion to the amplitudes
 # evaluated. None until taken for the current kernels.
-STAGE_TRAFFIC_PER_AMP = {"mixed": None, "fp64_shared": None}
+STAGE_TRAFFIC_PER_AMP = {"mixed": 328.5, "fp64_shared": None}
 
 DTYPES = {"mixed": "f16x3 tensor-core products (f32 accumulate) + f32 gathers; f64 H, psi(n), "
                    "ratios, sums; heaviest samples re-evaluated in f64 to the energy tolerance",
