@@ -239,7 +239,10 @@ int nqs_draws_noalloc(nqs_ctx* ctx, const uint64_t* samples, int64_t Ns, double 
  *  e_loc [Ns] receives E_loc; `out` (host struct, may be NULL) the summary.
  *  n_draws = 0 keeps only the deterministic part (biased); an empty or
  *  zero-weight remainder gives E^s = 0. A sample with psi(n) = 0 yields
- *  NQS_ERR_INVALID_ARG. */
+ *  NQS_ERR_INVALID_ARG. The shared-prefix forms return NQS_ERR_UNSUPPORTED
+ *  for n_hidden > 512 and when one sample batch's tables would exceed 2^32
+ *  rows of D elements (rows are addressed by 32-bit indices; the batch size
+ *  follows the memory budget, so this needs a budget far above 2^32 rows). */
 int nqs_local_energy(nqs_ctx* ctx, const uint64_t* samples, const double* counts, int64_t Ns,
                      double det_threshold, int n_draws, uint64_t philox_seed, double* e_loc,
                      nqs_energy_summary* out);
