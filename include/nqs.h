@@ -106,8 +106,9 @@ enum {
     NQS_STAGE_AMP_DRAW = 5,   /* amplitudes and ratios of the drawn rows */
     NQS_STAGE_FINAL = 6,      /* E_loc sums and the weighted summary */
     NQS_STAGE_OTHER = 7,      /* nqs_connected / nqs_amplitude / gradient work */
-    NQS_STAGE_TABLES = 8,     /* shared-prefix tables: family sweeps, cluster marks,
-                                 two-change clusters and their propagation */
+    NQS_STAGE_TABLES = 8,     /* shared-prefix tables: one-change families, cluster
+                                 marks, two-change clusters and their propagation,
+                                 correlator factors */
     NQS_N_STAGES = 9
 };
 
@@ -126,8 +127,8 @@ typedef struct {
                                evaluation performs */
     int64_t matvecs;        /* D x D matrix-vector products this call performed
                                (equals span_sites, x in-degree for graphs, in the
-                               plain form; family sweeps plus two-change clusters in
-                               the shared-prefix form; of the pass over the whole
+                               plain form; one-change families plus two-change
+                               clusters in the shared-prefix form; of the pass over the whole
                                batch) */
     int64_t n_refined;      /* samples re-evaluated in FP64 (energy_tolerance) */
     double e_error_bound;   /* with energy_tolerance > 0 in the mixed form: the

@@ -405,7 +405,7 @@ int amp_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, RowSet rows, int64
     return NQS_OK;
 }
 
-// Site-synchronous sweeps, TL clusters and TR rows of one sample batch
+// Site-synchronous families, TL clusters and TR rows of one sample batch
 // (tensor-core path): boundary vectors and first-site families per sample,
 // then count the items per (step, group, sample), read the per-step group
 // bounds back, write the items, and one launch per site step.
@@ -549,7 +549,7 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
         stage_begin(c, NQS_STAGE_TABLES);
         CK(cudaMemsetAsync(c->ftl_end.p, 0xff, (size_t)nbb * nk * 4, c->stream));
         CK(cudaMemsetAsync(c->ftr_idx.p, 0, (size_t)nbb * nk * 4, c->stream));
-        // (the sweeps run with TL and TR, site-synchronously, below)
+        // (the families are built with TL and TR, site-synchronously, below)
         LAUNCH(NQS_STAGE_TABLES, fam_launch_mark<T>(f, rd, nbb, c->stream));
         if (n_draws > 0) LAUNCH(NQS_STAGE_TABLES, fam_launch_mark<T>(f, rs, nbb, c->stream));
         LAUNCH(NQS_STAGE_TABLES, fam_launch_compact<T>(f, nbb, c->stream));
@@ -575,7 +575,7 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
                 TRY(ensure(c, c->frbl, (size_t)lb[nbb] * rl * sizeof(T)));
                 TRY(ensure(c, c->frbr, (size_t)rb[nbb] * rl * sizeof(T)));
             }
-            // work: both sweeps (4 + 3t products at step t), every TL entry, every TR row
+            // work: both family sides (4 + 3t products at step t), every TL entry, every TR row
             c->fam_matvecs += (int64_t)nbb * 2 * (4 * (int64_t)K + 3 * (int64_t)K * (K - 1) / 2) +
                               tlb[nbb] + trb[nbb];
             CK(cudaMemcpyAsync(c->ftl_base.p, tlb.data(), (size_t)(nbb + 1) * 8, cudaMemcpyHostToDevice, c->stream));

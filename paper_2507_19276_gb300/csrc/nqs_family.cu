@@ -152,8 +152,8 @@ __device__ __forceinline__ bool use_tc(const FamArgs<T>& f)
 // `mat`: y_r = M x_r with x_r = acc.src(r), y_r rescaled by a power of two and
 // written to acc.dst(r), acc.set_exp(r, e) receiving the exponent added (the
 // row's power of two plus the image's). Row sources and destinations come
-// from the accessor, so the per-sample kernels and the site-synchronous
-// kernel share the arithmetic (results per row do not depend on the batch).
+// from the accessor; results per row do not depend on the other rows of the
+// tile. The scaled rows leave through shared memory (see the epilogue).
 template <class Acc>
 __device__ void tc_apply(const FamArgs<float>& f, BatchSmem<float>& sm, const Acc& acc, int n, int mat)
 {
@@ -713,8 +713,10 @@ __global__ void __launch_bounds__(256) k_site_build(FamArgs<T> f, SiteBufs sb)
 }
 
 // Boundary vectors L_t (R_t) of each sample and side and the three families
-// that start at each site, on the CUDA cores in FP32 (the arithmetic of the
-// per-sample sweep): one block per (sample, side), steps in order.
+// that start at each site, on the CUDA cores (in the arithmetic type of the
+// tables; FP32 for the tensor-core form, whose split-FP16 products would put
+// their error into every vector built on the boundary): one block per
+// (sample, side), steps in order.
 template <typename T>
 __global__ void __launch_bounds__(256) k_site_boundary(FamArgs<T> f)
 {

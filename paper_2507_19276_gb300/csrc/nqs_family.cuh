@@ -62,7 +62,7 @@ template <typename T> int fam_launch_rows(const FamArgs<T>& f, const RowSet& row
 
 // ---- site-synchronous tables (tensor-core path) ----------------------------
 // The boundary vectors and the families at their first site are formed per
-// sample on the CUDA cores (FP32, as in the per-sample sweep); every other
+// sample on the CUDA cores (k_site_boundary); every other
 // vector update of the tables of a sample batch -- one-change families past
 // their first site, TL creation and propagation, TR rows -- is one item. The
 // items of site step tau fall into 8 groups (side x local state of the
