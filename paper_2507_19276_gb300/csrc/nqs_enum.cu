@@ -13,7 +13,7 @@
 namespace nqs {
 
 constexpr int kEnumWarps = 8;       // warps per block
-constexpr int kChunksPerWarp = 4;   // consecutive chunks per warp
+constexpr int kChunksPerWarp = 16;  // consecutive chunks per warp (amortises the block's list build)
 
 __global__ void __launch_bounds__(kEnumWarps * 32) k_enum(EnumArgs a)
 {
@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(kEnumWarps * 32) k_enum(EnumArgs a)
 // chunk's offset plus its rank among the chunk's set bits, so the lists stay
 // in canonical order.
 constexpr int kWriteChunks = 8;
+constexpr int kWriteGroups = 4;     // groups of kWriteChunks chunks per warp
 
 // position of the (k+1)-th set bit of m (k < popc(m)), by halving with popc
 __device__ __forceinline__ int nth_set_bit(uint32_t m, int k)
@@ -71,7 +72,7 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int k)
     return pos + (k >= (int)(m & 1u) ? 1 : 0);
 }
 
-__global__ void __launch_bounds__(kEnumWarps * 32) k_write_dets(EnumArgs a)
+__global__ void __launch_bounds__(kEnumWarps * 32, 4) k_write_dets(EnumArgs a)
 {
     __shared__ OrbLists lists;
     const int s = a.s0 + blockIdx.y;
@@ -81,52 +82,54 @@ __global__ void __launch_bounds__(kEnumWarps * 32) k_write_dets(EnumArgs a)
     __syncthreads();
     const HamView& h = a.h;
     const size_t srow = (size_t)s * a.n_chunks;
-    const uint32_t c0 = (blockIdx.x * kEnumWarps + warp) * kWriteChunks;
-    if (c0 >= a.n_chunks) return;
-    uint32_t m = 0, co = 0;
-    if (lane < kWriteChunks && c0 + lane < a.n_chunks) {
-        m = a.chunk_mask[srow + c0 + lane];
-        co = a.chunk_off[srow + c0 + lane];
-    }
-    const int cnt = __popc(m);
-    int incl = cnt;
-    for (int o = 1; o < kWriteChunks; o <<= 1) {
-        const int u = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += u;
-    }
-    int ex[kWriteChunks];
-    uint32_t mk[kWriteChunks], cof[kWriteChunks];
-    #pragma unroll
-    for (int k = 0; k < kWriteChunks; ++k) {
-        ex[k] = __shfl_sync(kFull, incl - cnt, k);
-        mk[k] = __shfl_sync(kFull, m, k);
-        cof[k] = __shfl_sync(kFull, co, k);
-    }
-    const int64_t base = a.det_off[s];
-    const int total = __shfl_sync(kFull, incl, kWriteChunks - 1);
-    for (int j = lane; j < total; j += 32) {
-        int k = 0, e0 = ex[0];                       // chunk of entry j, selected with
-        uint32_t bits = mk[0], off = cof[0];         // static indices (no local memory)
+    for (int grp = 0; grp < kWriteGroups; ++grp) {
+        const uint32_t c0 = ((blockIdx.x * kEnumWarps + warp) * kWriteGroups + grp) * kWriteChunks;
+        if (c0 >= a.n_chunks) break;
+        uint32_t m = 0, co = 0;
+        if (lane < kWriteChunks && c0 + lane < a.n_chunks) {
+            m = a.chunk_mask[srow + c0 + lane];
+            co = a.chunk_off[srow + c0 + lane];
+        }
+        const int cnt = __popc(m);
+        int incl = cnt;
+        for (int o = 1; o < kWriteChunks; o <<= 1) {
+            const int u = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += u;
+        }
+        int ex[kWriteChunks];
+        uint32_t mk[kWriteChunks], cof[kWriteChunks];
         #pragma unroll
-        for (int q = 1; q < kWriteChunks; ++q)
-            if (ex[q] <= j) { k = q; e0 = ex[q]; bits = mk[q]; off = cof[q]; }
-        const int idx = j - e0;                      // rank among the chunk's set bits
-        const uint32_t r = (c0 + k) * 32 + (uint32_t)nth_set_bit(bits, idx);
-        uint64_t ma, mb;
-        int odd;
-        const Exc e = decode_rank(h, lists, r);
-        const double H = matrix_element(h, na, nb, e, ma, mb, odd);
-        const int64_t pos = base + off + idx;
-        if (a.out_rank) a.out_rank[pos] = r;
-        if (a.out_H) a.out_H[pos] = H;
-        if (a.out_det) { a.out_det[2 * pos] = ma; a.out_det[2 * pos + 1] = mb; }
-        if (a.out_sign) a.out_sign[pos] = odd ? -1 : 1;
+        for (int k = 0; k < kWriteChunks; ++k) {
+            ex[k] = __shfl_sync(kFull, incl - cnt, k);
+            mk[k] = __shfl_sync(kFull, m, k);
+            cof[k] = __shfl_sync(kFull, co, k);
+        }
+        const int64_t base = a.det_off[s];
+        const int total = __shfl_sync(kFull, incl, kWriteChunks - 1);
+        for (int j = lane; j < total; j += 32) {
+            int k = 0, e0 = ex[0];                       // chunk of entry j, selected with
+            uint32_t bits = mk[0], off = cof[0];         // static indices (no local memory)
+            #pragma unroll
+            for (int q = 1; q < kWriteChunks; ++q)
+                if (ex[q] <= j) { k = q; e0 = ex[q]; bits = mk[q]; off = cof[q]; }
+            const int idx = j - e0;                      // rank among the chunk's set bits
+            const uint32_t r = (c0 + k) * 32 + (uint32_t)nth_set_bit(bits, idx);
+            uint64_t ma, mb;
+            int odd;
+            const Exc e = decode_rank(h, lists, r);
+            const double H = matrix_element(h, na, nb, e, ma, mb, odd);
+            const int64_t pos = base + off + idx;
+            if (a.out_rank) a.out_rank[pos] = r;
+            if (a.out_H) a.out_H[pos] = H;
+            if (a.out_det) { a.out_det[2 * pos] = ma; a.out_det[2 * pos + 1] = mb; }
+            if (a.out_sign) a.out_sign[pos] = odd ? -1 : 1;
+        }
     }
 }
 
 int launch_enum(const EnumArgs& args, int64_t Ns, bool write, cudaStream_t st)
 {
-    const uint32_t per_block = kEnumWarps * (write ? kWriteChunks : kChunksPerWarp);
+    const uint32_t per_block = kEnumWarps * (write ? kWriteChunks * kWriteGroups : kChunksPerWarp);
     const uint32_t gx = (args.n_chunks + per_block - 1) / per_block;
     if (gx == 0) return 0;
     int n = 0;
