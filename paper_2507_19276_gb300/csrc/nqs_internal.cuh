@@ -248,12 +248,6 @@ __device__ __forceinline__ int sigma_at(uint64_t wa, uint64_t wb, int p)
 }
 
 // Warp reductions.
-__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v)
-{
-    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-    return v;
-}
-
 // Exact warp sum of 64-bit values whose total stays below 2^64, on every
 // lane: three 24-bit slices summed by the warp-reduce unit (slice sums < 2^29).
 __device__ __forceinline__ uint64_t warp_sum_sliced(uint64_t v)
