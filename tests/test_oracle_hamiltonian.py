@@ -113,3 +113,40 @@ def test_canonical_order_blocks():
                     m = n.copy(); m[0] ^= np.uint64((1 << i) | (1 << a))
                     m[1] ^= np.uint64((1 << j) | (1 << b)); exp.append(m)
     assert np.array_equal(md, np.array(exp, np.uint64))
+
+
+def test_sixty_four_orbitals_use_the_top_bit():
+    """K = 64 fills the 64-bit occupation words: a determinant with orbital 63
+    occupied in both spins. Its connected list has n_conn entries that conserve
+    both electron counts, every element is Hermitian bitwise, and every sign
+    is the closed-form phase parity (Sec. 3 operator order)."""
+    from tests.test_identities import _closed_parity, _interleave
+    K, na, nb = 64, 2, 1
+    sys_ = W.tiny_system(K=K, na=na, nb=nb, seed=13, chol_rank=6, n_samples=4)
+    P = O.Problem(sys_)
+    n = np.array([(1 << 63) | (1 << 20), 1 << 63], np.uint64)
+    md, hv, sg = O.connected(P, n)
+    c2 = lambda x: x * (x - 1) // 2
+    assert len(md) == O.n_conn(K, na, nb) == (na * (K - na) + nb * (K - nb) + c2(na) * c2(K - na)
+                                              + c2(nb) * c2(K - nb) + na * (K - na) * nb * (K - nb))
+    pops = [bin(int(a)).count("1") for a in md[:, 0]], [bin(int(b)).count("1") for b in md[:, 1]]
+    assert set(pops[0]) == {na} and set(pops[1]) == {nb}
+    x = _interleave(n, K)
+    top = 0
+    for m, v, s in zip(md, hv, sg):
+        y = _interleave(m, K)
+        gone = [t for t in range(2 * K) if (x >> t & 1) and not (y >> t & 1)]
+        new = [t for t in range(2 * K) if (y >> t & 1) and not (x >> t & 1)]
+        top += (2 * 63) in gone or (2 * 63 + 1) in gone
+        if len(gone) == 1:
+            par = _closed_parity(x, gone[0], new[0])
+        else:
+            i, j = gone
+            a, b = new if ((i & 1) == (j & 1) or (new[0] & 1) == (i & 1)) else new[::-1]
+            par = _closed_parity(x, i, a, j, b)
+        assert (-1) ** par == int(s)
+    assert top > 0                       # excitations out of orbital 63 were enumerated
+    for m, v in zip(md[::97], hv[::97]):
+        back_d, back_h, _ = O.connected(P, m)
+        hit = np.nonzero((back_d[:, 0] == n[0]) & (back_d[:, 1] == n[1]))[0]
+        assert len(hit) == 1 and back_h[hit[0]] == v
