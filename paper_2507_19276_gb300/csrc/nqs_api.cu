@@ -1087,7 +1087,8 @@ extern "C" int nqs_draws(nqs_ctx* c, const uint64_t* samples, int64_t Ns, double
 namespace {
 
 // Per-sample error of the mixed form relative to max(|E_loc|, e_abs): the
-// bound the parity tests hold it to (measured up to ~2e-7 on the workloads).
+// bound the parity tests hold it to (measured 1.3e-7 to 2e-7 on the benchmark
+// workloads, up to 6.8e-7 at D = 256, where the FP32 accumulations are longest).
 constexpr double kMixedRelError = 1e-6;
 
 // The local-energy pipeline on device-resident samples in precision `prec`:
