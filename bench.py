@@ -53,20 +53,45 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-# FP64 FMA throughput of one GB300, measured with a dependent-chain-free DFMA
-# probe ("FP64 peak"); used as the ALU roofline of the FP64 form.
+# FP64 FMA throughput of one GB300, measured with an independent-chain DFMA
+# probe (1216 blocks x 256 threads x 8 chains); the ALU roofline of the FP64 form.
 FP64_PEAK_TFLOPS = 1.196
 
 
 # DRAM bytes (read + write) per evaluated amplitude of the amplitude stage,
 # summed over its kernels, from ncu counters on the H50 shape (D = 64) with
 # 512 samples; the stage's traffic grows in proportion to the amplitudes
-# evaluated. None until taken for the current kernels.
+# evaluated (None where not measured).
 STAGE_TRAFFIC_PER_AMP = {"mixed": 328.5, "fp64_shared": None}
 
 DTYPES = {"mixed": "f16x3 tensor-core products (f32 accumulate) + f32 gathers; f64 H, psi(n), "
                    "ratios, sums; heaviest samples re-evaluated in f64 to the energy tolerance",
           "fp64_shared": "f64", "fp64": "f64"}
+
+
+THROTTLE_REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+def summarize_clocks(lines):
+    """Median SM clock, the largest max clock and the throttle reasons seen in
+    nvidia-smi CSV lines (index, clocks.sm, clocks.max.sm, power.draw,
+    reasons.active, then the four reasons of THROTTLE_REASONS)."""
+    sm, mx, reasons = [], [], set()
+    for ln in lines:
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx.append(float(f[2]))
+        except ValueError:
+            continue
+        for n, v in zip(THROTTLE_REASONS, f[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(n)
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+            "samples": len(sm)}
 
 
 class ClockSampler:
@@ -105,23 +130,7 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.t.join(timeout=2)
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return summarize_clocks(self.lines)
 
 
 def dist_setup():

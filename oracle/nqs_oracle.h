@@ -8,7 +8,7 @@
  * tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg. It shares
  * no code, header, table or helper with the CUDA library.
  *
- * Conventions (the readings are listed in the design doc):
+ * Conventions (readings of the paper where it is silent or ambiguous):
  *  - K spatial orbitals, spin orbital s = 2p + spin (alpha=0, beta=1),
  *    the interleaved order of Sec. 3.
  *  - determinant = uint64 [alpha word, beta word]; bit p = orbital p.
