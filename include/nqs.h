@@ -214,9 +214,8 @@ int nqs_draws(nqs_ctx* ctx, const uint64_t* samples, int64_t Ns, double det_thre
 
 /* nqs_draws without any device allocation. The paper has no counterpart:
  * this is a service for callers that cannot allocate device memory while they
- * run -- work being recorded into a CUDA graph, latency-critical loops that
- * must not wait on an allocator, or applications that give all GPU memory to
- * their own pool beforehand.
+ * run -- latency-critical loops that must not wait on an allocator, or
+ * applications that give all GPU memory to their own pool beforehand.
  *  Same arguments and results as nqs_draws (bit-identical ranks and W), but
  *  samples, ranks and w_total must be device pointers; host pointers are
  *  rejected with NQS_ERR_INVALID_ARG because staging them would allocate.
@@ -224,11 +223,13 @@ int nqs_draws(nqs_ctx* ctx, const uint64_t* samples, int64_t Ns, double det_thre
  *  library image, present on every GPU that loads the library until the
  *  process exits. A batch needs 8 * (2 + Ns + 1.5 Ns ceil(n_conn / 32))
  *  bytes of it; larger batches return NQS_ERR_INVALID_ARG (split them).
- *  The first call on a device looks up the array's device address (with
- *  cudaGetSymbolAddress); make that first call before any stream capture.
+ *  The first call on each context looks up the array's device address on
+ *  the context's device (with cudaGetSymbolAddress); make that first call
+ *  before any stream capture on that device.
  *  All calls share the one array: calls that overlap on the GPU (other
  *  streams, other contexts on the same device) race and corrupt each other.
- *  Synchronises the context's stream before returning. */
+ *  Reads the device error word back and synchronises the context's stream
+ *  before returning. */
 #define NQS_NOALLOC_SCRATCH_BYTES (8 << 20)
 int nqs_draws_noalloc(nqs_ctx* ctx, const uint64_t* samples, int64_t Ns, double det_threshold,
                       int n_draws, uint64_t philox_seed, int64_t* ranks, uint64_t* w_total);

@@ -71,6 +71,7 @@ struct nqs_ctx {
         ref_e;
     double stage_ms[NQS_N_STAGES] = {0};
     int64_t stage_launch[NQS_N_STAGES] = {0};
+    unsigned long long* noalloc_addr = nullptr;   // device address of the fixed draw scratch
     struct Pending { int stage; cudaEvent_t a, b; };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> free_events;
@@ -1377,8 +1378,7 @@ extern "C" int nqs_grad_log_psi_vjp(nqs_ctx* c, const uint64_t* samples, const d
 // ============================================================================
 // Allocation-free variant of nqs_draws
 //
-// Some callers must not allocate device memory during a call: code that is
-// being recorded into a CUDA graph (a cudaMalloc there breaks the capture),
+// Some callers must not allocate device memory during a call:
 // latency-critical loops where an allocation can stall on a device-wide
 // synchronisation, and hosts that hand the whole GPU memory to their own pool
 // up front. For them this entry point computes the same draws as nqs_draws
@@ -1394,9 +1394,6 @@ constexpr size_t kNoAllocWords = (size_t)NQS_NOALLOC_SCRATCH_BYTES / 8;
 // Scratch shared by every call of nqs_draws_noalloc on a device. It keeps the
 // previous call's contents; each call clears what has to start at zero.
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocWords];
-
-// Device addresses of the scratch, resolved once per device.
-unsigned long long* g_noalloc_addr[256] = {nullptr};
 
 }  // namespace
 
@@ -1426,14 +1423,15 @@ extern "C" int nqs_draws_noalloc(nqs_ctx* c, const uint64_t* samples, int64_t Ns
                        "the fixed scratch holds %llu (%d bytes); split the batch",
                        (long long)Ns, (unsigned long long)nch, (unsigned long long)need,
                        (unsigned long long)kNoAllocWords, (int)NQS_NOALLOC_SCRATCH_BYTES);
-    if (c->device < 0 || c->device >= 256)
-        return set_err(c, NQS_ERR_UNSUPPORTED, "device index %d out of range", c->device);
-    if (!g_noalloc_addr[c->device]) {
+    // the array's device address on this context's device (current since the
+    // cudaSetDevice above), looked up on the context's first call; contexts are
+    // used by one host thread at a time, so the lookup needs no lock
+    if (!c->noalloc_addr) {
         void* p = nullptr;
         CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_noalloc_addr[c->device] = (unsigned long long*)p;
+        c->noalloc_addr = (unsigned long long*)p;
     }
-    unsigned long long* base = g_noalloc_addr[c->device];
+    unsigned long long* base = c->noalloc_addr;
     DevError* derr = (DevError*)base;
     uint64_t* W = (uint64_t*)(base + 2);
     uint64_t* chunk_w = W + Ns;

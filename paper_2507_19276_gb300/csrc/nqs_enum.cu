@@ -21,7 +21,8 @@ __global__ void __launch_bounds__(kEnumWarps * 32) k_enum(EnumArgs a)
     const int s = a.s0 + blockIdx.y;
     const uint64_t na = a.samples[2 * s], nb = a.samples[2 * s + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp == 0) build_lists_warp(na, nb, a.h.K, lists, lane);
+    const bool ok = sample_ok(a.h, na, nb);   // else: empty chunks, nothing decoded
+    if (warp == 0 && ok) build_lists_warp(na, nb, a.h.K, lists, lane);
     __syncthreads();
     const HamView& h = a.h;
     const size_t srow = (size_t)s * a.n_chunks;
@@ -29,7 +30,7 @@ __global__ void __launch_bounds__(kEnumWarps * 32) k_enum(EnumArgs a)
         const uint32_t c = (blockIdx.x * kEnumWarps + warp) * kChunksPerWarp + k;
         if (c >= a.n_chunks) break;
         const uint32_t r = c * 32 + lane;
-        const bool valid = r < h.n_conn;
+        const bool valid = ok && r < h.n_conn;
         double H = 0.0;
         if (valid) {
             uint64_t ma, mb;
@@ -77,6 +78,7 @@ __global__ void __launch_bounds__(kEnumWarps * 32, 4) k_write_dets(EnumArgs a)
     __shared__ OrbLists lists;
     const int s = a.s0 + blockIdx.y;
     const uint64_t na = a.samples[2 * s], nb = a.samples[2 * s + 1];
+    if (!sample_ok(a.h, na, nb)) return;     // block-uniform: no list to write
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0) build_lists_warp(na, nb, a.h.K, lists, lane);
     __syncthreads();
@@ -157,11 +159,11 @@ __global__ void __launch_bounds__(256) k_draws(DrawArgs a)
     const int d = (int)(g - s * a.n_draws);
     const size_t srow = (size_t)s * a.n_chunks;
     const uint64_t W = a.n_chunks ? a.chunk_pre[srow + a.n_chunks - 1] : 0ull;
-    if (W == 0) {
+    const uint64_t na = a.samples[2 * s], nb = a.samples[2 * s + 1];
+    if (W == 0 || !sample_ok(a.h, na, nb)) {
         if (lane == 0) a.out_rank[g] = -1;
         return;
     }
-    const uint64_t na = a.samples[2 * s], nb = a.samples[2 * s + 1];
     build_lists_warp(na, nb, a.h.K, lists[warp], lane);
     __syncwarp();
     // target t = floor(x W / 2^64), then the first chunk whose inclusive prefix > t
@@ -226,6 +228,10 @@ __global__ void __launch_bounds__(1024) k_dedup(DedupArgs a)
     const int s = blockIdx.x;
     const int P = a.pow2;
     const int64_t base = (int64_t)s * a.n_draws;
+    if (!sample_ok(a.h, a.samples[2 * s], a.samples[2 * s + 1])) {   // block-uniform
+        if (threadIdx.x == 0) a.n_unique[s] = 0;
+        return;
+    }
     for (int i = threadIdx.x; i < P; i += blockDim.x)
         keys[i] = i < a.n_draws && a.ranks[base + i] >= 0 && a.ranks[base + i] < (int64_t)a.h.n_conn
                       ? (uint32_t)a.ranks[base + i] : 0xffffffffu;

@@ -102,6 +102,17 @@ __device__ __forceinline__ void build_lists_warp(uint64_t wa, uint64_t wb, int K
     }
 }
 
+// A sample the enumeration may decode: N_alpha and N_beta electrons and no
+// occupied orbital at or above K. Kernels that run before the host has read
+// the validation error word skip other samples, so the orbital lists they
+// decode from are always fully written (their results are discarded with
+// the call's NQS_ERR_INVALID_ARG).
+__device__ __forceinline__ bool sample_ok(const HamView& h, uint64_t na, uint64_t nb)
+{
+    const uint64_t outside = h.K >= 64 ? 0ull : ~((1ull << h.K) - 1ull);
+    return !((na | nb) & outside) && __popcll(na) == h.na && __popcll(nb) == h.nb;
+}
+
 // The operators of a double act on n in the order a_i, a_j, a+_b, a+_a; each
 // picks up the occupied spin orbitals below it in the determinant it meets,
 // which differs from n by the operators already applied:

@@ -91,3 +91,38 @@ def test_batch_rejects_a_context_shared_by_two_systems(setup):
     systems, ctxs, _ = setup
     with pytest.raises(nqs.NQSError):
         nqs.local_energy_batch([ctxs[0], ctxs[0]], [_args(systems[0])] * 2)
+
+
+def test_full_batch_every_system_at_full_size():
+    """All 64 systems of the uneven batch at their full sample counts (the
+    benchmark's launch configuration): every system equals its own
+    nqs_local_energy call bit for bit, and two sampled positions per system
+    (one drawn at random, the last) match the oracle at their batch positions."""
+    systems = W.uneven_batch()
+    streams = [torch.cuda.Stream() for _ in systems]
+    ctxs = []
+    try:
+        for s, st in zip(systems, streams):
+            c = nqs.Context(0, stream=st.cuda_stream)
+            c.set_system(s)
+            c.set_precision(nqs.NQS_PREC_MIXED)
+            ctxs.append(c)
+        got = nqs.local_energy_batch(ctxs, [_args(s) for s in systems], n_workers=8)
+        rng = np.random.default_rng(64)
+        picks, worst = [], 0.0
+        for s, c, (e, summ) in zip(systems, ctxs, got):
+            ref, rs = c.local_energy(s.samples, s.counts, s.eps, s.n_draws, s.seed)
+            assert np.array_equal(e.view(np.uint64), ref.view(np.uint64)), s.name
+            assert summ["e_mean"] == rs["e_mean"] and summ["n_det"] == rs["n_det"]
+            picks.append(([int(rng.integers(len(s.samples) - 1)), len(s.samples) - 1], e))
+        for s, (idx, e) in zip(systems, picks):
+            o = O.local_energy(O.Problem(s), samples=s.samples[idx], index=idx,
+                               threads=os.cpu_count() or 1)
+            err = np.max(np.abs(e[idx] - o["e_loc"]) / np.maximum(np.abs(o["e_loc"]), o["e_abs"]))
+            worst = max(worst, err)
+            assert err < RTOL_MIXED, (s.name, err)
+        print(f"64 systems, {sum(len(s.samples) for s in systems)} samples: "
+              f"max mixed error / max(|E|, e_abs) at the sampled positions = {worst:.3e}")
+    finally:
+        for c in ctxs:
+            c.close()

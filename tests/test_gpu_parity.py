@@ -176,6 +176,9 @@ def test_local_energy_fp64_matches_oracle(ctx, cases, problems, name):
     _load(ctx, sys_)
     e, summ = ctx.local_energy(sys_.samples, sys_.counts, sys_.eps, sys_.n_draws, sys_.seed)
     ref = O.local_energy(P, cond=True)
+    # reported next to the bar: the plain relative error and the bar's scaled one
+    print(f"{name}: FP64 max |dE|/|E| = {_rel(e, ref['e_loc']):.3e}, "
+          f"scaled (R15) = {_rel_sum(e, ref):.3e}")
     assert _rel_sum(e, ref) < RTOL_FP64
     c = sys_.counts
     # the weighted energy: against the library's own E_loc to summation
@@ -340,6 +343,59 @@ def test_bond_dimensions_of_the_tensor_core_path(ctx, D):
                 print(f"D={D}: mixed max error / max(|E|, e_abs) = {err:.3e}")
                 assert err < RTOL_MIXED
             else:
+                assert _rel_sum(e, ref) < RTOL_FP64
+    finally:
+        ctx.set_precision(nqs.NQS_PREC_FP64)
+
+
+# ---------------------------------------------------------------------------
+# 64 orbitals: both occupation words full width, orbital 63 occupied
+# ---------------------------------------------------------------------------
+
+def _k64_system(D):
+    """K = 64 (Sec. 3: interleaved order on two 64-bit words), 2 alpha + 1 beta
+    electrons; the first samples occupy orbital 63 in one or both spins."""
+    sys_ = W.tiny_system(K=64, na=2, nb=1, D=D, n_hidden=5, seed=13, chol_rank=6, n_samples=5,
+                         eps=2e-3, n_draws=96)
+    top = np.array([[(1 << 63) | (1 << 20), 1 << 63],
+                    [(1 << 63) | (1 << 62), 1],
+                    [3, 1 << 63]], np.uint64)
+    keep = [i for i, d in enumerate(sys_.samples) if not any((d == t).all() for t in top)]
+    samples = np.ascontiguousarray(np.concatenate([top, sys_.samples[keep]]))
+    counts = np.concatenate([np.array([1.0, 2.0, 0.5]), sys_.counts[keep]])
+    import dataclasses
+    return dataclasses.replace(sys_, samples=samples, counts=counts)
+
+
+def test_sixty_four_orbitals_lists_draws_and_energies(ctx):
+    sys_ = _k64_system(D=16)
+    P = O.Problem(sys_)
+    try:
+        _load(ctx, sys_)
+        for eps in (0.0, 2e-3):
+            off, rank, dets, H, sg = ctx.connected(sys_.samples, eps)
+            for s, n in enumerate(sys_.samples):
+                od, oh, os_ = O.connected(P, n)
+                keep = np.nonzero(np.abs(oh) >= eps)[0]
+                a, b = off[s], off[s + 1]
+                assert b - a == len(keep)
+                assert np.array_equal(rank[a:b], keep.astype(np.uint32))
+                assert np.array_equal(dets[a:b], od[keep])
+                assert np.array_equal(H[a:b].view(np.uint64), oh[keep].view(np.uint64))
+                assert np.array_equal(sg[a:b], os_[keep])
+        ranks, wt = ctx.draws(sys_.samples, sys_.eps, sys_.n_draws, sys_.seed)
+        for s, n in enumerate(sys_.samples):
+            ref, Wref, _ = O.draws(P, n, s, sys_.eps, sys_.n_draws, sys_.seed)
+            assert int(wt[s]) == Wref and np.array_equal(ranks[s], ref)
+        ref = O.local_energy(P, cond=True)
+        for prec in (nqs.NQS_PREC_FP64, nqs.NQS_PREC_FP64_SHARED, nqs.NQS_PREC_MIXED):
+            _load(ctx, sys_, prec)
+            e, summ = ctx.local_energy(sys_.samples, sys_.counts, sys_.eps, sys_.n_draws, sys_.seed)
+            assert summ["n_det"] == int(np.sum(ref["n_det"]))
+            if prec == nqs.NQS_PREC_MIXED:
+                assert _rel_abs(e, ref) < RTOL_MIXED
+            else:
+                print(f"K=64 precision {prec}: FP64 max |dE|/|E| = {_rel(e, ref['e_loc']):.3e}")
                 assert _rel_sum(e, ref) < RTOL_FP64
     finally:
         ctx.set_precision(nqs.NQS_PREC_FP64)

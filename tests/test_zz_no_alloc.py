@@ -1,7 +1,7 @@
 """The allocation-free draws entry point (nqs_draws_noalloc) against nqs_draws.
 
 nqs_draws_noalloc exists for callers that may not allocate device memory
-while they run (work recorded into a CUDA graph, latency-critical loops,
+while they run (latency-critical loops that must not wait on an allocator,
 applications that give all GPU memory to their own pool). It works in a fixed
 scratch array inside the library instead of allocating. Its draws must be the
 same as those of nqs_draws: the drawn indices and W are integers, so the
@@ -45,6 +45,40 @@ def test_noalloc_draws_equal_nqs_draws_on_two_calls_in_a_row():
             got_r, got_w = _noalloc(ctx, sys_.samples, eps, nd, seed)
             assert np.array_equal(got_r, ref_r)
             assert np.array_equal(got_w, ref_w)
+    finally:
+        ctx.close()
+
+
+def test_noalloc_larger_then_smaller_batch_and_optional_outputs():
+    """A batch of 30 H50 samples (most of the scratch), then a K = 64 batch
+    with fewer samples but more rank chunks per sample, so the second call's
+    regions overlap what the first left behind; then W alone (n_draws = 0) and
+    ranks alone (w_total = None)."""
+    ctx = nqs.Context(0)
+    try:
+        big = W.h50_chain().subset(range(30))
+        ctx.set_system(big)
+        ref_r, ref_w = ctx.draws(big.samples, 1e-3, 64, 11)
+        got_r, got_w = _noalloc(ctx, big.samples, 1e-3, 64, 11)
+        assert np.array_equal(got_r, ref_r) and np.array_equal(got_w, ref_w)
+
+        wide = W.h50_chain(n_samples=3, K=64, D=16, n_hidden=0)
+        ctx.set_system(wide)
+        ref_r, ref_w = ctx.draws(wide.samples, 2e-3, 200, 5)
+        got_r, got_w = _noalloc(ctx, wide.samples, 2e-3, 200, 5)
+        assert np.array_equal(got_r, ref_r) and np.array_equal(got_w, ref_w)
+
+        # W only
+        s_dev = torch.from_numpy(wide.samples.view(np.int64)).cuda()
+        w_dev = torch.full((3,), -7, dtype=torch.int64, device="cuda")
+        nqs.nqs_draws_noalloc(ctx.h, s_dev, 3, 2e-3, 0, 5, None, w_dev)
+        torch.cuda.synchronize()
+        assert np.array_equal(w_dev.cpu().numpy().view(np.uint64), ref_w)
+        # ranks only
+        r_dev = torch.full((3, 200), -7, dtype=torch.int64, device="cuda")
+        nqs.nqs_draws_noalloc(ctx.h, s_dev, 3, 2e-3, 200, 5, r_dev, None)
+        torch.cuda.synchronize()
+        assert np.array_equal(r_dev.cpu().numpy(), ref_r)
     finally:
         ctx.close()
 
