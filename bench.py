@@ -53,9 +53,40 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-# FP64 FMA throughput of one GB300, measured with an independent-chain DFMA
-# probe (1216 blocks x 256 threads x 8 chains); the ALU roofline of the FP64 form.
-FP64_PEAK_TFLOPS = 1.196
+def measured_ceilings(device, args):
+    """L2 read and gather rates and CUDA-core FMA rates, measured on this GPU
+    before the timed region (paper_2507_19276_gb300/peaks): the denominators of
+    the enumeration and FP64 rooflines, which MEASURED_PEAKS.json does not hold."""
+    if getattr(args, "no_peaks", False):
+        return None
+    from paper_2507_19276_gb300.peaks import probe
+    return probe.measure(device)
+
+
+def with_overrides(sys_, args):
+    """The workload with the command line's eps / N_eps / uniform counts."""
+    import dataclasses
+    ch = {}
+    if getattr(args, "eps", None) is not None:
+        ch["eps"] = args.eps
+    if getattr(args, "draws", None) is not None:
+        ch["n_draws"] = args.draws
+    if getattr(args, "uniform_counts", False):
+        ch["counts"] = np.ones(len(sys_.samples))
+    return dataclasses.replace(sys_, **ch) if ch else sys_
+
+
+def enum_bytes(K, na, nb, n_samples, n_det):
+    """Algorithmic bytes of the enumeration stage (Slater-Condon elements of
+    every connected determinant, the eps split, the deterministic lists): per
+    element the integral reads of its rule -- 8 B for a single (one Fock
+    element per sample), 16 B for a same-spin double ((ai|bj) and (aj|bi)),
+    8 B for an alpha-beta double -- and 12 B (rank + H) per listed entry."""
+    c2 = lambda x: x * (x - 1) // 2
+    singles = na * (K - na) + nb * (K - nb)
+    same = c2(na) * c2(K - na) + c2(nb) * c2(K - nb)
+    ab = na * (K - na) * nb * (K - nb)
+    return n_samples * (8.0 * singles + 16.0 * same + 8.0 * ab) + 12.0 * n_det
 
 
 # DRAM bytes (read + write) per evaluated amplitude of the amplitude stage,
@@ -199,7 +230,7 @@ def run_reference(args):
             return sum(cpu_oracle_rate(s, len(s.samples), cores)[1] for s in systems)
     else:
         gen, n_def, _, metric = WORKLOADS[args.workload]
-        sys_ = gen(args.samples or n_def, 0)
+        sys_ = with_overrides(gen(args.samples or n_def, 0), args)
         per_step = min(len(sys_.samples), max(2, cores))
 
         def one_step():
@@ -228,12 +259,13 @@ def run(args):
     ws, rank, local = dist_setup()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    live = measured_ceilings(local, args)
     # weak scaling: one batch of args.samples unique samples per GPU, split
     # contiguously; each shard's draws are keyed by global sample position
     gen, n_def, _, metric = WORKLOADS[args.workload]
     total = (args.samples or n_def) * ws
     lo, hi = shard.shard_range(total, ws, rank)
-    sys_ = gen(total, 0).subset(range(lo, hi))
+    sys_ = with_overrides(gen(total, 0), args).subset(range(lo, hi))
     Ns = len(sys_.samples)
     ctx = nqs.Context(local)
     ctx.set_system(sys_)
@@ -321,11 +353,33 @@ def run(args):
                 "kernel": "amplitude stage: k_fam_mark, k_fam_compact, k_site_boundary, "
                           "k_site_build, k_site_tiles_pipe (tcgen05), k_fam_rbm, k_fam_rows"}
     else:
-        roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "peak_source": "FP64 FMA probe, measured",
+        roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved,
+                "peak": live["fma64_tflops"] if live else 1.196,
+                "peak_source": ("FP64 FMA rate measured before the timed region (peaks probe)" if live
+                                else "FP64 FMA rate of an earlier probe run on this pool's GB300"),
                 "kernel": ("amplitude stage (shared prefixes, FP64)" if prec == nqs.NQS_PREC_FP64_SHARED
                            else "k_amp_chain_fp64 / k_amp_graph_fp64 (one amplitude per row)")}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    # the same stage against the work the shared-prefix form executes
+    roof["executed_frac"] = executed / (amp_ms / 1e3) / 1e12 / roof["peak"]
+    # enumeration stage (count pass, write pass, draws): algorithmic integral
+    # bytes against the measured L2 rates (the integral table is L2-resident)
+    enum_ms = sum(stages[k][0] for k in ("count", "write", "draw")) / args.steps
+    eb = enum_bytes(sys_.K, sys_.n_alpha, sys_.n_beta, Ns, work["n_det"])
+    roof_enum = None
+    if live and enum_ms > 0:
+        eri_mb = 8 * sys_.K ** 4 / 2 ** 20
+        l2 = max(live["l2_read_gbs"].values())
+        g8 = live["gather8_gbs"]["64" if eri_mb > 32 else "32"]
+        ach = eb / (enum_ms / 1e3) / 1e9
+        roof_enum = {"bound": "l2", "unit": "GB/s", "achieved": ach, "peak": l2, "frac": ach / l2,
+                     "peak_source": "L2 streaming read rate measured before the timed region "
+                                    "(peaks probe, best over 16..96 MB)",
+                     "gather8_peak": g8, "frac_of_gather8": ach / g8,
+                     "hbm_peak": peaks["hbm_gbs"], "frac_of_hbm": ach / peaks["hbm_gbs"],
+                     "traffic": None, "algorithmic_bytes_per_step": eb, "stage_ms_per_step": enum_ms,
+                     "kernel": "enumeration stage: k_enum (count), k_write_dets, k_draws, k_dedup",
+                     "eri_mb": eri_mb}
     key = args.precision if args.workload == "h50" else None
     roof["traffic"] = STAGE_TRAFFIC_PER_AMP.get(key, None)
     if roof["traffic"] is not None:
@@ -348,11 +402,25 @@ def run(args):
         torch.cuda.synchronize()
         ms64 = start.elapsed_time(stop)
         d = (e_loc - e_mixed).abs()
+        e64 = s64.as_dict()["e_mean"]
+        # the mixed form without the FP64 re-evaluation: its energy error and time
+        ctx.set_precision(nqs.NQS_PREC_MIXED, timing=False, sample_index_base=lo, energy_tolerance=0.0)
+        s0 = nqs.EnergySummary()
+        step(s0)
+        torch.cuda.synchronize()
+        start.record(stream)
+        step(s0)
+        stop.record(stream)
+        torch.cuda.synchronize()
+        ms0 = start.elapsed_time(stop)
         fp64 = {"precision": "fp64_shared", "value": total / (ms64 / 1e3), "unit": UNIT,
                 "ms_per_step": ms64,
-                "e_mean_diff_ha": abs(s64.as_dict()["e_mean"] - work["e_mean"]),
+                "e_mean_diff_ha": abs(e64 - work["e_mean"]),
+                "e_mean_diff_unrefined_ha": abs(e64 - s0.as_dict()["e_mean"]),
+                "mixed_unrefined_ms_per_step": ms0,
                 "max_abs_diff_ha": float(d.max().item()),
-                "median_abs_diff_ha": float(d.median().item())}
+                "median_abs_diff_ha": float(d.median().item()),
+                "max_rel_diff": float((d / e_loc.abs().clamp_min(1e-300)).max().item())}
 
     line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -363,6 +431,8 @@ def run(args):
             "amplitudes_per_s": ws * n_amp * args.steps / (ms / 1e3),
             "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
             "roofline": roof,
+            "roofline_enum": roof_enum,
+            "measured_ceilings": live,
             "fp64_gpu": fp64,
             "e2e": {"value": total * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": Ns * 16 + Ns * 8, "d2h_bytes_per_step": Ns * 8},
@@ -524,7 +594,21 @@ def main():
     ap.add_argument("--energy-tol", type=float, default=1e-6,
                     help="mixed form: bound (Ha) on the weighted-energy error, met by "
                          "re-evaluating the heaviest samples in FP64 (0: none)")
+    ap.add_argument("--eps", type=float, default=None,
+                    help="deterministic threshold (default: the workload's; the paper's runs use 0.01)")
+    ap.add_argument("--draws", type=int, default=None,
+                    help="stochastic draws per sample (default: the workload's; the paper's runs use 100)")
+    ap.add_argument("--uniform-counts", action="store_true",
+                    help="every sample count 1 instead of the workload's Zipf counts")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip the L2 / FMA ceilings measured before the timed region")
+    ap.add_argument("--peaks", action="store_true",
+                    help="print the measured ceilings (L2 read, random gathers, FMA) and exit")
     args = ap.parse_args()
+    if args.peaks:
+        from paper_2507_19276_gb300.peaks import probe
+        print(json.dumps(probe.measure(0)), flush=True)
+        return
     if args.precision is None:
         args.precision = "mixed" if args.workload == "uneven" else WORKLOADS[args.workload][2]
     if args.impl == "reference":

@@ -69,7 +69,27 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    build_peaks(force)
     return LIB
+
+
+PEAKS_SRC = os.path.join(HERE, "peaks", "peaks.cu")
+PEAKS_LIB = os.path.join(BUILD, "libnqs_peaks.so")
+
+
+def build_peaks(force: bool = False) -> str:
+    """The measurement probes (L2 read and gather rates, FMA rates) the bench
+    reports its rooflines against: a separate small library."""
+    os.makedirs(BUILD, exist_ok=True)
+    if not force and not _stale(PEAKS_LIB, [PEAKS_SRC]):
+        return PEAKS_LIB
+    tmp = PEAKS_LIB + f".{os.getpid()}.tmp"
+    cmd = [nvcc()] + _flags() + ["-shared", PEAKS_SRC, "-o", tmp, "-lcudart"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on {PEAKS_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PEAKS_LIB)
+    return PEAKS_LIB
 
 
 if __name__ == "__main__":
