@@ -303,20 +303,125 @@ static double log2cosh(double x)
     return ax + log1p(exp(-2.0 * ax));
 }
 
-static double rbm_log_f(const or_ansatz* a, const uint64_t* det)
+/* theta_k(n) of the correlator (Sec. 2.3): b_k + sum_s W[k][s] n_s, plus
+ * 1/2 sum_{s,t} W2[k][s][t] n_s n_t for the Ising-RBM. */
+static double corr_theta(const or_ansatz* a, const int* occ, int k)
 {
+    const int N = 2 * a->K;
+    double th = a->rbm_b[k];
+    for (int s = 0; s < N; ++s)
+        if (occ[s]) th += a->rbm_W[(size_t)k * N + s];
+    if (a->corr == 2) {
+        double q = 0.0;
+        for (int s = 0; s < N; ++s)
+            for (int t = 0; t < N; ++t)
+                if (occ[s] && occ[t]) q += a->rbm_W2[((size_t)k * N + s) * N + t];
+        th += 0.5 * q;
+    }
+    return th;
+}
+
+/* log|f(n)| and the sign of f (Eq. RBM, cos-RBM and Ising-RBM of Sec. 2.3). */
+static double rbm_log_f(const or_ansatz* a, const uint64_t* det, int* sign_f)
+{
+    *sign_f = 1;
     if (a->n_hidden <= 0) return 0.0;
     const int K = a->K;
     int occ[128];
     unpack(K, det, occ);
     double lf = 0.0;
     for (int k = 0; k < a->n_hidden; ++k) {
-        double th = a->rbm_b[k];
-        for (int s = 0; s < 2 * K; ++s)
-            if (occ[s]) th += a->rbm_W[(size_t)k * 2 * K + s];
-        lf += log2cosh(th);
+        const double th = corr_theta(a, occ, k);
+        if (a->corr == 0) {
+            lf += log2cosh(th);
+        } else {
+            const double c = cos(th);
+            if (c < 0.0) *sign_f = -*sign_f;
+            lf += log(fabs(c));
+        }
     }
+    if (isinf(lf) && lf < 0) *sign_f = 0;
     return lf;
+}
+
+/* Local state s = n_alpha + 2 n_beta at vertex i is allowed when, after it,
+ * neither spin exceeds its electron count and the vertices after i can still
+ * hold the electrons left (the N_alpha / N_beta constraint of Sec. 3). */
+static int state_allowed(const or_ansatz* a, int i, int na_done, int nb_done, int s)
+{
+    if (a->n_alpha < 0) return 1;        /* no particle-number constraint */
+    const int ea = na_done + (s & 1), eb = nb_done + (s >> 1), left = a->K - 1 - i;
+    return ea <= a->n_alpha && eb <= a->n_beta && a->n_alpha - ea <= left && a->n_beta - eb <= left;
+}
+
+/* Candidate cells cand[s][r] = v_i^s[r] + sum_{e=(j->i)} sum_c M_e^s[r][c] h_j[c]
+ * for the four local states of vertex i, and P_i(s) = sum_r eta_i[r] cand[s][r]^2
+ * (Eq. MPS-RNN-1D / bdg-rnn-update without the tensor term, Sec. 2.2). */
+static void rnn_candidates(const or_ansatz* a, int i, const double* hs, double* cand, double* P)
+{
+    const int D = a->D;
+    int e0, e1;
+    edges_of(a, i, &e0, &e1);
+    for (int s = 0; s < 4; ++s) {
+        double* h = cand + (size_t)s * D;
+        for (int r = 0; r < D; ++r) {
+            double acc = a->rnn_v[((size_t)i * 4 + s) * D + r];
+            for (int e = e0; e < e1; ++e) {
+                const int j = edge_src(a, e);
+                const double* M = tensor(a, e, s);
+                for (int c = 0; c < D; ++c) {
+                    const double hj = (j < 0) ? (c == 0 ? 1.0 : 0.0) : hs[(size_t)j * D + c];
+                    acc += M[r * D + c] * hj;
+                }
+            }
+            h[r] = acc;
+        }
+        double p = 0.0;
+        for (int r = 0; r < D; ++r) p += a->rnn_eta[(size_t)i * D + r] * h[r] * h[r];
+        P[s] = p;
+    }
+}
+
+/* log|Phi(n)| of the normalised readout; the chosen cells go to hs [K][D],
+ * the conditionals P~_i(s) to probs [K][4] (may be NULL). */
+static double rnn_log_phi(const or_ansatz* a, const int* sigma, double* hs, int* sign, double* probs)
+{
+    const int K = a->K, D = a->D;
+    double* cand = (double*)malloc(sizeof(double) * 4 * D);
+    double lp = 0.0;
+    int sg = 1, na_done = 0, nb_done = 0;
+    for (int i = 0; i < K; ++i) {
+        double P[4], Z = 0.0;
+        rnn_candidates(a, i, hs, cand, P);
+        for (int s = 0; s < 4; ++s)
+            if (state_allowed(a, i, na_done, nb_done, s)) Z += P[s];
+        if (probs)
+            for (int s = 0; s < 4; ++s)
+                probs[i * 4 + s] = state_allowed(a, i, na_done, nb_done, s) && Z > 0.0 ? P[s] / Z : 0.0;
+        const int s = sigma[i];
+        if (!state_allowed(a, i, na_done, nb_done, s) || P[s] == 0.0 || Z == 0.0) { sg = 0; lp = -INFINITY; }
+        if (sg != 0) {
+            lp += 0.5 * (log(P[s]) - log(Z));
+            double ph = a->rnn_c[i];
+            for (int r = 0; r < D; ++r) ph += a->rnn_w[(size_t)i * D + r] * cand[(size_t)s * D + r];
+            if (ph < 0.0) sg = -sg;
+        }
+        for (int r = 0; r < D; ++r) hs[(size_t)i * D + r] = cand[(size_t)s * D + r];
+        na_done += s & 1;
+        nb_done += s >> 1;
+    }
+    free(cand);
+    *sign = sg;
+    return lp;
+}
+
+void or_rnn_conditionals(const or_ansatz* a, const uint64_t* det, double* probs)
+{
+    int sigma[64], sg;
+    sigma_of(a->K, det, sigma);
+    double* hs = (double*)malloc(sizeof(double) * (size_t)a->K * a->D);
+    rnn_log_phi(a, sigma, hs, &sg, probs);
+    free(hs);
 }
 
 void or_log_psi(const or_ansatz* a, const uint64_t* det, double* log_abs, int* sign,
@@ -326,17 +431,101 @@ void or_log_psi(const or_ansatz* a, const uint64_t* det, double* log_abs, int* s
     int sigma[64];
     sigma_of(K, det, sigma);
     double* hs = (double*)malloc(sizeof(double) * (size_t)K * D);
-    int* ex = (int*)malloc(sizeof(int) * K);
-    forward_states(a, sigma, hs, ex);
-    double mant = hs[(size_t)(K - 1) * D + 0];
-    int e = ex[K - 1];
+    double la_tn;
+    int sg_tn;
+    if (a->readout == 1) {
+        la_tn = rnn_log_phi(a, sigma, hs, &sg_tn, NULL);
+    } else {
+        int* ex = (int*)malloc(sizeof(int) * K);
+        forward_states(a, sigma, hs, ex);
+        const double mant = hs[(size_t)(K - 1) * D + 0];
+        sg_tn = mant == 0.0 ? 0 : (mant < 0 ? -1 : 1);
+        la_tn = mant == 0.0 ? -INFINITY : log(fabs(mant)) + (double)ex[K - 1] * M_LN2;
+        free(ex);
+    }
     free(hs);
-    free(ex);
-    double lf = rbm_log_f(a, det);
+    int sg_f;
+    double lf = rbm_log_f(a, det, &sg_f);
     if (log_f) *log_f = lf;
-    if (mant == 0.0) { *sign = 0; *log_abs = -INFINITY; return; }
-    *sign = mant < 0 ? -1 : 1;
-    *log_abs = log(fabs(mant)) + (double)e * M_LN2 + lf;
+    if (sg_tn == 0 || sg_f == 0) { *sign = 0; *log_abs = -INFINITY; return; }
+    *sign = sg_tn * sg_f;
+    *log_abs = la_tn + lf;
+}
+
+int64_t or_sample(const or_ansatz* a, int64_t n_samples, uint64_t seed, uint64_t* dets,
+                  double* counts, int64_t capacity)
+{
+    const int K = a->K, D = a->D;
+    if (n_samples <= 0) return 0;
+    /* nodes of the current level: prefix words, offset, count, cells [K][D] */
+    int64_t n = 1, cap = 1;
+    uint64_t* pa = (uint64_t*)calloc(cap, 8);
+    uint64_t* pb = (uint64_t*)calloc(cap, 8);
+    int64_t* off = (int64_t*)calloc(cap, 8);
+    int64_t* cnt = (int64_t*)calloc(cap, 8);
+    double* cells = (double*)calloc((size_t)cap * K * D, 8);
+    cnt[0] = n_samples;
+    double* cand = (double*)malloc(sizeof(double) * 4 * D);
+    for (int i = 0; i < K; ++i) {
+        const int64_t ncap = n * 4;
+        uint64_t* qa = (uint64_t*)calloc(ncap, 8);
+        uint64_t* qb = (uint64_t*)calloc(ncap, 8);
+        int64_t* qo = (int64_t*)calloc(ncap, 8);
+        int64_t* qc = (int64_t*)calloc(ncap, 8);
+        double* qcells = (double*)calloc((size_t)ncap * K * D, 8);
+        int64_t m = 0;
+        for (int64_t q = 0; q < n; ++q) {
+            double* hs = cells + (size_t)q * K * D;
+            double P[4];
+            rnn_candidates(a, i, hs, cand, P);
+            const int na_done = __builtin_popcountll(pa[q]), nb_done = __builtin_popcountll(pb[q]);
+            int ok[4], last = -1;
+            double Z = 0.0;
+            for (int s = 0; s < 4; ++s) {
+                ok[s] = state_allowed(a, i, na_done, nb_done, s);
+                if (ok[s]) { Z += P[s]; last = s; }
+            }
+            int64_t hist[4] = {0, 0, 0, 0};
+            for (int64_t j = off[q]; j < off[q] + cnt[q]; ++j) {
+                const uint64_t ctr[4] = {(uint64_t)j, (uint64_t)i, 1, 0}, key[2] = {seed, 0};
+                uint64_t x[4];
+                or_philox4x64_10(ctr, key, x);
+                const double u = (double)(x[0] >> 11) * 0x1.0p-53;
+                const double t = u * Z;
+                double cum = 0.0;
+                int pick = last;
+                for (int s = 0; s < 4; ++s) {
+                    if (!ok[s]) continue;
+                    cum += P[s];
+                    if (t < cum) { pick = s; break; }
+                }
+                if (pick >= 0) hist[pick] += 1;
+            }
+            int64_t o = off[q];
+            for (int s = 0; s < 4; ++s) {
+                if (hist[s] == 0) continue;
+                qa[m] = pa[q] | ((uint64_t)(s & 1) << i);
+                qb[m] = pb[q] | ((uint64_t)(s >> 1) << i);
+                qo[m] = o;
+                qc[m] = hist[s];
+                double* dst = qcells + (size_t)m * K * D;
+                memcpy(dst, hs, sizeof(double) * (size_t)K * D);
+                memcpy(dst + (size_t)i * D, cand + (size_t)s * D, sizeof(double) * D);
+                o += hist[s];
+                ++m;
+            }
+        }
+        free(pa); free(pb); free(off); free(cnt); free(cells);
+        pa = qa; pb = qb; off = qo; cnt = qc; cells = qcells;
+        n = m;
+    }
+    for (int64_t q = 0; q < n && q < capacity; ++q) {
+        dets[2 * q] = pa[q];
+        dets[2 * q + 1] = pb[q];
+        counts[q] = (double)cnt[q];
+    }
+    free(pa); free(pb); free(off); free(cnt); free(cells); free(cand);
+    return n;
 }
 
 /* S 2^Se += v 2^e, keeping the larger exponent */
@@ -527,6 +716,8 @@ static void one_sample(const or_ham* h, const or_ansatz* a, const uint64_t* n, i
                        double eps, int n_draws, uint64_t seed, or_sample_out* o, int with_cond)
 {
     memset(o, 0, sizeof(*o));
+    /* the first-order bound P1 describes the linear readout's contraction */
+    if (a->readout != 0) with_cond = 0;
     double la_n, lf_n;
     int sg_n;
     or_log_psi(a, n, &la_n, &sg_n, &lf_n);
@@ -671,10 +862,9 @@ void or_grad_log_psi(const or_ansatz* a, const uint64_t* det, double* grad_t, do
         int occ[128];
         unpack(K, det, occ);
         for (int k = 0; k < a->n_hidden; ++k) {
-            double th = a->rbm_b[k];
-            for (int s = 0; s < 2 * K; ++s)
-                if (occ[s]) th += a->rbm_W[(size_t)k * 2 * K + s];
-            double t = tanh(th);
+            /* d log|f| / d theta_k: tanh (2 cosh), -tan (cos, Ising) */
+            const double th = corr_theta(a, occ, k);
+            const double t = a->corr == 0 ? tanh(th) : -tan(th);
             if (grad_b) grad_b[k] = t;
             if (grad_W)
                 for (int s = 0; s < 2 * K; ++s) grad_W[(size_t)k * 2 * K + s] = occ[s] ? t : 0.0;
@@ -682,4 +872,17 @@ void or_grad_log_psi(const or_ansatz* a, const uint64_t* det, double* grad_t, do
     }
     free(hs);
     free(ex);
+}
+
+void or_grad_corr_W2(const or_ansatz* a, const uint64_t* det, double* grad_W2)
+{
+    const int K = a->K, N = 2 * K;
+    int occ[128];
+    unpack(K, det, occ);
+    for (int k = 0; k < a->n_hidden; ++k) {
+        const double t = a->corr == 0 ? tanh(corr_theta(a, occ, k)) : -tan(corr_theta(a, occ, k));
+        for (int s = 0; s < N; ++s)
+            for (int u = 0; u < N; ++u)
+                grad_W2[((size_t)k * N + s) * N + u] = (a->corr == 2 && occ[s] && occ[u]) ? 0.5 * t : 0.0;
+    }
 }

@@ -49,6 +49,29 @@ typedef struct {
     int n_hidden;            /* 0 = no correlator */
     const double* rbm_W;     /* [n_hidden][2K] */
     const double* rbm_b;     /* [n_hidden] */
+    /* Readout of Sec. 2.2. 0: linear, psi_TN = (h_{K-1})_0 (as above).
+     * 1: the normalised MPS-RNN / BDG-RNN of Eq. (MPS-RNN-1D) and
+     * Eq. (bdg-rnn-update) without the tensor term: at vertex i (vertices in
+     * computation order; vertex i is spatial orbital i) the candidate cells
+     * h_i^s = sum_{e=(j->i)} M_e^s h_j + v_i^s, with h_j the cells of the local
+     * states already chosen (h_{-1} = e_0), give P_i(s) = sum_a eta_i[a]
+     * (h_i^s[a])^2; P~_i(s) = P_i(s) / sum over the local states s' still
+     * allowed by the N_alpha / N_beta constraint of Sec. 3 (0 for the others);
+     * Phi(n) = prod_i sqrt(P~_i(s_i)) * prod_i sign(w_i . h_i^{s_i} + c_i)
+     * (real parameters: the phase arg(.) is a sign; a zero argument counts +). */
+    int readout;
+    int n_alpha, n_beta;     /* the constraint (readout 1); n_alpha < 0: none,
+                                every local state allowed everywhere */
+    const double* rnn_v;     /* [K][4][D] */
+    const double* rnn_eta;   /* [K][D], >= 0 */
+    const double* rnn_w;     /* [K][D] */
+    const double* rnn_c;     /* [K] */
+    /* Correlator of Sec. 2.3. 0: f = prod_k 2 cosh(theta_k) (Eq. RBM);
+     * 1: cos-RBM, f = prod_k cos(theta_k); 2: Ising-RBM, f = prod_k
+     * cos(theta_k + 1/2 sum_{s,t} W2[k][s][t] n_s n_t); theta_k = b_k +
+     * sum_s W[k][s] n_s over the 2K interleaved spin orbitals. */
+    int corr;
+    const double* rbm_W2;    /* [n_hidden][2K][2K] (corr 2) */
 } or_ansatz;
 
 typedef struct {
@@ -117,9 +140,31 @@ int or_local_energy(const or_ham* ham, const or_ansatz* a, const uint64_t* sampl
                     or_sample_out* out, int n_threads, const int64_t* index, int with_cond);
 
 /* d log|psi(n)| / d theta for one determinant: grad_t [n_edges][4][D][D],
- * grad_W [n_hidden][2K], grad_b [n_hidden] (any may be NULL). */
+ * grad_W [n_hidden][2K], grad_b [n_hidden] (any may be NULL). The tensor
+ * part needs the linear readout (readout 0). */
 void or_grad_log_psi(const or_ansatz* a, const uint64_t* det, double* grad_t,
                      double* grad_W, double* grad_b);
+
+/* d log|f(n)| / d W2 [n_hidden][2K][2K] of the Ising-RBM correlator (corr 2). */
+void or_grad_corr_W2(const or_ansatz* a, const uint64_t* det, double* grad_W2);
+
+/* Conditional probabilities of the normalised readout (readout 1) along
+ * `det`: P~_i(s) for every vertex i and local state s, [K][4]. */
+void or_rnn_conditionals(const or_ansatz* a, const uint64_t* det, double* probs);
+
+/* Autoregressive sampling from |Phi|^2 (readout 1; Sec. 2.1, Sec. 3),
+ * breadth-first over the vertices. A node of level i is a prefix (the local
+ * states of vertices < i) holding `c` of the n_samples draws at offsets
+ * o .. o+c-1 (nodes of a level tile [0, n_samples) in prefix order). At vertex
+ * i, draw j of a node takes the first allowed local state s with
+ * u_j Z < sum_{allowed s' <= s} P_i(s') (Z the sum over the allowed states;
+ * the last allowed state if rounding leaves none), where u_j = (x >> 11) 2^-53
+ * and x is the first output of Philox4x64-10 with key (seed, 0) and counter
+ * (j, i, 1, 0); the children keep the node's offsets in the order of s.
+ * Writes up to `capacity` unique determinants and their counts in prefix
+ * order and returns how many there are. */
+int64_t or_sample(const or_ansatz* a, int64_t n_samples, uint64_t seed, uint64_t* dets,
+                  double* counts, int64_t capacity);
 
 #ifdef __cplusplus
 }

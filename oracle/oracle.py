@@ -43,7 +43,10 @@ class Ham(C.Structure):
 class Ansatz(C.Structure):
     _fields_ = [("K", C.c_int), ("D", C.c_int), ("n_edges", C.c_int),
                 ("pred_ptr", C.c_void_p), ("pred_idx", C.c_void_p), ("tensors", C.c_void_p),
-                ("n_hidden", C.c_int), ("rbm_W", C.c_void_p), ("rbm_b", C.c_void_p)]
+                ("n_hidden", C.c_int), ("rbm_W", C.c_void_p), ("rbm_b", C.c_void_p),
+                ("readout", C.c_int), ("n_alpha", C.c_int), ("n_beta", C.c_int),
+                ("rnn_v", C.c_void_p), ("rnn_eta", C.c_void_p), ("rnn_w", C.c_void_p),
+                ("rnn_c", C.c_void_p), ("corr", C.c_int), ("rbm_W2", C.c_void_p)]
 
 
 class SampleOut(C.Structure):
@@ -90,12 +93,16 @@ class Problem:
         self.b = _c(sys.rbm_b, np.float64)
         self.ham = Ham(sys.K, sys.n_alpha, sys.n_beta, self.h1e.ctypes.data,
                        self.eri.ctypes.data, float(sys.e_core))
+        rnn = getattr(sys, "rnn", None)          # (v, eta, w, c) of the normalised readout
+        self.rnn = None if rnn is None else tuple(_c(x, np.float64) for x in rnn)
+        self.W2 = _c(getattr(sys, "rbm_W2", None), np.float64)
+        ptr = lambda a: a.ctypes.data if a is not None else None
         self.ans = Ansatz(sys.K, sys.D, int(self.tensors.shape[0]),
-                          self.pred_ptr.ctypes.data if self.pred_ptr is not None else None,
-                          self.pred_idx.ctypes.data if self.pred_idx is not None else None,
-                          self.tensors.ctypes.data, sys.n_hidden,
-                          self.W.ctypes.data if self.W is not None else None,
-                          self.b.ctypes.data if self.b is not None else None)
+                          ptr(self.pred_ptr), ptr(self.pred_idx),
+                          self.tensors.ctypes.data, sys.n_hidden, ptr(self.W), ptr(self.b),
+                          1 if self.rnn is not None else 0, sys.n_alpha, sys.n_beta,
+                          *(ptr(x) for x in (self.rnn or (None,) * 4)),
+                          int(getattr(sys, "corr", 0)), ptr(self.W2))
 
 
 def build_eri(chol):
@@ -185,6 +192,36 @@ def local_energy(P: Problem, samples=None, eps=None, n_draws=None, seed=None, th
                           C.c_double(eps), int(n_draws), C.c_uint64(seed), _p(out),
                           int(threads), _p(idx), int(bool(cond)))
     return out
+
+
+def rnn_conditionals(P: Problem, det):
+    """P~_i(s) of the normalised readout along ``det``, [K][4] (Sec. 2.2)."""
+    d = _c(det, np.uint64)
+    out = np.zeros((P.sys.K, 4), np.float64)
+    lib().or_rnn_conditionals(C.byref(P.ans), _p(d), _p(out))
+    return out
+
+
+def sample(P: Problem, n_samples, seed, capacity=None):
+    """Autoregressive sampling from |Phi|^2 (Sec. 2.1, Sec. 3): unique
+    determinants [n][2] and their counts, in prefix order."""
+    cap = int(n_samples if capacity is None else capacity)
+    dets = np.zeros((max(cap, 1), 2), np.uint64)
+    counts = np.zeros(max(cap, 1), np.float64)
+    lib().or_sample.restype = C.c_int64
+    n = lib().or_sample(C.byref(P.ans), C.c_int64(n_samples), C.c_uint64(seed), _p(dets), _p(counts),
+                        C.c_int64(cap))
+    n = int(n)
+    return dets[:min(n, cap)], counts[:min(n, cap)], n
+
+
+def grad_corr_W2(P: Problem, det):
+    """d log|f| / d W2 of the Ising-RBM correlator, [N_h][2K][2K]."""
+    d = _c(det, np.uint64)
+    N = 2 * P.sys.K
+    g = np.zeros((P.sys.n_hidden, N, N), np.float64)
+    lib().or_grad_corr_W2(C.byref(P.ans), _p(d), _p(g))
+    return g
 
 
 def grad_log_psi(P: Problem, det):

@@ -21,7 +21,10 @@ Conventions (shared with the library and the oracle):
   * tensor-network edges: tensors[e][sigma][a][b], h_i = sum_e M_e^{sigma_i} h_j
     (column convention, Eq. (MPS-RNN-1D) with v = 0); pred_idx = -1 marks the
     boundary vector l = e_0; the read-out vector is r = e_0;
-  * RBM correlator W[k][s] over the 2K interleaved spin orbitals, b[k].
+  * RBM correlator W[k][s] over the 2K interleaved spin orbitals, b[k];
+    `corr` selects 2cosh (0), cos (1) or Ising-cos (2, with W2[k][s][t]);
+  * `rnn` = (v [K][4][D], eta [K][D], w [K][D], c [K]) switches the readout to
+    the normalised MPS-RNN / BDG-RNN of Sec. 2.2 (None: the linear readout).
 """
 from __future__ import annotations
 
@@ -55,6 +58,9 @@ class System:
     eps: float                 # deterministic threshold epsilon
     n_draws: int               # N_epsilon
     seed: int                  # Philox key for the stochastic part
+    rnn: Optional[tuple] = None          # (v, eta, w, c): normalised readout
+    corr: int = 0                        # 0 2cosh, 1 cos-RBM, 2 Ising-RBM
+    rbm_W2: Optional[np.ndarray] = None  # [N_h][2K][2K] (Ising-RBM)
 
     @property
     def n_hidden(self) -> int:
@@ -305,3 +311,45 @@ CONFIGS = {
     "fe2s2": fe2s2_dense,
     "h18": h18_graph,
 }
+
+
+def rnn_params(rng, K, D, v_std=0.1):
+    """Parameters of the normalised readout (Sec. 2.2): v [K][4][D] ~ N(0, v_std),
+    eta [K][D] ~ U(0.5, 1.5), w [K][D] ~ N(0, 1/sqrt(D)), c [K] ~ N(0, 0.1)."""
+    v = rng.normal(0.0, v_std, size=(K, 4, D))
+    eta = rng.uniform(0.5, 1.5, size=(K, D))
+    w = rng.normal(0.0, 1.0 / math.sqrt(D), size=(K, D))
+    c = rng.normal(0.0, 0.1, size=K)
+    return (v, eta, w, c)
+
+
+def with_readout(sys_, seed=0, v_std=0.1):
+    """The same system with the normalised MPS-RNN / BDG-RNN readout of Sec. 2.2
+    (site tensors unchanged; v, eta, w, c drawn from their own seeded stream)."""
+    rng = np.random.Generator(np.random.PCG64(BASE_SEED + 300 + seed))
+    return dataclasses.replace(sys_, rnn=rnn_params(rng, sys_.K, sys_.D, v_std), name=sys_.name + "_rnn")
+
+
+def with_correlator(sys_, corr, seed=0, w2_std=0.005):
+    """The same system with the cos-RBM (corr 1) or Ising-RBM (corr 2)
+    correlator of Sec. 2.3: the same W and b; for corr 2 a symmetric
+    W2 [N_h][2K][2K] with entries N(0, w2_std)."""
+    W2 = None
+    if corr == 2:
+        rng = np.random.Generator(np.random.PCG64(BASE_SEED + 400 + seed))
+        N = 2 * sys_.K
+        W2 = rng.normal(0.0, w2_std, size=(sys_.n_hidden, N, N))
+        W2 = 0.5 * (W2 + W2.transpose(0, 2, 1))
+    return dataclasses.replace(sys_, corr=corr, rbm_W2=W2,
+                               name=sys_.name + ("_cosrbm" if corr == 1 else "_isingrbm"))
+
+
+def h50_rnn(n_samples=4096, seed_offset=0, K=50, D=10, n_hidden=0, eps=0.01, n_draws=100):
+    """H50-shaped chain with the paper's BDG(1)-RNN readout at chi = 10 and its
+    semistochastic setting eps = 0.01, N_eps = 100 (Sec. 4.1, Fig. 3a): the
+    Hamiltonian of h50_chain, site tensors I + G/sqrt(D), v, eta, w, c from
+    rnn_params; unique samples uniform over fixed N_alpha / N_beta (the bench
+    draws its samples autoregressively instead)."""
+    base = h50_chain(n_samples=n_samples, seed_offset=seed_offset, K=K, D=D, n_hidden=n_hidden,
+                     eps=eps, n_draws=n_draws)
+    return with_readout(base, seed=seed_offset)
