@@ -486,6 +486,17 @@ def run_batch(args):
                           out=np.empty(len(s.samples), np.float64)))
     n_total = sum(len(s.samples) for s in systems)
 
+    # schedule and tiles from the autotuner (cached per workload signature)
+    tuned = None
+    if not args.no_autotune:
+        from paper_2507_19276_gb300 import autotune
+        cfg, entry = autotune.tune(ctxs, dargs, systems, prec, tol)
+        args.workers = cfg["workers"]
+        tuned = {"config": cfg, "trials": entry.get("trials", [])}
+        for c in ctxs:
+            c.set_precision(prec, timing=True, energy_tolerance=tol,
+                            tile_blocks_per_sm=cfg["tile_blocks_per_sm"], table_mb=cfg["table_mb"])
+
     def step(a):
         return nqs.local_energy_batch(ctxs, a, n_workers=args.workers)
 
@@ -532,6 +543,38 @@ def run_batch(args):
     for c in ctxs:
         c.stage_times()
 
+    # energy gradient of every system in the same batch call (Eq. egrad)
+    grad = None
+    if args.grad:
+        gargs = [dict(a, grad=True) for a in hargs]
+        nqs.local_energy_batch(ctxs, gargs, n_workers=args.workers)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nqs.local_energy_batch(ctxs, gargs, n_workers=args.workers)
+        torch.cuda.synchronize()
+        grad = {"ms_per_step": 1e3 * (time.perf_counter() - t0),
+                "what": "E_loc + u_n on the device + FP64 VJP of every system, host buffers"}
+        for c in ctxs:
+            c.stage_times()
+
+    # the FP64 shared-prefix form on the same batch: per-system weighted-energy differences
+    fp64 = None
+    if not args.no_fp64_compare and prec == nqs.NQS_PREC_MIXED:
+        for c in ctxs:
+            c.set_precision(nqs.NQS_PREC_FP64_SHARED)
+        r64 = step(hargs)
+        torch.cuda.synchronize()
+        for c in ctxs:
+            c.set_precision(nqs.NQS_PREC_MIXED, energy_tolerance=0.0)
+        r0 = step(hargs)
+        torch.cuda.synchronize()
+        d = [abs(a[1]["e_mean"] - b[1]["e_mean"]) for a, b in zip(res, r64)]
+        d0 = [abs(a[1]["e_mean"] - b[1]["e_mean"]) for a, b in zip(r0, r64)]
+        fp64 = {"precision": "fp64_shared", "e_mean_diff_ha_max_over_systems": max(d),
+                "e_mean_diff_ha_median": float(np.median(d)),
+                "e_mean_diff_unrefined_ha_max": max(d0), "e_mean_diff_unrefined_ha_median": float(np.median(d0)),
+                "n_refined_total": int(sum(r[1]["n_refined"] for r in res))}
+
     peaks, src = _peaks()
     flops = sum(2.0 * s.D * s.D * r[1]["span_sites"] + 2.0 * s.D * r[1]["n_amplitudes"]
                 for s, r in zip(systems, res))
@@ -563,7 +606,9 @@ def run_batch(args):
             "e2e": {"value": ws * n_total * args.steps / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": 24 * n_total, "d2h_bytes_per_step": 8 * n_total},
             "clocks": clk, "gpu_launches": int(launches),
-            "summary": {"n_refined": int(sum(r[1]["n_refined"] for r in res))}}
+            "autotune": tuned, "fp64_gpu": fp64, "energy_gradient": grad,
+            "summary": {"n_refined": int(sum(r[1]["n_refined"] for r in res)),
+                        "audit_rel_error_max": max(r[1]["audit_rel_error"] for r in res)}}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         sub_ = [s.subset(range(2)) for s in systems[:8]]
@@ -602,6 +647,10 @@ def main():
                     help="every sample count 1 instead of the workload's Zipf counts")
     ap.add_argument("--no-peaks", action="store_true",
                     help="skip the L2 / FMA ceilings measured before the timed region")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="uneven batch: default schedule instead of the autotuner's")
+    ap.add_argument("--grad", action="store_true",
+                    help="also time the energy gradient (uneven batch; h18 / h50_rnn workloads)")
     ap.add_argument("--peaks", action="store_true",
                     help="print the measured ceilings (L2 read, random gathers, FMA) and exit")
     args = ap.parse_args()

@@ -83,18 +83,45 @@ typedef struct {
                              must be >= 0) */
     double energy_tolerance;    /* mixed form, chain ansatz: bound (Ha) on the
                              error of the weighted energy sum c E_loc / sum c
-                             that nqs_local_energy guarantees by re-evaluating
-                             samples in the FP64 shared-prefix form. After the
-                             mixed pass, samples are taken in decreasing order
-                             of c_n e_abs_n (e_abs = |H_nn| + sum |terms|) until
-                             1e-6 * sum over the others of c_n e_abs_n / sum c
-                             <= energy_tolerance (1e-6: the per-sample error of
-                             the mixed form relative to e_abs that the parity
-                             tests hold it to); their E_loc are replaced by the
-                             FP64 values. 0 (default): no re-evaluation.
-                             Ignored by the FP64 forms. Must be finite, >= 0 */
-    int reserved[10];     /* must be zero */
+                             that nqs_local_energy meets by re-evaluating
+                             samples in the FP64 shared-prefix form. The
+                             per-sample error of the mixed form relative to
+                             e_abs = |H_nn| + sum |terms| is taken as a factor f
+                             (1e-6 to start: what the parity tests hold the mixed
+                             form to); samples are taken in decreasing order of
+                             c_n e_abs_n until f * sum over the others of
+                             c_n e_abs_n / sum c <= energy_tolerance. Each call
+                             also re-evaluates audit_samples of the others and,
+                             if one of them errs by more than f, raises f to
+                             twice the largest observed error and extends the
+                             re-evaluation (the summary reports both). The
+                             re-evaluated E_loc are replaced by the FP64 values.
+                             The factor is measured, not proven: the bound holds
+                             for errors no larger than the audit saw.
+                             0 (default): no re-evaluation. Ignored by the FP64
+                             forms. Must be finite, >= 0 */
+    int grad_chunk;       /* gradient calls: samples whose environments live on
+                             the device at once (0, default: the whole batch);
+                             bounds the gradient's memory at the cost of forming
+                             the environments chunk by chunk. Must be >= 0 */
+    int audit_samples;    /* samples of the energy-tolerance audit (0: the
+                             default, 4; -1: none). Must be >= -1 */
+    int tile_blocks_per_sm;   /* shared-prefix forms: blocks per multiprocessor of
+                             each site-step tile launch (0: the default, 4; at most
+                             32). A schedule parameter: results do not depend on it */
+    int table_mb;         /* shared-prefix forms: cap (MiB) on the tables of one
+                             sample batch (0: the default, min(8 GiB, free / 3)).
+                             Smaller batches trade launches for memory; results do
+                             not depend on it */
+    int reserved[6];      /* must be zero */
 } nqs_options;
+
+/* Correlator kinds of Sec. 2.3 (nqs_set_correlator). */
+typedef enum {
+    NQS_CORR_COSH = 0,    /* f = prod_k 2 cosh(theta_k) (Eq. RBM, the default) */
+    NQS_CORR_COS = 1,     /* cos-RBM: f = prod_k cos(theta_k) */
+    NQS_CORR_ISING = 2    /* Ising-RBM: f = prod_k cos(theta_k + 1/2 sum_{s,t} W2[k][s][t] n_s n_t) */
+} nqs_correlator;
 
 /* Stages of the local-energy path, as reported by nqs_stage_times. */
 enum {
@@ -130,10 +157,15 @@ typedef struct {
                                plain form; one-change families plus two-change
                                clusters in the shared-prefix form; of the pass over the whole
                                batch) */
-    int64_t n_refined;      /* samples re-evaluated in FP64 (energy_tolerance) */
+    int64_t n_refined;      /* samples re-evaluated in FP64 (energy_tolerance),
+                               the audited ones included */
     double e_error_bound;   /* with energy_tolerance > 0 in the mixed form: the
-                               bound 1e-6 * sum c_n e_abs_n / sum c over the samples
+                               bound f * sum c_n e_abs_n / sum c over the samples
                                left in the mixed form (<= energy_tolerance); else 0 */
+    int64_t n_audited;      /* samples of the audit (see nqs_options.energy_tolerance) */
+    double audit_rel_error; /* largest |E_mixed - E_FP64| / max(|E|, e_abs) the audit saw */
+    double error_factor;    /* the factor f the bound used (1e-6, or twice the audit's
+                               largest error when that was larger) */
 } nqs_energy_summary;
 
 /* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t
@@ -178,10 +210,40 @@ int nqs_set_hamiltonian(nqs_ctx* ctx, const double* h1e, const double* cholesky_
  *  rbm_W [n_hidden][2*n_orb], rbm_b [n_hidden]: f = prod_k 2cosh(b_k +
  *    sum_s W[k][s] n_s) over the interleaved spin orbitals; n_hidden = 0 and
  *    NULL pointers: f = 1.
- *  1 <= D <= 256; a graph needs in-degree <= 8. */
+ *  1 <= D <= 256; a graph needs in-degree <= 8. Resets the readout to the
+ *  linear one and the correlator kind to 2cosh. */
 int nqs_set_ansatz(nqs_ctx* ctx, const double* site_tensors, int n_edges, int bond_dim,
                    const int* pred_ptr, const int* pred_idx, const double* rbm_W,
                    const double* rbm_b, int n_hidden);
+
+/* The normalised MPS-RNN / BDG-RNN readout of Sec. 2.2 (Eq. MPS-RNN-1D with
+ * the affine term; Eq. bdg-rnn-update without the tensor term) on the site
+ * tensors of nqs_set_ansatz. Vertex i (spatial orbital i, the computation
+ * order) forms the candidate cells h_i^s = sum_{e=(j->i)} M_e^s h_j + v_i^s
+ * from the cells of the local states already chosen (h_{-1} = e_0), and
+ *   P_i(s) = sum_a eta_i[a] (h_i^s[a])^2,  P~_i(s) = P_i(s) / sum_{s' allowed} P_i(s'),
+ *   Phi(n) = prod_i sqrt(P~_i(s_i)) * prod_i sign(w_i . h_i^{s_i} + c_i)
+ * (real parameters: the phase arg(.) of Sec. 2.2 is a sign; a zero argument
+ * counts as +). With `constrained`, a local state is allowed at vertex i when,
+ * after it, neither spin exceeds N_alpha / N_beta and the later vertices can
+ * still hold the electrons left (Sec. 3); otherwise every state is allowed.
+ * Phi is normalised over the (constrained) determinants, so psi = f Phi with
+ * the correlator f as in Sec. 2.3.
+ *  v [n_orb][4][D], eta [n_orb][D] (finite, >= 0), w [n_orb][D], c [n_orb].
+ *  All four NULL: back to the linear readout.
+ * Only the plain FP64 form evaluates this readout (the shared-prefix forms
+ * return NQS_ERR_UNSUPPORTED); nqs_amplitude returns log|Phi f|; the
+ * site-tensor gradient needs the linear readout (NQS_ERR_UNSUPPORTED). */
+int nqs_set_readout(nqs_ctx* ctx, const double* v, const double* eta, const double* w,
+                    const double* c, int constrained);
+
+/* Correlator kind of Sec. 2.3 for the rbm_W, rbm_b of nqs_set_ansatz:
+ * NQS_CORR_COSH (Eq. RBM), NQS_CORR_COS (cos-RBM) or NQS_CORR_ISING
+ * (Ising-RBM, W2 [n_hidden][2 n_orb][2 n_orb] over the interleaved spin
+ * orbitals, copied; NULL otherwise). The cos forms may make f and psi
+ * negative; psi(n) = 0 for a sample is NQS_ERR_INVALID_ARG as before. The
+ * shared-prefix forms support NQS_CORR_COSH only (NQS_ERR_UNSUPPORTED). */
+int nqs_set_correlator(nqs_ctx* ctx, int kind, const double* W2);
 
 /* Connected determinants with |H_mn| >= det_threshold, canonical order.
  *  samples [Ns][2]; offsets [Ns+1] receives the start of each sample's list.
@@ -250,7 +312,9 @@ int nqs_local_energy(nqs_ctx* ctx, const uint64_t* samples, const double* counts
                      nqs_energy_summary* out);
 
 /* One system of a multi-system batch (nqs_local_energy_batch): the arguments
- * of nqs_local_energy for that system, and its status on return. */
+ * of nqs_local_energy for that system, and its status on return. With any of
+ * grad_sites / grad_W / grad_b non-NULL the system runs nqs_energy_gradient
+ * instead (the energy gradient of Eq. egrad, or of Sec. 2.3 with reweighted). */
 typedef struct {
     const uint64_t* samples;     /* [n_samples][2], host or device */
     const double* counts;        /* [n_samples] or NULL */
@@ -261,6 +325,10 @@ typedef struct {
     double* e_loc;               /* [n_samples] out */
     nqs_energy_summary* summary; /* host struct or NULL */
     int status;                  /* out: this system's nqs_status */
+    int reweighted;              /* energy gradient form (see nqs_energy_gradient) */
+    double* grad_sites;          /* [n_edges][4][D][D] out, or NULL */
+    double* grad_W;              /* [n_hidden][2K] out, or NULL */
+    double* grad_b;              /* [n_hidden] out, or NULL */
 } nqs_batch_item;
 
 /* Local energies of independent systems in one call (no counterpart in the
@@ -283,9 +351,52 @@ int nqs_local_energy_batch(nqs_ctx* const* ctxs, int n_sys, nqs_batch_item* item
  *  grad = sum_n u[n] d log|psi(n)| / d theta, theta = (site tensors, W, b).
  *  grad_sites [n_edges][4][D][D], grad_W [n_hidden][2K], grad_b [n_hidden];
  *  outputs are overwritten (not accumulated); NULL skips one. With
- *  u_n = 2 c_n (E_loc(n) - E_mean) / sum c this is the energy gradient. */
+ *  u_n = 2 c_n (E_loc(n) - E_mean) / sum c this is the energy gradient.
+ *  FP64. The site-tensor part is, per edge and local state, the sum over the
+ *  samples of that local state of u_n / psi_TN(n) g_i(n) h_j(n)^T (adjoint
+ *  times forward cell); nqs_options.grad_chunk bounds how many samples'
+ *  environments are held at once. */
 int nqs_grad_log_psi_vjp(nqs_ctx* ctx, const uint64_t* samples, const double* u, int64_t Ns,
                          double* grad_sites, double* grad_W, double* grad_b);
+
+/* nqs_grad_log_psi_vjp with the Ising-RBM couplings as well:
+ *  grad_W2 [n_hidden][2K][2K] (d theta_k / d W2[k][s][t] = n_s n_t / 2);
+ *  non-NULL grad_W2 needs NQS_CORR_ISING. */
+int nqs_grad_log_psi_vjp2(nqs_ctx* ctx, const uint64_t* samples, const double* u, int64_t Ns,
+                          double* grad_sites, double* grad_W, double* grad_b, double* grad_W2);
+
+/* Energy gradient in one call: nqs_local_energy (the context's precision and
+ * options), then on the device the weights
+ *   reweighted = 0 (Eq. egrad):  u_n = 2 c_n (E_loc(n) - E_mean) / sum c
+ *   reweighted = 1 (Sec. 2.3):   u_n = 2 c_n f~_n^2 (E_loc(n) - E_theta) / sum c,
+ *                                f~_n^2 = f_n^2 / B, E_theta = e_tilde_mean
+ * (the latter for samples drawn from |Phi|^2 with the correlator f outside the
+ * normalised part), then the FP64 VJP. Outputs as in nqs_grad_log_psi_vjp2
+ * (any may be NULL); e_loc [Ns] (may be NULL) receives E_loc, `out` the
+ * summary. Needs Ns > 0. */
+int nqs_energy_gradient(nqs_ctx* ctx, const uint64_t* samples, const double* counts, int64_t Ns,
+                        double det_threshold, int n_draws, uint64_t philox_seed, int reweighted,
+                        double* grad_sites, double* grad_W, double* grad_b, double* grad_W2,
+                        double* e_loc, nqs_energy_summary* out);
+
+/* Autoregressive sampling from |Phi|^2 of the normalised readout (Sec. 2.1:
+ * the ansatz's conditionals allow exact sampling; Sec. 3: breadth first over
+ * the vertices, the constraint built into the conditionals). n_samples draws
+ * grouped into unique determinants: a node of level i is a distinct prefix
+ * holding `cnt` of the draws at offsets off .. off+cnt-1 (the nodes of a level
+ * tile the draws in prefix order); draw j picks the local state of vertex i
+ * as the first allowed s with u_j Z < sum_{allowed s' <= s} P_i(s') (Z the
+ * sum over the allowed states; the last allowed state if rounding leaves
+ * none), u_j = (x >> 11) 2^-53 with x the first output of Philox4x64-10 with
+ * key (seed, 0) and counter (j, i, 1, 0); the children keep the offsets in the
+ * order of s. The result depends on seed and n_samples only.
+ *  samples [capacity][2], counts [capacity] (host or device) receive the
+ *  unique determinants in prefix order (vertex 0 most significant, local
+ *  state order 0..3) and their counts; *n_unique (host) their number.
+ *  capacity < n_unique -> NQS_ERR_INVALID_ARG with *n_unique written.
+ *  Needs nqs_set_readout (NQS_ERR_STATE otherwise). */
+int nqs_sample(nqs_ctx* ctx, int64_t n_samples, uint64_t seed, uint64_t* samples, double* counts,
+               int64_t capacity, int64_t* n_unique);
 
 #ifdef __cplusplus
 }

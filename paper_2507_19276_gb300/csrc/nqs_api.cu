@@ -17,6 +17,10 @@ using namespace nqs;
 
 namespace {
 
+// mixed form with an energy tolerance: samples re-evaluated in FP64 each call
+// to check the per-sample error factor (nqs_options.audit_samples = 0)
+constexpr int kDefaultAudit = 4;
+
 struct DevBuf {
     void* p = nullptr;
     size_t n = 0;
@@ -72,6 +76,18 @@ struct nqs_ctx {
     double stage_ms[NQS_N_STAGES] = {0};
     int64_t stage_launch[NQS_N_STAGES] = {0};
     unsigned long long* noalloc_addr = nullptr;   // device address of the fixed draw scratch
+    // normalised readout, correlator kind, gradient and audit options
+    DevBuf rv, reta, rw, rc, W2, rnn_cells, rnn_lp, rnn_sg, grad_scr, u_dev, ebar_dev;
+    int grad_chunk = 0;        // samples whose environments live at once in the gradient (0: all)
+    int audit = 4;             // mixed form: samples re-evaluated in FP64 to check the error factor
+    double audit_rel = 0.0, err_factor = 0.0;
+    int64_t n_audited = 0;
+    const double* last_logf = nullptr;   // log|f| of the last nqs_local_energy batch
+    int tile_bps = 4;          // site-step tile launch: blocks per multiprocessor
+    int table_mb = 0;          // cap on one sample batch's shared-prefix tables (0: none)
+    // autoregressive sampler levels
+    std::vector<DevBuf> smp_pa, smp_pb, smp_off, smp_cnt, smp_par, smp_cell;
+    DevBuf smp_cand, smp_ccnt, smp_cpos, smp_tabs;
     struct Pending { int stage; cudaEvent_t a, b; };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> free_events;
@@ -322,8 +338,32 @@ int count_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, uint64_t eb, int
     return NQS_OK;
 }
 
+// Cells, conditionals and phase signs of the normalised readout for every
+// sample (after env_pass with tn = 0, which leaves the correlator and H_nn).
+int rnn_env_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns)
+{
+    const int K = c->K, D = c->av.D;
+    TRY(ensure(c, c->rnn_cells, (size_t)Ns * K * D * 8));
+    TRY(ensure(c, c->rnn_lp, (size_t)Ns * K * 8));
+    TRY(ensure(c, c->rnn_sg, (size_t)Ns * K));
+    RnnEnvArgs r{};
+    r.an = c->av;
+    r.samples = samples;
+    r.Ns = Ns;
+    r.cells = (double*)c->rnn_cells.p;
+    r.lp = (double*)c->rnn_lp.p;
+    r.sg = (int8_t*)c->rnn_sg.p;
+    r.log_f = (const double*)c->logf.p;
+    r.psi_mant = (double*)c->pmant.p;
+    r.psi_exp = (int*)c->pexp.p;
+    LAUNCH(NQS_STAGE_ENV, launch_rnn_env(r, c->stream));
+    CK(cudaGetLastError());
+    return NQS_OK;
+}
+
 // tn: 1 = psi(n) and the environments; 2 = psi(n) only (chain, shared-prefix
-// path: its FP64 value is the denominator of every ratio of the sample)
+// path: its FP64 value is the denominator of every ratio of the sample);
+// 0 = no tensor-network part (the normalised readout has its own pass)
 int env_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, bool adjoints, int tn = 1)
 {
     const int K = c->K, D = c->av.D, NH = c->av.n_hidden;
@@ -333,7 +373,7 @@ int env_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, bool adjoints, int
     e.samples = samples;
     e.Ns = Ns;
     e.tn = tn;
-    if (tn == 2) {
+    if (tn == 2 || tn == 0) {
         // psi(n) only
     } else if (c->av.chain) {
         TRY(ensure(c, c->Lenv, (size_t)Ns * (K + 1) * D * 8));
@@ -375,7 +415,8 @@ int amp_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, RowSet rows, int64
              int64_t max_rows_per_sample, int stage)
 {
     StageScope sc(c, stage);
-    const int R = amp_fp64_rows_per_block(c->av);
+    const bool rnn = c->av.readout == 1;
+    const int R = rnn ? rnn_rows_per_block() : amp_fp64_rows_per_block(c->av);
     int64_t max_chunks = total_rows / R + Ns;
     if (max_rows_per_sample >= 0) max_chunks = Ns * ((max_rows_per_sample + R - 1) / R);
     TRY(ensure(c, base, (size_t)(Ns + 1) * 8));
@@ -385,6 +426,25 @@ int amp_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, RowSet rows, int64
     rows.count = count_dev;
     rows.chunk_base = (const int64_t*)base.p;
     rows.max_chunks = max_chunks;
+    if (rnn) {
+        RnnAmpArgs r{};
+        r.an = c->av;
+        r.h = c->hv;
+        r.samples = samples;
+        r.Ns = Ns;
+        r.rows = rows;
+        r.rows_per_block = R;
+        r.cells = (const double*)c->rnn_cells.p;
+        r.lp = (const double*)c->rnn_lp.p;
+        r.sg = (const int8_t*)c->rnn_sg.p;
+        r.theta = (const double*)c->theta.p;
+        r.lc = (const double*)c->lc.p;
+        r.partial = (double*)part.p;
+        r.span = (int64_t*)span.p;
+        LAUNCH(stage, launch_rnn_amp(r, c->stream));
+        CK(cudaGetLastError());
+        return NQS_OK;
+    }
     AmpArgs a{};
     a.an = c->av;
     a.h = c->hv;
@@ -432,7 +492,7 @@ int site_tables(nqs_ctx* c, const FamArgs<T>& f, int nbb)
     sb.items = c->site_items.p;
     LAUNCH(NQS_STAGE_TABLES, fam_site_fill(f, sb, nbb, c->stream));
     for (int tau = 0; tau < K; ++tau)
-        LAUNCH(NQS_STAGE_TABLES, fam_site_step(f, sb, tau, bounds.data(), 4 * c->n_sm, c->stream));
+        LAUNCH(NQS_STAGE_TABLES, fam_site_step(f, sb, tau, bounds.data(), c->tile_bps * c->n_sm, c->stream));
     CK(cudaGetLastError());
     return NQS_OK;
 }
@@ -467,6 +527,7 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
     cudaMemGetInfo(&free_b, &total_b);
     size_t budget = std::min<size_t>((size_t)8 << 30, free_b / 3);
     if (c->fam_budget > 0) budget = std::min(budget, c->fam_budget);
+    if (c->table_mb > 0) budget = std::min(budget, (size_t)c->table_mb << 20);
     const size_t per = fam_bytes_per_sample(K, D, sizeof(T));
     int64_t nb = (int64_t)std::max<size_t>(1, budget / per);
     if (nb > Ns) nb = Ns;
@@ -675,6 +736,12 @@ extern "C" int nqs_destroy(nqs_ctx* c)
                       &c->ref_s, &c->ref_c, &c->ref_pos, &c->ref_e, &c->site_cnt,
                       &c->site_offs, &c->site_bounds, &c->site_items, &c->site_scan};
     for (DevBuf* b : bufs) release(*b);
+    DevBuf* more[] = {&c->rv, &c->reta, &c->rw, &c->rc, &c->W2, &c->rnn_cells, &c->rnn_lp, &c->rnn_sg,
+                      &c->grad_scr, &c->u_dev, &c->ebar_dev, &c->smp_cand, &c->smp_ccnt, &c->smp_cpos,
+                      &c->smp_tabs};
+    for (DevBuf* b : more) release(*b);
+    for (auto* v : {&c->smp_pa, &c->smp_pb, &c->smp_off, &c->smp_cnt, &c->smp_par, &c->smp_cell})
+        for (DevBuf& b : *v) release(b);
     for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);
     delete c;
@@ -692,16 +759,25 @@ extern "C" int nqs_set_options(nqs_ctx* c, const nqs_options* o)
     if (o->precision != NQS_PREC_FP64 && o->precision != NQS_PREC_MIXED &&
         o->precision != NQS_PREC_FP64_SHARED)
         return set_err(c, NQS_ERR_INVALID_ARG, "unknown precision %d", o->precision);
-    for (int i = 0; i < 10; ++i)
+    for (int i = 0; i < 6; ++i)
         if (o->reserved[i]) return set_err(c, NQS_ERR_INVALID_ARG, "nqs_options.reserved[%d] != 0", i);
+    if (o->tile_blocks_per_sm < 0 || o->tile_blocks_per_sm > 32)
+        return set_err(c, NQS_ERR_INVALID_ARG, "nqs_options.tile_blocks_per_sm outside 0..32");
+    if (o->table_mb < 0) return set_err(c, NQS_ERR_INVALID_ARG, "nqs_options.table_mb < 0");
+    c->tile_bps = o->tile_blocks_per_sm ? o->tile_blocks_per_sm : 4;
+    c->table_mb = o->table_mb;
     if (o->sample_index_base < 0)
         return set_err(c, NQS_ERR_INVALID_ARG, "nqs_options.sample_index_base < 0");
     if (!(o->energy_tolerance >= 0.0) || !std::isfinite(o->energy_tolerance))
         return set_err(c, NQS_ERR_INVALID_ARG, "nqs_options.energy_tolerance must be finite and >= 0");
+    if (o->grad_chunk < 0) return set_err(c, NQS_ERR_INVALID_ARG, "nqs_options.grad_chunk < 0");
+    if (o->audit_samples < -1) return set_err(c, NQS_ERR_INVALID_ARG, "nqs_options.audit_samples < -1");
     c->precision = o->precision;
     c->index_base = o->sample_index_base;
     c->energy_tol = o->energy_tolerance;
     c->timing = o->timing ? 1 : 0;
+    c->grad_chunk = o->grad_chunk;
+    c->audit = o->audit_samples == 0 ? kDefaultAudit : (o->audit_samples < 0 ? 0 : o->audit_samples);
     return NQS_OK;
 }
 
@@ -893,6 +969,10 @@ extern "C" int nqs_set_ansatz(nqs_ctx* c, const double* site_tensors, int n_edge
     a.n_hidden = n_hidden;
     a.W = n_hidden ? (const double*)c->W.p : nullptr;
     a.b = n_hidden ? (const double*)c->b.p : nullptr;
+    a.readout = 0;                 // linear readout and 2cosh correlator until set otherwise
+    a.mask_na = c->na;
+    a.mask_nb = c->nb;
+    a.corr = 0;
     c->av = a;
     c->has_tc = false;
     // tensor-core batches: D % 16 == 0 up to 128 in one reduction chunk, or
@@ -909,6 +989,63 @@ extern "C" int nqs_set_ansatz(nqs_ctx* c, const double* site_tensors, int n_edge
     }
     CK(cudaStreamSynchronize(c->stream));
     c->has_ans = true;
+    return NQS_OK;
+}
+
+extern "C" int nqs_set_readout(nqs_ctx* c, const double* v, const double* eta, const double* w,
+                               const double* cst, int constrained)
+{
+    if (!c) return NQS_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    cudaSetDevice(c->device);
+    TRY(check_ready(c, true));
+    const int K = c->K, D = c->av.D;
+    if (!v && !eta && !w && !cst) {
+        c->av.readout = 0;
+        return NQS_OK;
+    }
+    if (!v || !eta || !w || !cst)
+        return set_err(c, NQS_ERR_INVALID_ARG, "nqs_set_readout: v, eta, w and c must all be given (or all NULL)");
+    std::vector<double> he((size_t)K * D);
+    CK(cudaMemcpy(he.data(), eta, he.size() * 8, cudaMemcpyDefault));
+    for (size_t q = 0; q < he.size(); ++q)
+        if (!(he[q] >= 0.0) || !std::isfinite(he[q]))
+            return set_err(c, NQS_ERR_INVALID_ARG, "nqs_set_readout: eta[%zu] = %g is not finite and >= 0", q, he[q]);
+    TRY(ensure(c, c->rv, (size_t)K * 4 * D * 8));
+    TRY(ensure(c, c->reta, (size_t)K * D * 8));
+    TRY(ensure(c, c->rw, (size_t)K * D * 8));
+    TRY(ensure(c, c->rc, (size_t)K * 8));
+    CK(cudaMemcpy(c->rv.p, v, (size_t)K * 4 * D * 8, cudaMemcpyDefault));
+    CK(cudaMemcpy(c->reta.p, he.data(), (size_t)K * D * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->rw.p, w, (size_t)K * D * 8, cudaMemcpyDefault));
+    CK(cudaMemcpy(c->rc.p, cst, (size_t)K * 8, cudaMemcpyDefault));
+    c->av.rv = (const double*)c->rv.p;
+    c->av.reta = (const double*)c->reta.p;
+    c->av.rw = (const double*)c->rw.p;
+    c->av.rc = (const double*)c->rc.p;
+    c->av.mask_na = constrained ? c->na : -1;
+    c->av.mask_nb = constrained ? c->nb : -1;
+    c->av.readout = 1;
+    return NQS_OK;
+}
+
+extern "C" int nqs_set_correlator(nqs_ctx* c, int kind, const double* W2)
+{
+    if (!c) return NQS_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    cudaSetDevice(c->device);
+    TRY(check_ready(c, true));
+    if (kind < NQS_CORR_COSH || kind > NQS_CORR_ISING)
+        return set_err(c, NQS_ERR_INVALID_ARG, "unknown correlator kind %d", kind);
+    if (kind == NQS_CORR_ISING && c->av.n_hidden > 0 && !W2)
+        return set_err(c, NQS_ERR_INVALID_ARG, "the Ising-RBM correlator needs W2");
+    if (kind == NQS_CORR_ISING && c->av.n_hidden > 0) {
+        const size_t n = (size_t)c->av.n_hidden * 4 * c->K * c->K;
+        TRY(ensure(c, c->W2, n * 8));
+        CK(cudaMemcpy(c->W2.p, W2, n * 8, cudaMemcpyDefault));
+        c->av.W2 = (const double*)c->W2.p;
+    }
+    c->av.corr = kind;
     return NQS_OK;
 }
 
@@ -994,7 +1131,8 @@ extern "C" int nqs_amplitude(nqs_ctx* c, const uint64_t* dets, int64_t n, double
     TRY(stage_out(c, c->st_out0, log_abs, (size_t)n, &dla, &h0));
     TRY(stage_out(c, c->st_out1, sign, (size_t)n, &dsg, &h1));
     TRY(read_dev_error(c));
-    LAUNCH(NQS_STAGE_OTHER, launch_full_amp_fp64(c->av, dd, n, dla, dsg, c->stream));
+    if (c->av.readout == 1) LAUNCH(NQS_STAGE_OTHER, launch_rnn_full(c->av, dd, n, dla, dsg, c->stream));
+    else LAUNCH(NQS_STAGE_OTHER, launch_full_amp_fp64(c->av, dd, n, dla, dsg, c->stream));
     CK(cudaGetLastError());
     TRY(copy_back(c, log_abs, dla, (size_t)n, h0));
     TRY(copy_back(c, sign, dsg, (size_t)n, h1));
@@ -1087,9 +1225,10 @@ extern "C" int nqs_draws(nqs_ctx* c, const uint64_t* samples, int64_t Ns, double
 
 namespace {
 
-// Per-sample error of the mixed form relative to max(|E_loc|, e_abs): the
-// bound the parity tests hold it to (measured 1.3e-7 to 2e-7 on the benchmark
-// workloads, up to 6.8e-7 at D = 256, where the FP32 accumulations are longest).
+// Per-sample error of the mixed form relative to max(|E_loc|, e_abs) that the
+// refinement starts from: the bound the parity tests hold it to (measured 1.3e-7
+// to 2e-7 on the benchmark workloads, up to 6.8e-7 at D = 256, where the FP32
+// accumulations are longest); each call checks it on an FP64 audit sample.
 constexpr double kMixedRelError = 1e-6;
 
 // The local-energy pipeline on device-resident samples in precision `prec`:
@@ -1101,14 +1240,22 @@ int le_core(nqs_ctx* c, const uint64_t* ds, const double* dc, int64_t Ns, uint64
             bool want_summary)
 {
     TRY(reset_dev_error(c));
+    const bool rnn = c->av.readout == 1;
     const bool shared = c->av.chain && (prec == NQS_PREC_MIXED || prec == NQS_PREC_FP64_SHARED);
+    if (!c->av.chain && prec != NQS_PREC_FP64)
+        return set_err(c, NQS_ERR_UNSUPPORTED, "graph ansatze run the plain FP64 form (NQS_PREC_FP64)");
+    if (shared && (rnn || c->av.corr != NQS_CORR_COSH))
+        return set_err(c, NQS_ERR_UNSUPPORTED,
+                       "the shared-prefix forms need the linear readout and the 2cosh correlator; "
+                       "use NQS_PREC_FP64");
     if (shared && c->av.n_hidden > 512)
         return set_err(c, NQS_ERR_UNSUPPORTED, "shared-prefix path supports n_hidden <= 512");
     if (deabs && !shared) return set_err(c, NQS_ERR_STATE, "e_abs needs a shared-prefix form");
     {
         StageScope sc(c, NQS_STAGE_ENV);
         LAUNCH(NQS_STAGE_ENV, launch_validate(ds, Ns, c->K, c->na, c->nb, (DevError*)c->derr.p, c->stream));
-        TRY(env_pass(c, ds, Ns, false, shared ? 2 : 1));
+        TRY(env_pass(c, ds, Ns, false, rnn ? 0 : (shared ? 2 : 1)));
+        if (rnn) TRY(rnn_env_pass(c, ds, Ns));
         k_check_psi<<<(unsigned)((Ns + 255) / 256), 256, 0, c->stream>>>((const double*)c->pmant.p, Ns,
                                                                        (DevError*)c->derr.p);
         LAUNCH(NQS_STAGE_ENV, 1);
@@ -1196,15 +1343,52 @@ int le_core(nqs_ctx* c, const uint64_t* ds, const double* dc, int64_t Ns, uint64
     return NQS_OK;
 }
 
-// Error-budgeted refinement of a mixed-form result (de, with c->eabs): the
-// samples with the largest c_n e_abs_n are re-evaluated in the FP64
-// shared-prefix form until kMixedRelError * sum_{rest} c_n e_abs_n / sum c is
-// within c->energy_tol; the corrected summary goes to c->summary2.
+// FP64 shared-prefix re-evaluation of the samples `pick` (ascending) of a
+// mixed-form result: their E_loc in de are replaced; the FP64 values also go
+// to `fp64` (host, same order as pick) when it is non-NULL.
+int reevaluate(nqs_ctx* c, const uint64_t* ds, const double* dc, const std::vector<int64_t>& pick,
+               uint64_t eb, int n_draws, uint64_t seed, double* de, std::vector<double>* fp64)
+{
+    const int64_t k = (int64_t)pick.size();
+    if (k == 0) return NQS_OK;
+    TRY(ensure(c, c->ref_idx, (size_t)k * 8));
+    TRY(ensure(c, c->ref_s, (size_t)k * 16));
+    TRY(ensure(c, c->ref_c, (size_t)k * 8));
+    TRY(ensure(c, c->ref_pos, (size_t)k * 8));
+    TRY(ensure(c, c->ref_e, (size_t)k * 8));
+    CK(cudaMemcpyAsync(c->ref_idx.p, pick.data(), (size_t)k * 8, cudaMemcpyHostToDevice, c->stream));
+    LAUNCH(NQS_STAGE_OTHER, launch_gather_picked((const int64_t*)c->ref_idx.p, k, ds, dc, c->index_base,
+                                                 (uint64_t*)c->ref_s.p, (double*)c->ref_c.p,
+                                                 (int64_t*)c->ref_pos.p, c->stream));
+    TRY(le_core(c, (const uint64_t*)c->ref_s.p, (const double*)c->ref_c.p, k, eb, n_draws, seed,
+                NQS_PREC_FP64_SHARED, (const int64_t*)c->ref_pos.p, (double*)c->ref_e.p, nullptr,
+                false));
+    LAUNCH(NQS_STAGE_OTHER, launch_scatter_picked((const int64_t*)c->ref_idx.p, k,
+                                                  (const double*)c->ref_e.p, de, c->stream));
+    if (fp64) {
+        fp64->resize((size_t)k);
+        CK(cudaMemcpyAsync(fp64->data(), c->ref_e.p, (size_t)k * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+    // pick is host memory the copy above reads: wait before it goes away
+    CK(cudaStreamSynchronize(c->stream));
+    return NQS_OK;
+}
+
+// Error-budgeted refinement of a mixed-form result (de, with c->eabs). The
+// per-sample error of the mixed form relative to e_abs is bounded by a factor
+// f, kMixedRelError to start; the samples with the largest c_n e_abs_n are
+// re-evaluated in the FP64 shared-prefix form until f * sum_{rest} c_n e_abs_n
+// / sum c is within c->energy_tol. With them, c->audit of the other samples
+// (evenly spaced in sample order) are re-evaluated as a check of f: when their
+// largest |E_mixed - E_FP64| / max(|E|, e_abs) exceeds f, f becomes twice that
+// value and the selection grows to meet the tolerance with it. The corrected
+// summary goes to c->summary2.
 int refine_pass(nqs_ctx* c, const uint64_t* ds, const double* dc, int64_t Ns, uint64_t eb,
                 int n_draws, uint64_t seed, double* de, int64_t* n_ref, double* bound)
 {
-    std::vector<double> ea((size_t)Ns), cn((size_t)Ns, 1.0);
+    std::vector<double> ea((size_t)Ns), cn((size_t)Ns, 1.0), em((size_t)Ns);
     CK(cudaMemcpyAsync(ea.data(), c->eabs.p, (size_t)Ns * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(em.data(), de, (size_t)Ns * 8, cudaMemcpyDeviceToHost, c->stream));
     if (dc) CK(cudaMemcpyAsync(cn.data(), dc, (size_t)Ns * 8, cudaMemcpyDeviceToHost, c->stream));
     TRY(ensure(c, c->logf_save, (size_t)Ns * 8));
     CK(cudaMemcpyAsync(c->logf_save.p, c->logf.p, (size_t)Ns * 8, cudaMemcpyDeviceToDevice, c->stream));
@@ -1217,44 +1401,70 @@ int refine_pass(nqs_ctx* c, const uint64_t* ds, const double* dc, int64_t Ns, ui
         const double a = cn[(size_t)x] * ea[(size_t)x], b = cn[(size_t)y] * ea[(size_t)y];
         return a != b ? a > b : x < y;
     });
-    // suffix bounds: rest[k] = bound when the first k of `order` are re-evaluated
-    std::vector<double> rest((size_t)Ns + 1, 0.0);
-    for (int64_t k = Ns - 1; k >= 0; --k) {
-        const int64_t s = order[(size_t)k];
-        rest[(size_t)k] = rest[(size_t)k + 1] + kMixedRelError * cn[(size_t)s] * ea[(size_t)s] / sc;
+    // smallest k such that f * sum over order[k..] of c e_abs / sum c <= tolerance
+    auto select = [&](double f) {
+        std::vector<double> rest((size_t)Ns + 1, 0.0);
+        for (int64_t q = Ns - 1; q >= 0; --q) {
+            const int64_t s = order[(size_t)q];
+            rest[(size_t)q] = rest[(size_t)q + 1] + f * cn[(size_t)s] * ea[(size_t)s] / sc;
+        }
+        int64_t k = 0;
+        while (k < Ns && !(rest[(size_t)k] <= c->energy_tol)) ++k;
+        return k;
+    };
+    double f = kMixedRelError;
+    int64_t k = select(f);
+    std::vector<char> done((size_t)Ns, 0);
+    for (int64_t q = 0; q < k; ++q) done[(size_t)order[(size_t)q]] = 1;
+    // audit: c->audit of the others, evenly spaced in sample order
+    std::vector<int64_t> others, audit;
+    for (int64_t s = 0; s < Ns; ++s)
+        if (!done[(size_t)s]) others.push_back(s);
+    const int64_t na = std::min<int64_t>(c->audit, (int64_t)others.size());
+    for (int64_t j = 0; j < na; ++j) audit.push_back(others[(size_t)(((2 * j + 1) * others.size()) / (2 * na))]);
+    std::vector<int64_t> pick;
+    for (int64_t s = 0; s < Ns; ++s)
+        if (done[(size_t)s]) pick.push_back(s);
+    for (int64_t s : audit) done[(size_t)s] = 1;
+    pick.insert(pick.end(), audit.begin(), audit.end());
+    std::sort(pick.begin(), pick.end());
+    std::vector<double> e64;
+    TRY(reevaluate(c, ds, dc, pick, eb, n_draws, seed, de, &e64));
+    double observed = 0.0;
+    for (int64_t s : audit) {
+        const size_t at = (size_t)(std::lower_bound(pick.begin(), pick.end(), s) - pick.begin());
+        const double scale = std::max(std::fabs(e64[at]), ea[(size_t)s]);
+        if (scale > 0.0) observed = std::max(observed, std::fabs(em[(size_t)s] - e64[at]) / scale);
     }
-    int64_t k = 0;
-    while (k < Ns && !(rest[(size_t)k] <= c->energy_tol)) ++k;
-    *n_ref = k;
-    *bound = rest[(size_t)k];
-    if (k > 0) {
-        std::vector<int64_t> pick(order.begin(), order.begin() + k);
-        std::sort(pick.begin(), pick.end());
-        TRY(ensure(c, c->ref_idx, (size_t)k * 8));
-        TRY(ensure(c, c->ref_s, (size_t)k * 16));
-        TRY(ensure(c, c->ref_c, (size_t)k * 8));
-        TRY(ensure(c, c->ref_pos, (size_t)k * 8));
-        TRY(ensure(c, c->ref_e, (size_t)k * 8));
-        CK(cudaMemcpyAsync(c->ref_idx.p, pick.data(), (size_t)k * 8, cudaMemcpyHostToDevice, c->stream));
-        LAUNCH(NQS_STAGE_OTHER, launch_gather_picked((const int64_t*)c->ref_idx.p, k, ds, dc, c->index_base,
-                                                     (uint64_t*)c->ref_s.p, (double*)c->ref_c.p,
-                                                     (int64_t*)c->ref_pos.p, c->stream));
-        TRY(le_core(c, (const uint64_t*)c->ref_s.p, (const double*)c->ref_c.p, k, eb, n_draws, seed,
-                    NQS_PREC_FP64_SHARED, (const int64_t*)c->ref_pos.p, (double*)c->ref_e.p, nullptr,
-                    false));
-        LAUNCH(NQS_STAGE_OTHER, launch_scatter_picked((const int64_t*)c->ref_idx.p, k,
-                                                      (const double*)c->ref_e.p, de, c->stream));
-        // pick is host memory the copy above reads: wait before it goes away
-        CK(cudaStreamSynchronize(c->stream));
+    if (observed > f) {
+        f = 2.0 * observed;
+        const int64_t k2 = select(f);
+        std::vector<int64_t> extra;
+        for (int64_t q = 0; q < k2; ++q)
+            if (!done[(size_t)order[(size_t)q]]) extra.push_back(order[(size_t)q]);
+        std::sort(extra.begin(), extra.end());
+        for (int64_t s : extra) done[(size_t)s] = 1;
+        TRY(reevaluate(c, ds, dc, extra, eb, n_draws, seed, de, nullptr));
     }
+    double b = 0.0;
+    int64_t nd = 0;
+    for (int64_t s = 0; s < Ns; ++s) {
+        if (done[(size_t)s]) ++nd;
+        else b += f * cn[(size_t)s] * ea[(size_t)s] / sc;
+    }
+    *n_ref = nd;
+    *bound = b;
+    c->audit_rel = observed;
+    c->err_factor = f;
+    c->n_audited = (int64_t)audit.size();
     TRY(ensure(c, c->summary2, 8 * 8));
-    FinalArgs f{};
-    f.Ns = Ns;
-    f.counts = dc;
-    f.log_f = (const double*)c->logf_save.p;
-    f.e_loc = de;
-    f.summary = (double*)c->summary2.p;
-    LAUNCH(NQS_STAGE_FINAL, launch_summary(f, c->stream));
+    FinalArgs fa{};
+    fa.Ns = Ns;
+    fa.counts = dc;
+    fa.log_f = (const double*)c->logf_save.p;
+    fa.e_loc = de;
+    fa.summary = (double*)c->summary2.p;
+    LAUNCH(NQS_STAGE_FINAL, launch_summary(fa, c->stream));
     CK(cudaGetLastError());
     return NQS_OK;
 }
@@ -1291,7 +1501,12 @@ extern "C" int nqs_local_energy(nqs_ctx* c, const uint64_t* samples, const doubl
     int64_t n_ref = 0;
     double bound = 0.0;
     const int64_t matvecs = c->fam_matvecs;      // of the pass over the whole batch
+    c->audit_rel = 0.0;
+    c->err_factor = 0.0;
+    c->n_audited = 0;
     if (refine) TRY(refine_pass(c, ds, dc, Ns, eb, n_draws, seed, de, &n_ref, &bound));
+    // log|f| of the whole batch (the re-evaluation overwrites c->logf with its subset's)
+    c->last_logf = refine ? (const double*)c->logf_save.p : (const double*)c->logf.p;
     TRY(copy_back(c, e_loc, de, (size_t)Ns, he));
     if (out) {
         double sm[8], sm2[8];
@@ -1312,49 +1527,53 @@ extern "C" int nqs_local_energy(nqs_ctx* c, const uint64_t* samples, const doubl
         out->matvecs = shared ? matvecs : out->span_sites;
         out->n_refined = n_ref;
         out->e_error_bound = bound;
+        out->n_audited = c->n_audited;
+        out->audit_rel_error = c->audit_rel;
+        out->error_factor = c->err_factor;
     } else if (he) {
         CK(cudaStreamSynchronize(c->stream));
     }
     return NQS_OK;
 }
 
-extern "C" int nqs_grad_log_psi_vjp(nqs_ctx* c, const uint64_t* samples, const double* u, int64_t Ns,
-                                    double* grad_sites, double* grad_W, double* grad_b)
+namespace {
+
+// The VJP on device-resident samples and weights into device outputs (any may
+// be NULL). The environments of at most c->grad_chunk samples (0: all) live at
+// once: each chunk's environments are formed, its outer products added to the
+// outputs, and the next chunk reuses the memory.
+int vjp_core(nqs_ctx* c, const uint64_t* ds, const double* du, int64_t Ns, double* dg, double* dW,
+             double* db, double* dW2)
 {
-    if (!c) return NQS_ERR_INVALID_ARG;
-    c->err[0] = 0;
-    cudaSetDevice(c->device);
-    TRY(check_ready(c, true));
-    if (Ns < 0 || (Ns > 0 && (!samples || !u)))
-        return set_err(c, NQS_ERR_INVALID_ARG, "bad samples / u arguments");
     const int K = c->K, D = c->av.D, NH = c->av.n_hidden;
     const size_t nt = (size_t)c->av.n_edges * 4 * D * D, nw = (size_t)NH * 2 * K;
-    double *dg, *dW, *db;
-    bool hg, hW, hb;
-    TRY(stage_out(c, c->st_out1, grad_sites, nt, &dg, &hg));
-    TRY(stage_out(c, c->st_out2, grad_W, nw, &dW, &hW));
-    TRY(stage_out(c, c->st_out3, grad_b, (size_t)NH, &db, &hb));
+    if (dg && c->av.readout != 0)
+        return set_err(c, NQS_ERR_UNSUPPORTED, "the site-tensor gradient needs the linear readout");
     if (Ns == 0) {
         if (dg) CK(cudaMemsetAsync(dg, 0, nt * 8, c->stream));
         if (dW && nw) CK(cudaMemsetAsync(dW, 0, nw * 8, c->stream));
         if (db && NH) CK(cudaMemsetAsync(db, 0, (size_t)NH * 8, c->stream));
-    } else {
-        const uint64_t* ds;
-        const double* du;
-        TRY(stage_in(c, c->st_samples, samples, (size_t)Ns * 2, &ds));
-        TRY(stage_in(c, c->st_u, u, (size_t)Ns, &du));
+        if (dW2 && NH) CK(cudaMemsetAsync(dW2, 0, (size_t)NH * 4 * K * K * 8, c->stream));
+        return NQS_OK;
+    }
+    const int64_t ch = c->grad_chunk > 0 ? c->grad_chunk : Ns;
+    TRY(ensure(c, c->grad_scr, grad_scratch_bytes(c->av, ch < Ns ? ch : Ns)));
+    for (int64_t s0 = 0; s0 < Ns; s0 += ch) {
+        const int64_t n = Ns - s0 < ch ? Ns - s0 : ch;
+        const uint64_t* cs = ds + 2 * s0;
         TRY(reset_dev_error(c));
-        LAUNCH(NQS_STAGE_OTHER, launch_validate(ds, Ns, c->K, c->na, c->nb, (DevError*)c->derr.p, c->stream));
-        TRY(env_pass(c, ds, Ns, true));
-        k_check_psi<<<(unsigned)((Ns + 255) / 256), 256, 0, c->stream>>>((const double*)c->pmant.p, Ns,
-                                                                       (DevError*)c->derr.p);
+        LAUNCH(NQS_STAGE_OTHER, launch_validate(cs, n, c->K, c->na, c->nb, (DevError*)c->derr.p, c->stream));
+        TRY(env_pass(c, cs, n, true, c->av.readout == 1 ? 0 : 1));
+        if (c->av.readout == 1) TRY(rnn_env_pass(c, cs, n));
+        k_check_psi<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>((const double*)c->pmant.p, n,
+                                                                      (DevError*)c->derr.p, s0);
         LAUNCH(NQS_STAGE_OTHER, 1);
         TRY(read_dev_error(c));
         GradArgs g{};
         g.an = c->av;
-        g.samples = ds;
-        g.Ns = Ns;
-        g.u = du;
+        g.samples = cs;
+        g.Ns = n;
+        g.u = du + s0;
         g.Lenv = (const double*)c->Lenv.p; g.Lexp = (const int*)c->Lexp.p;
         g.Renv = (const double*)c->Renv.p; g.Rexp = (const int*)c->Rexp.p;
         g.Hst = (const double*)c->Hst.p; g.Hexp = (const int*)c->Hexp.p;
@@ -1365,12 +1584,191 @@ extern "C" int nqs_grad_log_psi_vjp(nqs_ctx* c, const uint64_t* samples, const d
         g.grad_sites = dg;
         g.grad_W = dW;
         g.grad_b = db;
+        g.grad_W2 = dW2;
+        g.accumulate = s0 > 0;
+        char* scr = (char*)c->grad_scr.p;
+        g.sidx = (int32_t*)scr;
+        g.soff = (int64_t*)(scr + (((size_t)K * n * 4 + 255) & ~(size_t)255));
+        g.part = (double*)((char*)g.soff + (((size_t)K * 5 * 8 + 255) & ~(size_t)255));
         LAUNCH(NQS_STAGE_OTHER, launch_grad_fp64(g, c->stream));
         CK(cudaGetLastError());
     }
+    return NQS_OK;
+}
+
+}  // namespace
+
+extern "C" int nqs_grad_log_psi_vjp2(nqs_ctx* c, const uint64_t* samples, const double* u, int64_t Ns,
+                                     double* grad_sites, double* grad_W, double* grad_b, double* grad_W2)
+{
+    if (!c) return NQS_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    cudaSetDevice(c->device);
+    TRY(check_ready(c, true));
+    if (Ns < 0 || (Ns > 0 && (!samples || !u)))
+        return set_err(c, NQS_ERR_INVALID_ARG, "bad samples / u arguments");
+    if (grad_W2 && c->av.corr != NQS_CORR_ISING)
+        return set_err(c, NQS_ERR_INVALID_ARG, "grad_W2 needs the Ising-RBM correlator");
+    const int K = c->K, D = c->av.D, NH = c->av.n_hidden;
+    const size_t nt = (size_t)c->av.n_edges * 4 * D * D, nw = (size_t)NH * 2 * K, nw2 = (size_t)NH * 4 * K * K;
+    double *dg, *dW, *db, *dW2;
+    bool hg, hW, hb, hW2;
+    TRY(stage_out(c, c->st_out1, grad_sites, nt, &dg, &hg));
+    TRY(stage_out(c, c->st_out2, grad_W, nw, &dW, &hW));
+    TRY(stage_out(c, c->st_out3, grad_b, (size_t)NH, &db, &hb));
+    TRY(stage_out(c, c->st_out4, grad_W2, nw2, &dW2, &hW2));
+    const uint64_t* ds = nullptr;
+    const double* du = nullptr;
+    if (Ns > 0) {
+        TRY(stage_in(c, c->st_samples, samples, (size_t)Ns * 2, &ds));
+        TRY(stage_in(c, c->st_u, u, (size_t)Ns, &du));
+    }
+    TRY(vjp_core(c, ds, du, Ns, dg, dW, db, dW2));
     TRY(copy_back(c, grad_sites, dg, nt, hg));
     TRY(copy_back(c, grad_W, dW, nw, hW));
     TRY(copy_back(c, grad_b, db, (size_t)NH, hb));
+    TRY(copy_back(c, grad_W2, dW2, nw2, hW2));
+    CK(cudaStreamSynchronize(c->stream));
+    return NQS_OK;
+}
+
+extern "C" int nqs_grad_log_psi_vjp(nqs_ctx* c, const uint64_t* samples, const double* u, int64_t Ns,
+                                    double* grad_sites, double* grad_W, double* grad_b)
+{
+    return nqs_grad_log_psi_vjp2(c, samples, u, Ns, grad_sites, grad_W, grad_b, nullptr);
+}
+
+extern "C" int nqs_energy_gradient(nqs_ctx* c, const uint64_t* samples, const double* counts, int64_t Ns,
+                                   double eps, int n_draws, uint64_t seed, int reweighted,
+                                   double* grad_sites, double* grad_W, double* grad_b, double* grad_W2,
+                                   double* e_loc, nqs_energy_summary* out)
+{
+    if (!c) return NQS_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    cudaSetDevice(c->device);
+    TRY(check_ready(c, true));
+    if (Ns <= 0 || !samples) return set_err(c, NQS_ERR_INVALID_ARG, "nqs_energy_gradient needs Ns > 0 samples");
+    if (grad_W2 && c->av.corr != NQS_CORR_ISING)
+        return set_err(c, NQS_ERR_INVALID_ARG, "grad_W2 needs the Ising-RBM correlator");
+    const uint64_t* ds;
+    const double* dc;
+    TRY(stage_in(c, c->st_samples, samples, (size_t)Ns * 2, &ds));
+    TRY(stage_in(c, c->st_counts, counts, (size_t)Ns, &dc));
+    TRY(ensure(c, c->eloc, (size_t)Ns * 8));
+    nqs_energy_summary sm;
+    TRY(nqs_local_energy(c, ds, dc, Ns, eps, n_draws, seed, (double*)c->eloc.p, &sm));
+    TRY(ensure(c, c->u_dev, (size_t)Ns * 8));
+    // u_n = 2 c_n (E_loc(n) - E) / sum c (Eq. egrad); reweighted (Sec. 2.3):
+    // u_n = 2 c_n f~_n^2 (E_loc(n) - E_theta) / sum c, f~^2 = f^2 / B, E_theta = mean of E~
+    LAUNCH(NQS_STAGE_OTHER, launch_energy_weights((const double*)c->eloc.p, dc, c->last_logf, Ns,
+                                                  reweighted ? sm.e_tilde_mean : sm.e_mean, sm.sum_counts,
+                                                  reweighted ? sm.log_B : 0.0, reweighted != 0,
+                                                  (double*)c->u_dev.p, c->stream));
+    CK(cudaGetLastError());
+    const int K = c->K, D = c->av.D, NH = c->av.n_hidden;
+    const size_t nt = (size_t)c->av.n_edges * 4 * D * D, nw = (size_t)NH * 2 * K, nw2 = (size_t)NH * 4 * K * K;
+    double *dg, *dW, *db, *dW2, *de;
+    bool hg, hW, hb, hW2, he;
+    TRY(stage_out(c, c->st_out1, grad_sites, nt, &dg, &hg));
+    TRY(stage_out(c, c->st_out2, grad_W, nw, &dW, &hW));
+    TRY(stage_out(c, c->st_out3, grad_b, (size_t)NH, &db, &hb));
+    TRY(stage_out(c, c->st_out4, grad_W2, nw2, &dW2, &hW2));
+    TRY(stage_out(c, c->st_out0, e_loc, (size_t)Ns, &de, &he));
+    if (de) CK(cudaMemcpyAsync(de, c->eloc.p, (size_t)Ns * 8, cudaMemcpyDeviceToDevice, c->stream));
+    TRY(vjp_core(c, ds, (const double*)c->u_dev.p, Ns, dg, dW, db, dW2));
+    TRY(copy_back(c, grad_sites, dg, nt, hg));
+    TRY(copy_back(c, grad_W, dW, nw, hW));
+    TRY(copy_back(c, grad_b, db, (size_t)NH, hb));
+    TRY(copy_back(c, grad_W2, dW2, nw2, hW2));
+    TRY(copy_back(c, e_loc, de, (size_t)Ns, he));
+    CK(cudaStreamSynchronize(c->stream));
+    if (out) *out = sm;
+    return NQS_OK;
+}
+
+extern "C" int nqs_sample(nqs_ctx* c, int64_t n_samples, uint64_t seed, uint64_t* samples, double* counts,
+                          int64_t capacity, int64_t* n_unique)
+{
+    if (!c) return NQS_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    cudaSetDevice(c->device);
+    TRY(check_ready(c, true));
+    if (c->av.readout != 1)
+        return set_err(c, NQS_ERR_STATE, "nqs_sample needs the normalised readout (nqs_set_readout)");
+    if (n_samples < 0 || !n_unique || (capacity > 0 && (!samples || !counts)))
+        return set_err(c, NQS_ERR_INVALID_ARG, "bad n_samples / outputs");
+    *n_unique = 0;
+    if (n_samples == 0) return NQS_OK;
+    const int K = c->K, D = c->av.D;
+    c->smp_pa.resize(K + 1); c->smp_pb.resize(K + 1); c->smp_off.resize(K + 1);
+    c->smp_cnt.resize(K + 1); c->smp_par.resize(K + 1); c->smp_cell.resize(K + 1);
+    // level 0: the empty prefix holds every draw
+    int64_t n = 1;
+    TRY(ensure(c, c->smp_pa[0], 8)); TRY(ensure(c, c->smp_pb[0], 8));
+    TRY(ensure(c, c->smp_off[0], 8)); TRY(ensure(c, c->smp_cnt[0], 8));
+    CK(cudaMemsetAsync(c->smp_pa[0].p, 0, 8, c->stream));
+    CK(cudaMemsetAsync(c->smp_pb[0].p, 0, 8, c->stream));
+    CK(cudaMemsetAsync(c->smp_off[0].p, 0, 8, c->stream));
+    CK(cudaMemcpyAsync(c->smp_cnt[0].p, &n_samples, 8, cudaMemcpyHostToDevice, c->stream));
+    TRY(ensure(c, c->smp_tabs, (size_t)2 * (K + 1) * sizeof(void*)));
+    std::vector<const void*> tabs((size_t)2 * (K + 1), nullptr);
+    for (int i = 0; i < K; ++i) {
+        // tables of the parent links and cells of levels 1..i
+        for (int l = 1; l <= i; ++l) { tabs[l] = c->smp_par[l].p; tabs[K + 1 + l] = c->smp_cell[l].p; }
+        CK(cudaMemcpyAsync(c->smp_tabs.p, tabs.data(), tabs.size() * sizeof(void*), cudaMemcpyHostToDevice,
+                           c->stream));
+        TRY(ensure(c, c->smp_cand, (size_t)n * 4 * D * 8));
+        TRY(ensure(c, c->smp_ccnt, (size_t)n * 8 * 8));          // counts, then child flags
+        TRY(ensure(c, c->smp_cpos, (size_t)(n * 4 + 1) * 8));
+        TRY(ensure(c, c->site_scan, (size_t)scan_i64_tmp_elems(n * 4) * 8));
+        SampleLevel L{};
+        L.an = c->av;
+        L.level = i;
+        L.n_nodes = n;
+        L.pa = (const uint64_t*)c->smp_pa[i].p; L.pb = (const uint64_t*)c->smp_pb[i].p;
+        L.off = (const int64_t*)c->smp_off[i].p; L.cnt = (const int64_t*)c->smp_cnt[i].p;
+        L.parents = (const int32_t* const*)c->smp_tabs.p;
+        L.cells = (const double* const*)((const void* const*)c->smp_tabs.p + (K + 1));
+        L.cand = (double*)c->smp_cand.p;
+        L.child_cnt = (int64_t*)c->smp_ccnt.p;
+        L.child_flag = (int64_t*)c->smp_ccnt.p + n * 4;
+        L.seed = seed;
+        LAUNCH(NQS_STAGE_OTHER, launch_sample_level(L, c->stream));
+        // child positions: exclusive scan of the flags (prefix order), total = children
+        LAUNCH(NQS_STAGE_OTHER, launch_scan_i64_wide(L.child_flag, (int64_t*)c->smp_cpos.p, n * 4,
+                                                     (int64_t*)c->site_scan.p, c->stream));
+        int64_t m = 0;
+        CK(cudaMemcpyAsync(&m, (const int64_t*)c->smp_cpos.p + n * 4, 8, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));      // also keeps `tabs` alive until copied
+        if (m <= 0) return set_err(c, NQS_ERR_INVALID_ARG, "no local state is allowed at vertex %d", i);
+        TRY(ensure(c, c->smp_pa[i + 1], (size_t)m * 8)); TRY(ensure(c, c->smp_pb[i + 1], (size_t)m * 8));
+        TRY(ensure(c, c->smp_off[i + 1], (size_t)m * 8)); TRY(ensure(c, c->smp_cnt[i + 1], (size_t)m * 8));
+        TRY(ensure(c, c->smp_par[i + 1], (size_t)m * 4)); TRY(ensure(c, c->smp_cell[i + 1], (size_t)m * D * 8));
+        SampleChildren S{};
+        S.level = i; S.D = D; S.n_nodes = n;
+        S.pa = L.pa; S.pb = L.pb; S.off = L.off;
+        S.cand = L.cand; S.child_cnt = L.child_cnt; S.child_pos = (const int64_t*)c->smp_cpos.p;
+        S.qa = (uint64_t*)c->smp_pa[i + 1].p; S.qb = (uint64_t*)c->smp_pb[i + 1].p;
+        S.qoff = (int64_t*)c->smp_off[i + 1].p; S.qcnt = (int64_t*)c->smp_cnt[i + 1].p;
+        S.qparent = (int32_t*)c->smp_par[i + 1].p; S.qcell = (double*)c->smp_cell[i + 1].p;
+        LAUNCH(NQS_STAGE_OTHER, launch_sample_children(S, c->stream));
+        CK(cudaGetLastError());
+        n = m;
+    }
+    *n_unique = n;
+    if (capacity < n)
+        return set_err(c, NQS_ERR_INVALID_ARG, "capacity %lld < %lld unique samples (n_unique written)",
+                       (long long)capacity, (long long)n);
+    uint64_t* dsm;
+    double* dcn;
+    bool hs, hc;
+    TRY(stage_out(c, c->st_out0, samples, (size_t)n * 2, &dsm, &hs));
+    TRY(stage_out(c, c->st_out1, counts, (size_t)n, &dcn, &hc));
+    LAUNCH(NQS_STAGE_OTHER, launch_sample_output((const uint64_t*)c->smp_pa[K].p, (const uint64_t*)c->smp_pb[K].p,
+                                                 (const int64_t*)c->smp_cnt[K].p, n, dsm, dcn, c->stream));
+    CK(cudaGetLastError());
+    TRY(copy_back(c, samples, dsm, (size_t)n * 2, hs));
+    TRY(copy_back(c, counts, dcn, (size_t)n, hc));
     CK(cudaStreamSynchronize(c->stream));
     return NQS_OK;
 }

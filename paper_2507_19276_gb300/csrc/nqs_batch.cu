@@ -64,8 +64,13 @@ extern "C" int nqs_local_energy_batch(nqs_ctx* const* ctxs, int n_sys, nqs_batch
             if (q >= n_sys) break;
             const int i = order[(size_t)q];
             nqs_batch_item& it = items[i];
-            it.status = nqs_local_energy(ctxs[i], it.samples, it.counts, it.n_samples, it.det_threshold,
-                                         it.n_draws, it.philox_seed, it.e_loc, it.summary);
+            if (it.grad_sites || it.grad_W || it.grad_b)
+                it.status = nqs_energy_gradient(ctxs[i], it.samples, it.counts, it.n_samples, it.det_threshold,
+                                                it.n_draws, it.philox_seed, it.reweighted, it.grad_sites,
+                                                it.grad_W, it.grad_b, nullptr, it.e_loc, it.summary);
+            else
+                it.status = nqs_local_energy(ctxs[i], it.samples, it.counts, it.n_samples, it.det_threshold,
+                                             it.n_draws, it.philox_seed, it.e_loc, it.summary);
             // leave nothing in flight on this system's stream
             if (it.status == NQS_OK) it.status = nqs::ctx_sync(ctxs[i]);
         }

@@ -211,18 +211,13 @@ __global__ void k_env_fp64(EnvArgs a)
         }
     }
 
-    // RBM angles theta_k(n) = b_k + sum_s W[k][s] n_s and log f(n)
+    // correlator angles theta_k(n) (Sec. 2.3) and log|f(n)|
     const int NH = a.an.n_hidden;
     if (NH > 0) {
         for (int k = threadIdx.x; k < NH; k += blockDim.x) {
-            const double* Wk = a.an.W + (size_t)k * 2 * K;
-            double th = a.an.b[k];
-            for (int p = 0; p < K; ++p) {
-                if ((na >> p) & 1ull) th += __ldg(Wk + 2 * p);
-                if ((nb >> p) & 1ull) th += __ldg(Wk + 2 * p + 1);
-            }
+            const double th = corr_theta(a.an, k, na, nb);
             a.theta[(size_t)s * NH + k] = th;
-            a.lc[(size_t)s * NH + k] = log2cosh(th);
+            a.lc[(size_t)s * NH + k] = corr_log_factor(a.an.corr, th);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -306,25 +301,15 @@ __device__ __forceinline__ int64_t find_sample(const int64_t* base, int64_t Ns, 
     return lo;
 }
 
-// RBM ratio f(m)/f(n) for the spin orbitals flipped between n and m (one warp).
+// Correlator ratio f(m)/f(n) (one warp): its log magnitude and sign.
 __device__ double rbm_log_ratio_warp(const AnsatzView& an, int64_t s, const double* theta,
                                      const double* lc, uint64_t na, uint64_t nb, uint64_t ma,
-                                     uint64_t mb, int lane)
+                                     uint64_t mb, int lane, double* sign)
 {
-    const int NH = an.n_hidden;
-    if (NH == 0) return 0.0;
-    int fs[4], sg[4], nf = 0;
-    uint64_t da = na ^ ma, db = nb ^ mb;
-    while (da && nf < 4) { int p = __ffsll((long long)da) - 1; fs[nf] = 2 * p; sg[nf] = ((ma >> p) & 1ull) ? 1 : -1; ++nf; da &= da - 1; }
-    while (db && nf < 4) { int p = __ffsll((long long)db) - 1; fs[nf] = 2 * p + 1; sg[nf] = ((mb >> p) & 1ull) ? 1 : -1; ++nf; db &= db - 1; }
-    double acc = 0.0;
-    const int K2 = 2 * an.K;
-    for (int k = lane; k < NH; k += 32) {
-        double d = 0.0;
-        for (int f = 0; f < nf; ++f) d += sg[f] * __ldg(an.W + (size_t)k * K2 + fs[f]);
-        acc += log2cosh(theta[(size_t)s * NH + k] + d) - lc[(size_t)s * NH + k];
-    }
-    return warp_sum_f64(acc);
+    int neg;
+    const double lr = corr_log_ratio_warp(an, s, theta, lc, na, nb, ma, mb, lane, &neg);
+    *sign = neg ? -1.0 : 1.0;
+    return lr;
 }
 
 __global__ void k_amp_chain_fp64(AmpArgs a)
@@ -414,8 +399,9 @@ __global__ void k_amp_chain_fp64(AmpArgs a)
         __syncthreads();
     }
     for (int r = warp; r < nr; r += nw) {
-        const double lr = rbm_log_ratio_warp(a.an, s, a.theta, a.lc, na, nb, info[r].ma, info[r].mb, lane);
-        if (lane == 0) info[r].tn = info[r].coef * info[r].tn * exp(lr);
+        double fsg;
+        const double lr = rbm_log_ratio_warp(a.an, s, a.theta, a.lc, na, nb, info[r].ma, info[r].mb, lane, &fsg);
+        if (lane == 0) info[r].tn = info[r].coef * info[r].tn * (fsg * exp(lr));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -510,11 +496,12 @@ __global__ void k_amp_graph_fp64(AmpArgs a)
     const double mant_n = a.psi_mant[s];
     const int exp_n = a.psi_exp[s];
     for (int r = warp; r < nr; r += nw) {
-        const double lr = rbm_log_ratio_warp(a.an, s, a.theta, a.lc, na, nb, info[r].ma, info[r].mb, lane);
+        double fsg;
+        const double lr = rbm_log_ratio_warp(a.an, s, a.theta, a.lc, na, nb, info[r].ma, info[r].mb, lane, &fsg);
         if (lane == 0) {
             const double mm = S[((size_t)r * K + K - 1) * D];
             const double tn = ldexp(mm / mant_n, SX[r * K + K - 1] - exp_n);
-            info[r].tn = info[r].coef * tn * exp(lr);
+            info[r].tn = info[r].coef * tn * (fsg * exp(lr));
         }
     }
     __syncthreads();
@@ -607,17 +594,15 @@ __global__ void k_full_amp_fp64(AnsatzView an, const uint64_t* dets, int64_t n, 
     __syncthreads();
     const double mant = sh[33];
     __syncthreads();
-    // RBM log f
+    // correlator log|f| and the parity of its negative factors (cos forms)
     double lf = 0.0;
+    int odd = 0;
     for (int k = threadIdx.x; k < an.n_hidden; k += blockDim.x) {
-        const double* Wk = an.W + (size_t)k * 2 * K;
-        double th = an.b[k];
-        for (int p = 0; p < K; ++p) {
-            if ((na >> p) & 1ull) th += __ldg(Wk + 2 * p);
-            if ((nb >> p) & 1ull) th += __ldg(Wk + 2 * p + 1);
-        }
-        lf += log2cosh(th);
+        const double th = corr_theta(an, k, na, nb);
+        lf += corr_log_factor(an.corr, th);
+        if (an.corr != 0) odd ^= cos(th) < 0.0;
     }
+    const int nodd = __syncthreads_count(odd);
     lf = warp_sum_f64(lf);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = lf;
     __syncthreads();
@@ -625,9 +610,9 @@ __global__ void k_full_amp_fp64(AnsatzView an, const uint64_t* dets, int64_t n, 
         double l = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) l += sh[w];
         const double m = mant;
-        if (m == 0.0) { sign[id] = 0; log_abs[id] = -INFINITY; }
+        if (m == 0.0 || l == -INFINITY) { sign[id] = 0; log_abs[id] = -INFINITY; }
         else {
-            sign[id] = m < 0 ? -1 : 1;
+            sign[id] = ((m < 0) ^ (nodd & 1)) ? -1 : 1;
             log_abs[id] = log(fabs(m)) + (double)ex[K - 1] * 0.69314718055994530942 + l;
         }
     }
@@ -647,84 +632,6 @@ int launch_full_amp_fp64(const AnsatzView& an, const uint64_t* dets, int64_t n, 
         ++launches;
     }
     return launches;
-}
-
-// ---------------------------------------------------------------------------
-// Gradient: grad[e][sigma][a][b] = sum_{n: sigma_i(n)=sigma} u_n / psi_TN(n)
-//           * g_i(n)[a] h_j(n)[b];  RBM: u_n tanh(theta_k) (n_s or 1)
-// Deterministic: every thread sums over samples in index order.
-// ---------------------------------------------------------------------------
-
-__global__ void k_grad_tn_fp64(GradArgs a)
-{
-    const int D = a.an.D, K = a.an.K;
-    const int e = blockIdx.y;
-    const int64_t ab = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (ab >= (int64_t)D * D) return;
-    const int ra = (int)(ab / D), cb = (int)(ab - (int64_t)ra * D);
-    int i, j;
-    if (a.an.chain) { i = e; j = e - 1; }
-    else {
-        j = a.an.pred_idx[e];
-        int lo = 0;
-        while (a.an.pred_ptr[lo + 1] <= e) ++lo;
-        i = lo;
-    }
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t s = 0; s < a.Ns; ++s) {
-        const uint64_t na = a.samples[2 * s], nb = a.samples[2 * s + 1];
-        const int sg = sigma_at(na, nb, i);
-        double g, h;
-        int eg, eh;
-        if (a.an.chain) {
-            g = a.Renv[((size_t)s * (K + 1) + i + 1) * D + ra];
-            eg = a.Rexp[(size_t)s * (K + 1) + i + 1];
-            h = a.Lenv[((size_t)s * (K + 1) + i) * D + cb];
-            eh = a.Lexp[(size_t)s * (K + 1) + i];
-        } else {
-            g = a.Gst[((size_t)s * K + i) * D + ra];
-            eg = a.Gexp[(size_t)s * K + i];
-            if (j < 0) { h = cb == 0 ? 1.0 : 0.0; eh = 0; }
-            else { h = a.Hst[((size_t)s * K + j) * D + cb]; eh = a.Hexp[(size_t)s * K + j]; }
-        }
-        const double w = ldexp(a.u[s] / a.psi_mant[s], eg + eh - a.psi_exp[s]);
-        acc[sg] += w * g * h;
-    }
-    for (int sg = 0; sg < 4; ++sg) a.grad_sites[(((size_t)e * 4 + sg) * D + ra) * D + cb] = acc[sg];
-}
-
-__global__ void k_grad_rbm_fp64(GradArgs a)
-{
-    const int k = blockIdx.x, K = a.an.K, NH = a.an.n_hidden;
-    const int col = threadIdx.x;             // 0..2K-1: W[k][col]; 2K: b[k]
-    if (col > 2 * K) return;
-    double acc = 0.0;
-    for (int64_t s = 0; s < a.Ns; ++s) {
-        const double t = tanh(a.theta[(size_t)s * NH + k]);
-        if (col == 2 * K) acc += a.u[s] * t;
-        else {
-            const uint64_t w = a.samples[2 * s + (col & 1)];
-            if ((w >> (col >> 1)) & 1ull) acc += a.u[s] * t;
-        }
-    }
-    if (col == 2 * K) { if (a.grad_b) a.grad_b[k] = acc; }
-    else if (a.grad_W) a.grad_W[(size_t)k * 2 * K + col] = acc;
-}
-
-int launch_grad_fp64(const GradArgs& a, cudaStream_t st)
-{
-    const int D = a.an.D;
-    int n = 0;
-    if (a.grad_sites) {
-        dim3 grid((unsigned)(((int64_t)D * D + 255) / 256), (unsigned)a.an.n_edges);
-        k_grad_tn_fp64<<<grid, 256, 0, st>>>(a);
-        ++n;
-    }
-    if (a.an.n_hidden > 0 && (a.grad_W || a.grad_b)) {
-        k_grad_rbm_fp64<<<a.an.n_hidden, ((2 * a.an.K + 1 + 31) / 32) * 32, 0, st>>>(a);
-        ++n;
-    }
-    return n;
 }
 
 }  // namespace nqs

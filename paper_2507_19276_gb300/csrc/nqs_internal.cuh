@@ -237,7 +237,23 @@ __device__ __forceinline__ uint64_t weight_of(double H, int shift)
     return q + ((M & ((1ull << s) - 1ull)) != 0 ? 1ull : 0ull);
 }
 
-// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): first output word.
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): first output word for
+// counter (c0, c1, c2, 0) and key (k0, 0).
+__device__ __forceinline__ uint64_t philox_first4(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t k0)
+{
+    uint64_t x0 = c0, x1 = c1, x2 = c2, x3 = 0, k1 = 0;
+    #pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B97F4A7C15ull; k1 += 0xBB67AE8584CAA73Bull; }
+        const uint64_t lo0 = 0xD2E7470EE14C6C93ull * x0, hi0 = __umul64hi(0xD2E7470EE14C6C93ull, x0);
+        const uint64_t lo1 = 0xCA5A826395121157ull * x2, hi1 = __umul64hi(0xCA5A826395121157ull, x2);
+        const uint64_t y0 = hi1 ^ x1 ^ k0, y2 = hi0 ^ x3 ^ k1;
+        x0 = y0; x1 = lo1; x2 = y2; x3 = lo0;
+    }
+    return x0;
+}
+
+// The same with counter (c0, c1, 0, 0): the draws of the stochastic part.
 __device__ __forceinline__ uint64_t philox_first(uint64_t c0, uint64_t c1, uint64_t k0)
 {
     uint64_t x0 = c0, x1 = c1, x2 = 0, x3 = 0, k1 = 0;

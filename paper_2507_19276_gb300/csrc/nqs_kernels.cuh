@@ -137,6 +137,20 @@ struct AnsatzView {
     int n_hidden;
     const double* W;                     // [n_hidden][2K]
     const double* b;                     // [n_hidden]
+    // readout (Sec. 2.2): 0 linear psi_TN = (h_{K-1})_0; 1 the normalised
+    // MPS-RNN / BDG-RNN: candidate cells h_i^s = sum_e M_e^s h_j + v_i^s,
+    // P_i(s) = sum_a eta_i[a] (h_i^s[a])^2 normalised over the local states
+    // the N_alpha / N_beta constraint allows, sign of w_i . h_i^{s_i} + c_i
+    int readout;
+    int mask_na, mask_nb;                // the constraint's electron counts (mask_na < 0: none)
+    const double* rv;                    // [K][4][D]
+    const double* reta;                  // [K][D]
+    const double* rw;                    // [K][D]
+    const double* rc;                    // [K]
+    // correlator (Sec. 2.3): 0 prod 2cosh(theta_k); 1 cos-RBM prod cos(theta_k);
+    // 2 Ising-RBM, theta_k + 1/2 sum_{s,t} W2[k][s][t] n_s n_t inside the cos
+    int corr;
+    const double* W2;                    // [n_hidden][2K][2K] (corr 2)
 };
 
 struct EnvArgs {
@@ -205,7 +219,187 @@ struct GradArgs {
     double* grad_sites;                   // [E][4][D][D]
     double* grad_W;
     double* grad_b;
+    double* grad_W2;                      // [n_hidden][2K][2K] (Ising-RBM; NULL: skip)
+    int accumulate;                       // 0: overwrite the outputs; 1: add to them
+    // scratch of the tensor part (see grad_scratch_bytes): per vertex the
+    // sample indices grouped by local state, and per chunk of samples the
+    // partial outer-product sums
+    int32_t* sidx;                        // [K][Ns]
+    int64_t* soff;                        // [K][5]
+    double* part;                         // [n_chunks][E][4][D][D]
 };
+// scratch bytes of the tensor-part gradient for Ns samples
+size_t grad_scratch_bytes(const AnsatzView& an, int64_t Ns);
 int launch_grad_fp64(const GradArgs& a, cudaStream_t st);
+
+// d log|f| / d theta_k of the correlator: tanh (2cosh), -tan (cos, Ising)
+__device__ __forceinline__ double corr_dlog(int corr, double theta)
+{
+    return corr == 0 ? tanh(theta) : -tan(theta);
+}
+
+// log|factor_k| of the correlator at angle theta: log 2cosh or log|cos|
+__device__ __forceinline__ double corr_log_factor(int corr, double theta)
+{
+    return corr == 0 ? log2cosh(theta) : log(fabs(cos(theta)));
+}
+
+// theta_k(n) = b_k + sum_s W[k][s] n_s (+ 1/2 sum_{s,t} W2[k][s][t] n_s n_t for
+// the Ising-RBM), spin orbitals s = 2p + spin
+__device__ __forceinline__ double corr_theta(const AnsatzView& an, int k, uint64_t na, uint64_t nb)
+{
+    const int K = an.K, N = 2 * K;
+    const double* Wk = an.W + (size_t)k * N;
+    double th = an.b[k];
+    for (int p = 0; p < K; ++p) {
+        if ((na >> p) & 1ull) th += __ldg(Wk + 2 * p);
+        if ((nb >> p) & 1ull) th += __ldg(Wk + 2 * p + 1);
+    }
+    if (an.corr == 2) {
+        const double* W2 = an.W2 + (size_t)k * N * N;
+        double q = 0.0;
+        for (int s = 0; s < N; ++s) {
+            if (!(((s & 1) ? nb : na) >> (s >> 1) & 1ull)) continue;
+            for (int t = 0; t < N; ++t)
+                if ((((t & 1) ? nb : na) >> (t >> 1)) & 1ull) q += __ldg(W2 + (size_t)s * N + t);
+        }
+        th += 0.5 * q;
+    }
+    return th;
+}
+
+// Ising-RBM: 1/2 sum_{s,t in occ(m)} W2 - 1/2 sum_{s,t in occ(n)} W2 for the
+// flips fs[] (sign +1 created, -1 removed): the cross terms with the spin
+// orbitals occupied in both, and the pairs inside the created / removed sets.
+__device__ __forceinline__ double ising_dq(const AnsatzView& an, int k, uint64_t na, uint64_t nb,
+                                           const int* fs, const int* sg, int nf)
+{
+    const int N = 2 * an.K;
+    const double* Wk = an.W2 + (size_t)k * N * N;
+    uint64_t ra = 0, rb = 0;                 // removed spin orbitals
+    for (int f = 0; f < nf; ++f)
+        if (sg[f] < 0) { if (fs[f] & 1) rb |= 1ull << (fs[f] >> 1); else ra |= 1ull << (fs[f] >> 1); }
+    double q = 0.0;
+    for (int f = 0; f < nf; ++f) {
+        const int s = fs[f];
+        double x = 0.0;
+        for (uint64_t w = na & ~ra; w; w &= w - 1) {
+            const int t = 2 * (__ffsll((long long)w) - 1);
+            x += __ldg(Wk + (size_t)s * N + t) + __ldg(Wk + (size_t)t * N + s);
+        }
+        for (uint64_t w = nb & ~rb; w; w &= w - 1) {
+            const int t = 2 * (__ffsll((long long)w) - 1) + 1;
+            x += __ldg(Wk + (size_t)s * N + t) + __ldg(Wk + (size_t)t * N + s);
+        }
+        q += sg[f] * x;
+        for (int g = 0; g < nf; ++g)
+            if (sg[g] == sg[f]) q += sg[f] * __ldg(Wk + (size_t)s * N + fs[g]);
+    }
+    return 0.5 * q;
+}
+
+// log|f(m) / f(n)| for the spin orbitals flipped between n and m, one warp,
+// the result on every lane; *neg = 1 when the ratio is negative (cos forms).
+__device__ __forceinline__ double corr_log_ratio_warp(const AnsatzView& an, int64_t s,
+                                                      const double* theta, const double* lc,
+                                                      uint64_t na, uint64_t nb, uint64_t ma,
+                                                      uint64_t mb, int lane, int* neg)
+{
+    *neg = 0;
+    const int NH = an.n_hidden;
+    if (NH == 0) return 0.0;
+    int fs[4], sg[4], nf = 0;
+    uint64_t da = na ^ ma, db = nb ^ mb;
+    while (da && nf < 4) { const int p = __ffsll((long long)da) - 1; fs[nf] = 2 * p; sg[nf] = ((ma >> p) & 1ull) ? 1 : -1; ++nf; da &= da - 1; }
+    while (db && nf < 4) { const int p = __ffsll((long long)db) - 1; fs[nf] = 2 * p + 1; sg[nf] = ((mb >> p) & 1ull) ? 1 : -1; ++nf; db &= db - 1; }
+    const int K2 = 2 * an.K;
+    double acc = 0.0;
+    int odd = 0;
+    for (int k = lane; k < NH; k += 32) {
+        double d = 0.0;
+        for (int f = 0; f < nf; ++f) d += sg[f] * __ldg(an.W + (size_t)k * K2 + fs[f]);
+        if (an.corr == 2) d += ising_dq(an, k, na, nb, fs, sg, nf);
+        const double th = theta[(size_t)s * NH + k];
+        if (an.corr == 0) {
+            acc += log2cosh(th + d) - lc[(size_t)s * NH + k];
+        } else {
+            const double cm = cos(th + d);
+            acc += log(fabs(cm)) - lc[(size_t)s * NH + k];
+            odd ^= (cm < 0.0) ^ (cos(th) < 0.0);
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        acc += __shfl_xor_sync(kFull, acc, o);
+        odd ^= __shfl_xor_sync(kFull, odd, o);
+    }
+    *neg = odd;
+    return acc;
+}
+
+// ---- normalised readout and autoregressive sampling (nqs_rnn.cu) -----------
+
+struct RnnEnvArgs {
+    AnsatzView an;
+    const uint64_t* samples;
+    int64_t Ns;
+    double* cells;                        // [Ns][K][D] chosen cells h_i(n)
+    double* lp;                           // [Ns][K] 1/2 log P~_i(s_i(n))
+    int8_t* sg;                           // [Ns][K] sign of w_i . h_i + c_i
+    const double* log_f;                  // [Ns] log|f(n)| (from the correlator pass)
+    double* psi_mant;                     // [Ns] sign of Phi(n) f(n) (0: psi(n) = 0)
+    int* psi_exp;                         // [Ns] 0
+};
+int launch_rnn_env(const RnnEnvArgs& a, cudaStream_t st);
+
+struct RnnAmpArgs {
+    AnsatzView an;
+    HamView h;
+    const uint64_t* samples;
+    int64_t Ns;
+    RowSet rows;
+    int rows_per_block;
+    const double* cells; const double* lp; const int8_t* sg;
+    const double* theta; const double* lc;
+    double* partial;                      // [chunks]
+    int64_t* span;                        // [chunks] vertices recomputed per chunk
+};
+int rnn_rows_per_block();
+int launch_rnn_amp(const RnnAmpArgs& a, cudaStream_t st);
+int launch_rnn_full(const AnsatzView& an, const uint64_t* dets, int64_t n, double* log_abs,
+                    int8_t* sign, cudaStream_t st);
+
+// breadth-first autoregressive sampling, one level (vertex i) per call pair.
+// A node of level l holds a prefix of the local states of vertices < l; the
+// cell of vertex j of a level-l node lives at level j + 1, reached through
+// the parent links of levels l, l-1, ..., j + 2.
+struct SampleLevel {
+    AnsatzView an;
+    int level;                            // vertex i (nodes of level i)
+    int64_t n_nodes;
+    const uint64_t* pa; const uint64_t* pb;   // [n] prefix words
+    const int64_t* off; const int64_t* cnt;   // [n] draw offsets and counts
+    const int32_t* const* parents;        // device table [K+1]: level l >= 1 -> parent index per node
+    const double* const* cells;           // device table [K+1]: level l >= 1 -> [nodes][D], vertex l-1
+    double* cand;                         // [n][4][D] candidate cells of vertex i
+    int64_t* child_cnt;                   // [n][4] draws per local state
+    int64_t* child_flag;                  // [n][4] 1 where a child exists (its draws > 0)
+    uint64_t seed;
+};
+int launch_sample_level(const SampleLevel& a, cudaStream_t st);
+struct SampleChildren {
+    int level, D;
+    int64_t n_nodes;
+    const uint64_t* pa; const uint64_t* pb; const int64_t* off;
+    const double* cand; const int64_t* child_cnt;
+    const int64_t* child_pos;             // [n*4+1] exclusive scan of the child flags
+    uint64_t* qa; uint64_t* qb; int64_t* qoff; int64_t* qcnt; int32_t* qparent; double* qcell;
+};
+int launch_sample_children(const SampleChildren& a, cudaStream_t st);
+int launch_sample_output(const uint64_t* pa, const uint64_t* pb, const int64_t* cnt, int64_t n,
+                         uint64_t* dets, double* counts, cudaStream_t st);
+// u_n of the energy gradient (nqs_grad.cu)
+int launch_energy_weights(const double* e_loc, const double* counts, const double* log_f, int64_t Ns,
+                          double e_mean, double sum_c, double log_B, bool reweighted, double* u,
+                          cudaStream_t st);
 
 }  // namespace nqs

@@ -32,10 +32,17 @@ class NQSError(RuntimeError):
         self.status = status
 
 
+NQS_CORR_COSH = 0
+NQS_CORR_COS = 1
+NQS_CORR_ISING = 2
+
+
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("timing", C.c_int),
                 ("sample_index_base", C.c_int64), ("energy_tolerance", C.c_double),
-                ("reserved", C.c_int * 10)]
+                ("grad_chunk", C.c_int), ("audit_samples", C.c_int),
+                ("tile_blocks_per_sm", C.c_int), ("table_mb", C.c_int),
+                ("reserved", C.c_int * 6)]
 
 
 N_STAGES = 9
@@ -47,7 +54,8 @@ class EnergySummary(C.Structure):
                 ("e_tilde_mean", C.c_double), ("n_conn", C.c_int64), ("n_det", C.c_int64),
                 ("n_draw_unique", C.c_int64), ("n_amplitudes", C.c_int64),
                 ("span_sites", C.c_int64), ("matvecs", C.c_int64), ("n_refined", C.c_int64),
-                ("e_error_bound", C.c_double)]
+                ("e_error_bound", C.c_double), ("n_audited", C.c_int64),
+                ("audit_rel_error", C.c_double), ("error_factor", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -56,7 +64,9 @@ class EnergySummary(C.Structure):
 class BatchItem(C.Structure):
     _fields_ = [("samples", C.c_void_p), ("counts", C.c_void_p), ("n_samples", C.c_int64),
                 ("det_threshold", C.c_double), ("n_draws", C.c_int), ("philox_seed", C.c_uint64),
-                ("e_loc", C.c_void_p), ("summary", C.POINTER(EnergySummary)), ("status", C.c_int)]
+                ("e_loc", C.c_void_p), ("summary", C.POINTER(EnergySummary)), ("status", C.c_int),
+                ("reweighted", C.c_int), ("grad_sites", C.c_void_p), ("grad_W", C.c_void_p),
+                ("grad_b", C.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -89,7 +99,13 @@ def load():
             "nqs_draws_noalloc": [vp, vp, i64, dbl, C.c_int, u64, vp, vp],
             "nqs_local_energy": [vp, vp, vp, i64, dbl, C.c_int, u64, vp, C.POINTER(EnergySummary)],
             "nqs_grad_log_psi_vjp": [vp, vp, vp, i64, vp, vp, vp],
+            "nqs_grad_log_psi_vjp2": [vp, vp, vp, i64, vp, vp, vp, vp],
+            "nqs_energy_gradient": [vp, vp, vp, i64, dbl, C.c_int, u64, C.c_int, vp, vp, vp, vp, vp,
+                                    C.POINTER(EnergySummary)],
             "nqs_local_energy_batch": [C.POINTER(vp), C.c_int, C.POINTER(BatchItem), C.c_int],
+            "nqs_set_readout": [vp, vp, vp, vp, vp, C.c_int],
+            "nqs_set_correlator": [vp, C.c_int, vp],
+            "nqs_sample": [vp, i64, u64, vp, vp, i64, C.POINTER(i64)],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
@@ -105,7 +121,8 @@ def exported_symbols():
     return ["nqs_create", "nqs_destroy", "nqs_last_error", "nqs_set_options", "nqs_stage_times",
             "nqs_set_hamiltonian", "nqs_set_ansatz", "nqs_connected", "nqs_amplitude",
             "nqs_draws", "nqs_draws_noalloc", "nqs_local_energy", "nqs_local_energy_batch",
-            "nqs_grad_log_psi_vjp"]
+            "nqs_grad_log_psi_vjp", "nqs_grad_log_psi_vjp2", "nqs_energy_gradient", "nqs_set_readout",
+            "nqs_set_correlator", "nqs_sample"]
 
 
 def _ptr(x):
@@ -148,13 +165,52 @@ def nqs_last_error(ctx) -> str:
 
 
 def nqs_set_options(ctx, precision: int, timing: int = 0, sample_index_base: int = 0,
-                    energy_tolerance: float = 0.0):
+                    energy_tolerance: float = 0.0, grad_chunk: int = 0, audit_samples: int = 0,
+                    tile_blocks_per_sm: int = 0, table_mb: int = 0):
     o = Options()
     o.precision = precision
     o.timing = timing
     o.sample_index_base = sample_index_base
     o.energy_tolerance = energy_tolerance
+    o.grad_chunk = grad_chunk
+    o.audit_samples = audit_samples
+    o.tile_blocks_per_sm = tile_blocks_per_sm
+    o.table_mb = table_mb
     _check(ctx, load().nqs_set_options(ctx, C.byref(o)))
+
+
+def nqs_set_readout(ctx, v, eta, w, c, constrained=1):
+    _check(ctx, load().nqs_set_readout(ctx, _ptr(v), _ptr(eta), _ptr(w), _ptr(c), int(constrained)))
+
+
+def nqs_set_correlator(ctx, kind, W2=None):
+    _check(ctx, load().nqs_set_correlator(ctx, int(kind), _ptr(W2)))
+
+
+def nqs_sample(ctx, n_samples, seed, samples, counts, capacity):
+    """Returns the number of unique samples (also when capacity is too small,
+    in which case NQSError is raised after the count is known)."""
+    n = C.c_int64(0)
+    st = load().nqs_sample(ctx, int(n_samples), int(seed), _ptr(samples), _ptr(counts), int(capacity),
+                           C.byref(n))
+    if st != NQS_OK:
+        err = NQSError(st, nqs_last_error(ctx))
+        err.n_unique = n.value
+        raise err
+    return n.value
+
+
+def nqs_grad_log_psi_vjp2(ctx, samples, u, Ns, grad_sites, grad_W, grad_b, grad_W2):
+    _check(ctx, load().nqs_grad_log_psi_vjp2(ctx, _ptr(samples), _ptr(u), Ns, _ptr(grad_sites),
+                                             _ptr(grad_W), _ptr(grad_b), _ptr(grad_W2)))
+
+
+def nqs_energy_gradient(ctx, samples, counts, Ns, eps, n_draws, seed, reweighted, grad_sites, grad_W,
+                        grad_b, grad_W2, e_loc=None, summary=None):
+    _check(ctx, load().nqs_energy_gradient(ctx, _ptr(samples), _ptr(counts), Ns, float(eps), n_draws, seed,
+                                           int(reweighted), _ptr(grad_sites), _ptr(grad_W), _ptr(grad_b),
+                                           _ptr(grad_W2), _ptr(e_loc),
+                                           C.byref(summary) if summary is not None else None))
 
 
 def nqs_stage_times(ctx, ms, launches, n=N_STAGES):
@@ -248,8 +304,10 @@ class Context:
             pass
 
     def set_precision(self, precision: int, timing: bool = False, sample_index_base: int = 0,
-                      energy_tolerance: float = 0.0):
-        nqs_set_options(self.h, precision, int(bool(timing)), sample_index_base, energy_tolerance)
+                      energy_tolerance: float = 0.0, grad_chunk: int = 0, audit_samples: int = 0,
+                      tile_blocks_per_sm: int = 0, table_mb: int = 0):
+        nqs_set_options(self.h, precision, int(bool(timing)), sample_index_base, energy_tolerance,
+                        grad_chunk, audit_samples, tile_blocks_per_sm, table_mb)
 
     def stage_times(self):
         """{stage: (device ms, kernel launches)} since the previous call."""
@@ -270,6 +328,51 @@ class Context:
                                 sys_.e_core)
         self.K = sys_.K
         self.set_ansatz(sys_.tensors, sys_.pred_ptr, sys_.pred_idx, sys_.rbm_W, sys_.rbm_b)
+        rnn = getattr(sys_, "rnn", None)
+        if rnn is not None:
+            self.set_readout(*rnn)
+        if getattr(sys_, "corr", 0):
+            self.set_correlator(sys_.corr, getattr(sys_, "rbm_W2", None))
+
+    def set_readout(self, v, eta, w, c, constrained=True):
+        """The normalised MPS-RNN / BDG-RNN readout (nqs_set_readout)."""
+        self._keep_rnn = tuple(_np(x, np.float64) for x in (v, eta, w, c))
+        nqs_set_readout(self.h, *self._keep_rnn, int(bool(constrained)))
+
+    def set_correlator(self, kind, W2=None):
+        self._keep_W2 = _np(W2, np.float64)
+        nqs_set_correlator(self.h, kind, self._keep_W2)
+        self._corr = kind
+
+    def sample(self, n_samples, seed):
+        """Autoregressive sampling (nqs_sample): (unique determinants [n][2], counts)."""
+        cap = int(min(n_samples, 1 << 20))
+        while True:
+            s = np.empty((max(cap, 1), 2), np.uint64)
+            c = np.empty(max(cap, 1), np.float64)
+            try:
+                n = nqs_sample(self.h, n_samples, seed, s, c, cap)
+                return s[:n], c[:n]
+            except NQSError as e:
+                if getattr(e, "n_unique", 0) > cap:
+                    cap = e.n_unique
+                    continue
+                raise
+
+    def energy_gradient(self, samples, counts, eps, n_draws, seed, reweighted=False):
+        """(grad_sites, grad_W, grad_b, grad_W2, e_loc, summary) of nqs_energy_gradient."""
+        s = _np(samples, np.uint64).reshape(-1, 2)
+        c = _np(counts, np.float64)
+        gT = np.empty((self.n_edges, 4, self.D, self.D), np.float64) if getattr(self, "_keep_rnn", None) is None \
+            else None
+        gW = np.empty((self.n_hidden, 2 * self.K), np.float64) if self.n_hidden else None
+        gb = np.empty(self.n_hidden, np.float64) if self.n_hidden else None
+        gW2 = np.empty((self.n_hidden, 2 * self.K, 2 * self.K), np.float64) \
+            if self.n_hidden and getattr(self, "_corr", 0) == NQS_CORR_ISING else None
+        e = np.empty(len(s), np.float64)
+        summ = EnergySummary()
+        nqs_energy_gradient(self.h, s, c, len(s), eps, n_draws, seed, reweighted, gT, gW, gb, gW2, e, summ)
+        return gT, gW, gb, gW2, e, summ.as_dict()
 
     def set_ansatz(self, tensors, pred_ptr=None, pred_idx=None, W=None, b=None):
         T = tensors if hasattr(tensors, "data_ptr") else _np(tensors, np.float64)
@@ -280,6 +383,8 @@ class Context:
                       b if (b is None or hasattr(b, "data_ptr")) else _np(b, np.float64))
         T, pp, pi, Wc, bc = self._keep
         nqs_set_ansatz(self.h, T, self.n_edges, self.D, pp, pi, Wc, bc, self.n_hidden)
+        self._keep_rnn = None           # the library resets the readout and correlator kind
+        self._corr = NQS_CORR_COSH
 
     def connected(self, samples, eps=0.0):
         """Host-side lists: (offsets, rank, dets, H, sign) as numpy arrays."""
@@ -343,7 +448,7 @@ def local_energy_batch(contexts, args, n_workers=0):
     array or CUDA tensor). Returns [(e_loc, summary dict)]."""
     n = len(contexts)
     items = (BatchItem * n)()
-    keep, outs, sums = [], [], []
+    keep, outs, sums, grads = [], [], [], []
     for i, (ctx, a) in enumerate(zip(contexts, args)):
         smp = a["samples"]
         if not hasattr(smp, "data_ptr"):
@@ -368,8 +473,19 @@ def local_energy_batch(contexts, args, n_workers=0):
         it.philox_seed = int(a.get("seed", 0))
         it.e_loc = _ptr(e)
         it.summary = C.pointer(sm)
+        if a.get("grad"):
+            # energy gradient of this system: site tensors, and W, b with a correlator
+            gT = np.empty((ctx.n_edges, 4, ctx.D, ctx.D), np.float64)
+            gW = np.empty((ctx.n_hidden, 2 * ctx.K), np.float64) if ctx.n_hidden else None
+            gb = np.empty(ctx.n_hidden, np.float64) if ctx.n_hidden else None
+            grads.append((gT, gW, gb))
+            it.reweighted = int(bool(a.get("reweighted", False)))
+            it.grad_sites, it.grad_W, it.grad_b = _ptr(gT), _ptr(gW), _ptr(gb)
+        else:
+            grads.append(None)
     nqs_local_energy_batch([c.h for c in contexts], items, n_workers)
-    return [(e, sm.as_dict()) for e, sm in zip(outs, sums)]
+    return [(e, sm.as_dict()) if g is None else (e, sm.as_dict(), g)
+            for e, sm, g in zip(outs, sums, grads)]
 
 
 _LOG_PSI = None

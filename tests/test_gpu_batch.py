@@ -126,3 +126,18 @@ def test_full_batch_every_system_at_full_size():
     finally:
         for c in ctxs:
             c.close()
+
+
+def test_batch_energy_gradient_equals_per_system_calls(setup):
+    """With gradient outputs, each system of the batch runs nqs_energy_gradient
+    (E_loc, u_n on the device, the VJP): bit-equal to its own call."""
+    systems, ctxs, _ = setup
+    sel = [0, 3, 5]
+    got = nqs.local_energy_batch([ctxs[i] for i in sel], [dict(_args(systems[i]), grad=True) for i in sel],
+                                 n_workers=3)
+    for i, (e, summ, (gT, gW, gb)) in zip(sel, got):
+        s, c = systems[i], ctxs[i]
+        rT, rW, rb, _, re, rs = c.energy_gradient(s.samples, s.counts, s.eps, s.n_draws, s.seed)
+        assert np.array_equal(e, re) and summ["e_mean"] == rs["e_mean"]
+        assert np.array_equal(gT, rT)
+        assert (gW is None and rW is None) or np.array_equal(gW, rW)
