@@ -76,6 +76,47 @@ def with_overrides(sys_, args):
     return dataclasses.replace(sys_, **ch) if ch else sys_
 
 
+def time_gradient(ctx, sys_, samples, counts, prec, tol, base, dev):
+    """The backward pass on the bench's batch (device buffers): the VJP alone
+    (nqs_grad_log_psi_vjp with fixed weights) and the energy gradient
+    (nqs_energy_gradient: E_loc, the weights on the device, the VJP), each
+    timed once after one untimed call, with CUDA events; plus the VJP with the
+    environments formed 1024 samples at a time (nqs_options.grad_chunk)."""
+    import torch
+    from paper_2507_19276_gb300 import nqs
+    Ns = int(samples.shape[0])
+    u = torch.from_numpy(np.random.default_rng(1).normal(size=Ns)).to(dev)
+    NH, K, D, E = sys_.n_hidden, sys_.K, sys_.D, sys_.n_edges
+    gT = torch.empty((E, 4, D, D), dtype=torch.float64, device=dev)
+    gW = torch.empty((NH, 2 * K), dtype=torch.float64, device=dev) if NH else None
+    gb = torch.empty(NH, dtype=torch.float64, device=dev) if NH else None
+    st = torch.cuda.current_stream(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a.record(st)
+        fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    out = {}
+    for chunk in (0, 1024):
+        ctx.set_precision(prec, timing=False, sample_index_base=base, energy_tolerance=tol, grad_chunk=chunk)
+        out[f"vjp_ms{'_chunk1024' if chunk else ''}"] = timed(
+            lambda: nqs.nqs_grad_log_psi_vjp(ctx.h, samples, u, Ns, gT, gW, gb))
+    ctx.set_precision(prec, timing=False, sample_index_base=base, energy_tolerance=tol)
+    e = torch.empty(Ns, dtype=torch.float64, device=dev)
+    out["energy_gradient_ms"] = timed(lambda: nqs.nqs_energy_gradient(
+        ctx.h, samples, counts, Ns, sys_.eps, sys_.n_draws, sys_.seed, 0, gT, gW, gb, None, e))
+    out["vjp_samples_per_s"] = Ns / (out["vjp_ms"] / 1e3)
+    # FP64 outer-product work of the site-tensor gradient: 2 D^2 per sample and edge
+    out["vjp_flops"] = 2.0 * D * D * E * Ns
+    return out
+
+
 def enum_bytes(K, na, nb, n_samples, n_det):
     """Algorithmic bytes of the enumeration stage (Slater-Condon elements of
     every connected determinant, the eps split, the deterministic lists): per
@@ -229,7 +270,11 @@ def run_reference(args):
         def one_step():
             return sum(cpu_oracle_rate(s, len(s.samples), cores)[1] for s in systems)
     else:
-        gen, n_def, _, metric = WORKLOADS[args.workload]
+        if args.workload == "h50_rnn":
+            # the oracle has its own sampler; its E_loc is timed on uniform samples
+            gen, n_def, metric = (lambda n, o: W.h50_rnn(n_samples=n, seed_offset=o)), 64, RNN_METRIC
+        else:
+            gen, n_def, _, metric = WORKLOADS[args.workload]
         sys_ = with_overrides(gen(args.samples or n_def, 0), args)
         per_step = min(len(sys_.samples), max(2, cores))
 
@@ -440,7 +485,10 @@ def run(args):
             "gpu_launches": int(sum(v[1] for v in stages.values())),
             "summary": {"e_mean": work["e_mean"], "n_det": work["n_det"],
                         "n_draw_unique": work["n_draw_unique"], "n_refined": work["n_refined"],
-                        "e_error_bound_ha": work["e_error_bound"]}}
+                        "e_error_bound_ha": work["e_error_bound"], "n_audited": work["n_audited"],
+                        "audit_rel_error": work["audit_rel_error"], "error_factor": work["error_factor"]}}
+    if args.grad:
+        line["gradient"] = time_gradient(ctx, sys_, samples, counts, prec, tol, lo, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         n_cpu = max(2, min(cores, 16))
@@ -450,6 +498,120 @@ def run(args):
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
+
+
+RNN_METRIC = "E_loc samples/s (H50 shape, BDG(1)-RNN chi=10, autoregressive samples)"
+
+
+def run_rnn(args):
+    """The paper's H50 setting of Fig. 3a (Sec. 4.1): the normalised BDG(1)-RNN
+    readout at chi = 10, eps = 0.01, N_eps = 100. One step = nqs_sample of
+    N_s draws (autoregressive, breadth first) + nqs_local_energy (FP64) over
+    the unique samples with their counts; device buffers throughout."""
+    import torch
+    from paper_2507_19276_gb300 import nqs
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    live = measured_ceilings(local, args)
+    sys_ = with_overrides(W.h50_rnn(n_samples=2, seed_offset=rank), args)
+    n_draw = args.samples or 4096
+    ctx = nqs.Context(local)
+    ctx.set_system(sys_)
+    ctx.set_precision(nqs.NQS_PREC_FP64, timing=True)
+    smp = torch.empty((n_draw, 2), dtype=torch.int64, device=dev)
+    cnt = torch.empty(n_draw, dtype=torch.float64, device=dev)
+    e_loc = torch.empty(n_draw, dtype=torch.float64, device=dev)
+
+    def step(k, summ=None):
+        nu = nqs.nqs_sample(ctx.h, n_draw, sys_.seed + k, smp, cnt, n_draw)
+        nqs.nqs_local_energy(ctx.h, smp, cnt, nu, sys_.eps, sys_.n_draws, sys_.seed, e_loc, summ)
+        return nu
+
+    summ = nqs.EnergySummary()
+    for k in range(args.warmup):
+        step(k, summ)
+    torch.cuda.synchronize()
+    ctx.stage_times()
+    st = torch.cuda.current_stream(dev)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(1.0)
+    barrier(ws)
+    torch.cuda.synchronize()
+    start.record(st)
+    uniq = 0
+    for k in range(args.steps):
+        uniq += step(1000 + k)
+    stop.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(ws)
+    ms = max_over_ranks(start.elapsed_time(stop), ws, dev)
+    stages = ctx.stage_times()
+    value = ws * uniq / (ms / 1e3)
+    nu = step(0, summ)
+    torch.cuda.synchronize()
+    work = summ.as_dict()
+    ctx.stage_times()
+    # FP64 work of the amplitudes: per recomputed vertex four candidate cells
+    # (2 D^2 each) and their weights (2 D each), plus the sampler's per-node cells
+    D = sys_.D
+    amp_ms = (stages["amp_det"][0] + stages["amp_draw"][0]) / args.steps
+    flops = work["span_sites"] * (4 * 2.0 * D * D + 4 * 3.0 * D)
+    peak = live["fma64_tflops"] if live else 1.196
+    roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": flops / (amp_ms / 1e3) / 1e12, "peak": peak,
+            "peak_source": "FP64 FMA rate measured before the timed region (peaks probe)" if live
+            else "FP64 FMA rate of an earlier probe run on this pool's GB300",
+            "kernel": "k_rnn_amp (normalised readout, FP64, one warp per row)", "traffic": None,
+            "algorithmic_flops_per_step": flops, "stage_ms_per_step": amp_ms}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    # end to end: the same step with host-side outputs (samples back to the host,
+    # then E_loc through host buffers)
+    hs = np.empty((n_draw, 2), np.uint64)
+    hc = np.empty(n_draw, np.float64)
+    he = np.empty(n_draw, np.float64)
+    t0 = time.perf_counter()
+    ue = 0
+    for k in range(args.steps):
+        n_u = nqs.nqs_sample(ctx.h, n_draw, sys_.seed + 2000 + k, hs, hc, n_draw)
+        nqs.nqs_local_energy(ctx.h, hs[:n_u], hc[:n_u], n_u, sys_.eps, sys_.n_draws, sys_.seed, he, None)
+        ue += n_u
+    e2e_s = time.perf_counter() - t0
+    line = {"metric": RNN_METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"h50_rnn chain K={sys_.K} {sys_.n_alpha}a+{sys_.n_beta}b BDG(1)-RNN "
+                                   f"chi={D}, {n_draw} autoregressive draws per step, eps={sys_.eps:g} "
+                                   f"N_eps={sys_.n_draws}",
+                       "draws_per_step": n_draw, "unique_per_step": uniq / args.steps,
+                       "l2": "inputs > L2 (deterministic lists exceed 129 MB)"},
+            "draws_per_s": ws * n_draw * args.steps / (ms / 1e3),
+            "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+            "roofline": roof, "measured_ceilings": live,
+            "e2e": {"value": ws * ue / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 24 * n_draw,
+                    "d2h_bytes_per_step": 32 * n_draw},
+            "clocks": clk, "gpu_launches": int(sum(v[1] for v in stages.values())),
+            "summary": {"e_mean": work["e_mean"], "n_det": work["n_det"], "unique": nu}}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        hs0 = np.empty((n_draw, 2), np.uint64)
+        hc0 = np.empty(n_draw, np.float64)
+        n_u = nqs.nqs_sample(ctx.h, n_draw, sys_.seed, hs0, hc0, n_draw)
+        sub = dataclasses_replace(sys_, samples=hs0[:min(4, n_u)].copy(), counts=hc0[:min(4, n_u)].copy())
+        rate, dt = cpu_oracle_rate(sub, len(sub.samples), cores)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{len(sub.samples)} sampled determinants ({dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def dataclasses_replace(obj, **kw):
+    import dataclasses
+    return dataclasses.replace(obj, **kw)
 
 
 BATCH_METRIC = "E_loc samples/s (64-system uneven batch, one call)"
@@ -628,8 +790,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="h50", choices=sorted(WORKLOADS) + ["uneven"],
-                    help="h50 (default), k8, fe2s2, h18, or uneven (64 systems in one batch call)")
+    ap.add_argument("--workload", default="h50", choices=sorted(WORKLOADS) + ["uneven", "h50_rnn"],
+                    help="h50 (default), k8, fe2s2, h18, uneven (64 systems in one batch call) or "
+                         "h50_rnn (normalised BDG(1)-RNN, autoregressive samples)")
     ap.add_argument("--precision", default=None, choices=["mixed", "fp64", "fp64_shared"],
                     help="default: the workload's (mixed for chains with D %% 16 == 0, fp64 otherwise)")
     ap.add_argument("--samples", type=int, default=None, help="samples per GPU (default: the workload's)")
@@ -659,11 +822,14 @@ def main():
         print(json.dumps(probe.measure(0)), flush=True)
         return
     if args.precision is None:
-        args.precision = "mixed" if args.workload == "uneven" else WORKLOADS[args.workload][2]
+        args.precision = {"uneven": "mixed", "h50_rnn": "fp64"}.get(args.workload) or \
+            WORKLOADS[args.workload][2]
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "uneven":
         run_batch(args)
+    elif args.workload == "h50_rnn":
+        run_rnn(args)
     else:
         run(args)
 

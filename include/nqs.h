@@ -245,6 +245,19 @@ int nqs_set_readout(nqs_ctx* ctx, const double* v, const double* eta, const doub
  * shared-prefix forms support NQS_CORR_COSH only (NQS_ERR_UNSUPPORTED). */
 int nqs_set_correlator(nqs_ctx* ctx, int kind, const double* W2);
 
+/* The tensor term of Eq. (bdg-rnn-update) with the Tucker factors of Sec. 2.2
+ * (the BDG-TensorRNN), on a graph ansatz: a vertex i with d >= 2 in-edges and
+ * rank r = ranks[i] > 0 adds to its cell (every readout)
+ *   t_i^s[a] = sum_o Kout[a][o] sum_{q_1..q_d} U^s[o][q_1]..[q_d] prod_k z_k[q_k],
+ *   z_k[q] = sum_b K_k[b][q] h_{j_k}[b]
+ * (j_k the source of the k-th in-edge in pred_idx order, h_{-1} = e_0). The
+ * paper sets r = ceil(D^(2/(d+1))). params packs, per such vertex in vertex
+ * order, U [4][r^(d+1)] (index order o, q_1, .., q_d), Kout [D][r], then K_k
+ * [D][r] for k = 1..d; n_params must equal that total (NQS_ERR_INVALID_ARG
+ * otherwise, as for a chain or r outside 0..64). ranks NULL removes the term.
+ * FP64 forms only; the site-tensor gradient returns NQS_ERR_UNSUPPORTED. */
+int nqs_set_tensor_term(nqs_ctx* ctx, const int* ranks, const double* params, int64_t n_params);
+
 /* Connected determinants with |H_mn| >= det_threshold, canonical order.
  *  samples [Ns][2]; offsets [Ns+1] receives the start of each sample's list.
  *  rank [capacity], dets [capacity][2], H [capacity], sign [capacity]

@@ -243,6 +243,68 @@ static const double* tensor(const or_ansatz* a, int e, int sigma)
     return a->tensors + ((size_t)e * 4 + sigma) * a->D * a->D;
 }
 
+/* Parameters of vertex i's tensor term (NULL when it has none): *d in-edges,
+ * rank *r; the blocks of the vertices before i are skipped in order. */
+static const double* tucker_block(const or_ansatz* a, int i, int* d, int* r)
+{
+    if (!a->tucker_rank || !a->pred_ptr) return NULL;
+    const double* p = a->tucker;
+    for (int v = 0; v <= i; ++v) {
+        const int dv = a->pred_ptr[v + 1] - a->pred_ptr[v], rv = a->tucker_rank[v];
+        if (dv < 2 || rv <= 0) continue;
+        if (v == i) { *d = dv; *r = rv; return p; }
+        size_t core = 1;
+        for (int k = 0; k <= dv; ++k) core *= (size_t)rv;
+        p += 4 * core + (size_t)(dv + 1) * a->D * rv;
+    }
+    return NULL;
+}
+
+/* Tensor term t_i^s of vertex i for the in-edge sources src[k] (length D
+ * each): added to out[0..D). */
+static void tensor_term(const or_ansatz* a, int i, int s, const double* const* src, double* out)
+{
+    int d = 0, r = 0;
+    const double* blk = tucker_block(a, i, &d, &r);
+    if (!blk) return;
+    const int D = a->D;
+    size_t core = 1;
+    for (int k = 0; k < d; ++k) core *= (size_t)r;          /* r^d entries per output index */
+    const double* U = blk + (size_t)s * core * r;
+    const double* Kout = blk + 4 * core * r;
+    double* z = (double*)malloc(sizeof(double) * d * r);
+    for (int k = 0; k < d; ++k) {
+        const double* Kk = Kout + (size_t)(k + 1) * D * r;
+        for (int q = 0; q < r; ++q) {
+            double acc = 0.0;
+            for (int b = 0; b < D; ++b) acc += Kk[(size_t)b * r + q] * src[k][b];
+            z[k * r + q] = acc;
+        }
+    }
+    double* y = (double*)calloc(r, sizeof(double));
+    for (int o = 0; o < r; ++o) {
+        double acc = 0.0;
+        for (size_t m = 0; m < core; ++m) {
+            /* digits of m: a_1' (most significant) .. a_d' */
+            double prod = U[(size_t)o * core + m];
+            size_t rem = m;
+            for (int k = d - 1; k >= 0; --k) {
+                prod *= z[k * r + (int)(rem % (size_t)r)];
+                rem /= (size_t)r;
+            }
+            acc += prod;
+        }
+        y[o] = acc;
+    }
+    for (int q = 0; q < D; ++q) {
+        double acc = 0.0;
+        for (int o = 0; o < r; ++o) acc += Kout[(size_t)q * r + o] * y[o];
+        out[q] += acc;
+    }
+    free(z);
+    free(y);
+}
+
 /* Rescale v by a power of two so that max|v| is in [0.5, 1); returns the exponent. */
 static int renorm(double* v, int D)
 {
@@ -260,6 +322,8 @@ static void forward_states(const or_ansatz* a, const int* sigma, double* hs, int
 {
     const int K = a->K, D = a->D;
     double* tmp = (double*)malloc(sizeof(double) * D);
+    double* e0v = (double*)calloc(D, sizeof(double));
+    e0v[0] = 1.0;
     for (int i = 0; i < K; ++i) {
         int e0, e1;
         edges_of(a, i, &e0, &e1);
@@ -268,6 +332,13 @@ static void forward_states(const or_ansatz* a, const int* sigma, double* hs, int
             int j = edge_src(a, e);
             int ej = j < 0 ? 0 : ex[j];
             if (ej > eref) eref = ej;
+        }
+        /* the tensor term scales with the product of its sources: exponent sum */
+        int dt = 0, rt = 0, et = 0;
+        const int has_t = tucker_block(a, i, &dt, &rt) != NULL;
+        if (has_t) {
+            for (int e = e0; e < e1; ++e) { int j = edge_src(a, e); et += j < 0 ? 0 : ex[j]; }
+            if (et > eref) eref = et;
         }
         double* hi = hs + (size_t)i * D;
         for (int k = 0; k < D; ++k) hi[k] = 0.0;
@@ -285,9 +356,20 @@ static void forward_states(const or_ansatz* a, const int* sigma, double* hs, int
             int ej = j < 0 ? 0 : ex[j];
             for (int r = 0; r < D; ++r) hi[r] += ldexp(tmp[r], ej - eref);
         }
+        if (has_t) {
+            const double* src[8];
+            for (int e = e0; e < e1; ++e) {
+                int j = edge_src(a, e);
+                src[e - e0] = j < 0 ? e0v : hs + (size_t)j * D;
+            }
+            for (int r = 0; r < D; ++r) tmp[r] = 0.0;
+            tensor_term(a, i, sigma[i], src, tmp);
+            for (int r = 0; r < D; ++r) hi[r] += ldexp(tmp[r], et - eref);
+        }
         ex[i] = eref + renorm(hi, D);
     }
     free(tmp);
+    free(e0v);
 }
 
 static void sigma_of(int K, const uint64_t* det, int* sigma)
@@ -375,6 +457,18 @@ static void rnn_candidates(const or_ansatz* a, int i, const double* hs, double* 
                 }
             }
             h[r] = acc;
+        }
+        int dt = 0, rt = 0;
+        if (tucker_block(a, i, &dt, &rt)) {
+            double* e0v = (double*)calloc(D, sizeof(double));
+            e0v[0] = 1.0;
+            const double* src[8];
+            for (int e = e0; e < e1; ++e) {
+                const int j = edge_src(a, e);
+                src[e - e0] = j < 0 ? e0v : hs + (size_t)j * D;
+            }
+            tensor_term(a, i, s, src, h);
+            free(e0v);
         }
         double p = 0.0;
         for (int r = 0; r < D; ++r) p += a->rnn_eta[(size_t)i * D + r] * h[r] * h[r];
@@ -716,8 +810,8 @@ static void one_sample(const or_ham* h, const or_ansatz* a, const uint64_t* n, i
                        double eps, int n_draws, uint64_t seed, or_sample_out* o, int with_cond)
 {
     memset(o, 0, sizeof(*o));
-    /* the first-order bound P1 describes the linear readout's contraction */
-    if (a->readout != 0) with_cond = 0;
+    /* the first-order bound P1 describes the linear readout's matrix contraction */
+    if (a->readout != 0 || a->tucker_rank) with_cond = 0;
     double la_n, lf_n;
     int sg_n;
     or_log_psi(a, n, &la_n, &sg_n, &lf_n);

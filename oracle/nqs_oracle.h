@@ -72,6 +72,18 @@ typedef struct {
      * sum_s W[k][s] n_s over the 2K interleaved spin orbitals. */
     int corr;
     const double* rbm_W2;    /* [n_hidden][2K][2K] (corr 2) */
+    /* Tensor term of Eq. (bdg-rnn-update) (the BDG-TensorRNN of Sec. 2.2) with
+     * the Tucker factors: for a vertex i with d >= 2 in-edges and rank
+     * r = tucker_rank[i] > 0 the cell gains
+     *   t_i^s[a] = sum_{i'} Kout[a][i'] sum_{a_1'..a_d'} U^s[i'][a_1']..[a_d'] prod_k z_k[a_k'],
+     *   z_k[a'] = sum_b K_k[b][a'] h_{j_k}[b]
+     * (j_k the source of the k-th in-edge in edge order, h_{-1} = e_0): the core
+     * U^s contracted with the factor matrices Kout, K_1 .. K_d (each D x r) on
+     * every mode. Parameters per such vertex, in vertex order: U [4][r^(d+1)]
+     * (index order i', a_1', .., a_d'), Kout [D][r], then K_k [D][r] for each
+     * in-edge k. */
+    const int* tucker_rank;  /* [K] (NULL: no tensor term) */
+    const double* tucker;    /* the packed parameters */
 } or_ansatz;
 
 typedef struct {
@@ -141,7 +153,7 @@ int or_local_energy(const or_ham* ham, const or_ansatz* a, const uint64_t* sampl
 
 /* d log|psi(n)| / d theta for one determinant: grad_t [n_edges][4][D][D],
  * grad_W [n_hidden][2K], grad_b [n_hidden] (any may be NULL). The tensor
- * part needs the linear readout (readout 0). */
+ * part needs the linear readout (readout 0) without the tensor term. */
 void or_grad_log_psi(const or_ansatz* a, const uint64_t* det, double* grad_t,
                      double* grad_W, double* grad_b);
 

@@ -46,7 +46,8 @@ class Ansatz(C.Structure):
                 ("n_hidden", C.c_int), ("rbm_W", C.c_void_p), ("rbm_b", C.c_void_p),
                 ("readout", C.c_int), ("n_alpha", C.c_int), ("n_beta", C.c_int),
                 ("rnn_v", C.c_void_p), ("rnn_eta", C.c_void_p), ("rnn_w", C.c_void_p),
-                ("rnn_c", C.c_void_p), ("corr", C.c_int), ("rbm_W2", C.c_void_p)]
+                ("rnn_c", C.c_void_p), ("corr", C.c_int), ("rbm_W2", C.c_void_p),
+                ("tucker_rank", C.c_void_p), ("tucker", C.c_void_p)]
 
 
 class SampleOut(C.Structure):
@@ -96,13 +97,16 @@ class Problem:
         rnn = getattr(sys, "rnn", None)          # (v, eta, w, c) of the normalised readout
         self.rnn = None if rnn is None else tuple(_c(x, np.float64) for x in rnn)
         self.W2 = _c(getattr(sys, "rbm_W2", None), np.float64)
+        tk = getattr(sys, "tucker", None)        # (ranks [K], packed parameters) of the tensor term
+        self.tk_rank = None if tk is None else _c(tk[0], np.int32)
+        self.tk = None if tk is None else _c(tk[1], np.float64)
         ptr = lambda a: a.ctypes.data if a is not None else None
         self.ans = Ansatz(sys.K, sys.D, int(self.tensors.shape[0]),
                           ptr(self.pred_ptr), ptr(self.pred_idx),
                           self.tensors.ctypes.data, sys.n_hidden, ptr(self.W), ptr(self.b),
                           1 if self.rnn is not None else 0, sys.n_alpha, sys.n_beta,
                           *(ptr(x) for x in (self.rnn or (None,) * 4)),
-                          int(getattr(sys, "corr", 0)), ptr(self.W2))
+                          int(getattr(sys, "corr", 0)), ptr(self.W2), ptr(self.tk_rank), ptr(self.tk))
 
 
 def build_eri(chol):

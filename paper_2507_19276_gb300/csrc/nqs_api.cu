@@ -78,6 +78,7 @@ struct nqs_ctx {
     unsigned long long* noalloc_addr = nullptr;   // device address of the fixed draw scratch
     // normalised readout, correlator kind, gradient and audit options
     DevBuf rv, reta, rw, rc, W2, rnn_cells, rnn_lp, rnn_sg, grad_scr, u_dev, ebar_dev;
+    DevBuf tk_rank, tk_off, tk;   // tensor term (Tucker form) of the graph ansatz
     int grad_chunk = 0;        // samples whose environments live at once in the gradient (0: all)
     int audit = 4;             // mixed form: samples re-evaluated in FP64 to check the error factor
     double audit_rel = 0.0, err_factor = 0.0;
@@ -738,7 +739,7 @@ extern "C" int nqs_destroy(nqs_ctx* c)
     for (DevBuf* b : bufs) release(*b);
     DevBuf* more[] = {&c->rv, &c->reta, &c->rw, &c->rc, &c->W2, &c->rnn_cells, &c->rnn_lp, &c->rnn_sg,
                       &c->grad_scr, &c->u_dev, &c->ebar_dev, &c->smp_cand, &c->smp_ccnt, &c->smp_cpos,
-                      &c->smp_tabs};
+                      &c->smp_tabs, &c->tk_rank, &c->tk_off, &c->tk};
     for (DevBuf* b : more) release(*b);
     for (auto* v : {&c->smp_pa, &c->smp_pb, &c->smp_off, &c->smp_cnt, &c->smp_par, &c->smp_cell})
         for (DevBuf& b : *v) release(b);
@@ -1046,6 +1047,54 @@ extern "C" int nqs_set_correlator(nqs_ctx* c, int kind, const double* W2)
         c->av.W2 = (const double*)c->W2.p;
     }
     c->av.corr = kind;
+    return NQS_OK;
+}
+
+extern "C" int nqs_set_tensor_term(nqs_ctx* c, const int* ranks, const double* params, int64_t n_params)
+{
+    if (!c) return NQS_ERR_INVALID_ARG;
+    c->err[0] = 0;
+    cudaSetDevice(c->device);
+    TRY(check_ready(c, true));
+    const int K = c->K, D = c->av.D;
+    if (!ranks) {
+        c->av.tk_rank = nullptr;
+        c->av.tk_off = nullptr;
+        c->av.tk = nullptr;
+        c->av.tk_zy = 0;
+        return NQS_OK;
+    }
+    if (c->av.chain) return set_err(c, NQS_ERR_INVALID_ARG, "the tensor term needs a graph ansatz (in-degree >= 2)");
+    std::vector<int> rk((size_t)K), ptr((size_t)K + 1);
+    CK(cudaMemcpy(rk.data(), ranks, (size_t)K * 4, cudaMemcpyDefault));
+    CK(cudaMemcpy(ptr.data(), c->pred_ptr.p, (size_t)(K + 1) * 4, cudaMemcpyDeviceToHost));
+    std::vector<long long> off((size_t)K, -1);
+    long long total = 0;
+    int zy = 0;
+    for (int i = 0; i < K; ++i) {
+        const int d = ptr[i + 1] - ptr[i], r = rk[(size_t)i];
+        if (r < 0 || r > 64) return set_err(c, NQS_ERR_INVALID_ARG, "tensor-term rank %d of vertex %d outside 0..64", r, i);
+        if (r == 0 || d < 2) continue;
+        double core = 1.0;
+        for (int k = 0; k <= d; ++k) core *= r;
+        if (core > 1e8) return set_err(c, NQS_ERR_INVALID_ARG, "tensor-term core of vertex %d has %g entries", i, core);
+        off[(size_t)i] = total;
+        total += 4 * (long long)core + (long long)(d + 1) * D * r;
+        zy = std::max(zy, (d + 1) * r);
+    }
+    if (n_params != total)
+        return set_err(c, NQS_ERR_INVALID_ARG, "n_params = %lld, the ranks and in-degrees need %lld",
+                       (long long)n_params, total);
+    TRY(ensure(c, c->tk_rank, (size_t)K * 4));
+    TRY(ensure(c, c->tk_off, (size_t)K * 8));
+    TRY(ensure(c, c->tk, (size_t)(total ? total : 1) * 8));
+    CK(cudaMemcpy(c->tk_rank.p, rk.data(), (size_t)K * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->tk_off.p, off.data(), (size_t)K * 8, cudaMemcpyHostToDevice));
+    if (total) CK(cudaMemcpy(c->tk.p, params, (size_t)total * 8, cudaMemcpyDefault));
+    c->av.tk_rank = (const int*)c->tk_rank.p;
+    c->av.tk_off = (const long long*)c->tk_off.p;
+    c->av.tk = (const double*)c->tk.p;
+    c->av.tk_zy = zy;
     return NQS_OK;
 }
 
@@ -1547,8 +1596,9 @@ int vjp_core(nqs_ctx* c, const uint64_t* ds, const double* du, int64_t Ns, doubl
 {
     const int K = c->K, D = c->av.D, NH = c->av.n_hidden;
     const size_t nt = (size_t)c->av.n_edges * 4 * D * D, nw = (size_t)NH * 2 * K;
-    if (dg && c->av.readout != 0)
-        return set_err(c, NQS_ERR_UNSUPPORTED, "the site-tensor gradient needs the linear readout");
+    if (dg && (c->av.readout != 0 || c->av.tk_rank))
+        return set_err(c, NQS_ERR_UNSUPPORTED,
+                       "the site-tensor gradient needs the linear readout without the tensor term");
     if (Ns == 0) {
         if (dg) CK(cudaMemsetAsync(dg, 0, nt * 8, c->stream));
         if (dW && nw) CK(cudaMemsetAsync(dW, 0, nw * 8, c->stream));

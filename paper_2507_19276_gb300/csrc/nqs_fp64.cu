@@ -79,6 +79,7 @@ __global__ void k_env_fp64(EnvArgs a)
     double* sh = sm + 2 * D;            // 33 doubles
     int* gx = (int*)(sh + 34);          // [K] adjoint exponents
     int* gset = gx + kMaxOrb;           // [K]
+    double* tkz = (double*)(gset + kMaxOrb);   // tensor-term scratch: z [d][r], then y [r]
     const int64_t s = blockIdx.x;
     const uint64_t na = a.samples[2 * s], nb = a.samples[2 * s + 1];
 
@@ -136,13 +137,24 @@ __global__ void k_env_fp64(EnvArgs a)
         int* He = a.Hexp + (size_t)s * K;
         for (int i = 0; i < K; ++i) {
             const int e0 = a.an.pred_ptr[i], e1 = a.an.pred_ptr[i + 1];
-            int eref = -1000000;
+            int eref = -1000000, et = 0;
             for (int e = e0; e < e1; ++e) {
                 const int j = a.an.pred_idx[e];
                 const int ej = j < 0 ? 0 : He[j];
                 eref = ej > eref ? ej : eref;
+                et += ej;
             }
             const int sg = sigma_at(na, nb, i);
+            const bool tk = tk_has(a.an, i);
+            if (tk) {
+                // the tensor term scales with the product of its sources (exponent sum)
+                eref = et > eref ? et : eref;
+                tk_project(a.an, i, [&](int j) { return (const double*)(Hs + (size_t)j * D); }, tkz,
+                           threadIdx.x, blockDim.x);
+                __syncthreads();
+                tk_core(a.an, i, sg, tkz, tkz + tk_degree(a.an, i) * a.an.tk_rank[i], threadIdx.x, blockDim.x);
+                __syncthreads();
+            }
             for (int r = threadIdx.x; r < D; r += blockDim.x) {
                 double acc = 0.0;
                 for (int e = e0; e < e1; ++e) {
@@ -156,6 +168,8 @@ __global__ void k_env_fp64(EnvArgs a)
                     }
                     acc += ldexp(t, (j < 0 ? 0 : He[j]) - eref);
                 }
+                if (tk)
+                    acc += ldexp(tk_out(a.an, i, r, tkz + tk_degree(a.an, i) * a.an.tk_rank[i]), et - eref);
                 y[r] = acc;
             }
             __syncthreads();
@@ -260,7 +274,7 @@ int launch_env_fp64(const EnvArgs& a, cudaStream_t st)
 {
     if (a.Ns == 0) return 0;
     const int threads = a.an.D >= 256 ? 256 : (a.an.D > 64 ? 128 : 64);
-    const size_t smem = (2 * a.an.D + 34) * sizeof(double) + 2 * kMaxOrb * sizeof(int);
+    const size_t smem = (2 * a.an.D + 34 + a.an.tk_zy) * sizeof(double) + 2 * kMaxOrb * sizeof(int);
     k_env_fp64<<<(unsigned)a.Ns, threads, smem, st>>>(a);
     return 1;
 }
@@ -282,7 +296,9 @@ int amp_fp64_rows_per_block(const AnsatzView& an)
 size_t amp_fp64_smem(const AnsatzView& an, int R)
 {
     size_t st = an.chain ? (size_t)2 * R * an.D : (size_t)R * an.K * an.D;
-    return st * sizeof(double) + (size_t)R * (an.chain ? 1 : an.K) * sizeof(int);
+    size_t ints = (size_t)R * (an.chain ? 1 : an.K);
+    ints = (ints + 1) & ~(size_t)1;                       // the tensor-term scratch after is 8-byte aligned
+    return st * sizeof(double) + ints * sizeof(int) + (size_t)R * an.tk_zy * sizeof(double);
 }
 
 struct RowInfo {
@@ -432,6 +448,7 @@ __global__ void k_amp_graph_fp64(AmpArgs a)
     const uint64_t na = a.samples[2 * s], nb = a.samples[2 * s + 1];
     double* S = sm;                                   // [R][K][D]
     int* SX = (int*)(sm + (size_t)R * K * D);         // [R][K]
+    double* TK = (double*)(SX + (((size_t)R * K + 1) & ~(size_t)1));   // [R][tk_zy] tensor-term scratch
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     if (warp == 0) build_lists_warp(na, nb, a.h.K, lists, lane);
     if (threadIdx.x == 0) s_min = 1 << 30;
@@ -457,17 +474,35 @@ __global__ void k_amp_graph_fp64(AmpArgs a)
     const int* He = a.Hexp + (size_t)s * K;
     for (int i = s_min; i < K; ++i) {
         const int e0 = a.an.pred_ptr[i], e1 = a.an.pred_ptr[i + 1];
+        const bool tk = tk_has(a.an, i);
+        const int dr = tk ? tk_degree(a.an, i) * a.an.tk_rank[i] : 0;
+        if (tk) {
+            // tensor term per row: project the sources, contract the core (one warp per row)
+            for (int r = warp; r < nr; r += nw) {
+                const int p = info[r].p;
+                if (i < p) continue;
+                double* z = TK + (size_t)r * a.an.tk_zy;
+                tk_project(a.an, i, [&](int jj) {
+                    return (const double*)(jj < p ? Hs + (size_t)jj * D : S + ((size_t)r * K + jj) * D); },
+                    z, lane, 32);
+                __syncwarp();
+                tk_core(a.an, i, sigma_at(info[r].ma, info[r].mb, i), z, z + dr, lane, 32);
+            }
+            __syncthreads();
+        }
         for (int q = threadIdx.x; q < nr * D; q += blockDim.x) {
             const int r = q / D, c = q - r * D;
             const int p = info[r].p;
             if (i < p) continue;
             const int sg = sigma_at(info[r].ma, info[r].mb, i);
-            int eref = -1000000;
+            int eref = -1000000, et = 0;
             for (int e = e0; e < e1; ++e) {
                 const int jj = a.an.pred_idx[e];
                 const int ej = jj < 0 ? 0 : (jj < p ? He[jj] : SX[r * K + jj]);
                 eref = ej > eref ? ej : eref;
+                et += ej;
             }
+            if (tk) eref = et > eref ? et : eref;
             double acc = 0.0;
             for (int e = e0; e < e1; ++e) {
                 const int jj = a.an.pred_idx[e];
@@ -482,6 +517,7 @@ __global__ void k_amp_graph_fp64(AmpArgs a)
                 }
                 acc += ldexp(t, ej - eref);
             }
+            if (tk) acc += ldexp(tk_out(a.an, i, c, TK + (size_t)r * a.an.tk_zy + dr), et - eref);
             S[((size_t)r * K + i) * D + c] = acc;
             if (c == 0) SX[r * K + i] = eref;     // exponent before renorm
         }
@@ -563,15 +599,27 @@ __global__ void k_full_amp_fp64(AnsatzView an, const uint64_t* dets, int64_t n, 
         }
         if (threadIdx.x == 0) { ex[K - 1] = e; sh[33] = x[0]; }
     } else {
+        double* tkz = st + (size_t)K * D;         // tensor-term scratch
         for (int i = 0; i < K; ++i) {
             const int e0 = an.pred_ptr[i], e1 = an.pred_ptr[i + 1];
-            int eref = -1000000;
+            int eref = -1000000, et = 0;
             for (int e = e0; e < e1; ++e) {
                 const int j = an.pred_idx[e];
                 const int ej = j < 0 ? 0 : ex[j];
                 eref = ej > eref ? ej : eref;
+                et += ej;
             }
             const int sg = sigma_at(na, nb, i);
+            const bool tk = tk_has(an, i);
+            const int dr = tk ? tk_degree(an, i) * an.tk_rank[i] : 0;
+            if (tk) {
+                eref = et > eref ? et : eref;
+                tk_project(an, i, [&](int j) { return (const double*)(st + (size_t)j * D); }, tkz,
+                           threadIdx.x, blockDim.x);
+                __syncthreads();
+                tk_core(an, i, sg, tkz, tkz + dr, threadIdx.x, blockDim.x);
+                __syncthreads();
+            }
             for (int r = threadIdx.x; r < D; r += blockDim.x) {
                 double acc = 0.0;
                 for (int e = e0; e < e1; ++e) {
@@ -582,6 +630,7 @@ __global__ void k_full_amp_fp64(AnsatzView an, const uint64_t* dets, int64_t n, 
                     else for (int c = 0; c < D; ++c) t = fma(__ldg(AT + c * D + r), st[(size_t)j * D + c], t);
                     acc += ldexp(t, (j < 0 ? 0 : ex[j]) - eref);
                 }
+                if (tk) acc += ldexp(tk_out(an, i, r, tkz + dr), et - eref);
                 st[(size_t)i * D + r] = acc;
             }
             __syncthreads();
@@ -623,7 +672,7 @@ int launch_full_amp_fp64(const AnsatzView& an, const uint64_t* dets, int64_t n, 
 {
     if (n == 0) return 0;
     int launches = 0;
-    const size_t smem = (34 + (an.chain ? 2 * (size_t)an.D : (size_t)an.K * an.D)) * sizeof(double);
+    const size_t smem = (34 + (an.chain ? 2 * (size_t)an.D : (size_t)an.K * an.D + an.tk_zy)) * sizeof(double);
     allow_max_smem(k_full_amp_fp64);
     const int threads = an.D >= 256 ? 256 : (an.D > 64 ? 128 : 64);
     for (int64_t i0 = 0; i0 < n; i0 += (1ll << 30)) {

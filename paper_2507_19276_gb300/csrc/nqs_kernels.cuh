@@ -151,7 +151,85 @@ struct AnsatzView {
     // 2 Ising-RBM, theta_k + 1/2 sum_{s,t} W2[k][s][t] n_s n_t inside the cos
     int corr;
     const double* W2;                    // [n_hidden][2K][2K] (corr 2)
+    // tensor term of Eq. (bdg-rnn-update) with Tucker factors (graph ansatz):
+    // vertex i with d >= 2 in-edges and rank r = tk_rank[i] > 0 owns, at
+    // tk[tk_off[i]], U [4][r^(d+1)] then Kout [D][r] then K_k [D][r] per in-edge
+    const int* tk_rank;                  // [K] (NULL: no tensor term)
+    const long long* tk_off;             // [K] (-1: none)
+    const double* tk;
+    int tk_zy;                           // scratch doubles per evaluation: max (d + 1) r
 };
+
+// ---- tensor term (Tucker form), shared by the FP64 kernels ------------------
+// t_i^s[a] = sum_o Kout[a][o] y[o],  y[o] = sum_{a_1'..a_d'} U^s[o][a_1']..[a_d']
+// prod_k z_k[a_k'],  z_k[q] = sum_b K_k[b][q] h_{j_k}[b] (h_{-1} = e_0).
+
+__device__ __forceinline__ int tk_degree(const AnsatzView& an, int i)
+{
+    return an.chain ? 1 : an.pred_ptr[i + 1] - an.pred_ptr[i];
+}
+
+__device__ __forceinline__ bool tk_has(const AnsatzView& an, int i)
+{
+    return an.tk_rank && an.tk_off[i] >= 0;
+}
+
+// z [d][r] for the in-edge sources of vertex i; threads tid, tid + nt, ...
+template <class Src>
+__device__ __forceinline__ void tk_project(const AnsatzView& an, int i, const Src& src, double* z, int tid, int nt)
+{
+    const int d = tk_degree(an, i), r = an.tk_rank[i], D = an.D;
+    size_t core = 1;
+    for (int k = 0; k <= d; ++k) core *= (size_t)r;
+    const double* K1 = an.tk + an.tk_off[i] + 4 * core + (size_t)D * r;   // K_1, then K_2, ...
+    for (int q = tid; q < d * r; q += nt) {
+        const int k = q / r, c = q - k * r;
+        const int j = an.pred_idx[an.pred_ptr[i] + k];
+        const double* Kk = K1 + (size_t)k * D * r;
+        double acc;
+        if (j < 0) acc = __ldg(Kk + c);                        // K_k^T e_0 = row 0 of K_k
+        else {
+            const double* h = src(j);
+            acc = 0.0;
+            for (int b = 0; b < D; ++b) acc = fma(__ldg(Kk + (size_t)b * r + c), h[b], acc);
+        }
+        z[q] = acc;
+    }
+}
+
+// y [r] for local state s from z
+__device__ __forceinline__ void tk_core(const AnsatzView& an, int i, int s, const double* z, double* y, int tid, int nt)
+{
+    const int d = tk_degree(an, i), r = an.tk_rank[i];
+    size_t cd = 1;
+    for (int k = 0; k < d; ++k) cd *= (size_t)r;
+    const double* U = an.tk + an.tk_off[i] + (size_t)s * cd * r;
+    for (int o = tid; o < r; o += nt) {
+        double acc = 0.0;
+        for (size_t m = 0; m < cd; ++m) {
+            double prod = __ldg(U + (size_t)o * cd + m);
+            size_t rem = m;
+            for (int k = d - 1; k >= 0; --k) {
+                prod *= z[k * r + (int)(rem % (size_t)r)];
+                rem /= (size_t)r;
+            }
+            acc += prod;
+        }
+        y[o] = acc;
+    }
+}
+
+// component a of the tensor term from y
+__device__ __forceinline__ double tk_out(const AnsatzView& an, int i, int a, const double* y)
+{
+    const int d = tk_degree(an, i), r = an.tk_rank[i];
+    size_t core = 1;
+    for (int k = 0; k <= d; ++k) core *= (size_t)r;
+    const double* Kout = an.tk + an.tk_off[i] + 4 * core;
+    double acc = 0.0;
+    for (int o = 0; o < r; ++o) acc = fma(__ldg(Kout + (size_t)a * r + o), y[o], acc);
+    return acc;
+}
 
 struct EnvArgs {
     AnsatzView an;

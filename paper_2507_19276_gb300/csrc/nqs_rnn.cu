@@ -46,12 +46,23 @@ __device__ __forceinline__ bool rnn_allowed(const AnsatzView& an, int i, int nad
 // the boundary source j = -1 is e_0 (M e_0 = column 0 of M).
 template <class Src>
 __device__ void rnn_vertex_warp(const AnsatzView& an, int i, const Src& src, double* cand,
-                                double P[4], int lane)
+                                double P[4], int lane, double* tkz)
 {
     const int D = an.D;
     const int e0 = an.chain ? i : an.pred_ptr[i];
     const int e1 = an.chain ? i + 1 : an.pred_ptr[i + 1];
+    // tensor term (BDG-TensorRNN): the sources' projections once, the core per local state
+    const bool tk = tk_has(an, i);
+    const int dr = tk ? tk_degree(an, i) * an.tk_rank[i] : 0;
+    if (tk) {
+        tk_project(an, i, src, tkz, lane, 32);
+        __syncwarp();
+    }
     for (int s = 0; s < 4; ++s) {
+        if (tk) {
+            tk_core(an, i, s, tkz, tkz + dr, lane, 32);
+            __syncwarp();
+        }
         double p = 0.0;
         for (int r = lane; r < D; r += 32) {
             double acc = __ldg(an.rv + ((size_t)i * 4 + s) * D + r);
@@ -65,12 +76,13 @@ __device__ void rnn_vertex_warp(const AnsatzView& an, int i, const Src& src, dou
                     for (int c = 0; c < D; ++c) acc = fma(__ldg(AT + (size_t)c * D + r), h[c], acc);
                 }
             }
+            if (tk) acc += tk_out(an, i, r, tkz + dr);
             cand[s * D + r] = acc;
             p = fma(__ldg(an.reta + (size_t)i * D + r) * acc, acc, p);
         }
         P[s] = warp_allsum(p);
+        __syncwarp();                   // y of this state read by every lane before the next
     }
-    __syncwarp();                       // cand visible to every lane
 }
 
 // The conditional of local state `sg` at vertex i and the sign of its phase:
@@ -105,13 +117,14 @@ __global__ void __launch_bounds__(256) k_rnn_env(RnnEnvArgs a)
     if (s >= a.Ns) return;
     const AnsatzView& an = a.an;
     const int K = an.K, D = an.D;
-    double* cand = sm + (size_t)warp * 4 * D;
+    double* cand = sm + (size_t)warp * (4 * D + an.tk_zy);
+    double* tkz = cand + 4 * D;
     const uint64_t na = a.samples[2 * s], nb = a.samples[2 * s + 1];
     double* cells = a.cells + (size_t)s * K * D;
     int nad = 0, nbd = 0, sign = 1;
     for (int i = 0; i < K; ++i) {
         double P[4];
-        rnn_vertex_warp(an, i, [&](int j) { return (const double*)(cells + (size_t)j * D); }, cand, P, lane);
+        rnn_vertex_warp(an, i, [&](int j) { return (const double*)(cells + (size_t)j * D); }, cand, P, lane, tkz);
         const int sg = sigma_at(na, nb, i);
         int neg;
         const double lp = rnn_pick(an, i, nad, nbd, sg, cand, P, lane, &neg);
@@ -136,7 +149,9 @@ __global__ void __launch_bounds__(256) k_rnn_env(RnnEnvArgs a)
 int launch_rnn_env(const RnnEnvArgs& a, cudaStream_t st)
 {
     if (a.Ns == 0) return 0;
-    k_rnn_env<<<(unsigned)((a.Ns + 7) / 8), 256, (size_t)8 * 4 * a.an.D * sizeof(double), st>>>(a);
+    const size_t smem = (size_t)8 * (4 * a.an.D + a.an.tk_zy) * sizeof(double);
+    allow_max_smem(k_rnn_env);
+    k_rnn_env<<<(unsigned)((a.Ns + 7) / 8), 256, smem, st>>>(a);
     return 1;
 }
 
@@ -150,7 +165,7 @@ int rnn_rows_per_block() { return kRnnRows; }
 
 static int rnn_warps(const AnsatzView& an)
 {
-    const size_t per = (size_t)(an.K + 4) * an.D * sizeof(double);
+    const size_t per = ((size_t)(an.K + 4) * an.D + an.tk_zy) * sizeof(double);
     int w = (int)((200u << 10) / per);
     return w < 1 ? 1 : (w > 8 ? 8 : w);
 }
@@ -181,8 +196,9 @@ __global__ void __launch_bounds__(256) k_rnn_amp(RnnAmpArgs a)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     if (warp == 0) build_lists_warp(na, nb, a.h.K, lists, lane);
     __syncthreads();
-    double* wc = sm + (size_t)warp * (K + 4) * D;    // this warp's cells of m, [K][D]
+    double* wc = sm + (size_t)warp * ((K + 4) * D + an.tk_zy);   // this warp's cells of m, [K][D]
     double* cand = wc + (size_t)K * D;
+    double* tkz = cand + 4 * D;
     const double* cn = a.cells + (size_t)s * K * D;  // n's cells
     for (int r = warp; r < nr; r += nw) {
         const Exc e = decode_rank(a.h, lists, a.rows.rank[r0 + r]);
@@ -197,7 +213,7 @@ __global__ void __launch_bounds__(256) k_rnn_amp(RnnAmpArgs a)
         for (int i = p; i < K; ++i) {
             double P[4];
             rnn_vertex_warp(an, i, [&](int jj) { return (const double*)(jj < p ? cn + (size_t)jj * D : wc + (size_t)jj * D); },
-                            cand, P, lane);
+                            cand, P, lane, tkz);
             const int sg = sigma_at(ma, mb, i);
             int neg;
             const double lp = rnn_pick(an, i, nad, nbd, sg, cand, P, lane, &neg);
@@ -246,7 +262,7 @@ int launch_rnn_amp(const RnnAmpArgs& a, cudaStream_t st)
 {
     if (a.rows.max_chunks == 0) return 0;
     const int w = rnn_warps(a.an);
-    const size_t smem = (size_t)w * (a.an.K + 4) * a.an.D * sizeof(double);
+    const size_t smem = (size_t)w * ((a.an.K + 4) * a.an.D + a.an.tk_zy) * sizeof(double);
     allow_max_smem(k_rnn_amp);
     k_rnn_amp<<<(unsigned)a.rows.max_chunks, 32 * w, smem, st>>>(a);
     return 1;
@@ -264,15 +280,16 @@ __global__ void __launch_bounds__(256) k_rnn_full(AnsatzView an, const uint64_t*
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int64_t id = (int64_t)blockIdx.x * nw + warp;
     if (id >= n) return;
-    double* wc = sm + (size_t)warp * (K + 4) * D;
+    double* wc = sm + (size_t)warp * ((K + 4) * D + an.tk_zy);
     double* cand = wc + (size_t)K * D;
+    double* tkz = cand + 4 * D;
     const uint64_t na = dets[2 * id], nb = dets[2 * id + 1];
     int nad = 0, nbd = 0, odd = 0;
     bool ok = true;
     double lp_sum = 0.0;
     for (int i = 0; i < K; ++i) {
         double P[4];
-        rnn_vertex_warp(an, i, [&](int jj) { return (const double*)(wc + (size_t)jj * D); }, cand, P, lane);
+        rnn_vertex_warp(an, i, [&](int jj) { return (const double*)(wc + (size_t)jj * D); }, cand, P, lane, tkz);
         const int sg = sigma_at(na, nb, i);
         int neg;
         const double lp = rnn_pick(an, i, nad, nbd, sg, cand, P, lane, &neg);
@@ -306,7 +323,7 @@ int launch_rnn_full(const AnsatzView& an, const uint64_t* dets, int64_t n, doubl
 {
     if (n == 0) return 0;
     const int w = rnn_warps(an);
-    const size_t smem = (size_t)w * (an.K + 4) * an.D * sizeof(double);
+    const size_t smem = (size_t)w * ((an.K + 4) * an.D + an.tk_zy) * sizeof(double);
     allow_max_smem(k_rnn_full);
     int launches = 0;
     const int64_t per = (int64_t)w * 65535 * 1024;
@@ -333,6 +350,8 @@ __global__ void __launch_bounds__(256) k_sample_level(SampleLevel a)
     const int64_t q = (int64_t)blockIdx.x * 8 + warp;
     if (q >= a.n_nodes) return;
     double* cand = a.cand + (size_t)q * 4 * D;
+    extern __shared__ double sm[];
+    double* tkz = sm + (size_t)warp * an.tk_zy;         // tensor-term scratch of this warp
     // cell of vertex jj (< i) of this node: level jj + 1 through the parent links
     auto src = [&](int jj) {
         int64_t idx = q;
@@ -340,7 +359,7 @@ __global__ void __launch_bounds__(256) k_sample_level(SampleLevel a)
         return (const double*)(a.cells[jj + 1] + (size_t)idx * D);
     };
     double P[4];
-    rnn_vertex_warp(an, i, src, cand, P, lane);
+    rnn_vertex_warp(an, i, src, cand, P, lane, tkz);
     const int nad = __popcll(a.pa[q]), nbd = __popcll(a.pb[q]);
     bool ok[4];
     int last = -1;
@@ -376,7 +395,7 @@ __global__ void __launch_bounds__(256) k_sample_level(SampleLevel a)
 int launch_sample_level(const SampleLevel& a, cudaStream_t st)
 {
     if (a.n_nodes == 0) return 0;
-    k_sample_level<<<(unsigned)((a.n_nodes + 7) / 8), 256, 0, st>>>(a);
+    k_sample_level<<<(unsigned)((a.n_nodes + 7) / 8), 256, (size_t)8 * a.an.tk_zy * sizeof(double), st>>>(a);
     return 1;
 }
 

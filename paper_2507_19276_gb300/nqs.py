@@ -105,6 +105,7 @@ def load():
             "nqs_local_energy_batch": [C.POINTER(vp), C.c_int, C.POINTER(BatchItem), C.c_int],
             "nqs_set_readout": [vp, vp, vp, vp, vp, C.c_int],
             "nqs_set_correlator": [vp, C.c_int, vp],
+            "nqs_set_tensor_term": [vp, vp, vp, i64],
             "nqs_sample": [vp, i64, u64, vp, vp, i64, C.POINTER(i64)],
         }
         for name, args in sig.items():
@@ -122,7 +123,7 @@ def exported_symbols():
             "nqs_set_hamiltonian", "nqs_set_ansatz", "nqs_connected", "nqs_amplitude",
             "nqs_draws", "nqs_draws_noalloc", "nqs_local_energy", "nqs_local_energy_batch",
             "nqs_grad_log_psi_vjp", "nqs_grad_log_psi_vjp2", "nqs_energy_gradient", "nqs_set_readout",
-            "nqs_set_correlator", "nqs_sample"]
+            "nqs_set_correlator", "nqs_set_tensor_term", "nqs_sample"]
 
 
 def _ptr(x):
@@ -185,6 +186,10 @@ def nqs_set_readout(ctx, v, eta, w, c, constrained=1):
 
 def nqs_set_correlator(ctx, kind, W2=None):
     _check(ctx, load().nqs_set_correlator(ctx, int(kind), _ptr(W2)))
+
+
+def nqs_set_tensor_term(ctx, ranks, params, n_params):
+    _check(ctx, load().nqs_set_tensor_term(ctx, _ptr(ranks), _ptr(params), int(n_params)))
 
 
 def nqs_sample(ctx, n_samples, seed, samples, counts, capacity):
@@ -333,6 +338,10 @@ class Context:
             self.set_readout(*rnn)
         if getattr(sys_, "corr", 0):
             self.set_correlator(sys_.corr, getattr(sys_, "rbm_W2", None))
+        tk = getattr(sys_, "tucker", None)
+        if tk is not None:
+            self._keep_tk = (_np(tk[0], np.int32), _np(tk[1], np.float64))
+            nqs_set_tensor_term(self.h, self._keep_tk[0], self._keep_tk[1], len(self._keep_tk[1]))
 
     def set_readout(self, v, eta, w, c, constrained=True):
         """The normalised MPS-RNN / BDG-RNN readout (nqs_set_readout)."""

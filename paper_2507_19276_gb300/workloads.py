@@ -61,6 +61,7 @@ class System:
     rnn: Optional[tuple] = None          # (v, eta, w, c): normalised readout
     corr: int = 0                        # 0 2cosh, 1 cos-RBM, 2 Ising-RBM
     rbm_W2: Optional[np.ndarray] = None  # [N_h][2K][2K] (Ising-RBM)
+    tucker: Optional[tuple] = None       # (ranks [K], packed parameters): tensor term
 
     @property
     def n_hidden(self) -> int:
@@ -342,6 +343,39 @@ def with_correlator(sys_, corr, seed=0, w2_std=0.005):
         W2 = 0.5 * (W2 + W2.transpose(0, 2, 1))
     return dataclasses.replace(sys_, corr=corr, rbm_W2=W2,
                                name=sys_.name + ("_cosrbm" if corr == 1 else "_isingrbm"))
+
+
+def tucker_ranks(pred_ptr, D):
+    """chi' = ceil(chi^(2/(d+1))) for every vertex with d >= 2 in-edges (Sec. 2.2),
+    0 for the others. Integer arithmetic: the smallest r with r^(d+1) >= chi^2."""
+    ranks = []
+    for i in range(len(pred_ptr) - 1):
+        d = int(pred_ptr[i + 1] - pred_ptr[i])
+        r = 0
+        if d >= 2:
+            r = 1
+            while r ** (d + 1) < D * D:
+                r += 1
+        ranks.append(r)
+    return np.array(ranks, np.int32)
+
+
+def with_tensor_term(sys_, seed=0, core_std=0.3):
+    """The same graph system with the BDG-TensorRNN tensor term (Sec. 2.2):
+    per vertex with d >= 2 in-edges and rank r = ceil(D^(2/(d+1))), a core
+    U [4][r^(d+1)] ~ N(0, core_std) and factor matrices Kout, K_1..K_d
+    [D][r] ~ N(0, 1/sqrt(D)), packed in vertex order."""
+    rng = np.random.Generator(np.random.PCG64(BASE_SEED + 500 + seed))
+    ranks = tucker_ranks(sys_.pred_ptr, sys_.D)
+    parts = []
+    for i, r in enumerate(ranks):
+        if r == 0:
+            continue
+        d = int(sys_.pred_ptr[i + 1] - sys_.pred_ptr[i])
+        parts.append(rng.normal(0.0, core_std, size=4 * r ** (d + 1)))
+        parts.append(rng.normal(0.0, 1.0 / math.sqrt(sys_.D), size=(d + 1) * sys_.D * r))
+    params = np.concatenate(parts) if parts else np.zeros(0)
+    return dataclasses.replace(sys_, tucker=(ranks, params), name=sys_.name + "_tensor")
 
 
 def h50_rnn(n_samples=4096, seed_offset=0, K=50, D=10, n_hidden=0, eps=0.01, n_draws=100):

@@ -194,3 +194,30 @@ def test_energy_gradient_matches_the_oracle(ctx, reweighted):
     rT, rW, rb, _ = _oracle_vjp(P, sys_, u, 1)
     assert np.max(np.abs(e - ref["e_loc"]) / _scale(ref)) < RTOL
     assert _close(gT, rT) and _close(gW, rW) and _close(gb, rb)
+
+
+def test_tensor_term_graph_linear_and_normalised_readouts(ctx):
+    """BDG-TensorRNN (Eq. bdg-rnn-update with the Tucker tensor term) on the
+    H18-shaped graph: amplitudes and FP64 E_loc with the linear readout, and
+    with the normalised readout (plus its sampler), against the oracle."""
+    base = W.with_tensor_term(W.h18_graph(n_samples=4), seed=3)
+    for sys_ in (base, W.with_readout(base, seed=6)):
+        P = O.Problem(sys_)
+        ctx.set_system(sys_)
+        ctx.set_precision(nqs.NQS_PREC_FP64)
+        la, sg = ctx.amplitude(sys_.samples)
+        for d, l, s in zip(sys_.samples, la, sg):
+            rl, rs, _ = O.log_psi(P, d)
+            assert s == rs and abs(l - rl) < 1e-12 * max(1.0, abs(rl))
+        e, _ = ctx.local_energy(sys_.samples, sys_.counts, sys_.eps, sys_.n_draws, sys_.seed)
+        ref = O.local_energy(P, cond=True)
+        err = np.max(np.abs(e - ref["e_loc"]) / _scale(ref))
+        print(f"{sys_.name}: FP64 max |dE| / max(|E|, e_abs) = {err:.3e}")
+        assert err < RTOL
+    got, cnt = ctx.sample(5000, 11)
+    ref, rcnt, _ = O.sample(O.Problem(W.with_readout(base, seed=6)), 5000, 11)
+    assert np.array_equal(got, ref) and np.array_equal(cnt, rcnt)
+    # the site-tensor gradient does not cover the tensor term
+    with pytest.raises(nqs.NQSError) as ei:
+        ctx.grad_log_psi_vjp(W.with_readout(base, seed=6).samples, np.ones(4))
+    assert ei.value.status == 6

@@ -212,3 +212,51 @@ def test_sampler_counts_follow_phi_squared():
     # a different seed gives a different but equally valid histogram
     got2, cnt2, _ = O.sample(P, N, 7)
     assert cnt2.sum() == N and not (len(got2) == len(got) and np.array_equal(cnt2, cnt))
+
+
+def _three_vertex_graph(D=3, seed=71):
+    """Vertices 0 <- l, 1 <- 0, 2 <- {0, 1}: vertex 2 carries the tensor term."""
+    base = W.tiny_system(K=3, na=1, nb=1, D=D, seed=seed)
+    rng = np.random.default_rng(seed)
+    ptr = np.array([0, 1, 2, 4], np.int32)
+    idx = np.array([-1, 0, 0, 1], np.int32)
+    T = rng.normal(0.0, 0.7, size=(4, 4, D, D))
+    return W.with_tensor_term(W.dataclasses.replace(base, tensors=T, pred_ptr=ptr, pred_idx=idx), seed=seed,
+                              core_std=0.8)
+
+
+def test_tensor_term_equals_the_dense_tucker_reconstruction():
+    """Eq. (bdg-rnn-update) with the Tucker form of Sec. 2.2: the factored
+    contraction of the oracle equals the full tensor T^s = U^s x Kout x K_1 x
+    K_2 rebuilt with numpy.einsum and applied to the source cells, for every
+    local-state string of a three-vertex graph (linear readout)."""
+    s = _three_vertex_graph()
+    D = s.D
+    ranks, params = s.tucker
+    assert list(ranks) == [0, 0, 3]          # ceil(3^(2/3)) = 3 for the two-edge vertex
+    r = 3
+    U = params[:4 * r ** 3].reshape(4, r, r, r)
+    Kout, K1, K2 = params[4 * r ** 3:].reshape(3, D, r)
+    Tfull = np.einsum("sopq,ao,bp,cq->sabc", U, Kout, K1, K2)
+    P = O.Problem(s)
+    e0 = np.eye(D)[:, 0]
+    for sig in itertools.product(range(4), repeat=3):
+        det = np.array([sum(((x & 1) << i) for i, x in enumerate(sig)),
+                        sum(((x >> 1) << i) for i, x in enumerate(sig))], np.uint64)
+        h0 = s.tensors[0, sig[0]] @ e0
+        h1 = s.tensors[1, sig[1]] @ h0
+        h2 = s.tensors[2, sig[2]] @ h0 + s.tensors[3, sig[2]] @ h1 + np.einsum("abc,b,c->a", Tfull[sig[2]], h0, h1)
+        la, sg, _ = O.log_psi(P, det)
+        if h2[0] == 0.0:
+            assert sg == 0
+        else:
+            assert sg == (1 if h2[0] > 0 else -1)
+            assert abs(la - np.log(abs(h2[0]))) < 1e-12
+
+
+def test_tensor_term_keeps_the_readout_normalised():
+    """BDG-TensorRNN with the normalised readout: sum |Phi|^2 = 1."""
+    s = W.with_readout(_three_vertex_graph(D=4, seed=72), seed=5)
+    s = W.dataclasses.replace(s, n_alpha=1, n_beta=2)
+    total = _phi2(O.Problem(s), W.all_dets(3, 1, 2)).sum()
+    assert abs(total - 1.0) < 1e-13
