@@ -261,8 +261,10 @@ static const double* tucker_block(const or_ansatz* a, int i, int* d, int* r)
 }
 
 /* Tensor term t_i^s of vertex i for the in-edge sources src[k] (length D
- * each): added to out[0..D). */
-static void tensor_term(const or_ansatz* a, int i, int s, const double* const* src, double* out)
+ * each): added to out[0..D). With absval, every parameter enters by its
+ * absolute value (the sources are passed as absolute values by the caller):
+ * the magnitude scale of the same expression (see or_log_psi_p1). */
+static void tensor_term_x(const or_ansatz* a, int i, int s, const double* const* src, double* out, int absval)
 {
     int d = 0, r = 0;
     const double* blk = tucker_block(a, i, &d, &r);
@@ -277,7 +279,10 @@ static void tensor_term(const or_ansatz* a, int i, int s, const double* const* s
         const double* Kk = Kout + (size_t)(k + 1) * D * r;
         for (int q = 0; q < r; ++q) {
             double acc = 0.0;
-            for (int b = 0; b < D; ++b) acc += Kk[(size_t)b * r + q] * src[k][b];
+            for (int b = 0; b < D; ++b) {
+                const double kk = Kk[(size_t)b * r + q];
+                acc += (absval ? fabs(kk) : kk) * src[k][b];
+            }
             z[k * r + q] = acc;
         }
     }
@@ -286,7 +291,7 @@ static void tensor_term(const or_ansatz* a, int i, int s, const double* const* s
         double acc = 0.0;
         for (size_t m = 0; m < core; ++m) {
             /* digits of m: a_1' (most significant) .. a_d' */
-            double prod = U[(size_t)o * core + m];
+            double prod = absval ? fabs(U[(size_t)o * core + m]) : U[(size_t)o * core + m];
             size_t rem = m;
             for (int k = d - 1; k >= 0; --k) {
                 prod *= z[k * r + (int)(rem % (size_t)r)];
@@ -298,11 +303,19 @@ static void tensor_term(const or_ansatz* a, int i, int s, const double* const* s
     }
     for (int q = 0; q < D; ++q) {
         double acc = 0.0;
-        for (int o = 0; o < r; ++o) acc += Kout[(size_t)q * r + o] * y[o];
+        for (int o = 0; o < r; ++o) {
+            const double ko = Kout[(size_t)q * r + o];
+            acc += (absval ? fabs(ko) : ko) * y[o];
+        }
         out[q] += acc;
     }
     free(z);
     free(y);
+}
+
+static void tensor_term(const or_ansatz* a, int i, int s, const double* const* src, double* out)
+{
+    tensor_term_x(a, i, s, src, out, 0);
 }
 
 /* Rescale v by a power of two so that max|v| is in [0.5, 1); returns the exponent. */
@@ -317,8 +330,10 @@ static int renorm(double* v, int D)
     return e;
 }
 
-/* Forward states h_i (scaled, exponents ex[i]) for sigma[0..K-1]. */
-static void forward_states(const or_ansatz* a, const int* sigma, double* hs, int* ex)
+/* Forward states h_i (scaled, exponents ex[i]) for sigma[0..K-1]; with
+ * absval every parameter enters by its absolute value (the magnitude scale of
+ * the same contraction, see or_log_psi_p1). */
+static void forward_states_x(const or_ansatz* a, const int* sigma, double* hs, int* ex, int absval)
 {
     const int K = a->K, D = a->D;
     double* tmp = (double*)malloc(sizeof(double) * D);
@@ -349,7 +364,7 @@ static void forward_states(const or_ansatz* a, const int* sigma, double* hs, int
                 double s = 0.0;
                 for (int c = 0; c < D; ++c) {
                     double hj = (j < 0) ? (c == 0 ? 1.0 : 0.0) : hs[(size_t)j * D + c];
-                    s += M[r * D + c] * hj;
+                    s += (absval ? fabs(M[r * D + c]) : M[r * D + c]) * hj;
                 }
                 tmp[r] = s;
             }
@@ -363,13 +378,18 @@ static void forward_states(const or_ansatz* a, const int* sigma, double* hs, int
                 src[e - e0] = j < 0 ? e0v : hs + (size_t)j * D;
             }
             for (int r = 0; r < D; ++r) tmp[r] = 0.0;
-            tensor_term(a, i, sigma[i], src, tmp);
+            tensor_term_x(a, i, sigma[i], src, tmp, absval);
             for (int r = 0; r < D; ++r) hi[r] += ldexp(tmp[r], et - eref);
         }
         ex[i] = eref + renorm(hi, D);
     }
     free(tmp);
     free(e0v);
+}
+
+static void forward_states(const or_ansatz* a, const int* sigma, double* hs, int* ex)
+{
+    forward_states_x(a, sigma, hs, ex, 0);
 }
 
 static void sigma_of(int K, const uint64_t* det, int* sigma)
@@ -641,6 +661,17 @@ double or_log_psi_p1(const or_ansatz* a, const uint64_t* det)
     sigma_of(K, det, sigma);
     double* hs = (double*)malloc(sizeof(double) * (size_t)K * D);
     int* ex = (int*)malloc(sizeof(int) * K);
+    if (a->tucker_rank) {
+        /* with the (multilinear) tensor term: the whole contraction evaluated with
+         * absolute values of every parameter -- a sum of products whose rounding
+         * error is at most ~(depth) u times this value (Higham, Ch. 3) */
+        forward_states_x(a, sigma, hs, ex, 1);
+        const double v = hs[(size_t)(K - 1) * D];
+        const int e = ex[K - 1];
+        free(hs);
+        free(ex);
+        return v > 0.0 ? log(v) + (double)e * M_LN2 : -INFINITY;
+    }
     forward_states(a, sigma, hs, ex);
     /* adjoints g_i = d psi_TN / d h_i, scaled with exponents gx */
     double* gs = (double*)calloc((size_t)K * D, sizeof(double));
@@ -810,8 +841,8 @@ static void one_sample(const or_ham* h, const or_ansatz* a, const uint64_t* n, i
                        double eps, int n_draws, uint64_t seed, or_sample_out* o, int with_cond)
 {
     memset(o, 0, sizeof(*o));
-    /* the first-order bound P1 describes the linear readout's matrix contraction */
-    if (a->readout != 0 || a->tucker_rank) with_cond = 0;
+    /* the first-order bound P1 describes the linear readout's contraction */
+    if (a->readout != 0) with_cond = 0;
     double la_n, lf_n;
     int sg_n;
     or_log_psi(a, n, &la_n, &sg_n, &lf_n);

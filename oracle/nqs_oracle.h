@@ -136,7 +136,11 @@ void or_log_psi(const or_ansatz* a, const uint64_t* det, double* log_abs, int* s
  * through g_i, so u P1 bounds the rounding error of psi_TN to first order
  * (running-error analysis; Higham, Accuracy and Stability of Numerical
  * Algorithms, 2nd ed., Ch. 3). For a chain it is
- * sum_t |R_{t+1}|^T |A_t^{sigma_t}| |L_{t-1}|, which grows linearly in K. */
+ * sum_t |R_{t+1}|^T |A_t^{sigma_t}| |L_{t-1}|, which grows linearly in K.
+ * With the tensor term (multilinear in the sources) it is instead the whole
+ * contraction evaluated with the absolute values of every parameter: psi_TN
+ * is a sum of products, and its rounding error is at most about (depth) u
+ * times that value (ibid.). */
 double or_log_psi_p1(const or_ansatz* a, const uint64_t* det);
 
 /* Draw indices (canonical rank) of the stochastic part for sample n with

@@ -260,3 +260,19 @@ def test_tensor_term_keeps_the_readout_normalised():
     s = W.dataclasses.replace(s, n_alpha=1, n_beta=2)
     total = _phi2(O.Problem(s), W.all_dets(3, 1, 2)).sum()
     assert abs(total - 1.0) < 1e-13
+
+
+def test_tensor_term_rounding_scale_is_psi_for_nonnegative_parameters():
+    """With the tensor term the rounding scale P1 is the contraction evaluated
+    with absolute values: for nonnegative tensors, factors and cores it is
+    psi_TN itself; with signs it can only be larger."""
+    s = _three_vertex_graph(D=3, seed=73)
+    pos = W.dataclasses.replace(s, tensors=np.abs(s.tensors), tucker=(s.tucker[0], np.abs(s.tucker[1])))
+    Pp, Ps = O.Problem(pos), O.Problem(s)
+    for sig in itertools.product(range(4), repeat=3):
+        det = np.array([sum(((x & 1) << i) for i, x in enumerate(sig)),
+                        sum(((x >> 1) << i) for i, x in enumerate(sig))], np.uint64)
+        la, sg, _ = O.log_psi(Pp, det)
+        assert sg == 1 and abs(O.log_psi_p1(Pp, det) - la) < 1e-12
+        la_s, _, _ = O.log_psi(Ps, det)
+        assert O.log_psi_p1(Ps, det) >= la_s - 1e-12
