@@ -317,7 +317,8 @@ def run(args):
     prec = {"mixed": nqs.NQS_PREC_MIXED, "fp64": nqs.NQS_PREC_FP64,
             "fp64_shared": nqs.NQS_PREC_FP64_SHARED}[args.precision]
     tol = args.energy_tol if prec == nqs.NQS_PREC_MIXED else 0.0
-    ctx.set_precision(prec, timing=True, sample_index_base=lo, energy_tolerance=tol)
+    ctx.set_precision(prec, timing=True, sample_index_base=lo, energy_tolerance=tol,
+                      tile_blocks_per_sm=args.tile_bps, table_mb=args.table_mb)
 
     samples = torch.from_numpy(sys_.samples.view(np.int64)).to(dev)
     counts = torch.from_numpy(sys_.counts).to(dev)
@@ -812,6 +813,10 @@ def main():
                     help="skip the L2 / FMA ceilings measured before the timed region")
     ap.add_argument("--no-autotune", action="store_true",
                     help="uneven batch: default schedule instead of the autotuner's")
+    ap.add_argument("--tile-bps", type=int, default=0,
+                    help="site-tile blocks per SM (schedule only; 0: the library's default)")
+    ap.add_argument("--table-mb", type=int, default=0,
+                    help="cap (MiB) on one sample batch's shared-prefix tables (schedule only; 0: default)")
     ap.add_argument("--grad", action="store_true",
                     help="also time the energy gradient (uneven batch; h18 / h50_rnn workloads)")
     ap.add_argument("--peaks", action="store_true",

@@ -526,9 +526,10 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
     // batch size from a memory budget
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
-    size_t budget = std::min<size_t>((size_t)8 << 30, free_b / 3);
+    // the table cap (table_mb, or 8 GiB), never more than a third of the free memory
+    const size_t cap = c->table_mb > 0 ? (size_t)c->table_mb << 20 : (size_t)8 << 30;
+    size_t budget = std::min<size_t>(cap, free_b / 3);
     if (c->fam_budget > 0) budget = std::min(budget, c->fam_budget);
-    if (c->table_mb > 0) budget = std::min(budget, (size_t)c->table_mb << 20);
     const size_t per = fam_bytes_per_sample(K, D, sizeof(T));
     int64_t nb = (int64_t)std::max<size_t>(1, budget / per);
     if (nb > Ns) nb = Ns;
@@ -1080,7 +1081,7 @@ extern "C" int nqs_set_tensor_term(nqs_ctx* c, const int* ranks, const double* p
         if (core > 1e8) return set_err(c, NQS_ERR_INVALID_ARG, "tensor-term core of vertex %d has %g entries", i, core);
         off[(size_t)i] = total;
         total += 4 * (long long)core + (long long)(d + 1) * D * r;
-        zy = std::max(zy, (d + 1) * r);
+        zy = std::max(zy, (d + 4) * r);      // z [d][r] and y of the four local states
     }
     if (n_params != total)
         return set_err(c, NQS_ERR_INVALID_ARG, "n_params = %lld, the ranks and in-degrees need %lld",

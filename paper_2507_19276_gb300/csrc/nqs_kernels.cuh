@@ -157,7 +157,7 @@ struct AnsatzView {
     const int* tk_rank;                  // [K] (NULL: no tensor term)
     const long long* tk_off;             // [K] (-1: none)
     const double* tk;
-    int tk_zy;                           // scratch doubles per evaluation: max (d + 1) r
+    int tk_zy;                           // scratch doubles per evaluation: max (d + 4) r
 };
 
 // ---- tensor term (Tucker form), shared by the FP64 kernels ------------------

@@ -51,37 +51,42 @@ __device__ void rnn_vertex_warp(const AnsatzView& an, int i, const Src& src, dou
     const int D = an.D;
     const int e0 = an.chain ? i : an.pred_ptr[i];
     const int e1 = an.chain ? i + 1 : an.pred_ptr[i + 1];
-    // tensor term (BDG-TensorRNN): the sources' projections once, the core per local state
+    // tensor term (BDG-TensorRNN): the sources' projections once, the core of
+    // every local state, z [d][r] then y [4][r] in the scratch
     const bool tk = tk_has(an, i);
-    const int dr = tk ? tk_degree(an, i) * an.tk_rank[i] : 0;
+    const int rk = tk ? an.tk_rank[i] : 0;
+    const int dr = tk ? tk_degree(an, i) * rk : 0;
     if (tk) {
         tk_project(an, i, src, tkz, lane, 32);
         __syncwarp();
+        for (int s = 0; s < 4; ++s) tk_core(an, i, s, tkz, tkz + dr + s * rk, lane, 32);
+        __syncwarp();
     }
-    for (int s = 0; s < 4; ++s) {
-        if (tk) {
-            tk_core(an, i, s, tkz, tkz + dr, lane, 32);
-            __syncwarp();
+    // the 4 D candidate entries spread over the lanes (local state, component)
+    for (int q = lane; q < 4 * D; q += 32) {
+        const int s = q / D, r = q - s * D;
+        double acc = __ldg(an.rv + ((size_t)i * 4 + s) * D + r);
+        for (int e = e0; e < e1; ++e) {
+            const int j = an.chain ? e - 1 : an.pred_idx[e];
+            const double* AT = an.AT + ((size_t)e * 4 + s) * D * D;    // AT[c][r] = M[r][c]
+            if (j < 0) {
+                acc += __ldg(AT + r);
+            } else {
+                const double* h = src(j);
+                for (int c = 0; c < D; ++c) acc = fma(__ldg(AT + (size_t)c * D + r), h[c], acc);
+            }
         }
+        if (tk) acc += tk_out(an, i, r, tkz + dr + s * rk);
+        cand[q] = acc;
+    }
+    __syncwarp();                       // cand visible to every lane
+    for (int s = 0; s < 4; ++s) {
         double p = 0.0;
         for (int r = lane; r < D; r += 32) {
-            double acc = __ldg(an.rv + ((size_t)i * 4 + s) * D + r);
-            for (int e = e0; e < e1; ++e) {
-                const int j = an.chain ? e - 1 : an.pred_idx[e];
-                const double* AT = an.AT + ((size_t)e * 4 + s) * D * D;    // AT[c][r] = M[r][c]
-                if (j < 0) {
-                    acc += __ldg(AT + r);
-                } else {
-                    const double* h = src(j);
-                    for (int c = 0; c < D; ++c) acc = fma(__ldg(AT + (size_t)c * D + r), h[c], acc);
-                }
-            }
-            if (tk) acc += tk_out(an, i, r, tkz + dr);
-            cand[s * D + r] = acc;
-            p = fma(__ldg(an.reta + (size_t)i * D + r) * acc, acc, p);
+            const double h = cand[s * D + r];
+            p = fma(__ldg(an.reta + (size_t)i * D + r) * h, h, p);
         }
         P[s] = warp_allsum(p);
-        __syncwarp();                   // y of this state read by every lane before the next
     }
 }
 

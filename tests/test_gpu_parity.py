@@ -399,3 +399,20 @@ def test_sixty_four_orbitals_lists_draws_and_energies(ctx):
                 assert _rel_sum(e, ref) < RTOL_FP64
     finally:
         ctx.set_precision(nqs.NQS_PREC_FP64)
+
+
+def test_schedule_options_do_not_change_results(ctx):
+    """tile_blocks_per_sm and table_mb (the autotuner's knobs) change only the
+    launch shapes and the sample-batch split of the shared-prefix tables: the
+    mixed and FP64-shared E_loc stay bit-identical."""
+    sys_ = W.h50_chain(n_samples=48)
+    try:
+        for prec in (nqs.NQS_PREC_MIXED, nqs.NQS_PREC_FP64_SHARED):
+            _load(ctx, sys_, prec)
+            ref, _ = ctx.local_energy(sys_.samples, sys_.counts, sys_.eps, sys_.n_draws, sys_.seed)
+            for bps, mb in [(2, 0), (8, 0), (4, 40)]:
+                ctx.set_precision(prec, tile_blocks_per_sm=bps, table_mb=mb)
+                e, _ = ctx.local_energy(sys_.samples, sys_.counts, sys_.eps, sys_.n_draws, sys_.seed)
+                assert np.array_equal(e.view(np.uint64), ref.view(np.uint64)), (prec, bps, mb)
+    finally:
+        ctx.set_precision(nqs.NQS_PREC_FP64)
