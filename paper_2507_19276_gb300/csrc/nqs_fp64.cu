@@ -289,7 +289,9 @@ int amp_fp64_rows_per_block(const AnsatzView& an)
         int r = 4096 / an.D;
         return r < 4 ? 4 : (r > 64 ? 64 : r);
     }
-    int r = 16384 / (an.K * an.D);
+    // rows of the states kept in shared memory ([R][K][D] doubles): about 32 KB,
+    // so that several blocks share an SM and their FMA chains overlap
+    int r = 4096 / (an.K * an.D);
     return r < 1 ? 1 : (r > 32 ? 32 : r);
 }
 
@@ -389,8 +391,7 @@ __global__ void k_amp_chain_fp64(AmpArgs a)
             if (t < info[r].p || t > info[r].q) continue;
             const double* AT = tens(a.an.AT, t, sigma_at(info[r].ma, info[r].mb, t), D);
             const double* x = X + (size_t)r * D;
-            double acc = 0.0;
-            for (int k = 0; k < D; ++k) acc = fma(__ldg(AT + k * D + c), x[k], acc);
+            const double acc = dot_col4(AT, x, D, c);
             Y[(size_t)r * D + c] = acc;
         }
         __syncthreads();
@@ -513,7 +514,7 @@ __global__ void k_amp_graph_fp64(AmpArgs a)
                 else {
                     const double* hj = jj < p ? Hs + (size_t)jj * D : S + ((size_t)r * K + jj) * D;
                     ej = jj < p ? He[jj] : SX[r * K + jj];
-                    for (int k = 0; k < D; ++k) t = fma(__ldg(AT + k * D + c), hj[k], t);
+                    t = dot_col4(AT, hj, D, c);
                 }
                 acc += ldexp(t, ej - eref);
             }

@@ -160,6 +160,23 @@ struct AnsatzView {
     int tk_zy;                           // scratch doubles per evaluation: max (d + 4) r
 };
 
+// sum_k AT[k][c] x[k] (AT row-major D x D) with four interleaved partial sums:
+// independent FMA chains that hide the FP64 pipe's latency, combined as
+// (s0 + s1) + (s2 + s3)
+__device__ __forceinline__ double dot_col4(const double* AT, const double* x, int D, int c)
+{
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int k = 0;
+    for (; k + 3 < D; k += 4) {
+        s0 = fma(__ldg(AT + (size_t)k * D + c), x[k], s0);
+        s1 = fma(__ldg(AT + (size_t)(k + 1) * D + c), x[k + 1], s1);
+        s2 = fma(__ldg(AT + (size_t)(k + 2) * D + c), x[k + 2], s2);
+        s3 = fma(__ldg(AT + (size_t)(k + 3) * D + c), x[k + 3], s3);
+    }
+    for (; k < D; ++k) s0 = fma(__ldg(AT + (size_t)k * D + c), x[k], s0);
+    return (s0 + s1) + (s2 + s3);
+}
+
 // ---- tensor term (Tucker form), shared by the FP64 kernels ------------------
 // t_i^s[a] = sum_o Kout[a][o] y[o],  y[o] = sum_{a_1'..a_d'} U^s[o][a_1']..[a_d']
 // prod_k z_k[a_k'],  z_k[q] = sum_b K_k[b][q] h_{j_k}[b] (h_{-1} = e_0).

@@ -72,8 +72,7 @@ __device__ void rnn_vertex_warp(const AnsatzView& an, int i, const Src& src, dou
             if (j < 0) {
                 acc += __ldg(AT + r);
             } else {
-                const double* h = src(j);
-                for (int c = 0; c < D; ++c) acc = fma(__ldg(AT + (size_t)c * D + r), h[c], acc);
+                acc += dot_col4(AT, src(j), D, r);
             }
         }
         if (tk) acc += tk_out(an, i, r, tkz + dr + s * rk);
@@ -263,9 +262,167 @@ __global__ void __launch_bounds__(256) k_rnn_amp(RnnAmpArgs a)
     }
 }
 
+// Chain readout, the block's 32 rows in lockstep over the vertices: per vertex
+// the four site matrices are staged once in shared memory for every row, the
+// 4 D candidate entries of all rows spread over the block (four independent
+// FMA chains each), then one thread per (row, local state) forms P and one
+// thread per row the normaliser, the choice and the phase. The arithmetic of
+// each row is that of k_rnn_amp up to the order of the sums.
+constexpr int kRnnChainMaxD = 32;
+
+__global__ void __launch_bounds__(256) k_rnn_amp_chain(RnnAmpArgs a)
+{
+    extern __shared__ double sm[];
+    __shared__ OrbLists lists;
+    __shared__ uint64_t s_ma[kRnnRows], s_mb[kRnnRows];
+    __shared__ int s_p[kRnnRows], s_nad[kRnnRows], s_nbd[kRnnRows], s_odd[kRnnRows], s_ok[kRnnRows];
+    __shared__ int s_sig[kRnnRows];
+    __shared__ double s_lpm[kRnnRows], s_term[kRnnRows];
+    __shared__ int s_tmin;
+    const AnsatzView& an = a.an;
+    const int K = an.K, D = an.D;
+    const int64_t b = blockIdx.x;
+    const int64_t* cb = a.rows.chunk_base;
+    if (b >= cb[a.Ns]) return;
+    int64_t lo = 0, hi = a.Ns - 1;                  // largest s with cb[s] <= b
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (cb[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    const int64_t s = lo;
+    const int64_t j = b - cb[s];
+    const int64_t beg = a.rows.begin ? a.rows.begin[s] : s * a.rows.stride;
+    const int64_t cnt = a.rows.count[s];
+    const int64_t r0 = beg + j * kRnnRows;
+    const int nr = (int)((cnt - j * kRnnRows) < kRnnRows ? (cnt - j * kRnnRows) : kRnnRows);
+    const uint64_t na = a.samples[2 * s], nb = a.samples[2 * s + 1];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double* AT4 = sm;                                // [4][D][D]: AT4[s][c][a] = M_t^s[a][c]
+    double* cell = AT4 + (size_t)4 * D * D;          // [R][D] each row's previous cell
+    double* cand = cell + (size_t)kRnnRows * D;      // [R][4][D]
+    double* Pv = cand + (size_t)kRnnRows * 4 * D;    // [R][4]
+    if (tid < 32) build_lists_warp(na, nb, a.h.K, lists, tid);
+    if (tid == 0) s_tmin = K;
+    __syncthreads();
+    if (tid < nr) {
+        const Exc e = decode_rank(a.h, lists, a.rows.rank[r0 + tid]);
+        uint64_t ma = na, mb = nb;
+        flip(ma, mb, e.i); flip(ma, mb, e.a);
+        if (e.kind == 2) { flip(ma, mb, e.j); flip(ma, mb, e.b); }
+        const int p = __ffsll((long long)((na ^ ma) | (nb ^ mb))) - 1;
+        s_ma[tid] = ma; s_mb[tid] = mb; s_p[tid] = p;
+        s_nad[tid] = __popcll(na & low_mask(p));
+        s_nbd[tid] = __popcll(nb & low_mask(p));
+        s_odd[tid] = 0; s_ok[tid] = 1; s_lpm[tid] = 0.0;
+        atomicMin(&s_tmin, p);
+    }
+    __syncthreads();
+    const double* cn = a.cells + (size_t)s * K * D;  // n's cells
+    for (int t = s_tmin; t < K; ++t) {
+        // the site matrices of vertex t, and the previous cell of the rows entering at t
+        const double* ATg = an.AT + (size_t)t * 4 * D * D;
+        for (int q = tid; q < 4 * D * D; q += nt) AT4[q] = __ldg(ATg + q);
+        for (int q = tid; q < nr * D; q += nt) {
+            const int r = q / D, c = q - r * D;
+            if (s_p[r] == t) cell[q] = t == 0 ? (c == 0 ? 1.0 : 0.0) : cn[(size_t)(t - 1) * D + c];
+        }
+        __syncthreads();
+        for (int q = tid; q < nr * 4 * D; q += nt) {
+            const int r = q / (4 * D), sa = q - r * 4 * D, sg = sa / D, c = sa - sg * D;
+            if (t < s_p[r]) continue;
+            const double* M = AT4 + (size_t)sg * D * D;
+            const double* h = cell + (size_t)r * D;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int k = 0;
+            for (; k + 3 < D; k += 4) {
+                s0 = fma(M[(size_t)k * D + c], h[k], s0);
+                s1 = fma(M[(size_t)(k + 1) * D + c], h[k + 1], s1);
+                s2 = fma(M[(size_t)(k + 2) * D + c], h[k + 2], s2);
+                s3 = fma(M[(size_t)(k + 3) * D + c], h[k + 3], s3);
+            }
+            for (; k < D; ++k) s0 = fma(M[(size_t)k * D + c], h[k], s0);
+            cand[q] = __ldg(an.rv + ((size_t)t * 4 + sg) * D + c) + ((s0 + s1) + (s2 + s3));
+        }
+        __syncthreads();
+        for (int q = tid; q < nr * 4; q += nt) {
+            const int r = q >> 2, sg = q & 3;
+            if (t < s_p[r]) continue;
+            const double* h = cand + (size_t)(r * 4 + sg) * D;
+            double p = 0.0;
+            for (int c = 0; c < D; ++c) p = fma(__ldg(an.reta + (size_t)t * D + c) * h[c], h[c], p);
+            Pv[q] = p;
+        }
+        __syncthreads();
+        if (tid < nr && t >= s_p[tid]) {
+            const int r = tid, sg = sigma_at(s_ma[r], s_mb[r], t);
+            double Z = 0.0;
+            for (int q = 0; q < 4; ++q)
+                if (rnn_allowed(an, t, s_nad[r], s_nbd[r], q)) Z += Pv[r * 4 + q];
+            const double P = Pv[r * 4 + sg];
+            double ph = __ldg(an.rc + t);
+            const double* h = cand + (size_t)(r * 4 + sg) * D;
+            for (int c = 0; c < D; ++c) ph = fma(__ldg(an.rw + (size_t)t * D + c), h[c], ph);
+            if (!rnn_allowed(an, t, s_nad[r], s_nbd[r], sg) || !(P > 0.0) || !(Z > 0.0)) s_ok[r] = 0;
+            else {
+                s_lpm[r] += 0.5 * (log(P) - log(Z));
+                s_odd[r] ^= ph < 0.0;
+            }
+            s_sig[r] = sg;
+            s_nad[r] += sg & 1;
+            s_nbd[r] += sg >> 1;
+        }
+        __syncthreads();
+        for (int q = tid; q < nr * D; q += nt) {
+            const int r = q / D, c = q - r * D;
+            if (t >= s_p[r]) cell[q] = cand[(size_t)(r * 4 + s_sig[r]) * D + c];
+        }
+        __syncthreads();
+    }
+    // n's suffix of conditionals and signs, the correlator ratio, the term (one warp per row)
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    for (int r = warp; r < nr; r += nw) {
+        const int p = s_p[r];
+        double lpn = 0.0;
+        int oddn = 0;
+        for (int i = p + lane; i < K; i += 32) {
+            lpn += a.lp[(size_t)s * K + i];
+            oddn ^= a.sg[(size_t)s * K + i] < 0;
+        }
+        for (int o = 16; o; o >>= 1) {
+            lpn += __shfl_xor_sync(kFull, lpn, o);
+            oddn ^= __shfl_xor_sync(kFull, oddn, o);
+        }
+        int negf;
+        const double lr = corr_log_ratio_warp(an, s, a.theta, a.lc, na, nb, s_ma[r], s_mb[r], lane, &negf);
+        if (lane == 0) {
+            double tv = 0.0;
+            if (s_ok[r]) {
+                tv = a.rows.coef[r0 + r] * exp(s_lpm[r] - lpn + lr);
+                if (s_odd[r] ^ oddn ^ negf) tv = -tv;
+            }
+            s_term[r] = tv;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double acc = 0.0;
+        int64_t sp = 0;
+        for (int r = 0; r < nr; ++r) { acc += s_term[r]; sp += K - s_p[r]; }
+        a.partial[b] = acc;
+        if (a.span) a.span[b] = sp;
+    }
+}
+
 int launch_rnn_amp(const RnnAmpArgs& a, cudaStream_t st)
 {
     if (a.rows.max_chunks == 0) return 0;
+    if (a.an.chain && a.an.D <= kRnnChainMaxD) {
+        const int D = a.an.D;
+        const size_t smem = ((size_t)4 * D * D + (size_t)kRnnRows * D * 5 + (size_t)kRnnRows * 4) * sizeof(double);
+        allow_max_smem(k_rnn_amp_chain);
+        k_rnn_amp_chain<<<(unsigned)a.rows.max_chunks, 256, smem, st>>>(a);
+        return 1;
+    }
     const int w = rnn_warps(a.an);
     const size_t smem = (size_t)w * ((a.an.K + 4) * a.an.D + a.an.tk_zy) * sizeof(double);
     allow_max_smem(k_rnn_amp);
