@@ -408,6 +408,21 @@ def run(args):
     roof["frac"] = roof["achieved"] / roof["peak"]
     # the same stage against the work the shared-prefix form executes
     roof["executed_frac"] = executed / (amp_ms / 1e3) / 1e12 / roof["peak"]
+    # the row kernel (k_fam_rows, the largest share of the mixed step) against the
+    # on-chip rate it is bound by: per row it gathers the left and right vectors
+    # (D floats each) and, with a correlator, one factor row per side (N_h
+    # rounded up to 4, plus the P - 1 group: 4 more floats)
+    roof_rows = None
+    if live and prec == nqs.NQS_PREC_MIXED:
+        rows_ms = (stages["amp_det"][0] + stages["amp_draw"][0]) / args.steps
+        NH = sys_.n_hidden
+        per_row = 4.0 * (2 * D + (2 * (((NH + 3) // 4) * 4 + 4) if NH else 0))
+        l2 = max(live["l2_read_gbs"].values())
+        ach = per_row * n_amp / (rows_ms / 1e3) / 1e9
+        roof_rows = {"bound": "l2", "unit": "GB/s", "achieved": ach, "peak": l2, "frac": ach / l2,
+                     "peak_source": "L2 streaming read rate measured before the timed region (peaks probe)",
+                     "kernel": "k_fam_rows (gathers of the left/right vectors and correlator rows)",
+                     "bytes_per_row": per_row, "stage_ms_per_step": rows_ms, "traffic": None}
     # enumeration stage (count pass, write pass, draws): algorithmic integral
     # bytes against the measured L2 rates (the integral table is L2-resident)
     enum_ms = sum(stages[k][0] for k in ("count", "write", "draw")) / args.steps
@@ -478,6 +493,7 @@ def run(args):
             "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
             "roofline": roof,
             "roofline_enum": roof_enum,
+            "roofline_rows": roof_rows,
             "measured_ceilings": live,
             "fp64_gpu": fp64,
             "e2e": {"value": total * args.steps / (e2e_ms / 1e3), "unit": UNIT,
