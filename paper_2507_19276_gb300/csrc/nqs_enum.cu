@@ -35,7 +35,8 @@ __global__ void __launch_bounds__(kEnumWarps * 32) k_enum(EnumArgs a)
         if (valid) {
             uint64_t ma, mb;
             int odd;
-            Exc e = decode_rank(h, lists, r);
+            // the split and the weights depend on |H| only: no phase here
+            Exc e = decode_rank<false>(h, lists, r);
             H = matrix_element(h, na, nb, e, ma, mb, odd);
         }
         const bool det = valid && is_det(H, a.eps_bits);
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(256) k_draws(DrawArgs a)
     const uint32_t r = c * 32 + lane;
     uint64_t w = 0;
     if (r < a.h.n_conn) {
-        Exc e = decode_rank(a.h, lists[warp], r);
+        Exc e = decode_rank<false>(a.h, lists[warp], r);     // weights need |H| only
         uint64_t ma, mb;
         int odd;
         const double H = matrix_element(a.h, na, nb, e, ma, mb, odd);

@@ -378,7 +378,7 @@ struct RowParts {
 __device__ __forceinline__ RowParts row_parts(const HamView& h, const OrbLists& L, uint64_t na,
                                               uint64_t nb, uint32_t rank)
 {
-    const Exc e = decode_rank(h, L, rank);
+    const Exc e = decode_rank<false>(h, L, rank);     // sites only: the phase is in the row's coefficient
     RowParts r;
     uint64_t ma = na, mb = nb;
     flip(ma, mb, e.i); flip(ma, mb, e.a);

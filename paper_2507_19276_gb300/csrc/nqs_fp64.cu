@@ -354,7 +354,7 @@ __global__ void k_amp_chain_fp64(AmpArgs a)
     if (threadIdx.x == 0) { s_range[0] = 1 << 30; s_range[1] = -1; }
     __syncthreads();
     for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-        const Exc e = decode_rank(a.h, lists, a.rows.rank[r0 + r]);
+        const Exc e = decode_rank<false>(a.h, lists, a.rows.rank[r0 + r]);   // sites only
         uint64_t ma = na, mb = nb;
         flip(ma, mb, e.i); flip(ma, mb, e.a);
         if (e.kind == 2) { flip(ma, mb, e.j); flip(ma, mb, e.b); }
@@ -455,7 +455,7 @@ __global__ void k_amp_graph_fp64(AmpArgs a)
     if (threadIdx.x == 0) s_min = 1 << 30;
     __syncthreads();
     for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-        const Exc e = decode_rank(a.h, lists, a.rows.rank[r0 + r]);
+        const Exc e = decode_rank<false>(a.h, lists, a.rows.rank[r0 + r]);   // sites only
         uint64_t ma = na, mb = nb;
         flip(ma, mb, e.i); flip(ma, mb, e.a);
         if (e.kind == 2) { flip(ma, mb, e.j); flip(ma, mb, e.b); }

@@ -124,10 +124,13 @@ __device__ __forceinline__ int double_order(const Exc& e)
     return (e.i < e.j) + (e.i < e.b) + (e.j < e.b) + (e.i < e.a) + (e.j < e.a) + (e.b < e.a);
 }
 
-// Canonical rank -> excitation (with its phase parity).
+// Canonical rank -> excitation (with its phase parity; kPhase = false leaves
+// odd = 0 for callers that need only |H|, such as the count pass).
+template <bool kPhase = true>
 __device__ __forceinline__ Exc decode_rank(const HamView& h, const OrbLists& L, uint32_t r)
 {
     Exc e;
+    e.odd = 0;
     if (r < h.blk[2]) {                         // singles
         int sp = r >= h.blk[1];
         uint32_t x = r - h.blk[sp];
@@ -137,7 +140,7 @@ __device__ __forceinline__ Exc decode_rank(const HamView& h, const OrbLists& L, 
         e.i = 2 * L.occ[sp][io] + sp;
         e.a = 2 * L.vir[sp][ao] + sp;
         e.j = e.b = -1;
-        e.odd = (L.ocb[sp][io] + L.vcb[sp][ao] + (e.i < e.a)) & 1;
+        if (kPhase) e.odd = (L.ocb[sp][io] + L.vcb[sp][ao] + (e.i < e.a)) & 1;
     } else if (r < h.blk[4]) {                  // same-spin doubles
         int sp = r >= h.blk[3];
         uint32_t x = r - h.blk[2 + sp];
@@ -150,8 +153,9 @@ __device__ __forceinline__ Exc decode_rank(const HamView& h, const OrbLists& L, 
         e.j = 2 * L.occ[sp][to >> 8] + sp;
         e.a = 2 * L.vir[sp][tv & 0xff] + sp;
         e.b = 2 * L.vir[sp][tv >> 8] + sp;
-        e.odd = (L.ocb[sp][to & 0xff] + L.ocb[sp][to >> 8] + L.vcb[sp][tv & 0xff] +
-                 L.vcb[sp][tv >> 8] + double_order(e)) & 1;
+        if (kPhase)
+            e.odd = (L.ocb[sp][to & 0xff] + L.ocb[sp][to >> 8] + L.vcb[sp][tv & 0xff] +
+                     L.vcb[sp][tv >> 8] + double_order(e)) & 1;
     } else {                                    // alpha-beta doubles
         uint32_t x = r - h.blk[4];
         uint32_t ia = fdiv(x, h.div_sb);
@@ -165,7 +169,8 @@ __device__ __forceinline__ Exc decode_rank(const HamView& h, const OrbLists& L, 
         e.a = 2 * L.vir[0][ao];
         e.j = 2 * L.occ[1][jo] + 1;
         e.b = 2 * L.vir[1][bo] + 1;
-        e.odd = (L.ocb[0][io] + L.vcb[0][ao] + L.ocb[1][jo] + L.vcb[1][bo] + double_order(e)) & 1;
+        if (kPhase)
+            e.odd = (L.ocb[0][io] + L.vcb[0][ao] + L.ocb[1][jo] + L.vcb[1][bo] + double_order(e)) & 1;
     }
     return e;
 }

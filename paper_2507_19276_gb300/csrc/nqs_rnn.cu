@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(256) k_rnn_amp(RnnAmpArgs a)
     double* tkz = cand + 4 * D;
     const double* cn = a.cells + (size_t)s * K * D;  // n's cells
     for (int r = warp; r < nr; r += nw) {
-        const Exc e = decode_rank(a.h, lists, a.rows.rank[r0 + r]);
+        const Exc e = decode_rank<false>(a.h, lists, a.rows.rank[r0 + r]);   // sites only
         uint64_t ma = na, mb = nb;
         flip(ma, mb, e.i); flip(ma, mb, e.a);
         if (e.kind == 2) { flip(ma, mb, e.j); flip(ma, mb, e.b); }
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(256) k_rnn_amp_chain(RnnAmpArgs a)
     if (tid == 0) s_tmin = K;
     __syncthreads();
     if (tid < nr) {
-        const Exc e = decode_rank(a.h, lists, a.rows.rank[r0 + tid]);
+        const Exc e = decode_rank<false>(a.h, lists, a.rows.rank[r0 + tid]);   // sites only
         uint64_t ma = na, mb = nb;
         flip(ma, mb, e.i); flip(ma, mb, e.a);
         if (e.kind == 2) { flip(ma, mb, e.j); flip(ma, mb, e.b); }
