@@ -40,7 +40,7 @@ WORKLOADS = {
            "E_loc samples/s (K8 chain, D=8, plain FP64)"),
     "fe2s2": (lambda n, o: W.fe2s2_dense(n_samples=n, seed_offset=o), 8192, "mixed",
               "E_loc samples/s (Fe2S2 shape, D=256)"),
-    "h18": (lambda n, o: W.h18_graph(n_samples=n, seed_offset=o), 16384, "fp64",
+    "h18": (lambda n, o: W.h18_graph(n_samples=n, seed_offset=o), 16384, "mixed",
             "E_loc samples/s (H18 graph, D=32)"),
 }
 
@@ -392,12 +392,15 @@ def run(args):
     flops = 2.0 * D * D * mv_alg + 2.0 * D * n_amp
     executed = 2.0 * D * D * work["matvecs"] + 2.0 * D * n_amp
     achieved = flops / (amp_ms / 1e3) / 1e12
+    graph = sys_.pred_ptr is not None
     if prec == nqs.NQS_PREC_MIXED:
         roof = {"bound": "tensor", "unit": "TFLOP/s", "achieved": achieved,
                 "peak": peaks["bf16_tflops_sustained"],
                 "peak_source": f"{src} dense bf16 (sustained; f16 has the same nominal rate)",
-                "kernel": "amplitude stage: k_fam_mark, k_fam_compact, k_site_boundary, "
-                          "k_site_build, k_site_tiles_pipe (tcgen05), k_fam_rbm, k_fam_rows"}
+                "kernel": ("k_graph_tiles (tcgen05, 128-row tiles re-running the vertices from "
+                           "each row's first change)" if graph else
+                           "amplitude stage: k_fam_mark, k_fam_compact, k_site_boundary, "
+                           "k_site_build, k_site_tiles_pipe (tcgen05), k_fam_rbm, k_fam_rows")}
     else:
         roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved,
                 "peak": live["fma64_tflops"] if live else 1.196,
@@ -413,7 +416,7 @@ def run(args):
     # (D floats each) and, with a correlator, one factor row per side (N_h
     # rounded up to 4, plus the P - 1 group: 4 more floats)
     roof_rows = None
-    if live and prec == nqs.NQS_PREC_MIXED:
+    if live and prec == nqs.NQS_PREC_MIXED and not graph:
         rows_ms = (stages["amp_det"][0] + stages["amp_draw"][0]) / args.steps
         NH = sys_.n_hidden
         per_row = 4.0 * (2 * D + (2 * (((NH + 3) // 4) * 4 + 4) if NH else 0))
@@ -453,7 +456,11 @@ def run(args):
     fp64 = None
     if not args.no_fp64_compare and prec == nqs.NQS_PREC_MIXED:
         e_mixed = e_loc.clone()
-        ctx.set_precision(nqs.NQS_PREC_FP64_SHARED, timing=False, sample_index_base=lo)
+        # the FP64 form of the same evaluation order: shared prefixes for chains,
+        # the plain form for graphs
+        cmp_name = "fp64" if graph else "fp64_shared"
+        ctx.set_precision(nqs.NQS_PREC_FP64 if graph else nqs.NQS_PREC_FP64_SHARED, timing=False,
+                          sample_index_base=lo)
         s64 = nqs.EnergySummary()
         step(s64)
         torch.cuda.synchronize()
@@ -474,7 +481,7 @@ def run(args):
         stop.record(stream)
         torch.cuda.synchronize()
         ms0 = start.elapsed_time(stop)
-        fp64 = {"precision": "fp64_shared", "value": total / (ms64 / 1e3), "unit": UNIT,
+        fp64 = {"precision": cmp_name, "value": total / (ms64 / 1e3), "unit": UNIT,
                 "ms_per_step": ms64,
                 "e_mean_diff_ha": abs(e64 - work["e_mean"]),
                 "e_mean_diff_unrefined_ha": abs(e64 - s0.as_dict()["e_mean"]),

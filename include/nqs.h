@@ -63,11 +63,21 @@ typedef enum {
     NQS_PREC_FP64 = 0,        /* the plain form: every amplitude psi(m) is its own
                                  FP64 product over the sites where m differs from n
                                  (cached left/right environments outside that span) */
-    NQS_PREC_MIXED = 1,       /* shared-prefix evaluation (chain ansatz): partial
-                                 products common to many m of one n are formed once
-                                 and each psi(m) is one dot product; contractions in
-                                 FP32, H_nm, the ratios and the E_loc sums in FP64 */
-    NQS_PREC_FP64_SHARED = 2  /* the shared-prefix evaluation with FP64 contractions */
+    NQS_PREC_MIXED = 1,       /* contractions on the tensor cores (split FP16
+                                 operands, FP32 accumulation, per-site power-of-two
+                                 rescaling); H_nm, psi(n), the ratios and the E_loc
+                                 sums in FP64. Chain ansatz: shared-prefix
+                                 evaluation (partial products common to many m of
+                                 one n are formed once and each psi(m) is one dot
+                                 product). Graph ansatz: the vertices from each
+                                 row's first changed site on are re-run for 128 rows
+                                 of one sample at a time; needs D in {16, 32, 64},
+                                 in-degree x 4 x D <= 512, at most 16 vertex states
+                                 live at once, the linear readout, no tensor term
+                                 and the 2cosh or cos correlator (otherwise
+                                 NQS_ERR_UNSUPPORTED with the reason) */
+    NQS_PREC_FP64_SHARED = 2  /* the shared-prefix evaluation with FP64
+                                 contractions (chain ansatz only) */
 } nqs_precision;
 
 typedef struct nqs_ctx nqs_ctx;
@@ -81,10 +91,11 @@ typedef struct {
                              call draws with Philox counter (d, base + s), so
                              the draws do not depend on the split (default 0;
                              must be >= 0) */
-    double energy_tolerance;    /* mixed form, chain ansatz: bound (Ha) on the
-                             error of the weighted energy sum c E_loc / sum c
-                             that nqs_local_energy meets by re-evaluating
-                             samples in the FP64 shared-prefix form. The
+    double energy_tolerance;    /* mixed form: bound (Ha) on the error of the
+                             weighted energy sum c E_loc / sum c that
+                             nqs_local_energy meets by re-evaluating samples in
+                             FP64 (the shared-prefix form for chains, the plain
+                             form for graphs). The
                              per-sample error of the mixed form relative to
                              e_abs = |H_nn| + sum |terms| is taken as a factor f
                              (1e-6 to start: what the parity tests hold the mixed
@@ -153,11 +164,15 @@ typedef struct {
                                sites (chain) or vertices (graph) between the first
                                and last changed one: the products a per-amplitude
                                evaluation performs */
-    int64_t matvecs;        /* D x D matrix-vector products this call performed
-                               (equals span_sites, x in-degree for graphs, in the
-                               plain form; one-change families plus two-change
-                               clusters in the shared-prefix form; of the pass over the whole
-                               batch) */
+    int64_t matvecs;        /* D x D matrix-vector products of the evaluation:
+                               chains, plain form: span_sites; graphs (linear
+                               readout): the in-edges with a vertex source of
+                               every re-run vertex, summed over the amplitudes
+                               (the tensor-core tiles also run rows and local
+                               states a tile shares, not counted here);
+                               shared-prefix form: one-change families plus
+                               two-change clusters of the pass over the whole
+                               batch */
     int64_t n_refined;      /* samples re-evaluated in FP64 (energy_tolerance),
                                the audited ones included */
     double e_error_bound;   /* with energy_tolerance > 0 in the mixed form: the
@@ -243,7 +258,8 @@ int nqs_set_readout(nqs_ctx* ctx, const double* v, const double* eta, const doub
  * (Ising-RBM, W2 [n_hidden][2 n_orb][2 n_orb] over the interleaved spin
  * orbitals, copied; NULL otherwise). The cos forms may make f and psi
  * negative; psi(n) = 0 for a sample is NQS_ERR_INVALID_ARG as before. The
- * shared-prefix forms support NQS_CORR_COSH only (NQS_ERR_UNSUPPORTED). */
+ * shared-prefix forms (chains) support NQS_CORR_COSH only, the mixed form of
+ * a graph ansatz NQS_CORR_COSH and NQS_CORR_COS (NQS_ERR_UNSUPPORTED). */
 int nqs_set_correlator(nqs_ctx* ctx, int kind, const double* W2);
 
 /* The tensor term of Eq. (bdg-rnn-update) with the Tucker factors of Sec. 2.2

@@ -79,6 +79,11 @@ struct nqs_ctx {
     // normalised readout, correlator kind, gradient and audit options
     DevBuf rv, reta, rw, rc, W2, rnn_cells, rnn_lp, rnn_sg, grad_scr, u_dev, ebar_dev;
     DevBuf tk_rank, tk_off, tk;   // tensor term (Tucker form) of the graph ansatz
+    // mixed form of the graph ansatz: matrix images, e_0 columns, state slots
+    DevBuf g_img, g_bexp, g_col0, g_slot, g_last, mv_det, mv_draw;
+    int g_slots = 0, g_maxdeg = 0;
+    bool has_gtc = false;
+    char gtc_why[160] = {0};   // why the graph does not fit the tensor-core tiles
     int grad_chunk = 0;        // samples whose environments live at once in the gradient (0: all)
     int audit = 4;             // mixed form: samples re-evaluated in FP64 to check the error factor
     double audit_rel = 0.0, err_factor = 0.0;
@@ -411,13 +416,16 @@ int env_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, bool adjoints, int
 }
 
 // Amplitudes over one row set, accumulated into per-chunk partial sums.
+// gtc: the mixed form of the graph ansatz (tensor-core tiles of 128 rows),
+// which also sums the magnitudes of the terms into *pabs when it is non-NULL.
 int amp_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, RowSet rows, int64_t total_rows,
              const int64_t* count_dev, DevBuf& base, DevBuf& part, DevBuf& span,
-             int64_t max_rows_per_sample, int stage)
+             int64_t max_rows_per_sample, int stage, bool gtc = false, DevBuf* pabs = nullptr,
+             DevBuf* mvb = nullptr)
 {
     StageScope sc(c, stage);
     const bool rnn = c->av.readout == 1;
-    const int R = rnn ? rnn_rows_per_block() : amp_fp64_rows_per_block(c->av);
+    const int R = gtc ? 128 : (rnn ? rnn_rows_per_block() : amp_fp64_rows_per_block(c->av));
     int64_t max_chunks = total_rows / R + Ns;
     if (max_rows_per_sample >= 0) max_chunks = Ns * ((max_rows_per_sample + R - 1) / R);
     TRY(ensure(c, base, (size_t)(Ns + 1) * 8));
@@ -427,6 +435,40 @@ int amp_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, RowSet rows, int64
     rows.count = count_dev;
     rows.chunk_base = (const int64_t*)base.p;
     rows.max_chunks = max_chunks;
+    if (mvb) TRY(ensure(c, *mvb, (size_t)(max_chunks ? max_chunks : 1) * 8));
+    if (gtc) {
+        if (pabs) TRY(ensure(c, *pabs, (size_t)(max_chunks ? max_chunks : 1) * 8));
+        GraphTcArgs g{};
+        g.an = c->av;
+        g.h = c->hv;
+        g.samples = samples;
+        g.Ns = Ns;
+        g.rows = rows;
+        g.Hst = (const double*)c->Hst.p; g.Hexp = (const int*)c->Hexp.p;
+        g.theta = (const double*)c->theta.p;
+        g.psi_mant = (const double*)c->pmant.p;
+        g.psi_exp = (const int*)c->pexp.p;
+        g.bimg = (const unsigned char*)c->g_img.p;
+        g.bexp = (const int*)c->g_bexp.p;
+        g.col0 = (const float*)c->g_col0.p;
+        g.slot = (const int*)c->g_slot.p;
+        g.last_use = (const int*)c->g_last.p;
+        g.n_slots = c->g_slots;
+        g.max_deg = c->g_maxdeg;
+        uint32_t cols = 32;
+        while (cols < (uint32_t)(c->g_maxdeg * 4 * c->av.D)) cols <<= 1;
+        g.tmem_cols = cols;
+        g.WT = c->av.n_hidden ? (const float*)c->WTf.p : nullptr;
+        g.np = (c->av.n_hidden + 3) & ~3;
+        g.partial = (double*)part.p;
+        g.partial_abs = pabs ? (double*)pabs->p : nullptr;
+        g.span = (int64_t*)span.p;
+        g.mv = mvb ? (int64_t*)mvb->p : nullptr;
+        g.err = (DevError*)c->derr.p;
+        LAUNCH(stage, launch_graph_tiles(g, c->n_sm, c->stream));
+        CK(cudaGetLastError());
+        return NQS_OK;
+    }
     if (rnn) {
         RnnAmpArgs r{};
         r.an = c->av;
@@ -462,6 +504,7 @@ int amp_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, RowSet rows, int64
     a.psi_exp = (const int*)c->pexp.p;
     a.partial = (double*)part.p;
     a.span = (int64_t*)span.p;
+    a.mv = mvb ? (int64_t*)mvb->p : nullptr;
     LAUNCH(stage, launch_amp_fp64(a, c->stream));
     CK(cudaGetLastError());
     return NQS_OK;
@@ -740,7 +783,8 @@ extern "C" int nqs_destroy(nqs_ctx* c)
     for (DevBuf* b : bufs) release(*b);
     DevBuf* more[] = {&c->rv, &c->reta, &c->rw, &c->rc, &c->W2, &c->rnn_cells, &c->rnn_lp, &c->rnn_sg,
                       &c->grad_scr, &c->u_dev, &c->ebar_dev, &c->smp_cand, &c->smp_ccnt, &c->smp_cpos,
-                      &c->smp_tabs, &c->tk_rank, &c->tk_off, &c->tk};
+                      &c->smp_tabs, &c->tk_rank, &c->tk_off, &c->tk, &c->g_img, &c->g_bexp,
+                      &c->g_col0, &c->g_slot, &c->g_last, &c->mv_det, &c->mv_draw};
     for (DevBuf* b : more) release(*b);
     for (auto* v : {&c->smp_pa, &c->smp_pb, &c->smp_off, &c->smp_cnt, &c->smp_par, &c->smp_cell})
         for (DevBuf& b : *v) release(b);
@@ -988,6 +1032,29 @@ extern "C" int nqs_set_ansatz(nqs_ctx* c, const double* site_tensors, int n_edge
         CK(cudaMemcpy(c->tc_img.p, img.data(), img.size(), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(c->tc_exps.p, ex.data(), ex.size() * 4, cudaMemcpyHostToDevice));
         c->has_tc = true;
+    }
+    c->has_gtc = false;
+    c->gtc_why[0] = 0;
+    if (!chain) {
+        GraphTcPlan gp;
+        const char* why = nullptr;
+        if (graph_tc_plan(hA.data(), ptr.data(), idx.data(), K, D, n_hidden, gp, &why)) {
+            TRY(ensure(c, c->g_img, gp.img.size()));
+            TRY(ensure(c, c->g_bexp, gp.bexp.size() * 4));
+            TRY(ensure(c, c->g_col0, gp.col0.size() * 4));
+            TRY(ensure(c, c->g_slot, (size_t)K * 4));
+            TRY(ensure(c, c->g_last, (size_t)K * 4));
+            CK(cudaMemcpy(c->g_img.p, gp.img.data(), gp.img.size(), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(c->g_bexp.p, gp.bexp.data(), gp.bexp.size() * 4, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(c->g_col0.p, gp.col0.data(), gp.col0.size() * 4, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(c->g_slot.p, gp.slot.data(), (size_t)K * 4, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(c->g_last.p, gp.last_use.data(), (size_t)K * 4, cudaMemcpyHostToDevice));
+            c->g_slots = gp.n_slots;
+            c->g_maxdeg = gp.max_deg;
+            c->has_gtc = true;
+        } else {
+            snprintf(c->gtc_why, sizeof(c->gtc_why), "%s", why ? why : "unsupported graph");
+        }
     }
     CK(cudaStreamSynchronize(c->stream));
     c->has_ans = true;
@@ -1292,15 +1359,24 @@ int le_core(nqs_ctx* c, const uint64_t* ds, const double* dc, int64_t Ns, uint64
     TRY(reset_dev_error(c));
     const bool rnn = c->av.readout == 1;
     const bool shared = c->av.chain && (prec == NQS_PREC_MIXED || prec == NQS_PREC_FP64_SHARED);
-    if (!c->av.chain && prec != NQS_PREC_FP64)
-        return set_err(c, NQS_ERR_UNSUPPORTED, "graph ansatze run the plain FP64 form (NQS_PREC_FP64)");
+    const bool gtc = !c->av.chain && prec == NQS_PREC_MIXED;
+    const bool graph = !c->av.chain && !rnn;
+    if (!c->av.chain && prec == NQS_PREC_FP64_SHARED)
+        return set_err(c, NQS_ERR_UNSUPPORTED,
+                       "graph ansatze have no shared-prefix form (NQS_PREC_FP64 or NQS_PREC_MIXED)");
+    if (gtc && !c->has_gtc)
+        return set_err(c, NQS_ERR_UNSUPPORTED, "mixed form of this graph ansatz: %s", c->gtc_why);
+    if (gtc && (rnn || c->av.tk_rank || c->av.corr == NQS_CORR_ISING))
+        return set_err(c, NQS_ERR_UNSUPPORTED,
+                       "the mixed form of a graph ansatz needs the linear readout, no tensor term and "
+                       "the 2cosh or cos correlator; use NQS_PREC_FP64");
     if (shared && (rnn || c->av.corr != NQS_CORR_COSH))
         return set_err(c, NQS_ERR_UNSUPPORTED,
                        "the shared-prefix forms need the linear readout and the 2cosh correlator; "
                        "use NQS_PREC_FP64");
     if (shared && c->av.n_hidden > 512)
         return set_err(c, NQS_ERR_UNSUPPORTED, "shared-prefix path supports n_hidden <= 512");
-    if (deabs && !shared) return set_err(c, NQS_ERR_STATE, "e_abs needs a shared-prefix form");
+    if (deabs && !shared && !gtc) return set_err(c, NQS_ERR_STATE, "e_abs needs a mixed or shared-prefix form");
     {
         StageScope sc(c, NQS_STAGE_ENV);
         LAUNCH(NQS_STAGE_ENV, launch_validate(ds, Ns, c->K, c->na, c->nb, (DevError*)c->derr.p, c->stream));
@@ -1354,7 +1430,8 @@ int le_core(nqs_ctx* c, const uint64_t* ds, const double* dc, int64_t Ns, uint64
         rd.coef = (const double*)c->det_coef.p;
         rd.begin = (const int64_t*)c->det_off.p;
         TRY(amp_pass(c, ds, Ns, rd, total, (const int64_t*)c->det_tot.p, c->base_det, c->part_det,
-                     c->span_det, -1, NQS_STAGE_AMP_DET));
+                     c->span_det, -1, NQS_STAGE_AMP_DET, gtc, deabs ? &c->part_det_abs : nullptr,
+                     graph ? &c->mv_det : nullptr));
         if (n_draws > 0) {
             RowSet rs{};
             rs.rank = (const uint32_t*)c->draw_rank.p;
@@ -1362,7 +1439,8 @@ int le_core(nqs_ctx* c, const uint64_t* ds, const double* dc, int64_t Ns, uint64
             rs.begin = nullptr;
             rs.stride = n_draws;
             TRY(amp_pass(c, ds, Ns, rs, (int64_t)Ns * n_draws, (const int64_t*)c->n_unique.p,
-                         c->base_draw, c->part_draw, c->span_draw, n_draws, NQS_STAGE_AMP_DRAW));
+                         c->base_draw, c->part_draw, c->span_draw, n_draws, NQS_STAGE_AMP_DRAW, gtc,
+                         deabs ? &c->part_draw_abs : nullptr, graph ? &c->mv_draw : nullptr));
         }
     }
     TRY(ensure(c, c->summary, 8 * 8));
@@ -1384,17 +1462,19 @@ int le_core(nqs_ctx* c, const uint64_t* ds, const double* dc, int64_t Ns, uint64
     f.e_abs = deabs;
     f.part_det_abs = deabs ? (const double*)c->part_det_abs.p : nullptr;
     f.part_draw_abs = deabs && n_draws > 0 ? (const double*)c->part_draw_abs.p : nullptr;
+    f.mv_det = graph ? (const int64_t*)c->mv_det.p : nullptr;
+    f.mv_draw = graph && n_draws > 0 ? (const int64_t*)c->mv_draw.p : nullptr;
     {
         StageScope sc(c, NQS_STAGE_FINAL);
         LAUNCH(NQS_STAGE_FINAL, launch_finalize(f, c->stream));
     }
     CK(cudaGetLastError());
-    if (shared) TRY(read_dev_error(c));
+    if (shared || gtc) TRY(read_dev_error(c));
     return NQS_OK;
 }
 
-// FP64 shared-prefix re-evaluation of the samples `pick` (ascending) of a
-// mixed-form result: their E_loc in de are replaced; the FP64 values also go
+// FP64 re-evaluation (the shared-prefix form for chains, the plain form for
+// graphs) of the samples `pick` (ascending) of a mixed-form result: their E_loc in de are replaced; the FP64 values also go
 // to `fp64` (host, same order as pick) when it is non-NULL.
 int reevaluate(nqs_ctx* c, const uint64_t* ds, const double* dc, const std::vector<int64_t>& pick,
                uint64_t eb, int n_draws, uint64_t seed, double* de, std::vector<double>* fp64)
@@ -1411,8 +1491,8 @@ int reevaluate(nqs_ctx* c, const uint64_t* ds, const double* dc, const std::vect
                                                  (uint64_t*)c->ref_s.p, (double*)c->ref_c.p,
                                                  (int64_t*)c->ref_pos.p, c->stream));
     TRY(le_core(c, (const uint64_t*)c->ref_s.p, (const double*)c->ref_c.p, k, eb, n_draws, seed,
-                NQS_PREC_FP64_SHARED, (const int64_t*)c->ref_pos.p, (double*)c->ref_e.p, nullptr,
-                false));
+                c->av.chain ? NQS_PREC_FP64_SHARED : NQS_PREC_FP64, (const int64_t*)c->ref_pos.p,
+                (double*)c->ref_e.p, nullptr, false));
     LAUNCH(NQS_STAGE_OTHER, launch_scatter_picked((const int64_t*)c->ref_idx.p, k,
                                                   (const double*)c->ref_e.p, de, c->stream));
     if (fp64) {
@@ -1427,7 +1507,7 @@ int reevaluate(nqs_ctx* c, const uint64_t* ds, const double* dc, const std::vect
 // Error-budgeted refinement of a mixed-form result (de, with c->eabs). The
 // per-sample error of the mixed form relative to e_abs is bounded by a factor
 // f, kMixedRelError to start; the samples with the largest c_n e_abs_n are
-// re-evaluated in the FP64 shared-prefix form until f * sum_{rest} c_n e_abs_n
+// re-evaluated in FP64 (see reevaluate) until f * sum_{rest} c_n e_abs_n
 // / sum c is within c->energy_tol. With them, c->audit of the other samples
 // (evenly spaced in sample order) are re-evaluated as a check of f: when their
 // largest |E_mixed - E_FP64| / max(|E|, e_abs) exceeds f, f becomes twice that
@@ -1544,7 +1624,7 @@ extern "C" int nqs_local_energy(nqs_ctx* c, const uint64_t* samples, const doubl
     double* de;
     bool he;
     TRY(stage_out(c, c->st_out0, e_loc, (size_t)Ns, &de, &he));
-    const bool refine = c->energy_tol > 0.0 && c->precision == NQS_PREC_MIXED && c->av.chain;
+    const bool refine = c->energy_tol > 0.0 && c->precision == NQS_PREC_MIXED;
     if (refine) TRY(ensure(c, c->eabs, (size_t)Ns * 8));
     TRY(le_core(c, ds, dc, Ns, eb, n_draws, seed, c->precision, nullptr, de,
                 refine ? (double*)c->eabs.p : nullptr, out != nullptr));
@@ -1574,7 +1654,8 @@ extern "C" int nqs_local_energy(nqs_ctx* c, const uint64_t* samples, const doubl
         out->n_draw_unique = (int64_t)llround(sm[5]);
         out->n_amplitudes = out->n_det + out->n_draw_unique;
         out->span_sites = (int64_t)llround(sm[6]);
-        out->matvecs = shared ? matvecs : out->span_sites;
+        out->matvecs = shared ? matvecs : (c->av.chain || c->av.readout ? out->span_sites
+                                                                         : (int64_t)llround(sm[7]));
         out->n_refined = n_ref;
         out->e_error_bound = bound;
         out->n_audited = c->n_audited;

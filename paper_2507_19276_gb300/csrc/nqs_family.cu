@@ -521,16 +521,6 @@ __device__ __forceinline__ int site_flips(uint64_t na, uint64_t nb, int s, int a
     return nf;
 }
 
-// cosh d - 1 and sinh d for |d| <= 1 from their Taylor series in z = d^2
-// (terms up to d^10 and d^11; the first omitted term is below 2^-28 of the sum)
-__device__ __forceinline__ void cosh_sinh_small(float d, float& ch1, float& sh)
-{
-    const float z = d * d;
-    ch1 = z * fmaf(z, fmaf(z, fmaf(z, fmaf(z, 1.f / 3628800.f, 1.f / 40320.f), 1.f / 720.f), 1.f / 24.f), 0.5f);
-    sh = fmaf(d * z, fmaf(z, fmaf(z, fmaf(z, fmaf(z, 1.f / 39916800.f, 1.f / 362880.f), 1.f / 5040.f),
-                                 1.f / 120.f), 1.f / 6.f), d);
-}
-
 template <typename T>
 __global__ void k_fam_rbm(FamArgs<T> f)
 {

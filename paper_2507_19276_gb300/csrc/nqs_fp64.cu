@@ -544,10 +544,15 @@ __global__ void k_amp_graph_fp64(AmpArgs a)
     __syncthreads();
     if (threadIdx.x == 0) {
         double acc = 0.0;
-        int64_t sp = 0;
-        for (int r = 0; r < nr; ++r) { acc += info[r].tn; sp += K - info[r].p; }
+        int64_t sp = 0, mv = 0;
+        for (int r = 0; r < nr; ++r) {
+            acc += info[r].tn;
+            sp += K - info[r].p;
+            mv += graph_matvecs(a.an, info[r].p);
+        }
         a.partial[b] = acc;
         if (a.span) a.span[b] = sp;
+        if (a.mv) a.mv[b] = mv;
     }
 }
 

@@ -2,6 +2,8 @@
 // local-energy path (host orchestration lives in nqs_api.cu).
 #pragma once
 
+#include <vector>
+
 #include "nqs_internal.cuh"
 
 namespace nqs {
@@ -117,6 +119,8 @@ struct FinalArgs {
     const double* part_det_abs;          // chunk sums of |term| (NULL: no e_abs)
     const double* part_draw_abs;
     double* e_abs;                       // [Ns] |H_nn| + sum |terms| (optional)
+    const int64_t* mv_det;               // [chunks] in-edge products of the rows (graph
+    const int64_t* mv_draw;              // ansatz; NULL: summary[7] = 0)
 };
 int launch_finalize(const FinalArgs& a, cudaStream_t st);
 int launch_summary(const FinalArgs& a, cudaStream_t st);     // the summary alone
@@ -159,6 +163,15 @@ struct AnsatzView {
     const double* tk;
     int tk_zy;                           // scratch doubles per evaluation: max (d + 4) r
 };
+
+// D x D products a graph amplitude that first changes at vertex p performs:
+// the in-edges with a vertex source of the vertices p..K-1
+__device__ __forceinline__ int graph_matvecs(const AnsatzView& an, int p)
+{
+    int n = 0;
+    for (int e = an.pred_ptr[p]; e < an.pred_ptr[an.K]; ++e) n += an.pred_idx[e] >= 0;
+    return n;
+}
 
 // sum_k AT[k][c] x[k] (AT row-major D x D) with four interleaved partial sums:
 // independent FMA chains that hide the FP64 pipe's latency, combined as
@@ -291,10 +304,55 @@ struct AmpArgs {
     const double* psi_mant; const int* psi_exp;
     double* partial;                     // [chunks]
     int64_t* span;                       // [chunks] sites recomputed per chunk
+    int64_t* mv;                         // [chunks] in-edge products (graph; optional)
 };
 int amp_fp64_rows_per_block(const AnsatzView& an);
 size_t amp_fp64_smem(const AnsatzView& an, int rows);
 int launch_amp_fp64(const AmpArgs& a, cudaStream_t st);
+
+// ---- mixed form of the graph ansatz on the tensor cores (nqs_graph.cu) ------
+
+constexpr int kGtMaxSlots = 16;          // vertex states a tile keeps at once
+constexpr int kGtMaxDeg = 8;             // in-degree bound of the graph ansatz
+
+struct GraphTcPlan {
+    std::vector<unsigned char> img;      // [E][4] split images of M_e^sigma (hi, lo)
+    std::vector<int> bexp;               // [E][4] power of two taken out of each image
+    std::vector<float> col0;             // [E][4][D] column 0 of each matrix (e_0 sources)
+    std::vector<int> slot;               // [K] state slot of each vertex (-1: never read)
+    std::vector<int> last_use;           // [K] last vertex reading each state (-1: none)
+    int n_slots = 0, max_deg = 0;
+};
+// false (with the reason) when the graph does not fit the tile kernel
+bool graph_tc_plan(const double* A, const int* ptr, const int* idx, int K, int D, int n_hidden,
+                   GraphTcPlan& p, const char** why);
+size_t graph_tiles_smem(int D, int K, int n_slots, int max_deg, int n_hidden);
+
+struct GraphTcArgs {
+    AnsatzView an;
+    HamView h;
+    const uint64_t* samples;
+    int64_t Ns;
+    RowSet rows;                         // chunk_base over 128-row tiles
+    const double* Hst; const int* Hexp;  // h_j(n) and their powers of two (FP64 pass)
+    const double* theta;                 // [Ns][n_hidden]
+    const double* psi_mant; const int* psi_exp;
+    const unsigned char* bimg;           // GraphTcPlan::img on the device
+    const int* bexp;
+    const float* col0;
+    const int* slot;
+    const int* last_use;
+    int n_slots, max_deg;
+    uint32_t tmem_cols;                  // power of two >= max_deg * 4 * D
+    const float* WT;                     // [2K][np] FP32 correlator weights, transposed
+    int np;
+    double* partial;                     // [tiles] sum of the terms
+    double* partial_abs;                 // [tiles] sum of their magnitudes (optional)
+    int64_t* span;                       // [tiles] vertices re-run
+    int64_t* mv;                         // [tiles] in-edge D x D products of the rows (optional)
+    DevError* err;
+};
+int launch_graph_tiles(const GraphTcArgs& a, int n_sm, cudaStream_t st);
 
 // full K-site product for arbitrary determinants (nqs_amplitude)
 int launch_full_amp_fp64(const AnsatzView& an, const uint64_t* dets, int64_t n, double* log_abs,
@@ -341,6 +399,16 @@ __device__ __forceinline__ double corr_log_factor(int corr, double theta)
 
 // theta_k(n) = b_k + sum_s W[k][s] n_s (+ 1/2 sum_{s,t} W2[k][s][t] n_s n_t for
 // the Ising-RBM), spin orbitals s = 2p + spin
+// cosh d - 1 and sinh d for |d| <= 1 from their Taylor series in z = d^2
+// (terms up to d^10 and d^11; the first omitted term is below 2^-28 of the sum)
+__device__ __forceinline__ void cosh_sinh_small(float d, float& ch1, float& sh)
+{
+    const float z = d * d;
+    ch1 = z * fmaf(z, fmaf(z, fmaf(z, fmaf(z, 1.f / 3628800.f, 1.f / 40320.f), 1.f / 720.f), 1.f / 24.f), 0.5f);
+    sh = fmaf(d * z, fmaf(z, fmaf(z, fmaf(z, fmaf(z, 1.f / 39916800.f, 1.f / 362880.f), 1.f / 5040.f),
+                                 1.f / 120.f), 1.f / 6.f), d);
+}
+
 __device__ __forceinline__ double corr_theta(const AnsatzView& an, int k, uint64_t na, uint64_t nb)
 {
     const int K = an.K, N = 2 * K;

@@ -247,7 +247,13 @@ __global__ void __launch_bounds__(256) k_summary(FinalArgs a)
         for (int64_t b = threadIdx.x; b < a.base_det[a.Ns]; b += blockDim.x) sp += (double)a.span_det[b];
     if (a.span_draw && a.base_draw)
         for (int64_t b = threadIdx.x; b < a.base_draw[a.Ns]; b += blockDim.x) sp += (double)a.span_draw[b];
+    double mv = 0.0;
+    if (a.mv_det)
+        for (int64_t b = threadIdx.x; b < a.base_det[a.Ns]; b += blockDim.x) mv += (double)a.mv_det[b];
+    if (a.mv_draw && a.base_draw)
+        for (int64_t b = threadIdx.x; b < a.base_draw[a.Ns]; b += blockDim.x) mv += (double)a.mv_draw[b];
     sp = block_reduce_sum(sp, sh);
+    mv = block_reduce_sum(mv, sh);
     sc = block_reduce_sum(sc, sh);
     sce = block_reduce_sum(sce, sh);
     scf = block_reduce_sum(scf, sh);
@@ -270,6 +276,7 @@ __global__ void __launch_bounds__(256) k_summary(FinalArgs a)
         a.summary[4] = ndet;
         a.summary[5] = nu;
         a.summary[6] = sp;
+        a.summary[7] = mv;
     }
 }
 

@@ -163,3 +163,45 @@ def test_h50_energy_tolerance_refinement_meets_the_bound(ctx):
     # within the tolerance, plus the FP64 form's own rounding of the mean
     assert abs(summ["e_mean"] - s64["e_mean"]) <= 1e-6 + 1e-12 * abs(s64["e_mean"])
     assert summ["n_det"] == smx["n_det"] and summ["log_B"] == smx["log_B"]
+
+
+def test_h18_graph_full_batch_mixed_sampled_against_oracle(ctx):
+    """16384 samples of the graph-ordered ansatz on the tensor-core tiles
+    (D = 32, up to three in-edges per vertex)."""
+    sys_ = W.h18_graph()
+    e, summ, dt = _run_full(ctx, sys_, nqs.NQS_PREC_MIXED)
+    _check_properties(ctx, sys_, e, summ)
+    idx = _picked(ctx, sys_, 4, 15)
+    err, _ = _check_sampled(sys_, e, idx, RTOL_MIXED)
+    print(f"h18 full mixed: {dt:.2f} s, sampled max error / max(|E|, e_abs) {err:.3e}")
+    assert err < RTOL_MIXED
+
+
+def test_h18_energy_tolerance_refinement_meets_the_bound(ctx):
+    """The graph ansatz's mixed form with energy_tolerance = 1e-6 Ha: the
+    heaviest samples are re-evaluated in the plain FP64 form, the weighted
+    energy lands within the tolerance of the FP64 form's, and every other
+    sample keeps its mixed value."""
+    sys_ = W.h18_graph()
+    e64, s64, t64 = _run_full(ctx, sys_, nqs.NQS_PREC_FP64)
+    emx, smx, tmx = _run_full(ctx, sys_, nqs.NQS_PREC_MIXED)
+    ctx.set_precision(nqs.NQS_PREC_MIXED, energy_tolerance=1e-6)
+    try:
+        s = torch.from_numpy(sys_.samples.view(np.int64)).cuda()
+        c = torch.from_numpy(sys_.counts).cuda()
+        out = torch.empty(len(sys_.samples), dtype=torch.float64, device="cuda")
+        _, summ = ctx.local_energy(s, c, sys_.eps, sys_.n_draws, sys_.seed, out=out)
+        e = out.cpu().numpy()
+    finally:
+        ctx.set_precision(nqs.NQS_PREC_FP64)
+    k = summ["n_refined"]
+    print(f"fp64 {t64:.2f} s, mixed {tmx:.2f} s; refined {k} of {len(e)}; bound "
+          f"{summ['e_error_bound']:.3e}; |E_bar - E_bar_fp64| mixed "
+          f"{abs(smx['e_mean'] - s64['e_mean']):.3e} refined {abs(summ['e_mean'] - s64['e_mean']):.3e}; "
+          f"audit {summ['audit_rel_error']:.3e}")
+    assert 0 < k < len(e) and summ["e_error_bound"] <= 1e-6
+    changed = e != emx
+    assert changed.sum() <= k
+    np.testing.assert_allclose(e[changed], e64[changed], rtol=1e-13, atol=0)
+    assert np.array_equal(e[~changed], emx[~changed])
+    assert abs(summ["e_mean"] - s64["e_mean"]) <= 1e-6 + 1e-12 * abs(s64["e_mean"])

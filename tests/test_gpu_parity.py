@@ -40,6 +40,8 @@ def _cases():
     return {
         "tiny": W.tiny_system(K=6, na=3, nb=2, D=4, n_hidden=5, seed=3),
         "tiny_graph": W.tiny_system(K=6, na=3, nb=3, D=4, n_hidden=5, seed=4, graph=True),
+        # the smallest bond dimension of the graph ansatz's tensor-core tiles
+        "graph16": W.tiny_system(K=6, na=3, nb=3, D=16, n_hidden=5, seed=4, graph=True),
         "k8": W.small_chain(),
         # 3532: the batch's smallest |psi(n)| (E_loc ~ 1.9e6 Ha, ratios ~ 1e4):
         # the ratio denominators must not lose accuracy to cancellation
@@ -212,7 +214,7 @@ def test_local_energy_shared_prefix_fp64_matches_oracle(ctx, cases, problems, na
 RTOL_MIXED = 1e-6
 
 
-@pytest.mark.parametrize("name", ["tiny", "k8", "h50", "fe2s2"])
+@pytest.mark.parametrize("name", ["tiny", "k8", "h50", "fe2s2", "graph16", "h18"])
 def test_local_energy_mixed_matches_oracle(ctx, cases, problems, name):
     sys_, P = cases[name], problems[name]
     _load(ctx, sys_, nqs.NQS_PREC_MIXED)
@@ -222,6 +224,49 @@ def test_local_energy_mixed_matches_oracle(ctx, cases, problems, name):
     print(f"{name}: mixed max error / max(|E|, e_abs) = {err:.3e}")
     assert err < RTOL_MIXED
     assert summ["n_det"] == int(np.sum(ref["n_det"]))
+
+
+def test_graph_mixed_cos_correlator(ctx, cases):
+    """The graph ansatz's tensor-core form with the cos-RBM correlator (its
+    ratio cos(theta + d) / cos(theta) = 1 + (cos d - 1) - tan(theta) sin d)."""
+    for name in ("graph16", "h18"):
+        sys_ = W.with_correlator(cases[name], 1)
+        _load(ctx, sys_, nqs.NQS_PREC_MIXED)
+        e, _ = ctx.local_energy(sys_.samples, sys_.counts, sys_.eps, sys_.n_draws, sys_.seed)
+        err = _rel_abs(e, O.local_energy(O.Problem(sys_)))
+        print(f"{name} cos-RBM: mixed max error / max(|E|, e_abs) = {err:.3e}")
+        assert err < RTOL_MIXED
+
+
+def test_graph_mixed_semistochastic(ctx, cases, problems):
+    """Deterministic and drawn rows through the graph tiles (the drawn rows of
+    a sample are a second row set with its own tiles)."""
+    sys_, P = cases["graph16"], problems["graph16"]
+    _load(ctx, sys_, nqs.NQS_PREC_MIXED)
+    for eps, nd in [(0.02, 64), (1e3, 200)]:
+        e, s = ctx.local_energy(sys_.samples, sys_.counts, eps, nd, 17)
+        ref = O.local_energy(P, eps=eps, n_draws=nd, seed=17)
+        err = _rel_abs(e, ref)
+        print(f"eps={eps}: mixed max error / max(|E|, e_abs) = {err:.3e}")
+        assert err < RTOL_MIXED
+        assert s["n_det"] == int(np.sum(ref["n_det"]))
+
+
+def test_graph_mixed_unsupported_cases(ctx, cases):
+    """The tensor-core tiles need D in {16, 32, 64}, the linear readout, no
+    tensor term and the 2cosh or cos correlator; graphs have no shared-prefix
+    form. Each refusal is NQS_ERR_UNSUPPORTED with the reason."""
+    def refused(sys_, prec, words):
+        _load(ctx, sys_, prec)
+        with pytest.raises(nqs.NQSError) as ei:
+            ctx.local_energy(sys_.samples, None, 0.0, 0, 0)
+        assert ei.value.status == 6 and words in str(ei.value), str(ei.value)
+    refused(cases["tiny_graph"], nqs.NQS_PREC_MIXED, "bond dimension")
+    refused(cases["graph16"], nqs.NQS_PREC_FP64_SHARED, "shared-prefix")
+    refused(W.with_correlator(cases["graph16"], 2), nqs.NQS_PREC_MIXED, "correlator")
+    g = cases["graph16"]
+    refused(W.with_tensor_term(g), nqs.NQS_PREC_MIXED, "tensor term")
+    ctx.set_precision(nqs.NQS_PREC_FP64)
 
 
 def test_local_energy_stochastic_edge_cases(ctx, cases, problems):
