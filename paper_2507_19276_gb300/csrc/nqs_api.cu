@@ -80,8 +80,8 @@ struct nqs_ctx {
     DevBuf rv, reta, rw, rc, W2, rnn_cells, rnn_lp, rnn_sg, grad_scr, u_dev, ebar_dev;
     DevBuf tk_rank, tk_off, tk;   // tensor term (Tucker form) of the graph ansatz
     // mixed form of the graph ansatz: matrix images, e_0 columns, state slots
-    DevBuf g_img, g_bexp, g_col0, g_slot, g_last, mv_det, mv_draw;
-    int g_slots = 0, g_maxdeg = 0;
+    DevBuf g_img, g_bexp, g_col0, g_slot, g_last, mv_det, mv_draw, g_simg, g_tts;
+    int g_slots = 0, g_maxdeg = 0, g_nbuf = 1;
     bool has_gtc = false;
     char gtc_why[160] = {0};   // why the graph does not fit the tensor-core tiles
     int grad_chunk = 0;        // samples whose environments live at once in the gradient (0: all)
@@ -445,6 +445,10 @@ int amp_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, RowSet rows, int64
         g.Ns = Ns;
         g.rows = rows;
         g.Hst = (const double*)c->Hst.p; g.Hexp = (const int*)c->Hexp.p;
+        TRY(ensure(c, c->g_simg, (size_t)Ns * c->K * 4 * c->av.D));
+        TRY(ensure(c, c->g_tts, (size_t)Ns * (((c->av.n_hidden + 3) & ~3) ? ((c->av.n_hidden + 3) & ~3) : 1) * 4));
+        g.simg = (unsigned char*)c->g_simg.p;
+        g.tts = (float*)c->g_tts.p;
         g.theta = (const double*)c->theta.p;
         g.psi_mant = (const double*)c->pmant.p;
         g.psi_exp = (const int*)c->pexp.p;
@@ -455,6 +459,7 @@ int amp_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, RowSet rows, int64
         g.last_use = (const int*)c->g_last.p;
         g.n_slots = c->g_slots;
         g.max_deg = c->g_maxdeg;
+        g.nbuf = c->g_nbuf;
         uint32_t cols = 32;
         while (cols < (uint32_t)(c->g_maxdeg * 4 * c->av.D)) cols <<= 1;
         g.tmem_cols = cols;
@@ -784,7 +789,8 @@ extern "C" int nqs_destroy(nqs_ctx* c)
     DevBuf* more[] = {&c->rv, &c->reta, &c->rw, &c->rc, &c->W2, &c->rnn_cells, &c->rnn_lp, &c->rnn_sg,
                       &c->grad_scr, &c->u_dev, &c->ebar_dev, &c->smp_cand, &c->smp_ccnt, &c->smp_cpos,
                       &c->smp_tabs, &c->tk_rank, &c->tk_off, &c->tk, &c->g_img, &c->g_bexp,
-                      &c->g_col0, &c->g_slot, &c->g_last, &c->mv_det, &c->mv_draw};
+                      &c->g_col0, &c->g_slot, &c->g_last, &c->mv_det, &c->mv_draw, &c->g_simg,
+                      &c->g_tts};
     for (DevBuf* b : more) release(*b);
     for (auto* v : {&c->smp_pa, &c->smp_pb, &c->smp_off, &c->smp_cnt, &c->smp_par, &c->smp_cell})
         for (DevBuf& b : *v) release(b);
@@ -1051,6 +1057,7 @@ extern "C" int nqs_set_ansatz(nqs_ctx* c, const double* site_tensors, int n_edge
             CK(cudaMemcpy(c->g_last.p, gp.last_use.data(), (size_t)K * 4, cudaMemcpyHostToDevice));
             c->g_slots = gp.n_slots;
             c->g_maxdeg = gp.max_deg;
+            c->g_nbuf = gp.nbuf;
             c->has_gtc = true;
         } else {
             snprintf(c->gtc_why, sizeof(c->gtc_why), "%s", why ? why : "unsupported graph");

@@ -322,11 +322,12 @@ struct GraphTcPlan {
     std::vector<int> slot;               // [K] state slot of each vertex (-1: never read)
     std::vector<int> last_use;           // [K] last vertex reading each state (-1: none)
     int n_slots = 0, max_deg = 0;
+    int nbuf = 1;                        // matrix-image buffers that fit next to the slots
 };
 // false (with the reason) when the graph does not fit the tile kernel
 bool graph_tc_plan(const double* A, const int* ptr, const int* idx, int K, int D, int n_hidden,
                    GraphTcPlan& p, const char** why);
-size_t graph_tiles_smem(int D, int K, int n_slots, int max_deg, int n_hidden);
+size_t graph_tiles_smem(int D, int K, int n_slots, int max_deg, int n_hidden, int nbuf);
 
 struct GraphTcArgs {
     AnsatzView an;
@@ -335,6 +336,8 @@ struct GraphTcArgs {
     int64_t Ns;
     RowSet rows;                         // chunk_base over 128-row tiles
     const double* Hst; const int* Hexp;  // h_j(n) and their powers of two (FP64 pass)
+    unsigned char* simg;                 // [Ns][K][4D] bytes: split images of h_j(n) (written here)
+    float* tts;                          // [Ns][np] tanh (cos form: tan) of theta_k(n) (written here)
     const double* theta;                 // [Ns][n_hidden]
     const double* psi_mant; const int* psi_exp;
     const unsigned char* bimg;           // GraphTcPlan::img on the device
@@ -342,7 +345,7 @@ struct GraphTcArgs {
     const float* col0;
     const int* slot;
     const int* last_use;
-    int n_slots, max_deg;
+    int n_slots, max_deg, nbuf;
     uint32_t tmem_cols;                  // power of two >= max_deg * 4 * D
     const float* WT;                     // [2K][np] FP32 correlator weights, transposed
     int np;

@@ -98,6 +98,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase, uint32
     return false;
 }
 
+// Arrive on an mbarrier (count 1) announcing `bytes` of bulk copies that
+// complete on it.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bulk copy global -> shared by the copy engine (both addresses 16-byte
+// aligned, bytes a multiple of 16); its bytes complete on `mbar`.
+__device__ __forceinline__ void bulk_g2s(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_addr(sdst)), "l"(gsrc), "r"(bytes), "r"(smem_addr(mbar)) : "memory");
+}
+
 // 32 lanes x 8 consecutive 32-bit columns per warp
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v)
 {
@@ -108,6 +124,16 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v)
                  : "r"(taddr) : "memory");
     #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 32 lanes x 8 consecutive 32-bit columns per warp (raw words; read them
+// after tmem_wait_ld)
+__device__ __forceinline__ void tmem_ld8u(uint32_t taddr, uint32_t* r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr) : "memory");
 }
 
 // 32 lanes x 16 consecutive 32-bit columns per warp (raw words; read them
