@@ -121,7 +121,7 @@ typedef struct {
                              each site-step tile launch (0: the default, 4; at most
                              32). A schedule parameter: results do not depend on it */
     int table_mb;         /* shared-prefix forms: cap (MiB) on the tables of one
-                             sample batch (0: the default, 8 GiB); never more
+                             sample batch (0: the default, 32 GiB); never more
                              than a third of the free device memory. Larger
                              batches mean fewer, fuller launches; results do not
                              depend on it */

@@ -574,14 +574,16 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
     // batch size from a memory budget
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
-    // the table cap (table_mb, or 8 GiB), never more than a third of the free memory
-    const size_t cap = c->table_mb > 0 ? (size_t)c->table_mb << 20 : (size_t)8 << 30;
+    // the table cap (table_mb, or 32 GiB), never more than a third of the free memory
+    const size_t cap = c->table_mb > 0 ? (size_t)c->table_mb << 20 : (size_t)32 << 30;
     size_t budget = std::min<size_t>(cap, free_b / 3);
     if (c->fam_budget > 0) budget = std::min(budget, c->fam_budget);
     const size_t per = fam_bytes_per_sample(K, D, sizeof(T));
     int64_t nb = (int64_t)std::max<size_t>(1, budget / per);
-    if (nb > Ns) nb = Ns;
     if (nb > 65535) nb = 65535;
+    // equal batches (a short last batch would run its site steps on few items)
+    if (nb < Ns) nb = (Ns + (Ns + nb - 1) / nb - 1) / ((Ns + nb - 1) / nb);
+    if (nb > Ns) nb = Ns;
     TRY(ensure(c, c->ftl_end, nb * nk * 4));
     TRY(ensure(c, c->ftl_idx, nb * nk * 4));
     TRY(ensure(c, c->ftr_idx, nb * nk * 4));
