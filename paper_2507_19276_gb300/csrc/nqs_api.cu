@@ -80,7 +80,7 @@ struct nqs_ctx {
     DevBuf rv, reta, rw, rc, W2, rnn_cells, rnn_lp, rnn_sg, grad_scr, u_dev, ebar_dev;
     DevBuf tk_rank, tk_off, tk;   // tensor term (Tucker form) of the graph ansatz
     // mixed form of the graph ansatz: matrix images, e_0 columns, state slots
-    DevBuf g_img, g_bexp, g_col0, g_slot, g_last, mv_det, mv_draw, g_simg, g_tts;
+    DevBuf g_img, g_bexp, g_col0, g_slot, g_last, mv_det, mv_draw, g_simg, g_tts, g_rank, g_coef;
     int g_slots = 0, g_maxdeg = 0, g_nbuf = 1;
     bool has_gtc = false;
     char gtc_why[160] = {0};   // why the graph does not fit the tensor-core tiles
@@ -438,6 +438,15 @@ int amp_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, RowSet rows, int64
     if (mvb) TRY(ensure(c, *mvb, (size_t)(max_chunks ? max_chunks : 1) * 8));
     if (gtc) {
         if (pabs) TRY(ensure(c, *pabs, (size_t)(max_chunks ? max_chunks : 1) * 8));
+        // rows with the same first changed vertex side by side: a tile re-runs
+        // the vertices its rows need, not those of its earliest row
+        const size_t span_rows = rows.begin ? (size_t)total_rows : (size_t)Ns * rows.stride;
+        TRY(ensure(c, c->g_rank, (span_rows ? span_rows : 1) * 4));
+        TRY(ensure(c, c->g_coef, (span_rows ? span_rows : 1) * 8));
+        LAUNCH(stage, launch_graph_sort(c->hv, samples, rows, Ns, c->K, (uint32_t*)c->g_rank.p,
+                                        (double*)c->g_coef.p, c->stream));
+        rows.rank = (const uint32_t*)c->g_rank.p;
+        rows.coef = (const double*)c->g_coef.p;
         GraphTcArgs g{};
         g.an = c->av;
         g.h = c->hv;
@@ -792,7 +801,7 @@ extern "C" int nqs_destroy(nqs_ctx* c)
                       &c->grad_scr, &c->u_dev, &c->ebar_dev, &c->smp_cand, &c->smp_ccnt, &c->smp_cpos,
                       &c->smp_tabs, &c->tk_rank, &c->tk_off, &c->tk, &c->g_img, &c->g_bexp,
                       &c->g_col0, &c->g_slot, &c->g_last, &c->mv_det, &c->mv_draw, &c->g_simg,
-                      &c->g_tts};
+                      &c->g_tts, &c->g_rank, &c->g_coef};
     for (DevBuf* b : more) release(*b);
     for (auto* v : {&c->smp_pa, &c->smp_pb, &c->smp_off, &c->smp_cnt, &c->smp_par, &c->smp_cell})
         for (DevBuf& b : *v) release(b);

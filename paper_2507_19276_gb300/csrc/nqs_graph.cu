@@ -623,6 +623,86 @@ bool graph_tc_plan(const double* A, const int* ptr, const int* idx, int K, int D
     return true;
 }
 
+namespace {
+
+// first changed vertex of the row with canonical rank r of sample (na, nb)
+__device__ __forceinline__ int gt_first_change(const HamView& h, const OrbLists& L, uint64_t na, uint64_t nb,
+                                               uint32_t r, int K)
+{
+    const Exc e = decode_rank<false>(h, L, r);
+    uint64_t ma = na, mb = nb;
+    flip(ma, mb, e.i); flip(ma, mb, e.a);
+    if (e.kind == 2) { flip(ma, mb, e.j); flip(ma, mb, e.b); }
+    const uint64_t ch = (na ^ ma) | (nb ^ mb);
+    return ch ? __ffsll((long long)ch) - 1 : K - 1;
+}
+
+// Stable counting sort of each sample's rows by their first changed vertex
+// (rows with the same one keep their canonical order), one block of 256
+// threads per sample: a tile then holds rows that re-run the same vertices.
+__global__ void __launch_bounds__(256) k_graph_sort(HamView h, const uint64_t* samples, RowSet in, int K,
+                                                    uint32_t* out_rank, double* out_coef)
+{
+    __shared__ OrbLists lists;
+    __shared__ int off[kMaxOrb];                  // next output position of each vertex
+    __shared__ int wc[8][kMaxOrb];                // per-warp counts of the current 256 rows
+    const int64_t s = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t beg = in.begin ? in.begin[s] : s * in.stride;
+    const int cnt = (int)in.count[s];
+    const uint64_t na = samples[2 * s], nb = samples[2 * s + 1];
+    if (warp == 0) build_lists_warp(na, nb, h.K, lists, lane);
+    for (int q = tid; q < 8 * kMaxOrb; q += 256) (&wc[0][0])[q] = 0;
+    if (tid < kMaxOrb) off[tid] = 0;
+    __syncthreads();
+    for (int r = tid; r < cnt; r += 256) atomicAdd(&off[gt_first_change(h, lists, na, nb, in.rank[beg + r], K)], 1);
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int v = 0; v < K; ++v) { const int c = off[v]; off[v] = acc; acc += c; }
+    }
+    __syncthreads();
+    const unsigned below = (1u << lane) - 1u;
+    for (int c0 = 0; c0 < cnt; c0 += 256) {
+        const int r = c0 + tid;
+        const bool valid = r < cnt;
+        uint32_t rk = 0;
+        double cf = 0.0;
+        int p = K;                                // past every vertex: no bucket
+        if (valid) {
+            rk = in.rank[beg + r];
+            cf = in.coef[beg + r];
+            p = gt_first_change(h, lists, na, nb, rk, K);
+        }
+        const unsigned m = __match_any_sync(kFull, p);
+        if (valid && lane == __ffs(m) - 1) wc[warp][p] = __popc(m);
+        __syncthreads();
+        if (valid) {
+            int pos = off[p] + __popc(m & below);
+            for (int w = 0; w < warp; ++w) pos += wc[w][p];
+            out_rank[beg + pos] = rk;
+            out_coef[beg + pos] = cf;
+        }
+        __syncthreads();
+        if (tid < K) {
+            int t = 0;
+            for (int w = 0; w < 8; ++w) { t += wc[w][tid]; wc[w][tid] = 0; }
+            off[tid] += t;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+int launch_graph_sort(const HamView& h, const uint64_t* samples, const RowSet& in, int64_t Ns, int K,
+                      uint32_t* out_rank, double* out_coef, cudaStream_t st)
+{
+    if (Ns == 0) return 0;
+    k_graph_sort<<<(unsigned)Ns, 256, 0, st>>>(h, samples, in, K, out_rank, out_coef);
+    return 1;
+}
+
 int launch_graph_tiles(const GraphTcArgs& a, int n_sm, cudaStream_t st)
 {
     if (a.rows.max_chunks == 0) return 0;

@@ -356,6 +356,9 @@ struct GraphTcArgs {
     DevError* err;
 };
 int launch_graph_tiles(const GraphTcArgs& a, int n_sm, cudaStream_t st);
+// each sample's rows (rank, coefficient) stably sorted by their first changed vertex
+int launch_graph_sort(const HamView& h, const uint64_t* samples, const RowSet& in, int64_t Ns, int K,
+                      uint32_t* out_rank, double* out_coef, cudaStream_t st);
 
 // full K-site product for arbitrary determinants (nqs_amplitude)
 int launch_full_amp_fp64(const AnsatzView& an, const uint64_t* dets, int64_t n, double* log_abs,
