@@ -1142,6 +1142,7 @@ int fam_site_step(const FamArgs<T>& f, const SiteBufs& b, int tau, const int64_t
 // one at a time with coalesced loads (lanes split the vectors and the hidden
 // units), a compensated tree for the dot product and a tree for the product.
 constexpr int kFamRows = 128;
+constexpr int kFamRowsMB64 = 8;          // blocks per SM of the compile-time-D row kernels
 
 template <typename T>
 __device__ __forceinline__ void two_sum(T a, T b, T& s, T& e)
@@ -1163,9 +1164,14 @@ __device__ __forceinline__ double scale_pow2(double x, int e)
     return ldexp(x, e);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kFamRows, 12) k_fam_rows(FamArgs<T> f, RowSet rows, double* partial,
-                                                       int64_t* span, double* partial_abs)
+// DT > 0: the bond dimension at compile time. Each lane group then issues
+// all of its row's loads (left / right vector pieces, correlator groups) before
+// the arithmetic, with fully unrolled loops; more registers per thread, fewer
+// blocks per SM (MB), more loads in flight per warp. The arithmetic and its
+// order are those of the general path (DT = 0).
+template <typename T, int DT, int MB>
+__global__ void __launch_bounds__(kFamRows, MB) k_fam_rows(FamArgs<T> f, RowSet rows, double* partial,
+                                                           int64_t* span, double* partial_abs)
 {
     __shared__ OrbLists lists;
     __shared__ T s_ratio[kFamRows];                  // each row's ratio in the contraction type
@@ -1266,65 +1272,137 @@ __global__ void __launch_bounds__(kFamRows, 12) k_fam_rows(FamArgs<T> f, RowSet 
         const T* ltq = (const T*)p23.x;
         const T* rsq = (const T*)p23.y;
         const bool live = q < wrows;
-        // dot product with error-free product / sum transformations
-        T sum = T(0), comp = T(0);
-        if (live) {
-            if ((D & 3) == 0) {
-                typedef typename Vec4<T>::type V4;
-                for (int c4 = sub; c4 < D / 4; c4 += 8) {
-                    const V4 x = ((const V4*)Lq)[c4], y = ((const V4*)Rq)[c4];
-                    const T xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+        T ratio;
+        if constexpr (DT > 0) {
+            typedef typename Vec4<T>::type V4;
+            constexpr int NV = DT / 4, PER = (NV + 7) / 8;
+            const int NG = NP / 4 + 1;           // correlator groups, the last holding P - 1
+            V4 xv[PER], yv[PER], tv[4], uv[4];
+            if (live) {
+                #pragma unroll
+                for (int u = 0; u < PER; ++u)
+                    if (sub + 8 * u < NV) { xv[u] = ((const V4*)Lq)[sub + 8 * u]; yv[u] = ((const V4*)Rq)[sub + 8 * u]; }
+                if (NH > 0) {
                     #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const T pr = xs[u] * ys[u];
-                        const T pe2 = fma(xs[u], ys[u], -pr);
+                    for (int u = 0; u < 4; ++u)
+                        if (sub + 8 * u < NG) {
+                            tv[u] = ((const V4*)ltq)[sub + 8 * u];
+                            uv[u] = ((const V4*)rsq)[sub + 8 * u];
+                        }
+                }
+            }
+            T sum = T(0), comp = T(0);
+            if (live) {
+                #pragma unroll
+                for (int u = 0; u < PER; ++u) {
+                    if (sub + 8 * u < NV) {
+                        const T xs[4] = {xv[u].x, xv[u].y, xv[u].z, xv[u].w};
+                        const T ys[4] = {yv[u].x, yv[u].y, yv[u].z, yv[u].w};
+                        #pragma unroll
+                        for (int w = 0; w < 4; ++w) {
+                            const T pr = xs[w] * ys[w];
+                            const T pe2 = fma(xs[w], ys[w], -pr);
+                            T t, e;
+                            two_sum(sum, pr, t, e);
+                            sum = t;
+                            comp += e + pe2;
+                        }
+                    }
+                }
+            }
+            for (int o = 4; o; o >>= 1) {
+                const T so = __shfl_xor_sync(kFull, sum, o);
+                const T co = __shfl_xor_sync(kFull, comp, o);
+                T t, e;
+                two_sum(sum, so, t, e);
+                sum = t;
+                comp += co + e;
+            }
+            ratio = sum + comp;
+            if (NH > 0) {
+                T X = T(0);                        // product of (1 + x_k) minus 1
+                if (live) {
+                    auto group = [&](const V4& t, const V4& u, bool last) {
+                        T x;
+                        // the last group holds PL - 1 and PR - 1 (then zeros): (1 + a)(1 + b) - 1
+                        x = last ? fma(t.x, u.x, t.x + u.x) : t.x * u.x; X = fma(X, x, X + x);
+                        x = t.y * u.y; X = fma(X, x, X + x);
+                        x = t.z * u.z; X = fma(X, x, X + x);
+                        x = t.w * u.w; X = fma(X, x, X + x);
+                    };
+                    #pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (sub + 8 * u < NG) group(tv[u], uv[u], sub + 8 * u == NG - 1);
+                    for (int k4 = sub + 32; k4 < NG; k4 += 8)
+                        group(((const V4*)ltq)[k4], ((const V4*)rsq)[k4], k4 == NG - 1);
+                }
+                for (int o = 4; o; o >>= 1) {
+                    const T Y = __shfl_xor_sync(kFull, X, o);
+                    X = fma(X, Y, X + Y);
+                }
+                if (live) ratio *= T(1) + X;
+            }
+        } else {
+            // dot product with error-free product / sum transformations
+            T sum = T(0), comp = T(0);
+            if (live) {
+                if ((D & 3) == 0) {
+                    typedef typename Vec4<T>::type V4;
+                    for (int c4 = sub; c4 < D / 4; c4 += 8) {
+                        const V4 x = ((const V4*)Lq)[c4], y = ((const V4*)Rq)[c4];
+                        const T xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+                        #pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const T pr = xs[u] * ys[u];
+                            const T pe2 = fma(xs[u], ys[u], -pr);
+                            T t, e;
+                            two_sum(sum, pr, t, e);
+                            sum = t;
+                            comp += e + pe2;
+                        }
+                    }
+                } else {
+                    for (int c = sub; c < D; c += 8) {
+                        const T pr = Lq[c] * Rq[c];
+                        const T pe2 = fma(Lq[c], Rq[c], -pr);
                         T t, e;
                         two_sum(sum, pr, t, e);
                         sum = t;
                         comp += e + pe2;
                     }
                 }
-            } else {
-                for (int c = sub; c < D; c += 8) {
-                    const T pr = Lq[c] * Rq[c];
-                    const T pe2 = fma(Lq[c], Rq[c], -pr);
-                    T t, e;
-                    two_sum(sum, pr, t, e);
-                    sum = t;
-                    comp += e + pe2;
-                }
-            }
-        }
-        for (int o = 4; o; o >>= 1) {
-            const T so = __shfl_xor_sync(kFull, sum, o);
-            const T co = __shfl_xor_sync(kFull, comp, o);
-            T t, e;
-            two_sum(sum, so, t, e);
-            sum = t;
-            comp += co + e;
-        }
-        T ratio = sum + comp;
-        if (NH > 0) {
-            typedef typename Vec4<T>::type V4;
-            T X = T(0);                            // product of (1 + x_k) minus 1
-            if (live) {
-                const V4* l4 = (const V4*)ltq;
-                const V4* r4 = (const V4*)rsq;
-                for (int k4 = sub; k4 <= NP / 4; k4 += 8) {
-                    const V4 t = l4[k4], u = r4[k4];
-                    T x;
-                    // the last group holds PL - 1 and PR - 1 (then zeros): (1 + a)(1 + b) - 1
-                    x = k4 == NP / 4 ? fma(t.x, u.x, t.x + u.x) : t.x * u.x; X = fma(X, x, X + x);
-                    x = t.y * u.y; X = fma(X, x, X + x);
-                    x = t.z * u.z; X = fma(X, x, X + x);
-                    x = t.w * u.w; X = fma(X, x, X + x);
-                }
             }
             for (int o = 4; o; o >>= 1) {
-                const T Y = __shfl_xor_sync(kFull, X, o);
-                X = fma(X, Y, X + Y);
+                const T so = __shfl_xor_sync(kFull, sum, o);
+                const T co = __shfl_xor_sync(kFull, comp, o);
+                T t, e;
+                two_sum(sum, so, t, e);
+                sum = t;
+                comp += co + e;
             }
-            if (live) ratio *= T(1) + X;
+            ratio = sum + comp;
+            if (NH > 0) {
+                typedef typename Vec4<T>::type V4;
+                T X = T(0);                            // product of (1 + x_k) minus 1
+                if (live) {
+                    const V4* l4 = (const V4*)ltq;
+                    const V4* r4 = (const V4*)rsq;
+                    for (int k4 = sub; k4 <= NP / 4; k4 += 8) {
+                        const V4 t = l4[k4], u = r4[k4];
+                        T x;
+                        // the last group holds PL - 1 and PR - 1 (then zeros): (1 + a)(1 + b) - 1
+                        x = k4 == NP / 4 ? fma(t.x, u.x, t.x + u.x) : t.x * u.x; X = fma(X, x, X + x);
+                        x = t.y * u.y; X = fma(X, x, X + x);
+                        x = t.z * u.z; X = fma(X, x, X + x);
+                        x = t.w * u.w; X = fma(X, x, X + x);
+                    }
+                }
+                for (int o = 4; o; o >>= 1) {
+                    const T Y = __shfl_xor_sync(kFull, X, o);
+                    X = fma(X, Y, X + Y);
+                }
+                if (live) ratio *= T(1) + X;
+            }
         }
         if (live && sub == 0) s_ratio[wbase + q] = ratio;
     }
@@ -1387,7 +1465,17 @@ int fam_launch_rows(const FamArgs<T>& f, const RowSet& rows, int64_t grid, doubl
                     int64_t* span, double* partial_abs, cudaStream_t st)
 {
     if (grid <= 0) return 0;
-    k_fam_rows<T><<<(unsigned)grid, kFamRows, 0, st>>>(f, rows, partial, span, partial_abs);
+    if constexpr (std::is_same<T, float>::value) {
+        if (f.D == 64) {
+            k_fam_rows<T, 64, kFamRowsMB64><<<(unsigned)grid, kFamRows, 0, st>>>(f, rows, partial, span, partial_abs);
+            return 1;
+        }
+        if (f.D == 32) {
+            k_fam_rows<T, 32, kFamRowsMB64><<<(unsigned)grid, kFamRows, 0, st>>>(f, rows, partial, span, partial_abs);
+            return 1;
+        }
+    }
+    k_fam_rows<T, 0, 12><<<(unsigned)grid, kFamRows, 0, st>>>(f, rows, partial, span, partial_abs);
     return 1;
 }
 
