@@ -46,6 +46,7 @@ struct nqs_ctx {
     DevBuf A, AT, W, b, pred_ptr, pred_idx;
     DevBuf WT;                // W transposed, [2K][n_hidden rounded up to 4], zero-padded
     DevBuf Af, ATf, WTf;      // FP32 copies for the shared-prefix FP32 path
+    DevBuf csite;             // FP32 path: per-site correlator factors (fam_corr_sites)
     DevBuf tc_img, tc_exps;   // split-FP16 operand images for the tensor-core batches
     bool has_tc = false;
 
@@ -634,6 +635,7 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
     f.samples = ds;
     f.n_hidden = c->av.n_hidden;
     f.WT = (const T*)(dbl ? c->WT.p : c->WTf.p);
+    f.csite = dbl ? nullptr : (const float4*)c->csite.p;
     f.theta = (const double*)c->theta.p;
     const int NH = c->av.n_hidden;
     RowSet rd{};
@@ -788,7 +790,7 @@ extern "C" int nqs_destroy(nqs_ctx* c)
                       &c->draw_rank, &c->draw_coef, &c->n_unique, &c->base_det, &c->base_draw,
                       &c->part_det, &c->part_draw, &c->eloc, &c->edet, &c->estoch, &c->summary,
                       &c->derr, &c->span_det, &c->span_draw, &c->Af, &c->ATf,
-                      &c->WT, &c->WTf, &c->fpool, &c->fpoole, &c->ftl_end,
+                      &c->WT, &c->WTf, &c->csite, &c->fpool, &c->fpoole, &c->ftl_end,
                       &c->ftl_idx, &c->ftr_idx, &c->ftl_tot, &c->ftr_tot, &c->ftl_base,
                       &c->ftr_base, &c->ftl_ci,
                       &c->ftl_list, &c->ftr_list, &c->ftl_cnt, &c->frbl, &c->frbr, &c->frbl_base,
@@ -1021,6 +1023,10 @@ extern "C" int nqs_set_ansatz(nqs_ctx* c, const double* site_tensors, int n_edge
             TRY(ensure(c, c->WTf, fWT.size() * 4));
             CK(cudaMemcpy(c->WT.p, hWT.data(), hWT.size() * 8, cudaMemcpyHostToDevice));
             CK(cudaMemcpy(c->WTf.p, fWT.data(), fWT.size() * 4, cudaMemcpyHostToDevice));
+            TRY(ensure(c, c->csite, (size_t)K * 12 * np * 16));
+            fam_corr_sites((const double*)c->W.p, K, n_hidden, (float4*)c->csite.p, c->stream);
+            CK(cudaGetLastError());
+            CK(cudaStreamSynchronize(c->stream));
         }
     }
     AnsatzView a{};

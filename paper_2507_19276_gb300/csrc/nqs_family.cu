@@ -545,62 +545,81 @@ __global__ void k_fam_rbm(FamArgs<T> f)
          ob += gridDim.x * (blockDim.x >> 5) * 2) {
         const int o = ob + (lane >> 4);
         const bool valid = o < nobj;
-        uint32_t pk = 0;
-        int nf = 0;
         const bool left = o < nleft;
         const int oi = left ? o : o - nleft;
+        // the object's changed sites (one for a family, two for a cluster)
+        int ns = 0, s_hi = 0, a_hi = 0, s_lo = 0, a_lo = 0;
         if (!valid) {
         } else if (oi < 3 * K) {
-            nf = site_flips(na, nb, oi / 3, oi % 3, pk, 0);
+            ns = 1; s_hi = oi / 3; a_hi = oi % 3;
         } else {
             const int key = left ? f.tl_list[(size_t)b * nk + (oi - 3 * K)]
                                  : f.tr_list[(size_t)b * nk + (oi - 3 * K)];
-            int s_hi, a_hi, s_lo, a_lo;
             key_fields(f, key, s_hi, a_hi, s_lo, a_lo);
-            nf = site_flips(na, nb, s_hi, a_hi, pk, 0);
-            nf = site_flips(na, nb, s_lo, a_lo, pk, nf);
+            ns = 2;
         }
         // products of (1 + y_k) are carried as P - 1 (X <- X + y + X y), exact
         // for P near 1 and free of a logarithm per unit
         const int RL = rbm_row_len(NH);
         T* out = (left ? f.rbl + (size_t)(lbase + oi) * RL : f.rbr + (size_t)(rbase + oi) * RL);
         T pm1 = T(0);
-        for (int k = hl; valid && k < NP; k += 16) {
-            if (k >= NH) { out[k] = T(0); continue; }
-            T d = T(0);
-            #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (q < nf) {
-                    const uint32_t fb = (pk >> (8 * q)) & 0xFFu;
-                    const T w = f.WT[(size_t)(fb & 0x7Fu) * NP + k];
-                    d += (fb & 0x80u) ? w : -w;
+        if constexpr (std::is_same<T, float>::value) {
+            // FP32: the object's change of theta is the sum of its sites' changes
+            // d1 (+ d2), whose tanh u and cosh - 1 c come from the per-site table.
+            // With t = tanh theta, s = u1 + u2, p = u1 u2 (0 for one site):
+            //   cosh(theta + d1 + d2) / (cosh theta cosh d1 cosh d2) = 1 + p + t s =: den
+            //   tanh(theta + d1 + d2) = (t + s + t p) / den,  tanh(d1 + d2) = s / (1 + p)
+            //   PL factor - 1 = (1 + e)(1 + p + t s) - 1,  PR factor - 1 = (1 + e)(1 + p) - 1
+            // with e = (1 + c1)(1 + c2) - 1. A denominator below 1/2 (|theta| and
+            // |d| both large) would lose bits to cancellation: such units take
+            // tanh and expm1 of theta + d directly.
+            const float4* r1 = f.csite + ((size_t)(s_hi * 4 + sigma_at(na, nb, s_hi)) * 3 + a_hi) * NP;
+            const float4* r2 = f.csite + ((size_t)(s_lo * 4 + sigma_at(na, nb, s_lo)) * 3 + a_lo) * NP;
+            for (int k = hl; valid && k < NP; k += 16) {
+                if (k >= NH) { out[k] = 0.f; continue; }
+                const float4 u = __ldg(r1 + k);
+                const float4 v = ns == 2 ? __ldg(r2 + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float sx = u.x + v.x, px = u.x * v.x;
+                const float e = fmaf(u.y, v.y, u.y + v.y);
+                const float t = tt_s[k];
+                float val, y;
+                const float den = left ? fmaf(t, sx, 1.f + px) : 1.f + px;
+                if (den >= 0.5f) {
+                    const float g = left ? fmaf(t, sx, px) : px;      // den - 1
+                    val = __fdividef(left ? fmaf(t, px, t + sx) : sx, den);
+                    y = fmaf(e, g, e + g);
+                } else {
+                    const float d = u.z + v.z;
+                    const float em = expm1f(d);
+                    const float inv = 1.f / (1.f + em);
+                    const float ch1 = 0.5f * em * em * inv, sh = 0.5f * em * (1.f + inv);
+                    val = left ? tanhf(th_s[k] + d) : sh / (1.f + ch1);
+                    y = left ? ch1 + t * sh : ch1;
                 }
+                out[k] = val;
+                pm1 = fmaf(pm1, y, pm1 + y);
             }
-            T y;
-            bool done = false;
-            if constexpr (std::is_same<T, float>::value) {
-                // FP32 tables, |d| <= 1: series for cosh d - 1 and sinh d, and
-                // tanh(theta + d) = (t cosh d + sinh d) / (cosh d + t sinh d),
-                // t = tanh theta (the denominator is at least e^-|d|)
-                if (fabsf(d) <= 1.f) {
-                    float ch1, sh;
-                    cosh_sinh_small(d, ch1, sh);
-                    const float c = 1.f + ch1;
-                    if (left) {
-                        out[k] = __fdividef(fmaf(tt_s[k], c, sh), fmaf(tt_s[k], sh, c));
-                        y = ch1 + tt_s[k] * sh;
-                    } else {
-                        out[k] = __fdividef(sh, c);
-                        y = ch1;
+        } else {
+            uint32_t pk = 0;
+            int nf = 0;
+            if (ns >= 1) nf = site_flips(na, nb, s_hi, a_hi, pk, 0);
+            if (ns == 2) nf = site_flips(na, nb, s_lo, a_lo, pk, nf);
+            for (int k = hl; valid && k < NP; k += 16) {
+                if (k >= NH) { out[k] = T(0); continue; }
+                T d = T(0);
+                #pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (q < nf) {
+                        const uint32_t fb = (pk >> (8 * q)) & 0xFFu;
+                        const T w = f.WT[(size_t)(fb & 0x7Fu) * NP + k];
+                        d += (fb & 0x80u) ? w : -w;
                     }
-                    done = true;
                 }
-            }
-            if (!done) {
                 // em = e^d - 1, inv = e^-d: cosh d - 1 = em^2 inv / 2, sinh d = em (1 + inv) / 2
                 const T em = expm1(d);
                 const T inv = T(1) / (T(1) + em);
                 const T ch1 = T(0.5) * em * em * inv, sh = T(0.5) * em * (T(1) + inv);
+                T y;
                 if (left) {
                     out[k] = tanh(th_s[k] + d);
                     y = ch1 + tt_s[k] * sh;             // cosh(theta + d) / cosh(theta) - 1
@@ -608,8 +627,8 @@ __global__ void k_fam_rbm(FamArgs<T> f)
                     out[k] = sh / (T(1) + ch1);         // tanh d
                     y = ch1;                            // cosh d - 1
                 }
+                pm1 = fma(pm1, y, pm1 + y);
             }
-            pm1 = fma(pm1, y, pm1 + y);
         }
         for (int o2 = 8; o2; o2 >>= 1) {
             const T z = __shfl_xor_sync(kFull, pm1, o2);
@@ -618,6 +637,33 @@ __global__ void k_fam_rbm(FamArgs<T> f)
         if (valid && hl == 0) out[NP] = pm1;
         if (valid && hl < 3) out[NP + 1 + hl] = T(0);
     }
+}
+
+// per-site factors of the FP32 correlator path (see fam_corr_sites)
+__global__ void k_corr_sites(const double* __restrict__ W, int K, int NH, int NP, float4* out)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= K * 12 * NP) return;
+    const int k = idx % NP, row = idx / NP;
+    const int p = row / 12, own = (row % 12) / 3, a = row % 3;
+    const int to = sig_of_alt(a, own);
+    double d = 0.0;
+    if (k < NH) {
+        if ((own ^ to) & 1) d += (to & 1) ? W[(size_t)k * 2 * K + 2 * p] : -W[(size_t)k * 2 * K + 2 * p];
+        if ((own ^ to) & 2) d += (to & 2) ? W[(size_t)k * 2 * K + 2 * p + 1] : -W[(size_t)k * 2 * K + 2 * p + 1];
+    }
+    // em = e^d - 1, inv = e^-d: cosh d - 1 = em^2 inv / 2, sinh d = em (1 + inv) / 2
+    const double em = expm1(d), inv = 1.0 / (1.0 + em);
+    const double ch1 = 0.5 * em * em * inv, sh = 0.5 * em * (1.0 + inv);
+    out[idx] = make_float4((float)(sh / (1.0 + ch1)), (float)ch1, (float)d, 0.f);
+}
+
+int fam_corr_sites(const double* W, int K, int n_hidden, float4* out, cudaStream_t st)
+{
+    const int NP = (n_hidden + 3) & ~3, n = K * 12 * NP;
+    if (n_hidden <= 0) return 0;
+    k_corr_sites<<<(n + 255) / 256, 256, 0, st>>>(W, K, n_hidden, NP, out);
+    return 1;
 }
 
 // ---------------------------------------------------------------------------
