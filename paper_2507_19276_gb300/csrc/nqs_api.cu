@@ -47,6 +47,7 @@ struct nqs_ctx {
     DevBuf WT;                // W transposed, [2K][n_hidden rounded up to 4], zero-padded
     DevBuf Af, ATf, WTf;      // FP32 copies for the shared-prefix FP32 path
     DevBuf csite;             // FP32 path: per-site correlator factors (fam_corr_sites)
+    DevBuf ATdf;              // chain: AT as FP32 (hi, lo) pairs for psi(n) in the mixed form
     DevBuf tc_img, tc_exps;   // split-FP16 operand images for the tensor-core batches
     bool has_tc = false;
 
@@ -380,7 +381,8 @@ int env_pass(nqs_ctx* c, const uint64_t* samples, int64_t Ns, bool adjoints, int
     e.samples = samples;
     e.Ns = Ns;
     e.tn = tn;
-    if (tn == 2 || tn == 0) {
+    e.ATdf = (const float2*)c->ATdf.p;
+    if (tn == 2 || tn == 3 || tn == 0) {
         // psi(n) only
     } else if (c->av.chain) {
         TRY(ensure(c, c->Lenv, (size_t)Ns * (K + 1) * D * 8));
@@ -790,7 +792,7 @@ extern "C" int nqs_destroy(nqs_ctx* c)
                       &c->draw_rank, &c->draw_coef, &c->n_unique, &c->base_det, &c->base_draw,
                       &c->part_det, &c->part_draw, &c->eloc, &c->edet, &c->estoch, &c->summary,
                       &c->derr, &c->span_det, &c->span_draw, &c->Af, &c->ATf,
-                      &c->WT, &c->WTf, &c->csite, &c->fpool, &c->fpoole, &c->ftl_end,
+                      &c->WT, &c->WTf, &c->csite, &c->ATdf, &c->fpool, &c->fpoole, &c->ftl_end,
                       &c->ftl_idx, &c->ftr_idx, &c->ftl_tot, &c->ftr_tot, &c->ftl_base,
                       &c->ftr_base, &c->ftl_ci,
                       &c->ftl_list, &c->ftr_list, &c->ftl_cnt, &c->frbl, &c->frbr, &c->frbl_base,
@@ -894,7 +896,8 @@ extern "C" int nqs_set_hamiltonian(nqs_ctx* c, const double* h1e, const double* 
     } else {
         const double* de;
         TRY(stage_in(c, c->st_out1, cholesky_or_eri, KK * KK, &de));
-        CK(cudaMemcpyAsync(c->eri.p, de, KK * KK * 8, cudaMemcpyDeviceToDevice, c->stream));
+        LAUNCH(NQS_STAGE_OTHER, launch_swap_eri(de, K, (double*)c->eri.p, c->stream));
+        CK(cudaGetLastError());
     }
     // blocks of the canonical order and the pair-unranking tables
     HamView h{};
@@ -1007,6 +1010,16 @@ extern "C" int nqs_set_ansatz(nqs_ctx* c, const double* site_tensors, int n_edge
         TRY(ensure(c, c->ATf, nt * 4));
         CK(cudaMemcpy(c->Af.p, fA.data(), nt * 4, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(c->ATf.p, fAT.data(), nt * 4, cudaMemcpyHostToDevice));
+        if (chain) {
+            // (hi, lo) with hi = fl32(AT), lo = fl32(AT - hi): 48 of AT's 53 bits
+            std::vector<float2> dAT(nt);
+            for (size_t i = 0; i < nt; ++i) {
+                const float h = (float)hAT[i];
+                dAT[i] = make_float2(h, (float)(hAT[i] - (double)h));
+            }
+            TRY(ensure(c, c->ATdf, nt * 8));
+            CK(cudaMemcpy(c->ATdf.p, dAT.data(), nt * 8, cudaMemcpyHostToDevice));
+        }
         if (n_hidden > 0) {
             // transposed copies for the correlator factors: lanes over hidden units
             // read consecutive words of one spin-orbital's column
@@ -1404,7 +1417,8 @@ int le_core(nqs_ctx* c, const uint64_t* ds, const double* dc, int64_t Ns, uint64
     {
         StageScope sc(c, NQS_STAGE_ENV);
         LAUNCH(NQS_STAGE_ENV, launch_validate(ds, Ns, c->K, c->na, c->nb, (DevError*)c->derr.p, c->stream));
-        TRY(env_pass(c, ds, Ns, false, rnn ? 0 : (shared ? 2 : 1)));
+        // the mixed form takes psi(n) in double-FP32 arithmetic, the FP64 forms in FP64
+        TRY(env_pass(c, ds, Ns, false, rnn ? 0 : (shared ? (prec == NQS_PREC_MIXED ? 3 : 2) : 1)));
         if (rnn) TRY(rnn_env_pass(c, ds, Ns));
         k_check_psi<<<(unsigned)((Ns + 255) / 256), 256, 0, c->stream>>>((const double*)c->pmant.p, Ns,
                                                                        (DevError*)c->derr.p);

@@ -26,19 +26,9 @@ __global__ void __launch_bounds__(kEnumWarps * 32) k_enum(EnumArgs a)
     __syncthreads();
     const HamView& h = a.h;
     const size_t srow = (size_t)s * a.n_chunks;
-    for (int k = 0; k < kChunksPerWarp; ++k) {
-        const uint32_t c = (blockIdx.x * kEnumWarps + warp) * kChunksPerWarp + k;
-        if (c >= a.n_chunks) break;
-        const uint32_t r = c * 32 + lane;
-        const bool valid = ok && r < h.n_conn;
-        double H = 0.0;
-        if (valid) {
-            uint64_t ma, mb;
-            int odd;
-            // the split and the weights depend on |H| only: no phase here
-            Exc e = decode_rank<false>(h, lists, r);
-            H = matrix_element(h, na, nb, e, ma, mb, odd);
-        }
+    const uint32_t c_beg = (blockIdx.x * kEnumWarps + warp) * kChunksPerWarp;
+    // the chunk's ballot of |H| >= eps, its count and its remainder weight sum
+    auto record = [&](uint32_t c, bool valid, double H) {
         const bool det = valid && is_det(H, a.eps_bits);
         const unsigned bal = __ballot_sync(kFull, det);
         if (lane == 0) {
@@ -50,6 +40,45 @@ __global__ void __launch_bounds__(kEnumWarps * 32) k_enum(EnumArgs a)
             w = warp_sum_sliced(w);
             if (lane == 0) a.chunk_w[srow + c] = w;
         }
+    };
+    if (ok && c_beg * 32 >= h.blk[4] && h.blk[4] < h.n_conn) {
+        // every rank of this warp is an alpha-beta double (or past the end):
+        // decode the first rank, then step the indices by 32 ranks per chunk.
+        // H = (ai|bj) with i, a alpha and j, b beta, as in matrix_element.
+        const uint32_t x = c_beg * 32 + lane - h.blk[4];
+        const uint32_t ia = fdiv(x, h.div_sb), jb = x - ia * h.div_sb.d;
+        int io = (int)fdiv(ia, h.div_nv[0]), ao = (int)ia - io * h.nv[0];
+        int jo = (int)fdiv(jb, h.div_nv[1]), bo = (int)jb - jo * h.nv[1];
+        for (int k = 0; k < kChunksPerWarp; ++k) {
+            const uint32_t c = c_beg + k;
+            if (c >= a.n_chunks) break;
+            const bool valid = c * 32 + lane < h.n_conn;
+            double H = 0.0;
+            if (valid)
+                H = eri_at(h, lists.vir[0][ao], lists.occ[0][io], lists.vir[1][bo], lists.occ[1][jo]);
+            record(c, valid, H);
+            bo += 32;
+            while (bo >= h.nv[1]) {          // nv_beta >= 1 when the block is not empty
+                bo -= h.nv[1];
+                if (++jo == h.no[1]) { jo = 0; if (++ao == h.nv[0]) { ao = 0; ++io; } }
+            }
+        }
+        return;
+    }
+    for (int k = 0; k < kChunksPerWarp; ++k) {
+        const uint32_t c = c_beg + k;
+        if (c >= a.n_chunks) break;
+        const uint32_t r = c * 32 + lane;
+        const bool valid = ok && r < h.n_conn;
+        double H = 0.0;
+        if (valid) {
+            uint64_t ma, mb;
+            int odd;
+            // the split and the weights depend on |H| only: no phase here
+            Exc e = decode_rank<false>(h, lists, r);
+            H = matrix_element(h, na, nb, e, ma, mb, odd);
+        }
+        record(c, valid, H);
     }
 }
 

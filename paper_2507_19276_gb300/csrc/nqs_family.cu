@@ -575,29 +575,44 @@ __global__ void k_fam_rbm(FamArgs<T> f)
             // tanh and expm1 of theta + d directly.
             const float4* r1 = f.csite + ((size_t)(s_hi * 4 + sigma_at(na, nb, s_hi)) * 3 + a_hi) * NP;
             const float4* r2 = f.csite + ((size_t)(s_lo * 4 + sigma_at(na, nb, s_lo)) * 3 + a_lo) * NP;
-            for (int k = hl; valid && k < NP; k += 16) {
-                if (k >= NH) { out[k] = 0.f; continue; }
-                const float4 u = __ldg(r1 + k);
-                const float4 v = ns == 2 ? __ldg(r2 + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float sx = u.x + v.x, px = u.x * v.x;
-                const float e = fmaf(u.y, v.y, u.y + v.y);
-                const float t = tt_s[k];
-                float val, y;
-                const float den = left ? fmaf(t, sx, 1.f + px) : 1.f + px;
-                if (den >= 0.5f) {
-                    const float g = left ? fmaf(t, sx, px) : px;      // den - 1
-                    val = __fdividef(left ? fmaf(t, px, t + sx) : sx, den);
-                    y = fmaf(e, g, e + g);
-                } else {
-                    const float d = u.z + v.z;
-                    const float em = expm1f(d);
-                    const float inv = 1.f / (1.f + em);
-                    const float ch1 = 0.5f * em * em * inv, sh = 0.5f * em * (1.f + inv);
-                    val = left ? tanhf(th_s[k] + d) : sh / (1.f + ch1);
-                    y = left ? ch1 + t * sh : ch1;
+            // four units per lane at a time, their table loads issued first
+            for (int k0 = hl; valid && k0 < NP; k0 += 64) {
+                float4 uu[4], vv[4];
+                #pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int k = k0 + 16 * i;
+                    uu[i] = vv[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (k < NH) {
+                        uu[i] = __ldg(r1 + k);
+                        if (ns == 2) vv[i] = __ldg(r2 + k);
+                    }
                 }
-                out[k] = val;
-                pm1 = fmaf(pm1, y, pm1 + y);
+                #pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int k = k0 + 16 * i;
+                    if (k >= NP) break;
+                    if (k >= NH) { out[k] = 0.f; continue; }
+                    const float4 u = uu[i], v = vv[i];
+                    const float sx = u.x + v.x, px = u.x * v.x;
+                    const float e = fmaf(u.y, v.y, u.y + v.y);
+                    const float t = tt_s[k];
+                    float val, y;
+                    const float den = left ? fmaf(t, sx, 1.f + px) : 1.f + px;
+                    if (den >= 0.5f) {
+                        const float g = left ? fmaf(t, sx, px) : px;      // den - 1
+                        val = __fdividef(left ? fmaf(t, px, t + sx) : sx, den);
+                        y = fmaf(e, g, e + g);
+                    } else {
+                        const float d = u.z + v.z;
+                        const float em = expm1f(d);
+                        const float inv = 1.f / (1.f + em);
+                        const float ch1 = 0.5f * em * em * inv, sh = 0.5f * em * (1.f + inv);
+                        val = left ? tanhf(th_s[k] + d) : sh / (1.f + ch1);
+                        y = left ? ch1 + t * sh : ch1;
+                    }
+                    out[k] = val;
+                    pm1 = fmaf(pm1, y, pm1 + y);
+                }
             }
         } else {
             uint32_t pk = 0;
@@ -751,51 +766,73 @@ __global__ void __launch_bounds__(256) k_site_build(FamArgs<T> f, SiteBufs sb)
 // Boundary vectors L_t (R_t) of each sample and side and the three families
 // that start at each site, on the CUDA cores (in the arithmetic type of the
 // tables; FP32 for the tensor-core form, whose split-FP16 products would put
-// their error into every vector built on the boundary): one block per
-// (sample, side), steps in order.
-template <typename T>
+// their error into every vector built on the boundary). One block per side and
+// group of S samples, steps in order: at each site the four matrices
+// [A^0; A^1; A^2; A^3] are read once per block and applied to the S samples'
+// vectors (every sample needs all four: its three alternatives and its own
+// state), one output row per thread and pass with an fma over the input index
+// in ascending order (the order of mv_block, so the results are the same bit
+// for bit).
+template <typename T, int S>
 __global__ void __launch_bounds__(256) k_site_boundary(FamArgs<T> f)
 {
     extern __shared__ __align__(16) unsigned char smb[];
-    __shared__ int eo[4];
-    __shared__ int eL;
-    const int b = blockIdx.x >> 1, side = blockIdx.x & 1, K = f.K, D = f.D;
-    T* X = (T*)smb;                               // [D]
-    T* Y = X + D;                                 // [4][D]
-    const int64_t s = f.s0 + b;
-    const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
-    T* Tb = (side == 0 ? f.G : f.H) + (size_t)b * 3 * K * K * D;
-    int* Te = (side == 0 ? f.Ge : f.He) + (size_t)b * 3 * K * K;
+    __shared__ int eo[S * 4];
+    __shared__ int eL[S];
+    __shared__ int own_s[S];
+    const int nbb = (int)(f.s1 - f.s0);
+    const int side = blockIdx.x & 1, g0 = (blockIdx.x >> 1) * S;
+    const int ns = nbb - g0 < S ? nbb - g0 : S;
+    const int K = f.K, D = f.D;
+    T* X = (T*)smb;                               // [S][D] the samples' vectors
+    T* Z = X + (size_t)S * D;                     // [S][4][D] their four products
     const T* Mats = side == 0 ? f.AT : f.A;       // column convention left, row vectors right
-    for (int c = threadIdx.x; c < D; c += blockDim.x) X[c] = c == 0 ? T(1) : T(0);
-    if (threadIdx.x == 0) eL = 0;
+    for (int q = threadIdx.x; q < S * D; q += blockDim.x) X[q] = (q % D) == 0 ? T(1) : T(0);
+    if (threadIdx.x < S) eL[threadIdx.x] = 0;
     __syncthreads();
     for (int step = 0; step < K; ++step) {
         const int t = side == 0 ? step : K - 1 - step;
-        const int own = sigma_at(na, nb, t);
-        // the four products (three alternatives, then the own state) at once: one
-        // output per thread, fma over the input index in ascending order (the
-        // order of mv_block, so the results are the same bit for bit)
+        if (threadIdx.x < ns) {
+            const int64_t s = f.s0 + g0 + threadIdx.x;
+            own_s[threadIdx.x] = sigma_at(f.samples[2 * s], f.samples[2 * s + 1], t);
+        }
         for (int q = threadIdx.x; q < 4 * D; q += blockDim.x) {
-            const int a = q / D, r = q - a * D;
-            const int sg = a == 3 ? own : sig_of_alt(a, own);
+            const int sg = q / D, r = q - sg * D;
             const T* MT = Mats + ((size_t)t * 4 + sg) * D * D;
-            T acc = T(0);
-            for (int c = 0; c < D; ++c) acc = fma(__ldg(MT + (size_t)c * D + r), X[c], acc);
-            Y[q] = acc;
+            T acc[S];
+            #pragma unroll
+            for (int j = 0; j < S; ++j) acc[j] = T(0);
+            for (int c = 0; c < D; ++c) {
+                const T m = __ldg(MT + (size_t)c * D + r);
+                #pragma unroll
+                for (int j = 0; j < S; ++j) acc[j] = fma(m, X[j * D + c], acc[j]);
+            }
+            #pragma unroll
+            for (int j = 0; j < S; ++j)
+                if (j < ns) Z[((size_t)j * 4 + sg) * D + r] = acc[j];
         }
         __syncthreads();
-        renorm_rows<T>(Y, D, 4, eo);
+        renorm_rows<T>(Z, D, ns * 4, eo);
         __syncthreads();
-        const int e_in = eL;
-        for (int q = threadIdx.x; q < 3 * D; q += blockDim.x) {
-            const int a = q / D, c = q - a * D;
-            Tb[(((size_t)a * K + t) * K + t) * D + c] = Y[q];
+        // the three alternatives' families at their first site, then the own
+        // state's product as the next boundary vector
+        for (int q = threadIdx.x; q < ns * 3 * D; q += blockDim.x) {
+            const int j = q / (3 * D), ac = q - j * 3 * D, a = ac / D, c = ac - a * D;
+            const int sg = sig_of_alt(a, own_s[j]);
+            T* Tb = (side == 0 ? f.G : f.H) + (size_t)(g0 + j) * 3 * K * K * D;
+            Tb[(((size_t)a * K + t) * K + t) * D + c] = Z[((size_t)j * 4 + sg) * D + c];
         }
-        for (int a = threadIdx.x; a < 3; a += blockDim.x) Te[((size_t)a * K + t) * K + t] = e_in + eo[a];
-        for (int c = threadIdx.x; c < D; c += blockDim.x) X[c] = Y[3 * D + c];
+        for (int q = threadIdx.x; q < ns * 3; q += blockDim.x) {
+            const int j = q / 3, a = q - 3 * j;
+            int* Te = (side == 0 ? f.Ge : f.He) + (size_t)(g0 + j) * 3 * K * K;
+            Te[((size_t)a * K + t) * K + t] = eL[j] + eo[j * 4 + sig_of_alt(a, own_s[j])];
+        }
+        for (int q = threadIdx.x; q < ns * D; q += blockDim.x) {
+            const int j = q / D, c = q - j * D;
+            X[q] = Z[((size_t)j * 4 + own_s[j]) * D + c];
+        }
         __syncthreads();
-        if (threadIdx.x == 0) eL = e_in + eo[3];
+        if (threadIdx.x < ns) eL[threadIdx.x] += eo[threadIdx.x * 4 + own_s[threadIdx.x]];
         __syncthreads();
     }
 }
@@ -1121,7 +1158,19 @@ template <typename T>
 int fam_site_count(const FamArgs<T>& f, const SiteBufs& b, int nbb, cudaStream_t st)
 {
     const int n = f.K * 8;
-    k_site_boundary<T><<<nbb * 2, 256, (size_t)5 * f.D * sizeof(T), st>>>(f);
+    // eight samples per block when the batch fills the GPU with them (the
+    // matrices are then read once per eight samples), else one (small calls
+    // keep one short chain per block)
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (nbb >= 8 * n_sm) {
+        const size_t smem = (size_t)5 * 8 * f.D * sizeof(T);
+        allow_max_smem(k_site_boundary<T, 8>);
+        k_site_boundary<T, 8><<<(unsigned)((nbb + 7) / 8) * 2, 256, smem, st>>>(f);
+    } else {
+        k_site_boundary<T, 1><<<(unsigned)nbb * 2, 256, (size_t)5 * f.D * sizeof(T), st>>>(f);
+    }
     k_site_build<T, false><<<nbb, 256, 0, st>>>(f, b);
     const int ns = launch_scan_i64_wide(b.counts, b.offs, (int64_t)n * nbb, b.scan_tmp, st);
     k_site_bounds<<<1, 256, 0, st>>>(b.offs, n, nbb, b.bounds);

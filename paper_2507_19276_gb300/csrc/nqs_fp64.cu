@@ -85,6 +85,44 @@ __global__ void k_env_fp64(EnvArgs a)
 
     if (!a.tn) {
         // tensor-network part done elsewhere
+    } else if (a.an.chain && a.tn == 3) {
+        // psi(n) alone in double-FP32 arithmetic (the error-free product by FMA
+        // and Knuth's two-sum, as in the double-double algorithms of Hida, Li and
+        // Bailey), on the FP32 pipe: the state as (hi, lo) float pairs in place of
+        // x, the site matrices as pairs, each output accumulated as an
+        // unnormalised pair (relative error about D 2^-48), then rounded to FP64
+        // for the exact power-of-two rescaling and split again
+        float* xh = (float*)x;
+        float* xl = xh + D;
+        for (int i = threadIdx.x; i < D; i += blockDim.x) { xh[i] = i == 0 ? 1.f : 0.f; xl[i] = 0.f; }
+        int ex = 0;
+        __syncthreads();
+        for (int t = 0; t < K; ++t) {
+            const float2* M = a.ATdf + ((size_t)t * 4 + sigma_at(na, nb, t)) * D * D;
+            for (int r = threadIdx.x; r < D; r += blockDim.x) {
+                float hi = 0.f, lo = 0.f;
+                for (int c = 0; c < D; ++c) {
+                    const float2 m = __ldg(M + (size_t)c * D + r);
+                    const float ah = xh[c], al = xl[c];
+                    const float ph = m.x * ah;
+                    const float pl = fmaf(m.x, ah, -ph) + fmaf(m.x, al, m.y * ah);
+                    const float u = hi + ph, z = u - hi;
+                    lo += ((hi - (u - z)) + (ph - z)) + pl;
+                    hi = u;
+                }
+                y[r] = (double)hi + (double)lo;
+            }
+            __syncthreads();
+            ex += block_renorm(y, D, sh);
+            for (int i = threadIdx.x; i < D; i += blockDim.x) {
+                const float h = (float)y[i];
+                xh[i] = h;
+                xl[i] = (float)(y[i] - (double)h);
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) { a.psi_mant[s] = (double)xh[0] + (double)xl[0]; a.psi_exp[s] = ex; }
+        __syncthreads();
     } else if (a.an.chain) {
         const bool keep = a.tn == 1;    // store the environments
         double* Ls = keep ? a.Lenv + (size_t)s * (K + 1) * D : nullptr;

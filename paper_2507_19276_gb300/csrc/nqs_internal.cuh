@@ -175,10 +175,13 @@ __device__ __forceinline__ Exc decode_rank(const HamView& h, const OrbLists& L, 
     return e;
 }
 
+// (pq|rs): the table keeps the last two indices swapped, [p][q][s][r], so that
+// the doubles' reads (pq|rs) over consecutive virtual orbitals r of one warp
+// fall on consecutive words
 __device__ __forceinline__ double eri_at(const HamView& h, int p, int q, int r, int s)
 {
     const uint32_t K = (uint32_t)h.K;          // K <= 64: K^4 <= 2^24
-    return __ldg(h.eri + ((((uint32_t)p * K + (uint32_t)q) * K + (uint32_t)r) * K + (uint32_t)s));
+    return __ldg(h.eri + ((((uint32_t)p * K + (uint32_t)q) * K + (uint32_t)s) * K + (uint32_t)r));
 }
 
 // <m|H|n> for m = gamma a+_a (a+_b a_j) a_i |n>; writes m and the phase bit

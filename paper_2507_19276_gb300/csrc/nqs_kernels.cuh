@@ -85,6 +85,7 @@ int launch_validate(const uint64_t* samples, int64_t Ns, int K, int na, int nb, 
 // ---- utilities (nqs_util.cu) -----------------------------------------------
 
 int launch_build_eri(const double* L, int n_chol, int K, double* eri, cudaStream_t st);
+int launch_swap_eri(const double* in, int K, double* eri, cudaStream_t st);
 // per sample: exclusive scan of u32 chunk counts -> chunk_off, totals -> n_det
 int launch_scan_chunks_u32(const uint32_t* cnt, uint32_t* off, int64_t* total, int64_t Ns,
                             uint32_t n_chunks, cudaStream_t st);
@@ -276,7 +277,9 @@ struct EnvArgs {
     double* psi_mant; int* psi_exp;      // [Ns] psi_TN = mant 2^exp
     double* h_diag;                      // [Ns]
     int tn;                              // 0: skip the tensor-network part; 1: psi(n) and the
-                                         // environments; 2 (chain): psi(n) only
+                                         // environments; 2 (chain): psi(n) only; 3 (chain):
+                                         // psi(n) only, in double-FP32 arithmetic (ATdf)
+    const float2* ATdf;                  // tn == 3: AT as FP32 (hi, lo) pairs, hi + lo = AT
 };
 int launch_env_fp64(const EnvArgs& a, cudaStream_t st);
 

@@ -4,13 +4,15 @@
 
 namespace nqs {
 
-// (pq|rs) = sum_x L[x][p][q] L[x][r][s], ascending x, fused multiply-add.
+// (pq|rs) = sum_x L[x][p][q] L[x][r][s], ascending x, fused multiply-add,
+// stored at [p][q][s][r] (the layout eri_at reads).
 __global__ void k_build_eri(const double* L, int n_chol, int K, double* eri)
 {
     const int64_t KK = (int64_t)K * K;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= KK * KK) return;
-    const int64_t pq = idx / KK, rs = idx - pq * KK;
+    const int64_t pq = idx / KK, sr = idx - pq * KK;
+    const int64_t s = sr / K, r = sr - s * K, rs = r * K + s;
     double acc = 0.0;
     for (int x = 0; x < n_chol; ++x)
         acc = __fma_rn(__ldg(L + x * KK + pq), __ldg(L + x * KK + rs), acc);
@@ -21,6 +23,24 @@ int launch_build_eri(const double* L, int n_chol, int K, double* eri, cudaStream
 {
     const int64_t n = (int64_t)K * K * K * K;
     k_build_eri<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(L, n_chol, K, eri);
+    return 1;
+}
+
+// a full (pq|rs) table [p][q][r][s] into the layout eri_at reads, [p][q][s][r]
+__global__ void k_swap_eri(const double* in, int K, double* eri)
+{
+    const int64_t KK = (int64_t)K * K;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= KK * KK) return;
+    const int64_t pq = idx / KK, sr = idx - pq * KK;
+    const int64_t s = sr / K, r = sr - s * K;
+    eri[idx] = in[pq * KK + r * K + s];
+}
+
+int launch_swap_eri(const double* in, int K, double* eri, cudaStream_t st)
+{
+    const int64_t n = (int64_t)K * K * K * K;
+    k_swap_eri<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, K, eri);
     return 1;
 }
 
