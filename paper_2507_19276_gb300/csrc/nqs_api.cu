@@ -642,6 +642,7 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
     const int NH = c->av.n_hidden;
     RowSet rd{};
     rd.rank = (const uint32_t*)c->det_rank.p;
+    rd.sites = 1;                                   // site words once marked (k_fam_mark)
     rd.coef = (const double*)c->det_coef.p;
     rd.begin = (const int64_t*)c->det_off.p;
     rd.count = (const int64_t*)c->det_tot.p;
@@ -677,8 +678,13 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
         CK(cudaMemsetAsync(c->ftl_end.p, 0xff, (size_t)nbb * nk * 4, c->stream));
         CK(cudaMemsetAsync(c->ftr_idx.p, 0, (size_t)nbb * nk * 4, c->stream));
         // (the families are built with TL and TR, site-synchronously, below)
-        LAUNCH(NQS_STAGE_TABLES, fam_launch_mark<T>(f, rd, nbb, c->stream));
-        if (n_draws > 0) LAUNCH(NQS_STAGE_TABLES, fam_launch_mark<T>(f, rs, nbb, c->stream));
+        {
+            // the deterministic rows: marks, and their ranks replaced by site words
+            RowSet rk = rd;
+            rk.sites = 0;
+            LAUNCH(NQS_STAGE_TABLES, fam_launch_mark<T>(f, rk, nbb, (uint32_t*)c->det_rank.p, c->stream));
+        }
+        if (n_draws > 0) LAUNCH(NQS_STAGE_TABLES, fam_launch_mark<T>(f, rs, nbb, nullptr, c->stream));
         LAUNCH(NQS_STAGE_TABLES, fam_launch_compact<T>(f, nbb, c->stream));
         // packed table offsets per sample of the batch
         {

@@ -403,9 +403,44 @@ __device__ __forceinline__ RowParts row_parts(const HamView& h, const OrbLists& 
     return r;
 }
 
+// Site word of a row: its changed sites in ascending order, 6 bits each at
+// bits 0, 6, 12, 18 (a 2- or 3-site change repeats its last site), and at bits
+// 24 + 2q the index of site q's new local state among the three states other
+// than n's. The marking pass replaces the deterministic rows' ranks by these
+// words, so that the row kernel reads the parts instead of decoding them.
+__device__ __forceinline__ uint32_t site_word(const RowParts& p)
+{
+    uint32_t w = 0;
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int qq = q < p.nsite ? q : p.nsite - 1;
+        w |= ((uint32_t)p.s[qq] << (6 * q)) | ((uint32_t)(q < p.nsite ? p.a[q] : 0) << (24 + 2 * q));
+    }
+    return w;
+}
+
+// the parts of row `idx` of a row set: from its site word, or by decoding its
+// canonical rank
+__device__ __forceinline__ RowParts row_parts_of(const HamView& h, const OrbLists& L, uint64_t na,
+                                                 uint64_t nb, const RowSet& rows, int64_t idx)
+{
+    if (!rows.sites) return row_parts(h, L, na, nb, rows.rank[idx]);
+    const uint32_t x = rows.rank[idx];
+    RowParts r;
+    #pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        r.s[q] = (int)((x >> (6 * q)) & 63u);
+        r.a[q] = (int)((x >> (24 + 2 * q)) & 3u);
+    }
+    r.nsite = 2 + (r.s[2] != r.s[1] ? 1 : 0) + (r.s[3] != r.s[2] ? 1 : 0);
+    r.last = r.s[3];
+    r.ma = r.mb = 0;
+    return r;
+}
+
 // F2: mark the clusters the rows need (TL end site, TR use)
 template <typename T>
-__global__ void k_fam_mark(FamArgs<T> f, RowSet rows)
+__global__ void k_fam_mark(FamArgs<T> f, RowSet rows, uint32_t* words)
 {
     __shared__ OrbLists lists;
     const int b = blockIdx.y;
@@ -413,13 +448,14 @@ __global__ void k_fam_mark(FamArgs<T> f, RowSet rows)
     const int64_t beg = rows.begin ? rows.begin[s] : s * rows.stride;
     const int64_t cnt = rows.count[s];
     const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
-    if (threadIdx.x < 32) build_lists_warp(na, nb, f.h.K, lists, threadIdx.x);
+    if (threadIdx.x < 32 && !rows.sites) build_lists_warp(na, nb, f.h.K, lists, threadIdx.x);
     __syncthreads();
     const int K = f.K;
     const size_t nk = (size_t)K * K * 9;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < cnt;
          r += (int64_t)gridDim.x * blockDim.x) {
-        const RowParts p = row_parts(f.h, lists, na, nb, rows.rank[beg + r]);
+        const RowParts p = row_parts_of(f.h, lists, na, nb, rows, beg + r);
+        if (words) words[beg + r] = site_word(p);      // in place of the rank just read
         if (p.nsite == 3) {
             f.tr_idx[(size_t)b * nk + tr_key(K, p.s[1], p.a[1], p.s[2], p.a[2])] = 1;
         } else if (p.nsite == 4) {
@@ -521,8 +557,20 @@ __device__ __forceinline__ int site_flips(uint64_t na, uint64_t nb, int s, int a
     return nf;
 }
 
+// A correlator factor evaluated directly from theta + d (FP32): the rare units
+// whose addition-formula denominator is below 1/2 (out of line, so that the
+// common path keeps few registers)
+__device__ __noinline__ void rbm_direct(bool left, float th, float t, float d, float& val, float& y)
+{
+    const float em = expm1f(d);
+    const float inv = 1.f / (1.f + em);
+    const float ch1 = 0.5f * em * em * inv, sh = 0.5f * em * (1.f + inv);
+    val = left ? tanhf(th + d) : sh / (1.f + ch1);
+    y = left ? ch1 + t * sh : ch1;
+}
+
 template <typename T>
-__global__ void k_fam_rbm(FamArgs<T> f)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 2) k_fam_rbm(FamArgs<T> f)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
     T* th_s = (T*)smraw;               // theta_k(n)
@@ -575,45 +623,71 @@ __global__ void k_fam_rbm(FamArgs<T> f)
             // tanh and expm1 of theta + d directly.
             const float4* r1 = f.csite + ((size_t)(s_hi * 4 + sigma_at(na, nb, s_hi)) * 3 + a_hi) * NP;
             const float4* r2 = f.csite + ((size_t)(s_lo * 4 + sigma_at(na, nb, s_lo)) * 3 + a_lo) * NP;
-            // four units per lane at a time, their table loads issued first
-            for (int k0 = hl; valid && k0 < NP; k0 += 64) {
-                float4 uu[4], vv[4];
-                #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int k = k0 + 16 * i;
-                    uu[i] = vv[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (k < NH) {
-                        uu[i] = __ldg(r1 + k);
-                        if (ns == 2) vv[i] = __ldg(r2 + k);
-                    }
-                }
-                #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int k = k0 + 16 * i;
-                    if (k >= NP) break;
-                    if (k >= NH) { out[k] = 0.f; continue; }
-                    const float4 u = uu[i], v = vv[i];
+            // one loop per kind of object (left / right, one / two sites), each
+            // with only its own arithmetic; rare units with den < 1/2 take the
+            // direct evaluation
+            auto direct = [&](int k, float d, float& val, float& y) {
+                rbm_direct(left, th_s[k], tt_s[k], d, val, y);
+            };
+            if (!valid) {
+            } else if (left && ns == 2) {
+                for (int k = hl; k < NH; k += 16) {
+                    const float4 u = __ldg(r1 + k), v = __ldg(r2 + k);
+                    const float t = tt_s[k];
                     const float sx = u.x + v.x, px = u.x * v.x;
                     const float e = fmaf(u.y, v.y, u.y + v.y);
-                    const float t = tt_s[k];
+                    const float den = fmaf(t, sx, 1.f + px);
                     float val, y;
-                    const float den = left ? fmaf(t, sx, 1.f + px) : 1.f + px;
                     if (den >= 0.5f) {
-                        const float g = left ? fmaf(t, sx, px) : px;      // den - 1
-                        val = __fdividef(left ? fmaf(t, px, t + sx) : sx, den);
+                        const float g = fmaf(t, sx, px);
+                        val = __fdividef(fmaf(t, px, t + sx), den);
                         y = fmaf(e, g, e + g);
                     } else {
-                        const float d = u.z + v.z;
-                        const float em = expm1f(d);
-                        const float inv = 1.f / (1.f + em);
-                        const float ch1 = 0.5f * em * em * inv, sh = 0.5f * em * (1.f + inv);
-                        val = left ? tanhf(th_s[k] + d) : sh / (1.f + ch1);
-                        y = left ? ch1 + t * sh : ch1;
+                        direct(k, u.z + v.z, val, y);
                     }
                     out[k] = val;
                     pm1 = fmaf(pm1, y, pm1 + y);
                 }
+            } else if (left) {
+                for (int k = hl; k < NH; k += 16) {
+                    const float4 u = __ldg(r1 + k);
+                    const float t = tt_s[k];
+                    const float den = fmaf(t, u.x, 1.f);
+                    float val, y;
+                    if (den >= 0.5f) {
+                        const float g = t * u.x;
+                        val = __fdividef(t + u.x, den);
+                        y = fmaf(u.y, g, u.y + g);
+                    } else {
+                        direct(k, u.z, val, y);
+                    }
+                    out[k] = val;
+                    pm1 = fmaf(pm1, y, pm1 + y);
+                }
+            } else if (ns == 2) {
+                for (int k = hl; k < NH; k += 16) {
+                    const float4 u = __ldg(r1 + k), v = __ldg(r2 + k);
+                    const float sx = u.x + v.x, px = u.x * v.x;
+                    const float e = fmaf(u.y, v.y, u.y + v.y);
+                    const float den = 1.f + px;
+                    float val, y;
+                    if (den >= 0.5f) {
+                        val = __fdividef(sx, den);
+                        y = fmaf(e, px, e + px);
+                    } else {
+                        direct(k, u.z + v.z, val, y);
+                    }
+                    out[k] = val;
+                    pm1 = fmaf(pm1, y, pm1 + y);
+                }
+            } else {
+                for (int k = hl; k < NH; k += 16) {          // tanh d1 and cosh d1 - 1 as stored
+                    const float4 u = __ldg(r1 + k);
+                    out[k] = u.x;
+                    pm1 = fmaf(pm1, u.y, pm1 + u.y);
+                }
             }
+            for (int k = NH + ((hl - NH) % 16 + 16) % 16; valid && k < NP; k += 16) out[k] = 0.f;
         } else {
             uint32_t pk = 0;
             int nf = 0;
@@ -1295,7 +1369,7 @@ __global__ void __launch_bounds__(kFamRows, MB) k_fam_rows(FamArgs<T> f, RowSet 
     const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
     const int NH = f.n_hidden, NP = nh_pad(NH);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (warp == 0) build_lists_warp(na, nb, f.h.K, lists, lane);
+    if (warp == 0 && !rows.sites) build_lists_warp(na, nb, f.h.K, lists, lane);
     if (threadIdx.x == 32) s_inv_pm = 1.0 / f.pm[b];
     __syncthreads();
     const size_t nk = (size_t)K * K * 9;
@@ -1308,7 +1382,7 @@ __global__ void __launch_bounds__(kFamRows, MB) k_fam_rows(FamArgs<T> f, RowSet 
     double coef = 0.0;
     const int myrow = (int)threadIdx.x;
     if (myrow < nr) {
-        const RowParts p = row_parts(f.h, lists, na, nb, rows.rank[r0 + myrow]);
+        const RowParts p = row_parts_of(f.h, lists, na, nb, rows, r0 + myrow);
         const T* G = f.G + (size_t)b * 3 * K * K * D;
         const int* Ge = f.Ge + (size_t)b * 3 * K * K;
         const T* H = f.H + (size_t)b * 3 * K * K * D;
@@ -1532,10 +1606,10 @@ __global__ void __launch_bounds__(kFamRows, MB) k_fam_rows(FamArgs<T> f, RowSet 
 // ---------------------------------------------------------------------------
 
 template <typename T>
-int fam_launch_mark(const FamArgs<T>& f, const RowSet& rows, int nb, cudaStream_t st)
+int fam_launch_mark(const FamArgs<T>& f, const RowSet& rows, int nb, uint32_t* words, cudaStream_t st)
 {
     dim3 grid(16, nb);
-    k_fam_mark<T><<<grid, 256, 0, st>>>(f, rows);
+    k_fam_mark<T><<<grid, 256, 0, st>>>(f, rows, words);
     return 1;
 }
 
@@ -1609,7 +1683,7 @@ void fam_tc_images(const double* A, int K, int D, std::vector<unsigned char>& im
 }
 
 #define NQS_FAM_INST(T)                                                                    \
-    template int fam_launch_mark<T>(const FamArgs<T>&, const RowSet&, int, cudaStream_t);  \
+    template int fam_launch_mark<T>(const FamArgs<T>&, const RowSet&, int, uint32_t*, cudaStream_t);  \
     template int fam_launch_compact<T>(const FamArgs<T>&, int, cudaStream_t);              \
     template int fam_launch_rbm<T>(const FamArgs<T>&, int, cudaStream_t);                  \
     template int fam_site_count<T>(const FamArgs<T>&, const SiteBufs&, int, cudaStream_t);  \

@@ -52,7 +52,10 @@ struct FamArgs {
     const int64_t* rbl_base; const int64_t* rbr_base;   // [b] object offsets
 };
 
-template <typename T> int fam_launch_mark(const FamArgs<T>& f, const RowSet& rows, int nb, cudaStream_t st);
+// marks of the clusters the rows need; words (may be NULL) receives each row's
+// site word in place of its rank (rows.rank may point to the same array)
+template <typename T> int fam_launch_mark(const FamArgs<T>& f, const RowSet& rows, int nb, uint32_t* words,
+                                          cudaStream_t st);
 template <typename T> int fam_launch_compact(const FamArgs<T>& f, int nb, cudaStream_t st);
 // grid = upper bound of the batch's row chunks (128 rows each); blocks map to
 // rows.chunk_base[s0] + blockIdx.x. partial_abs (may be NULL) gets each chunk's

@@ -284,7 +284,8 @@ struct EnvArgs {
 int launch_env_fp64(const EnvArgs& a, cudaStream_t st);
 
 struct RowSet {
-    const uint32_t* rank;
+    const uint32_t* rank;                // canonical ranks, or site words (see nqs_family.cu)
+    int sites;                           // when set
     const double* coef;
     const int64_t* begin;                // [Ns] first row of each sample (NULL: s * stride)
     int64_t stride;
