@@ -46,8 +46,9 @@ struct nqs_ctx {
     DevBuf A, AT, W, b, pred_ptr, pred_idx;
     DevBuf WT;                // W transposed, [2K][n_hidden rounded up to 4], zero-padded
     DevBuf Af, ATf, WTf;      // FP32 copies for the shared-prefix FP32 path
-    DevBuf csite;             // FP32 path: per-site correlator factors (fam_corr_sites)
-    DevBuf ATdf;              // chain: AT as FP32 (hi, lo) pairs for psi(n) in the mixed form
+    DevBuf csite, csite64;    // per-site correlator factors, FP32 and FP64 (fam_corr_sites)
+    DevBuf ATdf, Adf;         // chain: AT and A as FP32 (hi, lo) pairs (double-FP32 arithmetic)
+    bool refine_df = false;   // FP64 tables of the error-budgeted re-evaluation: double-FP32 mat-vecs
     DevBuf tc_img, tc_exps;   // split-FP16 operand images for the tensor-core batches
     bool has_tc = false;
 
@@ -634,10 +635,14 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
     f.err = (DevError*)c->derr.p;
     f.A = (const T*)(dbl ? c->A.p : c->Af.p);
     f.AT = (const T*)(dbl ? c->AT.p : c->ATf.p);
+    f.df = (dbl && c->refine_df) ? 1 : 0;
+    f.Adf = (const float2*)c->Adf.p;
+    f.ATdf = (const float2*)c->ATdf.p;
     f.samples = ds;
     f.n_hidden = c->av.n_hidden;
     f.WT = (const T*)(dbl ? c->WT.p : c->WTf.p);
-    f.csite = dbl ? nullptr : (const float4*)c->csite.p;
+    f.csite = (const float4*)c->csite.p;
+    f.csite64 = (const double4_32a*)c->csite64.p;
     f.theta = (const double*)c->theta.p;
     const int NH = c->av.n_hidden;
     RowSet rd{};
@@ -798,7 +803,7 @@ extern "C" int nqs_destroy(nqs_ctx* c)
                       &c->draw_rank, &c->draw_coef, &c->n_unique, &c->base_det, &c->base_draw,
                       &c->part_det, &c->part_draw, &c->eloc, &c->edet, &c->estoch, &c->summary,
                       &c->derr, &c->span_det, &c->span_draw, &c->Af, &c->ATf,
-                      &c->WT, &c->WTf, &c->csite, &c->ATdf, &c->fpool, &c->fpoole, &c->ftl_end,
+                      &c->WT, &c->WTf, &c->csite, &c->csite64, &c->ATdf, &c->Adf, &c->fpool, &c->fpoole, &c->ftl_end,
                       &c->ftl_idx, &c->ftr_idx, &c->ftl_tot, &c->ftr_tot, &c->ftl_base,
                       &c->ftr_base, &c->ftl_ci,
                       &c->ftl_list, &c->ftr_list, &c->ftl_cnt, &c->frbl, &c->frbr, &c->frbl_base,
@@ -1017,14 +1022,17 @@ extern "C" int nqs_set_ansatz(nqs_ctx* c, const double* site_tensors, int n_edge
         CK(cudaMemcpy(c->Af.p, fA.data(), nt * 4, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(c->ATf.p, fAT.data(), nt * 4, cudaMemcpyHostToDevice));
         if (chain) {
-            // (hi, lo) with hi = fl32(AT), lo = fl32(AT - hi): 48 of AT's 53 bits
-            std::vector<float2> dAT(nt);
+            // (hi, lo) with hi = fl32(x), lo = fl32(x - hi): 48 of the entry's 53 bits
+            std::vector<float2> dAT(nt), dA(nt);
             for (size_t i = 0; i < nt; ++i) {
-                const float h = (float)hAT[i];
+                const float h = (float)hAT[i], g = (float)hA[i];
                 dAT[i] = make_float2(h, (float)(hAT[i] - (double)h));
+                dA[i] = make_float2(g, (float)(hA[i] - (double)g));
             }
             TRY(ensure(c, c->ATdf, nt * 8));
+            TRY(ensure(c, c->Adf, nt * 8));
             CK(cudaMemcpy(c->ATdf.p, dAT.data(), nt * 8, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(c->Adf.p, dA.data(), nt * 8, cudaMemcpyHostToDevice));
         }
         if (n_hidden > 0) {
             // transposed copies for the correlator factors: lanes over hidden units
@@ -1043,7 +1051,9 @@ extern "C" int nqs_set_ansatz(nqs_ctx* c, const double* site_tensors, int n_edge
             CK(cudaMemcpy(c->WT.p, hWT.data(), hWT.size() * 8, cudaMemcpyHostToDevice));
             CK(cudaMemcpy(c->WTf.p, fWT.data(), fWT.size() * 4, cudaMemcpyHostToDevice));
             TRY(ensure(c, c->csite, (size_t)K * 12 * np * 16));
-            fam_corr_sites((const double*)c->W.p, K, n_hidden, (float4*)c->csite.p, c->stream);
+            TRY(ensure(c, c->csite64, (size_t)K * 12 * np * 32));
+            fam_corr_sites((const double*)c->W.p, K, n_hidden, (float4*)c->csite.p, (double4_32a*)c->csite64.p,
+                           c->stream);
             CK(cudaGetLastError());
             CK(cudaStreamSynchronize(c->stream));
         }
@@ -1534,9 +1544,14 @@ int reevaluate(nqs_ctx* c, const uint64_t* ds, const double* dc, const std::vect
     LAUNCH(NQS_STAGE_OTHER, launch_gather_picked((const int64_t*)c->ref_idx.p, k, ds, dc, c->index_base,
                                                  (uint64_t*)c->ref_s.p, (double*)c->ref_c.p,
                                                  (int64_t*)c->ref_pos.p, c->stream));
-    TRY(le_core(c, (const uint64_t*)c->ref_s.p, (const double*)c->ref_c.p, k, eb, n_draws, seed,
-                c->av.chain ? NQS_PREC_FP64_SHARED : NQS_PREC_FP64, (const int64_t*)c->ref_pos.p,
-                (double*)c->ref_e.p, nullptr, false));
+    // the shared-prefix form's tables advance in double-FP32 (about 2^-44 per
+    // product, far below the tolerance such a re-evaluation serves)
+    c->refine_df = true;
+    const int rc = le_core(c, (const uint64_t*)c->ref_s.p, (const double*)c->ref_c.p, k, eb, n_draws, seed,
+                           c->av.chain ? NQS_PREC_FP64_SHARED : NQS_PREC_FP64, (const int64_t*)c->ref_pos.p,
+                           (double*)c->ref_e.p, nullptr, false);
+    c->refine_df = false;
+    TRY(rc);
     LAUNCH(NQS_STAGE_OTHER, launch_scatter_picked((const int64_t*)c->ref_idx.p, k,
                                                   (const double*)c->ref_e.p, de, c->stream));
     if (fp64) {

@@ -42,7 +42,7 @@ __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
 
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { typedef float4 type; };
-template <> struct Vec4<double> { typedef double4 type; };
+template <> struct Vec4<double> { typedef double4_32a type; };
 
 // Block-wide: y_i = M x_i for nv vectors in shared memory; MT[b][a] = M[a][b].
 // Each thread owns two outputs (a, a + D/2) of four vectors.
@@ -87,6 +87,34 @@ __device__ void mv_block(const T* __restrict__ MT, int D, const T* X, T* Y, int 
         for (int q = 0; q < n4; ++q) {
             Y[(size_t)(i + q) * D + a] = acc0[q];
             Y[(size_t)(i + q) * D + a + H] = acc1[q];
+        }
+    }
+}
+
+// Block-wide y_i = M x_i as mv_block, in double-FP32 arithmetic: M as (hi, lo)
+// float pairs (MT[b][a] = M[a][b]), x_i split into float halves Xh + Xl, one
+// output per thread and pass accumulated as an unnormalised pair (the
+// error-free product by FMA and Knuth's two-sum, as in the double-double
+// algorithms of Hida, Li and Bailey; relative error about D 2^-48).
+__device__ void mv_block_df(const float2* __restrict__ MT, int D, const float* Xh, const float* Xl,
+                            double* Y, int nv)
+{
+    const int G = (int)blockDim.x >= D ? (int)blockDim.x / D : 1;
+    for (int q = threadIdx.x; q < G * D; q += blockDim.x) {
+        const int a = q % D, g = q / D;
+        for (int i = g; i < nv; i += G) {
+            float hi = 0.f, lo = 0.f;
+            const float* xh = Xh + (size_t)i * D;
+            const float* xl = Xl + (size_t)i * D;
+            for (int b = 0; b < D; ++b) {
+                const float2 m = __ldg(MT + (size_t)b * D + a);
+                const float p = m.x * xh[b];
+                const float pe = fmaf(m.x, xh[b], -p) + fmaf(m.x, xl[b], m.y * xh[b]);
+                const float u = hi + p, z = u - hi;
+                lo += ((hi - (u - z)) + (p - z)) + pe;
+                hi = u;
+            }
+            Y[(size_t)i * D + a] = (double)hi + (double)lo;
         }
     }
 }
@@ -545,21 +573,9 @@ __global__ void k_fam_compact(FamArgs<T> f)
 // elements, a multiple of 32, so that every row starts on a 128-byte line)
 // ---------------------------------------------------------------------------
 
-// spin-orbital flips of the change of site s to its a-th alternative state
-// appended to `pk` one byte per flip: spin-orbital index, bit 7 set when the
-// orbital becomes occupied
-__device__ __forceinline__ int site_flips(uint64_t na, uint64_t nb, int s, int a, uint32_t& pk, int nf)
-{
-    const int own = sigma_at(na, nb, s);
-    const int to = sig_of_alt(a, own);
-    if ((own ^ to) & 1) { pk |= (uint32_t)(2 * s | ((to & 1) ? 0x80 : 0)) << (8 * nf); ++nf; }
-    if ((own ^ to) & 2) { pk |= (uint32_t)((2 * s + 1) | ((to & 2) ? 0x80 : 0)) << (8 * nf); ++nf; }
-    return nf;
-}
-
-// A correlator factor evaluated directly from theta + d (FP32): the rare units
-// whose addition-formula denominator is below 1/2 (out of line, so that the
-// common path keeps few registers)
+// A correlator factor evaluated directly from theta + d: the rare units whose
+// addition-formula denominator is below 1/2 (out of line, so that the common
+// path keeps few registers)
 __device__ __noinline__ void rbm_direct(bool left, float th, float t, float d, float& val, float& y)
 {
     const float em = expm1f(d);
@@ -568,9 +584,22 @@ __device__ __noinline__ void rbm_direct(bool left, float th, float t, float d, f
     val = left ? tanhf(th + d) : sh / (1.f + ch1);
     y = left ? ch1 + t * sh : ch1;
 }
+__device__ __noinline__ void rbm_direct(bool left, double th, double t, double d, double& val, double& y)
+{
+    const double em = expm1(d);
+    const double inv = 1.0 / (1.0 + em);
+    const double ch1 = 0.5 * em * em * inv, sh = 0.5 * em * (1.0 + inv);
+    val = left ? tanh(th + d) : sh / (1.0 + ch1);
+    y = left ? ch1 + t * sh : ch1;
+}
+
+__device__ __forceinline__ float div_fast(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double div_fast(double a, double b) { return a / b; }
+__device__ __forceinline__ const float4* site_table(const FamArgs<float>& f) { return f.csite; }
+__device__ __forceinline__ const double4_32a* site_table(const FamArgs<double>& f) { return f.csite64; }
 
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 2) k_fam_rbm(FamArgs<T> f)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_fam_rbm(FamArgs<T> f)
 {
     extern __shared__ __align__(1024) unsigned char smraw[];
     T* th_s = (T*)smraw;               // theta_k(n)
@@ -611,114 +640,79 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 2) k_fam_rbm(FamArgs
         const int RL = rbm_row_len(NH);
         T* out = (left ? f.rbl + (size_t)(lbase + oi) * RL : f.rbr + (size_t)(rbase + oi) * RL);
         T pm1 = T(0);
-        if constexpr (std::is_same<T, float>::value) {
-            // FP32: the object's change of theta is the sum of its sites' changes
-            // d1 (+ d2), whose tanh u and cosh - 1 c come from the per-site table.
-            // With t = tanh theta, s = u1 + u2, p = u1 u2 (0 for one site):
-            //   cosh(theta + d1 + d2) / (cosh theta cosh d1 cosh d2) = 1 + p + t s =: den
-            //   tanh(theta + d1 + d2) = (t + s + t p) / den,  tanh(d1 + d2) = s / (1 + p)
-            //   PL factor - 1 = (1 + e)(1 + p + t s) - 1,  PR factor - 1 = (1 + e)(1 + p) - 1
-            // with e = (1 + c1)(1 + c2) - 1. A denominator below 1/2 (|theta| and
-            // |d| both large) would lose bits to cancellation: such units take
-            // tanh and expm1 of theta + d directly.
-            const float4* r1 = f.csite + ((size_t)(s_hi * 4 + sigma_at(na, nb, s_hi)) * 3 + a_hi) * NP;
-            const float4* r2 = f.csite + ((size_t)(s_lo * 4 + sigma_at(na, nb, s_lo)) * 3 + a_lo) * NP;
-            // one loop per kind of object (left / right, one / two sites), each
-            // with only its own arithmetic; rare units with den < 1/2 take the
-            // direct evaluation
-            auto direct = [&](int k, float d, float& val, float& y) {
-                rbm_direct(left, th_s[k], tt_s[k], d, val, y);
-            };
-            if (!valid) {
-            } else if (left && ns == 2) {
-                for (int k = hl; k < NH; k += 16) {
-                    const float4 u = __ldg(r1 + k), v = __ldg(r2 + k);
-                    const float t = tt_s[k];
-                    const float sx = u.x + v.x, px = u.x * v.x;
-                    const float e = fmaf(u.y, v.y, u.y + v.y);
-                    const float den = fmaf(t, sx, 1.f + px);
-                    float val, y;
-                    if (den >= 0.5f) {
-                        const float g = fmaf(t, sx, px);
-                        val = __fdividef(fmaf(t, px, t + sx), den);
-                        y = fmaf(e, g, e + g);
-                    } else {
-                        direct(k, u.z + v.z, val, y);
-                    }
-                    out[k] = val;
-                    pm1 = fmaf(pm1, y, pm1 + y);
-                }
-            } else if (left) {
-                for (int k = hl; k < NH; k += 16) {
-                    const float4 u = __ldg(r1 + k);
-                    const float t = tt_s[k];
-                    const float den = fmaf(t, u.x, 1.f);
-                    float val, y;
-                    if (den >= 0.5f) {
-                        const float g = t * u.x;
-                        val = __fdividef(t + u.x, den);
-                        y = fmaf(u.y, g, u.y + g);
-                    } else {
-                        direct(k, u.z, val, y);
-                    }
-                    out[k] = val;
-                    pm1 = fmaf(pm1, y, pm1 + y);
-                }
-            } else if (ns == 2) {
-                for (int k = hl; k < NH; k += 16) {
-                    const float4 u = __ldg(r1 + k), v = __ldg(r2 + k);
-                    const float sx = u.x + v.x, px = u.x * v.x;
-                    const float e = fmaf(u.y, v.y, u.y + v.y);
-                    const float den = 1.f + px;
-                    float val, y;
-                    if (den >= 0.5f) {
-                        val = __fdividef(sx, den);
-                        y = fmaf(e, px, e + px);
-                    } else {
-                        direct(k, u.z + v.z, val, y);
-                    }
-                    out[k] = val;
-                    pm1 = fmaf(pm1, y, pm1 + y);
-                }
-            } else {
-                for (int k = hl; k < NH; k += 16) {          // tanh d1 and cosh d1 - 1 as stored
-                    const float4 u = __ldg(r1 + k);
-                    out[k] = u.x;
-                    pm1 = fmaf(pm1, u.y, pm1 + u.y);
-                }
-            }
-            for (int k = NH + ((hl - NH) % 16 + 16) % 16; valid && k < NP; k += 16) out[k] = 0.f;
-        } else {
-            uint32_t pk = 0;
-            int nf = 0;
-            if (ns >= 1) nf = site_flips(na, nb, s_hi, a_hi, pk, 0);
-            if (ns == 2) nf = site_flips(na, nb, s_lo, a_lo, pk, nf);
-            for (int k = hl; valid && k < NP; k += 16) {
-                if (k >= NH) { out[k] = T(0); continue; }
-                T d = T(0);
-                #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (q < nf) {
-                        const uint32_t fb = (pk >> (8 * q)) & 0xFFu;
-                        const T w = f.WT[(size_t)(fb & 0x7Fu) * NP + k];
-                        d += (fb & 0x80u) ? w : -w;
-                    }
-                }
-                // em = e^d - 1, inv = e^-d: cosh d - 1 = em^2 inv / 2, sinh d = em (1 + inv) / 2
-                const T em = expm1(d);
-                const T inv = T(1) / (T(1) + em);
-                const T ch1 = T(0.5) * em * em * inv, sh = T(0.5) * em * (T(1) + inv);
-                T y;
-                if (left) {
-                    out[k] = tanh(th_s[k] + d);
-                    y = ch1 + tt_s[k] * sh;             // cosh(theta + d) / cosh(theta) - 1
+        // The object's change of theta is the sum of its sites' changes d1 (+ d2),
+        // whose tanh u and cosh - 1 c come from the per-site table (FP32 or FP64
+        // as T). With t = tanh theta, s = u1 + u2, p = u1 u2 (0 for one site):
+        //   cosh(theta + d1 + d2) / (cosh theta cosh d1 cosh d2) = 1 + p + t s =: den
+        //   tanh(theta + d1 + d2) = (t + s + t p) / den,  tanh(d1 + d2) = s / (1 + p)
+        //   PL factor - 1 = (1 + e)(1 + p + t s) - 1,  PR factor - 1 = (1 + e)(1 + p) - 1
+        // with e = (1 + c1)(1 + c2) - 1. A denominator below 1/2 (|theta| and
+        // |d| both large) would lose bits to cancellation: such units take tanh
+        // and expm1 of theta + d directly. One loop per kind of object (left /
+        // right, one / two sites), each with only its own arithmetic.
+        typedef typename Vec4<T>::type V4;
+        const V4* tab = site_table(f);
+        const V4* r1 = tab + ((size_t)(s_hi * 4 + sigma_at(na, nb, s_hi)) * 3 + a_hi) * NP;
+        const V4* r2 = tab + ((size_t)(s_lo * 4 + sigma_at(na, nb, s_lo)) * 3 + a_lo) * NP;
+        if (!valid) {
+        } else if (left && ns == 2) {
+            for (int k = hl; k < NH; k += 16) {
+                const V4 u = r1[k], v = r2[k];
+                const T t = tt_s[k];
+                const T sx = u.x + v.x, px = u.x * v.x;
+                const T e = fma(u.y, v.y, u.y + v.y);
+                const T den = fma(t, sx, T(1) + px);
+                T val, y;
+                if (den >= T(0.5)) {
+                    const T g = fma(t, sx, px);
+                    val = div_fast(fma(t, px, t + sx), den);
+                    y = fma(e, g, e + g);
                 } else {
-                    out[k] = sh / (T(1) + ch1);         // tanh d
-                    y = ch1;                            // cosh d - 1
+                    rbm_direct(true, th_s[k], t, u.z + v.z, val, y);
                 }
+                out[k] = val;
                 pm1 = fma(pm1, y, pm1 + y);
             }
+        } else if (left) {
+            for (int k = hl; k < NH; k += 16) {
+                const V4 u = r1[k];
+                const T t = tt_s[k];
+                const T den = fma(t, u.x, T(1));
+                T val, y;
+                if (den >= T(0.5)) {
+                    const T g = t * u.x;
+                    val = div_fast(t + u.x, den);
+                    y = fma(u.y, g, u.y + g);
+                } else {
+                    rbm_direct(true, th_s[k], t, u.z, val, y);
+                }
+                out[k] = val;
+                pm1 = fma(pm1, y, pm1 + y);
+            }
+        } else if (ns == 2) {
+            for (int k = hl; k < NH; k += 16) {
+                const V4 u = r1[k], v = r2[k];
+                const T sx = u.x + v.x, px = u.x * v.x;
+                const T e = fma(u.y, v.y, u.y + v.y);
+                const T den = T(1) + px;
+                T val, y;
+                if (den >= T(0.5)) {
+                    val = div_fast(sx, den);
+                    y = fma(e, px, e + px);
+                } else {
+                    rbm_direct(false, th_s[k], tt_s[k], u.z + v.z, val, y);
+                }
+                out[k] = val;
+                pm1 = fma(pm1, y, pm1 + y);
+            }
+        } else {
+            for (int k = hl; k < NH; k += 16) {          // tanh d1 and cosh d1 - 1 as stored
+                const V4 u = r1[k];
+                out[k] = u.x;
+                pm1 = fma(pm1, u.y, pm1 + u.y);
+            }
         }
+        for (int k = NH + ((hl - NH) % 16 + 16) % 16; valid && k < NP; k += 16) out[k] = T(0);
         for (int o2 = 8; o2; o2 >>= 1) {
             const T z = __shfl_xor_sync(kFull, pm1, o2);
             pm1 = fma(pm1, z, pm1 + z);
@@ -729,7 +723,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 2) k_fam_rbm(FamArgs
 }
 
 // per-site factors of the FP32 correlator path (see fam_corr_sites)
-__global__ void k_corr_sites(const double* __restrict__ W, int K, int NH, int NP, float4* out)
+template <typename V4>
+__global__ void k_corr_sites(const double* __restrict__ W, int K, int NH, int NP, V4* out)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= K * 12 * NP) return;
@@ -744,15 +739,18 @@ __global__ void k_corr_sites(const double* __restrict__ W, int K, int NH, int NP
     // em = e^d - 1, inv = e^-d: cosh d - 1 = em^2 inv / 2, sinh d = em (1 + inv) / 2
     const double em = expm1(d), inv = 1.0 / (1.0 + em);
     const double ch1 = 0.5 * em * em * inv, sh = 0.5 * em * (1.0 + inv);
-    out[idx] = make_float4((float)(sh / (1.0 + ch1)), (float)ch1, (float)d, 0.f);
+    V4 o;
+    o.x = sh / (1.0 + ch1); o.y = ch1; o.z = d; o.w = 0.0;
+    out[idx] = o;
 }
 
-int fam_corr_sites(const double* W, int K, int n_hidden, float4* out, cudaStream_t st)
+int fam_corr_sites(const double* W, int K, int n_hidden, float4* out, double4_32a* out64, cudaStream_t st)
 {
     const int NP = (n_hidden + 3) & ~3, n = K * 12 * NP;
     if (n_hidden <= 0) return 0;
-    k_corr_sites<<<(n + 255) / 256, 256, 0, st>>>(W, K, n_hidden, NP, out);
-    return 1;
+    k_corr_sites<float4><<<(n + 255) / 256, 256, 0, st>>>(W, K, n_hidden, NP, out);
+    k_corr_sites<double4_32a><<<(n + 255) / 256, 256, 0, st>>>(W, K, n_hidden, NP, out64);
+    return 2;
 }
 
 // ---------------------------------------------------------------------------
@@ -972,7 +970,26 @@ __global__ void __launch_bounds__(256, 4) k_site_tiles(FamArgs<T> f, const SiteI
             sm.X[q] = s_src[i][c];
         }
         __syncthreads();
-        mv_block<T>((side == 0 ? f.AT : f.A) + ((size_t)t * 4 + sg) * D * D, D, sm.X, sm.Y, n);
+        if constexpr (std::is_same<T, double>::value) {
+            if (f.df) {
+                // the gathered rows as float halves in Y, the products back into X
+                float* Xh = (float*)sm.Y;
+                float* Xl = Xh + (size_t)n * D;
+                for (int q = threadIdx.x; q < n * D; q += blockDim.x) {
+                    const float h = (float)sm.X[q];
+                    Xh[q] = h;
+                    Xl[q] = (float)(sm.X[q] - (double)h);
+                }
+                __syncthreads();
+                mv_block_df((side == 0 ? f.ATdf : f.Adf) + ((size_t)t * 4 + sg) * D * D, D, Xh, Xl, sm.X, n);
+                __syncthreads();
+                for (int q = threadIdx.x; q < n * D; q += blockDim.x) sm.Y[q] = sm.X[q];
+            } else {
+                mv_block<T>((side == 0 ? f.AT : f.A) + ((size_t)t * 4 + sg) * D * D, D, sm.X, sm.Y, n);
+            }
+        } else {
+            mv_block<T>((side == 0 ? f.AT : f.A) + ((size_t)t * 4 + sg) * D * D, D, sm.X, sm.Y, n);
+        }
         __syncthreads();
         renorm_rows<T>(sm.Y, D, n, s_eo);
         __syncthreads();
@@ -1512,42 +1529,48 @@ __global__ void __launch_bounds__(kFamRows, MB) k_fam_rows(FamArgs<T> f, RowSet 
                 if (live) ratio *= T(1) + X;
             }
         } else {
-            // dot product with error-free product / sum transformations
+            // dot product: FP32 with error-free product / sum transformations; FP64
+            // with plain fused multiply-adds (its rounding, ~D 2^-53 of sum |x y|,
+            // is far inside the FP64 forms' bar)
+            constexpr bool dbl = std::is_same<T, double>::value;
+            auto acc = [&](T x, T y, T& sum, T& comp) {
+                if constexpr (dbl) {
+                    sum = fma(x, y, sum);
+                } else {
+                    const T pr = x * y;
+                    const T pe2 = fma(x, y, -pr);
+                    T t, e;
+                    two_sum(sum, pr, t, e);
+                    sum = t;
+                    comp += e + pe2;
+                }
+            };
             T sum = T(0), comp = T(0);
             if (live) {
                 if ((D & 3) == 0) {
                     typedef typename Vec4<T>::type V4;
                     for (int c4 = sub; c4 < D / 4; c4 += 8) {
                         const V4 x = ((const V4*)Lq)[c4], y = ((const V4*)Rq)[c4];
-                        const T xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
-                        #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const T pr = xs[u] * ys[u];
-                            const T pe2 = fma(xs[u], ys[u], -pr);
-                            T t, e;
-                            two_sum(sum, pr, t, e);
-                            sum = t;
-                            comp += e + pe2;
-                        }
+                        acc(x.x, y.x, sum, comp);
+                        acc(x.y, y.y, sum, comp);
+                        acc(x.z, y.z, sum, comp);
+                        acc(x.w, y.w, sum, comp);
                     }
                 } else {
-                    for (int c = sub; c < D; c += 8) {
-                        const T pr = Lq[c] * Rq[c];
-                        const T pe2 = fma(Lq[c], Rq[c], -pr);
-                        T t, e;
-                        two_sum(sum, pr, t, e);
-                        sum = t;
-                        comp += e + pe2;
-                    }
+                    for (int c = sub; c < D; c += 8) acc(Lq[c], Rq[c], sum, comp);
                 }
             }
             for (int o = 4; o; o >>= 1) {
                 const T so = __shfl_xor_sync(kFull, sum, o);
-                const T co = __shfl_xor_sync(kFull, comp, o);
-                T t, e;
-                two_sum(sum, so, t, e);
-                sum = t;
-                comp += co + e;
+                if constexpr (dbl) {
+                    sum += so;
+                } else {
+                    const T co = __shfl_xor_sync(kFull, comp, o);
+                    T t, e;
+                    two_sum(sum, so, t, e);
+                    sum = t;
+                    comp += co + e;
+                }
             }
             ratio = sum + comp;
             if (NH > 0) {

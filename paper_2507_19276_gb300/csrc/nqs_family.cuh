@@ -23,6 +23,9 @@ struct FamArgs {
     DevError* err;
     const T* A;               // [K][4][D][D] site tensors in T, A[a][b]
     const T* AT;              // transposed copy, AT[b][a]
+    int df;                   // FP64 tables only: CUDA-core mat-vecs in double-FP32 arithmetic
+    const float2* Adf;        // with df: A and AT as FP32 (hi, lo) pairs, hi + lo = the FP64 entry
+    const float2* ATdf;
     const uint64_t* samples;  // all samples of the call
     int64_t s0, s1;           // batch = samples [s0, s1)
     // table pool of the batch: rows of D elements (and one exponent each) for the
@@ -46,7 +49,8 @@ struct FamArgs {
     // correlator
     int n_hidden;
     const T* WT;              // [2K][NP] W transposed, zero-padded to NP = n_hidden rounded up to 4
-    const float4* csite;      // FP32 path: [K][4][3][NP] per-site factors (fam_corr_sites)
+    const float4* csite;      // [K][4][3][NP] per-site correlator factors, FP32 (fam_corr_sites)
+    const double4_32a* csite64;   // the same in FP64
     const double* theta;      // [Ns][n_hidden] (all samples)
     T* rbl; T* rbr;           // per-object correlator factors (see nqs_family.cu)
     const int64_t* rbl_base; const int64_t* rbr_base;   // [b] object offsets
@@ -97,11 +101,12 @@ template <typename T> int fam_site_step(const FamArgs<T>& f, const SiteBufs& b, 
                                         const int64_t* bounds, int max_ctas, cudaStream_t st);
 // the correlator factors alone (the site-synchronous path builds the tables)
 template <typename T> int fam_launch_rbm(const FamArgs<T>& f, int nb, cudaStream_t st);
-// per-site correlator factors of the FP32 path from W [n_hidden][2K] (device,
-// FP64): out[((p * 4 + own) * 3 + a) * NP + k] = {tanh d, cosh d - 1, d, 0},
-// d = the change of theta_k when site p goes from local state own to its a-th
-// alternative; NP = n_hidden rounded up to 4 (zero rows past n_hidden)
-int fam_corr_sites(const double* W, int K, int n_hidden, float4* out, cudaStream_t st);
+// per-site correlator factors from W [n_hidden][2K] (device, FP64), in FP32
+// (out) and FP64 (out64): [((p * 4 + own) * 3 + a) * NP + k] = {tanh d,
+// cosh d - 1, d, 0}, d = the change of theta_k when site p goes from local
+// state own to its a-th alternative; NP = n_hidden rounded up to 4 (zero rows
+// past n_hidden); returns launches
+int fam_corr_sites(const double* W, int K, int n_hidden, float4* out, double4_32a* out64, cudaStream_t st);
 
 // shared memory of the batch buffers of the site tiles
 // width of the reduction chunks of a tensor-core batch: the whole D up to 128,
