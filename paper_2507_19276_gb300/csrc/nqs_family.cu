@@ -530,27 +530,37 @@ __global__ void k_fam_compact(FamArgs<T> f)
     int* tll = f.tl_list + (size_t)b * nk;
     int* trl = f.tr_list + (size_t)b * nk;
     int carry_e = 0, carry_c = 0, carry_r = 0;
-    for (size_t k0 = 0; k0 < nk; k0 += blockDim.x) {
-        const size_t k = k0 + threadIdx.x;
-        int ce = 0, cc = 0, cr = 0, end = -1, flag = 0;
-        if (k < nk) {
-            end = te[k];
-            flag = tr[k];
+    // four consecutive keys per thread and pass: local prefixes, then one
+    // block scan of the thread totals per quantity
+    constexpr int Q = 4;
+    for (size_t k0 = 0; k0 < nk; k0 += (size_t)Q * blockDim.x) {
+        const size_t kb = k0 + (size_t)Q * threadIdx.x;
+        int end[Q], flag[Q], ce = 0, cc = 0, cr = 0;
+        #pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const size_t k = kb + j;
+            end[j] = -1; flag[j] = 0;
+            if (k < nk) { end[j] = te[k]; flag[j] = tr[k]; }
             const int s2 = (int)(k / (9 * (size_t)K));
-            ce = end >= 0 ? end - s2 + 1 : 0;
-            cc = end >= 0 ? 1 : 0;
-            cr = flag > 0 ? 1 : 0;
+            ce += end[j] >= 0 ? end[j] - s2 + 1 : 0;
+            cc += end[j] >= 0 ? 1 : 0;
+            cr += flag[j] > 0 ? 1 : 0;
         }
         int xe, xc, xr;
         const int te_tot = block_excl_scan(ce, &xe, wt);
         const int tc_tot = block_excl_scan(cc, &xc, wt);
         const int tr_tot = block_excl_scan(cr, &xr, wt);
-        if (k < nk) {
-            tl[k] = end >= 0 ? carry_e + xe : -1;
-            tci[k] = end >= 0 ? carry_c + xc : -1;
-            if (end >= 0) tll[carry_c + xc] = (int)k;
-            tr[k] = flag > 0 ? carry_r + xr : -1;
-            if (flag > 0) trl[carry_r + xr] = (int)k;
+        int pe = carry_e + xe, pc = carry_c + xc, pr = carry_r + xr;
+        #pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            const size_t k = kb + j;
+            if (k >= nk) break;
+            const int s2 = (int)(k / (9 * (size_t)K));
+            tl[k] = end[j] >= 0 ? pe : -1;
+            tci[k] = end[j] >= 0 ? pc : -1;
+            if (end[j] >= 0) { tll[pc] = (int)k; pe += end[j] - s2 + 1; ++pc; }
+            tr[k] = flag[j] > 0 ? pr : -1;
+            if (flag[j] > 0) { trl[pr] = (int)k; ++pr; }
         }
         carry_e += te_tot;
         carry_c += tc_tot;
@@ -769,8 +779,15 @@ __global__ void __launch_bounds__(256) k_site_build(FamArgs<T> f, SiteBufs sb)
     const int nbb = (int)(f.s1 - f.s0);
     const int64_t s = f.s0 + b;
     const uint64_t na = f.samples[2 * s], nb = f.samples[2 * s + 1];
-    for (int i = threadIdx.x; i < K * 8; i += blockDim.x) cnt[i] = 0;
     for (int i = threadIdx.x; i < K; i += blockDim.x) own[i] = sigma_at(na, nb, i);
+    __syncthreads();
+    // the 3 tau one-change families of each side that step tau advances take
+    // the first slots of their group (part 1 below); the other items follow
+    for (int i = threadIdx.x; i < K * 8; i += blockDim.x) {
+        const int tau = i >> 3, g = i & 7, side = g >> 2;
+        const int t = side == 0 ? tau : K - 1 - tau;
+        cnt[i] = (g & 3) == own[t] ? 3 * tau : 0;
+    }
     __syncthreads();
     const size_t nk = (size_t)K * K * 9;
     // pool rows of this sample's G and H families
@@ -785,19 +802,21 @@ __global__ void __launch_bounds__(256) k_site_build(FamArgs<T> f, SiteBufs sb)
         }
     };
     // (1) families created before the step (k_site_boundary makes the new ones
-    // at their first site): thread per (step, side)
-    for (int w = threadIdx.x; w < 2 * K; w += blockDim.x) {
-        const int tau = w >> 1, side = w & 1;
+    // at their first site): family (j, a) of step tau at slot 3 j + a of its
+    // group, one (side, step, j) per thread, so that a warp's items are adjacent
+    for (int q = threadIdx.x; FILL && q < 2 * K * K; q += blockDim.x) {
+        const int side = q / (K * K), rem = q - side * K * K, tau = rem / K, j = rem - tau * K;
+        if (j >= tau) continue;
         const int t = side == 0 ? tau : K - 1 - tau;
-        const int o = own[t];
         const int64_t Tr = side == 0 ? Gr : Hr;
         const int tp = side == 0 ? t - 1 : t + 1;      // the family's previous site
-        for (int j = 0; j < tau; ++j) {
-            const int sf = side == 0 ? j : K - 1 - j;
-            for (int a = 0; a < 3; ++a) {
-                const int64_t base = Tr + ((int64_t)a * K + sf) * K;
-                put(tau, side * 4 + o, base + tp, base + t);
-            }
+        const int sf = side == 0 ? j : K - 1 - j;
+        const int64_t at = sb.offs[((int64_t)tau * 8 + side * 4 + own[t]) * nbb + b] + 3 * j;
+        for (int a = 0; a < 3; ++a) {
+            const int64_t base = Tr + ((int64_t)a * K + sf) * K;
+            SiteItem it;
+            it.src = (uint32_t)(base + tp); it.dst = (uint32_t)(base + t);
+            ((SiteItem*)sb.items)[at + a] = it;
         }
     }
     // (2) TL clusters: creation at s2 with A_{s2}^{a2}, then A_t^{own} up to the last use
