@@ -518,7 +518,7 @@ __device__ int block_excl_scan(int v, int* ex, int* wt)
 //   tl_ci[key]  = cluster index (TL list position), tl_list[ci] = key,
 //   tr_idx[key] = TR row index, tr_list[row] = key; -1 where unused.
 template <typename T>
-__global__ void k_fam_compact(FamArgs<T> f)
+__global__ void __launch_bounds__(1024, 2) k_fam_compact(FamArgs<T> f)
 {
     __shared__ int wt[32];
     const int b = blockIdx.x, K = f.K;
@@ -530,9 +530,9 @@ __global__ void k_fam_compact(FamArgs<T> f)
     int* tll = f.tl_list + (size_t)b * nk;
     int* trl = f.tr_list + (size_t)b * nk;
     int carry_e = 0, carry_c = 0, carry_r = 0;
-    // four consecutive keys per thread and pass: local prefixes, then one
+    // two consecutive keys per thread and pass: local prefixes, then one
     // block scan of the thread totals per quantity
-    constexpr int Q = 4;
+    constexpr int Q = 2;
     for (size_t k0 = 0; k0 < nk; k0 += (size_t)Q * blockDim.x) {
         const size_t kb = k0 + (size_t)Q * threadIdx.x;
         int end[Q], flag[Q], ce = 0, cc = 0, cr = 0;
