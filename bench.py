@@ -136,8 +136,9 @@ def enum_bytes(K, na, nb, n_samples, n_det):
 # evaluated (None where not measured).
 STAGE_TRAFFIC_PER_AMP = {"mixed": 328.5, "fp64_shared": None}
 
-DTYPES = {"mixed": "f16x3 tensor-core products (f32 accumulate) + f32 gathers; f64 H, psi(n), "
-                   "ratios, sums; heaviest samples re-evaluated in f64 to the energy tolerance",
+DTYPES = {"mixed": "f16x3 tensor-core products (f32 accumulate) + f32 gathers; f64 H, ratios, sums; "
+                   "psi(n) in double-f32; heaviest samples re-evaluated (f64, tables in double-f32) "
+                   "to the energy tolerance",
           "fp64_shared": "f64", "fp64": "f64"}
 
 

@@ -94,8 +94,10 @@ typedef struct {
     double energy_tolerance;    /* mixed form: bound (Ha) on the error of the
                              weighted energy sum c E_loc / sum c that
                              nqs_local_energy meets by re-evaluating samples in
-                             FP64 (the shared-prefix form for chains, the plain
-                             form for graphs). The
+                             FP64 (the shared-prefix form for chains, whose
+                             tables then advance in double-FP32 arithmetic,
+                             about 2^-44 per product; the plain form for
+                             graphs). The
                              per-sample error of the mixed form relative to
                              e_abs = |H_nn| + sum |terms| is taken as a factor f
                              (1e-6 to start: what the parity tests hold the mixed
