@@ -12,6 +12,11 @@ definitions (the GPU parity tests then check the kernels themselves).
   PL = prod cosh(theta + dL) / cosh(theta) and PR = prod cosh(dR).
 * The product recursion X <- X + y + X y carries prod (1 + y) - 1 without
   cancellation near 1.
+* The per-site correlator table: an object's factors from the tanh and
+  cosh - 1 of its one or two site changes by the addition formulas, in FP64
+  and in FP32 where the kernel uses them (denominator >= 1/2).
+* Double-FP32 dot products (psi(n) of the mixed form, the re-evaluation's
+  tables) within D 2^-46 of sum |m x|.
 """
 import math
 import random
@@ -142,3 +147,104 @@ def test_series_for_cosh_and_sinh_in_float32():
     nz = D != 0
     assert np.max(np.abs(ch1[nz] - ref_ch1[nz]) / ref_ch1[nz]) < 4 * 2.0 ** -24
     assert np.max(np.abs(sh[nz] - ref_sh[nz]) / np.abs(ref_sh[nz])) < 4 * 2.0 ** -24
+
+
+def _site_factors(d):
+    """tanh d and cosh d - 1 (the per-site table entries), FP64."""
+    return np.tanh(d), 2.0 * np.sinh(d / 2) ** 2
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_site_table_addition_formulas(seed):
+    """The per-site correlator table (Eq. RBM): an object's factors from the
+    tanh u and cosh - 1 c of its one or two site changes d1, d2:
+      den = 1 + p + t s, s = u1 + u2, p = u1 u2, t = tanh theta,
+      tanh(theta + d1 + d2) = (t + s + t p) / den,
+      cosh(theta + d1 + d2) / cosh(theta) - 1 = (1 + e) den - 1,
+      tanh(d1 + d2) = s / (1 + p),  cosh(d1 + d2) - 1 = (1 + e)(1 + p) - 1,
+    with e = (1 + c1)(1 + c2) - 1 (d2 = 0 gives the one-site forms)."""
+    rng = np.random.default_rng(seed)
+    n = 20000
+    theta = rng.normal(0, 1.5, n)
+    for scale in (0.01, 0.3, 1.5):
+        d1 = rng.normal(0, scale, n)
+        d2 = np.where(rng.random(n) < 0.3, 0.0, rng.normal(0, scale, n))
+        (u1, c1), (u2, c2) = _site_factors(d1), _site_factors(d2)
+        t = np.tanh(theta)
+        s, p = u1 + u2, u1 * u2
+        e = c1 + c2 + c1 * c2
+        den = 1 + p + t * s
+        assert np.all(den > 0)
+        d = d1 + d2
+        # rounding grows as 1 / den (the cancellation the kernel's den >= 1/2 test avoids)
+        err = np.abs((t + s + t * p) / den - np.tanh(theta + d))
+        assert np.all(err <= 1e-14 / den)
+        assert np.max(err[den >= 0.5]) <= 16 * 2.0 ** -53
+        ref_pl = np.expm1(np.log(np.cosh(theta + d)) - np.log(np.cosh(theta)))
+        g = t * s + p                         # den - 1 formed directly, as the kernel does
+        np.testing.assert_allclose(e + g + e * g, ref_pl, rtol=1e-10, atol=1e-13)
+        np.testing.assert_allclose(s / (1 + p), np.tanh(d), rtol=0, atol=1e-13)
+        # formed as e + p + e p (the kernel's order); when opposite changes cancel
+        # the error is absolute, relative to the factor PR itself (~1)
+        np.testing.assert_allclose(e + p + e * p, 2.0 * np.sinh(d / 2) ** 2, rtol=1e-10, atol=1e-13)
+
+
+def test_site_table_formulas_in_float32_above_the_threshold():
+    """The FP32 kernel evaluates the left factors from FP32-rounded table
+    entries only when den >= 1/2 (else directly from theta + d): there the
+    tanh and P - 1 terms stay within a few FP32 units of the FP64 values."""
+    f = np.float32
+    rng = np.random.default_rng(9)
+    n = 50000
+    theta = rng.normal(0, 1.5, n)
+    d1, d2 = rng.normal(0, 0.3, n), rng.normal(0, 0.3, n)
+    (u1, c1), (u2, c2) = _site_factors(d1), _site_factors(d2)
+    t = np.tanh(theta).astype(f)
+    u1, c1, u2, c2 = (x.astype(f) for x in (u1, c1, u2, c2))
+    s, p = u1 + u2, u1 * u2
+    e = c1 + c2 + c1 * c2
+    den = t * s + (f(1) + p)
+    keep = den >= f(0.5)
+    assert keep.mean() > 0.95
+    val = (t * p + (t + s)) / den
+    g = t * s + p
+    y = e * g + (e + g)
+    d = d1 + d2
+    ref_t = np.tanh(theta + d)
+    ref_y = np.expm1(np.log(np.cosh(theta + d)) - np.log(np.cosh(theta)))
+    assert np.max(np.abs(val[keep] - ref_t[keep])) < 16 * 2.0 ** -24
+    assert np.max(np.abs(y[keep] - ref_y[keep]) / (1 + np.abs(ref_y[keep]))) < 16 * 2.0 ** -24
+
+
+def _fmaf(a, b, c):
+    """float32 fused multiply-add (the product of two floats is exact in FP64)."""
+    return np.float32(np.float64(a) * np.float64(b) + np.float64(c))
+
+
+def test_double_float_dot_products():
+    """psi(n) of the mixed form and the re-evaluation's tables use double-FP32
+    dot products: matrix and vector as (hi, lo) float pairs, each term the
+    error-free product by FMA plus the cross terms, summed with Knuth's
+    two-sum into an unnormalised pair. Emulated here in float32 with the
+    kernels' operation order: the result is within D 2^-46 of sum |m x| of
+    the exact FP64 dot product."""
+    f = np.float32
+    rng = np.random.default_rng(11)
+    for D in (32, 64, 256):
+        for _ in range(20):
+            m = rng.normal(0, 1, D)
+            x = rng.normal(0, 1, D) * np.exp(rng.normal(0, 2, D))
+            mh = m.astype(f); ml = (m - mh.astype(np.float64)).astype(f)
+            xh = x.astype(f); xl = (x - xh.astype(np.float64)).astype(f)
+            hi, lo = f(0), f(0)
+            for k in range(D):
+                pr = f(mh[k] * xh[k])
+                pe = f(_fmaf(mh[k], xh[k], -pr) + _fmaf(mh[k], xl[k], f(ml[k] * xh[k])))
+                u = f(hi + pr)
+                z = f(u - hi)
+                lo = f(lo + f(f(f(hi - f(u - z)) + f(pr - z)) + pe))
+                hi = u
+            got = float(hi) + float(lo)
+            exact = math.fsum(float(a) * float(b) for a, b in zip(m, x))
+            scale = math.fsum(abs(float(a) * float(b)) for a, b in zip(m, x))
+            assert abs(got - exact) <= D * 2.0 ** -46 * scale
