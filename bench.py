@@ -404,9 +404,9 @@ def run(args):
                            "k_site_build, k_site_tiles_pipe (tcgen05), k_fam_rbm, k_fam_rows")}
     else:
         roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved,
-                "peak": live["fma64_tflops"] if live else 1.196,
+                "peak": live["fma64_tflops"] if live else 1.056,
                 "peak_source": ("FP64 FMA rate measured before the timed region (peaks probe)" if live
-                                else "FP64 FMA rate of an earlier probe run on this pool's GB300"),
+                                else "FP64 FMA rate of an earlier peaks-probe run on a GB300"),
                 "kernel": ("amplitude stage (shared prefixes, FP64)" if prec == nqs.NQS_PREC_FP64_SHARED
                            else "k_amp_chain_fp64 / k_amp_graph_fp64 (one amplitude per row)")}
     roof["frac"] = roof["achieved"] / roof["peak"]
@@ -586,7 +586,7 @@ def run_rnn(args):
     D = sys_.D
     amp_ms = (stages["amp_det"][0] + stages["amp_draw"][0]) / args.steps
     flops = work["span_sites"] * (4 * 2.0 * D * D + 4 * 3.0 * D)
-    peak = live["fma64_tflops"] if live else 1.196
+    peak = live["fma64_tflops"] if live else 1.056
     roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": flops / (amp_ms / 1e3) / 1e12, "peak": peak,
             "peak_source": "FP64 FMA rate measured before the timed region (peaks probe)" if live
             else "FP64 FMA rate of an earlier probe run on this pool's GB300",

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kEnumWarps * 32) k_enum(EnumArgs a)
         }
         if (a.chunk_w) {
             uint64_t w = (valid && !det) ? weight_of(H, a.shift) : 0ull;
-            w = warp_sum_sliced(w);
+            w = a.h.bitlen_nconn >= 15 ? warp_sum_sliced2(w) : warp_sum_sliced(w);
             if (lane == 0) a.chunk_w[srow + c] = w;
         }
     };
@@ -103,7 +103,7 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int k)
     return pos + (k >= (int)(m & 1u) ? 1 : 0);
 }
 
-__global__ void __launch_bounds__(kEnumWarps * 32, 4) k_write_dets(EnumArgs a)
+__global__ void __launch_bounds__(kEnumWarps * 32, 5) k_write_dets(EnumArgs a)
 {
     __shared__ OrbLists lists;
     const int s = a.s0 + blockIdx.y;

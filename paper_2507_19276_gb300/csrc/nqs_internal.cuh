@@ -293,6 +293,15 @@ __device__ __forceinline__ uint64_t warp_sum_sliced(uint64_t v)
     return (uint64_t)s0 + ((uint64_t)s1 << 24) + ((uint64_t)s2 << 48);
 }
 
+// The same for v < 2^48 (the remainder weights when n_conn >= 2^14, each at
+// most 2^(62 - bitlen(n_conn))): two 24-bit slices.
+__device__ __forceinline__ uint64_t warp_sum_sliced2(uint64_t v)
+{
+    const unsigned s0 = __reduce_add_sync(kFull, (unsigned)(v & 0xFFFFFFu));
+    const unsigned s1 = __reduce_add_sync(kFull, (unsigned)(v >> 24));
+    return (uint64_t)s0 + ((uint64_t)s1 << 24);
+}
+
 __device__ __forceinline__ double warp_sum_f64(double v)
 {
     for (int o = 16; o; o >>= 1) v += __shfl_down_sync(kFull, v, o);
