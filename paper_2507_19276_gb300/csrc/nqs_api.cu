@@ -44,8 +44,9 @@ struct nqs_ctx {
     bool has_ans = false;
     AnsatzView av{};
     DevBuf A, AT, W, b, pred_ptr, pred_idx;
-    DevBuf WT;                // W transposed, [2K][n_hidden rounded up to 4], zero-padded
-    DevBuf Af, ATf, WTf;      // FP32 copies for the shared-prefix FP32 path
+    DevBuf Af, ATf;           // FP32 copies for the shared-prefix FP32 path
+    DevBuf WTf;               // W transposed in FP32, [2K][n_hidden rounded up to 4], zero-padded
+                              // (the graph tiles' correlator)
     DevBuf csite, csite64;    // per-site correlator factors, FP32 and FP64 (fam_corr_sites)
     DevBuf ATdf, Adf;         // chain: AT and A as FP32 (hi, lo) pairs (double-FP32 arithmetic)
     bool refine_df = false;   // FP64 tables of the error-budgeted re-evaluation: double-FP32 mat-vecs
@@ -640,7 +641,6 @@ int family_pass(nqs_ctx* c, const uint64_t* ds, int64_t Ns, int64_t total_det, i
     f.ATdf = (const float2*)c->ATdf.p;
     f.samples = ds;
     f.n_hidden = c->av.n_hidden;
-    f.WT = (const T*)(dbl ? c->WT.p : c->WTf.p);
     f.csite = (const float4*)c->csite.p;
     f.csite64 = (const double4_32a*)c->csite64.p;
     f.theta = (const double*)c->theta.p;
@@ -803,7 +803,7 @@ extern "C" int nqs_destroy(nqs_ctx* c)
                       &c->draw_rank, &c->draw_coef, &c->n_unique, &c->base_det, &c->base_draw,
                       &c->part_det, &c->part_draw, &c->eloc, &c->edet, &c->estoch, &c->summary,
                       &c->derr, &c->span_det, &c->span_draw, &c->Af, &c->ATf,
-                      &c->WT, &c->WTf, &c->csite, &c->csite64, &c->ATdf, &c->Adf, &c->fpool, &c->fpoole, &c->ftl_end,
+                      &c->WTf, &c->csite, &c->csite64, &c->ATdf, &c->Adf, &c->fpool, &c->fpoole, &c->ftl_end,
                       &c->ftl_idx, &c->ftr_idx, &c->ftl_tot, &c->ftr_tot, &c->ftl_base,
                       &c->ftr_base, &c->ftl_ci,
                       &c->ftl_list, &c->ftr_list, &c->ftl_cnt, &c->frbl, &c->frbr, &c->frbl_base,
@@ -1035,20 +1035,15 @@ extern "C" int nqs_set_ansatz(nqs_ctx* c, const double* site_tensors, int n_edge
             CK(cudaMemcpy(c->Adf.p, dA.data(), nt * 8, cudaMemcpyHostToDevice));
         }
         if (n_hidden > 0) {
-            // transposed copies for the correlator factors: lanes over hidden units
-            // read consecutive words of one spin-orbital's column
+            // transposed FP32 copy for the graph tiles' correlator: lanes over hidden
+            // units read consecutive words of one spin-orbital's column
             const size_t nw = (size_t)n_hidden * 2 * K, np = (size_t)((n_hidden + 3) & ~3);
-            std::vector<double> hW(nw), hWT((size_t)2 * K * np, 0.0);
+            std::vector<double> hW(nw);
             CK(cudaMemcpy(hW.data(), c->W.p, nw * 8, cudaMemcpyDeviceToHost));
-            std::vector<float> fWT(hWT.size(), 0.0f);
+            std::vector<float> fWT((size_t)2 * K * np, 0.0f);
             for (int k = 0; k < n_hidden; ++k)
-                for (int q = 0; q < 2 * K; ++q) {
-                    hWT[(size_t)q * np + k] = hW[(size_t)k * 2 * K + q];
-                    fWT[(size_t)q * np + k] = (float)hW[(size_t)k * 2 * K + q];
-                }
-            TRY(ensure(c, c->WT, hWT.size() * 8));
+                for (int q = 0; q < 2 * K; ++q) fWT[(size_t)q * np + k] = (float)hW[(size_t)k * 2 * K + q];
             TRY(ensure(c, c->WTf, fWT.size() * 4));
-            CK(cudaMemcpy(c->WT.p, hWT.data(), hWT.size() * 8, cudaMemcpyHostToDevice));
             CK(cudaMemcpy(c->WTf.p, fWT.data(), fWT.size() * 4, cudaMemcpyHostToDevice));
             TRY(ensure(c, c->csite, (size_t)K * 12 * np * 16));
             TRY(ensure(c, c->csite64, (size_t)K * 12 * np * 32));

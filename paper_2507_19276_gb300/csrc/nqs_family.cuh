@@ -48,7 +48,6 @@ struct FamArgs {
     T* TR; int* TRe;          // packed TR rows
     // correlator
     int n_hidden;
-    const T* WT;              // [2K][NP] W transposed, zero-padded to NP = n_hidden rounded up to 4
     const float4* csite;      // [K][4][3][NP] per-site correlator factors, FP32 (fam_corr_sites)
     const double4_32a* csite64;   // the same in FP64
     const double* theta;      // [Ns][n_hidden] (all samples)
