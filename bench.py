@@ -133,8 +133,10 @@ def enum_bytes(K, na, nb, n_samples, n_det):
 # DRAM bytes (read + write) per evaluated amplitude of the amplitude stage,
 # summed over its kernels, from ncu counters on the H50 shape (D = 64) with
 # 512 samples; the stage's traffic grows in proportion to the amplitudes
-# evaluated (None where not measured).
-STAGE_TRAFFIC_PER_AMP = {"mixed": 328.5, "fp64_shared": None}
+# evaluated. None where not measured, or where the stage's kernels changed
+# after the counters were taken (the mixed form's correlator factors, marks
+# and row kernel have since; 328.5 B per amplitude was the earlier figure).
+STAGE_TRAFFIC_PER_AMP = {"mixed": None, "fp64_shared": None}
 
 DTYPES = {"mixed": "f16x3 tensor-core products (f32 accumulate) + f32 gathers; f64 H, ratios, sums; "
                    "psi(n) in double-f32; heaviest samples re-evaluated (f64, tables in double-f32) "
